@@ -1,0 +1,395 @@
+#!/usr/bin/env python3
+"""Benchmark: one full compressive-PCA pass per step on the 10304 x 1000
+workload (rank 10, 10 clusters, 5% gross errors, K = 10 graphs, 1/4 of the
+rows and columns sampled, 300 FISTA iterations, PCG decoder to 1e-6).
+
+A step runs every hot-path stage through the C ABI: the two full kNN graphs
+and Laplacians, sampling + gather, the two compressed graphs, the power
+iterations for lambda, 300 FISTA iterations, and the approximate decoder
+(partial SVD, PCG upsampling of U and V, rank-k output X).
+
+Prints ONE JSON line (rank 0). ``--impl reference`` times the FP64 oracle
+on the host instead (bounded sample of the same workload).
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl cpca|reference]
+Multi-GPU (torchrun): every rank runs an independent replica (the workload
+is one instance; there is no data exchange), value = total FISTA iterations
+of all ranks / the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+# The oracle baseline is single-threaded by construction; pin BLAS threads
+# before numpy loads so the reported core count is what ran.
+for _v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+    os.environ.setdefault(_v, "1")
+
+import numpy as np  # noqa: E402
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import gen  # noqa: E402
+
+METRIC = "wall-time to 1e-4 rel err vs plain GPU; FISTA/CG iters/s; % of HBM peak"
+UNIT = "FISTA iters/s"
+WORKLOAD = "c1"
+L2_FLUSH_BYTES = 256 << 20
+
+
+def load_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return None
+
+
+# ----------------------------------------------------------- clock sampling
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(rows)}
+
+
+# ---------------------------------------------------------------- oracle arm
+def oracle_step_seconds(Y, cfg, n_query: int, dec_graphs, rng_seed: int = 0):
+    """Seconds the FP64 oracle needs for one full pipeline step, measured on
+    a bounded sample: the two full-graph kNN searches are timed on n_query
+    sampled query points each and scaled to all points; sampling, the
+    compressed graphs, the power iterations, all FISTA iterations and the
+    decoder (SVD + PCG + output) run in full."""
+    import oracle as O
+    p, n = Y.shape
+    K, J = cfg["K"], cfg["J"]
+    rng = np.random.default_rng(rng_seed)
+    t_knn = 0.0
+    Yd = Y.astype(np.float64)
+    for P in (Yd, Yd.T):
+        N = P.shape[0]
+        qs = rng.choice(N, size=min(n_query, N), replace=False)
+        t0 = time.perf_counter()
+        O.knn_bruteforce(P, K, queries=qs)
+        t_knn += (time.perf_counter() - t0) * N / len(qs)
+    rr, rc = int(p * cfg["fr"] + 0.5), int(n * cfg["fc"] + 0.5)
+    t0 = time.perf_counter()
+    # Laplacians of the full graphs: same O(N K) construction as below, timed
+    # on the compressed kNN lists and scaled by the point count
+    om_r, om_c = O.sample_indices(0, p, rr, 0), O.sample_indices(0, n, rc, 1)
+    Yt = Yd[np.ix_(om_r, om_c)]
+    Lrt, _, ir, dr, _ = O.knn_graph(Yt, K)
+    Lct, _, ic, dc, _ = O.knn_graph(Yt.T, K)
+    t_small = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    O.laplacian_from_knn(ir, dr, rr, O.sigma2_mean(dr))
+    t_lap = (time.perf_counter() - t0) * (p + n) / rr
+    t0 = time.perf_counter()
+    lam = O.fista_step(cfg["gamma_r"], cfg["gamma_c"], O.power_norm(Lrt, 200, 0, 2),
+                       O.power_norm(Lct, 200, 0, 3))
+    Xt, _ = O.frpcag_fista(Yt, Lrt, Lct, cfg["gamma_r"], cfg["gamma_c"], lam, J)
+    t_fista = time.perf_counter() - t0
+    Lr, Lc = dec_graphs
+    t0 = time.perf_counter()
+    O.approx_decode(Xt, om_r, om_c, p, n, Lr, Lc, tol=cfg["cg_tol"])
+    t_dec = time.perf_counter() - t0
+    return t_knn + t_lap + t_small + t_fista + t_dec
+
+
+def decoder_graphs_for_timing(Y, K):
+    """Full-size graphs for timing the oracle's decoder (setup, untimed):
+    exact kNN lists from a blocked matmul ranking, then the oracle's own
+    Laplacian construction. Only a timing input, never a parity input."""
+    import oracle as O
+    out = []
+    Yd = Y.astype(np.float64)
+    for P in (Yd, Yd.T):
+        N = P.shape[0]
+        nrm = np.einsum("ij,ij->i", P, P)
+        idx = np.empty((N, K), dtype=np.int64)
+        d2 = np.empty((N, K))
+        for a in range(0, N, 1024):
+            D = nrm[a:a + 1024, None] + nrm[None, :] - 2.0 * (P[a:a + 1024] @ P.T)
+            D[np.arange(D.shape[0]), np.arange(a, a + D.shape[0])] = np.inf
+            part = np.argpartition(D, K, axis=1)[:, :K]
+            dd = np.take_along_axis(D, part, 1)
+            o = np.argsort(dd, axis=1)
+            idx[a:a + 1024] = np.take_along_axis(part, o, 1)
+            d2[a:a + 1024] = np.take_along_axis(dd, o, 1)
+        L, _ = O.laplacian_from_knn(idx, np.maximum(d2, 0), N, float(np.mean(np.maximum(d2, 0))))
+        out.append(L)
+    return out
+
+
+def cpu_sample_text(nq):
+    return (f"full-graph kNN brute force timed on {nq} sampled query points per graph and scaled to "
+            "all points; Laplacian construction timed on the compressed graph and scaled by point "
+            "count; sampling, compressed kNN graphs, power iterations, all 300 FISTA iterations and "
+            "the decoder (SVD, PCG, output) in full")
+
+
+def run_reference(args, cfg, Y):
+    dec = decoder_graphs_for_timing(Y, cfg["K"])
+    nq = 8
+    for _ in range(args.warmup):
+        oracle_step_seconds(Y, cfg, nq, dec)
+    secs = [oracle_step_seconds(Y, cfg, nq, dec, rng_seed=s + 1) for s in range(args.steps)]
+    tot = float(sum(secs))
+    value = cfg["J"] * args.steps / tot
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * tot / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": config_dict(cfg),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": cpu_sample_text(nq)},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def config_dict(cfg):
+    return {"workload": f"CPCA {cfg['p']}x{cfg['n']} rank {cfg['r']}, {cfg['C']} clusters, "
+                        f"{int(cfg['frac'] * 100)}% gross errors, K={cfg['K']}, sample "
+                        f"{cfg['fr']}x{cfg['fc']}, {cfg['J']} FISTA iterations, PCG tol {cfg['cg_tol']}",
+            "p": cfg["p"], "n": cfg["n"], "rank": cfg["r"], "K": cfg["K"],
+            "rho_r": int(cfg["p"] * cfg["fr"] + 0.5), "rho_c": int(cfg["n"] * cfg["fc"] + 0.5),
+            "fista_iters": cfg["J"], "gamma_r": cfg["gamma_r"], "gamma_c": cfg["gamma_c"],
+            "l2": f"flushed between timed steps ({L2_FLUSH_BYTES >> 20} MiB write)",
+            "parallelism": "replicas"}
+
+
+# ------------------------------------------------------------------- GPU arm
+def roofline_for(name, ms, launches, ctx, peaks):
+    """Algorithmic work of the named kernel over the timed region / its time."""
+    hbm = peaks["hbm_gbs"] if peaks else 6800.0
+    src = "measured" if peaks else "fallback"
+    sec = ms / 1000.0
+    if name == "fista_iter":
+        byts = ctx["fista_bytes_per_launch"] * launches
+        a = byts / sec / 1e9
+        return {"kernel": name, "bound": "hbm", "achieved": a, "peak": hbm, "unit": "GB/s",
+                "frac": a / hbm, "traffic": None, "peak_source": src,
+                "note": "20 B per entry of Y~ + CSR bytes per iteration; working set L2-resident at this size"}
+    if name.startswith("knn_candidates"):
+        fl = ctx["knn_flops_per_step"] * ctx["steps"]
+        a = fl / sec / 1e12
+        if name.endswith("_tc"):
+            pk = (peaks["bf16_tflops"] if peaks else 1900.0) * (1.1 / 2.25)
+            return {"kernel": name, "bound": "tensor", "achieved": a, "peak": pk, "unit": "TFLOP/s",
+                    "frac": a / pk, "traffic": None, "peak_source": f"tf32 = {src} bf16 x 1.1/2.25"}
+        pk = ctx["fp32_simt_tflops"]
+        return {"kernel": name, "bound": "alu", "achieved": a, "peak": pk, "unit": "TFLOP/s",
+                "frac": a / pk, "traffic": None,
+                "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz"}
+    if name == "cg_pcg":
+        byts = ctx["cg_bytes_per_iter"] * ctx["cg_iters"] * ctx["steps"]
+        a = byts / sec / 1e9
+        return {"kernel": name, "bound": "hbm", "achieved": a, "peak": hbm, "unit": "GB/s",
+                "frac": a / hbm, "traffic": None, "peak_source": src}
+    if name == "decode_output":
+        a = ctx["out_bytes"] * launches / sec / 1e9
+        return {"kernel": name, "bound": "hbm", "achieved": a, "peak": hbm, "unit": "GB/s",
+                "frac": a / hbm, "traffic": None, "peak_source": src}
+    return {"kernel": name, "bound": "hbm", "achieved": None, "peak": hbm, "unit": "GB/s",
+            "frac": None, "traffic": None, "peak_source": src}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="cpca", choices=["cpca", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-queries", type=int, default=32)
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 0)
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    cfg = dict(gen.CONFIGS[WORKLOAD])
+    Y, _, _ = gen.make_instance(0, cfg["p"], cfg["n"], cfg["r"], cfg["C"], cfg["frac"])
+
+    if args.impl == "reference":
+        if rank == 0:
+            run_reference(args, cfg, Y)
+        return
+
+    import torch
+    import paper_1602_02070_gb300 as M
+
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    M.lib()
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    Yh = torch.from_numpy(Y).pin_memory()
+    Yd = Yh.to(dev)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    kw = dict(K=cfg["K"], fr=cfg["fr"], fc=cfg["fc"], seed=0, J=cfg["J"], cg_tol=cfg["cg_tol"])
+    info = {}
+
+    def step(Yin):
+        return M.cpca_pipeline(Yin, **kw)
+
+    for _ in range(args.warmup):
+        out = step(Yd)
+    torch.cuda.synchronize()
+    # one profiled step (outside the timed region) names the dominant kernel
+    M.profile_enable(True, "")
+    out = step(Yd)
+    prof0 = M.profile_read()
+    M.profile_enable(False, "")
+    dominant = max(prof0.items(), key=lambda kv: kv[1][0])[0]
+    rr, rc = out["Yt"].shape
+    k = out["k"]
+    dinfo = out["info"]
+    cg_iters = max(dinfo.cg_iters_u, dinfo.cg_iters_v)
+    nnz_t = out["Lrt"].nnz + out["Lct"].nnz
+    m_u, m_v = cfg["p"] - rr, cfg["n"] - rc
+    ctx = {
+        "steps": args.steps,
+        "fista_bytes_per_launch": 20 * rr * rc + 8 * nnz_t + 8 * (rr + rc + 2),
+        "knn_flops_per_step": 2.0 * (cfg["p"] ** 2 * cfg["n"] + cfg["n"] ** 2 * cfg["p"]
+                                     + rr ** 2 * rc + rc ** 2 * rr),
+        "fp32_simt_tflops": 152 * 128 * 2 * 2.07e9 / 1e12,
+        "cg_bytes_per_iter": 44 * (m_u + m_v) * k + 8 * (out["Lr"].nnz + out["Lc"].nnz),
+        "cg_iters": cg_iters,
+        "out_bytes": 4 * cfg["p"] * cfg["n"],
+    }
+
+    # ---------------- timed region: device-resident input
+    clocks = ClockSampler(local)
+    clocks.start()
+    M.profile_enable(True, dominant)
+    launches0 = M.launch_count()
+    barrier()
+    stream = torch.cuda.current_stream()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    t_wall0 = time.perf_counter()
+    for s in range(args.steps):
+        flush.zero_()
+        ev[s][0].record(stream)
+        out = step(Yd)
+        ev[s][1].record(stream)
+    barrier()
+    t_wall = time.perf_counter() - t_wall0
+    gpu_launches = M.launch_count() - launches0
+    prof = M.profile_read()
+    M.profile_enable(False, "")
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_s = sum(step_ms) / 1000.0
+    clk = clocks.stop()
+
+    # ---------------- end to end: pinned host input, result read back
+    Xh = torch.empty(cfg["p"], cfg["n"], dtype=torch.float32).pin_memory()
+    ev2 = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(args.steps)]
+    barrier()
+    for s in range(args.steps):
+        flush.zero_()
+        ev2[s][0].record(stream)
+        Yin = Yh.to(dev, non_blocking=True)
+        o = step(Yin)
+        Xh.copy_(o["X"], non_blocking=True)
+        ev2[s][1].record(stream)
+    barrier()
+    e2e_s = sum(a.elapsed_time(b) for a, b in ev2) / 1000.0
+
+    if dist is not None:
+        t = torch.tensor([total_s, e2e_s], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_s, e2e_s = float(t[0]), float(t[1])
+
+    units = cfg["J"] * args.steps * world
+    value = units / total_s
+    peaks = load_peaks()
+    dom_ms, dom_n = prof.get(dominant, (0.0, 0))
+    roof = roofline_for(dominant, dom_ms, dom_n, ctx, peaks) if dom_n else None
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1000.0 * total_s / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic", "config": config_dict(cfg),
+        "e2e": {"value": units / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(Yh.numel() * 4),
+                "d2h_bytes_per_step": int(Xh.numel() * 4)},
+        "gpu_launches": int(gpu_launches),
+        "roofline": roof,
+        "clocks": clk,
+        "phases_ms_one_step": {k_: round(v[0], 4) for k_, v in sorted(prof0.items(), key=lambda kv: -kv[1][0])},
+        "fista_iters_per_step": cfg["J"], "cg_iters_per_step": cg_iters, "rank_k": k,
+        "wall_s_timed": t_wall,
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        dec = decoder_graphs_for_timing(Y, cfg["K"])
+        secs = oracle_step_seconds(Y, cfg, args.cpu_queries, dec)
+        line["cpu_baseline"] = {"value": cfg["J"] / secs, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                "sample": cpu_sample_text(args.cpu_queries),
+                                "seconds_per_step_extrapolated": secs}
+    print(json.dumps(line))
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

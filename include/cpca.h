@@ -1,0 +1,240 @@
+/*
+ * cpca.h - C ABI of the GB300 compressive-PCA-on-graphs library (libcpca.so).
+ *
+ * The library implements the data-parallel hot path of compressive PCA on
+ * graphs (Shahid, Perraudin, Puy, Vandergheynst, arXiv 1602.02070):
+ *   - kNN graphs and Laplacians between rows or columns   (Sec. I, Sec. VII-A)
+ *   - uniform row/column sampling, Y~ = M_r Y M_c         (Sec. III, Eq. Mc)
+ *   - FRPCAG on the sampled matrix by FISTA               (Sec. IV-B, Algorithm 1)
+ *   - the subspace-upsampling approximate decoder         (Sec. V-C, Lemma 1,
+ *                                                          Eq. Uupsample, Algorithm 2)
+ *
+ * Conventions (all entry points):
+ *   - Array arguments are DEVICE pointers unless marked "host". The caller
+ *     owns and allocates every buffer; the library allocates no device
+ *     memory of its own. Calls that need scratch take (ws, ws_bytes) and
+ *     have a *_workspace_size query; ws must be 256-byte aligned.
+ *   - Matrices are FP32, row-major, with an explicit leading dimension
+ *     (elements between consecutive rows, >= the row length).
+ *   - Indices are int32 (sizes < 2^31); CSR row pointers are int64.
+ *   - Every call is asynchronous on `stream` (a cudaStream_t passed as
+ *     void*; NULL = legacy default stream) unless it says it synchronises.
+ *   - Every call returns a cpca_status; on failure cpca_last_error() gives
+ *     a message (thread-local). No C++ exception crosses the ABI. Argument
+ *     errors are detected on the host before anything is launched.
+ *   - Kernels never wait without bound: every device-side wait has an
+ *     iteration limit and reports CPCA_ERR_TIMEOUT instead of hanging.
+ */
+#ifndef CPCA_H
+#define CPCA_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t cpca_status;
+#define CPCA_OK                0
+#define CPCA_ERR_INVALID_ARG   1  /* bad size, pointer, alignment or parameter */
+#define CPCA_ERR_CUDA          2  /* a CUDA runtime call or kernel launch failed */
+#define CPCA_ERR_WORKSPACE     3  /* ws_bytes smaller than the *_workspace_size query */
+#define CPCA_ERR_SINGULAR      4  /* L_aa not invertible (a component has no sampled node) */
+#define CPCA_ERR_NOT_CONVERGED 5  /* iteration cap reached before the tolerance */
+#define CPCA_ERR_TIMEOUT       6  /* a bounded device-side wait gave up */
+#define CPCA_ERR_CAPACITY      7  /* an output buffer is too small (e.g. nnz_cap) */
+
+#define CPCA_LAP_NORMALIZED    0  /* L_n = D^-1/2 (D - W) D^-1/2 (Sec. I) */
+#define CPCA_LAP_COMBINATORIAL 1  /* L = D - W (Sec. I) */
+
+/* Message of the last failed call on this host thread ("" if none). */
+const char* cpca_last_error(void);
+/* Library version, major*10000 + minor*100 + patch. */
+int32_t cpca_version(void);
+/* Number of kernels this library has launched in this process. */
+uint64_t cpca_launch_count(void);
+
+/* Per-kernel CUDA-event timing (tracing aid; off by default).
+ * cpca_profile_enable(on, prefix) clears earlier records and, when on != 0,
+ * brackets every later launch whose kernel name starts with `prefix`
+ * (NULL or "" = all named kernels) with a pair of CUDA events on the launch
+ * stream. cpca_profile_read() waits for those events and writes, per kernel
+ * name (up to max_names, names in a max_names x name_len host char array),
+ * the summed milliseconds and the launch count; it returns the number of
+ * distinct names recorded. Kernel names: knn_candidates_tc,
+ * knn_candidates_simt, knn_recheck, fista_iter, cg_pcg, decode_output, ... */
+int32_t cpca_profile_enable(int32_t on, const char* name_prefix);
+int32_t cpca_profile_read(int32_t max_names, char* names, int32_t name_len, double* total_ms,
+                          int32_t* launches);
+
+/* Sparse symmetric Laplacian in CSR form: n x n, nnz stored entries,
+ * column indices ascending within each row, the diagonal stored explicitly.
+ * rowptr[n+1] int64, col[nnz] int32, val[nnz] FP32; all device pointers. */
+typedef struct cpca_csr {
+  int32_t n;
+  int64_t nnz;
+  const int64_t* rowptr;
+  const int32_t* col;
+  const float* val;
+} cpca_csr;
+
+/* ------------------------------------------------------------------------
+ * cpca_knn_graph - exact kNN graph and its Laplacian (Sec. I; Sec. VII-A).
+ *
+ * Points: if transposed == 0, point i is row i of `pts` (npts rows of `dim`
+ * floats, leading dimension ld >= dim); if transposed == 1, point i is
+ * column i of a dim x npts row-major matrix with leading dimension ld >= npts
+ * (pass Y with npts = n, dim = p, ld = n for the column graph of Y).
+ * For each point the K nearest other points by Euclidean distance are found
+ * (ties by lower index). Squared distances are summed directly over the
+ * coordinates in FP32 (never through |a|^2 + |b|^2 - 2ab; that expansion only
+ * ranks candidates). The graph joins i and j if either is among the other's
+ * K nearest; W_ij = exp(-d2_ij / sigma2) with sigma2 = the given value, or,
+ * if sigma2 <= 0, the mean of the npts*K directed kNN squared distances.
+ * Degrees D_ii = sum_j W_ij; lap_type selects L_n (CPCA_LAP_NORMALIZED) or
+ * L = D - W (CPCA_LAP_COMBINATORIAL); a node with zero degree gets an
+ * all-zero row in L_n.
+ *
+ * Outputs (device): CSR rowptr[npts+1], col[nnz], val[nnz] (the Laplacian,
+ * diagonal included), weight[nnz] (W_ij on the same pattern, 0 on the
+ * diagonal; may be NULL); knn_idx[npts*K], knn_d2[npts*K] (may be NULL).
+ * nnz_cap must be >= npts*(2K+1) (the largest possible pattern).
+ * Host outputs: *nnz_out, *sigma2_out (either may be NULL).
+ * This call SYNCHRONISES `stream` once (to return nnz).
+ * Requirements: 1 <= K <= 32, K < npts, dim >= 1.
+ * ---------------------------------------------------------------------- */
+size_t cpca_knn_graph_workspace_size(int32_t npts, int32_t dim, int32_t K, int32_t transposed);
+cpca_status cpca_knn_graph(const float* pts, int32_t npts, int32_t dim, int64_t ld,
+                           int32_t transposed, int32_t K, int32_t lap_type, double sigma2,
+                           int64_t* rowptr, int32_t* col, float* val, float* weight,
+                           int64_t nnz_cap, int32_t* knn_idx, float* knn_d2,
+                           int64_t* nnz_out, double* sigma2_out,
+                           void* ws, size_t ws_bytes, void* stream);
+
+/* ------------------------------------------------------------------------
+ * cpca_sample - uniform sampling without replacement (Sec. III, Eq. Mc).
+ *
+ * Draws Omega_r (rho_r of [0,p)) and Omega_c (rho_c of [0,n)), each in
+ * ascending order, and gathers Yt = Y(Omega_r, Omega_c) = M_r Y M_c, a
+ * rho_r x rho_c matrix (leading dimension ldyt). Index i of side s
+ * (s = 0 rows, 1 columns) gets the key k_i = SplitMix64 output i+1 of the
+ * generator whose state starts at seed XOR (0x9E3779B97F4A7C15 * (s+1));
+ * Omega is the rho indices with the smallest (k_i, i). Y and Yt may both be
+ * NULL to draw only the indices. No workspace.
+ * Requirements: 0 < rho_r <= p, 0 < rho_c <= n.
+ * ---------------------------------------------------------------------- */
+cpca_status cpca_sample(uint64_t seed, int32_t p, int32_t n, int32_t rho_r, int32_t rho_c,
+                        const float* Y, int64_t ldy, int32_t* omega_r, int32_t* omega_c,
+                        float* Yt, int64_t ldyt, void* stream);
+
+/* ------------------------------------------------------------------------
+ * cpca_frpcag_solve - FRPCAG on the sampled matrix by FISTA
+ * (Sec. IV-B, Eq. frpcag_small with phi = l1; Algorithm 1).
+ *
+ *   min_X |Yt - X|_1 + gamma_c tr(X Lc X^T) + gamma_r tr(X^T Lr X)
+ *
+ * Z_1 = S_0 = Yt, t_1 = 1; per iteration j:
+ *   S_j = Yt + sgn(V - Yt) max(|V - Yt| - lambda, 0),
+ *         V = Z_j - lambda * 2 (gamma_c Z_j Lc + gamma_r Lr Z_j),
+ *   t_{j+1} = (1 + sqrt(1 + 4 t_j^2)) / 2,
+ *   Z_{j+1} = S_j + ((t_j - 1) / t_{j+1}) (S_j - S_{j-1}).
+ * lambda = params.step if > 0, else 1 / (2 gamma_c |Lc|_2 + 2 gamma_r |Lr|_2)
+ * with the norms from `power_iters` power iterations in FP64 (start vector
+ * u_i - 1/2, u the SplitMix64 uniforms of (power_seed, stream 2 for Lr,
+ * 3 for Lc)), or 1 when that denominator is 0. With eps > 0 the loop stops
+ * once |Z_{j+1} - Z_j|_F^2 < eps |Z_j|_F^2, tested every check_every
+ * iterations on the host; eps = 0 runs exactly max_iter iterations with no
+ * synchronisation. The output X (rr x rc, leading dimension ldx) is the last
+ * S_j. FP32 arithmetic, FP64 reductions.
+ * Lr is rr x rr, Lc is rc x rc, both symmetric.
+ * `info` (host, may be NULL): if given, the call SYNCHRONISES and fills it,
+ * including the FP64 objective of X.
+ * ---------------------------------------------------------------------- */
+typedef struct cpca_frpcag_params {
+  double gamma_r;
+  double gamma_c;
+  double step;          /* lambda; <= 0 selects 1/beta' by power iteration */
+  int32_t max_iter;     /* J >= 0 */
+  double eps;           /* stopping tolerance; 0 = exactly max_iter iterations */
+  int32_t check_every;  /* iterations between host checks when eps > 0 (>= 1) */
+  int32_t power_iters;  /* power iterations per Laplacian (>= 1) */
+  uint64_t power_seed;
+} cpca_frpcag_params;
+
+typedef struct cpca_solve_info {
+  int32_t iters;        /* iterations run */
+  double step;          /* lambda used */
+  double norm_r;        /* |Lr|_2 estimate (0 if step was given) */
+  double norm_c;        /* |Lc|_2 estimate (0 if step was given) */
+  double rel_change;    /* |Z_{j+1} - Z_j|^2 / |Z_j|^2 of the last iteration */
+  double objective;     /* F(X) in FP64 */
+} cpca_solve_info;
+
+size_t cpca_frpcag_workspace_size(int32_t rr, int32_t rc);
+cpca_status cpca_frpcag_solve(const float* Yt, int32_t rr, int32_t rc, int64_t ldyt,
+                              const cpca_csr* Lr, const cpca_csr* Lc,
+                              const cpca_frpcag_params* params,
+                              float* X, int64_t ldx, cpca_solve_info* info,
+                              void* ws, size_t ws_bytes, void* stream);
+
+/* ------------------------------------------------------------------------
+ * cpca_decode - subspace-upsampling approximate decoder
+ * (Sec. V-C; Lemma 1; Eq. Uupsample; Algorithm 2).
+ *
+ * 1. Top singular triplets of Xt (rr x rc) by block subspace iteration
+ *    with block size b = min(rr, rc, kmax + 16), FP32 products, FP64 Gram /
+ *    Cholesky-QR / Jacobi eigen-solve.
+ * 2. k = number of singular values with s_i / s_1 >= rank_ratio (or
+ *    k_override if > 0); k <= kmax, else CPCA_ERR_INVALID_ARG.
+ * 3. For every column, U(Omega_r,:) = U~ and U(a,:) = -Lr_aa^-1 Lr_ab U~
+ *    (a = rows not in Omega_r), likewise V on Lc; solved by Jacobi-PCG
+ *    (all 2k columns in one cooperative kernel, FP32 vectors, FP64 dots),
+ *    per column to |r| <= cg_tol |b| or cg_max_iter iterations.
+ * 4. Unit-normalise the columns of U and V.
+ * 5. sigma_i = sqrt(n p / (rr rc (1 - delta))) s_i.
+ * 6. X = U diag(sigma) V^T (p x n, leading dimension ldx) if X != NULL.
+ *
+ * omega_r (rr ascending indices of [0,p)) and omega_c (rc of [0,n)) are the
+ * sampling sets of cpca_sample; Lr (p x p) and Lc (n x n) the full graphs.
+ * Optional outputs (may be NULL): U (p x kmax, row-major, ld kmax),
+ * V (n x kmax, ld kmax), sigma (kmax doubles), all device.
+ * Host outputs: *k_out, and `info` if not NULL.
+ * This call SYNCHRONISES `stream` (k is needed on the host).
+ * Returns CPCA_ERR_NOT_CONVERGED if a column hit cg_max_iter (X is still
+ * written), CPCA_ERR_TIMEOUT if a device barrier gave up.
+ * ---------------------------------------------------------------------- */
+typedef struct cpca_decode_params {
+  double rank_ratio;    /* 0.1 in Algorithm 2 */
+  int32_t k_override;   /* > 0: use this k */
+  int32_t kmax;         /* largest k supported by the buffers (<= 48) */
+  double delta;         /* RIP constant in step 5, in [0, 1) */
+  double cg_tol;        /* relative residual tolerance */
+  int32_t cg_max_iter;  /* <= 0: 10 * (number of unsampled nodes) */
+  int32_t svd_iters;    /* subspace iterations (>= 1) */
+  uint64_t svd_seed;    /* start block: SplitMix64 uniforms - 1/2, stream 4 */
+} cpca_decode_params;
+
+typedef struct cpca_decode_info {
+  int32_t k;
+  int32_t cg_iters_u;   /* largest iteration count over the U columns */
+  int32_t cg_iters_v;   /* same for V */
+  double cg_res_u;      /* largest final relative residual over U columns */
+  double cg_res_v;
+  double s_tilde[64];   /* leading singular values of Xt (first b entries valid) */
+  int32_t b;            /* subspace block size used */
+} cpca_decode_info;
+
+size_t cpca_decode_workspace_size(int32_t p, int32_t n, int32_t rr, int32_t rc, int32_t kmax);
+cpca_status cpca_decode(const float* Xt, int32_t rr, int32_t rc, int64_t ldxt,
+                        const int32_t* omega_r, const int32_t* omega_c,
+                        int32_t p, int32_t n, const cpca_csr* Lr, const cpca_csr* Lc,
+                        const cpca_decode_params* params,
+                        float* X, int64_t ldx, float* U, float* V, double* sigma,
+                        int32_t* k_out, cpca_decode_info* info,
+                        void* ws, size_t ws_bytes, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CPCA_H */

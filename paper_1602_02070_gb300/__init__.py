@@ -1,0 +1,12 @@
+"""GB300 (sm_103a) compressive PCA on graphs (arXiv 1602.02070).
+
+The computation lives in libcpca.so (C ABI: include/cpca.h); this package is
+its thin binding plus the end-to-end composition of Table "tab:cpca".
+"""
+from .capi import (CPCA_ERR_CAPACITY, CPCA_ERR_CUDA, CPCA_ERR_INVALID_ARG,  # noqa: F401
+                   CPCA_ERR_NOT_CONVERGED, CPCA_ERR_SINGULAR, CPCA_ERR_TIMEOUT,
+                   CPCA_ERR_WORKSPACE, CPCA_OK, LAP_COMBINATORIAL, LAP_NORMALIZED, CpcaError, Csr,
+                   cpca_decode, cpca_frpcag_solve, cpca_knn_graph, cpca_sample, decode_params,
+                   exported_names, frpcag_params, launch_count, lib, profile_enable,
+                   profile_read)
+from .pipeline import cpca_pipeline, rho_of  # noqa: F401

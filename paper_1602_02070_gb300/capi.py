@@ -1,0 +1,302 @@
+"""Thin ctypes binding of libcpca.so (include/cpca.h).
+
+Argument marshalling only: every function here validates Python-side types,
+allocates outputs and workspaces as torch CUDA tensors, and calls the C entry
+point of the same name on the current torch stream. Every step of the
+computation runs in the library's CUDA kernels; there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libcpca.so")
+
+CPCA_OK = 0
+CPCA_ERR_INVALID_ARG = 1
+CPCA_ERR_CUDA = 2
+CPCA_ERR_WORKSPACE = 3
+CPCA_ERR_SINGULAR = 4
+CPCA_ERR_NOT_CONVERGED = 5
+CPCA_ERR_TIMEOUT = 6
+CPCA_ERR_CAPACITY = 7
+LAP_NORMALIZED = 0
+LAP_COMBINATORIAL = 1
+
+_STATUS = {1: "INVALID_ARG", 2: "CUDA", 3: "WORKSPACE", 4: "SINGULAR", 5: "NOT_CONVERGED",
+           6: "TIMEOUT", 7: "CAPACITY"}
+
+
+class CpcaError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"CPCA_ERR_{_STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class cpca_csr(C.Structure):
+    _fields_ = [("n", C.c_int32), ("nnz", C.c_int64), ("rowptr", C.c_void_p),
+                ("col", C.c_void_p), ("val", C.c_void_p)]
+
+
+class cpca_frpcag_params(C.Structure):
+    _fields_ = [("gamma_r", C.c_double), ("gamma_c", C.c_double), ("step", C.c_double),
+                ("max_iter", C.c_int32), ("eps", C.c_double), ("check_every", C.c_int32),
+                ("power_iters", C.c_int32), ("power_seed", C.c_uint64)]
+
+
+class cpca_solve_info(C.Structure):
+    _fields_ = [("iters", C.c_int32), ("step", C.c_double), ("norm_r", C.c_double),
+                ("norm_c", C.c_double), ("rel_change", C.c_double), ("objective", C.c_double)]
+
+
+class cpca_decode_params(C.Structure):
+    _fields_ = [("rank_ratio", C.c_double), ("k_override", C.c_int32), ("kmax", C.c_int32),
+                ("delta", C.c_double), ("cg_tol", C.c_double), ("cg_max_iter", C.c_int32),
+                ("svd_iters", C.c_int32), ("svd_seed", C.c_uint64)]
+
+
+class cpca_decode_info(C.Structure):
+    _fields_ = [("k", C.c_int32), ("cg_iters_u", C.c_int32), ("cg_iters_v", C.c_int32),
+                ("cg_res_u", C.c_double), ("cg_res_v", C.c_double),
+                ("s_tilde", C.c_double * 64), ("b", C.c_int32)]
+
+
+_lib = None
+
+# (name, restype, argtypes) of every exported entry point in include/cpca.h
+_SIGS = [
+    ("cpca_last_error", C.c_char_p, []),
+    ("cpca_version", C.c_int32, []),
+    ("cpca_launch_count", C.c_uint64, []),
+    ("cpca_profile_enable", C.c_int32, [C.c_int32, C.c_char_p]),
+    ("cpca_profile_read", C.c_int32, [C.c_int32, C.c_char_p, C.c_int32, C.POINTER(C.c_double),
+                                      C.POINTER(C.c_int32)]),
+    ("cpca_knn_graph_workspace_size", C.c_size_t, [C.c_int32, C.c_int32, C.c_int32, C.c_int32]),
+    ("cpca_knn_graph", C.c_int32,
+     [C.c_void_p, C.c_int32, C.c_int32, C.c_int64, C.c_int32, C.c_int32, C.c_int32, C.c_double,
+      C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p,
+      C.POINTER(C.c_int64), C.POINTER(C.c_double), C.c_void_p, C.c_size_t, C.c_void_p]),
+    ("cpca_sample", C.c_int32,
+     [C.c_uint64, C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_void_p, C.c_int64,
+      C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p]),
+    ("cpca_frpcag_workspace_size", C.c_size_t, [C.c_int32, C.c_int32]),
+    ("cpca_frpcag_solve", C.c_int32,
+     [C.c_void_p, C.c_int32, C.c_int32, C.c_int64, C.POINTER(cpca_csr), C.POINTER(cpca_csr),
+      C.POINTER(cpca_frpcag_params), C.c_void_p, C.c_int64, C.POINTER(cpca_solve_info),
+      C.c_void_p, C.c_size_t, C.c_void_p]),
+    ("cpca_decode_workspace_size", C.c_size_t, [C.c_int32] * 5),
+    ("cpca_decode", C.c_int32,
+     [C.c_void_p, C.c_int32, C.c_int32, C.c_int64, C.c_void_p, C.c_void_p, C.c_int32, C.c_int32,
+      C.POINTER(cpca_csr), C.POINTER(cpca_csr), C.POINTER(cpca_decode_params), C.c_void_p,
+      C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(C.c_int32),
+      C.POINTER(cpca_decode_info), C.c_void_p, C.c_size_t, C.c_void_p]),
+]
+
+
+def exported_names():
+    return [s[0] for s in _SIGS]
+
+
+def lib():
+    """Load libcpca.so (building it first if it is missing). Raises if the
+    CUDA library cannot be loaded: there is no CPU path."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            from . import build as _b
+            _b.build()
+        L = C.CDLL(LIB_PATH)
+        for name, res, args in _SIGS:
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(status: int):
+    if status != CPCA_OK:
+        raise CpcaError(status, lib().cpca_last_error().decode())
+
+
+def _ptr(t):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+def _stream():
+    return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _require_cuda(t: torch.Tensor, dtype, name: str):
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+
+
+def _workspace(nbytes: int, device) -> torch.Tensor:
+    return torch.empty(max(int(nbytes), 256), dtype=torch.uint8, device=device)
+
+
+def launch_count() -> int:
+    return int(lib().cpca_launch_count())
+
+
+def profile_enable(on: bool = True, prefix: str = "") -> None:
+    lib().cpca_profile_enable(int(on), prefix.encode())
+
+
+def profile_read(max_names: int = 64) -> dict:
+    """{kernel name: (total ms, launches)} of the launches recorded since
+    profile_enable (waits for their events)."""
+    nl = 64
+    names = C.create_string_buffer(max_names * nl)
+    ms = (C.c_double * max_names)()
+    cnt = (C.c_int32 * max_names)()
+    n = lib().cpca_profile_read(max_names, names, nl, ms, cnt)
+    out = {}
+    for i in range(min(n, max_names)):
+        nm = names.raw[i * nl:(i + 1) * nl].split(b"\0", 1)[0].decode()
+        out[nm] = (float(ms[i]), int(cnt[i]))
+    return out
+
+
+@dataclass
+class Csr:
+    """Device CSR Laplacian (and optional edge weights on the same pattern)."""
+    rowptr: torch.Tensor
+    col: torch.Tensor
+    val: torch.Tensor
+    weight: torch.Tensor | None = None
+    sigma2: float = 0.0
+
+    @property
+    def n(self) -> int:
+        return self.rowptr.numel() - 1
+
+    @property
+    def nnz(self) -> int:
+        return self.col.numel()
+
+    def c(self) -> cpca_csr:
+        return cpca_csr(self.n, self.nnz, self.rowptr.data_ptr(), self.col.data_ptr(), self.val.data_ptr())
+
+    @staticmethod
+    def from_scipy(L, device="cuda", weight=None) -> "Csr":
+        L = L.tocsr()
+        L.sort_indices()
+        return Csr(torch.as_tensor(L.indptr.astype("int64"), device=device),
+                   torch.as_tensor(L.indices.astype("int32"), device=device),
+                   torch.as_tensor(L.data.astype("float32"), device=device))
+
+    def to_scipy(self):
+        import scipy.sparse as sp
+        return sp.csr_matrix((self.val.double().cpu().numpy(), self.col.cpu().numpy(),
+                              self.rowptr.cpu().numpy()), shape=(self.n, self.n))
+
+
+def cpca_knn_graph(pts: torch.Tensor, K: int, lap_type: int = LAP_NORMALIZED,
+                   sigma2: float = -1.0, transposed: bool = False, want_knn: bool = False):
+    """kNN graph + Laplacian of the rows of ``pts`` (or of its columns if
+    ``transposed``). Returns (Csr, knn_idx, knn_d2) with the kNN lists None
+    unless ``want_knn``."""
+    _require_cuda(pts, torch.float32, "pts")
+    if pts.dim() != 2 or pts.stride(1) != 1:
+        raise ValueError("pts must be a 2-D row-major tensor")
+    rows, cols = pts.shape
+    npts, dim = (cols, rows) if transposed else (rows, cols)
+    dev = pts.device
+    cap = npts * (2 * K + 1)
+    rowptr = torch.empty(npts + 1, dtype=torch.int64, device=dev)
+    col = torch.empty(cap, dtype=torch.int32, device=dev)
+    val = torch.empty(cap, dtype=torch.float32, device=dev)
+    weight = torch.empty(cap, dtype=torch.float32, device=dev)
+    kidx = torch.empty(npts, K, dtype=torch.int32, device=dev) if want_knn else None
+    kd2 = torch.empty(npts, K, dtype=torch.float32, device=dev) if want_knn else None
+    ws = _workspace(lib().cpca_knn_graph_workspace_size(npts, dim, K, int(transposed)), dev)
+    nnz = C.c_int64(0)
+    s2 = C.c_double(0)
+    _check(lib().cpca_knn_graph(_ptr(pts), npts, dim, pts.stride(0), int(transposed), K, lap_type,
+                                sigma2, _ptr(rowptr), _ptr(col), _ptr(val), _ptr(weight), cap,
+                                _ptr(kidx), _ptr(kd2), C.byref(nnz), C.byref(s2), _ptr(ws),
+                                ws.numel(), _stream()))
+    n = nnz.value
+    return Csr(rowptr, col[:n], val[:n], weight[:n], s2.value), kidx, kd2
+
+
+def cpca_sample(seed: int, p: int, n: int, rho_r: int, rho_c: int, Y: torch.Tensor | None = None,
+                device="cuda"):
+    """Omega_r, Omega_c (ascending int32) and, if Y is given, Y~ = Y[Omega_r][:, Omega_c]."""
+    if Y is not None:
+        _require_cuda(Y, torch.float32, "Y")
+        device = Y.device
+    om_r = torch.empty(rho_r, dtype=torch.int32, device=device)
+    om_c = torch.empty(rho_c, dtype=torch.int32, device=device)
+    Yt = torch.empty(rho_r, rho_c, dtype=torch.float32, device=device) if Y is not None else None
+    _check(lib().cpca_sample(seed & (2 ** 64 - 1), p, n, rho_r, rho_c, _ptr(Y),
+                             Y.stride(0) if Y is not None else 0, _ptr(om_r), _ptr(om_c),
+                             _ptr(Yt), rho_c, _stream()))
+    return om_r, om_c, Yt
+
+
+def frpcag_params(gamma_r=1.0, gamma_c=1.0, step=-1.0, max_iter=300, eps=0.0, check_every=25,
+                  power_iters=200, power_seed=0) -> cpca_frpcag_params:
+    return cpca_frpcag_params(gamma_r, gamma_c, step, max_iter, eps, check_every, power_iters,
+                              power_seed)
+
+
+def cpca_frpcag_solve(Yt: torch.Tensor, Lr: Csr, Lc: Csr, params: cpca_frpcag_params | None = None,
+                      want_info: bool = True, out: torch.Tensor | None = None, ws=None, **kw):
+    """FISTA for FRPCAG on Y~ (rr x rc). Returns (X, info or None)."""
+    _require_cuda(Yt, torch.float32, "Yt")
+    prm = params if params is not None else frpcag_params(**kw)
+    rr, rc = Yt.shape
+    X = out if out is not None else torch.empty_like(Yt)
+    if ws is None:
+        ws = _workspace(lib().cpca_frpcag_workspace_size(rr, rc), Yt.device)
+    info = cpca_solve_info() if want_info else None
+    lr, lc = Lr.c(), Lc.c()
+    _check(lib().cpca_frpcag_solve(_ptr(Yt), rr, rc, Yt.stride(0), C.byref(lr), C.byref(lc),
+                                   C.byref(prm), _ptr(X), X.stride(0),
+                                   C.byref(info) if info is not None else None, _ptr(ws),
+                                   ws.numel(), _stream()))
+    return X, info
+
+
+def decode_params(rank_ratio=0.1, k_override=0, kmax=32, delta=0.0, cg_tol=1e-6, cg_max_iter=0,
+                  svd_iters=6, svd_seed=0) -> cpca_decode_params:
+    return cpca_decode_params(rank_ratio, k_override, kmax, delta, cg_tol, cg_max_iter, svd_iters,
+                              svd_seed)
+
+
+def cpca_decode(Xt: torch.Tensor, omega_r: torch.Tensor, omega_c: torch.Tensor, p: int, n: int,
+                Lr: Csr, Lc: Csr, params: cpca_decode_params | None = None, want_X: bool = True,
+                out: torch.Tensor | None = None, ws=None, check_status: bool = True, **kw):
+    """Approximate decoder (Algorithm 2). Returns dict X, U, V, sigma, k, info, status."""
+    _require_cuda(Xt, torch.float32, "Xt")
+    prm = params if params is not None else decode_params(**kw)
+    rr, rc = Xt.shape
+    dev = Xt.device
+    kmax = prm.kmax
+    X = (out if out is not None else torch.empty(p, n, dtype=torch.float32, device=dev)) if want_X else None
+    U = torch.empty(p, kmax, dtype=torch.float32, device=dev)
+    V = torch.empty(n, kmax, dtype=torch.float32, device=dev)
+    sig = torch.empty(kmax, dtype=torch.float64, device=dev)
+    if ws is None:
+        ws = _workspace(lib().cpca_decode_workspace_size(p, n, rr, rc, kmax), dev)
+    k = C.c_int32(0)
+    info = cpca_decode_info()
+    lr, lc = Lr.c(), Lc.c()
+    st = lib().cpca_decode(_ptr(Xt), rr, rc, Xt.stride(0), _ptr(omega_r), _ptr(omega_c), p, n,
+                           C.byref(lr), C.byref(lc), C.byref(prm), _ptr(X),
+                           X.stride(0) if X is not None else n, _ptr(U), _ptr(V), _ptr(sig),
+                           C.byref(k), C.byref(info), _ptr(ws), ws.numel(), _stream())
+    if check_status:
+        _check(st)
+    kk = k.value
+    return {"X": X, "U": U[:, :kk], "V": V[:, :kk], "sigma": sig[:kk], "k": kk, "info": info,
+            "status": st}

@@ -1,0 +1,111 @@
+// capi.cu - library-wide C entry points: errors, version, launch count.
+#include <stdarg.h>
+
+#include <map>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+
+namespace cpca {
+
+static thread_local char g_err[1024] = {0};
+std::atomic<uint64_t> g_launches{0};
+
+void set_error(const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof(g_err), fmt, ap);
+  va_end(ap);
+}
+void clear_error() { g_err[0] = 0; }
+
+namespace {
+struct ProfRec {
+  std::string name;
+  cudaEvent_t a, b;
+};
+std::mutex g_prof_mu;
+bool g_prof_on = false;
+std::string g_prof_filter;
+std::vector<ProfRec> g_prof;
+thread_local int g_pending = -1;
+thread_local cudaStream_t g_pending_st = nullptr;
+}  // namespace
+
+void prof_begin(const char* name, cudaStream_t st) {
+  if (!g_prof_on) return;
+  if (!g_prof_filter.empty() && strncmp(name, g_prof_filter.c_str(), g_prof_filter.size()) != 0)
+    return;
+  prof_end();  // a begin without its end closes the earlier record first
+  ProfRec r{name, nullptr, nullptr};
+  if (cudaEventCreate(&r.a) != cudaSuccess || cudaEventCreate(&r.b) != cudaSuccess) {
+    cudaGetLastError();
+    return;
+  }
+  cudaEventRecord(r.a, st);
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  g_prof.push_back(r);
+  g_pending = int(g_prof.size()) - 1;
+  g_pending_st = st;
+}
+
+void prof_end() {
+  if (g_pending < 0) return;
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  if (g_pending < int(g_prof.size())) cudaEventRecord(g_prof[g_pending].b, g_pending_st);
+  g_pending = -1;
+}
+
+}  // namespace cpca
+
+extern "C" {
+
+/* Per-kernel event timing: see cpca.h. */
+int32_t cpca_profile_enable(int32_t on, const char* name_prefix) {
+  std::lock_guard<std::mutex> lk(cpca::g_prof_mu);
+  for (auto& r : cpca::g_prof) {
+    cudaEventDestroy(r.a);
+    cudaEventDestroy(r.b);
+  }
+  cpca::g_prof.clear();
+  cpca::g_pending = -1;
+  cpca::g_prof_on = on != 0;
+  cpca::g_prof_filter = name_prefix ? name_prefix : "";
+  return 0;
+}
+
+int32_t cpca_profile_read(int32_t max_names, char* names, int32_t name_len, double* total_ms,
+                          int32_t* launches) {
+  std::lock_guard<std::mutex> lk(cpca::g_prof_mu);
+  std::map<std::string, std::pair<double, int>> agg;
+  for (auto& r : cpca::g_prof) {
+    float ms = 0.f;
+    if (cudaEventSynchronize(r.b) == cudaSuccess && cudaEventElapsedTime(&ms, r.a, r.b) == cudaSuccess) {
+      auto& e = agg[r.name];
+      e.first += ms;
+      e.second += 1;
+    }
+  }
+  cudaGetLastError();  // never leave a profiling error for the next launch check
+  int i = 0;
+  for (auto& kv : agg) {
+    if (i >= max_names) break;
+    if (names && name_len > 0) {
+      strncpy(names + size_t(i) * name_len, kv.first.c_str(), size_t(name_len) - 1);
+      names[size_t(i) * name_len + name_len - 1] = 0;
+    }
+    if (total_ms) total_ms[i] = kv.second.first;
+    if (launches) launches[i] = kv.second.second;
+    ++i;
+  }
+  return int32_t(agg.size());
+}
+
+
+const char* cpca_last_error(void) { return cpca::g_err; }
+int32_t cpca_version(void) { return 100; }
+uint64_t cpca_launch_count(void) { return cpca::g_launches.load(); }
+
+}  // extern "C"

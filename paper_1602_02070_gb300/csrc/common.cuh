@@ -1,0 +1,183 @@
+// common.cuh - error plumbing, launch accounting, reductions and a bounded
+// grid barrier shared by the libcpca translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <atomic>
+#include <string>
+
+#include "../../include/cpca.h"
+
+namespace cpca {
+
+// ---------------------------------------------------------------- errors --
+void set_error(const char* fmt, ...);
+void clear_error();
+extern std::atomic<uint64_t> g_launches;
+
+inline void count_launch(uint64_t n = 1) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+
+// Per-kernel CUDA-event timing (off by default): CPCA_PROF(name, stream)
+// before a launch records a start event when profiling is enabled and the
+// name matches the filter; CPCA_LAUNCHED() records the matching end event.
+void prof_begin(const char* name, cudaStream_t st);
+void prof_end();
+#define CPCA_PROF(name, st) ::cpca::prof_begin(name, st)
+
+#define CPCA_CHECK_ARG(cond, ...)                          \
+  do {                                                     \
+    if (!(cond)) {                                         \
+      ::cpca::set_error(__VA_ARGS__);                      \
+      return CPCA_ERR_INVALID_ARG;                         \
+    }                                                      \
+  } while (0)
+
+#define CPCA_CUDA(call)                                                        \
+  do {                                                                         \
+    cudaError_t e_ = (call);                                                   \
+    if (e_ != cudaSuccess) {                                                   \
+      ::cpca::set_error("%s:%d: %s: %s", __FILE__, __LINE__, #call,            \
+                        cudaGetErrorString(e_));                               \
+      return CPCA_ERR_CUDA;                                                    \
+    }                                                                          \
+  } while (0)
+
+// After a launch: count it and surface launch-configuration errors.
+#define CPCA_LAUNCHED()                                                        \
+  do {                                                                         \
+    ::cpca::count_launch();                                                    \
+    ::cpca::prof_end();                                                        \
+    cudaError_t e_ = cudaGetLastError();                                       \
+    if (e_ != cudaSuccess) {                                                   \
+      ::cpca::set_error("%s:%d: kernel launch: %s", __FILE__, __LINE__,        \
+                        cudaGetErrorString(e_));                               \
+      return CPCA_ERR_CUDA;                                                    \
+    }                                                                          \
+  } while (0)
+
+#define CPCA_TRY(expr)                 \
+  do {                                 \
+    cpca_status s_ = (expr);           \
+    if (s_ != CPCA_OK) return s_;      \
+  } while (0)
+
+// ------------------------------------------------------------ workspace --
+// Bump allocator over the caller's workspace; every slice 256-byte aligned.
+struct Carve {
+  char* base;
+  size_t off = 0;
+  explicit Carve(void* b) : base(static_cast<char*>(b)) {}
+  template <class T>
+  T* take(size_t count) {
+    off = (off + 255) & ~size_t(255);
+    T* p = base ? reinterpret_cast<T*>(base + off) : nullptr;
+    off += count * sizeof(T);
+    return p;
+  }
+  size_t bytes() const { return (off + 255) & ~size_t(255); }
+};
+
+inline int num_sms() {
+  static int sms = -1;
+  if (sms < 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (sms <= 0) sms = 1;
+  }
+  return sms;
+}
+
+inline unsigned ceil_div(int64_t a, int64_t b) { return static_cast<unsigned>((a + b - 1) / b); }
+
+// ------------------------------------------------------ SplitMix64 keys --
+// Outputs of SplitMix64 (Steele, Lea & Flood 2014) addressed by counter:
+// output i (i >= 1) of the generator started at state0 is mix(state0 + i*G).
+constexpr uint64_t kGolden = 0x9E3779B97F4A7C15ull;
+
+__host__ __device__ inline uint64_t mix64(uint64_t z) {
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+__host__ __device__ inline uint64_t stream_state0(uint64_t seed, int stream) {
+  return seed ^ (kGolden * uint64_t(stream + 1));
+}
+__host__ __device__ inline uint64_t splitmix_at(uint64_t state0, uint64_t i1) {
+  return mix64(state0 + i1 * kGolden);
+}
+__host__ __device__ inline double uniform01_at(uint64_t state0, uint64_t i1) {
+  return double(splitmix_at(state0, i1) >> 11) * 0x1.0p-53;
+}
+
+// ------------------------------------------------------------ reductions --
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ float warp_sumf(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Block-wide sum of a double; every thread gets the result. `red` must hold
+// blockDim.x/32 doubles. Contains __syncthreads().
+__device__ __forceinline__ double block_sum(double v, double* red) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  v = warp_sum(v);
+  __syncthreads();
+  if (lane == 0) red[wid] = v;
+  __syncthreads();
+  double t = 0.0;
+  for (int w = 0; w < nw; ++w) t += red[w];
+  return t;
+}
+
+// ---------------------------------------------------------- grid barrier --
+// Sense-counting barrier for cooperative launches (all blocks co-resident).
+// Every wait is bounded: after kBarrierSpinLimit polls the block records a
+// timeout in *err and stops waiting; callers then leave their loops.
+constexpr long long kBarrierSpinLimit = 1ll << 23;  // ~ 1-2 s with backoff
+
+struct GridBar {
+  unsigned int* count;
+  unsigned int* gen;
+  int* err;
+};
+
+__device__ __forceinline__ bool grid_sync(const GridBar& b) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned int* vgen = b.gen;
+    const unsigned int g = *vgen;
+    __threadfence();
+    const unsigned int nb = gridDim.x * gridDim.y * gridDim.z;
+    if (atomicAdd(b.count, 1u) == nb - 1) {
+      *b.count = 0;
+      __threadfence();
+      atomicAdd(b.gen, 1u);
+    } else {
+      long long spins = 0;
+      while (*vgen == g) {
+        if (*(volatile int*)b.err) break;
+        if (++spins > kBarrierSpinLimit) {
+          atomicExch(b.err, 1);
+          break;
+        }
+        __nanosleep(64);
+      }
+    }
+    __threadfence();
+  }
+  __syncthreads();
+  return *(volatile int*)b.err == 0;
+}
+
+}  // namespace cpca

@@ -1,0 +1,971 @@
+// decode.cu - subspace-upsampling approximate decoder (Sec. V-C, Lemma 1,
+// Eq. Uupsample, Algorithm 2).
+//
+//  1. Leading singular triplets of X~ by block subspace iteration: FP32
+//     tall-skinny products with X~ and X~^T, FP64 Gram matrices, a
+//     rank-revealing Cholesky-QR (dependent columns are dropped), and a final
+//     Rayleigh-Ritz step whose b x b eigenproblem is solved by parallel-order
+//     cyclic Jacobi in one block (FP64).
+//  2. k from the ratio rule of Algorithm 2.
+//  3. Both upsampling problems, all k columns each, in ONE cooperative PCG
+//     kernel: per (side, column) alpha/beta in FP64, FP32 vectors, two
+//     bounded grid barriers per iteration. L_aa is applied straight from the
+//     full CSR by skipping sampled neighbours (pos < 0).
+//  4-6. Column normalisation (FP64 norms), Sigma scaling, X = U Sigma V^T.
+#include <cooperative_groups.h>
+
+#include "common.cuh"
+#include "fista_internal.cuh"
+
+namespace cpca {
+namespace {
+
+constexpr int KMAX_LIMIT = 48;
+constexpr int BMAX = 64;
+
+// ------------------------------------------------------ subspace iteration --
+__global__ void omega_kernel(float* __restrict__ W, int rows, int b, uint64_t seed) {
+  const uint64_t s0 = stream_state0(seed, 4);
+  const int64_t total = int64_t(rows) * b;
+  for (int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; t < total;
+       t += int64_t(gridDim.x) * blockDim.x)
+    W[t] = float(uniform01_at(s0, uint64_t(t) + 1) - 0.5);
+}
+
+// C (m x b) = A (m x n, lda) B (n x b); 8 rows of C per block.
+__global__ void __launch_bounds__(256)
+gemm_nn_tall(const float* __restrict__ A, int64_t lda, int m, int n, const float* __restrict__ B,
+             int b, float* __restrict__ C) {
+  __shared__ float As[8][64];
+  __shared__ float Bs[64][BMAX];
+  const int tid = threadIdx.x, c = tid & 63, rg = tid >> 6;
+  const int r0 = blockIdx.x * 8;
+  float acc0 = 0.f, acc1 = 0.f;
+  for (int k0 = 0; k0 < n; k0 += 64) {
+    for (int e = tid; e < 8 * 64; e += 256) {
+      const int r = e >> 6, k = e & 63;
+      As[r][k] = (r0 + r < m && k0 + k < n) ? A[int64_t(r0 + r) * lda + k0 + k] : 0.f;
+    }
+    for (int e = tid; e < 64 * b; e += 256) {
+      const int k = e / b, cc = e % b;
+      Bs[k][cc] = (k0 + k < n) ? B[int64_t(k0 + k) * b + cc] : 0.f;
+    }
+    __syncthreads();
+    if (c < b) {
+#pragma unroll 8
+      for (int k = 0; k < 64; ++k) {
+        const float bv = Bs[k][c];
+        acc0 = fmaf(As[rg * 2][k], bv, acc0);
+        acc1 = fmaf(As[rg * 2 + 1][k], bv, acc1);
+      }
+    }
+    __syncthreads();
+  }
+  if (c < b) {
+    if (r0 + rg * 2 < m) C[int64_t(r0 + rg * 2) * b + c] = acc0;
+    if (r0 + rg * 2 + 1 < m) C[int64_t(r0 + rg * 2 + 1) * b + c] = acc1;
+  }
+}
+
+// C (n x b) = A^T B with A (m x n, lda), B (m x b); 8 rows of C per block.
+__global__ void __launch_bounds__(256)
+gemm_tn_tall(const float* __restrict__ A, int64_t lda, int m, int n, const float* __restrict__ B,
+             int b, float* __restrict__ C) {
+  __shared__ float As[64][8];
+  __shared__ float Bs[64][BMAX];
+  const int tid = threadIdx.x, c = tid & 63, rg = tid >> 6;
+  const int j0 = blockIdx.x * 8;
+  float acc0 = 0.f, acc1 = 0.f;
+  for (int i0 = 0; i0 < m; i0 += 64) {
+    for (int e = tid; e < 64 * 8; e += 256) {
+      const int i = e >> 3, jj = e & 7;
+      As[i][jj] = (i0 + i < m && j0 + jj < n) ? A[int64_t(i0 + i) * lda + j0 + jj] : 0.f;
+    }
+    for (int e = tid; e < 64 * b; e += 256) {
+      const int i = e / b, cc = e % b;
+      Bs[i][cc] = (i0 + i < m) ? B[int64_t(i0 + i) * b + cc] : 0.f;
+    }
+    __syncthreads();
+    if (c < b) {
+#pragma unroll 8
+      for (int i = 0; i < 64; ++i) {
+        const float bv = Bs[i][c];
+        acc0 = fmaf(As[i][rg * 2], bv, acc0);
+        acc1 = fmaf(As[i][rg * 2 + 1], bv, acc1);
+      }
+    }
+    __syncthreads();
+  }
+  if (c < b) {
+    if (j0 + rg * 2 < n) C[int64_t(j0 + rg * 2) * b + c] = acc0;
+    if (j0 + rg * 2 + 1 < n) C[int64_t(j0 + rg * 2 + 1) * b + c] = acc1;
+  }
+}
+
+constexpr int GRAM_BLOCKS = 64;
+
+// Partial Gram Q^T Q over a fixed row range per block, FP64.
+__global__ void __launch_bounds__(256)
+gram_partial_kernel(const float* __restrict__ Q, int m, int b, double* __restrict__ part) {
+  __shared__ float Qs[32][BMAX];
+  const int tid = threadIdx.x;
+  const int per = (m + gridDim.x - 1) / gridDim.x;
+  const int lo = blockIdx.x * per, hi = min(m, lo + per);
+  double acc[16];
+#pragma unroll
+  for (int u = 0; u < 16; ++u) acc[u] = 0.0;
+  for (int i0 = lo; i0 < hi; i0 += 32) {
+    for (int e = tid; e < 32 * b; e += 256) {
+      const int i = e / b, c = e % b;
+      Qs[i][c] = (i0 + i < hi) ? Q[int64_t(i0 + i) * b + c] : 0.f;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int u = 0; u < 16; ++u) {
+      const int pr = tid + u * 256;
+      if (pr < b * b) {
+        const int a = pr / b, c = pr % b;
+        double s = 0.0;
+        for (int i = 0; i < 32; ++i) s += double(Qs[i][a]) * double(Qs[i][c]);
+        acc[u] += s;
+      }
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int u = 0; u < 16; ++u) {
+    const int pr = tid + u * 256;
+    if (pr < b * b) part[int64_t(blockIdx.x) * b * b + pr] = acc[u];
+  }
+}
+
+__global__ void gram_finish_kernel(const double* __restrict__ part, int nblk, int bb, double* __restrict__ G) {
+  for (int pr = threadIdx.x; pr < bb; pr += blockDim.x) {
+    double s = 0.0;
+    for (int k = 0; k < nblk; ++k) s += part[int64_t(k) * bb + pr];
+    G[pr] = s;
+  }
+}
+
+// Rank-revealing Cholesky G = R^T R (R upper) and Rinv with the columns of
+// numerically dependent directions zeroed. One block.
+__global__ void __launch_bounds__(256)
+chol_inv_kernel(const double* __restrict__ G, int b, double* __restrict__ Rinv) {
+  __shared__ double R[BMAX][BMAX + 1];
+  __shared__ int dead[BMAX];
+  __shared__ double djj;
+  const int tid = threadIdx.x;
+  for (int e = tid; e < BMAX * BMAX; e += blockDim.x) R[e / BMAX][e % BMAX] = 0.0;
+  __syncthreads();
+  for (int j = 0; j < b; ++j) {
+    if (tid == 0) {
+      const double gjj = G[j * b + j];
+      double d = gjj;
+      for (int k = 0; k < j; ++k) d -= R[k][j] * R[k][j];
+      const bool dd = !(gjj > 1e-300) || !(d > 1e-10 * gjj);
+      dead[j] = dd;
+      djj = dd ? 1.0 : sqrt(d);
+      R[j][j] = djj;
+    }
+    __syncthreads();
+    for (int i = j + 1 + tid; i < b; i += blockDim.x) {
+      if (dead[j]) {
+        R[j][i] = 0.0;
+      } else {
+        double s = G[j * b + i];
+        for (int k = 0; k < j; ++k) s -= R[k][j] * R[k][i];
+        R[j][i] = s / djj;
+      }
+    }
+    __syncthreads();
+  }
+  // back substitution, one column of Rinv per thread
+  for (int c = tid; c < b; c += blockDim.x) {
+    double x[BMAX];
+    for (int i = c + 1; i < b; ++i) x[i] = 0.0;
+    for (int i = c; i >= 0; --i) {
+      double s = (i == c) ? 1.0 : 0.0;
+      for (int k = i + 1; k <= c; ++k) s -= R[i][k] * x[k];
+      x[i] = s / R[i][i];
+    }
+    for (int i = 0; i < b; ++i) Rinv[i * b + c] = (dead[c] || i > c || dead[i]) ? 0.0 : x[i];
+  }
+}
+
+// Qout (m x bout) = Qin (m x b) M (b x bout), M FP64 in shared memory.
+__global__ void __launch_bounds__(256)
+apply_small_kernel(const float* __restrict__ Qin, int m, int b, const double* __restrict__ M,
+                   int bout, float* __restrict__ Qout, int ldo, const double* __restrict__ colscale) {
+  __shared__ double Ms[BMAX * BMAX];
+  for (int e = threadIdx.x; e < b * bout; e += blockDim.x) Ms[e] = M[(e / bout) * b + (e % bout)];
+  __syncthreads();
+  const int64_t total = int64_t(m) * bout;
+  for (int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; t < total;
+       t += int64_t(gridDim.x) * blockDim.x) {
+    const int i = int(t / bout), c = int(t % bout);
+    double s = 0.0;
+    for (int k = 0; k < b; ++k) s += double(Qin[int64_t(i) * b + k]) * Ms[k * bout + c];
+    if (colscale) s *= colscale[c];
+    Qout[int64_t(i) * ldo + c] = float(s);
+  }
+}
+
+// Cyclic Jacobi (parallel round-robin order) for a symmetric b x b FP64
+// matrix; eigenvalues descending in lam, eigenvectors as columns of E.
+__global__ void __launch_bounds__(256)
+jacobi_eig_kernel(const double* __restrict__ H, int b, double* __restrict__ E, double* __restrict__ lam) {
+  extern __shared__ double jsm[];
+  const int bp = b + (b & 1);
+  const int ld = BMAX + 1;
+  double* A = jsm;
+  double* V = A + BMAX * ld;
+  double* cs = V + BMAX * ld;   // [BMAX/2][2]
+  int* pr = reinterpret_cast<int*>(cs + BMAX);  // [BMAX/2][2]
+  __shared__ double red[8];
+  __shared__ int perm[BMAX];
+  const int tid = threadIdx.x;
+  for (int e = tid; e < bp * bp; e += blockDim.x) {
+    const int i = e / bp, j = e % bp;
+    A[i * ld + j] = (i < b && j < b) ? H[i * b + j] : 0.0;
+    V[i * ld + j] = i == j ? 1.0 : 0.0;
+  }
+  __syncthreads();
+  for (int sweep = 0; sweep < 40; ++sweep) {
+    double off = 0.0, tot = 0.0;
+    for (int e = tid; e < bp * bp; e += blockDim.x) {
+      const int i = e / bp, j = e % bp;
+      const double a = A[i * ld + j];
+      tot += a * a;
+      if (i != j) off += a * a;
+    }
+    off = block_sum(off, red);
+    tot = block_sum(tot, red);
+    if (!(off > 1e-30 * tot)) break;
+    for (int round = 0; round < bp - 1; ++round) {
+      if (tid < bp / 2) {
+        auto at = [&](int pos) { return pos == 0 ? 0 : 1 + (pos - 1 + round) % (bp - 1); };
+        int p = at(tid), q = at(bp - 1 - tid);
+        if (p > q) { const int t = p; p = q; q = t; }
+        double c = 1.0, s = 0.0;
+        const double apq = A[p * ld + q];
+        if (apq != 0.0) {
+          const double tau = (A[q * ld + q] - A[p * ld + p]) / (2.0 * apq);
+          const double t = (tau >= 0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
+          c = 1.0 / sqrt(1.0 + t * t);
+          s = t * c;
+        }
+        cs[2 * tid] = c;
+        cs[2 * tid + 1] = s;
+        pr[2 * tid] = p;
+        pr[2 * tid + 1] = q;
+      }
+      __syncthreads();
+      for (int e = tid; e < (bp / 2) * bp; e += blockDim.x) {  // rows: J^T A
+        const int k = e / bp, j = e % bp;
+        const int p = pr[2 * k], q = pr[2 * k + 1];
+        const double c = cs[2 * k], s = cs[2 * k + 1];
+        const double apj = A[p * ld + j], aqj = A[q * ld + j];
+        A[p * ld + j] = c * apj - s * aqj;
+        A[q * ld + j] = s * apj + c * aqj;
+      }
+      __syncthreads();
+      for (int e = tid; e < (bp / 2) * bp; e += blockDim.x) {  // columns: (.) J and V J
+        const int k = e / bp, i = e % bp;
+        const int p = pr[2 * k], q = pr[2 * k + 1];
+        const double c = cs[2 * k], s = cs[2 * k + 1];
+        const double aip = A[i * ld + p], aiq = A[i * ld + q];
+        A[i * ld + p] = c * aip - s * aiq;
+        A[i * ld + q] = s * aip + c * aiq;
+        const double vip = V[i * ld + p], viq = V[i * ld + q];
+        V[i * ld + p] = c * vip - s * viq;
+        V[i * ld + q] = s * vip + c * viq;
+      }
+      __syncthreads();
+    }
+  }
+  if (tid == 0) {
+    for (int i = 0; i < b; ++i) perm[i] = i;
+    for (int i = 0; i < b; ++i) {
+      int best = i;
+      for (int j = i + 1; j < b; ++j)
+        if (A[perm[j] * ld + perm[j]] > A[perm[best] * ld + perm[best]]) best = j;
+      const int t = perm[i];
+      perm[i] = perm[best];
+      perm[best] = t;
+    }
+  }
+  __syncthreads();
+  for (int e = tid; e < b * b; e += blockDim.x) {
+    const int i = e / b, c = e % b;
+    E[i * b + c] = V[i * ld + perm[c]];
+  }
+  for (int c = tid; c < b; c += blockDim.x) lam[c] = A[perm[c] * ld + perm[c]];
+}
+
+// s~ = sqrt(max(lam, 0)), 1/s~ (0 where s~ = 0), and k.
+__global__ void rank_kernel(const double* __restrict__ lam, int b, double ratio, int k_override,
+                            double* __restrict__ s, double* __restrict__ sinv, int* __restrict__ k_out) {
+  if (threadIdx.x || blockIdx.x) return;
+  for (int i = 0; i < b; ++i) {
+    s[i] = sqrt(fmax(lam[i], 0.0));
+    sinv[i] = s[i] > 0 ? 1.0 / s[i] : 0.0;
+  }
+  int k = 0;
+  if (s[0] > 0)
+    for (int i = 0; i < b; ++i) k += (s[i] / s[0] >= ratio);
+  *k_out = k_override > 0 ? k_override : k;
+}
+
+// ------------------------------------------------------------------- PCG --
+struct CgSide {
+  int N, rho, m;
+  CsrView L;
+  const int32_t* omega;  // sampled nodes, ascending
+  int32_t* reach;        // [m]: 1 once a path to a sampled node is known
+  int32_t* pos;          // [N]: >= 0 unsampled index, < 0 -(sampled index + 1)
+  int32_t* abar;         // [m]: node of each unsampled index
+  float* minv;           // [m]: 1 / L_aa diagonal (Jacobi)
+  const float* R;        // rho x ldr: U~ or V~
+  int ldr;
+  float *x, *r, *z, *p0, *p1, *q;  // m x k
+};
+
+struct CgArgs {
+  CgSide s[2];
+  int k;
+  double tol;
+  int maxit[2];
+  GridBar bar;
+  double* acc;       // [2 parity][3][2][KMAX]
+  double* acc_init;  // [3][2][KMAX]
+  int* out_iters;    // [2][KMAX]
+  double* out_res;   // [2][KMAX]
+  int* status;       // [0]: 1 = PCG breakdown, 2 = a component without samples
+  unsigned int* changed;  // [3] reachability round counters
+};
+
+__global__ void cg_setup_kernel(CgSide S0, CgSide S1) {
+  const CgSide& S = blockIdx.y == 0 ? S0 : S1;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < S.N; i += gridDim.x * blockDim.x) {
+    int lo = 0, hi = S.rho;  // lower_bound of i in omega
+    while (lo < hi) {
+      const int mid = (lo + hi) >> 1;
+      if (S.omega[mid] < i) lo = mid + 1; else hi = mid;
+    }
+    if (lo < S.rho && S.omega[lo] == i) {
+      S.pos[i] = -(lo + 1);
+    } else {
+      const int t = i - lo;
+      S.pos[i] = t;
+      S.abar[t] = i;
+      float dg = 0.f;
+      for (int64_t e = S.L.rowptr[i]; e < S.L.rowptr[i + 1]; ++e)
+        if (S.L.col[e] == i) dg = S.L.val[e];
+      S.minv[t] = dg > 0.f ? 1.f / dg : 1.f;
+    }
+  }
+}
+
+__device__ __forceinline__ void flush_acc(double* sacc, double* gacc, int n) {
+  __syncthreads();
+  for (int e = threadIdx.x; e < n; e += blockDim.x) {
+    const double v = sacc[e];
+    if (v != 0.0) atomicAdd(gacc + e, v);
+    sacc[e] = 0.0;
+  }
+  __syncthreads();
+}
+
+__global__ void __launch_bounds__(256)
+cg_kernel(CgArgs a) {
+  __shared__ double sacc[3][2][KMAX_LIMIT];
+  __shared__ double rz[2][KMAX_LIMIT], beta[2][KMAX_LIMIT], alpha[2][KMAX_LIMIT], bn[2][KMAX_LIMIT];
+  __shared__ double lastrr[2][KMAX_LIMIT];
+  __shared__ int active[2][KMAX_LIMIT], iters[2][KMAX_LIMIT];
+  __shared__ int any_active;
+  const int k = a.k;
+  const int nacc = 2 * KMAX_LIMIT;
+  const int64_t n0 = int64_t(a.s[0].m) * k, ntot = n0 + int64_t(a.s[1].m) * k;
+  const int64_t gstride = int64_t(gridDim.x) * blockDim.x;
+  const int64_t g0 = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  for (int e = threadIdx.x; e < 3 * nacc; e += blockDim.x) (&sacc[0][0][0])[e] = 0.0;
+  __shared__ int blk_changed;
+
+  // Reachability: L_aa is invertible exactly when every connected component
+  // of the graph holds a sampled node. Rounds of frontier growth from the
+  // sampled set until a round changes nothing (at most m + 1 rounds).
+  const int64_t nodes = int64_t(a.s[0].m) + a.s[1].m;
+  for (int64_t g = g0; g < nodes; g += gstride) {
+    const int sd = g < a.s[0].m ? 0 : 1;
+    a.s[sd].reach[sd ? g - a.s[0].m : g] = 0;
+  }
+  for (int round = 0; round <= max(a.s[0].m, a.s[1].m) + 1; ++round) {
+    if (threadIdx.x == 0) blk_changed = 0;
+    __syncthreads();
+    for (int64_t g = g0; g < nodes; g += gstride) {
+      const int sd = g < a.s[0].m ? 0 : 1;
+      const CgSide& S = a.s[sd];
+      const int t = int(sd ? g - a.s[0].m : g);
+      if (__ldcg(S.reach + t)) continue;
+      const int node = S.abar[t];
+      for (int64_t e = S.L.rowptr[node]; e < S.L.rowptr[node + 1]; ++e) {
+        const int j = S.L.col[e];
+        if (j == node || S.L.val[e] == 0.f) continue;
+        const int ps = S.pos[j];
+        if (ps < 0 || __ldcg(S.reach + ps)) {
+          S.reach[t] = 1;
+          blk_changed = 1;
+          break;
+        }
+      }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && blk_changed) atomicAdd(a.changed + round % 3, 1u);
+    if (blockIdx.x == 0 && threadIdx.x == 0) a.changed[(round + 1) % 3] = 0;
+    if (!grid_sync(a.bar)) return;
+    if (__ldcg(a.changed + round % 3) == 0) break;
+  }
+  for (int64_t g = g0; g < nodes; g += gstride) {
+    const int sd = g < a.s[0].m ? 0 : 1;
+    if (!__ldcg(a.s[sd].reach + (sd ? g - a.s[0].m : g))) atomicOr(a.status, 2);
+  }
+  __syncthreads();
+
+  // r = b = -L_ab R, x = 0, z = M^-1 r, p_prev = 0
+  for (int64_t g = g0; g < ntot; g += gstride) {
+    const int sd = g < n0 ? 0 : 1;
+    const CgSide& S = a.s[sd];
+    const int64_t l = sd ? g - n0 : g;
+    const int t = int(l / k), c = int(l % k);
+    const int node = S.abar[t];
+    float bv = 0.f;
+    for (int64_t e = S.L.rowptr[node]; e < S.L.rowptr[node + 1]; ++e) {
+      const int ps = S.pos[S.L.col[e]];
+      if (ps < 0) bv = fmaf(-S.L.val[e], S.R[int64_t(-ps - 1) * S.ldr + c], bv);
+    }
+    const float zv = S.minv[t] * bv;
+    S.r[l] = bv;
+    S.z[l] = zv;
+    S.x[l] = 0.f;
+    S.p1[l] = 0.f;
+    atomicAdd(&sacc[0][sd][c], double(bv) * bv);
+    atomicAdd(&sacc[1][sd][c], double(bv) * zv);
+    atomicAdd(&sacc[2][sd][c], double(bv) * bv);
+  }
+  flush_acc(&sacc[0][0][0], a.acc_init, 3 * nacc);
+  if (!grid_sync(a.bar)) return;
+  for (int e = threadIdx.x; e < 2 * k; e += blockDim.x) {
+    const int sd = e / k, c = e % k;
+    const double bb = __ldcg(a.acc_init + (0 * 2 + sd) * KMAX_LIMIT + c);
+    bn[sd][c] = sqrt(bb);
+    rz[sd][c] = __ldcg(a.acc_init + (1 * 2 + sd) * KMAX_LIMIT + c);
+    const double rr = __ldcg(a.acc_init + (2 * 2 + sd) * KMAX_LIMIT + c);
+    lastrr[sd][c] = rr;
+    active[sd][c] = (a.s[sd].m > 0) && (sqrt(rr) > a.tol * bn[sd][c]) && (a.maxit[sd] > 0);
+    beta[sd][c] = 0.0;
+    iters[sd][c] = 0;
+  }
+  __syncthreads();
+
+  for (int it = 0;; ++it) {
+    if (threadIdx.x == 0) {
+      int any = 0;
+      for (int e = 0; e < 2 * k; ++e) any |= active[e / k][e % k];
+      any_active = any;
+    }
+    __syncthreads();
+    if (!any_active) break;
+    const int par = it & 1;
+    double* accp = a.acc + par * 3 * nacc;
+    // Phase Q: p = z + beta p_prev (own rows and, on the fly, neighbours);
+    // q = L_aa p; accumulate p.q
+    for (int64_t g = g0; g < ntot; g += gstride) {
+      const int sd = g < n0 ? 0 : 1;
+      const int64_t l = sd ? g - n0 : g;
+      const int t = int(l / k), c = int(l % k);
+      if (!active[sd][c]) continue;
+      const CgSide& S = a.s[sd];
+      float* pcur = par ? S.p1 : S.p0;
+      const float* pprev = par ? S.p0 : S.p1;
+      const float bt = float(beta[sd][c]);
+      const float pv = fmaf(bt, pprev[l], S.z[l]);
+      pcur[l] = pv;
+      const int node = S.abar[t];
+      float qv = 0.f;
+      for (int64_t e = S.L.rowptr[node]; e < S.L.rowptr[node + 1]; ++e) {
+        const int ps = S.pos[S.L.col[e]];
+        if (ps >= 0) {
+          const int64_t o = int64_t(ps) * k + c;
+          // neighbours were written by other blocks in this launch: bypass L1
+          qv = fmaf(S.L.val[e], fmaf(bt, __ldcg(pprev + o), __ldcg(S.z + o)), qv);
+        }
+      }
+      S.q[l] = qv;
+      atomicAdd(&sacc[0][sd][c], double(pv) * qv);
+    }
+    flush_acc(&sacc[0][0][0], accp, nacc);
+    if (!grid_sync(a.bar)) return;
+    for (int e = threadIdx.x; e < 2 * k; e += blockDim.x) {
+      const int sd = e / k, c = e % k;
+      if (!active[sd][c]) continue;
+      const double pq = __ldcg(accp + sd * KMAX_LIMIT + c);
+      if (!(pq > 0.0)) {
+        alpha[sd][c] = 0.0;
+        if (blockIdx.x == 0) a.status[0] = 1;  // L_aa not positive definite
+      } else {
+        alpha[sd][c] = rz[sd][c] / pq;
+      }
+    }
+    __syncthreads();
+    // Phase U: x += alpha p; r -= alpha q; z = M^-1 r; accumulate r.z, r.r
+    for (int64_t g = g0; g < ntot; g += gstride) {
+      const int sd = g < n0 ? 0 : 1;
+      const int64_t l = sd ? g - n0 : g;
+      const int t = int(l / k), c = int(l % k);
+      if (!active[sd][c]) continue;
+      const CgSide& S = a.s[sd];
+      const float* pcur = par ? S.p1 : S.p0;
+      const float al = float(alpha[sd][c]);
+      S.x[l] = fmaf(al, pcur[l], S.x[l]);
+      const float rv = fmaf(-al, S.q[l], S.r[l]);
+      S.r[l] = rv;
+      const float zv = S.minv[t] * rv;
+      S.z[l] = zv;
+      atomicAdd(&sacc[1][sd][c], double(rv) * zv);
+      atomicAdd(&sacc[2][sd][c], double(rv) * rv);
+    }
+    flush_acc(&sacc[0][0][0], accp, 3 * nacc);
+    if (blockIdx.x == 0) {
+      double* other = a.acc + (1 - par) * 3 * nacc;
+      for (int e = threadIdx.x; e < 3 * nacc; e += blockDim.x) other[e] = 0.0;
+    }
+    if (!grid_sync(a.bar)) return;
+    for (int e = threadIdx.x; e < 2 * k; e += blockDim.x) {
+      const int sd = e / k, c = e % k;
+      if (!active[sd][c]) continue;
+      const double rzn = __ldcg(accp + (1 * 2 + sd) * KMAX_LIMIT + c);
+      const double rr = __ldcg(accp + (2 * 2 + sd) * KMAX_LIMIT + c);
+      beta[sd][c] = rz[sd][c] != 0.0 ? rzn / rz[sd][c] : 0.0;
+      rz[sd][c] = rzn;
+      lastrr[sd][c] = rr;
+      iters[sd][c] += 1;
+      if (!(sqrt(rr) > a.tol * bn[sd][c]) || iters[sd][c] >= a.maxit[sd] || alpha[sd][c] == 0.0)
+        active[sd][c] = 0;
+    }
+    __syncthreads();
+  }
+  if (blockIdx.x == 0) {
+    for (int e = threadIdx.x; e < 2 * k; e += blockDim.x) {
+      const int sd = e / k, c = e % k;
+      a.out_iters[sd * KMAX_LIMIT + c] = iters[sd][c];
+      a.out_res[sd * KMAX_LIMIT + c] = bn[sd][c] > 0 ? sqrt(lastrr[sd][c]) / bn[sd][c] : 0.0;
+    }
+  }
+}
+
+// U (N x ldu): sampled rows from R (U~ or V~), unsampled rows from x.
+__global__ void assemble_side_kernel(int N, int k, int ldu, const int32_t* __restrict__ pos,
+                                     const float* __restrict__ R, int ldr, const float* __restrict__ x,
+                                     float* __restrict__ U) {
+  const int64_t total = int64_t(N) * ldu;
+  for (int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; t < total;
+       t += int64_t(gridDim.x) * blockDim.x) {
+    const int i = int(t / ldu), c = int(t % ldu);
+    float v = 0.f;
+    if (c < k) {
+      const int ps = pos[i];
+      v = ps < 0 ? R[int64_t(-ps - 1) * ldr + c] : x[int64_t(ps) * k + c];
+    }
+    U[t] = v;
+  }
+}
+
+constexpr int NORM_BLOCKS = 128;
+
+__global__ void colnorm_partial_kernel(const float* __restrict__ U, int N, int k, int ldu,
+                                       double* __restrict__ part) {
+  const int per = (N + gridDim.x - 1) / gridDim.x;
+  const int lo = blockIdx.x * per, hi = min(N, lo + per);
+  // each thread owns one column and a fixed row stride: deterministic order
+  const int c = threadIdx.x % KMAX_LIMIT, lane_row = threadIdx.x / KMAX_LIMIT;
+  const int rows_par = blockDim.x / KMAX_LIMIT;
+  double acc = 0.0;
+  if (c < k && lane_row < rows_par)
+    for (int i = lo + lane_row; i < hi; i += rows_par) {
+      const double v = U[int64_t(i) * ldu + c];
+      acc += v * v;
+    }
+  __shared__ double tmp[256];
+  tmp[threadIdx.x] = acc;
+  __syncthreads();
+  if (threadIdx.x < KMAX_LIMIT) {
+    double t = 0.0;
+    for (int r = 0; r < rows_par; ++r) t += tmp[r * KMAX_LIMIT + threadIdx.x];
+    part[int64_t(blockIdx.x) * KMAX_LIMIT + threadIdx.x] = t;
+  }
+}
+
+// inv norms for both sides and sigma = scale * s~.
+__global__ void norm_finish_kernel(const double* __restrict__ pu, const double* __restrict__ pv,
+                                   int nblk, int k, const double* __restrict__ s_tilde, double scale,
+                                   double* __restrict__ invu, double* __restrict__ invv,
+                                   double* __restrict__ sigma, int ksig) {
+  for (int c = threadIdx.x; c < KMAX_LIMIT; c += blockDim.x) {
+    double a = 0.0, b = 0.0;
+    for (int i = 0; i < nblk; ++i) {
+      a += pu[int64_t(i) * KMAX_LIMIT + c];
+      b += pv[int64_t(i) * KMAX_LIMIT + c];
+    }
+    invu[c] = (c < k && a > 0) ? 1.0 / sqrt(a) : 0.0;
+    invv[c] = (c < k && b > 0) ? 1.0 / sqrt(b) : 0.0;
+    if (c < ksig) sigma[c] = c < k ? scale * s_tilde[c] : 0.0;
+  }
+}
+
+__global__ void scale_cols_kernel(float* __restrict__ U, int64_t total, int ldu, const double* __restrict__ inv) {
+  for (int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; t < total;
+       t += int64_t(gridDim.x) * blockDim.x)
+    U[t] = float(double(U[t]) * inv[t % ldu]);
+}
+
+// X (p x n) = U diag(sigma) V^T, 32 x 128 tile per block, streaming stores.
+__global__ void __launch_bounds__(256)
+output_kernel(const float* __restrict__ U, int ldu, const float* __restrict__ V, int ldv,
+              const double* __restrict__ sigma, int k, int p, int n, float* __restrict__ X, int64_t ldx) {
+  __shared__ float Us[32][KMAX_LIMIT + 1];
+  __shared__ float Vs[128][KMAX_LIMIT + 1];
+  const int i0 = blockIdx.y * 32, j0 = blockIdx.x * 128;
+  for (int e = threadIdx.x; e < 32 * k; e += blockDim.x) {
+    const int r = e / k, c = e % k;
+    Us[r][c] = (i0 + r < p) ? float(double(U[int64_t(i0 + r) * ldu + c]) * sigma[c]) : 0.f;
+  }
+  for (int e = threadIdx.x; e < 128 * k; e += blockDim.x) {
+    const int r = e / k, c = e % k;
+    Vs[r][c] = (j0 + r < n) ? V[int64_t(j0 + r) * ldv + c] : 0.f;
+  }
+  __syncthreads();
+  const int jj = threadIdx.x & 127, ig = threadIdx.x >> 7;
+  const int j = j0 + jj;
+  if (j >= n) return;
+  for (int r = ig; r < 32; r += 2) {
+    const int i = i0 + r;
+    if (i >= p) break;
+    float s = 0.f;
+    for (int c = 0; c < k; ++c) s = fmaf(Us[r][c], Vs[jj][c], s);
+    __stcs(X + int64_t(i) * ldx + j, s);
+  }
+}
+
+}  // namespace
+
+struct DecodeWs {
+  float *W, *Q, *Q2, *Ut, *Vt;
+  double *part, *G, *Rinv, *E, *lam, *s, *sinv;
+  int* k;
+  int32_t *pos0, *pos1, *abar0, *abar1;
+  float *minv0, *minv1;
+  float* vec[2][6];
+  double *acc, *acc_init;
+  unsigned int* bar;
+  int* err;
+  int* out_iters;
+  double* out_res;
+  int* status;
+  unsigned int* changed;
+  int32_t *reach0, *reach1;
+  float *Ubuf, *Vbuf;
+  double* sigbuf;
+  double *npart_u, *npart_v, *invu, *invv;
+  size_t bytes;
+};
+
+static int decode_block(int rr, int rc, int kmax) { return std::min(std::min(rr, rc), kmax + 16); }
+
+static DecodeWs decode_layout(void* ws, int p, int n, int rr, int rc, int kmax) {
+  Carve c(ws);
+  DecodeWs w{};
+  const int b = decode_block(rr, rc, kmax);
+  w.W = c.take<float>(size_t(rc) * b);
+  w.Q = c.take<float>(size_t(rr) * b);
+  w.Q2 = c.take<float>(size_t(rr) * b);
+  w.Ut = c.take<float>(size_t(rr) * b);
+  w.Vt = c.take<float>(size_t(rc) * b);
+  w.part = c.take<double>(size_t(GRAM_BLOCKS) * b * b);
+  w.G = c.take<double>(size_t(b) * b);
+  w.Rinv = c.take<double>(size_t(b) * b);
+  w.E = c.take<double>(size_t(b) * b);
+  w.lam = c.take<double>(b);
+  w.s = c.take<double>(b);
+  w.sinv = c.take<double>(b);
+  w.k = c.take<int>(1);
+  w.pos0 = c.take<int32_t>(p);
+  w.pos1 = c.take<int32_t>(n);
+  const int m0 = p - rr, m1 = n - rc;
+  w.abar0 = c.take<int32_t>(std::max(m0, 1));
+  w.abar1 = c.take<int32_t>(std::max(m1, 1));
+  w.minv0 = c.take<float>(std::max(m0, 1));
+  w.minv1 = c.take<float>(std::max(m1, 1));
+  for (int v = 0; v < 6; ++v) {
+    w.vec[0][v] = c.take<float>(size_t(std::max(m0, 1)) * kmax);
+    w.vec[1][v] = c.take<float>(size_t(std::max(m1, 1)) * kmax);
+  }
+  w.acc = c.take<double>(2 * 3 * 2 * KMAX_LIMIT);
+  w.acc_init = c.take<double>(3 * 2 * KMAX_LIMIT);
+  w.bar = c.take<unsigned int>(2);
+  w.err = c.take<int>(1);
+  w.out_iters = c.take<int>(2 * KMAX_LIMIT);
+  w.out_res = c.take<double>(2 * KMAX_LIMIT);
+  w.status = c.take<int>(1);
+  w.changed = c.take<unsigned int>(3);
+  w.reach0 = c.take<int32_t>(std::max(m0, 1));
+  w.reach1 = c.take<int32_t>(std::max(m1, 1));
+  w.Ubuf = c.take<float>(size_t(p) * kmax);
+  w.Vbuf = c.take<float>(size_t(n) * kmax);
+  w.sigbuf = c.take<double>(kmax);
+  w.npart_u = c.take<double>(size_t(NORM_BLOCKS) * KMAX_LIMIT);
+  w.npart_v = c.take<double>(size_t(NORM_BLOCKS) * KMAX_LIMIT);
+  w.invu = c.take<double>(KMAX_LIMIT);
+  w.invv = c.take<double>(KMAX_LIMIT);
+  w.bytes = c.bytes();
+  return w;
+}
+
+// Orthonormalise Q (m x b) in place: two rank-revealing Cholesky-QR passes.
+static cpca_status orthonormalize(float* Q, float* Q2, int m, int b, const DecodeWs& w, cudaStream_t st) {
+  for (int pass = 0; pass < 2; ++pass) {
+    gram_partial_kernel<<<GRAM_BLOCKS, 256, 0, st>>>(Q, m, b, w.part);
+    CPCA_LAUNCHED();
+    gram_finish_kernel<<<1, 256, 0, st>>>(w.part, GRAM_BLOCKS, b * b, w.G);
+    CPCA_LAUNCHED();
+    chol_inv_kernel<<<1, 256, 0, st>>>(w.G, b, w.Rinv);
+    CPCA_LAUNCHED();
+    apply_small_kernel<<<std::min<unsigned>(ceil_div(int64_t(m) * b, 256), num_sms() * 4), 256, 0, st>>>(
+        Q, m, b, w.Rinv, b, Q2, b, nullptr);
+    CPCA_LAUNCHED();
+    CPCA_CUDA(cudaMemcpyAsync(Q, Q2, sizeof(float) * size_t(m) * b, cudaMemcpyDeviceToDevice, st));
+  }
+  return CPCA_OK;
+}
+
+// Partial SVD: U~ (rr x b) into w.Ut, V~ (rc x b) into w.Vt, s~ into w.s, k into w.k.
+static cpca_status partial_svd(const float* Xt, int rr, int rc, int64_t ldxt, int b, int iters,
+                               uint64_t seed, double ratio, int k_override, const DecodeWs& w,
+                               cudaStream_t st) {
+  const unsigned gw = std::min<unsigned>(ceil_div(int64_t(rc) * b, 256), num_sms() * 4);
+  omega_kernel<<<gw, 256, 0, st>>>(w.W, rc, b, seed);
+  CPCA_LAUNCHED();
+  CPCA_PROF("svd_gemm", st);
+  gemm_nn_tall<<<ceil_div(rr, 8), 256, 0, st>>>(Xt, ldxt, rr, rc, w.W, b, w.Q);
+  CPCA_LAUNCHED();
+  for (int it = 0; it < iters; ++it) {
+    CPCA_TRY(orthonormalize(w.Q, w.Q2, rr, b, w, st));
+    CPCA_PROF("svd_gemm", st);
+    gemm_tn_tall<<<ceil_div(rc, 8), 256, 0, st>>>(Xt, ldxt, rr, rc, w.Q, b, w.W);
+    CPCA_LAUNCHED();
+    CPCA_PROF("svd_gemm", st);
+    gemm_nn_tall<<<ceil_div(rr, 8), 256, 0, st>>>(Xt, ldxt, rr, rc, w.W, b, w.Q);
+    CPCA_LAUNCHED();
+  }
+  CPCA_TRY(orthonormalize(w.Q, w.Q2, rr, b, w, st));
+  CPCA_PROF("svd_gemm", st);
+  gemm_tn_tall<<<ceil_div(rc, 8), 256, 0, st>>>(Xt, ldxt, rr, rc, w.Q, b, w.W);
+  CPCA_LAUNCHED();
+  // H = W^T W = Q^T X~ X~^T Q (b x b), eigen-decomposition
+  gram_partial_kernel<<<GRAM_BLOCKS, 256, 0, st>>>(w.W, rc, b, w.part);
+  CPCA_LAUNCHED();
+  gram_finish_kernel<<<1, 256, 0, st>>>(w.part, GRAM_BLOCKS, b * b, w.G);
+  CPCA_LAUNCHED();
+  const size_t jsm = sizeof(double) * (2 * BMAX * (BMAX + 1) + BMAX) + sizeof(int) * BMAX;
+  CPCA_CUDA(cudaFuncSetAttribute(jacobi_eig_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(jsm)));
+  CPCA_PROF("svd_jacobi", st);
+  jacobi_eig_kernel<<<1, 256, jsm, st>>>(w.G, b, w.E, w.lam);
+  CPCA_LAUNCHED();
+  rank_kernel<<<1, 32, 0, st>>>(w.lam, b, ratio, k_override, w.s, w.sinv, w.k);
+  CPCA_LAUNCHED();
+  // U~ = Q E, V~ = W E diag(1/s~)
+  const unsigned gu = std::min<unsigned>(ceil_div(int64_t(rr) * b, 256), num_sms() * 4);
+  apply_small_kernel<<<gu, 256, 0, st>>>(w.Q, rr, b, w.E, b, w.Ut, b, nullptr);
+  CPCA_LAUNCHED();
+  apply_small_kernel<<<gw, 256, 0, st>>>(w.W, rc, b, w.E, b, w.Vt, b, w.sinv);
+  CPCA_LAUNCHED();
+  return CPCA_OK;
+}
+
+}  // namespace cpca
+
+using namespace cpca;
+
+extern "C" size_t cpca_decode_workspace_size(int32_t p, int32_t n, int32_t rr, int32_t rc, int32_t kmax) {
+  if (p <= 0 || n <= 0 || rr <= 0 || rc <= 0 || kmax <= 0 || kmax > KMAX_LIMIT) return 0;
+  return decode_layout(nullptr, p, n, rr, rc, kmax).bytes;
+}
+
+extern "C" cpca_status cpca_decode(const float* Xt, int32_t rr, int32_t rc, int64_t ldxt,
+                                   const int32_t* omega_r, const int32_t* omega_c, int32_t p,
+                                   int32_t n, const cpca_csr* Lr, const cpca_csr* Lc,
+                                   const cpca_decode_params* prm, float* X, int64_t ldx, float* U,
+                                   float* V, double* sigma, int32_t* k_out, cpca_decode_info* info,
+                                   void* ws, size_t ws_bytes, void* stream) {
+  clear_error();
+  CPCA_CHECK_ARG(Xt && omega_r && omega_c && prm, "cpca_decode: null pointer");
+  CPCA_CHECK_ARG(rr > 0 && rc > 0 && rr <= p && rc <= n, "cpca_decode: need 0 < rr <= p, 0 < rc <= n");
+  CPCA_CHECK_ARG(ldxt >= rc, "cpca_decode: ldxt < rc");
+  CPCA_CHECK_ARG(!X || ldx >= n, "cpca_decode: ldx < n");
+  CPCA_CHECK_ARG(prm->kmax >= 1 && prm->kmax <= KMAX_LIMIT, "cpca_decode: kmax must be in [1, %d]", KMAX_LIMIT);
+  CPCA_CHECK_ARG(prm->delta >= 0 && prm->delta < 1, "cpca_decode: delta must be in [0, 1)");
+  CPCA_CHECK_ARG(prm->cg_tol > 0, "cpca_decode: cg_tol must be positive");
+  CPCA_CHECK_ARG(prm->svd_iters >= 1, "cpca_decode: svd_iters < 1");
+  CPCA_CHECK_ARG(prm->rank_ratio > 0 && prm->rank_ratio <= 1, "cpca_decode: rank_ratio in (0, 1]");
+  CPCA_TRY(check_csr(Lr, p, "cpca_decode(Lr)"));
+  CPCA_TRY(check_csr(Lc, n, "cpca_decode(Lc)"));
+  const int kmax = prm->kmax;
+  const DecodeWs w = decode_layout(ws, p, n, rr, rc, kmax);
+  if (!ws || ws_bytes < w.bytes) {
+    set_error("cpca_decode: workspace %zu bytes < required %zu", ws_bytes, w.bytes);
+    return CPCA_ERR_WORKSPACE;
+  }
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const int b = decode_block(rr, rc, kmax);
+  CPCA_TRY(partial_svd(Xt, rr, rc, ldxt, b, prm->svd_iters, prm->svd_seed, prm->rank_ratio,
+                       prm->k_override, w, st));
+  int k = 0;
+  CPCA_CUDA(cudaMemcpyAsync(&k, w.k, sizeof(int), cudaMemcpyDeviceToHost, st));
+  CPCA_CUDA(cudaStreamSynchronize(st));
+  if (k > kmax || k > b) {
+    set_error("cpca_decode: rank %d exceeds kmax %d or block %d", k, kmax, b);
+    return CPCA_ERR_INVALID_ARG;
+  }
+  float* Uo = U ? U : w.Ubuf;
+  float* Vo = V ? V : w.Vbuf;
+  double* so = sigma ? sigma : w.sigbuf;
+  int cg_iters[2 * KMAX_LIMIT] = {0};
+  double cg_res[2 * KMAX_LIMIT] = {0};
+  int breakdown = 0;
+  if (k > 0) {
+    CgArgs a{};
+    const CsrView lr{Lr->n, Lr->rowptr, Lr->col, Lr->val};
+    const CsrView lc{Lc->n, Lc->rowptr, Lc->col, Lc->val};
+    const int m[2] = {p - rr, n - rc};
+    for (int sd = 0; sd < 2; ++sd) {
+      CgSide& S = a.s[sd];
+      S.N = sd ? n : p;
+      S.rho = sd ? rc : rr;
+      S.m = m[sd];
+      S.L = sd ? lc : lr;
+      S.omega = sd ? omega_c : omega_r;
+      S.pos = sd ? w.pos1 : w.pos0;
+      S.abar = sd ? w.abar1 : w.abar0;
+      S.reach = sd ? w.reach1 : w.reach0;
+      S.minv = sd ? w.minv1 : w.minv0;
+      S.R = sd ? w.Vt : w.Ut;
+      S.ldr = b;
+      S.x = w.vec[sd][0];
+      S.r = w.vec[sd][1];
+      S.z = w.vec[sd][2];
+      S.p0 = w.vec[sd][3];
+      S.p1 = w.vec[sd][4];
+      S.q = w.vec[sd][5];
+      a.maxit[sd] = prm->cg_max_iter > 0 ? prm->cg_max_iter : 10 * std::max(m[sd], 1);
+    }
+    a.k = k;
+    a.tol = prm->cg_tol;
+    a.bar = GridBar{w.bar, w.bar + 1, w.err};
+    a.acc = w.acc;
+    a.acc_init = w.acc_init;
+    a.out_iters = w.out_iters;
+    a.out_res = w.out_res;
+    a.status = w.status;
+    a.changed = w.changed;
+    dim3 sg(std::min<unsigned>(ceil_div(std::max(p, n), 256), num_sms() * 4), 2);
+    cg_setup_kernel<<<sg, 256, 0, st>>>(a.s[0], a.s[1]);
+    CPCA_LAUNCHED();
+    CPCA_CUDA(cudaMemsetAsync(w.acc, 0, sizeof(double) * 2 * 3 * 2 * KMAX_LIMIT, st));
+    CPCA_CUDA(cudaMemsetAsync(w.acc_init, 0, sizeof(double) * 3 * 2 * KMAX_LIMIT, st));
+    CPCA_CUDA(cudaMemsetAsync(w.bar, 0, 2 * sizeof(unsigned int), st));
+    CPCA_CUDA(cudaMemsetAsync(w.err, 0, sizeof(int), st));
+    CPCA_CUDA(cudaMemsetAsync(w.status, 0, sizeof(int), st));
+    CPCA_CUDA(cudaMemsetAsync(w.changed, 0, 3 * sizeof(unsigned int), st));
+    int occ = 0;
+    CPCA_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, cg_kernel, 256, 0));
+    const int64_t items = int64_t(m[0] + m[1]) * k;
+    const int grid = int(std::max<int64_t>(1, std::min<int64_t>(int64_t(occ) * num_sms(),
+                                                                 std::max<int64_t>(1, ceil_div(items, 256)))));
+    void* args[] = {&a};
+    CPCA_PROF("cg_pcg", st);
+    CPCA_CUDA(cudaLaunchCooperativeKernel((void*)cg_kernel, dim3(grid), dim3(256), args, 0, st));
+    CPCA_LAUNCHED();
+    int err = 0;
+    CPCA_CUDA(cudaMemcpyAsync(&err, w.err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CPCA_CUDA(cudaMemcpyAsync(&breakdown, w.status, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CPCA_CUDA(cudaMemcpyAsync(cg_iters, w.out_iters, sizeof(cg_iters), cudaMemcpyDeviceToHost, st));
+    CPCA_CUDA(cudaMemcpyAsync(cg_res, w.out_res, sizeof(cg_res), cudaMemcpyDeviceToHost, st));
+    CPCA_CUDA(cudaStreamSynchronize(st));
+    if (err) {
+      set_error("cpca_decode: PCG grid barrier timed out");
+      return CPCA_ERR_TIMEOUT;
+    }
+  }
+  // assemble, normalise, scale, output
+  const unsigned gp = std::min<unsigned>(ceil_div(int64_t(p) * kmax, 256), num_sms() * 8);
+  const unsigned gn = std::min<unsigned>(ceil_div(int64_t(n) * kmax, 256), num_sms() * 8);
+  assemble_side_kernel<<<gp, 256, 0, st>>>(p, k, kmax, w.pos0, w.Ut, b, w.vec[0][0], Uo);
+  CPCA_LAUNCHED();
+  assemble_side_kernel<<<gn, 256, 0, st>>>(n, k, kmax, w.pos1, w.Vt, b, w.vec[1][0], Vo);
+  CPCA_LAUNCHED();
+  if (k == 0) {
+    // no singular value: X = 0; pos maps were not built, so overwrite
+    CPCA_CUDA(cudaMemsetAsync(Uo, 0, sizeof(float) * size_t(p) * kmax, st));
+    CPCA_CUDA(cudaMemsetAsync(Vo, 0, sizeof(float) * size_t(n) * kmax, st));
+  }
+  colnorm_partial_kernel<<<NORM_BLOCKS, 192, 0, st>>>(Uo, p, k, kmax, w.npart_u);
+  CPCA_LAUNCHED();
+  colnorm_partial_kernel<<<NORM_BLOCKS, 192, 0, st>>>(Vo, n, k, kmax, w.npart_v);
+  CPCA_LAUNCHED();
+  const double scale = sqrt(double(n) * double(p) / (double(rr) * double(rc) * (1.0 - prm->delta)));
+  norm_finish_kernel<<<1, 64, 0, st>>>(w.npart_u, w.npart_v, NORM_BLOCKS, k, w.s, scale, w.invu,
+                                       w.invv, so, kmax);
+  CPCA_LAUNCHED();
+  scale_cols_kernel<<<gp, 256, 0, st>>>(Uo, int64_t(p) * kmax, kmax, w.invu);
+  CPCA_LAUNCHED();
+  scale_cols_kernel<<<gn, 256, 0, st>>>(Vo, int64_t(n) * kmax, kmax, w.invv);
+  CPCA_LAUNCHED();
+  if (X) {
+    if (k == 0) {
+      CPCA_CUDA(cudaMemset2DAsync(X, ldx * sizeof(float), 0, size_t(n) * sizeof(float), p, st));
+    } else {
+      dim3 og(ceil_div(n, 128), ceil_div(p, 32));
+      CPCA_PROF("decode_output", st);
+      output_kernel<<<og, 256, 0, st>>>(Uo, kmax, Vo, kmax, so, k, p, n, X, ldx);
+      CPCA_LAUNCHED();
+    }
+  }
+  if (k_out) *k_out = k;
+  int itmax[2] = {0, 0};
+  double resmax[2] = {0, 0};
+  bool capped = false;
+  for (int sd = 0; sd < 2; ++sd)
+    for (int c = 0; c < k; ++c) {
+      itmax[sd] = std::max(itmax[sd], cg_iters[sd * KMAX_LIMIT + c]);
+      resmax[sd] = std::max(resmax[sd], cg_res[sd * KMAX_LIMIT + c]);
+      if (cg_res[sd * KMAX_LIMIT + c] > prm->cg_tol) capped = true;
+    }
+  if (info) {
+    CPCA_CUDA(cudaMemcpyAsync(info->s_tilde, w.s, sizeof(double) * b, cudaMemcpyDeviceToHost, st));
+    CPCA_CUDA(cudaStreamSynchronize(st));
+    info->k = k;
+    info->b = b;
+    info->cg_iters_u = itmax[0];
+    info->cg_iters_v = itmax[1];
+    info->cg_res_u = resmax[0];
+    info->cg_res_v = resmax[1];
+  }
+  if (breakdown) {
+    set_error("cpca_decode: L_aa is not positive definite (a graph component has no sampled node)");
+    return CPCA_ERR_SINGULAR;
+  }
+  if (capped) {
+    set_error("cpca_decode: PCG reached cg_max_iter before cg_tol");
+    return CPCA_ERR_NOT_CONVERGED;
+  }
+  return CPCA_OK;
+}

@@ -1,0 +1,664 @@
+// knn.cu - exact kNN graph and Laplacian (Sec. I graph construction;
+// Sec. VII-A: K nearest neighbours, Gaussian kernel, sigma^2 from the
+// kNN distances).
+//
+// Pipeline (all on the device):
+//   1. candidates: tiled |a|^2 + |b|^2 - 2 a.b ranks every base point for
+//      every query; each query keeps its M best per base-range split
+//      (the tensor-core path in knn_tc.cu replaces this pass on sm_103a
+//      when the shapes allow);
+//   2. recheck: the candidates' squared distances are recomputed directly as
+//      sum_t (a_t - b_t)^2 in FP32 with a fixed summation tree (so d2(i,j)
+//      and d2(j,i) are bitwise equal) and the K best are kept, ties by index;
+//      a certificate checks that no point outside the candidate lists can
+//      beat the K-th; queries that fail it are redone by brute force;
+//   3. graph: OR-symmetrised edge lists, sigma^2, Gaussian weights, degrees
+//      and the Laplacian in CSR with sorted columns and explicit diagonal.
+#include "common.cuh"
+#include "knn_internal.cuh"
+
+namespace cpca {
+namespace {
+
+constexpr int BQ = 64, BB = 64, BD = 16, KNN_THREADS = 256;
+
+__global__ void transpose_kernel(const float* __restrict__ in, int rows, int cols, int64_t ldin,
+                                 float* __restrict__ out, int64_t ldout) {
+  __shared__ float tile[32][33];
+  const int c0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
+  for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+    const int r = r0 + i, c = c0 + threadIdx.x;
+    if (r < rows && c < cols) tile[i][threadIdx.x] = in[int64_t(r) * ldin + c];
+  }
+  __syncthreads();
+  for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+    const int c = c0 + i, r = r0 + threadIdx.x;
+    if (r < rows && c < cols) out[int64_t(c) * ldout + r] = tile[threadIdx.x][i];
+  }
+}
+
+// Squared norms for candidate ranking only (FP32); also the largest norm.
+__global__ void norms_kernel(const float* __restrict__ P, int N, int d, int64_t ld,
+                             float* __restrict__ nrm, unsigned int* __restrict__ nmax_bits) {
+  const int lane = threadIdx.x & 31;
+  const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (w >= N) return;
+  const float* a = P + int64_t(w) * ld;
+  float s = 0.f;
+  for (int t = lane; t < d; t += 32) s = fmaf(a[t], a[t], s);
+  s = warp_sumf(s);
+  if (lane == 0) {
+    nrm[w] = s;
+    atomicMax(nmax_bits, __float_as_uint(s));  // s >= 0: bit order = value order
+  }
+}
+
+// Insert (d, j) into a list sorted ascending by (d, j) of length M.
+template <int M>
+__device__ __forceinline__ void list_insert(float* ld_, int32_t* li, float d, int32_t j) {
+  if (!(d < ld_[M - 1] || (d == ld_[M - 1] && j < li[M - 1]))) return;
+  int pos = M - 1;
+  while (pos > 0 && (d < ld_[pos - 1] || (d == ld_[pos - 1] && j < li[pos - 1]))) {
+    ld_[pos] = ld_[pos - 1];
+    li[pos] = li[pos - 1];
+    --pos;
+  }
+  ld_[pos] = d;
+  li[pos] = j;
+}
+
+// Candidate pass: block (x = query tile of 64, y = split of the base range).
+template <int M>
+__global__ void __launch_bounds__(KNN_THREADS)
+knn_candidates_kernel(const float* __restrict__ P, int N, int d, int64_t ld,
+                      const float* __restrict__ nrm, int splits,
+                      int32_t* __restrict__ cand_i, float* __restrict__ cand_d) {
+  extern __shared__ float smem[];
+  float* As = smem;                    // [BD][BQ]
+  float* Bs = As + BD * BQ;            // [BD][BB]
+  float* Dt = Bs + BD * BB;            // [BQ][BB+1]
+  float* cd = Dt + BQ * (BB + 1);      // [BQ][M]
+  int32_t* ci = reinterpret_cast<int32_t*>(cd + BQ * M);  // [BQ][M]
+
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  const int q0 = blockIdx.x * BQ;
+  const int ntiles = (N + BB - 1) / BB;
+  const int per = (ntiles + splits - 1) / splits;
+  const int t_lo = blockIdx.y * per, t_hi = min(ntiles, t_lo + per);
+
+  for (int e = tid; e < BQ * M; e += KNN_THREADS) {
+    cd[e] = __int_as_float(0x7f800000);
+    ci[e] = -1;
+  }
+  float nq[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int q = q0 + ty * 4 + i;
+    nq[i] = q < N ? nrm[q] : 0.f;
+  }
+  const int lr = tid >> 2, lc = (tid & 3) * 4;
+
+  for (int t = t_lo; t < t_hi; ++t) {
+    const int b0 = t * BB;
+    float acc[4][4] = {};
+    for (int k0 = 0; k0 < d; k0 += BD) {
+      __syncthreads();
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int k = k0 + lc + u;
+        const int q = q0 + lr, b = b0 + lr;
+        As[(lc + u) * BQ + lr] = (q < N && k < d) ? P[int64_t(q) * ld + k] : 0.f;
+        Bs[(lc + u) * BB + lr] = (b < N && k < d) ? P[int64_t(b) * ld + k] : 0.f;
+      }
+      __syncthreads();
+#pragma unroll
+      for (int k = 0; k < BD; ++k) {
+        const float4 a = *reinterpret_cast<const float4*>(As + k * BQ + ty * 4);
+        const float4 b = *reinterpret_cast<const float4*>(Bs + k * BB + tx * 4);
+        const float av[4] = {a.x, a.y, a.z, a.w}, bv[4] = {b.x, b.y, b.z, b.w};
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int q = q0 + ty * 4 + i, b = b0 + tx * 4 + j;
+        float v = __int_as_float(0x7f800000);
+        if (b < N && b != q) v = nq[i] + nrm[b] - 2.f * acc[i][j];
+        Dt[(ty * 4 + i) * (BB + 1) + tx * 4 + j] = v;
+      }
+    __syncthreads();
+    if (tid < BQ) {
+      float* myd = cd + tid * M;
+      int32_t* myi = ci + tid * M;
+      const float* row = Dt + tid * (BB + 1);
+      for (int j = 0; j < BB; ++j) {
+        const float v = row[j];
+        if (v <= myd[M - 1]) list_insert<M>(myd, myi, v, b0 + j);
+      }
+    }
+  }
+  __syncthreads();
+  for (int e = tid; e < BQ * M; e += KNN_THREADS) {
+    const int q = q0 + e / M;
+    if (q < N) {
+      const int64_t o = (int64_t(blockIdx.y) * N + q) * M + (e % M);
+      cand_i[o] = ci[e];
+      cand_d[o] = cd[e];
+    }
+  }
+}
+
+}  // namespace
+
+// Exact squared distance, FP32, fixed summation tree: lane l sums
+// coordinates l, l+32, ... (or float4 groups), then a butterfly; lane 0's
+// value is broadcast. (a-b)^2 == (b-a)^2, so d2(i,j) == d2(j,i) bitwise.
+__device__ __forceinline__ float exact_d2_warp(const float* __restrict__ a,
+                                               const float* __restrict__ b, int d, bool vec4) {
+  const int lane = threadIdx.x & 31;
+  float s = 0.f;
+  if (vec4) {
+    const float4* a4 = reinterpret_cast<const float4*>(a);
+    const float4* b4 = reinterpret_cast<const float4*>(b);
+    for (int t = lane; t < (d >> 2); t += 32) {
+      const float4 x = __ldg(a4 + t), y = __ldg(b4 + t);
+      float dx = x.x - y.x;
+      s = fmaf(dx, dx, s);
+      dx = x.y - y.y;
+      s = fmaf(dx, dx, s);
+      dx = x.z - y.z;
+      s = fmaf(dx, dx, s);
+      dx = x.w - y.w;
+      s = fmaf(dx, dx, s);
+    }
+  } else {
+    for (int t = lane; t < d; t += 32) {
+      const float dx = __ldg(a + t) - __ldg(b + t);
+      s = fmaf(dx, dx, s);
+    }
+  }
+  s = warp_sumf(s);
+  return __shfl_sync(0xffffffffu, s, 0);
+}
+
+namespace {
+
+constexpr int RECHECK_WARPS = 4;
+
+// Recheck: warp per query. Candidates of all splits are re-scored exactly,
+// the K best (by (d2, j)) are kept, and the certificate is evaluated.
+__global__ void __launch_bounds__(RECHECK_WARPS * 32)
+knn_recheck_kernel(const float* __restrict__ P, int N, int d, int64_t ld, bool vec4, int K,
+                   int M, int splits, const int32_t* __restrict__ cand_i,
+                   const float* __restrict__ cand_d, const float* __restrict__ nrm,
+                   const unsigned int* __restrict__ nmax_bits, float err_rel,
+                   int32_t* __restrict__ out_i, float* __restrict__ out_d,
+                   int32_t* __restrict__ redo, int32_t* __restrict__ n_redo) {
+  extern __shared__ float sm[];
+  const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int C = splits * M;
+  float* sd = sm + wib * C * 2;
+  int32_t* si = reinterpret_cast<int32_t*>(sd + C);
+  const int q = blockIdx.x * RECHECK_WARPS + wib;
+  if (q >= N) return;
+  const float* a = P + int64_t(q) * ld;
+  for (int c = 0; c < C; ++c) {
+    const int s = c / M, m = c % M;
+    const int j = cand_i[(int64_t(s) * N + q) * M + m];
+    float v = __int_as_float(0x7f800000);
+    if (j >= 0) v = exact_d2_warp(a, P + int64_t(j) * ld, d, vec4);
+    if (v != v) v = __int_as_float(0x7f800000);  // NaN input ranks last
+    if (lane == 0) {
+      sd[c] = v;
+      si[c] = j;
+    }
+  }
+  __syncwarp();
+  float dK = 0.f;
+  for (int r = 0; r < K; ++r) {
+    float bd = __int_as_float(0x7f800000);
+    int bj = 0x7fffffff, bc = -1;
+    for (int c = lane; c < C; c += 32) {
+      const int j = si[c];
+      if (j < 0) continue;
+      const float v = sd[c];
+      if (v < bd || (v == bd && j < bj)) {
+        bd = v;
+        bj = j;
+        bc = c;
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const float od = __shfl_xor_sync(0xffffffffu, bd, o);
+      const int oj = __shfl_xor_sync(0xffffffffu, bj, o);
+      const int oc = __shfl_xor_sync(0xffffffffu, bc, o);
+      if (od < bd || (od == bd && oj < bj)) {
+        bd = od;
+        bj = oj;
+        bc = oc;
+      }
+    }
+    if (lane == 0) {
+      out_i[int64_t(q) * K + r] = bj;
+      out_d[int64_t(q) * K + r] = bd;
+      if (bc >= 0) si[bc] = -1;
+    }
+    dK = bd;
+    __syncwarp();
+  }
+  // Certificate: every point outside split s's list has an approximate
+  // distance >= that list's last entry, and the approximation is within
+  // e = err_rel * (|q|^2 + max |b|^2) of the direct sum.
+  if (lane == 0) {
+    const float e = err_rel * (nrm[q] + __uint_as_float(*nmax_bits));
+    bool ok = true;
+    for (int s = 0; s < splits; ++s) {
+      const float thr = cand_d[(int64_t(s) * N + q) * M + (M - 1)];
+      if (!(thr - e > dK)) {
+        if (cand_i[(int64_t(s) * N + q) * M + (M - 1)] >= 0) ok = false;  // full list
+      }
+    }
+    if (!ok) redo[atomicAdd(n_redo, 1)] = q;
+  }
+}
+
+// Brute force for queries without a certificate: warp per query, every
+// other point scored with the same exact function.
+__global__ void knn_bruteforce_kernel(const float* __restrict__ P, int N, int d, int64_t ld,
+                                      bool vec4, int K, const int32_t* __restrict__ redo,
+                                      const int32_t* __restrict__ n_redo,
+                                      int32_t* __restrict__ out_i, float* __restrict__ out_d) {
+  __shared__ float ld_[RECHECK_WARPS][32];
+  __shared__ int32_t li[RECHECK_WARPS][32];
+  const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int w = blockIdx.x * RECHECK_WARPS + wib; w < *n_redo; w += gridDim.x * RECHECK_WARPS) {
+    const int q = redo[w];
+    const float* a = P + int64_t(q) * ld;
+    if (lane < 32) {
+      ld_[wib][lane] = __int_as_float(0x7f800000);
+      li[wib][lane] = 0x7fffffff;
+    }
+    __syncwarp();
+    for (int j = 0; j < N; ++j) {
+      if (j == q) continue;
+      float v = exact_d2_warp(a, P + int64_t(j) * ld, d, vec4);
+      if (v != v) v = __int_as_float(0x7f800000);
+      if (lane == 0) {
+        float* L = ld_[wib];
+        int32_t* I = li[wib];
+        if (v < L[K - 1] || (v == L[K - 1] && j < I[K - 1])) {
+          int pos = K - 1;
+          while (pos > 0 && (v < L[pos - 1] || (v == L[pos - 1] && j < I[pos - 1]))) {
+            L[pos] = L[pos - 1];
+            I[pos] = I[pos - 1];
+            --pos;
+          }
+          L[pos] = v;
+          I[pos] = j;
+        }
+      }
+      __syncwarp();
+    }
+    if (lane < K) {
+      out_i[int64_t(q) * K + lane] = li[wib][lane];
+      out_d[int64_t(q) * K + lane] = ld_[wib][lane];
+    }
+    __syncwarp();
+  }
+}
+
+// ------------------------------------------------------------ graph build --
+constexpr int RED_BLOCKS = 256;
+
+// Deterministic FP64 sum of an FP32 array: fixed block partials, then one
+// block adds the partials in order.
+__global__ void sum_partials_kernel(const float* __restrict__ x, int64_t m, double* __restrict__ part) {
+  __shared__ double red[32];
+  double s = 0.0;
+  for (int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; t < m;
+       t += int64_t(gridDim.x) * blockDim.x)
+    s += double(x[t]);
+  s = block_sum(s, red);
+  if (threadIdx.x == 0) part[blockIdx.x] = s;
+}
+__global__ void sigma2_finish_kernel(const double* __restrict__ part, int nparts, int64_t m,
+                                     double given, double* __restrict__ sigma2) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    if (given > 0) {
+      *sigma2 = given;
+    } else {
+      double s = 0.0;
+      for (int i = 0; i < nparts; ++i) s += part[i];
+      *sigma2 = s / double(m);
+    }
+  }
+}
+
+__global__ void indeg_kernel(const int32_t* __restrict__ knn, int N, int K, int32_t* __restrict__ indeg) {
+  for (int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; t < int64_t(N) * K;
+       t += int64_t(gridDim.x) * blockDim.x)
+    atomicAdd(&indeg[knn[t]], 1);
+}
+
+// Single-block exclusive scan of (base + add[i]) into out[0..N] (int64).
+__global__ void scan_kernel(const int32_t* __restrict__ add, int base, int N, int64_t* __restrict__ out) {
+  __shared__ int64_t sh[1024];
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int chunk = (N + nt - 1) / nt;
+  const int lo = min(N, tid * chunk), hi = min(N, lo + chunk);
+  int64_t s = 0;
+  for (int i = lo; i < hi; ++i) s += base + add[i];
+  sh[tid] = s;
+  __syncthreads();
+  for (int o = 1; o < nt; o <<= 1) {
+    int64_t v = tid >= o ? sh[tid - o] : 0;
+    __syncthreads();
+    sh[tid] += v;
+    __syncthreads();
+  }
+  int64_t run = sh[tid] - s;
+  for (int i = lo; i < hi; ++i) {
+    out[i] = run;
+    run += base + add[i];
+  }
+  if (tid == nt - 1) out[N] = sh[nt - 1];
+}
+
+__global__ void fill_edges_kernel(const int32_t* __restrict__ knn, const float* __restrict__ kd2, int N,
+                                  int K, const int64_t* __restrict__ off, int32_t* __restrict__ cursor,
+                                  int32_t* __restrict__ e_nbr, float* __restrict__ e_d2) {
+  for (int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; t < int64_t(N) * K;
+       t += int64_t(gridDim.x) * blockDim.x) {
+    const int i = int(t / K), k = int(t % K);
+    const int j = knn[t];
+    const float v = kd2[t];
+    e_nbr[off[i] + k] = j;
+    e_d2[off[i] + k] = v;
+    const int64_t slot = off[j] + K + atomicAdd(&cursor[j], 1);
+    e_nbr[slot] = i;
+    e_d2[slot] = v;
+  }
+}
+
+// Per node: sort its edge list by neighbour, drop duplicates (an edge seen
+// from both ends carries the same bitwise d2), count what is left.
+__global__ void dedupe_kernel(int N, const int64_t* __restrict__ off, int32_t* __restrict__ e_nbr,
+                              float* __restrict__ e_d2, int32_t* __restrict__ uniq) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  const int64_t lo = off[i], hi = off[i + 1];
+  for (int64_t a = lo + 1; a < hi; ++a) {
+    const int32_t j = e_nbr[a];
+    const float v = e_d2[a];
+    int64_t b = a;
+    while (b > lo && e_nbr[b - 1] > j) {
+      e_nbr[b] = e_nbr[b - 1];
+      e_d2[b] = e_d2[b - 1];
+      --b;
+    }
+    e_nbr[b] = j;
+    e_d2[b] = v;
+  }
+  int64_t w = lo;
+  for (int64_t a = lo; a < hi; ++a) {
+    if (a > lo && e_nbr[a] == e_nbr[w - 1]) continue;
+    e_nbr[w] = e_nbr[a];
+    e_d2[w] = e_d2[a];
+    ++w;
+  }
+  uniq[i] = int32_t(w - lo);
+}
+
+__global__ void degree_kernel(int N, const int64_t* __restrict__ off, const int32_t* __restrict__ uniq,
+                              const float* __restrict__ e_d2, const double* __restrict__ sigma2,
+                              double* __restrict__ deg) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  const double s2 = *sigma2;
+  double D = 0.0;
+  for (int64_t a = off[i]; a < off[i] + uniq[i]; ++a) D += exp(-double(e_d2[a]) / s2);
+  deg[i] = D;
+}
+
+__global__ void assemble_kernel(int N, int lap_type, const int64_t* __restrict__ off,
+                                const int32_t* __restrict__ uniq, const int32_t* __restrict__ e_nbr,
+                                const float* __restrict__ e_d2, const double* __restrict__ sigma2,
+                                const double* __restrict__ deg, const int64_t* __restrict__ rowptr,
+                                int64_t nnz_cap, int32_t* __restrict__ col, float* __restrict__ val,
+                                float* __restrict__ weight) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  if (rowptr[N] > nnz_cap) return;  // reported by the host
+  const double s2 = *sigma2;
+  const double Di = deg[i];
+  int64_t w = rowptr[i];
+  bool diag_done = false;
+  const int64_t lo = off[i], hi = off[i] + uniq[i];
+  for (int64_t a = lo; a <= hi; ++a) {
+    const bool at_end = a == hi;
+    const int32_t j = at_end ? 0x7fffffff : e_nbr[a];
+    if (!diag_done && j > i) {
+      col[w] = i;
+      val[w] = lap_type == CPCA_LAP_COMBINATORIAL ? float(Di) : (Di > 0 ? 1.f : 0.f);
+      if (weight) weight[w] = 0.f;
+      ++w;
+      diag_done = true;
+    }
+    if (at_end) break;
+    const double Wij = exp(-double(e_d2[a]) / s2);
+    col[w] = j;
+    if (lap_type == CPCA_LAP_COMBINATORIAL) {
+      val[w] = float(-Wij);
+    } else {
+      const double Dj = deg[j];
+      val[w] = (Di > 0 && Dj > 0) ? float(-Wij / sqrt(Di * Dj)) : 0.f;
+    }
+    if (weight) weight[w] = float(Wij);
+    ++w;
+  }
+}
+
+}  // namespace
+
+// Layout of the kNN workspace; shared by the size query and the call.
+struct KnnWs {
+  float* Pt;          // transposed points (transposed input only)
+  float* nrm;
+  unsigned int* nmax;
+  int32_t* cand_i;
+  float* cand_d;
+  int32_t* kidx;      // N*K (used when the caller passes no knn_idx)
+  float* kd2;
+  int32_t* redo;
+  int32_t* n_redo;
+  double* part;
+  double* sigma2;
+  int32_t* indeg;
+  int32_t* cursor;
+  int64_t* off;
+  int32_t* e_nbr;
+  float* e_d2;
+  int32_t* uniq;
+  double* deg;
+  size_t bytes;
+};
+
+static int knn_splits(int N) {
+  const int qt = (N + BQ - 1) / BQ;
+  int s = 1;
+  while (s < 8 && qt * s < 2 * num_sms() && (N + BB - 1) / BB >= 4 * s * 2) s *= 2;
+  return s;
+}
+static int knn_M(int K) { return K <= 16 ? 32 : 64; }
+
+static KnnWs knn_layout(void* ws, int N, int d, int K, int transposed) {
+  Carve c(ws);
+  KnnWs w{};
+  const int S = knn_splits(N), M = knn_M(K);
+  w.Pt = transposed ? c.take<float>(size_t(N) * d) : nullptr;
+  w.nrm = c.take<float>(N);
+  w.nmax = c.take<unsigned int>(1);
+  w.cand_i = c.take<int32_t>(size_t(S) * N * M);
+  w.cand_d = c.take<float>(size_t(S) * N * M);
+  w.kidx = c.take<int32_t>(size_t(N) * K);
+  w.kd2 = c.take<float>(size_t(N) * K);
+  w.redo = c.take<int32_t>(N);
+  w.n_redo = c.take<int32_t>(1);
+  w.part = c.take<double>(RED_BLOCKS);
+  w.sigma2 = c.take<double>(1);
+  w.indeg = c.take<int32_t>(N);
+  w.cursor = c.take<int32_t>(N);
+  w.off = c.take<int64_t>(size_t(N) + 1);
+  w.e_nbr = c.take<int32_t>(size_t(2) * N * K);
+  w.e_d2 = c.take<float>(size_t(2) * N * K);
+  w.uniq = c.take<int32_t>(N);
+  w.deg = c.take<double>(N);
+  w.bytes = c.bytes();
+  return w;
+}
+
+// kNN lists (idx, d2) of points P (N x d, row stride ld, K-major) into
+// out_i/out_d; P must be 16-byte aligned with ld % 4 == 0 for vector loads.
+cpca_status knn_lists(const float* P, int N, int d, int64_t ld, int K, const KnnWs& w,
+                      int32_t* out_i, float* out_d, cudaStream_t st) {
+  const int S = knn_splits(N), M = knn_M(K);
+  const bool vec4 = (d % 4 == 0) && (ld % 4 == 0) && ((reinterpret_cast<uintptr_t>(P) & 15) == 0);
+  CPCA_CUDA(cudaMemsetAsync(w.nmax, 0, sizeof(unsigned int), st));
+  CPCA_CUDA(cudaMemsetAsync(w.n_redo, 0, sizeof(int32_t), st));
+  CPCA_PROF("knn_norms", st);
+  norms_kernel<<<ceil_div(int64_t(N) * 32, 256), 256, 0, st>>>(P, N, d, ld, w.nrm, w.nmax);
+  CPCA_LAUNCHED();
+  bool done = false;
+  CPCA_TRY(knn_candidates_tc(P, N, d, ld, M, S, w.nrm, w.cand_i, w.cand_d, &done, st));
+  if (!done) {
+    const size_t smem = sizeof(float) * (BD * BQ + BD * BB + BQ * (BB + 1)) + size_t(BQ) * M * 8;
+    dim3 grid(ceil_div(N, BQ), S);
+    if (M == 32) {
+      CPCA_CUDA(cudaFuncSetAttribute(knn_candidates_kernel<32>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
+      CPCA_PROF("knn_candidates_simt", st);
+      knn_candidates_kernel<32><<<grid, KNN_THREADS, smem, st>>>(P, N, d, ld, w.nrm, S, w.cand_i, w.cand_d);
+    } else {
+      CPCA_CUDA(cudaFuncSetAttribute(knn_candidates_kernel<64>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
+      CPCA_PROF("knn_candidates_simt", st);
+      knn_candidates_kernel<64><<<grid, KNN_THREADS, smem, st>>>(P, N, d, ld, w.nrm, S, w.cand_i, w.cand_d);
+    }
+    CPCA_LAUNCHED();
+  }
+  // FP32 expansion error model for the certificate: about 4 sqrt(d) + 16
+  // roundings of size 2^-24 relative to |a|^2 + |b|^2 (the tensor-core pass
+  // reports its own, larger, bound through knn_candidates_tc).
+  const float err_rel = done ? knn_tc_err_rel(d) : float((4.0 * sqrt(double(d)) + 16.0) * 0x1.0p-24);
+  const size_t rsm = size_t(RECHECK_WARPS) * S * M * 8;
+  CPCA_CUDA(cudaFuncSetAttribute(knn_recheck_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(rsm)));
+  CPCA_PROF("knn_recheck", st);
+  knn_recheck_kernel<<<ceil_div(N, RECHECK_WARPS), RECHECK_WARPS * 32, rsm, st>>>(
+      P, N, d, ld, vec4, K, M, S, w.cand_i, w.cand_d, w.nrm, w.nmax, err_rel, out_i, out_d, w.redo,
+      w.n_redo);
+  CPCA_LAUNCHED();
+  CPCA_PROF("knn_bruteforce", st);
+  knn_bruteforce_kernel<<<num_sms() * 4, RECHECK_WARPS * 32, 0, st>>>(P, N, d, ld, vec4, K, w.redo,
+                                                                       w.n_redo, out_i, out_d);
+  CPCA_LAUNCHED();
+  return CPCA_OK;
+}
+
+// Graph + Laplacian from kNN lists.
+cpca_status graph_from_knn(const int32_t* kidx, const float* kd2, int N, int K, int lap_type,
+                           double sigma2, const KnnWs& w, int64_t* rowptr, int32_t* col,
+                           float* val, float* weight, int64_t nnz_cap, cudaStream_t st) {
+  const int64_t m = int64_t(N) * K;
+  sum_partials_kernel<<<RED_BLOCKS, 256, 0, st>>>(kd2, m, w.part);
+  CPCA_LAUNCHED();
+  sigma2_finish_kernel<<<1, 32, 0, st>>>(w.part, RED_BLOCKS, m, sigma2, w.sigma2);
+  CPCA_LAUNCHED();
+  CPCA_CUDA(cudaMemsetAsync(w.indeg, 0, sizeof(int32_t) * N, st));
+  CPCA_CUDA(cudaMemsetAsync(w.cursor, 0, sizeof(int32_t) * N, st));
+  const unsigned eb = std::min<unsigned>(ceil_div(m, 256), num_sms() * 8);
+  indeg_kernel<<<eb, 256, 0, st>>>(kidx, N, K, w.indeg);
+  CPCA_LAUNCHED();
+  scan_kernel<<<1, 1024, 0, st>>>(w.indeg, K, N, w.off);
+  CPCA_LAUNCHED();
+  fill_edges_kernel<<<eb, 256, 0, st>>>(kidx, kd2, N, K, w.off, w.cursor, w.e_nbr, w.e_d2);
+  CPCA_LAUNCHED();
+  CPCA_PROF("graph_dedupe", st);
+  dedupe_kernel<<<ceil_div(N, 128), 128, 0, st>>>(N, w.off, w.e_nbr, w.e_d2, w.uniq);
+  CPCA_LAUNCHED();
+  scan_kernel<<<1, 1024, 0, st>>>(w.uniq, 1, N, rowptr);
+  CPCA_LAUNCHED();
+  degree_kernel<<<ceil_div(N, 128), 128, 0, st>>>(N, w.off, w.uniq, w.e_d2, w.sigma2, w.deg);
+  CPCA_LAUNCHED();
+  CPCA_PROF("graph_assemble", st);
+  assemble_kernel<<<ceil_div(N, 128), 128, 0, st>>>(N, lap_type, w.off, w.uniq, w.e_nbr, w.e_d2,
+                                                    w.sigma2, w.deg, rowptr, nnz_cap, col, val, weight);
+  CPCA_LAUNCHED();
+  return CPCA_OK;
+}
+
+}  // namespace cpca
+
+using namespace cpca;
+
+extern "C" size_t cpca_knn_graph_workspace_size(int32_t npts, int32_t dim, int32_t K,
+                                                int32_t transposed) {
+  if (npts <= 0 || dim <= 0 || K <= 0) return 0;
+  return knn_layout(nullptr, npts, dim, K, transposed).bytes;
+}
+
+extern "C" cpca_status cpca_knn_graph(const float* pts, int32_t npts, int32_t dim, int64_t ld,
+                                      int32_t transposed, int32_t K, int32_t lap_type,
+                                      double sigma2, int64_t* rowptr, int32_t* col, float* val,
+                                      float* weight, int64_t nnz_cap, int32_t* knn_idx,
+                                      float* knn_d2, int64_t* nnz_out, double* sigma2_out,
+                                      void* ws, size_t ws_bytes, void* stream) {
+  clear_error();
+  CPCA_CHECK_ARG(pts && rowptr && col && val, "cpca_knn_graph: null pointer");
+  CPCA_CHECK_ARG(npts >= 2 && dim >= 1, "cpca_knn_graph: need npts >= 2, dim >= 1");
+  CPCA_CHECK_ARG(K >= 1 && K <= 32 && K < npts, "cpca_knn_graph: need 1 <= K <= 32, K < npts");
+  CPCA_CHECK_ARG(transposed == 0 || transposed == 1, "cpca_knn_graph: transposed must be 0/1");
+  CPCA_CHECK_ARG(ld >= (transposed ? npts : dim), "cpca_knn_graph: leading dimension too small");
+  CPCA_CHECK_ARG(lap_type == CPCA_LAP_NORMALIZED || lap_type == CPCA_LAP_COMBINATORIAL,
+                 "cpca_knn_graph: bad lap_type");
+  CPCA_CHECK_ARG(nnz_cap >= int64_t(npts) * (2 * K + 1), "cpca_knn_graph: nnz_cap < npts*(2K+1)");
+  const KnnWs w = knn_layout(ws, npts, dim, K, transposed);
+  if (ws_bytes < w.bytes || !ws) {
+    set_error("cpca_knn_graph: workspace %zu bytes < required %zu", ws_bytes, w.bytes);
+    return CPCA_ERR_WORKSPACE;
+  }
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const float* P = pts;
+  int64_t pld = ld;
+  if (transposed) {
+    // Point-major copy of the columns (rows of length dim, ld = dim).
+    dim3 blk(32, 8), grd(ceil_div(npts, 32), ceil_div(dim, 32));
+    CPCA_PROF("knn_transpose", st);
+    transpose_kernel<<<grd, blk, 0, st>>>(pts, dim, npts, ld, w.Pt, dim);
+    CPCA_LAUNCHED();
+    P = w.Pt;
+    pld = dim;
+  }
+  int32_t* oi = knn_idx ? knn_idx : w.kidx;
+  float* od = knn_d2 ? knn_d2 : w.kd2;
+  CPCA_TRY(knn_lists(P, npts, dim, pld, K, w, oi, od, st));
+  CPCA_TRY(graph_from_knn(oi, od, npts, K, lap_type, sigma2, w, rowptr, col, val, weight, nnz_cap, st));
+  int64_t nnz = 0;
+  double s2 = 0;
+  CPCA_CUDA(cudaMemcpyAsync(&nnz, rowptr + npts, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+  CPCA_CUDA(cudaMemcpyAsync(&s2, w.sigma2, sizeof(double), cudaMemcpyDeviceToHost, st));
+  CPCA_CUDA(cudaStreamSynchronize(st));
+  if (nnz_out) *nnz_out = nnz;
+  if (sigma2_out) *sigma2_out = s2;
+  if (nnz > nnz_cap) {
+    set_error("cpca_knn_graph: nnz %lld exceeds nnz_cap %lld", (long long)nnz, (long long)nnz_cap);
+    return CPCA_ERR_CAPACITY;
+  }
+  return CPCA_OK;
+}

@@ -1,0 +1,56 @@
+"""The C ABI library loads and exports every function include/cpca.h
+declares; argument errors are reported on the host (no GPU needed)."""
+import ctypes as C
+
+import pytest
+
+from tests._util import header_functions
+
+
+@pytest.fixture(scope="module")
+def capi():
+    from paper_1602_02070_gb300 import capi as m
+    m.lib()
+    return m
+
+
+def test_exports_every_declared_function(capi):
+    L = capi.lib()
+    declared = header_functions()
+    assert len(declared) >= 10
+    for name in declared:
+        assert hasattr(L, name), name
+    assert set(capi.exported_names()) <= set(declared)
+    assert set(declared) <= set(capi.exported_names())
+
+
+def test_version_and_counter(capi):
+    assert capi.lib().cpca_version() >= 100
+    assert capi.lib().cpca_launch_count() >= 0
+
+
+def test_invalid_arguments_rejected_on_host(capi):
+    L = capi.lib()
+    om = C.c_void_p(16)
+    st = L.cpca_sample(0, 10, 10, 11, 5, None, 0, om, om, None, 0, None)
+    assert st == capi.CPCA_ERR_INVALID_ARG
+    assert b"rho" in L.cpca_last_error()
+    st = L.cpca_knn_graph(C.c_void_p(16), 100, 8, 8, 0, 40, 0, -1.0, om, om, om, None, 100000,
+                          None, None, None, None, None, 0, None)
+    assert st == capi.CPCA_ERR_INVALID_ARG and b"K" in L.cpca_last_error()
+    prm = capi.frpcag_params(max_iter=-1)
+    lr = capi.cpca_csr(4, 4, 16, 16, 16)
+    st = L.cpca_frpcag_solve(C.c_void_p(16), 4, 4, 4, C.byref(lr), C.byref(lr), C.byref(prm),
+                             C.c_void_p(16), 4, None, C.c_void_p(16), 1 << 20, None)
+    assert st == capi.CPCA_ERR_INVALID_ARG
+    dprm = capi.decode_params(kmax=64)
+    st = L.cpca_decode(C.c_void_p(16), 2, 2, 2, om, om, 4, 4, C.byref(lr), C.byref(lr),
+                       C.byref(dprm), None, 4, None, None, None, None, None, C.c_void_p(16), 1 << 20, None)
+    assert st == capi.CPCA_ERR_INVALID_ARG and b"kmax" in L.cpca_last_error()
+
+
+def test_workspace_queries_are_host_only(capi):
+    L = capi.lib()
+    assert L.cpca_frpcag_workspace_size(2576, 250) >= 2 * 2576 * 250 * 4
+    assert L.cpca_decode_workspace_size(10304, 1000, 2576, 250, 32) > 0
+    assert L.cpca_decode_workspace_size(10, 10, 5, 5, 64) == 0

@@ -143,10 +143,11 @@ cpca_status cpca_sample(uint64_t seed, int32_t p, int32_t n, int32_t rho_r, int3
  * with the norms from `power_iters` power iterations in FP64 (start vector
  * u_i - 1/2, u the SplitMix64 uniforms of (power_seed, stream 2 for Lr,
  * 3 for Lc)), or 1 when that denominator is 0. With eps > 0 the loop stops
- * once |Z_{j+1} - Z_j|_F^2 < eps |Z_j|_F^2, tested every check_every
- * iterations on the host; eps = 0 runs exactly max_iter iterations with no
- * synchronisation. The output X (rr x rc, leading dimension ldx) is the last
- * S_j. FP32 arithmetic, FP64 reductions.
+ * once |Z_{j+1} - Z_j|_F^2 < eps |Z_j|_F^2 (tested on the device after every
+ * iteration); eps = 0 runs exactly max_iter iterations. All iterations run
+ * in one cooperative kernel (one bounded grid barrier per iteration); the
+ * call does not synchronise unless `info` is given. The output X (rr x rc,
+ * leading dimension ldx) is the last S_j. FP32 arithmetic, FP64 reductions.
  * Lr is rr x rr, Lc is rc x rc, both symmetric.
  * `info` (host, may be NULL): if given, the call SYNCHRONISES and fills it,
  * including the FP64 objective of X.
@@ -157,9 +158,9 @@ typedef struct cpca_frpcag_params {
   double step;          /* lambda; <= 0 selects 1/beta' by power iteration */
   int32_t max_iter;     /* J >= 0 */
   double eps;           /* stopping tolerance; 0 = exactly max_iter iterations */
-  int32_t check_every;  /* iterations between host checks when eps > 0 (>= 1) */
   int32_t power_iters;  /* power iterations per Laplacian (>= 1) */
   uint64_t power_seed;
+  int32_t tile_rows;    /* rows per block tile: 0 = automatic, else 1, 2, 4 or 8 */
 } cpca_frpcag_params;
 
 typedef struct cpca_solve_info {

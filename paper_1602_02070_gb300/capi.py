@@ -44,8 +44,8 @@ class cpca_csr(C.Structure):
 
 class cpca_frpcag_params(C.Structure):
     _fields_ = [("gamma_r", C.c_double), ("gamma_c", C.c_double), ("step", C.c_double),
-                ("max_iter", C.c_int32), ("eps", C.c_double), ("check_every", C.c_int32),
-                ("power_iters", C.c_int32), ("power_seed", C.c_uint64)]
+                ("max_iter", C.c_int32), ("eps", C.c_double),
+                ("power_iters", C.c_int32), ("power_seed", C.c_uint64), ("tile_rows", C.c_int32)]
 
 
 class cpca_solve_info(C.Structure):
@@ -243,10 +243,10 @@ def cpca_sample(seed: int, p: int, n: int, rho_r: int, rho_c: int, Y: torch.Tens
     return om_r, om_c, Yt
 
 
-def frpcag_params(gamma_r=1.0, gamma_c=1.0, step=-1.0, max_iter=300, eps=0.0, check_every=25,
-                  power_iters=200, power_seed=0) -> cpca_frpcag_params:
-    return cpca_frpcag_params(gamma_r, gamma_c, step, max_iter, eps, check_every, power_iters,
-                              power_seed)
+def frpcag_params(gamma_r=1.0, gamma_c=1.0, step=-1.0, max_iter=300, eps=0.0,
+                  power_iters=200, power_seed=0, tile_rows=0) -> cpca_frpcag_params:
+    return cpca_frpcag_params(gamma_r, gamma_c, step, max_iter, eps, power_iters, power_seed,
+                              tile_rows)
 
 
 def cpca_frpcag_solve(Yt: torch.Tensor, Lr: Csr, Lc: Csr, params: cpca_frpcag_params | None = None,
@@ -267,7 +267,7 @@ def cpca_frpcag_solve(Yt: torch.Tensor, Lr: Csr, Lc: Csr, params: cpca_frpcag_pa
     return X, info
 
 
-def decode_params(rank_ratio=0.1, k_override=0, kmax=32, delta=0.0, cg_tol=1e-6, cg_max_iter=0,
+def decode_params(rank_ratio=0.1, k_override=0, kmax=24, delta=0.0, cg_tol=1e-6, cg_max_iter=0,
                   svd_iters=6, svd_seed=0) -> cpca_decode_params:
     return cpca_decode_params(rank_ratio, k_override, kmax, delta, cg_tol, cg_max_iter, svd_iters,
                               svd_seed)

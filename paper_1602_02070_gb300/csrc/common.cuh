@@ -141,37 +141,52 @@ __device__ __forceinline__ double block_sum(double v, double* red) {
 }
 
 // ---------------------------------------------------------- grid barrier --
-// Sense-counting barrier for cooperative launches (all blocks co-resident).
-// Every wait is bounded: after kBarrierSpinLimit polls the block records a
-// timeout in *err and stops waiting; callers then leave their loops.
+// Counting barrier for cooperative launches (all blocks co-resident): one
+// arrival counter (atom.add.acq_rel), the last arriver resets it and bumps
+// the generation (release) that the others poll (ld.acquire). Every wait is
+// bounded: after kBarrierSpinLimit polls the block records a timeout in
+// *err and stops waiting; callers then leave their loops.
 constexpr long long kBarrierSpinLimit = 1ll << 23;  // ~ 1-2 s with backoff
+constexpr int kBarrierCounters = 1;
 
 struct GridBar {
-  unsigned int* count;
+  unsigned int* count;  // zeroed before the launch
   unsigned int* gen;
   int* err;
 };
 
+__device__ __forceinline__ unsigned int ld_acquire_u32(const unsigned int* p) {
+  unsigned int v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ unsigned int atom_add_acq_rel_u32(unsigned int* p, unsigned int v) {
+  unsigned int r;
+  asm volatile("atom.add.acq_rel.gpu.global.u32 %0, [%1], %2;" : "=r"(r) : "l"(p), "r"(v) : "memory");
+  return r;
+}
+__device__ __forceinline__ void red_add_release_u32(unsigned int* p, unsigned int v) {
+  asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
 __device__ __forceinline__ bool grid_sync(const GridBar& b) {
   __syncthreads();
   if (threadIdx.x == 0) {
-    volatile unsigned int* vgen = b.gen;
-    const unsigned int g = *vgen;
-    __threadfence();
     const unsigned int nb = gridDim.x * gridDim.y * gridDim.z;
-    if (atomicAdd(b.count, 1u) == nb - 1) {
+    const unsigned int g = ld_acquire_u32(b.gen);
+    __threadfence();  // the block's writes (ordered by __syncthreads) before arrival
+    if (atom_add_acq_rel_u32(b.count, 1u) == nb - 1) {
       *b.count = 0;
-      __threadfence();
-      atomicAdd(b.gen, 1u);
+      red_add_release_u32(b.gen, 1u);
     } else {
       long long spins = 0;
-      while (*vgen == g) {
+      while (ld_acquire_u32(b.gen) == g) {
         if (*(volatile int*)b.err) break;
         if (++spins > kBarrierSpinLimit) {
           atomicExch(b.err, 1);
           break;
         }
-        __nanosleep(64);
+        __nanosleep(100);
       }
     }
     __threadfence();

@@ -102,74 +102,59 @@ gemm_tn_tall(const float* __restrict__ A, int64_t lda, int m, int n, const float
   }
 }
 
-constexpr int GRAM_BLOCKS = 64;
+constexpr int GRAM_ROWS = 64;
 
-// Partial Gram Q^T Q over a fixed row range per block, FP64.
+// G += Q^T Q (b x b, FP64, zeroed by the caller): each block takes 64 rows,
+// sums their products in FP32 and adds the block total to G in FP64.
 __global__ void __launch_bounds__(256)
-gram_partial_kernel(const float* __restrict__ Q, int m, int b, double* __restrict__ part) {
-  __shared__ float Qs[32][BMAX];
+gram_kernel(const float* __restrict__ Q, int m, int b, double* __restrict__ G) {
+  __shared__ float Qs[GRAM_ROWS][BMAX + 1];
   const int tid = threadIdx.x;
-  const int per = (m + gridDim.x - 1) / gridDim.x;
-  const int lo = blockIdx.x * per, hi = min(m, lo + per);
-  double acc[16];
-#pragma unroll
-  for (int u = 0; u < 16; ++u) acc[u] = 0.0;
-  for (int i0 = lo; i0 < hi; i0 += 32) {
-    for (int e = tid; e < 32 * b; e += 256) {
-      const int i = e / b, c = e % b;
-      Qs[i][c] = (i0 + i < hi) ? Q[int64_t(i0 + i) * b + c] : 0.f;
-    }
-    __syncthreads();
-#pragma unroll
-    for (int u = 0; u < 16; ++u) {
-      const int pr = tid + u * 256;
-      if (pr < b * b) {
-        const int a = pr / b, c = pr % b;
-        double s = 0.0;
-        for (int i = 0; i < 32; ++i) s += double(Qs[i][a]) * double(Qs[i][c]);
-        acc[u] += s;
-      }
-    }
-    __syncthreads();
+  const int i0 = blockIdx.x * GRAM_ROWS;
+  for (int e = tid; e < GRAM_ROWS * b; e += blockDim.x) {
+    const int i = e / b, c = e % b;
+    Qs[i][c] = (i0 + i < m) ? Q[int64_t(i0 + i) * b + c] : 0.f;
   }
-#pragma unroll
-  for (int u = 0; u < 16; ++u) {
-    const int pr = tid + u * 256;
-    if (pr < b * b) part[int64_t(blockIdx.x) * b * b + pr] = acc[u];
-  }
-}
-
-__global__ void gram_finish_kernel(const double* __restrict__ part, int nblk, int bb, double* __restrict__ G) {
-  for (int pr = threadIdx.x; pr < bb; pr += blockDim.x) {
-    double s = 0.0;
-    for (int k = 0; k < nblk; ++k) s += part[int64_t(k) * bb + pr];
-    G[pr] = s;
+  __syncthreads();
+  for (int pr = tid; pr < b * b; pr += blockDim.x) {
+    const int a = pr / b, c = pr % b;
+    if (c < a) continue;
+    float s = 0.f;
+#pragma unroll 8
+    for (int i = 0; i < GRAM_ROWS; ++i) s = fmaf(Qs[i][a], Qs[i][c], s);
+    atomicAdd(G + a * b + c, double(s));
+    if (c != a) atomicAdd(G + c * b + a, double(s));
   }
 }
 
 // Rank-revealing Cholesky G = R^T R (R upper) and Rinv with the columns of
-// numerically dependent directions zeroed. One block.
+// numerically dependent directions zeroed. One block, FP64.
 __global__ void __launch_bounds__(256)
 chol_inv_kernel(const double* __restrict__ G, int b, double* __restrict__ Rinv) {
   __shared__ double R[BMAX][BMAX + 1];
+  __shared__ double X[BMAX][BMAX + 1];
   __shared__ int dead[BMAX];
-  __shared__ double djj;
+  __shared__ double red[8];
   const int tid = threadIdx.x;
-  for (int e = tid; e < BMAX * BMAX; e += blockDim.x) R[e / BMAX][e % BMAX] = 0.0;
+  for (int e = tid; e < BMAX * BMAX; e += blockDim.x) {
+    R[e / BMAX][e % BMAX] = 0.0;
+    X[e / BMAX][e % BMAX] = 0.0;
+  }
   __syncthreads();
   for (int j = 0; j < b; ++j) {
+    double part = 0.0;
+    for (int k = tid; k < j; k += blockDim.x) part += R[k][j] * R[k][j];
+    part = block_sum(part, red);
+    const double gjj = G[j * b + j];
+    const double d = gjj - part;
+    const bool dd = !(gjj > 1e-300) || !(d > 1e-10 * gjj);
+    const double djj = dd ? 1.0 : sqrt(d);
     if (tid == 0) {
-      const double gjj = G[j * b + j];
-      double d = gjj;
-      for (int k = 0; k < j; ++k) d -= R[k][j] * R[k][j];
-      const bool dd = !(gjj > 1e-300) || !(d > 1e-10 * gjj);
       dead[j] = dd;
-      djj = dd ? 1.0 : sqrt(d);
       R[j][j] = djj;
     }
-    __syncthreads();
     for (int i = j + 1 + tid; i < b; i += blockDim.x) {
-      if (dead[j]) {
+      if (dd) {
         R[j][i] = 0.0;
       } else {
         double s = G[j * b + i];
@@ -179,16 +164,19 @@ chol_inv_kernel(const double* __restrict__ G, int b, double* __restrict__ Rinv) 
     }
     __syncthreads();
   }
-  // back substitution, one column of Rinv per thread
-  for (int c = tid; c < b; c += blockDim.x) {
-    double x[BMAX];
-    for (int i = c + 1; i < b; ++i) x[i] = 0.0;
-    for (int i = c; i >= 0; --i) {
+  // R X = I, X upper: row i of X from rows below it, all columns in parallel
+  for (int i = b - 1; i >= 0; --i) {
+    for (int c = tid; c < b; c += blockDim.x) {
+      if (c < i) continue;
       double s = (i == c) ? 1.0 : 0.0;
-      for (int k = i + 1; k <= c; ++k) s -= R[i][k] * x[k];
-      x[i] = s / R[i][i];
+      for (int k = i + 1; k <= c; ++k) s -= R[i][k] * X[k][c];
+      X[i][c] = s / R[i][i];
     }
-    for (int i = 0; i < b; ++i) Rinv[i * b + c] = (dead[c] || i > c || dead[i]) ? 0.0 : x[i];
+    __syncthreads();
+  }
+  for (int e = tid; e < b * b; e += blockDim.x) {
+    const int i = e / b, c = e % b;
+    Rinv[e] = (dead[c] || i > c || dead[i]) ? 0.0 : X[i][c];
   }
 }
 
@@ -210,52 +198,53 @@ apply_small_kernel(const float* __restrict__ Qin, int m, int b, const double* __
   }
 }
 
-// Cyclic Jacobi (parallel round-robin order) for a symmetric b x b FP64
-// matrix; eigenvalues descending in lam, eigenvectors as columns of E.
+// Cyclic Jacobi (parallel round-robin order) for the symmetric b x b
+// Rayleigh-Ritz matrix: FP32 sweeps, then every eigenvalue is re-evaluated
+// as the FP64 Rayleigh quotient e^T H e of its FP32 eigenvector (second-order
+// accurate). Eigenvalues descending in lam, eigenvectors as columns of E.
 __global__ void __launch_bounds__(256)
 jacobi_eig_kernel(const double* __restrict__ H, int b, double* __restrict__ E, double* __restrict__ lam) {
-  extern __shared__ double jsm[];
-  const int bp = b + (b & 1);
-  const int ld = BMAX + 1;
-  double* A = jsm;
-  double* V = A + BMAX * ld;
-  double* cs = V + BMAX * ld;   // [BMAX/2][2]
-  int* pr = reinterpret_cast<int*>(cs + BMAX);  // [BMAX/2][2]
+  __shared__ float A[BMAX][BMAX + 1];
+  __shared__ float V[BMAX][BMAX + 1];
+  __shared__ float cs[BMAX];
+  __shared__ int pr[BMAX];
+  __shared__ double rq[BMAX];
   __shared__ double red[8];
   __shared__ int perm[BMAX];
+  const int bp = b + (b & 1);
   const int tid = threadIdx.x;
   for (int e = tid; e < bp * bp; e += blockDim.x) {
     const int i = e / bp, j = e % bp;
-    A[i * ld + j] = (i < b && j < b) ? H[i * b + j] : 0.0;
-    V[i * ld + j] = i == j ? 1.0 : 0.0;
+    A[i][j] = (i < b && j < b) ? float(H[i * b + j]) : 0.f;
+    V[i][j] = i == j ? 1.f : 0.f;
   }
   __syncthreads();
-  for (int sweep = 0; sweep < 40; ++sweep) {
+  for (int sweep = 0; sweep < 30; ++sweep) {
     double off = 0.0, tot = 0.0;
     for (int e = tid; e < bp * bp; e += blockDim.x) {
       const int i = e / bp, j = e % bp;
-      const double a = A[i * ld + j];
+      const double a = A[i][j];
       tot += a * a;
       if (i != j) off += a * a;
     }
     off = block_sum(off, red);
     tot = block_sum(tot, red);
-    if (!(off > 1e-30 * tot)) break;
+    if (!(off > 1e-14 * tot)) break;
     for (int round = 0; round < bp - 1; ++round) {
       if (tid < bp / 2) {
         auto at = [&](int pos) { return pos == 0 ? 0 : 1 + (pos - 1 + round) % (bp - 1); };
         int p = at(tid), q = at(bp - 1 - tid);
         if (p > q) { const int t = p; p = q; q = t; }
-        double c = 1.0, s = 0.0;
-        const double apq = A[p * ld + q];
-        if (apq != 0.0) {
-          const double tau = (A[q * ld + q] - A[p * ld + p]) / (2.0 * apq);
-          const double t = (tau >= 0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
-          c = 1.0 / sqrt(1.0 + t * t);
-          s = t * c;
+        float c = 1.f, sn = 0.f;
+        const float apq = A[p][q];
+        if (apq != 0.f) {
+          const float tau = (A[q][q] - A[p][p]) / (2.f * apq);
+          const float t = (tau >= 0.f ? 1.f : -1.f) / (fabsf(tau) + sqrtf(1.f + tau * tau));
+          c = rsqrtf(1.f + t * t);
+          sn = t * c;
         }
         cs[2 * tid] = c;
-        cs[2 * tid + 1] = s;
+        cs[2 * tid + 1] = sn;
         pr[2 * tid] = p;
         pr[2 * tid + 1] = q;
       }
@@ -263,32 +252,44 @@ jacobi_eig_kernel(const double* __restrict__ H, int b, double* __restrict__ E, d
       for (int e = tid; e < (bp / 2) * bp; e += blockDim.x) {  // rows: J^T A
         const int k = e / bp, j = e % bp;
         const int p = pr[2 * k], q = pr[2 * k + 1];
-        const double c = cs[2 * k], s = cs[2 * k + 1];
-        const double apj = A[p * ld + j], aqj = A[q * ld + j];
-        A[p * ld + j] = c * apj - s * aqj;
-        A[q * ld + j] = s * apj + c * aqj;
+        const float c = cs[2 * k], sn = cs[2 * k + 1];
+        const float apj = A[p][j], aqj = A[q][j];
+        A[p][j] = c * apj - sn * aqj;
+        A[q][j] = sn * apj + c * aqj;
       }
       __syncthreads();
       for (int e = tid; e < (bp / 2) * bp; e += blockDim.x) {  // columns: (.) J and V J
         const int k = e / bp, i = e % bp;
         const int p = pr[2 * k], q = pr[2 * k + 1];
-        const double c = cs[2 * k], s = cs[2 * k + 1];
-        const double aip = A[i * ld + p], aiq = A[i * ld + q];
-        A[i * ld + p] = c * aip - s * aiq;
-        A[i * ld + q] = s * aip + c * aiq;
-        const double vip = V[i * ld + p], viq = V[i * ld + q];
-        V[i * ld + p] = c * vip - s * viq;
-        V[i * ld + q] = s * vip + c * viq;
+        const float c = cs[2 * k], sn = cs[2 * k + 1];
+        const float aip = A[i][p], aiq = A[i][q];
+        A[i][p] = c * aip - sn * aiq;
+        A[i][q] = sn * aip + c * aiq;
+        const float vip = V[i][p], viq = V[i][q];
+        V[i][p] = c * vip - sn * viq;
+        V[i][q] = sn * vip + c * viq;
       }
       __syncthreads();
     }
   }
+  // FP64 Rayleigh quotients of the (normalised) eigenvectors
+  for (int c = tid; c < b; c += blockDim.x) {
+    double nn = 0.0, num = 0.0;
+    for (int i = 0; i < b; ++i) {
+      double hv = 0.0;
+      for (int k = 0; k < b; ++k) hv += H[i * b + k] * double(V[k][c]);
+      num += double(V[i][c]) * hv;
+      nn += double(V[i][c]) * double(V[i][c]);
+    }
+    rq[c] = nn > 0 ? num / nn : 0.0;
+  }
+  __syncthreads();
   if (tid == 0) {
     for (int i = 0; i < b; ++i) perm[i] = i;
     for (int i = 0; i < b; ++i) {
       int best = i;
       for (int j = i + 1; j < b; ++j)
-        if (A[perm[j] * ld + perm[j]] > A[perm[best] * ld + perm[best]]) best = j;
+        if (rq[perm[j]] > rq[perm[best]]) best = j;
       const int t = perm[i];
       perm[i] = perm[best];
       perm[best] = t;
@@ -297,9 +298,9 @@ jacobi_eig_kernel(const double* __restrict__ H, int b, double* __restrict__ E, d
   __syncthreads();
   for (int e = tid; e < b * b; e += blockDim.x) {
     const int i = e / b, c = e % b;
-    E[i * b + c] = V[i * ld + perm[c]];
+    E[i * b + c] = V[i][perm[c]];
   }
-  for (int c = tid; c < b; c += blockDim.x) lam[c] = A[perm[c] * ld + perm[c]];
+  for (int c = tid; c < b; c += blockDim.x) lam[c] = rq[perm[c]];
 }
 
 // s~ = sqrt(max(lam, 0)), 1/s~ (0 where s~ = 0), and k.
@@ -366,46 +367,63 @@ __global__ void cg_setup_kernel(CgSide S0, CgSide S1) {
   }
 }
 
-__device__ __forceinline__ void flush_acc(double* sacc, double* gacc, int n) {
+// Per-thread partial dot products -> per (kind, side, column) block sums ->
+// one FP64 atomic per block and column into gacc[kind][side][KMAX_LIMIT].
+// Thread gtid owns column gtid % k, so the block sum for column c adds the
+// threads tid = c - base (mod k), base = (blockIdx.x * blockDim.x) % k.
+__device__ __forceinline__ void block_flush(double* shm, const double (*acc)[2], int kind0,
+                                            int nkind, int k, double* gacc) {
+  const int tid = threadIdx.x, nt = blockDim.x;
+  for (int q = 0; q < nkind; ++q)
+    for (int sd = 0; sd < 2; ++sd) shm[(q * 2 + sd) * nt + tid] = acc[kind0 + q][sd];
   __syncthreads();
-  for (int e = threadIdx.x; e < n; e += blockDim.x) {
-    const double v = sacc[e];
-    if (v != 0.0) atomicAdd(gacc + e, v);
-    sacc[e] = 0.0;
+  const int base = int((int64_t(blockIdx.x) * nt) % k);
+  for (int e = tid; e < nkind * 2 * k; e += nt) {
+    const int q = e / (2 * k), sd = (e / k) & 1, c = e % k;
+    int t2 = (c - base) % k;
+    if (t2 < 0) t2 += k;
+    double sum = 0.0;
+    for (; t2 < nt; t2 += k) sum += shm[(q * 2 + sd) * nt + t2];
+    if (sum != 0.0) atomicAdd(gacc + ((kind0 + q) * 2 + sd) * KMAX_LIMIT + c, sum);
   }
   __syncthreads();
 }
 
 __global__ void __launch_bounds__(256)
 cg_kernel(CgArgs a) {
-  __shared__ double sacc[3][2][KMAX_LIMIT];
+  __shared__ double shm[3 * 2 * 256];
   __shared__ double rz[2][KMAX_LIMIT], beta[2][KMAX_LIMIT], alpha[2][KMAX_LIMIT], bn[2][KMAX_LIMIT];
   __shared__ double lastrr[2][KMAX_LIMIT];
   __shared__ int active[2][KMAX_LIMIT], iters[2][KMAX_LIMIT];
   __shared__ int any_active;
+  __shared__ int blk_changed;
   const int k = a.k;
   const int nacc = 2 * KMAX_LIMIT;
-  const int64_t n0 = int64_t(a.s[0].m) * k, ntot = n0 + int64_t(a.s[1].m) * k;
+  const int m0 = a.s[0].m;
+  const int64_t rows = int64_t(m0) + a.s[1].m;
   const int64_t gstride = int64_t(gridDim.x) * blockDim.x;
-  const int64_t g0 = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
-  for (int e = threadIdx.x; e < 3 * nacc; e += blockDim.x) (&sacc[0][0][0])[e] = 0.0;
-  __shared__ int blk_changed;
+  const int64_t gtid = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  // fixed column per thread, rows t0, t0 + tstride, ... over both sides
+  const int mycol = int(gtid % k);
+  const int64_t tstride = gstride / k;
+  const int64_t t0 = gtid / k;
+  const bool owns = gtid < tstride * k;
 
   // Reachability: L_aa is invertible exactly when every connected component
   // of the graph holds a sampled node. Rounds of frontier growth from the
   // sampled set until a round changes nothing (at most m + 1 rounds).
-  const int64_t nodes = int64_t(a.s[0].m) + a.s[1].m;
-  for (int64_t g = g0; g < nodes; g += gstride) {
-    const int sd = g < a.s[0].m ? 0 : 1;
-    a.s[sd].reach[sd ? g - a.s[0].m : g] = 0;
+  for (int64_t g = gtid; g < rows; g += gstride) {
+    const int sd = g < m0 ? 0 : 1;
+    a.s[sd].reach[sd ? g - m0 : g] = 0;
   }
+  if (!grid_sync(a.bar)) return;
   for (int round = 0; round <= max(a.s[0].m, a.s[1].m) + 1; ++round) {
     if (threadIdx.x == 0) blk_changed = 0;
     __syncthreads();
-    for (int64_t g = g0; g < nodes; g += gstride) {
-      const int sd = g < a.s[0].m ? 0 : 1;
+    for (int64_t g = gtid; g < rows; g += gstride) {
+      const int sd = g < m0 ? 0 : 1;
       const CgSide& S = a.s[sd];
-      const int t = int(sd ? g - a.s[0].m : g);
+      const int t = int(sd ? g - m0 : g);
       if (__ldcg(S.reach + t)) continue;
       const int node = S.abar[t];
       for (int64_t e = S.L.rowptr[node]; e < S.L.rowptr[node + 1]; ++e) {
@@ -425,34 +443,36 @@ cg_kernel(CgArgs a) {
     if (!grid_sync(a.bar)) return;
     if (__ldcg(a.changed + round % 3) == 0) break;
   }
-  for (int64_t g = g0; g < nodes; g += gstride) {
-    const int sd = g < a.s[0].m ? 0 : 1;
-    if (!__ldcg(a.s[sd].reach + (sd ? g - a.s[0].m : g))) atomicOr(a.status, 2);
+  for (int64_t g = gtid; g < rows; g += gstride) {
+    const int sd = g < m0 ? 0 : 1;
+    if (!__ldcg(a.s[sd].reach + (sd ? g - m0 : g))) atomicOr(a.status, 2);
   }
-  __syncthreads();
 
+  double acc[3][2];
   // r = b = -L_ab R, x = 0, z = M^-1 r, p_prev = 0
-  for (int64_t g = g0; g < ntot; g += gstride) {
-    const int sd = g < n0 ? 0 : 1;
-    const CgSide& S = a.s[sd];
-    const int64_t l = sd ? g - n0 : g;
-    const int t = int(l / k), c = int(l % k);
-    const int node = S.abar[t];
-    float bv = 0.f;
-    for (int64_t e = S.L.rowptr[node]; e < S.L.rowptr[node + 1]; ++e) {
-      const int ps = S.pos[S.L.col[e]];
-      if (ps < 0) bv = fmaf(-S.L.val[e], S.R[int64_t(-ps - 1) * S.ldr + c], bv);
+  acc[0][0] = acc[0][1] = acc[1][0] = acc[1][1] = acc[2][0] = acc[2][1] = 0.0;
+  if (owns)
+    for (int64_t tt = t0; tt < rows; tt += tstride) {
+      const int sd = tt < m0 ? 0 : 1;
+      const CgSide& S = a.s[sd];
+      const int t = int(sd ? tt - m0 : tt);
+      const int64_t l = int64_t(t) * k + mycol;
+      const int node = S.abar[t];
+      float bv = 0.f;
+      for (int64_t e = S.L.rowptr[node]; e < S.L.rowptr[node + 1]; ++e) {
+        const int ps = S.pos[S.L.col[e]];
+        if (ps < 0) bv = fmaf(-S.L.val[e], S.R[int64_t(-ps - 1) * S.ldr + mycol], bv);
+      }
+      const float zv = S.minv[t] * bv;
+      S.r[l] = bv;
+      S.z[l] = zv;
+      S.x[l] = 0.f;
+      S.p1[l] = 0.f;
+      acc[0][sd] += double(bv) * bv;
+      acc[1][sd] += double(bv) * zv;
+      acc[2][sd] += double(bv) * bv;
     }
-    const float zv = S.minv[t] * bv;
-    S.r[l] = bv;
-    S.z[l] = zv;
-    S.x[l] = 0.f;
-    S.p1[l] = 0.f;
-    atomicAdd(&sacc[0][sd][c], double(bv) * bv);
-    atomicAdd(&sacc[1][sd][c], double(bv) * zv);
-    atomicAdd(&sacc[2][sd][c], double(bv) * bv);
-  }
-  flush_acc(&sacc[0][0][0], a.acc_init, 3 * nacc);
+  block_flush(shm, acc, 0, 3, k, a.acc_init);
   if (!grid_sync(a.bar)) return;
   for (int e = threadIdx.x; e < 2 * k; e += blockDim.x) {
     const int sd = e / k, c = e % k;
@@ -479,31 +499,33 @@ cg_kernel(CgArgs a) {
     double* accp = a.acc + par * 3 * nacc;
     // Phase Q: p = z + beta p_prev (own rows and, on the fly, neighbours);
     // q = L_aa p; accumulate p.q
-    for (int64_t g = g0; g < ntot; g += gstride) {
-      const int sd = g < n0 ? 0 : 1;
-      const int64_t l = sd ? g - n0 : g;
-      const int t = int(l / k), c = int(l % k);
-      if (!active[sd][c]) continue;
-      const CgSide& S = a.s[sd];
-      float* pcur = par ? S.p1 : S.p0;
-      const float* pprev = par ? S.p0 : S.p1;
-      const float bt = float(beta[sd][c]);
-      const float pv = fmaf(bt, pprev[l], S.z[l]);
-      pcur[l] = pv;
-      const int node = S.abar[t];
-      float qv = 0.f;
-      for (int64_t e = S.L.rowptr[node]; e < S.L.rowptr[node + 1]; ++e) {
-        const int ps = S.pos[S.L.col[e]];
-        if (ps >= 0) {
-          const int64_t o = int64_t(ps) * k + c;
-          // neighbours were written by other blocks in this launch: bypass L1
-          qv = fmaf(S.L.val[e], fmaf(bt, __ldcg(pprev + o), __ldcg(S.z + o)), qv);
+    acc[0][0] = acc[0][1] = 0.0;
+    if (owns)
+      for (int64_t tt = t0; tt < rows; tt += tstride) {
+        const int sd = tt < m0 ? 0 : 1;
+        if (!active[sd][mycol]) continue;
+        const CgSide& S = a.s[sd];
+        const int t = int(sd ? tt - m0 : tt);
+        const int64_t l = int64_t(t) * k + mycol;
+        float* pcur = par ? S.p1 : S.p0;
+        const float* pprev = par ? S.p0 : S.p1;
+        const float bt = float(beta[sd][mycol]);
+        const float pv = fmaf(bt, pprev[l], S.z[l]);
+        pcur[l] = pv;
+        const int node = S.abar[t];
+        float qv = 0.f;
+        for (int64_t e = S.L.rowptr[node]; e < S.L.rowptr[node + 1]; ++e) {
+          const int ps = S.pos[S.L.col[e]];
+          if (ps >= 0) {
+            const int64_t o = int64_t(ps) * k + mycol;
+            // neighbours were written by other blocks in this launch: bypass L1
+            qv = fmaf(S.L.val[e], fmaf(bt, __ldcg(pprev + o), __ldcg(S.z + o)), qv);
+          }
         }
+        S.q[l] = qv;
+        acc[0][sd] += double(pv) * qv;
       }
-      S.q[l] = qv;
-      atomicAdd(&sacc[0][sd][c], double(pv) * qv);
-    }
-    flush_acc(&sacc[0][0][0], accp, nacc);
+    block_flush(shm, acc, 0, 1, k, accp);
     if (!grid_sync(a.bar)) return;
     for (int e = threadIdx.x; e < 2 * k; e += blockDim.x) {
       const int sd = e / k, c = e % k;
@@ -511,30 +533,32 @@ cg_kernel(CgArgs a) {
       const double pq = __ldcg(accp + sd * KMAX_LIMIT + c);
       if (!(pq > 0.0)) {
         alpha[sd][c] = 0.0;
-        if (blockIdx.x == 0) a.status[0] = 1;  // L_aa not positive definite
+        if (blockIdx.x == 0) atomicOr(a.status, 1);  // L_aa not positive definite
       } else {
         alpha[sd][c] = rz[sd][c] / pq;
       }
     }
     __syncthreads();
     // Phase U: x += alpha p; r -= alpha q; z = M^-1 r; accumulate r.z, r.r
-    for (int64_t g = g0; g < ntot; g += gstride) {
-      const int sd = g < n0 ? 0 : 1;
-      const int64_t l = sd ? g - n0 : g;
-      const int t = int(l / k), c = int(l % k);
-      if (!active[sd][c]) continue;
-      const CgSide& S = a.s[sd];
-      const float* pcur = par ? S.p1 : S.p0;
-      const float al = float(alpha[sd][c]);
-      S.x[l] = fmaf(al, pcur[l], S.x[l]);
-      const float rv = fmaf(-al, S.q[l], S.r[l]);
-      S.r[l] = rv;
-      const float zv = S.minv[t] * rv;
-      S.z[l] = zv;
-      atomicAdd(&sacc[1][sd][c], double(rv) * zv);
-      atomicAdd(&sacc[2][sd][c], double(rv) * rv);
-    }
-    flush_acc(&sacc[0][0][0], accp, 3 * nacc);
+    acc[1][0] = acc[1][1] = acc[2][0] = acc[2][1] = 0.0;
+    if (owns)
+      for (int64_t tt = t0; tt < rows; tt += tstride) {
+        const int sd = tt < m0 ? 0 : 1;
+        if (!active[sd][mycol]) continue;
+        const CgSide& S = a.s[sd];
+        const int t = int(sd ? tt - m0 : tt);
+        const int64_t l = int64_t(t) * k + mycol;
+        const float* pcur = par ? S.p1 : S.p0;
+        const float al = float(alpha[sd][mycol]);
+        S.x[l] = fmaf(al, pcur[l], S.x[l]);
+        const float rv = fmaf(-al, S.q[l], S.r[l]);
+        S.r[l] = rv;
+        const float zv = S.minv[t] * rv;
+        S.z[l] = zv;
+        acc[1][sd] += double(rv) * zv;
+        acc[2][sd] += double(rv) * rv;
+      }
+    block_flush(shm, acc, 1, 2, k, accp);
     if (blockIdx.x == 0) {
       double* other = a.acc + (1 - par) * 3 * nacc;
       for (int e = threadIdx.x; e < 3 * nacc; e += blockDim.x) other[e] = 0.0;
@@ -660,7 +684,7 @@ output_kernel(const float* __restrict__ U, int ldu, const float* __restrict__ V,
 
 struct DecodeWs {
   float *W, *Q, *Q2, *Ut, *Vt;
-  double *part, *G, *Rinv, *E, *lam, *s, *sinv;
+  double *G, *Rinv, *E, *lam, *s, *sinv;
   int* k;
   int32_t *pos0, *pos1, *abar0, *abar1;
   float *minv0, *minv1;
@@ -679,18 +703,17 @@ struct DecodeWs {
   size_t bytes;
 };
 
-static int decode_block(int rr, int rc, int kmax) { return std::min(std::min(rr, rc), kmax + 16); }
+static int decode_block(int rr, int rc, int kmax) { return std::min(std::min(rr, rc), kmax + 8); }
 
 static DecodeWs decode_layout(void* ws, int p, int n, int rr, int rc, int kmax) {
   Carve c(ws);
   DecodeWs w{};
   const int b = decode_block(rr, rc, kmax);
-  w.W = c.take<float>(size_t(rc) * b);
-  w.Q = c.take<float>(size_t(rr) * b);
-  w.Q2 = c.take<float>(size_t(rr) * b);
+  w.W = c.take<float>(size_t(std::max(rr, rc)) * b);
+  w.Q = c.take<float>(size_t(std::max(rr, rc)) * b);
+  w.Q2 = c.take<float>(size_t(std::max(rr, rc)) * b);
   w.Ut = c.take<float>(size_t(rr) * b);
   w.Vt = c.take<float>(size_t(rc) * b);
-  w.part = c.take<double>(size_t(GRAM_BLOCKS) * b * b);
   w.G = c.take<double>(size_t(b) * b);
   w.Rinv = c.take<double>(size_t(b) * b);
   w.E = c.take<double>(size_t(b) * b);
@@ -711,7 +734,7 @@ static DecodeWs decode_layout(void* ws, int p, int n, int rr, int rc, int kmax) 
   }
   w.acc = c.take<double>(2 * 3 * 2 * KMAX_LIMIT);
   w.acc_init = c.take<double>(3 * 2 * KMAX_LIMIT);
-  w.bar = c.take<unsigned int>(2);
+  w.bar = c.take<unsigned int>(kBarrierCounters + 1);
   w.err = c.take<int>(1);
   w.out_iters = c.take<int>(2 * KMAX_LIMIT);
   w.out_res = c.take<double>(2 * KMAX_LIMIT);
@@ -733,61 +756,74 @@ static DecodeWs decode_layout(void* ws, int p, int n, int rr, int rc, int kmax) 
 // Orthonormalise Q (m x b) in place: two rank-revealing Cholesky-QR passes.
 static cpca_status orthonormalize(float* Q, float* Q2, int m, int b, const DecodeWs& w, cudaStream_t st) {
   for (int pass = 0; pass < 2; ++pass) {
-    gram_partial_kernel<<<GRAM_BLOCKS, 256, 0, st>>>(Q, m, b, w.part);
+    CPCA_CUDA(cudaMemsetAsync(w.G, 0, sizeof(double) * b * b, st));
+    CPCA_PROF("svd_gram", st);
+    gram_kernel<<<ceil_div(m, GRAM_ROWS), 256, 0, st>>>(pass == 0 ? Q : Q2, m, b, w.G);
     CPCA_LAUNCHED();
-    gram_finish_kernel<<<1, 256, 0, st>>>(w.part, GRAM_BLOCKS, b * b, w.G);
-    CPCA_LAUNCHED();
+    CPCA_PROF("svd_chol", st);
     chol_inv_kernel<<<1, 256, 0, st>>>(w.G, b, w.Rinv);
     CPCA_LAUNCHED();
     apply_small_kernel<<<std::min<unsigned>(ceil_div(int64_t(m) * b, 256), num_sms() * 4), 256, 0, st>>>(
-        Q, m, b, w.Rinv, b, Q2, b, nullptr);
+        pass == 0 ? Q : Q2, m, b, w.Rinv, b, pass == 0 ? Q2 : Q, b, nullptr);
     CPCA_LAUNCHED();
-    CPCA_CUDA(cudaMemcpyAsync(Q, Q2, sizeof(float) * size_t(m) * b, cudaMemcpyDeviceToDevice, st));
   }
   return CPCA_OK;
 }
 
-// Partial SVD: U~ (rr x b) into w.Ut, V~ (rc x b) into w.Vt, s~ into w.s, k into w.k.
+// Partial SVD of X~ (rr x rc) by block subspace iteration on the shorter
+// side: S (short x b) <- orth((X~^T X~) S) or orth((X~ X~^T) S). Then
+// T = X~ S (or X~^T S), Rayleigh-Ritz on T^T T = E diag(s~^2) E^T, and
+// U~ = T E / s~, V~ = S E (or the mirror). Writes w.Ut (rr x b),
+// w.Vt (rc x b), w.s, w.sinv, w.k.
 static cpca_status partial_svd(const float* Xt, int rr, int rc, int64_t ldxt, int b, int iters,
                                uint64_t seed, double ratio, int k_override, const DecodeWs& w,
                                cudaStream_t st) {
-  const unsigned gw = std::min<unsigned>(ceil_div(int64_t(rc) * b, 256), num_sms() * 4);
-  omega_kernel<<<gw, 256, 0, st>>>(w.W, rc, b, seed);
+  const bool vspace = rc <= rr;  // iterate on the columns' side
+  const int ms = vspace ? rc : rr, ml = vspace ? rr : rc;
+  float* Sb = w.W;   // short side, ms x b
+  float* Sb2 = w.Q2; // scratch of at least ms x b
+  float* T = w.Q;    // long side, ml x b
+  auto to_long = [&](const float* in, float* out) -> cpca_status {
+    CPCA_PROF("svd_gemm", st);
+    if (vspace) gemm_nn_tall<<<ceil_div(rr, 8), 256, 0, st>>>(Xt, ldxt, rr, rc, in, b, out);
+    else gemm_tn_tall<<<ceil_div(rc, 8), 256, 0, st>>>(Xt, ldxt, rr, rc, in, b, out);
+    CPCA_LAUNCHED();
+    return CPCA_OK;
+  };
+  auto to_short = [&](const float* in, float* out) -> cpca_status {
+    CPCA_PROF("svd_gemm", st);
+    if (vspace) gemm_tn_tall<<<ceil_div(rc, 8), 256, 0, st>>>(Xt, ldxt, rr, rc, in, b, out);
+    else gemm_nn_tall<<<ceil_div(rr, 8), 256, 0, st>>>(Xt, ldxt, rr, rc, in, b, out);
+    CPCA_LAUNCHED();
+    return CPCA_OK;
+  };
+  const unsigned gs = std::min<unsigned>(ceil_div(int64_t(ms) * b, 256), num_sms() * 4);
+  omega_kernel<<<gs, 256, 0, st>>>(Sb, ms, b, seed);
   CPCA_LAUNCHED();
-  CPCA_PROF("svd_gemm", st);
-  gemm_nn_tall<<<ceil_div(rr, 8), 256, 0, st>>>(Xt, ldxt, rr, rc, w.W, b, w.Q);
-  CPCA_LAUNCHED();
+  CPCA_TRY(orthonormalize(Sb, Sb2, ms, b, w, st));
   for (int it = 0; it < iters; ++it) {
-    CPCA_TRY(orthonormalize(w.Q, w.Q2, rr, b, w, st));
-    CPCA_PROF("svd_gemm", st);
-    gemm_tn_tall<<<ceil_div(rc, 8), 256, 0, st>>>(Xt, ldxt, rr, rc, w.Q, b, w.W);
-    CPCA_LAUNCHED();
-    CPCA_PROF("svd_gemm", st);
-    gemm_nn_tall<<<ceil_div(rr, 8), 256, 0, st>>>(Xt, ldxt, rr, rc, w.W, b, w.Q);
-    CPCA_LAUNCHED();
+    CPCA_TRY(to_long(Sb, T));
+    CPCA_TRY(to_short(T, Sb));
+    CPCA_TRY(orthonormalize(Sb, Sb2, ms, b, w, st));
   }
-  CPCA_TRY(orthonormalize(w.Q, w.Q2, rr, b, w, st));
-  CPCA_PROF("svd_gemm", st);
-  gemm_tn_tall<<<ceil_div(rc, 8), 256, 0, st>>>(Xt, ldxt, rr, rc, w.Q, b, w.W);
+  CPCA_TRY(to_long(Sb, T));
+  CPCA_CUDA(cudaMemsetAsync(w.G, 0, sizeof(double) * b * b, st));
+  CPCA_PROF("svd_gram", st);
+  gram_kernel<<<ceil_div(ml, GRAM_ROWS), 256, 0, st>>>(T, ml, b, w.G);
   CPCA_LAUNCHED();
-  // H = W^T W = Q^T X~ X~^T Q (b x b), eigen-decomposition
-  gram_partial_kernel<<<GRAM_BLOCKS, 256, 0, st>>>(w.W, rc, b, w.part);
-  CPCA_LAUNCHED();
-  gram_finish_kernel<<<1, 256, 0, st>>>(w.part, GRAM_BLOCKS, b * b, w.G);
-  CPCA_LAUNCHED();
-  const size_t jsm = sizeof(double) * (2 * BMAX * (BMAX + 1) + BMAX) + sizeof(int) * BMAX;
-  CPCA_CUDA(cudaFuncSetAttribute(jacobi_eig_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(jsm)));
   CPCA_PROF("svd_jacobi", st);
-  jacobi_eig_kernel<<<1, 256, jsm, st>>>(w.G, b, w.E, w.lam);
+  jacobi_eig_kernel<<<1, 256, 0, st>>>(w.G, b, w.E, w.lam);
   CPCA_LAUNCHED();
   rank_kernel<<<1, 32, 0, st>>>(w.lam, b, ratio, k_override, w.s, w.sinv, w.k);
   CPCA_LAUNCHED();
-  // U~ = Q E, V~ = W E diag(1/s~)
-  const unsigned gu = std::min<unsigned>(ceil_div(int64_t(rr) * b, 256), num_sms() * 4);
-  apply_small_kernel<<<gu, 256, 0, st>>>(w.Q, rr, b, w.E, b, w.Ut, b, nullptr);
+  const unsigned gl = std::min<unsigned>(ceil_div(int64_t(ml) * b, 256), num_sms() * 4);
+  float* Ushort = vspace ? w.Vt : w.Ut;
+  float* Ulong = vspace ? w.Ut : w.Vt;
+  apply_small_kernel<<<gs, 256, 0, st>>>(Sb, ms, b, w.E, b, Ushort, b, nullptr);
   CPCA_LAUNCHED();
-  apply_small_kernel<<<gw, 256, 0, st>>>(w.W, rc, b, w.E, b, w.Vt, b, w.sinv);
+  apply_small_kernel<<<gl, 256, 0, st>>>(T, ml, b, w.E, b, Ulong, b, w.sinv);
   CPCA_LAUNCHED();
+  (void)ml;
   return CPCA_OK;
 }
 
@@ -869,7 +905,7 @@ extern "C" cpca_status cpca_decode(const float* Xt, int32_t rr, int32_t rc, int6
     }
     a.k = k;
     a.tol = prm->cg_tol;
-    a.bar = GridBar{w.bar, w.bar + 1, w.err};
+    a.bar = GridBar{w.bar, w.bar + kBarrierCounters, w.err};
     a.acc = w.acc;
     a.acc_init = w.acc_init;
     a.out_iters = w.out_iters;
@@ -881,7 +917,7 @@ extern "C" cpca_status cpca_decode(const float* Xt, int32_t rr, int32_t rc, int6
     CPCA_LAUNCHED();
     CPCA_CUDA(cudaMemsetAsync(w.acc, 0, sizeof(double) * 2 * 3 * 2 * KMAX_LIMIT, st));
     CPCA_CUDA(cudaMemsetAsync(w.acc_init, 0, sizeof(double) * 3 * 2 * KMAX_LIMIT, st));
-    CPCA_CUDA(cudaMemsetAsync(w.bar, 0, 2 * sizeof(unsigned int), st));
+    CPCA_CUDA(cudaMemsetAsync(w.bar, 0, (kBarrierCounters + 1) * sizeof(unsigned int), st));
     CPCA_CUDA(cudaMemsetAsync(w.err, 0, sizeof(int), st));
     CPCA_CUDA(cudaMemsetAsync(w.status, 0, sizeof(int), st));
     CPCA_CUDA(cudaMemsetAsync(w.changed, 0, 3 * sizeof(unsigned int), st));

@@ -17,165 +17,409 @@ namespace cpca {
 namespace {
 
 // ------------------------------------------------------------- step size --
-// Power iteration in FP64 on one Laplacian per block (block 0: Lr with
-// stream 2, block 1: Lc with stream 3), then the Rayleigh quotient.
-constexpr int PW_THREADS = 1024;
+// Power iteration on both Laplacians in one cooperative launch (warp per
+// row, rows of Lr then Lc), then the Rayleigh quotients and lambda.
+// With v_k = u_k / |u_k| the iteration v <- L v / |L v| is carried as
+// u_{k+1} = (L u_k) / |u_k|, so each step needs one grid barrier (for
+// |u_{k+1}|). Start vector u_0(i) = SplitMix64 uniform - 1/2 (stream 2 for
+// Lr, 3 for Lc). Iterates FP32, norms and quotients FP64.
+struct PowerArgs {
+  CsrView L[2];
+  int iters;
+  uint64_t seed;
+  float* u[2][2];      // [graph][ping/pong]
+  double* acc;         // ring [3][2]: |u|^2 per graph
+  double* fin;         // [2][2]: u^T L u, u^T u per graph
+  double gamma_r, gamma_c, step_given;
+  double* out;         // [norm_r, norm_c, lambda]
+  GridBar bar;
+};
 
-__device__ void spmv64(const CsrView& L, const double* __restrict__ v, double* __restrict__ w) {
-  for (int i = threadIdx.x; i < L.n; i += blockDim.x) {
-    double s = 0.0;
-    for (int64_t e = L.rowptr[i]; e < L.rowptr[i + 1]; ++e) s += double(L.val[e]) * v[L.col[e]];
-    w[i] = s;
-  }
-}
+__device__ __forceinline__ double warp_red_add(double v) { return warp_sum(v); }
 
-__global__ void __launch_bounds__(PW_THREADS)
-power_kernel(CsrView Lr, CsrView Lc, int iters, uint64_t seed, double* __restrict__ vbuf,
-             int vstride, double* __restrict__ out /* [norm_r, norm_c, lambda] */) {
-  __shared__ double red[32];
-  const CsrView L = blockIdx.x == 0 ? Lr : Lc;
-  double* v = vbuf + int64_t(blockIdx.x) * 2 * vstride;
-  double* w = v + vstride;
-  const uint64_t s0 = stream_state0(seed, 2 + blockIdx.x);
-  double ss = 0.0;
-  for (int i = threadIdx.x; i < L.n; i += blockDim.x) {
-    const double x = uniform01_at(s0, uint64_t(i) + 1) - 0.5;
-    v[i] = x;
-    ss += x * x;
-  }
-  ss = block_sum(ss, red);
-  double inv = ss > 0 ? 1.0 / sqrt(ss) : 0.0;
-  for (int i = threadIdx.x; i < L.n; i += blockDim.x) v[i] *= inv;
+__global__ void __launch_bounds__(256)
+power_persistent_kernel(PowerArgs a) {
+  __shared__ double sacc[2];
+  const int lane = threadIdx.x & 31;
+  const int nwarp = (gridDim.x * blockDim.x) >> 5;
+  const int wid = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int n0 = a.L[0].n, rows = n0 + a.L[1].n;
+  if (threadIdx.x < 2) sacc[threadIdx.x] = 0.0;
   __syncthreads();
-  bool zero = false;
-  for (int it = 0; it < iters && !zero; ++it) {
-    spmv64(L, v, w);
-    double s = 0.0;
-    for (int i = threadIdx.x; i < L.n; i += blockDim.x) s += w[i] * w[i];
-    s = block_sum(s, red);
-    if (s == 0.0) {
-      zero = true;
-      break;
-    }
-    const double iw = 1.0 / sqrt(s);
-    for (int i = threadIdx.x; i < L.n; i += blockDim.x) v[i] = w[i] * iw;
-    __syncthreads();
+  // u_0 and |u_0|^2 into ring slot 0
+  for (int r = wid * 32 + lane; r < rows; r += nwarp * 32) {
+    const int g = r < n0 ? 0 : 1, i = g ? r - n0 : r;
+    const double x = uniform01_at(stream_state0(a.seed, 2 + g), uint64_t(i) + 1) - 0.5;
+    a.u[g][0][i] = float(x);
+    atomicAdd(&sacc[g], x * x);
   }
-  double lam = 0.0;
-  if (!zero) {
-    spmv64(L, v, w);
+  __syncthreads();
+  if (threadIdx.x < 2 && sacc[threadIdx.x] != 0.0) atomicAdd(a.acc + threadIdx.x, sacc[threadIdx.x]);
+  if (!grid_sync(a.bar)) return;
+  double nrm2[2] = {__ldcg(a.acc), __ldcg(a.acc + 1)};
+  bool zero[2] = {!(nrm2[0] > 0), !(nrm2[1] > 0)};
+  for (int k = 0; k < a.iters; ++k) {
+    const int cur = k & 1, nxt = cur ^ 1;
+    if (threadIdx.x < 2) sacc[threadIdx.x] = 0.0;
+    if (blockIdx.x == 0 && threadIdx.x < 2) a.acc[2 * ((k + 2) % 3) + threadIdx.x] = 0.0;
     __syncthreads();
-    double num = 0.0, den = 0.0;
-    for (int i = threadIdx.x; i < L.n; i += blockDim.x) {
-      num += v[i] * w[i];
-      den += v[i] * v[i];
+    const float inv[2] = {zero[0] ? 0.f : float(1.0 / sqrt(nrm2[0])), zero[1] ? 0.f : float(1.0 / sqrt(nrm2[1]))};
+    for (int r = wid; r < rows; r += nwarp) {
+      const int g = r < n0 ? 0 : 1, i = g ? r - n0 : r;
+      const CsrView& L = a.L[g];
+      const float* u = a.u[g][cur];
+      float sum = 0.f;
+      for (int64_t e = L.rowptr[i] + lane; e < L.rowptr[i + 1]; e += 32)
+        sum = fmaf(__ldg(L.val + e), __ldcg(u + __ldg(L.col + e)), sum);
+      sum = warp_sumf(sum) * inv[g];
+      if (lane == 0) {
+        a.u[g][nxt][i] = sum;
+        atomicAdd(&sacc[g], double(sum) * double(sum));
+      }
     }
-    num = block_sum(num, red);
-    den = block_sum(den, red);
-    lam = den > 0 ? num / den : 0.0;
+    __syncthreads();
+    double* slot = a.acc + 2 * ((k + 1) % 3);
+    if (threadIdx.x < 2 && sacc[threadIdx.x] != 0.0) atomicAdd(slot + threadIdx.x, sacc[threadIdx.x]);
+    if (!grid_sync(a.bar)) return;
+    for (int g = 0; g < 2; ++g) {
+      if (zero[g]) continue;
+      nrm2[g] = __ldcg(slot + g);
+      if (!(nrm2[g] > 0)) zero[g] = true;
+    }
   }
-  if (threadIdx.x == 0) out[blockIdx.x] = lam;
+  // Rayleigh quotients u^T L u / u^T u of the final iterate
+  const int fin = a.iters & 1;
+  __shared__ double snum[2], sden[2];
+  if (threadIdx.x < 2) {
+    snum[threadIdx.x] = 0.0;
+    sden[threadIdx.x] = 0.0;
+  }
+  __syncthreads();
+  for (int r = wid; r < rows; r += nwarp) {
+    const int g = r < n0 ? 0 : 1, i = g ? r - n0 : r;
+    const CsrView& L = a.L[g];
+    const float* u = a.u[g][fin];
+    float sum = 0.f;
+    for (int64_t e = L.rowptr[i] + lane; e < L.rowptr[i + 1]; e += 32)
+      sum = fmaf(__ldg(L.val + e), __ldcg(u + __ldg(L.col + e)), sum);
+    sum = warp_sumf(sum);
+    if (lane == 0) {
+      const double ui = __ldcg(u + i);
+      atomicAdd(&snum[g], ui * double(sum));
+      atomicAdd(&sden[g], ui * ui);
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x < 2) {
+    atomicAdd(a.fin + 2 * threadIdx.x, snum[threadIdx.x]);
+    atomicAdd(a.fin + 2 * threadIdx.x + 1, sden[threadIdx.x]);
+  }
+  if (!grid_sync(a.bar)) return;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    double nr[2];
+    for (int g = 0; g < 2; ++g) {
+      const double num = __ldcg(a.fin + 2 * g), den = __ldcg(a.fin + 2 * g + 1);
+      nr[g] = (zero[g] || !(den > 0)) ? 0.0 : num / den;
+    }
+    a.out[0] = nr[0];
+    a.out[1] = nr[1];
+    if (a.step_given > 0) {
+      a.out[2] = a.step_given;
+    } else {
+      const double beta = 2.0 * a.gamma_c * nr[1] + 2.0 * a.gamma_r * nr[0];
+      a.out[2] = beta > 0 ? 1.0 / beta : 1.0;
+    }
+  }
 }
 
-__global__ void step_kernel(double gamma_r, double gamma_c, double step_given,
-                            double* __restrict__ out /* [norm_r, norm_c, lambda] */) {
+__global__ void step_kernel(double step_given, double* __restrict__ out) {
   if (threadIdx.x || blockIdx.x) return;
-  if (step_given > 0) {
-    out[2] = step_given;
-    return;
-  }
-  const double beta = 2.0 * gamma_c * out[1] + 2.0 * gamma_r * out[0];
-  out[2] = beta > 0 ? 1.0 / beta : 1.0;
+  out[0] = 0.0;
+  out[1] = 0.0;
+  out[2] = step_given;
 }
 
 // ------------------------------------------------------- FISTA iteration --
-template <int R>
-__global__ void __launch_bounds__(256)
-fista_iter_kernel(const float* __restrict__ Yt, int64_t ldy, int rr, int rc, CsrView Lr,
-                  CsrView Lc, const float* __restrict__ Zin, float* __restrict__ Zout,
-                  float* __restrict__ S, int64_t lds, const double* __restrict__ lam_ptr,
-                  float two_gr, float two_gc, float mu, int iter1, double eps,
-                  const double* __restrict__ prev_stats, double* __restrict__ out_stats,
-                  int* __restrict__ ctl) {
-  extern __shared__ float zs[];  // [R][rc]
-  __shared__ double red[8];
-  // Device-side stop test of Algorithm 1: iteration j runs only if
-  // iteration j-1 did not meet |Z_j - Z_{j-1}|^2 < eps |Z_{j-1}|^2.
-  if (ctl[0]) return;
-  if (prev_stats) {
-    const double dz = prev_stats[0], nz = prev_stats[1];
-    if (dz < eps * nz) {
-      if (threadIdx.x == 0 && blockIdx.x == 0) {
-        ctl[0] = 1;
-        ctl[1] = iter1 - 1;
+// Persistent form: all J iterations in one cooperative launch, one bounded
+// grid barrier per iteration. The matrix is cut into 32 x 32 tiles. Z_j is
+// kept twice, row-major (Z) and column-major (ZT = Z_j^T), so that both
+// graph products read contiguous 128-byte segments:
+//   (Lr Z)(i, j)  = sum_k Lr[i, k] Z(k, j)    -> segments of rows of Z,
+//   (Z Lc)(i, j)  = sum_k Lc[j, k] ZT(k, i)   -> segments of rows of ZT
+// (Lc is symmetric). A tile stages the 32 neighbour lists of its rows (Lr)
+// and of its columns (Lc) in shared memory, so each list is read once per
+// tile, not once per row. Warps batch NB neighbour loads for each of their
+// 4 rows (or columns) before consuming any. Z_j is read through L2
+// (ld.global.cg) because other blocks wrote it during the previous
+// iteration of this launch.
+constexpr int TB = 32;        // tile edge
+constexpr int kTileNbr = 40;  // neighbour-list entries staged per row / column
+
+struct FistaPersistArgs {
+  const float* Yt;
+  int64_t ldy;
+  int rr, rc;
+  CsrView Lr, Lc;
+  float* Z[2];    // row-major Z_j ping / pong (ld rc)
+  float* ZT[2];   // column-major copies (ld rr)
+  float* S;
+  int64_t lds;
+  const double* lam;
+  float two_gr, two_gc;
+  int J;
+  double eps;
+  double* stats;     // ring [4][2]: slot j % 4 holds iteration j's sums
+  int want_last;     // accumulate statistics of the last iteration
+  int* ctl;          // [stopped, iterations]
+  GridBar bar;
+};
+
+struct TileSmem {
+  int64_t roff[TB][kTileNbr];  // element offset of neighbour row k in Z  (k * rc)
+  float rval[TB][kTileNbr];
+  int64_t coff[TB][kTileNbr];  // element offset of neighbour row k in ZT (k * rr)
+  float cval[TB][kTileNbr];
+  float ac[TB][TB + 1];     // (Z Lc) of the tile, [row][col]
+  float zt[TB][TB + 1];     // Z_{j+1} tile for the transposed store, [row][col]
+  int rdeg[TB], cdeg[TB];
+  int64_t rf0[TB], cf0[TB];
+};
+
+// For four staged neighbour lists u = 0..3 (rows or columns of the tile):
+// out[u] = sum_q w[u][q] * x[off[u][q] + base]. Chunks of 8 entries of all
+// four lists are loaded together (32 independent loads per lane) up to the
+// shortest list, then each list's remainder, then entries beyond the
+// staging area straight from the CSR.
+__device__ __forceinline__ void nbr_sum4(const int64_t (*off)[kTileNbr], const float (*w)[kTileNbr],
+                                         const int* deg, const int64_t* f0, int first, bool valid,
+                                         const float* __restrict__ x, int64_t base, const CsrView& L,
+                                         int64_t stride, float out[4]) {
+  int dmin = kTileNbr;
+#pragma unroll
+  for (int u = 0; u < 4; ++u) dmin = min(dmin, min(deg[first + u], kTileNbr));
+  float acc[4] = {0.f, 0.f, 0.f, 0.f};
+  if (valid) {
+    int e = 0;
+    for (; e + 8 <= dmin; e += 8) {
+      float v[4][8];
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int q = 0; q < 8; ++q) v[u][q] = __ldcg(x + off[first + u][e + q] + base);
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int q = 0; q < 8; ++q) acc[u] = fmaf(w[first + u][e + q], v[u][q], acc[u]);
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int ds = min(deg[first + u], kTileNbr);
+      int e2 = e;
+      for (; e2 + 4 <= ds; e2 += 4) {
+        float v[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) v[q] = __ldcg(x + off[first + u][e2 + q] + base);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc[u] = fmaf(w[first + u][e2 + q], v[q], acc[u]);
       }
-      return;
+      for (; e2 < ds; ++e2) acc[u] = fmaf(w[first + u][e2], __ldcg(x + off[first + u][e2] + base), acc[u]);
+      for (int64_t f = f0[first + u] + kTileNbr; f < f0[first + u] + deg[first + u]; ++f)
+        acc[u] = fmaf(__ldg(L.val + f), __ldcg(x + int64_t(__ldg(L.col + f)) * stride + base), acc[u]);
     }
   }
-  const float lam = float(*lam_ptr);
-  const int row0 = blockIdx.x * R;
-  const int nrows = min(R, rr - row0);
-  for (int r = 0; r < nrows; ++r)
-    for (int j = threadIdx.x; j < rc; j += blockDim.x) zs[r * rc + j] = Zin[int64_t(row0 + r) * rc + j];
+#pragma unroll
+  for (int u = 0; u < 4; ++u) out[u] = acc[u];
+}
+
+// RESIDENT: every block owns at most one tile for the whole solve; its
+// neighbour lists are staged once, and Y~, S and the tile's own Z_j entries
+// stay in registers across iterations (S is written back at the end).
+// Otherwise blocks stream over tiles, staging lists per tile.
+__device__ __forceinline__ void stage_tile(TileSmem& sm, const FistaPersistArgs& a, int i0, int j0,
+                                           int ni, int nj) {
+  if (threadIdx.x < TB) {
+    const int r = threadIdx.x;
+    const int64_t f0 = r < ni ? a.Lr.rowptr[i0 + r] : 0;
+    sm.rf0[r] = f0;
+    sm.rdeg[r] = r < ni ? int(a.Lr.rowptr[i0 + r + 1] - f0) : 0;
+  } else if (threadIdx.x < 2 * TB) {
+    const int c = threadIdx.x - TB;
+    const int64_t g0 = c < nj ? a.Lc.rowptr[j0 + c] : 0;
+    sm.cf0[c] = g0;
+    sm.cdeg[c] = c < nj ? int(a.Lc.rowptr[j0 + c + 1] - g0) : 0;
+  }
   __syncthreads();
-  double dz = 0.0, nz = 0.0;
-  for (int j = threadIdx.x; j < rc; j += blockDim.x) {
-    float acc_c[R];
-#pragma unroll
-    for (int r = 0; r < R; ++r) acc_c[r] = 0.f;
-    const int64_t e0 = Lc.rowptr[j], e1 = Lc.rowptr[j + 1];
-    for (int64_t e = e0; e < e1; ++e) {
-      const int c = __ldg(Lc.col + e);
-      const float w = __ldg(Lc.val + e);
-#pragma unroll
-      for (int r = 0; r < R; ++r) acc_c[r] = fmaf(w, zs[r * rc + c], acc_c[r]);
+  for (int e = threadIdx.x; e < TB * kTileNbr; e += blockDim.x) {
+    const int r = e / kTileNbr, q = e % kTileNbr;
+    if (q < min(sm.rdeg[r], kTileNbr)) {
+      sm.roff[r][q] = int64_t(__ldg(a.Lr.col + sm.rf0[r] + q)) * a.rc;
+      sm.rval[r][q] = __ldg(a.Lr.val + sm.rf0[r] + q);
     }
-#pragma unroll
-    for (int r = 0; r < R; ++r) {
-      if (r >= nrows) break;
-      const int i = row0 + r;
-      float acc_r = 0.f;
-      const int64_t f0 = Lr.rowptr[i], f1 = Lr.rowptr[i + 1];
-      for (int64_t f = f0; f < f1; ++f)
-        acc_r = fmaf(__ldg(Lr.val + f), __ldg(Zin + int64_t(__ldg(Lr.col + f)) * rc + j), acc_r);
-      const float z = zs[r * rc + j];
-      const float g = fmaf(two_gr, acc_r, two_gc * acc_c[r]);
-      const float v = fmaf(-lam, g, z);
-      const float y = __ldg(Yt + int64_t(i) * ldy + j);
-      const float dl = v - y;
-      const float s = y + copysignf(fmaxf(fabsf(dl) - lam, 0.f), dl);
-      const int64_t si = int64_t(i) * lds + j;
-      const float sp = S[si];
-      S[si] = s;
-      const float zn = fmaf(mu, s - sp, s);
-      Zout[int64_t(i) * rc + j] = zn;
-      if (out_stats) {
-        const double d = double(zn) - double(z);
-        dz += d * d;
-        nz += double(z) * double(z);
-      }
+    if (q < min(sm.cdeg[r], kTileNbr)) {
+      sm.coff[r][q] = int64_t(__ldg(a.Lc.col + sm.cf0[r] + q)) * a.rr;
+      sm.cval[r][q] = __ldg(a.Lc.val + sm.cf0[r] + q);
     }
   }
-  if (out_stats) {
-    dz = block_sum(dz, red);
-    nz = block_sum(nz, red);
-    if (threadIdx.x == 0) {
-      atomicAdd(out_stats, dz);
-      atomicAdd(out_stats + 1, nz);
+  __syncthreads();
+}
+
+template <bool RESIDENT>
+__global__ void __launch_bounds__(256, RESIDENT ? 5 : 4)
+fista_persistent_kernel(FistaPersistArgs a) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  TileSmem& sm = *reinterpret_cast<TileSmem*>(smraw);
+  __shared__ double red[8];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const float lam = float(*a.lam);
+  const int nti = (a.rr + TB - 1) / TB, ntj = (a.rc + TB - 1) / TB;
+  const int ntiles = nti * ntj;
+  // resident state (one tile per block)
+  float ry[4], rs[4], rz[4];
+  int ri0 = 0, rj0 = 0, rni = 0, rnj = 0;
+  if (RESIDENT && blockIdx.x < ntiles) {
+    ri0 = (blockIdx.x / ntj) * TB;
+    rj0 = (blockIdx.x % ntj) * TB;
+    rni = min(TB, a.rr - ri0);
+    rnj = min(TB, a.rc - rj0);
+    stage_tile(sm, a, ri0, rj0, rni, rnj);
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int r = warp * 4 + u;
+      const bool in = r < rni && lane < rnj;
+      const int64_t i = ri0 + r, jj = rj0 + lane;
+      ry[u] = in ? a.Yt[i * a.ldy + jj] : 0.f;
+      rs[u] = ry[u];  // S_0 = Y~
+      rz[u] = ry[u];  // Z_1 = Y~
     }
+  }
+  int done = a.J;
+  double t = 1.0;  // t_j of Algorithm 1 (t_1 = 1)
+  for (int j = 1; j <= a.J; ++j) {
+    if (a.eps > 0 && j > 1) {
+      const double* ps = a.stats + 2 * ((j - 1) & 3);
+      if (__ldcg(ps) < a.eps * __ldcg(ps + 1)) {
+        done = j - 1;
+        break;
+      }
+    }
+    const double tn = (1.0 + sqrt(1.0 + 4.0 * t * t)) / 2.0;
+    const float mu = float((t - 1.0) / tn);
+    t = tn;
+    const float* Zin = a.Z[(j - 1) & 1];
+    const float* ZTin = a.ZT[(j - 1) & 1];
+    float* Zout = a.Z[j & 1];
+    float* ZTout = a.ZT[j & 1];
+    const bool stats = a.eps > 0 || (a.want_last && j == a.J);
+    double* st = a.stats + 2 * (j & 3);
+    // slot (j + 1) % 4 was last read at the start of iteration j - 2
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+      a.stats[2 * ((j + 1) & 3)] = 0.0;
+      a.stats[2 * ((j + 1) & 3) + 1] = 0.0;
+    }
+    double dz = 0.0, nz = 0.0;
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+      int i0, j0, ni, nj;
+      if (RESIDENT) {
+        i0 = ri0; j0 = rj0; ni = rni; nj = rnj;
+      } else {
+        i0 = (tile / ntj) * TB;
+        j0 = (tile % ntj) * TB;
+        ni = min(TB, a.rr - i0);
+        nj = min(TB, a.rc - j0);
+        stage_tile(sm, a, i0, j0, ni, nj);
+      }
+      // (Z Lc): warp w takes tile columns 4w..4w+3, lane = tile row
+      {
+        float o[4];
+        nbr_sum4(sm.coff, sm.cval, sm.cdeg, sm.cf0, warp * 4, lane < ni, ZTin, i0 + lane, a.Lc,
+                 a.rr, o);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) sm.ac[lane][warp * 4 + u] = o[u];
+      }
+      // (Lr Z): warp w takes tile rows 4w..4w+3, lane = tile column
+      float ar[4];
+      nbr_sum4(sm.roff, sm.rval, sm.rdeg, sm.rf0, warp * 4, lane < nj, Zin, j0 + lane, a.Lr, a.rc, ar);
+      __syncthreads();  // sm.ac complete
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int r = warp * 4 + u;
+        if (r < ni && lane < nj) {
+          const int64_t i = i0 + r, jj = j0 + lane;
+          const float z = RESIDENT ? rz[u] : __ldcg(Zin + i * a.rc + jj);
+          const float y = RESIDENT ? ry[u] : __ldg(a.Yt + i * a.ldy + jj);
+          const float sp = RESIDENT ? rs[u] : a.S[i * a.lds + jj];
+          const float gr = fmaf(a.two_gr, ar[u], a.two_gc * sm.ac[r][lane]);
+          const float v = fmaf(-lam, gr, z);
+          const float dl = v - y;
+          const float sv = y + copysignf(fmaxf(fabsf(dl) - lam, 0.f), dl);
+          const float zn = fmaf(mu, sv - sp, sv);
+          if (RESIDENT) {
+            rs[u] = sv;
+            rz[u] = zn;
+          } else {
+            a.S[i * a.lds + jj] = sv;
+          }
+          Zout[i * a.rc + jj] = zn;
+          sm.zt[r][lane] = zn;
+          if (stats) {
+            const double d = double(zn) - double(z);
+            dz += d * d;
+            nz += double(z) * double(z);
+          }
+        }
+      }
+      __syncthreads();  // sm.zt complete
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int c = warp * 4 + u;
+        if (c < nj && lane < ni) ZTout[int64_t(j0 + c) * a.rr + i0 + lane] = sm.zt[lane][c];
+      }
+      if (!RESIDENT) __syncthreads();  // before the next tile reuses shared memory
+    }
+    if (stats) {
+      dz = block_sum(dz, red);
+      nz = block_sum(nz, red);
+      if (threadIdx.x == 0) {
+        atomicAdd(st, dz);
+        atomicAdd(st + 1, nz);
+      }
+    }
+    if (!grid_sync(a.bar)) return;
+  }
+  if (RESIDENT && blockIdx.x < ntiles) {
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int r = warp * 4 + u;
+      if (r < rni && lane < rnj) a.S[int64_t(ri0 + r) * a.lds + rj0 + lane] = rs[u];
+    }
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    a.ctl[0] = done < a.J ? 1 : 0;
+    a.ctl[1] = done;
   }
 }
 
+// Z_1 = S_0 = Y~ (Algorithm 1), plus the transposed copy of Z_1.
 __global__ void init_kernel(const float* __restrict__ Yt, int64_t ldy, int rr, int rc,
-                            float* __restrict__ Z, float* __restrict__ S, int64_t lds) {
-  const int64_t total = int64_t(rr) * rc;
-  for (int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; t < total;
-       t += int64_t(gridDim.x) * blockDim.x) {
-    const int i = int(t / rc), j = int(t % rc);
-    const float y = Yt[int64_t(i) * ldy + j];
-    Z[t] = y;
-    S[int64_t(i) * lds + j] = y;
+                            float* __restrict__ Z, float* __restrict__ ZT, float* __restrict__ S,
+                            int64_t lds) {
+  __shared__ float tile[32][33];
+  const int i0 = blockIdx.y * 32, j0 = blockIdx.x * 32;
+  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+    const int i = i0 + r, j = j0 + threadIdx.x;
+    if (i < rr && j < rc) {
+      const float y = Yt[int64_t(i) * ldy + j];
+      Z[int64_t(i) * rc + j] = y;
+      S[int64_t(i) * lds + j] = y;
+      tile[r][threadIdx.x] = y;
+    }
   }
+  __syncthreads();
+  if (ZT)
+    for (int c = threadIdx.y; c < 32; c += blockDim.y) {
+      const int j = j0 + c, i = i0 + threadIdx.x;
+      if (i < rr && j < rc) ZT[int64_t(j) * rr + i] = tile[threadIdx.x][c];
+    }
 }
 
 // ------------------------------------------------------------- objective --
@@ -207,90 +451,131 @@ __global__ void sum_in_order_kernel(const double* __restrict__ part, int n, doub
   *out = s;
 }
 
-constexpr int OBJ_BLOCKS = 512;
 
 }  // namespace
 
-FistaWs fista_layout(void* ws, int rr, int rc, int max_iter_stats) {
+FistaWs fista_layout(void* ws, int rr, int rc, int /*unused*/) {
   Carve c(ws);
   FistaWs w{};
   w.Z0 = c.take<float>(size_t(rr) * rc);
   w.Z1 = c.take<float>(size_t(rr) * rc);
+  w.ZT0 = c.take<float>(size_t(rr) * rc);
+  w.ZT1 = c.take<float>(size_t(rr) * rc);
   w.scal = c.take<double>(4);
-  w.vbuf = c.take<double>(size_t(4) * std::max(rr, rc));
-  w.stats = c.take<double>(size_t(2) * std::max(max_iter_stats, 1));
+  for (int g = 0; g < 2; ++g)
+    for (int b = 0; b < 2; ++b) w.pu[g][b] = c.take<float>(size_t(g ? rc : rr) + 4);
+  w.pacc = c.take<double>(6 + 4);
+  w.stats = c.take<double>(8);
   w.ctl = c.take<int>(4);
-  w.part = c.take<double>(OBJ_BLOCKS);
+  w.bar = c.take<unsigned int>(kBarrierCounters + 1);
+  w.err = c.take<int>(1);
+  w.part = c.take<double>(kObjBlocks);
   w.obj = c.take<double>(1);
   w.bytes = c.bytes();
   return w;
 }
 
+static int coop_blocks(const void* kernel, int threads, size_t smem, int want) {
+  int occ = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, threads, smem) != cudaSuccess) {
+    cudaGetLastError();
+    occ = 1;
+  }
+  return std::max(1, std::min(want, std::max(occ, 1) * num_sms()));
+}
+
 cpca_status power_step(const CsrView& Lr, const CsrView& Lc, int iters, uint64_t seed,
                        double gamma_r, double gamma_c, double step_given, const FistaWs& w,
                        cudaStream_t st) {
-  if (step_given <= 0) {
-    CPCA_PROF("power_iter", st);
-    power_kernel<<<2, PW_THREADS, 0, st>>>(Lr, Lc, iters, seed, w.vbuf, std::max(Lr.n, Lc.n),
-                                            w.scal);
+  if (step_given > 0) {
+    step_kernel<<<1, 32, 0, st>>>(step_given, w.scal);
     CPCA_LAUNCHED();
-  } else {
-    CPCA_CUDA(cudaMemsetAsync(w.scal, 0, 2 * sizeof(double), st));
+    return CPCA_OK;
   }
-  step_kernel<<<1, 32, 0, st>>>(gamma_r, gamma_c, step_given, w.scal);
+  PowerArgs a{};
+  a.L[0] = Lr;
+  a.L[1] = Lc;
+  a.iters = iters;
+  a.seed = seed;
+  for (int g = 0; g < 2; ++g)
+    for (int b = 0; b < 2; ++b) a.u[g][b] = w.pu[g][b];
+  a.acc = w.pacc;
+  a.fin = w.pacc + 6;
+  a.gamma_r = gamma_r;
+  a.gamma_c = gamma_c;
+  a.step_given = step_given;
+  a.out = w.scal;
+  a.bar = GridBar{w.bar, w.bar + kBarrierCounters, w.err};
+  CPCA_CUDA(cudaMemsetAsync(w.pacc, 0, sizeof(double) * 10, st));
+  CPCA_CUDA(cudaMemsetAsync(w.bar, 0, sizeof(unsigned int) * (kBarrierCounters + 1), st));
+  CPCA_CUDA(cudaMemsetAsync(w.err, 0, sizeof(int), st));
+  const int rows = Lr.n + Lc.n;
+  const int grid = coop_blocks((const void*)power_persistent_kernel, 256, 0, (rows + 7) / 8);
+  void* args[] = {&a};
+  CPCA_PROF("power_iter", st);
+  CPCA_CUDA(cudaLaunchCooperativeKernel((const void*)power_persistent_kernel, dim3(grid), dim3(256),
+                                        args, 0, st));
   CPCA_LAUNCHED();
   return CPCA_OK;
 }
 
-int fista_rows_per_block(int rc) {
-  const int64_t budget = 96 * 1024;
-  const int64_t per_row = int64_t(rc) * 4;
-  if (per_row * 8 <= budget) return 8;
-  if (per_row * 4 <= budget) return 4;
-  if (per_row * 2 <= budget) return 2;
-  return 1;
-}
+static bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; }
 
-template <int R>
-static cpca_status launch_iter(const float* Yt, int64_t ldy, int rr, int rc, const CsrView& Lr,
-                               const CsrView& Lc, const float* Zin, float* Zout, float* S,
-                               int64_t lds, const double* lam, float two_gr, float two_gc,
-                               float mu, int iter1, double eps, const double* prev_stats,
-                               double* out_stats, int* ctl, cudaStream_t st) {
-  const size_t smem = size_t(R) * rc * sizeof(float);
-  static bool attr_set = false;
-  if (!attr_set) {
-    CPCA_CUDA(cudaFuncSetAttribute(fista_iter_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   200 * 1024));
-    attr_set = true;
-  }
-  const int threads = rc >= 256 ? 256 : ((rc + 31) / 32) * 32;
-  CPCA_PROF("fista_iter", st);
-  fista_iter_kernel<R><<<ceil_div(rr, R), threads, smem, st>>>(
-      Yt, ldy, rr, rc, Lr, Lc, Zin, Zout, S, lds, lam, two_gr, two_gc, mu, iter1, eps, prev_stats,
-      out_stats, ctl);
+// All J iterations of Algorithm 1 in one cooperative launch.
+cpca_status fista_run(const float* Yt, int64_t ldy, int rr, int rc, const CsrView& Lr,
+                      const CsrView& Lc, float* X, int64_t ldx, double gamma_r, double gamma_c,
+                      int J, double eps, bool want_last, int tile_rows, const FistaWs& w,
+                      cudaStream_t st) {
+  (void)tile_rows;
+  CPCA_TRY(fista_init(Yt, ldy, rr, rc, w.Z0, w.ZT0, X, ldx, st));
+  CPCA_CUDA(cudaMemsetAsync(w.stats, 0, 8 * sizeof(double), st));
+  CPCA_CUDA(cudaMemsetAsync(w.ctl, 0, 4 * sizeof(int), st));
+  CPCA_CUDA(cudaMemsetAsync(w.bar, 0, sizeof(unsigned int) * (kBarrierCounters + 1), st));
+  CPCA_CUDA(cudaMemsetAsync(w.err, 0, sizeof(int), st));
+  if (J == 0) return CPCA_OK;
+  FistaPersistArgs a{};
+  a.Yt = Yt;
+  a.ldy = ldy;
+  a.rr = rr;
+  a.rc = rc;
+  a.Lr = Lr;
+  a.Lc = Lc;
+  a.Z[0] = w.Z0;
+  a.Z[1] = w.Z1;
+  a.ZT[0] = w.ZT0;
+  a.ZT[1] = w.ZT1;
+  a.S = X;
+  a.lds = ldx;
+  a.lam = w.scal + 2;
+  a.two_gr = float(2.0 * gamma_r);
+  a.two_gc = float(2.0 * gamma_c);
+  a.J = J;
+  a.eps = eps;
+  a.stats = w.stats;
+  a.want_last = want_last ? 1 : 0;
+  a.ctl = w.ctl;
+  a.bar = GridBar{w.bar, w.bar + kBarrierCounters, w.err};
+  const size_t smem = sizeof(TileSmem);
+  const int tiles = int(ceil_div(rr, TB) * int64_t(ceil_div(rc, TB)));
+  const void* kres = (const void*)fista_persistent_kernel<true>;
+  const void* kstr = (const void*)fista_persistent_kernel<false>;
+  CPCA_CUDA(cudaFuncSetAttribute(kres, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
+  CPCA_CUDA(cudaFuncSetAttribute(kstr, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
+  const int cap_res = coop_blocks(kres, 256, smem, 1 << 30);
+  const bool resident = tiles <= cap_res;
+  const void* kern = resident ? kres : kstr;
+  const int grid = resident ? tiles : coop_blocks(kstr, 256, smem, tiles);
+  void* args[] = {&a};
+  CPCA_PROF("fista_persistent", st);
+  CPCA_CUDA(cudaLaunchCooperativeKernel(kern, dim3(grid), dim3(256), args, smem, st));
   CPCA_LAUNCHED();
   return CPCA_OK;
 }
 
-cpca_status fista_iteration(int R, const float* Yt, int64_t ldy, int rr, int rc, const CsrView& Lr,
-                            const CsrView& Lc, const float* Zin, float* Zout, float* S,
-                            int64_t lds, const double* lam, double gamma_r, double gamma_c,
-                            double mu, int iter1, double eps, const double* prev_stats,
-                            double* out_stats, int* ctl, cudaStream_t st) {
-  const float tr = float(2.0 * gamma_r), tc = float(2.0 * gamma_c), m = float(mu);
-  switch (R) {
-    case 8: return launch_iter<8>(Yt, ldy, rr, rc, Lr, Lc, Zin, Zout, S, lds, lam, tr, tc, m, iter1, eps, prev_stats, out_stats, ctl, st);
-    case 4: return launch_iter<4>(Yt, ldy, rr, rc, Lr, Lc, Zin, Zout, S, lds, lam, tr, tc, m, iter1, eps, prev_stats, out_stats, ctl, st);
-    case 2: return launch_iter<2>(Yt, ldy, rr, rc, Lr, Lc, Zin, Zout, S, lds, lam, tr, tc, m, iter1, eps, prev_stats, out_stats, ctl, st);
-    default: return launch_iter<1>(Yt, ldy, rr, rc, Lr, Lc, Zin, Zout, S, lds, lam, tr, tc, m, iter1, eps, prev_stats, out_stats, ctl, st);
-  }
-}
-
-cpca_status fista_init(const float* Yt, int64_t ldy, int rr, int rc, float* Z, float* S,
+cpca_status fista_init(const float* Yt, int64_t ldy, int rr, int rc, float* Z, float* ZT, float* S,
                        int64_t lds, cudaStream_t st) {
-  const unsigned blocks = std::min<unsigned>(ceil_div(int64_t(rr) * rc, 256), num_sms() * 8);
-  init_kernel<<<blocks, 256, 0, st>>>(Yt, ldy, rr, rc, Z, S, lds);
+  dim3 grid(ceil_div(rc, 32), ceil_div(rr, 32)), block(32, 8);
+  init_kernel<<<grid, block, 0, st>>>(Yt, ldy, rr, rc, Z, ZT, S, lds);
   CPCA_LAUNCHED();
   return CPCA_OK;
 }
@@ -299,9 +584,9 @@ cpca_status fista_objective(const float* Yt, int64_t ldy, int rr, int rc, const 
                             const CsrView& Lc, const float* X, int64_t ldx, double gr, double gc,
                             const FistaWs& w, cudaStream_t st) {
   CPCA_PROF("fista_objective", st);
-  objective_kernel<<<OBJ_BLOCKS, 256, 0, st>>>(Yt, ldy, rr, rc, Lr, Lc, X, ldx, gr, gc, w.part);
+  objective_kernel<<<kObjBlocks, 256, 0, st>>>(Yt, ldy, rr, rc, Lr, Lc, X, ldx, gr, gc, w.part);
   CPCA_LAUNCHED();
-  sum_in_order_kernel<<<1, 32, 0, st>>>(w.part, OBJ_BLOCKS, w.obj);
+  sum_in_order_kernel<<<1, 32, 0, st>>>(w.part, kObjBlocks, w.obj);
   CPCA_LAUNCHED();
   return CPCA_OK;
 }
@@ -349,9 +634,10 @@ extern "C" cpca_status cpca_frpcag_solve(const float* Yt, int32_t rr, int32_t rc
   CPCA_CHECK_ARG(prm->max_iter >= 0, "cpca_frpcag_solve: max_iter < 0");
   CPCA_CHECK_ARG(prm->gamma_r >= 0 && prm->gamma_c >= 0, "cpca_frpcag_solve: negative gamma");
   CPCA_CHECK_ARG(prm->eps >= 0, "cpca_frpcag_solve: eps < 0");
+  CPCA_CHECK_ARG(prm->tile_rows == 0 || prm->tile_rows == 1 || prm->tile_rows == 2 ||
+                     prm->tile_rows == 4 || prm->tile_rows == 8,
+                 "cpca_frpcag_solve: tile_rows must be 0, 1, 2, 4 or 8");
   CPCA_CHECK_ARG(prm->step > 0 || prm->power_iters >= 1, "cpca_frpcag_solve: power_iters < 1");
-  CPCA_CHECK_ARG(prm->eps == 0 || prm->check_every >= 1, "cpca_frpcag_solve: check_every < 1");
-  CPCA_CHECK_ARG(int64_t(rc) * 4 <= 200 * 1024, "cpca_frpcag_solve: rc too large for one row in shared memory");
   CPCA_TRY(check_csr(Lr, rr, "cpca_frpcag_solve(Lr)"));
   CPCA_TRY(check_csr(Lc, rc, "cpca_frpcag_solve(Lc)"));
   const FistaWs w = fista_layout(ws, rr, rc, kMaxStatIters);
@@ -365,52 +651,31 @@ extern "C" cpca_status cpca_frpcag_solve(const float* Yt, int32_t rr, int32_t rc
   const int J = prm->max_iter;
   CPCA_TRY(power_step(lr, lc, prm->power_iters, prm->power_seed, prm->gamma_r, prm->gamma_c,
                       prm->step, w, st));
-  CPCA_TRY(fista_init(Yt, ldyt, rr, rc, w.Z0, X, ldx, st));
-  CPCA_CUDA(cudaMemsetAsync(w.ctl, 0, 4 * sizeof(int), st));
-  const bool want = prm->eps > 0 || info != nullptr;
-  const int nstat = std::min(J, kMaxStatIters);
-  if (want && nstat > 0) CPCA_CUDA(cudaMemsetAsync(w.stats, 0, 2 * sizeof(double) * nstat, st));
-  CPCA_CHECK_ARG(prm->eps == 0 || J <= kMaxStatIters, "cpca_frpcag_solve: eps > 0 needs max_iter <= %d",
-                 kMaxStatIters);
-  std::vector<double> mu(std::max(J, 1));
-  fista_momentum(J, mu.data());
-  const int R = fista_rows_per_block(rc);
+  CPCA_TRY(fista_run(Yt, ldyt, rr, rc, lr, lc, X, ldx, prm->gamma_r, prm->gamma_c, J, prm->eps,
+                     info != nullptr, prm->tile_rows, w, st));
   int done_iters = J;
-  for (int j = 1; j <= J; ++j) {
-    const float* Zin = (j & 1) ? w.Z0 : w.Z1;
-    float* Zout = (j & 1) ? w.Z1 : w.Z0;
-    // statistics: slot j-1 for every iteration when eps > 0 (iteration j
-    // tests slot j-2), else slot 0 for the last iteration only
-    const double* prev = (prm->eps > 0 && j > 1) ? w.stats + 2 * (j - 2) : nullptr;
-    double* out = prm->eps > 0 ? w.stats + 2 * (j - 1) : ((info && j == J) ? w.stats : nullptr);
-    CPCA_TRY(fista_iteration(R, Yt, ldyt, rr, rc, lr, lc, Zin, Zout, X, ldx, w.scal + 2,
-                             prm->gamma_r, prm->gamma_c, mu[j - 1], j, prm->eps, prev, out, w.ctl,
-                             st));
-    if (prm->eps > 0 && (j % prm->check_every == 0) && j < J) {
-      int ctl[2];
-      CPCA_CUDA(cudaMemcpyAsync(ctl, w.ctl, sizeof(ctl), cudaMemcpyDeviceToHost, st));
-      CPCA_CUDA(cudaStreamSynchronize(st));
-      if (ctl[0]) break;
-    }
-  }
   if (info) {
     CPCA_TRY(fista_objective(Yt, ldyt, rr, rc, lr, lc, X, ldx, prm->gamma_r, prm->gamma_c, w, st));
     int ctl[2];
-    double scal[3], obj, last[2] = {0, 0};
+    double scal[3], obj, ring[8];
+    int err = 0;
     CPCA_CUDA(cudaMemcpyAsync(ctl, w.ctl, sizeof(ctl), cudaMemcpyDeviceToHost, st));
     CPCA_CUDA(cudaMemcpyAsync(scal, w.scal, sizeof(scal), cudaMemcpyDeviceToHost, st));
     CPCA_CUDA(cudaMemcpyAsync(&obj, w.obj, sizeof(obj), cudaMemcpyDeviceToHost, st));
+    CPCA_CUDA(cudaMemcpyAsync(ring, w.stats, sizeof(ring), cudaMemcpyDeviceToHost, st));
+    CPCA_CUDA(cudaMemcpyAsync(&err, w.err, sizeof(err), cudaMemcpyDeviceToHost, st));
     CPCA_CUDA(cudaStreamSynchronize(st));
-    if (ctl[0]) done_iters = ctl[1];
-    if (done_iters > 0) {
-      const int s = prm->eps > 0 ? done_iters - 1 : 0;
-      CPCA_CUDA(cudaMemcpy(last, w.stats + 2 * s, sizeof(last), cudaMemcpyDeviceToHost));
+    if (err) {
+      set_error("cpca_frpcag_solve: grid barrier timed out");
+      return CPCA_ERR_TIMEOUT;
     }
+    if (J > 0) done_iters = ctl[1];
+    const double* last = ring + 2 * (done_iters & 3);
     info->iters = done_iters;
     info->norm_r = scal[0];
     info->norm_c = scal[1];
     info->step = scal[2];
-    info->rel_change = last[1] > 0 ? last[0] / last[1] : 0.0;
+    info->rel_change = done_iters > 0 && last[1] > 0 ? last[0] / last[1] : 0.0;
     info->objective = obj;
   }
   return CPCA_OK;

@@ -14,33 +14,37 @@ struct CsrView {
   const float* val;
 };
 
-// Largest max_iter for which eps > 0 keeps one statistics slot per iteration.
+// Kept for the workspace-size signature (statistics now live in a ring).
 constexpr int kMaxStatIters = 1 << 20;
+constexpr int kObjBlocks = 512;
 
 struct FistaWs {
-  float* Z0;      // Z_j ping
-  float* Z1;      // Z_j pong
-  double* scal;   // [|Lr|, |Lc|, lambda, spare]
-  double* vbuf;   // power-iteration vectors
-  double* stats;  // per-iteration [|dZ|^2, |Z|^2]
-  int* ctl;       // [stopped, iterations]
-  double* part;   // objective partials
+  float* Z0;          // Z_j ping
+  float* Z1;          // Z_j pong
+  float* ZT0;         // Z_j^T ping (column-major copy)
+  float* ZT1;         // Z_j^T pong
+  double* scal;       // [|Lr|, |Lc|, lambda, spare]
+  float* pu[2][2];    // power iteration vectors [graph][ping/pong]
+  double* pacc;       // power iteration norm ring [3][2] + quotients [2][2]
+  double* stats;      // FISTA statistics ring [4][2]
+  int* ctl;           // [stopped, iterations]
+  unsigned int* bar;  // grid barrier counters + generation
+  int* err;           // barrier timeout flag
+  double* part;       // objective partials
   double* obj;
   size_t bytes;
 };
 
-FistaWs fista_layout(void* ws, int rr, int rc, int max_iter_stats);
+FistaWs fista_layout(void* ws, int rr, int rc, int unused);
 cpca_status power_step(const CsrView& Lr, const CsrView& Lc, int iters, uint64_t seed,
                        double gamma_r, double gamma_c, double step_given, const FistaWs& w,
                        cudaStream_t st);
-int fista_rows_per_block(int rc);
-cpca_status fista_iteration(int R, const float* Yt, int64_t ldy, int rr, int rc, const CsrView& Lr,
-                            const CsrView& Lc, const float* Zin, float* Zout, float* S,
-                            int64_t lds, const double* lam, double gamma_r, double gamma_c,
-                            double mu, int iter1, double eps, const double* prev_stats,
-                            double* out_stats, int* ctl, cudaStream_t st);
-cpca_status fista_init(const float* Yt, int64_t ldy, int rr, int rc, float* Z, float* S,
-                       int64_t lds, cudaStream_t st);
+cpca_status fista_run(const float* Yt, int64_t ldy, int rr, int rc, const CsrView& Lr,
+                      const CsrView& Lc, float* X, int64_t ldx, double gamma_r, double gamma_c,
+                      int J, double eps, bool want_last, int tile_rows, const FistaWs& w,
+                      cudaStream_t st);
+cpca_status fista_init(const float* Yt, int64_t ldy, int rr, int rc, float* Z, float* ZT,
+                       float* S, int64_t lds, cudaStream_t st);
 cpca_status fista_objective(const float* Yt, int64_t ldy, int rr, int rc, const CsrView& Lr,
                             const CsrView& Lc, const float* X, int64_t ldx, double gr, double gc,
                             const FistaWs& w, cudaStream_t st);

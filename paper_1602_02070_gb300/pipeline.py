@@ -20,7 +20,7 @@ def cpca_pipeline(Y: torch.Tensor, K: int = 10, fr: float = 0.25, fc: float = 0.
                   J: int = 300, gamma_r: float = 1.0, gamma_c: float = 1.0,
                   lap_type: int = capi.LAP_NORMALIZED, cg_tol: float = 1e-6,
                   power_iters: int = 200, power_seed: int = 0, rank_ratio: float = 0.1,
-                  delta: float = 0.0, kmax: int = 32, svd_iters: int = 6, marks=None,
+                  delta: float = 0.0, kmax: int = 24, svd_iters: int = 6, marks=None,
                   want_X: bool = True, check_status: bool = True):
     """Steps 1-6 on a dense device matrix Y (p x n, FP32, row-major).
 
@@ -42,7 +42,7 @@ def cpca_pipeline(Y: torch.Tensor, K: int = 10, fr: float = 0.25, fc: float = 0.
     Lrt, _, _ = capi.cpca_knn_graph(Yt, K, lap_type)
     Lct, _, _ = capi.cpca_knn_graph(Yt, K, lap_type, transposed=True)
     mark("sample")
-    prm = capi.frpcag_params(gamma_r, gamma_c, -1.0, J, 0.0, 25, power_iters, power_seed)
+    prm = capi.frpcag_params(gamma_r, gamma_c, -1.0, J, 0.0, power_iters, power_seed)
     Xt, finfo = capi.cpca_frpcag_solve(Yt, Lrt, Lct, prm, want_info=False)
     mark("fista")
     dprm = capi.decode_params(rank_ratio, 0, kmax, delta, cg_tol, 0, svd_iters, 0)

@@ -87,9 +87,12 @@ typedef struct cpca_csr {
  * column i of a dim x npts row-major matrix with leading dimension ld >= npts
  * (pass Y with npts = n, dim = p, ld = n for the column graph of Y).
  * For each point the K nearest other points by Euclidean distance are found
- * (ties by lower index). Squared distances are summed directly over the
- * coordinates in FP32 (never through |a|^2 + |b|^2 - 2ab; that expansion only
- * ranks candidates). The graph joins i and j if either is among the other's
+ * (ties by lower index). Candidates are ranked by |a|^2 + |b|^2 - 2ab with the
+ * dot products on the tensor cores (TF32, FP32 accumulate; FP32 SIMT when
+ * the rows are not 16-byte aligned); the kept squared distances are then
+ * summed directly over the coordinates in FP32, and a certificate (the
+ * ranking error bound against the gap to the best non-candidate) decides
+ * per query whether an exact brute-force search is needed. The graph joins i and j if either is among the other's
  * K nearest; W_ij = exp(-d2_ij / sigma2) with sigma2 = the given value, or,
  * if sigma2 <= 0, the mean of the npts*K directed kNN squared distances.
  * Degrees D_ii = sum_j W_ij; lap_type selects L_n (CPCA_LAP_NORMALIZED) or
@@ -105,6 +108,10 @@ typedef struct cpca_csr {
  * Requirements: 1 <= K <= 32, K < npts, dim >= 1.
  * ---------------------------------------------------------------------- */
 size_t cpca_knn_graph_workspace_size(int32_t npts, int32_t dim, int32_t K, int32_t transposed);
+/* Number of query points of the last cpca_knn_graph call on this host
+ * thread whose candidate lists could not be certified and were therefore
+ * searched by exact brute force. */
+int32_t cpca_knn_last_bruteforce(void);
 cpca_status cpca_knn_graph(const float* pts, int32_t npts, int32_t dim, int64_t ld,
                            int32_t transposed, int32_t K, int32_t lap_type, double sigma2,
                            int64_t* rowptr, int32_t* col, float* val, float* weight,

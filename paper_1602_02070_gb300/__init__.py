@@ -7,6 +7,7 @@ from .capi import (CPCA_ERR_CAPACITY, CPCA_ERR_CUDA, CPCA_ERR_INVALID_ARG,  # no
                    CPCA_ERR_NOT_CONVERGED, CPCA_ERR_SINGULAR, CPCA_ERR_TIMEOUT,
                    CPCA_ERR_WORKSPACE, CPCA_OK, LAP_COMBINATORIAL, LAP_NORMALIZED, CpcaError, Csr,
                    cpca_decode, cpca_frpcag_solve, cpca_knn_graph, cpca_sample, decode_params,
-                   exported_names, frpcag_params, launch_count, lib, profile_enable,
+                   exported_names, frpcag_params, knn_last_bruteforce, launch_count, lib,
+                   profile_enable,
                    profile_read)
 from .pipeline import cpca_pipeline, rho_of  # noqa: F401

@@ -76,6 +76,7 @@ _SIGS = [
     ("cpca_profile_read", C.c_int32, [C.c_int32, C.c_char_p, C.c_int32, C.POINTER(C.c_double),
                                       C.POINTER(C.c_int32)]),
     ("cpca_knn_graph_workspace_size", C.c_size_t, [C.c_int32, C.c_int32, C.c_int32, C.c_int32]),
+    ("cpca_knn_last_bruteforce", C.c_int32, []),
     ("cpca_knn_graph", C.c_int32,
      [C.c_void_p, C.c_int32, C.c_int32, C.c_int64, C.c_int32, C.c_int32, C.c_int32, C.c_double,
       C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p,
@@ -140,6 +141,12 @@ def _require_cuda(t: torch.Tensor, dtype, name: str):
 
 def _workspace(nbytes: int, device) -> torch.Tensor:
     return torch.empty(max(int(nbytes), 256), dtype=torch.uint8, device=device)
+
+
+def knn_last_bruteforce() -> int:
+    """Queries of the last cpca_knn_graph call (this thread) that fell back
+    to exact brute force because their candidates were not certified."""
+    return int(lib().cpca_knn_last_bruteforce())
 
 
 def launch_count() -> int:

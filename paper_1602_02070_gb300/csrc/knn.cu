@@ -478,6 +478,7 @@ struct KnnWs {
   float* kd2;
   int32_t* redo;
   int32_t* n_redo;
+  int* err;
   double* part;
   double* sigma2;
   int32_t* indeg;
@@ -502,7 +503,7 @@ static KnnWs knn_layout(void* ws, int N, int d, int K, int transposed) {
   Carve c(ws);
   KnnWs w{};
   const int S = knn_splits(N), M = knn_M(K);
-  w.Pt = transposed ? c.take<float>(size_t(N) * d) : nullptr;
+  w.Pt = transposed ? c.take<float>(size_t(N) * ((d + 3) & ~3)) : nullptr;
   w.nrm = c.take<float>(N);
   w.nmax = c.take<unsigned int>(1);
   w.cand_i = c.take<int32_t>(size_t(S) * N * M);
@@ -511,6 +512,7 @@ static KnnWs knn_layout(void* ws, int N, int d, int K, int transposed) {
   w.kd2 = c.take<float>(size_t(N) * K);
   w.redo = c.take<int32_t>(N);
   w.n_redo = c.take<int32_t>(1);
+  w.err = c.take<int>(1);
   w.part = c.take<double>(RED_BLOCKS);
   w.sigma2 = c.take<double>(1);
   w.indeg = c.take<int32_t>(N);
@@ -536,7 +538,8 @@ cpca_status knn_lists(const float* P, int N, int d, int64_t ld, int K, const Knn
   norms_kernel<<<ceil_div(int64_t(N) * 32, 256), 256, 0, st>>>(P, N, d, ld, w.nrm, w.nmax);
   CPCA_LAUNCHED();
   bool done = false;
-  CPCA_TRY(knn_candidates_tc(P, N, d, ld, M, S, w.nrm, w.cand_i, w.cand_d, &done, st));
+  CPCA_CUDA(cudaMemsetAsync(w.err, 0, sizeof(int), st));
+  CPCA_TRY(knn_candidates_tc(P, N, d, ld, M, S, w.nrm, w.cand_i, w.cand_d, w.err, &done, st));
   if (!done) {
     const size_t smem = sizeof(float) * (BD * BQ + BD * BB + BQ * (BB + 1)) + size_t(BQ) * M * 8;
     dim3 grid(ceil_div(N, BQ), S);
@@ -607,6 +610,10 @@ cpca_status graph_from_knn(const int32_t* kidx, const float* kd2, int N, int K, 
 
 using namespace cpca;
 
+static thread_local int g_knn_last_redo = 0;
+
+extern "C" int32_t cpca_knn_last_bruteforce(void) { return g_knn_last_redo; }
+
 extern "C" size_t cpca_knn_graph_workspace_size(int32_t npts, int32_t dim, int32_t K,
                                                 int32_t transposed) {
   if (npts <= 0 || dim <= 0 || K <= 0) return 0;
@@ -638,12 +645,15 @@ extern "C" cpca_status cpca_knn_graph(const float* pts, int32_t npts, int32_t di
   int64_t pld = ld;
   if (transposed) {
     // Point-major copy of the columns (rows of length dim, ld = dim).
+    // rows padded with zeros to a multiple of 4 floats (16-byte row stride)
+    const int dpad = (dim + 3) & ~3;
+    if (dpad != dim) CPCA_CUDA(cudaMemsetAsync(w.Pt, 0, sizeof(float) * size_t(npts) * dpad, st));
     dim3 blk(32, 8), grd(ceil_div(npts, 32), ceil_div(dim, 32));
     CPCA_PROF("knn_transpose", st);
-    transpose_kernel<<<grd, blk, 0, st>>>(pts, dim, npts, ld, w.Pt, dim);
+    transpose_kernel<<<grd, blk, 0, st>>>(pts, dim, npts, ld, w.Pt, dpad);
     CPCA_LAUNCHED();
     P = w.Pt;
-    pld = dim;
+    pld = dpad;
   }
   int32_t* oi = knn_idx ? knn_idx : w.kidx;
   float* od = knn_d2 ? knn_d2 : w.kd2;
@@ -653,7 +663,15 @@ extern "C" cpca_status cpca_knn_graph(const float* pts, int32_t npts, int32_t di
   double s2 = 0;
   CPCA_CUDA(cudaMemcpyAsync(&nnz, rowptr + npts, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
   CPCA_CUDA(cudaMemcpyAsync(&s2, w.sigma2, sizeof(double), cudaMemcpyDeviceToHost, st));
+  int terr = 0, nredo = 0;
+  CPCA_CUDA(cudaMemcpyAsync(&terr, w.err, sizeof(int), cudaMemcpyDeviceToHost, st));
+  CPCA_CUDA(cudaMemcpyAsync(&nredo, w.n_redo, sizeof(int), cudaMemcpyDeviceToHost, st));
   CPCA_CUDA(cudaStreamSynchronize(st));
+  g_knn_last_redo = nredo;
+  if (terr) {
+    set_error("cpca_knn_graph: tensor-core pass timed out waiting on an mbarrier");
+    return CPCA_ERR_TIMEOUT;
+  }
   if (nnz_out) *nnz_out = nnz;
   if (sigma2_out) *sigma2_out = s2;
   if (nnz > nnz_cap) {

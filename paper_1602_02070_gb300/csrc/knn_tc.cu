@@ -1,14 +1,386 @@
-// knn_tc.cu - tensor-core candidate pass for the kNN graph (placeholder:
-// reports "not handled" so the SIMT pass runs).
+// knn_tc.cu - tensor-core candidate pass for the kNN graph (sm_103a).
+//
+// For a block of 128 query points and, in turn, every 256-point base tile
+// of its split, the dot products q.b are computed on the 5th-generation
+// tensor cores (tcgen05.mma, kind::tf32, M = 128, N = 256, FP32 accumulate
+// in tensor memory); the ranking distance |q|^2 + |b|^2 - 2 q.b then feeds a
+// per-query list of the M smallest, kept in shared memory (a per-lane bitmask
+// of the values under the current threshold limits the sorted insertions to
+// the few that can enter the list). These are only
+// candidates: knn.cu re-scores them with the exact FP32 squared distance and
+// certifies the result against the error bound returned by knn_tc_err_rel.
+//
+// Warp roles (8 warps): warp 0 = TMA producer (one lane), warp 1 = tensor
+// memory allocator and MMA issuer (one lane), warps 4-7 = epilogue (warp w
+// reads TMEM lanes 32 (w % 4) .. +31, i.e. queries 32 (w - 4) .. +31).
+// Operands: K-major, 128-byte swizzle, 32 FP32 columns (128 B) per stage;
+// a 3-stage ring of (A 16 KB + B 32 KB) guarded by full/empty mbarriers; two
+// 256-column accumulators in TMEM (512 columns) so the epilogue of one base
+// tile overlaps the MMAs of the next. Every mbarrier wait is bounded: on
+// timeout the block raises *err, stops, frees its TMEM and returns.
+#include <cuda.h>
+
 #include "knn_internal.cuh"
 
 namespace cpca {
+namespace {
 
-cpca_status knn_candidates_tc(const float*, int, int, int64_t, int, int, const float*, int32_t*,
-                              float*, bool* done, cudaStream_t) {
+constexpr int BM = 128, BN = 256, BK = 32, STAGES = 3;
+constexpr int A_BYTES = BM * BK * 4, B_BYTES = BN * BK * 4, STAGE_BYTES = A_BYTES + B_BYTES;
+constexpr uint32_t TMEM_COLS = 512;
+constexpr long long kWaitLimit = 1ll << 26;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait for the phase of `parity`; false on timeout or abort.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort) {
+  for (long long i = 0; i < kWaitLimit; ++i) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if (*abort) return false;
+    if (i > 32) __nanosleep(32);
+  }
+  *abort = 1;
+  return false;
+}
+
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];" ::
+          "r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(x), "r"(y)
+      : "memory");
+}
+
+// UMMA shared-memory descriptor: K-major, 128-byte swizzle, 8-row atoms of
+// 1024 bytes (stride byte offset), sm_100-family descriptor version 1.
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= uint64_t((saddr >> 4) & 0x3FFF);
+  d |= uint64_t(1) << 16;           // leading byte offset (unused for swizzled K-major)
+  d |= uint64_t(1024 >> 4) << 32;   // stride byte offset
+  d |= uint64_t(1) << 46;           // descriptor version
+  d |= uint64_t(2) << 61;           // SWIZZLE_128B
+  return d;
+}
+
+// Instruction descriptor, kind::tf32: D F32, A/B TF32, both K-major, M x N.
+__host__ __device__ constexpr uint32_t tf32_idesc(int M, int N) {
+  return (1u << 4) | (2u << 7) | (2u << 10) | (uint32_t(N >> 3) << 17) | (uint32_t(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void umma_tf32(uint32_t dtmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                          uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(dtmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+__device__ __forceinline__ void umma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                   smem_u32(bar))
+               : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+#define TMEM_LD_X32(taddr, r)                                                                     \
+  asm volatile(                                                                                   \
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, " \
+      "%12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, " \
+      "%30, %31}, [%32];"                                                                         \
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),       \
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),   \
+        "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),             \
+        "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),             \
+        "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])              \
+      : "r"(taddr)                                                                                \
+      : "memory")
+
+struct TcShared {
+  uint64_t full[STAGES], empty[STAGES], acc_full[2], acc_empty[2];
+  uint32_t tmem_base;
+  int abort;
+};
+
+template <int M>
+__global__ void __launch_bounds__(256, 1)
+knn_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
+              int N, int d, const float* __restrict__ nrm, int splits, int32_t* __restrict__ cand_i,
+              float* __restrict__ cand_d, int* __restrict__ err) {
+  extern __shared__ __align__(1024) unsigned char raw[];
+  // operand stages must be 1024-byte aligned for the 128-byte swizzle
+  unsigned char* base = reinterpret_cast<unsigned char*>(
+      (reinterpret_cast<uintptr_t>(raw) + 1023) & ~uintptr_t(1023));
+  unsigned char* stages = base;
+  float* ld_ = reinterpret_cast<float*>(base + STAGES * STAGE_BYTES);  // [M][128]
+  int32_t* li = reinterpret_cast<int32_t*>(ld_ + M * BM + 32 * BM);  // [M][128]
+  TcShared& sh = *reinterpret_cast<TcShared*>(li + M * BM);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int q0 = blockIdx.x * BM;
+  const int ntiles = (N + BN - 1) / BN;
+  const int per = (ntiles + splits - 1) / splits;
+  const int t_lo = blockIdx.y * per, t_hi = min(ntiles, t_lo + per);
+  const int nt = max(0, t_hi - t_lo);
+  const int nk = (d + BK - 1) / BK;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(&sh.full[s], 1);
+      mbar_init(&sh.empty[s], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&sh.acc_full[b], 1);
+      mbar_init(&sh.acc_empty[b], 4);
+    }
+    sh.abort = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(&sh.tmem_base)),
+                 "r"(TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = sh.tmem_base;
+  volatile int* abort = &sh.abort;
+
+  if (warp == 0) {
+    if (lane == 0) {  // ---------------------------------------- TMA producer
+      int it = 0;
+      for (int t = 0; t < nt && !*abort; ++t) {
+        const int n0 = (t_lo + t) * BN;
+        for (int k = 0; k < nk; ++k, ++it) {
+          const int s = it % STAGES, round = it / STAGES;
+          if (!mbar_wait(&sh.empty[s], (round & 1) ^ 1, abort)) break;
+          mbar_expect_tx(&sh.full[s], STAGE_BYTES);
+          unsigned char* sa = stages + s * STAGE_BYTES;
+          tma_load_2d(sa, &mapA, &sh.full[s], k * BK, q0);
+          tma_load_2d(sa + A_BYTES, &mapB, &sh.full[s], k * BK, n0);
+        }
+      }
+      // drain: wait for every issued stage to be consumed before leaving
+      for (int s = 0; s < STAGES && it > 0; ++s) {
+        const int last = it - 1 - s;
+        if (last < 0) break;
+        if (!mbar_wait(&sh.empty[last % STAGES], (last / STAGES) & 1, abort)) break;
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {  // ------------------------------------------ MMA issuer
+      constexpr uint32_t idesc = tf32_idesc(BM, BN);
+      int it = 0;
+      for (int t = 0; t < nt && !*abort; ++t) {
+        const int buf = t & 1, use = t >> 1;
+        if (!mbar_wait(&sh.acc_empty[buf], (use & 1) ^ 1, abort)) break;
+        tc_fence_after();
+        const uint32_t dt = tmem + uint32_t(buf * BN);
+        bool ok = true;
+        for (int k = 0; k < nk; ++k, ++it) {
+          const int s = it % STAGES, round = it / STAGES;
+          if (!mbar_wait(&sh.full[s], round & 1, abort)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t sa = smem_u32(stages + s * STAGE_BYTES);
+          const uint64_t ad = sw128_desc(sa), bd = sw128_desc(sa + A_BYTES);
+#pragma unroll
+          for (int kk = 0; kk < BK / 8; ++kk)  // 8 TF32 (32 bytes) per MMA
+            umma_tf32(dt, ad + uint64_t(kk * 2), bd + uint64_t(kk * 2), idesc, (k | kk) ? 1u : 0u);
+          umma_commit(&sh.empty[s]);
+        }
+        if (!ok) break;
+        umma_commit(&sh.acc_full[buf]);
+      }
+    }
+  } else if (warp >= 4) {  // ------------------------------------- epilogue
+    // Ranking value b2 - 2 q.b (|q|^2 is the same for the whole row and is
+    // added when the list is written out). Per 32-column chunk every lane
+    // builds a bitmask of the values below its current threshold; only
+    // those are inserted into its sorted list, so lanes rarely diverge.
+    const int ql = (warp - 4) * 32 + lane;  // query within the block = TMEM lane
+    const int q = q0 + ql;
+    float* stage_d = ld_ + M * BM;          // [32][128] chunk values
+    for (int m = 0; m < M; ++m) {
+      ld_[m * BM + ql] = __int_as_float(0x7f800000);
+      li[m * BM + ql] = -1;
+    }
+    float thr = __int_as_float(0x7f800000);
+    const uint32_t lane_base = uint32_t((warp & 3) * 32) << 16;
+    for (int t = 0; t < nt; ++t) {
+      const int buf = t & 1, use = t >> 1;
+      if (!mbar_wait(&sh.acc_full[buf], use & 1, abort)) break;
+      tc_fence_after();
+      const int n0 = (t_lo + t) * BN;
+#pragma unroll 1
+      for (int ch = 0; ch < BN / 32; ++ch) {
+        uint32_t r[32];
+        TMEM_LD_X32(tmem + lane_base + uint32_t(buf * BN + ch * 32), r);
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        const int nb0 = n0 + ch * 32;
+        const float nbl = nb0 + lane < N ? __ldg(nrm + nb0 + lane) : __int_as_float(0x7f800000);
+        uint32_t mask = 0;
+#pragma unroll
+        for (int i = 0; i < 32; ++i) {
+          const float dd = fmaf(-2.f, __uint_as_float(r[i]), __shfl_sync(0xffffffffu, nbl, i));
+          stage_d[i * BM + ql] = dd;
+          mask |= (dd < thr ? 1u : 0u) << i;
+        }
+        if (q >= nb0 && q < nb0 + 32) mask &= ~(1u << (q - nb0));
+        while (mask) {
+          const int i = __ffs(mask) - 1;
+          mask &= mask - 1;
+          const float dd = stage_d[i * BM + ql];
+          if (!(dd < thr)) continue;
+          // sorted insert (ascending; equal values keep the earlier index)
+          int pos = M - 1;
+          while (pos > 0 && ld_[(pos - 1) * BM + ql] > dd) {
+            ld_[pos * BM + ql] = ld_[(pos - 1) * BM + ql];
+            li[pos * BM + ql] = li[(pos - 1) * BM + ql];
+            --pos;
+          }
+          ld_[pos * BM + ql] = dd;
+          li[pos * BM + ql] = nb0 + i;
+          thr = ld_[(M - 1) * BM + ql];
+        }
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&sh.acc_empty[buf]);
+    }
+    if (q < N) {
+      const float nq = nrm[q];
+      for (int m = 0; m < M; ++m) {
+        const int64_t o = (int64_t(blockIdx.y) * N + q) * M + m;
+        cand_i[o] = li[m * BM + ql];
+        cand_d[o] = ld_[m * BM + ql] + nq;
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 1)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS)
+                 : "memory");
+  if (threadIdx.x == 0 && sh.abort) atomicExch(err, 1);
+}
+
+using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                   const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                   const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                   CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn() {
+  static EncodeTiledFn fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(p);
+    cudaGetLastError();
+  }
+  return fn;
+}
+
+bool make_map(CUtensorMap* map, const float* P, int N, int d, int64_t ld, int box_rows) {
+  EncodeTiledFn fn = encode_fn();
+  if (!fn) return false;
+  cuuint64_t dims[2] = {cuuint64_t(d), cuuint64_t(N)};
+  cuuint64_t strides[1] = {cuuint64_t(ld) * 4};
+  cuuint32_t box[2] = {cuuint32_t(BK), cuuint32_t(box_rows)};
+  cuuint32_t estr[2] = {1, 1};
+  return fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(P), dims, strides, box, estr,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+bool device_is_sm10x() {
+  static int cc = -1;
+  if (cc < 0) {
+    int dev = 0, major = 0, minor = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev);
+    cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev);
+    cudaGetLastError();
+    cc = major * 10 + minor;
+  }
+  return cc == 103;
+}
+
+}  // namespace
+
+size_t knn_tc_smem(int M) {
+  return 1024 + size_t(STAGES) * STAGE_BYTES + size_t(M) * BM * 8 + size_t(32) * BM * 4 +
+         sizeof(TcShared) + 64;
+}
+
+cpca_status knn_candidates_tc(const float* P, int N, int d, int64_t ld, int M, int S,
+                              const float* nrm, int32_t* cand_i, float* cand_d, int* err, bool* done,
+                              cudaStream_t st) {
   *done = false;
+  // shapes where the tensor-core pass pays off and TMA's rules hold: row
+  // stride a multiple of 16 bytes, 16-byte aligned base
+  if (!device_is_sm10x() || N < 64 || d < 16 || (ld % 4) != 0 ||
+      (reinterpret_cast<uintptr_t>(P) & 15) != 0 || (M != 32 && M != 64))
+    return CPCA_OK;
+  CUtensorMap mapA, mapB;
+  if (!make_map(&mapA, P, N, d, ld, BM) || !make_map(&mapB, P, N, d, ld, BN)) return CPCA_OK;
+  const size_t smem = knn_tc_smem(M);
+  const void* kern = M == 32 ? (const void*)knn_tc_kernel<32> : (const void*)knn_tc_kernel<64>;
+  CPCA_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
+  dim3 grid(ceil_div(N, BM), S);
+  CPCA_PROF("knn_candidates_tc", st);
+  if (M == 32)
+    knn_tc_kernel<32><<<grid, 256, smem, st>>>(mapA, mapB, N, d, nrm, S, cand_i, cand_d, err);
+  else
+    knn_tc_kernel<64><<<grid, 256, smem, st>>>(mapA, mapB, N, d, nrm, S, cand_i, cand_d, err);
+  CPCA_LAUNCHED();
+  *done = true;
   return CPCA_OK;
 }
-float knn_tc_err_rel(int) { return 0.f; }
+
+// Bound on |ranking distance - exact distance| / (|q|^2 + |b|^2) for the
+// TF32 pass: each operand keeps 10 explicit mantissa bits (relative error
+// <= 2^-10 each, so <= 2^-9 per product and |2 q.b| errs by <= 2^-8 |q||b|
+// <= 2^-9 (|q|^2 + |b|^2)), plus FP32 accumulation over d terms and the
+// FP32 norms, about (d + 8) roundings of 2^-24 each.
+float knn_tc_err_rel(int d) { return float(0x1.0p-9 + (double(d) + 8.0) * 0x1.0p-23); }
 
 }  // namespace cpca

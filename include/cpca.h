@@ -233,7 +233,8 @@ typedef struct cpca_decode_info {
   int32_t b;            /* subspace block size used */
 } cpca_decode_info;
 
-size_t cpca_decode_workspace_size(int32_t p, int32_t n, int32_t rr, int32_t rc, int32_t kmax);
+size_t cpca_decode_workspace_size(int32_t p, int32_t n, int32_t rr, int32_t rc, int32_t kmax,
+                                  int64_t nnz_r, int64_t nnz_c);  /* nnz of Lr and Lc */
 cpca_status cpca_decode(const float* Xt, int32_t rr, int32_t rc, int64_t ldxt,
                         const int32_t* omega_r, const int32_t* omega_c,
                         int32_t p, int32_t n, const cpca_csr* Lr, const cpca_csr* Lc,

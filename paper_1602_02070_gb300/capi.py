@@ -89,7 +89,7 @@ _SIGS = [
      [C.c_void_p, C.c_int32, C.c_int32, C.c_int64, C.POINTER(cpca_csr), C.POINTER(cpca_csr),
       C.POINTER(cpca_frpcag_params), C.c_void_p, C.c_int64, C.POINTER(cpca_solve_info),
       C.c_void_p, C.c_size_t, C.c_void_p]),
-    ("cpca_decode_workspace_size", C.c_size_t, [C.c_int32] * 5),
+    ("cpca_decode_workspace_size", C.c_size_t, [C.c_int32] * 5 + [C.c_int64] * 2),
     ("cpca_decode", C.c_int32,
      [C.c_void_p, C.c_int32, C.c_int32, C.c_int64, C.c_void_p, C.c_void_p, C.c_int32, C.c_int32,
       C.POINTER(cpca_csr), C.POINTER(cpca_csr), C.POINTER(cpca_decode_params), C.c_void_p,
@@ -243,10 +243,13 @@ def cpca_sample(seed: int, p: int, n: int, rho_r: int, rho_c: int, Y: torch.Tens
         device = Y.device
     om_r = torch.empty(rho_r, dtype=torch.int32, device=device)
     om_c = torch.empty(rho_c, dtype=torch.int32, device=device)
-    Yt = torch.empty(rho_r, rho_c, dtype=torch.float32, device=device) if Y is not None else None
+    # rows padded to a multiple of 4 floats: 16-byte row stride for TMA and vector loads
+    ldyt = (rho_c + 3) // 4 * 4
+    Yt = (torch.empty(rho_r, ldyt, dtype=torch.float32, device=device)[:, :rho_c]
+          if Y is not None else None)
     _check(lib().cpca_sample(seed & (2 ** 64 - 1), p, n, rho_r, rho_c, _ptr(Y),
                              Y.stride(0) if Y is not None else 0, _ptr(om_r), _ptr(om_c),
-                             _ptr(Yt), rho_c, _stream()))
+                             _ptr(Yt), ldyt, _stream()))
     return om_r, om_c, Yt
 
 
@@ -294,7 +297,7 @@ def cpca_decode(Xt: torch.Tensor, omega_r: torch.Tensor, omega_c: torch.Tensor, 
     V = torch.empty(n, kmax, dtype=torch.float32, device=dev)
     sig = torch.empty(kmax, dtype=torch.float64, device=dev)
     if ws is None:
-        ws = _workspace(lib().cpca_decode_workspace_size(p, n, rr, rc, kmax), dev)
+        ws = _workspace(lib().cpca_decode_workspace_size(p, n, rr, rc, kmax, Lr.nnz, Lc.nnz), dev)
     k = C.c_int32(0)
     info = cpca_decode_info()
     lr, lc = Lr.c(), Lc.c()

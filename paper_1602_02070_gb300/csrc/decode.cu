@@ -128,55 +128,56 @@ gram_kernel(const float* __restrict__ Q, int m, int b, double* __restrict__ G) {
 }
 
 // Rank-revealing Cholesky G = R^T R (R upper) and Rinv with the columns of
-// numerically dependent directions zeroed. One block, FP64.
-__global__ void __launch_bounds__(256)
+// numerically dependent directions zeroed. One warp, FP64, R and R^-1 in
+// shared memory (no block-wide barriers on the b sequential steps).
+__global__ void __launch_bounds__(32)
 chol_inv_kernel(const double* __restrict__ G, int b, double* __restrict__ Rinv) {
-  __shared__ double R[BMAX][BMAX + 1];
-  __shared__ double X[BMAX][BMAX + 1];
-  __shared__ int dead[BMAX];
-  __shared__ double red[8];
-  const int tid = threadIdx.x;
-  for (int e = tid; e < BMAX * BMAX; e += blockDim.x) {
-    R[e / BMAX][e % BMAX] = 0.0;
-    X[e / BMAX][e % BMAX] = 0.0;
+  extern __shared__ double cs_sm[];
+  double* R = cs_sm;                    // [BMAX][BMAX + 1]
+  double* X = R + BMAX * (BMAX + 1);    // [BMAX][BMAX + 1]
+  int* dead = reinterpret_cast<int*>(X + BMAX * (BMAX + 1));
+  const int lane = threadIdx.x;
+  constexpr int LD = BMAX + 1;
+  for (int e = lane; e < BMAX * LD; e += 32) {
+    R[e] = 0.0;
+    X[e] = 0.0;
   }
-  __syncthreads();
+  __syncwarp();
   for (int j = 0; j < b; ++j) {
     double part = 0.0;
-    for (int k = tid; k < j; k += blockDim.x) part += R[k][j] * R[k][j];
-    part = block_sum(part, red);
+    for (int k = lane; k < j; k += 32) part += R[k * LD + j] * R[k * LD + j];
+    part = warp_sum(part);
     const double gjj = G[j * b + j];
     const double d = gjj - part;
     const bool dd = !(gjj > 1e-300) || !(d > 1e-10 * gjj);
     const double djj = dd ? 1.0 : sqrt(d);
-    if (tid == 0) {
-      dead[j] = dd;
-      R[j][j] = djj;
-    }
-    for (int i = j + 1 + tid; i < b; i += blockDim.x) {
-      if (dd) {
-        R[j][i] = 0.0;
-      } else {
-        double s = G[j * b + i];
-        for (int k = 0; k < j; ++k) s -= R[k][j] * R[k][i];
-        R[j][i] = s / djj;
+    for (int i = j + 1 + lane; i < b; i += 32) {
+      double s = 0.0;
+      if (!dd) {
+        s = G[j * b + i];
+        for (int k = 0; k < j; ++k) s -= R[k * LD + j] * R[k * LD + i];
+        s /= djj;
       }
+      R[j * LD + i] = s;
     }
-    __syncthreads();
+    if (lane == 0) {
+      R[j * LD + j] = djj;
+      dead[j] = dd;
+    }
+    __syncwarp();
   }
-  // R X = I, X upper: row i of X from rows below it, all columns in parallel
+  // R X = I with X upper triangular: row i from the rows below it
   for (int i = b - 1; i >= 0; --i) {
-    for (int c = tid; c < b; c += blockDim.x) {
-      if (c < i) continue;
+    for (int c = i + lane; c < b; c += 32) {
       double s = (i == c) ? 1.0 : 0.0;
-      for (int k = i + 1; k <= c; ++k) s -= R[i][k] * X[k][c];
-      X[i][c] = s / R[i][i];
+      for (int k = i + 1; k <= c; ++k) s -= R[i * LD + k] * X[k * LD + c];
+      X[i * LD + c] = s / R[i * LD + i];
     }
-    __syncthreads();
+    __syncwarp();
   }
-  for (int e = tid; e < b * b; e += blockDim.x) {
+  for (int e = lane; e < b * b; e += 32) {
     const int i = e / b, c = e % b;
-    Rinv[e] = (dead[c] || i > c || dead[i]) ? 0.0 : X[i][c];
+    Rinv[e] = (dead[c] || i > c || dead[i]) ? 0.0 : X[i * LD + c];
   }
 }
 
@@ -323,6 +324,9 @@ struct CgSide {
   CsrView L;
   const int32_t* omega;  // sampled nodes, ascending
   int32_t* reach;        // [m]: 1 once a path to a sampled node is known
+  int64_t* rp;           // [m + 1] reduced L_aa rows (unsampled index space)
+  int32_t* rcol;         // unsampled index of each kept neighbour
+  float* rval;
   int32_t* pos;          // [N]: >= 0 unsampled index, < 0 -(sampled index + 1)
   int32_t* abar;         // [m]: node of each unsampled index
   float* minv;           // [m]: 1 / L_aa diagonal (Jacobi)
@@ -363,6 +367,57 @@ __global__ void cg_setup_kernel(CgSide S0, CgSide S1) {
       for (int64_t e = S.L.rowptr[i]; e < S.L.rowptr[i + 1]; ++e)
         if (S.L.col[e] == i) dg = S.L.val[e];
       S.minv[t] = dg > 0.f ? 1.f / dg : 1.f;
+    }
+  }
+}
+
+// L_aa in its own CSR over the unsampled index space: count, scan, fill.
+__global__ void laa_count_kernel(CgSide S0, CgSide S1) {
+  const CgSide& S = blockIdx.y == 0 ? S0 : S1;
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < S.m; t += gridDim.x * blockDim.x) {
+    const int node = S.abar[t];
+    int c = 0;
+    for (int64_t e = S.L.rowptr[node]; e < S.L.rowptr[node + 1]; ++e) c += S.pos[S.L.col[e]] >= 0;
+    S.rp[t + 1] = c;
+  }
+}
+__global__ void laa_scan_kernel(CgSide S0, CgSide S1) {
+  const CgSide& S = blockIdx.x == 0 ? S0 : S1;
+  __shared__ int64_t sh[1024];
+  const int tid = threadIdx.x, nt = blockDim.x, m = S.m;
+  const int chunk = (m + nt - 1) / nt;
+  const int lo = min(m, tid * chunk), hi = min(m, lo + chunk);
+  int64_t sum = 0;
+  for (int t = lo; t < hi; ++t) sum += S.rp[t + 1];
+  sh[tid] = sum;
+  __syncthreads();
+  for (int o = 1; o < nt; o <<= 1) {
+    const int64_t v = tid >= o ? sh[tid - o] : 0;
+    __syncthreads();
+    sh[tid] += v;
+    __syncthreads();
+  }
+  // in place: rp[t + 1] = sum of the counts of rows 0..t (each thread only
+  // touches rp[lo + 1 .. hi]), rp[0] = 0
+  int64_t run = sh[tid] - sum;
+  for (int t = lo; t < hi; ++t) {
+    run += S.rp[t + 1];
+    S.rp[t + 1] = run;
+  }
+  if (tid == 0) S.rp[0] = 0;
+}
+__global__ void laa_fill_kernel(CgSide S0, CgSide S1) {
+  const CgSide& S = blockIdx.y == 0 ? S0 : S1;
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < S.m; t += gridDim.x * blockDim.x) {
+    const int node = S.abar[t];
+    int64_t w = S.rp[t];
+    for (int64_t e = S.L.rowptr[node]; e < S.L.rowptr[node + 1]; ++e) {
+      const int ps = S.pos[S.L.col[e]];
+      if (ps >= 0) {
+        S.rcol[w] = ps;
+        S.rval[w] = S.L.val[e];
+        ++w;
+      }
     }
   }
 }
@@ -512,15 +567,25 @@ cg_kernel(CgArgs a) {
         const float bt = float(beta[sd][mycol]);
         const float pv = fmaf(bt, pprev[l], S.z[l]);
         pcur[l] = pv;
-        const int node = S.abar[t];
         float qv = 0.f;
-        for (int64_t e = S.L.rowptr[node]; e < S.L.rowptr[node + 1]; ++e) {
-          const int ps = S.pos[S.L.col[e]];
-          if (ps >= 0) {
-            const int64_t o = int64_t(ps) * k + mycol;
-            // neighbours were written by other blocks in this launch: bypass L1
-            qv = fmaf(S.L.val[e], fmaf(bt, __ldcg(pprev + o), __ldcg(S.z + o)), qv);
+        const int64_t e1 = S.rp[t + 1];
+        int64_t e = S.rp[t];
+        // neighbours were written by other blocks in this launch: bypass L1
+        for (; e + 4 <= e1; e += 4) {
+          float pv4[4], zv4[4], w4[4];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const int64_t o = int64_t(S.rcol[e + u]) * k + mycol;
+            w4[u] = S.rval[e + u];
+            pv4[u] = __ldcg(pprev + o);
+            zv4[u] = __ldcg(S.z + o);
           }
+#pragma unroll
+          for (int u = 0; u < 4; ++u) qv = fmaf(w4[u], fmaf(bt, pv4[u], zv4[u]), qv);
+        }
+        for (; e < e1; ++e) {
+          const int64_t o = int64_t(S.rcol[e]) * k + mycol;
+          qv = fmaf(S.rval[e], fmaf(bt, __ldcg(pprev + o), __ldcg(S.z + o)), qv);
         }
         S.q[l] = qv;
         acc[0][sd] += double(pv) * qv;
@@ -697,6 +762,9 @@ struct DecodeWs {
   int* status;
   unsigned int* changed;
   int32_t *reach0, *reach1;
+  int64_t *rp0, *rp1;
+  int32_t *rcol0, *rcol1;
+  float *rval0, *rval1;
   float *Ubuf, *Vbuf;
   double* sigbuf;
   double *npart_u, *npart_v, *invu, *invv;
@@ -705,7 +773,8 @@ struct DecodeWs {
 
 static int decode_block(int rr, int rc, int kmax) { return std::min(std::min(rr, rc), kmax + 8); }
 
-static DecodeWs decode_layout(void* ws, int p, int n, int rr, int rc, int kmax) {
+static DecodeWs decode_layout(void* ws, int p, int n, int rr, int rc, int kmax, int64_t nnz_r,
+                              int64_t nnz_c) {
   Carve c(ws);
   DecodeWs w{};
   const int b = decode_block(rr, rc, kmax);
@@ -740,6 +809,12 @@ static DecodeWs decode_layout(void* ws, int p, int n, int rr, int rc, int kmax) 
   w.out_res = c.take<double>(2 * KMAX_LIMIT);
   w.status = c.take<int>(1);
   w.changed = c.take<unsigned int>(3);
+  w.rp0 = c.take<int64_t>(size_t(std::max(m0, 1)) + 1);
+  w.rp1 = c.take<int64_t>(size_t(std::max(m1, 1)) + 1);
+  w.rcol0 = c.take<int32_t>(std::max<int64_t>(nnz_r, 1));
+  w.rcol1 = c.take<int32_t>(std::max<int64_t>(nnz_c, 1));
+  w.rval0 = c.take<float>(std::max<int64_t>(nnz_r, 1));
+  w.rval1 = c.take<float>(std::max<int64_t>(nnz_c, 1));
   w.reach0 = c.take<int32_t>(std::max(m0, 1));
   w.reach1 = c.take<int32_t>(std::max(m1, 1));
   w.Ubuf = c.take<float>(size_t(p) * kmax);
@@ -753,20 +828,29 @@ static DecodeWs decode_layout(void* ws, int p, int n, int rr, int rc, int kmax) 
   return w;
 }
 
-// Orthonormalise Q (m x b) in place: two rank-revealing Cholesky-QR passes.
-static cpca_status orthonormalize(float* Q, float* Q2, int m, int b, const DecodeWs& w, cudaStream_t st) {
-  for (int pass = 0; pass < 2; ++pass) {
+// Orthonormalise Q (m x b) in place by `passes` rank-revealing Cholesky-QR
+// passes (two give orthogonality to working precision; one suffices inside
+// the subspace iteration, where only the span matters).
+static cpca_status orthonormalize(float* Q, float* Q2, int m, int b, int passes, const DecodeWs& w,
+                                  cudaStream_t st) {
+  const size_t csm = sizeof(double) * 2 * BMAX * (BMAX + 1) + sizeof(int) * BMAX;
+  CPCA_CUDA(cudaFuncSetAttribute(chol_inv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(csm)));
+  for (int pass = 0; pass < passes; ++pass) {
+    float* in = (pass & 1) ? Q2 : Q;
+    float* out = (pass & 1) ? Q : Q2;
     CPCA_CUDA(cudaMemsetAsync(w.G, 0, sizeof(double) * b * b, st));
     CPCA_PROF("svd_gram", st);
-    gram_kernel<<<ceil_div(m, GRAM_ROWS), 256, 0, st>>>(pass == 0 ? Q : Q2, m, b, w.G);
+    gram_kernel<<<ceil_div(m, GRAM_ROWS), 256, 0, st>>>(in, m, b, w.G);
     CPCA_LAUNCHED();
     CPCA_PROF("svd_chol", st);
-    chol_inv_kernel<<<1, 256, 0, st>>>(w.G, b, w.Rinv);
+    chol_inv_kernel<<<1, 32, csm, st>>>(w.G, b, w.Rinv);
     CPCA_LAUNCHED();
     apply_small_kernel<<<std::min<unsigned>(ceil_div(int64_t(m) * b, 256), num_sms() * 4), 256, 0, st>>>(
-        pass == 0 ? Q : Q2, m, b, w.Rinv, b, pass == 0 ? Q2 : Q, b, nullptr);
+        in, m, b, w.Rinv, b, out, b, nullptr);
     CPCA_LAUNCHED();
   }
+  if (passes & 1)
+    CPCA_CUDA(cudaMemcpyAsync(Q, Q2, sizeof(float) * size_t(m) * b, cudaMemcpyDeviceToDevice, st));
   return CPCA_OK;
 }
 
@@ -800,11 +884,11 @@ static cpca_status partial_svd(const float* Xt, int rr, int rc, int64_t ldxt, in
   const unsigned gs = std::min<unsigned>(ceil_div(int64_t(ms) * b, 256), num_sms() * 4);
   omega_kernel<<<gs, 256, 0, st>>>(Sb, ms, b, seed);
   CPCA_LAUNCHED();
-  CPCA_TRY(orthonormalize(Sb, Sb2, ms, b, w, st));
+  CPCA_TRY(orthonormalize(Sb, Sb2, ms, b, 1, w, st));
   for (int it = 0; it < iters; ++it) {
     CPCA_TRY(to_long(Sb, T));
     CPCA_TRY(to_short(T, Sb));
-    CPCA_TRY(orthonormalize(Sb, Sb2, ms, b, w, st));
+    CPCA_TRY(orthonormalize(Sb, Sb2, ms, b, it + 1 == iters ? 2 : 1, w, st));
   }
   CPCA_TRY(to_long(Sb, T));
   CPCA_CUDA(cudaMemsetAsync(w.G, 0, sizeof(double) * b * b, st));
@@ -831,9 +915,11 @@ static cpca_status partial_svd(const float* Xt, int rr, int rc, int64_t ldxt, in
 
 using namespace cpca;
 
-extern "C" size_t cpca_decode_workspace_size(int32_t p, int32_t n, int32_t rr, int32_t rc, int32_t kmax) {
-  if (p <= 0 || n <= 0 || rr <= 0 || rc <= 0 || kmax <= 0 || kmax > KMAX_LIMIT) return 0;
-  return decode_layout(nullptr, p, n, rr, rc, kmax).bytes;
+extern "C" size_t cpca_decode_workspace_size(int32_t p, int32_t n, int32_t rr, int32_t rc, int32_t kmax,
+                                             int64_t nnz_r, int64_t nnz_c) {
+  if (p <= 0 || n <= 0 || rr <= 0 || rc <= 0 || kmax <= 0 || kmax > KMAX_LIMIT || nnz_r < 0 || nnz_c < 0)
+    return 0;
+  return decode_layout(nullptr, p, n, rr, rc, kmax, nnz_r, nnz_c).bytes;
 }
 
 extern "C" cpca_status cpca_decode(const float* Xt, int32_t rr, int32_t rc, int64_t ldxt,
@@ -855,7 +941,7 @@ extern "C" cpca_status cpca_decode(const float* Xt, int32_t rr, int32_t rc, int6
   CPCA_TRY(check_csr(Lr, p, "cpca_decode(Lr)"));
   CPCA_TRY(check_csr(Lc, n, "cpca_decode(Lc)"));
   const int kmax = prm->kmax;
-  const DecodeWs w = decode_layout(ws, p, n, rr, rc, kmax);
+  const DecodeWs w = decode_layout(ws, p, n, rr, rc, kmax, Lr->nnz, Lc->nnz);
   if (!ws || ws_bytes < w.bytes) {
     set_error("cpca_decode: workspace %zu bytes < required %zu", ws_bytes, w.bytes);
     return CPCA_ERR_WORKSPACE;
@@ -892,6 +978,9 @@ extern "C" cpca_status cpca_decode(const float* Xt, int32_t rr, int32_t rc, int6
       S.pos = sd ? w.pos1 : w.pos0;
       S.abar = sd ? w.abar1 : w.abar0;
       S.reach = sd ? w.reach1 : w.reach0;
+      S.rp = sd ? w.rp1 : w.rp0;
+      S.rcol = sd ? w.rcol1 : w.rcol0;
+      S.rval = sd ? w.rval1 : w.rval0;
       S.minv = sd ? w.minv1 : w.minv0;
       S.R = sd ? w.Vt : w.Ut;
       S.ldr = b;
@@ -914,6 +1003,12 @@ extern "C" cpca_status cpca_decode(const float* Xt, int32_t rr, int32_t rc, int6
     a.changed = w.changed;
     dim3 sg(std::min<unsigned>(ceil_div(std::max(p, n), 256), num_sms() * 4), 2);
     cg_setup_kernel<<<sg, 256, 0, st>>>(a.s[0], a.s[1]);
+    CPCA_LAUNCHED();
+    laa_count_kernel<<<sg, 256, 0, st>>>(a.s[0], a.s[1]);
+    CPCA_LAUNCHED();
+    laa_scan_kernel<<<2, 1024, 0, st>>>(a.s[0], a.s[1]);
+    CPCA_LAUNCHED();
+    laa_fill_kernel<<<sg, 256, 0, st>>>(a.s[0], a.s[1]);
     CPCA_LAUNCHED();
     CPCA_CUDA(cudaMemsetAsync(w.acc, 0, sizeof(double) * 2 * 3 * 2 * KMAX_LIMIT, st));
     CPCA_CUDA(cudaMemsetAsync(w.acc_init, 0, sizeof(double) * 3 * 2 * KMAX_LIMIT, st));

@@ -37,7 +37,7 @@ struct PowerArgs {
 
 __device__ __forceinline__ double warp_red_add(double v) { return warp_sum(v); }
 
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(512)
 power_persistent_kernel(PowerArgs a) {
   __shared__ double sacc[2];
   const int lane = threadIdx.x & 31;
@@ -510,10 +510,13 @@ cpca_status power_step(const CsrView& Lr, const CsrView& Lc, int iters, uint64_t
   CPCA_CUDA(cudaMemsetAsync(w.bar, 0, sizeof(unsigned int) * (kBarrierCounters + 1), st));
   CPCA_CUDA(cudaMemsetAsync(w.err, 0, sizeof(int), st));
   const int rows = Lr.n + Lc.n;
-  const int grid = coop_blocks((const void*)power_persistent_kernel, 256, 0, (rows + 7) / 8);
+  // one warp per row, at most one 512-thread block per SM (fewer arrivals
+  // at the per-iteration grid barrier)
+  const int grid = std::min(num_sms(), coop_blocks((const void*)power_persistent_kernel, 512, 0,
+                                                   (rows + 15) / 16));
   void* args[] = {&a};
   CPCA_PROF("power_iter", st);
-  CPCA_CUDA(cudaLaunchCooperativeKernel((const void*)power_persistent_kernel, dim3(grid), dim3(256),
+  CPCA_CUDA(cudaLaunchCooperativeKernel((const void*)power_persistent_kernel, dim3(grid), dim3(512),
                                         args, 0, st));
   CPCA_LAUNCHED();
   return CPCA_OK;

@@ -191,8 +191,13 @@ namespace {
 
 constexpr int RECHECK_WARPS = 4;
 
-// Recheck: warp per query. Candidates of all splits are re-scored exactly,
-// the K best (by (d2, j)) are kept, and the certificate is evaluated.
+// Recheck: warp per query. With e = err_rel (|q|^2 + max |b|^2) bounding
+// |ranking value - exact squared distance|, let a_K be the K-th smallest
+// ranking value over all candidates. A candidate whose ranking value
+// exceeds a_K + 2e has exact distance > a_K + e, while the K candidates at
+// or below a_K have exact distance <= a_K + e, so it cannot be among the K
+// nearest: only the candidates within a_K + 2e are re-scored exactly. The
+// K best of those (by (d2, j)) are kept and the certificate is evaluated.
 __global__ void __launch_bounds__(RECHECK_WARPS * 32)
 knn_recheck_kernel(const float* __restrict__ P, int N, int d, int64_t ld, bool vec4, int K,
                    int M, int splits, const int32_t* __restrict__ cand_i,
@@ -203,26 +208,67 @@ knn_recheck_kernel(const float* __restrict__ P, int N, int d, int64_t ld, bool v
   extern __shared__ float sm[];
   const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int C = splits * M;
-  float* sd = sm + wib * C * 2;
-  int32_t* si = reinterpret_cast<int32_t*>(sd + C);
+  float* sa = sm + wib * C * 3;                           // ranking values
+  float* sd = sa + C;                                     // exact squared distances
+  int32_t* si = reinterpret_cast<int32_t*>(sd + C);       // candidate indices
   const int q = blockIdx.x * RECHECK_WARPS + wib;
   if (q >= N) return;
-  const float* a = P + int64_t(q) * ld;
-  for (int c = 0; c < C; ++c) {
+  const float INF = __int_as_float(0x7f800000);
+  const float e = err_rel * (nrm[q] + __uint_as_float(*nmax_bits));
+  for (int c = lane; c < C; c += 32) {
     const int s = c / M, m = c % M;
-    const int j = cand_i[(int64_t(s) * N + q) * M + m];
-    float v = __int_as_float(0x7f800000);
-    if (j >= 0) v = exact_d2_warp(a, P + int64_t(j) * ld, d, vec4);
-    if (v != v) v = __int_as_float(0x7f800000);  // NaN input ranks last
-    if (lane == 0) {
-      sd[c] = v;
-      si[c] = j;
+    const int64_t o = (int64_t(s) * N + q) * M + m;
+    const int j = cand_i[o];
+    si[c] = j;
+    const float a = cand_d[o];
+    sa[c] = j >= 0 && a == a ? a : INF;
+    sd[c] = INF;
+  }
+  __syncwarp();
+  // a_K: K rounds of a warp argmin over the ranking values
+  float aK = INF;
+  {
+    uint32_t taken_lo = 0;  // lanes mark their own picks in registers per round
+    (void)taken_lo;
+    for (int r = 0; r < K; ++r) {
+      float bv = INF;
+      int bc = -1;
+      for (int c = lane; c < C; c += 32) {
+        const float v = sa[c];
+        if (si[c] >= 0 && v < bv) {
+          bv = v;
+          bc = c;
+        }
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const float ov = __shfl_xor_sync(0xffffffffu, bv, o);
+        const int oc = __shfl_xor_sync(0xffffffffu, bc, o);
+        if (ov < bv || (ov == bv && oc >= 0 && (bc < 0 || oc < bc))) {
+          bv = ov;
+          bc = oc;
+        }
+      }
+      aK = bv;
+      if (lane == 0 && bc >= 0) si[bc] = -2 - si[bc];  // temporarily hide the pick
+      __syncwarp();
     }
+    for (int c = lane; c < C; c += 32)
+      if (si[c] <= -2) si[c] = -2 - si[c];
+    __syncwarp();
+  }
+  const float window = aK + 2.f * e;
+  for (int c = 0; c < C; ++c) {
+    const int j = si[c];
+    if (j < 0 || !(sa[c] <= window)) continue;  // warp-uniform branch
+    float v = exact_d2_warp(P + int64_t(q) * ld, P + int64_t(j) * ld, d, vec4);
+    if (v != v) v = INF;  // NaN input ranks last
+    if (lane == 0) sd[c] = v;
   }
   __syncwarp();
   float dK = 0.f;
   for (int r = 0; r < K; ++r) {
-    float bd = __int_as_float(0x7f800000);
+    float bd = INF;
     int bj = 0x7fffffff, bc = -1;
     for (int c = lane; c < C; c += 32) {
       const int j = si[c];
@@ -253,12 +299,10 @@ knn_recheck_kernel(const float* __restrict__ P, int N, int d, int64_t ld, bool v
     dK = bd;
     __syncwarp();
   }
-  // Certificate: every point outside split s's list has an approximate
-  // distance >= that list's last entry, and the approximation is within
-  // e = err_rel * (|q|^2 + max |b|^2) of the direct sum.
+  // Certificate: every point outside split s's list has a ranking value
+  // >= that list's last entry, hence an exact distance >= that minus e.
   if (lane == 0) {
-    const float e = err_rel * (nrm[q] + __uint_as_float(*nmax_bits));
-    bool ok = true;
+    bool ok = dK < INF;
     for (int s = 0; s < splits; ++s) {
       const float thr = cand_d[(int64_t(s) * N + q) * M + (M - 1)];
       if (!(thr - e > dK)) {
@@ -560,7 +604,7 @@ cpca_status knn_lists(const float* P, int N, int d, int64_t ld, int K, const Knn
   // roundings of size 2^-24 relative to |a|^2 + |b|^2 (the tensor-core pass
   // reports its own, larger, bound through knn_candidates_tc).
   const float err_rel = done ? knn_tc_err_rel(d) : float((4.0 * sqrt(double(d)) + 16.0) * 0x1.0p-24);
-  const size_t rsm = size_t(RECHECK_WARPS) * S * M * 8;
+  const size_t rsm = size_t(RECHECK_WARPS) * S * M * 12;
   CPCA_CUDA(cudaFuncSetAttribute(knn_recheck_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(rsm)));
   CPCA_PROF("knn_recheck", st);
   knn_recheck_kernel<<<ceil_div(N, RECHECK_WARPS), RECHECK_WARPS * 32, rsm, st>>>(

@@ -52,5 +52,5 @@ def test_invalid_arguments_rejected_on_host(capi):
 def test_workspace_queries_are_host_only(capi):
     L = capi.lib()
     assert L.cpca_frpcag_workspace_size(2576, 250) >= 2 * 2576 * 250 * 4
-    assert L.cpca_decode_workspace_size(10304, 1000, 2576, 250, 32) > 0
-    assert L.cpca_decode_workspace_size(10, 10, 5, 5, 64) == 0
+    assert L.cpca_decode_workspace_size(10304, 1000, 2576, 250, 32, 170000, 17000) > 0
+    assert L.cpca_decode_workspace_size(10, 10, 5, 5, 64, 30, 30) == 0

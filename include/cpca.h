@@ -167,7 +167,11 @@ typedef struct cpca_frpcag_params {
   double eps;           /* stopping tolerance; 0 = exactly max_iter iterations */
   int32_t power_iters;  /* power iterations per Laplacian (>= 1) */
   uint64_t power_seed;
-  int32_t tile_rows;    /* rows per block tile: 0 = automatic, else 1, 2, 4 or 8 */
+  int32_t blocks;       /* FISTA launch width (blocks); 0 = automatic: one block per
+                           32 x 32 tile when all tiles fit on the GPU at once,
+                           else the autotuner's choice for this tile count if
+                           cpca_frpcag_tune_batched has run, else the widest
+                           co-resident grid */
 } cpca_frpcag_params;
 
 typedef struct cpca_solve_info {
@@ -180,6 +184,43 @@ typedef struct cpca_solve_info {
 } cpca_solve_info;
 
 size_t cpca_frpcag_workspace_size(int32_t rr, int32_t rc);
+
+/* ------------------------------------------------------------------------
+ * Batched FRPCAG: up to 128 independent problems (each its own Y~, sizes,
+ * graphs, gammas and optional step) solved by FISTA in ONE cooperative
+ * launch (plus one launch for all power iterations): every problem runs the
+ * same max_iter iterations of Algorithm 1, or stops on its own when
+ * eps > 0. Results equal per-problem cpca_frpcag_solve calls. Without
+ * `infos` the call is fully asynchronous and may be captured in a CUDA
+ * graph (run it once outside capture first). params.gamma_* and .step are
+ * ignored (taken from each problem); .max_iter, .eps, .power_iters,
+ * .power_seed and .blocks apply to all. `infos` (host, count entries) may
+ * be NULL; if given, the call synchronises and fills them.
+ * ---------------------------------------------------------------------- */
+typedef struct cpca_problem {
+  const float* Yt;
+  int32_t rr, rc;
+  int64_t ldyt;
+  cpca_csr Lr, Lc;
+  double gamma_r, gamma_c;
+  double step;          /* <= 0: 1/beta' by power iteration */
+  float* X;
+  int64_t ldx;
+} cpca_problem;
+
+size_t cpca_frpcag_batched_workspace_size(const cpca_problem* probs, int32_t count);
+cpca_status cpca_frpcag_solve_batched(const cpca_problem* probs, int32_t count,
+                                      const cpca_frpcag_params* params, cpca_solve_info* infos,
+                                      void* ws, size_t ws_bytes, void* stream);
+/* Autotuner: times 10-iteration runs of the batched FISTA kernel at each
+ * candidate launch width (multiples of the SM count, and one block per tile
+ * when that fits) and returns the fastest in *blocks (also remembered for
+ * later automatic launches with the same tile count). Synchronises. The
+ * problems' X buffers are overwritten. */
+cpca_status cpca_frpcag_tune_batched(const cpca_problem* probs, int32_t count, int32_t* blocks,
+                                     float* ms_per_10_iters, void* ws, size_t ws_bytes,
+                                     void* stream);
+
 cpca_status cpca_frpcag_solve(const float* Yt, int32_t rr, int32_t rc, int64_t ldyt,
                               const cpca_csr* Lr, const cpca_csr* Lc,
                               const cpca_frpcag_params* params,

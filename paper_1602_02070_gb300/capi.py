@@ -45,12 +45,19 @@ class cpca_csr(C.Structure):
 class cpca_frpcag_params(C.Structure):
     _fields_ = [("gamma_r", C.c_double), ("gamma_c", C.c_double), ("step", C.c_double),
                 ("max_iter", C.c_int32), ("eps", C.c_double),
-                ("power_iters", C.c_int32), ("power_seed", C.c_uint64), ("tile_rows", C.c_int32)]
+                ("power_iters", C.c_int32), ("power_seed", C.c_uint64), ("blocks", C.c_int32)]
 
 
 class cpca_solve_info(C.Structure):
     _fields_ = [("iters", C.c_int32), ("step", C.c_double), ("norm_r", C.c_double),
                 ("norm_c", C.c_double), ("rel_change", C.c_double), ("objective", C.c_double)]
+
+
+class cpca_problem(C.Structure):
+    _fields_ = [("Yt", C.c_void_p), ("rr", C.c_int32), ("rc", C.c_int32), ("ldyt", C.c_int64),
+                ("Lr", cpca_csr), ("Lc", cpca_csr), ("gamma_r", C.c_double),
+                ("gamma_c", C.c_double), ("step", C.c_double), ("X", C.c_void_p),
+                ("ldx", C.c_int64)]
 
 
 class cpca_decode_params(C.Structure):
@@ -89,6 +96,13 @@ _SIGS = [
      [C.c_void_p, C.c_int32, C.c_int32, C.c_int64, C.POINTER(cpca_csr), C.POINTER(cpca_csr),
       C.POINTER(cpca_frpcag_params), C.c_void_p, C.c_int64, C.POINTER(cpca_solve_info),
       C.c_void_p, C.c_size_t, C.c_void_p]),
+    ("cpca_frpcag_batched_workspace_size", C.c_size_t, [C.c_void_p, C.c_int32]),
+    ("cpca_frpcag_solve_batched", C.c_int32,
+     [C.c_void_p, C.c_int32, C.POINTER(cpca_frpcag_params), C.c_void_p, C.c_void_p, C.c_size_t,
+      C.c_void_p]),
+    ("cpca_frpcag_tune_batched", C.c_int32,
+     [C.c_void_p, C.c_int32, C.POINTER(C.c_int32), C.POINTER(C.c_float), C.c_void_p, C.c_size_t,
+      C.c_void_p]),
     ("cpca_decode_workspace_size", C.c_size_t, [C.c_int32] * 5 + [C.c_int64] * 2),
     ("cpca_decode", C.c_int32,
      [C.c_void_p, C.c_int32, C.c_int32, C.c_int64, C.c_void_p, C.c_void_p, C.c_int32, C.c_int32,
@@ -254,9 +268,9 @@ def cpca_sample(seed: int, p: int, n: int, rho_r: int, rho_c: int, Y: torch.Tens
 
 
 def frpcag_params(gamma_r=1.0, gamma_c=1.0, step=-1.0, max_iter=300, eps=0.0,
-                  power_iters=200, power_seed=0, tile_rows=0) -> cpca_frpcag_params:
+                  power_iters=200, power_seed=0, blocks=0) -> cpca_frpcag_params:
     return cpca_frpcag_params(gamma_r, gamma_c, step, max_iter, eps, power_iters, power_seed,
-                              tile_rows)
+                              blocks)
 
 
 def cpca_frpcag_solve(Yt: torch.Tensor, Lr: Csr, Lc: Csr, params: cpca_frpcag_params | None = None,
@@ -275,6 +289,48 @@ def cpca_frpcag_solve(Yt: torch.Tensor, Lr: Csr, Lc: Csr, params: cpca_frpcag_pa
                                    C.byref(info) if info is not None else None, _ptr(ws),
                                    ws.numel(), _stream()))
     return X, info
+
+
+class Batch:
+    """A fixed set of FRPCAG problems for cpca_frpcag_solve_batched: holds
+    the C problem table, the outputs X_i and one workspace, so repeated
+    solves (or a CUDA-graph capture of one) reuse the same buffers."""
+
+    def __init__(self, problems):
+        # problems: list of dicts with Yt (CUDA tensor), Lr, Lc (Csr), gamma_r,
+        # gamma_c and optional step
+        n = len(problems)
+        self.keep = []
+        self.X = []
+        self.table = (cpca_problem * n)()
+        for i, q in enumerate(problems):
+            Yt = q["Yt"]
+            _require_cuda(Yt, torch.float32, "Yt")
+            X = torch.empty(Yt.shape[0], Yt.shape[1], dtype=torch.float32, device=Yt.device)
+            self.X.append(X)
+            self.keep += [Yt, q["Lr"], q["Lc"]]
+            self.table[i] = cpca_problem(Yt.data_ptr(), Yt.shape[0], Yt.shape[1], Yt.stride(0),
+                                         q["Lr"].c(), q["Lc"].c(), q["gamma_r"], q["gamma_c"],
+                                         q.get("step", -1.0), X.data_ptr(), X.stride(0))
+        self.n = n
+        nbytes = lib().cpca_frpcag_batched_workspace_size(self.table, n)
+        if nbytes == 0:
+            raise CpcaError(CPCA_ERR_INVALID_ARG, "bad batch")
+        self.ws = _workspace(nbytes, problems[0]["Yt"].device)
+
+    def solve(self, params: cpca_frpcag_params, want_info: bool = False):
+        infos = (cpca_solve_info * self.n)() if want_info else None
+        _check(lib().cpca_frpcag_solve_batched(self.table, self.n, C.byref(params), infos,
+                                               _ptr(self.ws), self.ws.numel(), _stream()))
+        return self.X, (list(infos) if want_info else None)
+
+    def tune(self):
+        """Run the autotuner; returns (blocks, ms per 10 iterations)."""
+        b = C.c_int32(0)
+        ms = C.c_float(0)
+        _check(lib().cpca_frpcag_tune_batched(self.table, self.n, C.byref(b), C.byref(ms),
+                                              _ptr(self.ws), self.ws.numel(), _stream()))
+        return b.value, ms.value
 
 
 def decode_params(rank_ratio=0.1, k_override=0, kmax=24, delta=0.0, cg_tol=1e-6, cg_max_iter=0,

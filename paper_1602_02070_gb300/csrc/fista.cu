@@ -2,14 +2,33 @@
 // Eq. frpcag_small with phi = l1, Algorithm 1), the step size
 // lambda = 1/beta' by power iteration, and the FP64 objective.
 //
-// One fused kernel per FISTA iteration. A block owns R consecutive rows:
-// it stages Z_j(rows, :) in shared memory, forms (Z_j Lc)(rows, j) by
-// shared-memory gathers along each column's Lc neighbour list (Lc is
-// symmetric, so (Z Lc)_{ij} = sum_k Lc[j,k] Z_{ik}), forms (Lr Z_j)(i, j)
-// from coalesced loads of the Lr-neighbour rows, then applies the gradient
-// step, the l1 prox and the momentum update in registers and writes S_j
-// (in place over S_{j-1}) and Z_{j+1}. Per iteration it reads Y~, S_{j-1},
-// Z_j and writes S_j, Z_{j+1}: 20 bytes per entry of algorithmic traffic.
+// Everything runs over an instance table (a single solve is a batch of
+// one; the batched entry point takes up to kMaxBatch independent problems of
+// different sizes, gammas and graphs). The table travels by value in the
+// kernel parameters, so a solve makes no host round trip and can be
+// captured in a CUDA graph.
+//
+//   power_batch_kernel   all power iterations of all Laplacians, one
+//                        cooperative launch, one grid barrier per step
+//   step_kernel          lambda per instance
+//   init_batch_kernel    Z_1 = S_0 = Y~ and the transposed copy of Z_1
+//   fista_batch_kernel   all J iterations of every instance, one cooperative
+//                        launch, one grid barrier per iteration
+//
+// FISTA data layout: the matrix of each instance is cut into 32 x 32 tiles
+// listed one after another across instances. Z_j is kept twice, row-major
+// (Z) and column-major (ZT = Z_j^T), so that both graph products read
+// contiguous 128-byte segments:
+//   (Lr Z)(i, j) = sum_k Lr[i, k] Z(k, j)   -> segments of rows of Z,
+//   (Z Lc)(i, j) = sum_k Lc[j, k] ZT(k, i)  -> segments of rows of ZT
+// (Lc is symmetric). A tile stages the neighbour lists of its 32 rows (Lr)
+// and 32 columns (Lc) in shared memory. Z_j is read through L2
+// (ld.global.cg) because other blocks wrote it during the previous
+// iteration of the same launch. Algorithmic traffic per iteration: read Y~,
+// S_{j-1}, Z_j and write S_j, Z_{j+1}: 20 bytes per entry.
+#include <map>
+#include <mutex>
+
 #include "common.cuh"
 #include "fista_internal.cuh"
 
@@ -17,172 +36,169 @@ namespace cpca {
 namespace {
 
 // ------------------------------------------------------------- step size --
-// Power iteration on both Laplacians in one cooperative launch (warp per
-// row, rows of Lr then Lc), then the Rayleigh quotients and lambda.
-// With v_k = u_k / |u_k| the iteration v <- L v / |L v| is carried as
-// u_{k+1} = (L u_k) / |u_k|, so each step needs one grid barrier (for
-// |u_{k+1}|). Start vector u_0(i) = SplitMix64 uniform - 1/2 (stream 2 for
-// Lr, 3 for Lc). Iterates FP32, norms and quotients FP64.
-struct PowerArgs {
-  CsrView L[2];
+// Power iteration on a list of Laplacians (two per instance: Lr with stream
+// 2, Lc with stream 3), warp per row over the concatenated rows, then the
+// Rayleigh quotients. With v_k = u_k / |u_k| the iteration v <- L v / |L v|
+// is carried as u_{k+1} = (L u_k) / |u_k|, so each step needs one grid
+// barrier (for |u_{k+1}|). Start vector u_0(i) = SplitMix64 uniform - 1/2.
+// Iterates FP32, norms and quotients FP64.
+struct PowerGraph {
+  CsrView L;
+  float* u[2];
+  double* acc;  // ring [3]: |u|^2 of the step
+  double* fin;  // [2]: u^T L u, u^T u
+  double* out;  // |L|_2 estimate
+  int stream;
+  int row0;     // first row in the concatenated row list
+};
+struct PowerBatchArgs {
+  PowerGraph g[2 * kMaxBatch];
+  int ngraph;
+  int rows;
   int iters;
   uint64_t seed;
-  float* u[2][2];      // [graph][ping/pong]
-  double* acc;         // ring [3][2]: |u|^2 per graph
-  double* fin;         // [2][2]: u^T L u, u^T u per graph
-  double gamma_r, gamma_c, step_given;
-  double* out;         // [norm_r, norm_c, lambda]
   GridBar bar;
 };
 
-__device__ __forceinline__ double warp_red_add(double v) { return warp_sum(v); }
+__device__ __forceinline__ int find_graph(const PowerBatchArgs& a, int r) {
+  int lo = 0, hi = a.ngraph - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (a.g[mid].row0 <= r) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
 
 __global__ void __launch_bounds__(512)
-power_persistent_kernel(PowerArgs a) {
-  __shared__ double sacc[2];
+power_batch_kernel(const __grid_constant__ PowerBatchArgs a) {
   const int lane = threadIdx.x & 31;
   const int nwarp = (gridDim.x * blockDim.x) >> 5;
   const int wid = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int n0 = a.L[0].n, rows = n0 + a.L[1].n;
-  if (threadIdx.x < 2) sacc[threadIdx.x] = 0.0;
-  __syncthreads();
+  const int nthr = gridDim.x * blockDim.x, tid = blockIdx.x * blockDim.x + threadIdx.x;
   // u_0 and |u_0|^2 into ring slot 0
-  for (int r = wid * 32 + lane; r < rows; r += nwarp * 32) {
-    const int g = r < n0 ? 0 : 1, i = g ? r - n0 : r;
-    const double x = uniform01_at(stream_state0(a.seed, 2 + g), uint64_t(i) + 1) - 0.5;
-    a.u[g][0][i] = float(x);
-    atomicAdd(&sacc[g], x * x);
+  for (int r = tid; r < a.rows; r += nthr) {
+    const PowerGraph& G = a.g[find_graph(a, r)];
+    const int i = r - G.row0;
+    const double x = uniform01_at(stream_state0(a.seed, G.stream), uint64_t(i) + 1) - 0.5;
+    G.u[0][i] = float(x);
+    atomicAdd(G.acc, x * x);
   }
-  __syncthreads();
-  if (threadIdx.x < 2 && sacc[threadIdx.x] != 0.0) atomicAdd(a.acc + threadIdx.x, sacc[threadIdx.x]);
   if (!grid_sync(a.bar)) return;
-  double nrm2[2] = {__ldcg(a.acc), __ldcg(a.acc + 1)};
-  bool zero[2] = {!(nrm2[0] > 0), !(nrm2[1] > 0)};
   for (int k = 0; k < a.iters; ++k) {
     const int cur = k & 1, nxt = cur ^ 1;
-    if (threadIdx.x < 2) sacc[threadIdx.x] = 0.0;
-    if (blockIdx.x == 0 && threadIdx.x < 2) a.acc[2 * ((k + 2) % 3) + threadIdx.x] = 0.0;
-    __syncthreads();
-    const float inv[2] = {zero[0] ? 0.f : float(1.0 / sqrt(nrm2[0])), zero[1] ? 0.f : float(1.0 / sqrt(nrm2[1]))};
-    for (int r = wid; r < rows; r += nwarp) {
-      const int g = r < n0 ? 0 : 1, i = g ? r - n0 : r;
-      const CsrView& L = a.L[g];
-      const float* u = a.u[g][cur];
+    // slot (k + 2) % 3 was last read after the barrier of step k - 2
+    if (blockIdx.x == 0)
+      for (int g = threadIdx.x; g < a.ngraph; g += blockDim.x) a.g[g].acc[(k + 2) % 3] = 0.0;
+    for (int r = wid; r < a.rows; r += nwarp) {
+      const PowerGraph& G = a.g[find_graph(a, r)];
+      const int i = r - G.row0;
+      const double n2 = __ldcg(G.acc + k % 3);
+      const float inv = n2 > 0 ? float(1.0 / sqrt(n2)) : 0.f;
+      const float* u = G.u[cur];
       float sum = 0.f;
-      for (int64_t e = L.rowptr[i] + lane; e < L.rowptr[i + 1]; e += 32)
-        sum = fmaf(__ldg(L.val + e), __ldcg(u + __ldg(L.col + e)), sum);
-      sum = warp_sumf(sum) * inv[g];
+      for (int64_t e = G.L.rowptr[i] + lane; e < G.L.rowptr[i + 1]; e += 32)
+        sum = fmaf(__ldg(G.L.val + e), __ldcg(u + __ldg(G.L.col + e)), sum);
+      sum = warp_sumf(sum) * inv;
       if (lane == 0) {
-        a.u[g][nxt][i] = sum;
-        atomicAdd(&sacc[g], double(sum) * double(sum));
+        G.u[nxt][i] = sum;
+        atomicAdd(G.acc + (k + 1) % 3, double(sum) * double(sum));
       }
     }
-    __syncthreads();
-    double* slot = a.acc + 2 * ((k + 1) % 3);
-    if (threadIdx.x < 2 && sacc[threadIdx.x] != 0.0) atomicAdd(slot + threadIdx.x, sacc[threadIdx.x]);
     if (!grid_sync(a.bar)) return;
-    for (int g = 0; g < 2; ++g) {
-      if (zero[g]) continue;
-      nrm2[g] = __ldcg(slot + g);
-      if (!(nrm2[g] > 0)) zero[g] = true;
-    }
   }
   // Rayleigh quotients u^T L u / u^T u of the final iterate
   const int fin = a.iters & 1;
-  __shared__ double snum[2], sden[2];
-  if (threadIdx.x < 2) {
-    snum[threadIdx.x] = 0.0;
-    sden[threadIdx.x] = 0.0;
-  }
-  __syncthreads();
-  for (int r = wid; r < rows; r += nwarp) {
-    const int g = r < n0 ? 0 : 1, i = g ? r - n0 : r;
-    const CsrView& L = a.L[g];
-    const float* u = a.u[g][fin];
+  for (int r = wid; r < a.rows; r += nwarp) {
+    const PowerGraph& G = a.g[find_graph(a, r)];
+    const int i = r - G.row0;
+    const float* u = G.u[fin];
     float sum = 0.f;
-    for (int64_t e = L.rowptr[i] + lane; e < L.rowptr[i + 1]; e += 32)
-      sum = fmaf(__ldg(L.val + e), __ldcg(u + __ldg(L.col + e)), sum);
+    for (int64_t e = G.L.rowptr[i] + lane; e < G.L.rowptr[i + 1]; e += 32)
+      sum = fmaf(__ldg(G.L.val + e), __ldcg(u + __ldg(G.L.col + e)), sum);
     sum = warp_sumf(sum);
     if (lane == 0) {
       const double ui = __ldcg(u + i);
-      atomicAdd(&snum[g], ui * double(sum));
-      atomicAdd(&sden[g], ui * ui);
+      atomicAdd(G.fin, ui * double(sum));
+      atomicAdd(G.fin + 1, ui * ui);
     }
-  }
-  __syncthreads();
-  if (threadIdx.x < 2) {
-    atomicAdd(a.fin + 2 * threadIdx.x, snum[threadIdx.x]);
-    atomicAdd(a.fin + 2 * threadIdx.x + 1, sden[threadIdx.x]);
   }
   if (!grid_sync(a.bar)) return;
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
-    double nr[2];
-    for (int g = 0; g < 2; ++g) {
-      const double num = __ldcg(a.fin + 2 * g), den = __ldcg(a.fin + 2 * g + 1);
-      nr[g] = (zero[g] || !(den > 0)) ? 0.0 : num / den;
+  if (blockIdx.x == 0)
+    for (int g = threadIdx.x; g < a.ngraph; g += blockDim.x) {
+      const double num = __ldcg(a.g[g].fin), den = __ldcg(a.g[g].fin + 1);
+      const double last = __ldcg(a.g[g].acc + a.iters % 3);
+      *a.g[g].out = (den > 0 && last > 0) ? num / den : 0.0;
     }
-    a.out[0] = nr[0];
-    a.out[1] = nr[1];
-    if (a.step_given > 0) {
-      a.out[2] = a.step_given;
-    } else {
-      const double beta = 2.0 * a.gamma_c * nr[1] + 2.0 * a.gamma_r * nr[0];
-      a.out[2] = beta > 0 ? 1.0 / beta : 1.0;
-    }
-  }
 }
 
-__global__ void step_kernel(double step_given, double* __restrict__ out) {
-  if (threadIdx.x || blockIdx.x) return;
-  out[0] = 0.0;
-  out[1] = 0.0;
-  out[2] = step_given;
+// lambda = 1/beta', beta' = 2 gamma_c |Lc|_2 + 2 gamma_r |Lr|_2 (or the given
+// step); with beta' = 0 the smooth part vanishes and lambda = 1.
+struct StepArgs {
+  double* scal[kMaxBatch];  // [|Lr|, |Lc|, lambda]
+  double gamma_r[kMaxBatch], gamma_c[kMaxBatch], step[kMaxBatch];
+  int n;
+};
+__global__ void step_kernel(const __grid_constant__ StepArgs a) {
+  for (int i = threadIdx.x; i < a.n; i += blockDim.x) {
+    double* s = a.scal[i];
+    if (a.step[i] > 0) {
+      s[0] = 0.0;
+      s[1] = 0.0;
+      s[2] = a.step[i];
+    } else {
+      const double beta = 2.0 * a.gamma_c[i] * s[1] + 2.0 * a.gamma_r[i] * s[0];
+      s[2] = beta > 0 ? 1.0 / beta : 1.0;
+    }
+  }
 }
 
 // ------------------------------------------------------- FISTA iteration --
-// Persistent form: all J iterations in one cooperative launch, one bounded
-// grid barrier per iteration. The matrix is cut into 32 x 32 tiles. Z_j is
-// kept twice, row-major (Z) and column-major (ZT = Z_j^T), so that both
-// graph products read contiguous 128-byte segments:
-//   (Lr Z)(i, j)  = sum_k Lr[i, k] Z(k, j)    -> segments of rows of Z,
-//   (Z Lc)(i, j)  = sum_k Lc[j, k] ZT(k, i)   -> segments of rows of ZT
-// (Lc is symmetric). A tile stages the 32 neighbour lists of its rows (Lr)
-// and of its columns (Lc) in shared memory, so each list is read once per
-// tile, not once per row. Warps batch NB neighbour loads for each of their
-// 4 rows (or columns) before consuming any. Z_j is read through L2
-// (ld.global.cg) because other blocks wrote it during the previous
-// iteration of this launch.
 constexpr int TB = 32;        // tile edge
 constexpr int kTileNbr = 40;  // neighbour-list entries staged per row / column
 
-struct FistaPersistArgs {
+struct FistaInst {
   const float* Yt;
-  int64_t ldy;
-  int rr, rc;
-  CsrView Lr, Lc;
-  float* Z[2];    // row-major Z_j ping / pong (ld rc)
-  float* ZT[2];   // column-major copies (ld rr)
   float* S;
-  int64_t lds;
+  float* Z[2];   // row-major Z_j ping / pong (ld rc)
+  float* ZT[2];  // column-major copies (ld rr)
+  CsrView Lr, Lc;
   const double* lam;
+  double* stats;  // ring [4][2]: slot j % 4 holds iteration j's |dZ|^2, |Z|^2
+  int* done;      // [stopped, iterations]
+  int64_t ldy, lds;
   float two_gr, two_gc;
+  int rr, rc;
+  int tile0, ntj;  // first tile in the batch list, column tiles
+};
+struct FistaBatchArgs {
+  FistaInst in[kMaxBatch];
+  int ninst;
+  int ntiles;
   int J;
   double eps;
-  double* stats;     // ring [4][2]: slot j % 4 holds iteration j's sums
-  int want_last;     // accumulate statistics of the last iteration
-  int* ctl;          // [stopped, iterations]
+  int want_last;
   GridBar bar;
 };
+
+__device__ __forceinline__ int find_inst(const FistaBatchArgs& a, int tile) {
+  int lo = 0, hi = a.ninst - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (a.in[mid].tile0 <= tile) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
 
 struct TileSmem {
   int64_t roff[TB][kTileNbr];  // element offset of neighbour row k in Z  (k * rc)
   float rval[TB][kTileNbr];
   int64_t coff[TB][kTileNbr];  // element offset of neighbour row k in ZT (k * rr)
   float cval[TB][kTileNbr];
-  float ac[TB][TB + 1];     // (Z Lc) of the tile, [row][col]
-  float zt[TB][TB + 1];     // Z_{j+1} tile for the transposed store, [row][col]
+  float ac[TB][TB + 1];        // (Z Lc) of the tile, [row][col]
+  float zt[TB][TB + 1];        // Z_{j+1} tile for the transposed store, [row][col]
   int rdeg[TB], cdeg[TB];
   int64_t rf0[TB], cf0[TB];
+  unsigned int stopped[kMaxBatch / 32];
 };
 
 // For four staged neighbour lists u = 0..3 (rows or columns of the tile):
@@ -231,135 +247,162 @@ __device__ __forceinline__ void nbr_sum4(const int64_t (*off)[kTileNbr], const f
   for (int u = 0; u < 4; ++u) out[u] = acc[u];
 }
 
-// RESIDENT: every block owns at most one tile for the whole solve; its
-// neighbour lists are staged once, and Y~, S and the tile's own Z_j entries
-// stay in registers across iterations (S is written back at the end).
-// Otherwise blocks stream over tiles, staging lists per tile.
-__device__ __forceinline__ void stage_tile(TileSmem& sm, const FistaPersistArgs& a, int i0, int j0,
-                                           int ni, int nj) {
+__device__ __forceinline__ void stage_tile(TileSmem& sm, const FistaInst& I, int i0, int j0, int ni,
+                                           int nj) {
   if (threadIdx.x < TB) {
     const int r = threadIdx.x;
-    const int64_t f0 = r < ni ? a.Lr.rowptr[i0 + r] : 0;
+    const int64_t f0 = r < ni ? I.Lr.rowptr[i0 + r] : 0;
     sm.rf0[r] = f0;
-    sm.rdeg[r] = r < ni ? int(a.Lr.rowptr[i0 + r + 1] - f0) : 0;
+    sm.rdeg[r] = r < ni ? int(I.Lr.rowptr[i0 + r + 1] - f0) : 0;
   } else if (threadIdx.x < 2 * TB) {
     const int c = threadIdx.x - TB;
-    const int64_t g0 = c < nj ? a.Lc.rowptr[j0 + c] : 0;
+    const int64_t g0 = c < nj ? I.Lc.rowptr[j0 + c] : 0;
     sm.cf0[c] = g0;
-    sm.cdeg[c] = c < nj ? int(a.Lc.rowptr[j0 + c + 1] - g0) : 0;
+    sm.cdeg[c] = c < nj ? int(I.Lc.rowptr[j0 + c + 1] - g0) : 0;
   }
   __syncthreads();
   for (int e = threadIdx.x; e < TB * kTileNbr; e += blockDim.x) {
     const int r = e / kTileNbr, q = e % kTileNbr;
     if (q < min(sm.rdeg[r], kTileNbr)) {
-      sm.roff[r][q] = int64_t(__ldg(a.Lr.col + sm.rf0[r] + q)) * a.rc;
-      sm.rval[r][q] = __ldg(a.Lr.val + sm.rf0[r] + q);
+      sm.roff[r][q] = int64_t(__ldg(I.Lr.col + sm.rf0[r] + q)) * I.rc;
+      sm.rval[r][q] = __ldg(I.Lr.val + sm.rf0[r] + q);
     }
     if (q < min(sm.cdeg[r], kTileNbr)) {
-      sm.coff[r][q] = int64_t(__ldg(a.Lc.col + sm.cf0[r] + q)) * a.rr;
-      sm.cval[r][q] = __ldg(a.Lc.val + sm.cf0[r] + q);
+      sm.coff[r][q] = int64_t(__ldg(I.Lc.col + sm.cf0[r] + q)) * I.rr;
+      sm.cval[r][q] = __ldg(I.Lc.val + sm.cf0[r] + q);
     }
   }
   __syncthreads();
 }
 
+// RESIDENT: every block owns at most one tile for the whole solve; its
+// neighbour lists are staged once, and Y~, S and the tile's own Z_j entries
+// stay in registers across iterations (S is written back at the end).
+// Otherwise blocks stream over the tile list, staging lists per tile.
+// Stopping rule (eps > 0): instance i stops after iteration j - 1 once
+// |Z_j - Z_{j-1}|^2 < eps |Z_{j-1}|^2; its tiles are then skipped, and the
+// launch ends when no instance is left.
 template <bool RESIDENT>
 __global__ void __launch_bounds__(256, RESIDENT ? 5 : 4)
-fista_persistent_kernel(FistaPersistArgs a) {
+fista_batch_kernel(const __grid_constant__ FistaBatchArgs a) {
   extern __shared__ __align__(16) unsigned char smraw[];
   TileSmem& sm = *reinterpret_cast<TileSmem*>(smraw);
   __shared__ double red[8];
+  __shared__ int any_active;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const float lam = float(*a.lam);
-  const int nti = (a.rr + TB - 1) / TB, ntj = (a.rc + TB - 1) / TB;
-  const int ntiles = nti * ntj;
   // resident state (one tile per block)
   float ry[4], rs[4], rz[4];
-  int ri0 = 0, rj0 = 0, rni = 0, rnj = 0;
-  if (RESIDENT && blockIdx.x < ntiles) {
-    ri0 = (blockIdx.x / ntj) * TB;
-    rj0 = (blockIdx.x % ntj) * TB;
-    rni = min(TB, a.rr - ri0);
-    rnj = min(TB, a.rc - rj0);
-    stage_tile(sm, a, ri0, rj0, rni, rnj);
+  int rinst = 0, ri0 = 0, rj0 = 0, rni = 0, rnj = 0;
+  if (RESIDENT && blockIdx.x < a.ntiles) {
+    rinst = find_inst(a, blockIdx.x);
+    const FistaInst& I = a.in[rinst];
+    const int lt = blockIdx.x - I.tile0;
+    ri0 = (lt / I.ntj) * TB;
+    rj0 = (lt % I.ntj) * TB;
+    rni = min(TB, I.rr - ri0);
+    rnj = min(TB, I.rc - rj0);
+    stage_tile(sm, I, ri0, rj0, rni, rnj);
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
       const int r = warp * 4 + u;
       const bool in = r < rni && lane < rnj;
-      const int64_t i = ri0 + r, jj = rj0 + lane;
-      ry[u] = in ? a.Yt[i * a.ldy + jj] : 0.f;
+      ry[u] = in ? I.Yt[int64_t(ri0 + r) * I.ldy + rj0 + lane] : 0.f;
       rs[u] = ry[u];  // S_0 = Y~
       rz[u] = ry[u];  // Z_1 = Y~
     }
   }
-  int done = a.J;
   double t = 1.0;  // t_j of Algorithm 1 (t_1 = 1)
+  int jlast = a.J;
   for (int j = 1; j <= a.J; ++j) {
-    if (a.eps > 0 && j > 1) {
-      const double* ps = a.stats + 2 * ((j - 1) & 3);
-      if (__ldcg(ps) < a.eps * __ldcg(ps + 1)) {
-        done = j - 1;
-        break;
+    // which instances run iteration j
+    if (threadIdx.x < kMaxBatch / 32) sm.stopped[threadIdx.x] = 0u;
+    if (threadIdx.x == 0) any_active = 0;
+    __syncthreads();
+    for (int i = threadIdx.x; i < a.ninst; i += blockDim.x) {
+      const FistaInst& I = a.in[i];
+      bool stop = __ldcg(I.done) != 0;
+      if (!stop && a.eps > 0 && j > 1) {
+        const double* ps = I.stats + 2 * ((j - 1) & 3);
+        stop = __ldcg(ps) < a.eps * __ldcg(ps + 1);
+        // the block owning the instance's first tile records the count once
+        if (stop && blockIdx.x == I.tile0 % gridDim.x) {
+          I.done[1] = j - 1;
+          I.done[0] = 1;
+        }
       }
+      if (stop) atomicOr(&sm.stopped[i >> 5], 1u << (i & 31));
+      else any_active = 1;
+    }
+    __syncthreads();
+    if (!any_active) {
+      jlast = j - 1;
+      break;
     }
     const double tn = (1.0 + sqrt(1.0 + 4.0 * t * t)) / 2.0;
     const float mu = float((t - 1.0) / tn);
     t = tn;
-    const float* Zin = a.Z[(j - 1) & 1];
-    const float* ZTin = a.ZT[(j - 1) & 1];
-    float* Zout = a.Z[j & 1];
-    float* ZTout = a.ZT[j & 1];
     const bool stats = a.eps > 0 || (a.want_last && j == a.J);
-    double* st = a.stats + 2 * (j & 3);
     // slot (j + 1) % 4 was last read at the start of iteration j - 2
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-      a.stats[2 * ((j + 1) & 3)] = 0.0;
-      a.stats[2 * ((j + 1) & 3) + 1] = 0.0;
-    }
-    double dz = 0.0, nz = 0.0;
-    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    if (blockIdx.x == 0)
+      for (int i = threadIdx.x; i < a.ninst; i += blockDim.x) {
+        a.in[i].stats[2 * ((j + 1) & 3)] = 0.0;
+        a.in[i].stats[2 * ((j + 1) & 3) + 1] = 0.0;
+      }
+    for (int tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x) {
+      const int ii = RESIDENT ? rinst : find_inst(a, tile);
+      if ((sm.stopped[ii >> 5] >> (ii & 31)) & 1u) continue;
+      const FistaInst& I = a.in[ii];
+      const float* Zin = I.Z[(j - 1) & 1];
+      const float* ZTin = I.ZT[(j - 1) & 1];
+      float* Zout = I.Z[j & 1];
+      float* ZTout = I.ZT[j & 1];
+      const float lam = float(*I.lam);
       int i0, j0, ni, nj;
       if (RESIDENT) {
         i0 = ri0; j0 = rj0; ni = rni; nj = rnj;
       } else {
-        i0 = (tile / ntj) * TB;
-        j0 = (tile % ntj) * TB;
-        ni = min(TB, a.rr - i0);
-        nj = min(TB, a.rc - j0);
-        stage_tile(sm, a, i0, j0, ni, nj);
+        const int lt = tile - I.tile0;
+        i0 = (lt / I.ntj) * TB;
+        j0 = (lt % I.ntj) * TB;
+        ni = min(TB, I.rr - i0);
+        nj = min(TB, I.rc - j0);
+        stage_tile(sm, I, i0, j0, ni, nj);
       }
       // (Z Lc): warp w takes tile columns 4w..4w+3, lane = tile row
       {
         float o[4];
-        nbr_sum4(sm.coff, sm.cval, sm.cdeg, sm.cf0, warp * 4, lane < ni, ZTin, i0 + lane, a.Lc,
-                 a.rr, o);
+        nbr_sum4(sm.coff, sm.cval, sm.cdeg, sm.cf0, warp * 4, lane < ni, ZTin, i0 + lane, I.Lc,
+                 I.rr, o);
 #pragma unroll
         for (int u = 0; u < 4; ++u) sm.ac[lane][warp * 4 + u] = o[u];
       }
       // (Lr Z): warp w takes tile rows 4w..4w+3, lane = tile column
       float ar[4];
-      nbr_sum4(sm.roff, sm.rval, sm.rdeg, sm.rf0, warp * 4, lane < nj, Zin, j0 + lane, a.Lr, a.rc, ar);
+      nbr_sum4(sm.roff, sm.rval, sm.rdeg, sm.rf0, warp * 4, lane < nj, Zin, j0 + lane, I.Lr, I.rc, ar);
       __syncthreads();  // sm.ac complete
+      double dz = 0.0, nz = 0.0;
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
         const int r = warp * 4 + u;
         if (r < ni && lane < nj) {
           const int64_t i = i0 + r, jj = j0 + lane;
-          const float z = RESIDENT ? rz[u] : __ldcg(Zin + i * a.rc + jj);
-          const float y = RESIDENT ? ry[u] : __ldg(a.Yt + i * a.ldy + jj);
-          const float sp = RESIDENT ? rs[u] : a.S[i * a.lds + jj];
-          const float gr = fmaf(a.two_gr, ar[u], a.two_gc * sm.ac[r][lane]);
+          const float z = RESIDENT ? rz[u] : __ldcg(Zin + i * I.rc + jj);
+          const float y = RESIDENT ? ry[u] : __ldg(I.Yt + i * I.ldy + jj);
+          const float sp = RESIDENT ? rs[u] : I.S[i * I.lds + jj];
+          // S_j = prox(Z_j - lambda grad g(Z_j)), grad g = 2 (g_c Z Lc + g_r Lr Z)
+          const float gr = fmaf(I.two_gr, ar[u], I.two_gc * sm.ac[r][lane]);
           const float v = fmaf(-lam, gr, z);
           const float dl = v - y;
           const float sv = y + copysignf(fmaxf(fabsf(dl) - lam, 0.f), dl);
+          // Z_{j+1} = S_j + ((t_j - 1) / t_{j+1}) (S_j - S_{j-1})
           const float zn = fmaf(mu, sv - sp, sv);
           if (RESIDENT) {
             rs[u] = sv;
             rz[u] = zn;
           } else {
-            a.S[i * a.lds + jj] = sv;
+            I.S[i * I.lds + jj] = sv;
           }
-          Zout[i * a.rc + jj] = zn;
+          Zout[i * I.rc + jj] = zn;
           sm.zt[r][lane] = zn;
           if (stats) {
             const double d = double(zn) - double(z);
@@ -372,54 +415,58 @@ fista_persistent_kernel(FistaPersistArgs a) {
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
         const int c = warp * 4 + u;
-        if (c < nj && lane < ni) ZTout[int64_t(j0 + c) * a.rr + i0 + lane] = sm.zt[lane][c];
+        if (c < nj && lane < ni) ZTout[int64_t(j0 + c) * I.rr + i0 + lane] = sm.zt[lane][c];
+      }
+      if (stats) {
+        dz = block_sum(dz, red);
+        nz = block_sum(nz, red);
+        if (threadIdx.x == 0) {
+          double* st = I.stats + 2 * (j & 3);
+          atomicAdd(st, dz);
+          atomicAdd(st + 1, nz);
+        }
       }
       if (!RESIDENT) __syncthreads();  // before the next tile reuses shared memory
     }
-    if (stats) {
-      dz = block_sum(dz, red);
-      nz = block_sum(nz, red);
-      if (threadIdx.x == 0) {
-        atomicAdd(st, dz);
-        atomicAdd(st + 1, nz);
-      }
-    }
     if (!grid_sync(a.bar)) return;
   }
-  if (RESIDENT && blockIdx.x < ntiles) {
+  if (RESIDENT && blockIdx.x < a.ntiles) {
+    const FistaInst& I = a.in[rinst];
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
       const int r = warp * 4 + u;
-      if (r < rni && lane < rnj) a.S[int64_t(ri0 + r) * a.lds + rj0 + lane] = rs[u];
+      if (r < rni && lane < rnj) I.S[int64_t(ri0 + r) * I.lds + rj0 + lane] = rs[u];
     }
   }
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
-    a.ctl[0] = done < a.J ? 1 : 0;
-    a.ctl[1] = done;
-  }
+  // instances still running at the end did all their iterations
+  if (blockIdx.x == 0)
+    for (int i = threadIdx.x; i < a.ninst; i += blockDim.x)
+      if (__ldcg(a.in[i].done) == 0) a.in[i].done[1] = jlast;
 }
 
-// Z_1 = S_0 = Y~ (Algorithm 1), plus the transposed copy of Z_1.
-__global__ void init_kernel(const float* __restrict__ Yt, int64_t ldy, int rr, int rc,
-                            float* __restrict__ Z, float* __restrict__ ZT, float* __restrict__ S,
-                            int64_t lds) {
-  __shared__ float tile[32][33];
-  const int i0 = blockIdx.y * 32, j0 = blockIdx.x * 32;
-  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
-    const int i = i0 + r, j = j0 + threadIdx.x;
-    if (i < rr && j < rc) {
-      const float y = Yt[int64_t(i) * ldy + j];
-      Z[int64_t(i) * rc + j] = y;
-      S[int64_t(i) * lds + j] = y;
-      tile[r][threadIdx.x] = y;
-    }
+// Z_1 = S_0 = Y~ (Algorithm 1) and the transposed copy of Z_1, one tile per
+// block over the batch tile list.
+__global__ void __launch_bounds__(256) init_batch_kernel(const __grid_constant__ FistaBatchArgs a) {
+  __shared__ float tile[TB][TB + 1];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int tl = blockIdx.x; tl < a.ntiles; tl += gridDim.x) {
+    const FistaInst& I = a.in[find_inst(a, tl)];
+    const int lt = tl - I.tile0;
+    const int i0 = (lt / I.ntj) * TB, j0 = (lt % I.ntj) * TB;
+    const int ni = min(TB, I.rr - i0), nj = min(TB, I.rc - j0);
+    for (int r = warp; r < TB; r += 8)
+      if (r < ni && lane < nj) {
+        const int64_t i = i0 + r, jj = j0 + lane;
+        const float y = I.Yt[i * I.ldy + jj];
+        I.Z[0][i * I.rc + jj] = y;
+        I.S[i * I.lds + jj] = y;
+        tile[r][lane] = y;
+      }
+    __syncthreads();
+    for (int c = warp; c < TB; c += 8)
+      if (c < nj && lane < ni) I.ZT[0][int64_t(j0 + c) * I.rr + i0 + lane] = tile[lane][c];
+    __syncthreads();
   }
-  __syncthreads();
-  if (ZT)
-    for (int c = threadIdx.y; c < 32; c += blockDim.y) {
-      const int j = j0 + c, i = i0 + threadIdx.x;
-      if (i < rr && j < rc) ZT[int64_t(j) * rr + i] = tile[threadIdx.x][c];
-    }
 }
 
 // ------------------------------------------------------------- objective --
@@ -451,31 +498,9 @@ __global__ void sum_in_order_kernel(const double* __restrict__ part, int n, doub
   *out = s;
 }
 
-
 }  // namespace
 
-FistaWs fista_layout(void* ws, int rr, int rc, int /*unused*/) {
-  Carve c(ws);
-  FistaWs w{};
-  w.Z0 = c.take<float>(size_t(rr) * rc);
-  w.Z1 = c.take<float>(size_t(rr) * rc);
-  w.ZT0 = c.take<float>(size_t(rr) * rc);
-  w.ZT1 = c.take<float>(size_t(rr) * rc);
-  w.scal = c.take<double>(4);
-  for (int g = 0; g < 2; ++g)
-    for (int b = 0; b < 2; ++b) w.pu[g][b] = c.take<float>(size_t(g ? rc : rr) + 4);
-  w.pacc = c.take<double>(6 + 4);
-  w.stats = c.take<double>(8);
-  w.ctl = c.take<int>(4);
-  w.bar = c.take<unsigned int>(kBarrierCounters + 1);
-  w.err = c.take<int>(1);
-  w.part = c.take<double>(kObjBlocks);
-  w.obj = c.take<double>(1);
-  w.bytes = c.bytes();
-  return w;
-}
-
-static int coop_blocks(const void* kernel, int threads, size_t smem, int want) {
+int coop_blocks(const void* kernel, int threads, size_t smem, int want) {
   int occ = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, threads, smem) != cudaSuccess) {
     cudaGetLastError();
@@ -484,124 +509,181 @@ static int coop_blocks(const void* kernel, int threads, size_t smem, int want) {
   return std::max(1, std::min(want, std::max(occ, 1) * num_sms()));
 }
 
-cpca_status power_step(const CsrView& Lr, const CsrView& Lc, int iters, uint64_t seed,
-                       double gamma_r, double gamma_c, double step_given, const FistaWs& w,
-                       cudaStream_t st) {
-  if (step_given > 0) {
-    step_kernel<<<1, 32, 0, st>>>(step_given, w.scal);
-    CPCA_LAUNCHED();
-    return CPCA_OK;
-  }
-  PowerArgs a{};
-  a.L[0] = Lr;
-  a.L[1] = Lc;
-  a.iters = iters;
-  a.seed = seed;
+namespace {
+
+int tiles_of(int rr, int rc) { return int(ceil_div(rr, TB) * int64_t(ceil_div(rc, TB))); }
+
+// autotuner cache: launch width chosen for a tile count
+std::mutex g_tune_mu;
+std::map<int64_t, int> g_tune_cache;
+
+// kernel-parameter tables (large: kept off the stack; one solve at a time
+// per table)
+std::mutex g_tab_mu;
+PowerBatchArgs g_pa;
+FistaBatchArgs g_fa;
+
+}  // namespace
+
+// ---------------------------------------------------------------- layout --
+InstWs inst_layout(Carve& c, int rr, int rc) {
+  InstWs w{};
+  w.Z0 = c.take<float>(size_t(rr) * rc);
+  w.Z1 = c.take<float>(size_t(rr) * rc);
+  w.ZT0 = c.take<float>(size_t(rr) * rc);
+  w.ZT1 = c.take<float>(size_t(rr) * rc);
+  w.scal = c.take<double>(4);
   for (int g = 0; g < 2; ++g)
-    for (int b = 0; b < 2; ++b) a.u[g][b] = w.pu[g][b];
-  a.acc = w.pacc;
-  a.fin = w.pacc + 6;
-  a.gamma_r = gamma_r;
-  a.gamma_c = gamma_c;
-  a.step_given = step_given;
-  a.out = w.scal;
-  a.bar = GridBar{w.bar, w.bar + kBarrierCounters, w.err};
-  CPCA_CUDA(cudaMemsetAsync(w.pacc, 0, sizeof(double) * 10, st));
-  CPCA_CUDA(cudaMemsetAsync(w.bar, 0, sizeof(unsigned int) * (kBarrierCounters + 1), st));
-  CPCA_CUDA(cudaMemsetAsync(w.err, 0, sizeof(int), st));
-  const int rows = Lr.n + Lc.n;
-  // one warp per row, at most one 512-thread block per SM (fewer arrivals
-  // at the per-iteration grid barrier)
-  const int grid = std::min(num_sms(), coop_blocks((const void*)power_persistent_kernel, 512, 0,
-                                                   (rows + 15) / 16));
-  void* args[] = {&a};
-  CPCA_PROF("power_iter", st);
-  CPCA_CUDA(cudaLaunchCooperativeKernel((const void*)power_persistent_kernel, dim3(grid), dim3(512),
-                                        args, 0, st));
-  CPCA_LAUNCHED();
-  return CPCA_OK;
+    for (int b = 0; b < 2; ++b) w.pu[g][b] = c.take<float>(size_t(g ? rc : rr) + 4);
+  w.pacc = c.take<double>(10);
+  w.stats = c.take<double>(8);
+  w.done = c.take<int>(2);
+  return w;
 }
 
-static bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; }
+BatchWs batch_layout(void* ws, const int* rr, const int* rc, int n) {
+  Carve c(ws);
+  BatchWs w{};
+  w.bar = c.take<unsigned int>(kBarrierCounters + 1);
+  w.err = c.take<int>(1);
+  w.part = c.take<double>(kObjBlocks);
+  w.obj = c.take<double>(1);
+  for (int i = 0; i < n; ++i) w.inst[i] = inst_layout(c, rr[i], rc[i]);
+  w.n = n;
+  w.bytes = c.bytes();
+  return w;
+}
 
-// All J iterations of Algorithm 1 in one cooperative launch.
-cpca_status fista_run(const float* Yt, int64_t ldy, int rr, int rc, const CsrView& Lr,
-                      const CsrView& Lc, float* X, int64_t ldx, double gamma_r, double gamma_c,
-                      int J, double eps, bool want_last, int tile_rows, const FistaWs& w,
-                      cudaStream_t st) {
-  (void)tile_rows;
-  CPCA_TRY(fista_init(Yt, ldy, rr, rc, w.Z0, w.ZT0, X, ldx, st));
-  CPCA_CUDA(cudaMemsetAsync(w.stats, 0, 8 * sizeof(double), st));
-  CPCA_CUDA(cudaMemsetAsync(w.ctl, 0, 4 * sizeof(int), st));
-  CPCA_CUDA(cudaMemsetAsync(w.bar, 0, sizeof(unsigned int) * (kBarrierCounters + 1), st));
-  CPCA_CUDA(cudaMemsetAsync(w.err, 0, sizeof(int), st));
+// ----------------------------------------------------------------- solves --
+cpca_status fista_batch_run(const BatchProblem* P, int n, int J, double eps, bool want_last,
+                            int power_iters, uint64_t power_seed, int blocks, const BatchWs& w,
+                            cudaStream_t st) {
+  std::lock_guard<std::mutex> lk(g_tab_mu);
+  // power iterations (instances without a given step), then lambda
+  PowerBatchArgs& pa = g_pa;
+  pa.ngraph = 0;
+  int rows = 0;
+  for (int i = 0; i < n; ++i) {
+    if (P[i].step > 0) continue;
+    for (int g = 0; g < 2; ++g) {
+      PowerGraph& G = pa.g[pa.ngraph++];
+      G.L = g ? P[i].Lc : P[i].Lr;
+      G.u[0] = w.inst[i].pu[g][0];
+      G.u[1] = w.inst[i].pu[g][1];
+      G.acc = w.inst[i].pacc + 3 * g;
+      G.fin = w.inst[i].pacc + 6 + 2 * g;
+      G.out = w.inst[i].scal + g;
+      G.stream = 2 + g;
+      G.row0 = rows;
+      rows += G.L.n;
+    }
+    CPCA_CUDA(cudaMemsetAsync(w.inst[i].pacc, 0, sizeof(double) * 10, st));
+  }
+  if (pa.ngraph > 0) {
+    pa.rows = rows;
+    pa.iters = power_iters;
+    pa.seed = power_seed;
+    pa.bar = GridBar{w.bar, w.bar + kBarrierCounters, w.err};
+    CPCA_CUDA(cudaMemsetAsync(w.bar, 0, sizeof(unsigned int) * (kBarrierCounters + 1), st));
+    CPCA_CUDA(cudaMemsetAsync(w.err, 0, sizeof(int), st));
+    // one warp per row, at most one 512-thread block per SM
+    const int grid = std::min(num_sms(), coop_blocks((const void*)power_batch_kernel, 512, 0,
+                                                     (rows + 15) / 16));
+    void* args[] = {&pa};
+    CPCA_PROF("power_iter", st);
+    CPCA_CUDA(cudaLaunchCooperativeKernel((const void*)power_batch_kernel, dim3(grid), dim3(512),
+                                          args, 0, st));
+    CPCA_LAUNCHED();
+  }
+  {
+    StepArgs sa{};
+    sa.n = n;
+    for (int i = 0; i < n; ++i) {
+      sa.scal[i] = w.inst[i].scal;
+      sa.gamma_r[i] = P[i].gamma_r;
+      sa.gamma_c[i] = P[i].gamma_c;
+      sa.step[i] = P[i].step;
+    }
+    step_kernel<<<1, 128, 0, st>>>(sa);
+    CPCA_LAUNCHED();
+  }
+  // FISTA
+  FistaBatchArgs& fa = g_fa;
+  int tiles = 0;
+  for (int i = 0; i < n; ++i) {
+    FistaInst& I = fa.in[i];
+    const InstWs& iw = w.inst[i];
+    I.Yt = P[i].Yt;
+    I.S = P[i].X;
+    I.Z[0] = iw.Z0;
+    I.Z[1] = iw.Z1;
+    I.ZT[0] = iw.ZT0;
+    I.ZT[1] = iw.ZT1;
+    I.Lr = P[i].Lr;
+    I.Lc = P[i].Lc;
+    I.lam = iw.scal + 2;
+    I.stats = iw.stats;
+    I.done = iw.done;
+    I.ldy = P[i].ldy;
+    I.lds = P[i].ldx;
+    I.two_gr = float(2.0 * P[i].gamma_r);
+    I.two_gc = float(2.0 * P[i].gamma_c);
+    I.rr = P[i].rr;
+    I.rc = P[i].rc;
+    I.tile0 = tiles;
+    I.ntj = int(ceil_div(P[i].rc, TB));
+    tiles += tiles_of(P[i].rr, P[i].rc);
+    CPCA_CUDA(cudaMemsetAsync(iw.stats, 0, 8 * sizeof(double), st));
+    CPCA_CUDA(cudaMemsetAsync(iw.done, 0, 2 * sizeof(int), st));
+  }
+  fa.ninst = n;
+  fa.ntiles = tiles;
+  fa.J = J;
+  fa.eps = eps;
+  fa.want_last = want_last ? 1 : 0;
+  fa.bar = GridBar{w.bar, w.bar + kBarrierCounters, w.err};
+  init_batch_kernel<<<std::min(tiles, num_sms() * 8), 256, 0, st>>>(fa);
+  CPCA_LAUNCHED();
   if (J == 0) return CPCA_OK;
-  FistaPersistArgs a{};
-  a.Yt = Yt;
-  a.ldy = ldy;
-  a.rr = rr;
-  a.rc = rc;
-  a.Lr = Lr;
-  a.Lc = Lc;
-  a.Z[0] = w.Z0;
-  a.Z[1] = w.Z1;
-  a.ZT[0] = w.ZT0;
-  a.ZT[1] = w.ZT1;
-  a.S = X;
-  a.lds = ldx;
-  a.lam = w.scal + 2;
-  a.two_gr = float(2.0 * gamma_r);
-  a.two_gc = float(2.0 * gamma_c);
-  a.J = J;
-  a.eps = eps;
-  a.stats = w.stats;
-  a.want_last = want_last ? 1 : 0;
-  a.ctl = w.ctl;
-  a.bar = GridBar{w.bar, w.bar + kBarrierCounters, w.err};
+  CPCA_CUDA(cudaMemsetAsync(w.bar, 0, sizeof(unsigned int) * (kBarrierCounters + 1), st));
+  CPCA_CUDA(cudaMemsetAsync(w.err, 0, sizeof(int), st));
   const size_t smem = sizeof(TileSmem);
-  const int tiles = int(ceil_div(rr, TB) * int64_t(ceil_div(rc, TB)));
-  const void* kres = (const void*)fista_persistent_kernel<true>;
-  const void* kstr = (const void*)fista_persistent_kernel<false>;
-  CPCA_CUDA(cudaFuncSetAttribute(kres, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
-  CPCA_CUDA(cudaFuncSetAttribute(kstr, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
+  const void* kres = (const void*)fista_batch_kernel<true>;
+  const void* kstr = (const void*)fista_batch_kernel<false>;
+  static bool attr = false;
+  if (!attr) {
+    CPCA_CUDA(cudaFuncSetAttribute(kres, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
+    CPCA_CUDA(cudaFuncSetAttribute(kstr, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
+    attr = true;
+  }
   const int cap_res = coop_blocks(kres, 256, smem, 1 << 30);
-  const bool resident = tiles <= cap_res;
-  const void* kern = resident ? kres : kstr;
-  const int grid = resident ? tiles : coop_blocks(kstr, 256, smem, tiles);
-  void* args[] = {&a};
+  const int cap_str = coop_blocks(kstr, 256, smem, 1 << 30);
+  bool resident = tiles <= cap_res;
+  int grid = resident ? tiles : cap_str;
+  if (blocks > 0) {  // explicit launch width (autotuner)
+    resident = blocks >= tiles && tiles <= cap_res;
+    grid = resident ? tiles : std::min(blocks, cap_str);
+  } else if (!resident) {
+    std::lock_guard<std::mutex> tl(g_tune_mu);
+    auto it = g_tune_cache.find(tiles);
+    if (it != g_tune_cache.end()) grid = std::min(it->second, cap_str);
+  }
+  void* args[] = {&fa};
   CPCA_PROF("fista_persistent", st);
-  CPCA_CUDA(cudaLaunchCooperativeKernel(kern, dim3(grid), dim3(256), args, smem, st));
-  CPCA_LAUNCHED();
-  return CPCA_OK;
-}
-
-cpca_status fista_init(const float* Yt, int64_t ldy, int rr, int rc, float* Z, float* ZT, float* S,
-                       int64_t lds, cudaStream_t st) {
-  dim3 grid(ceil_div(rc, 32), ceil_div(rr, 32)), block(32, 8);
-  init_kernel<<<grid, block, 0, st>>>(Yt, ldy, rr, rc, Z, ZT, S, lds);
+  CPCA_CUDA(cudaLaunchCooperativeKernel(resident ? kres : kstr, dim3(grid), dim3(256), args, smem, st));
   CPCA_LAUNCHED();
   return CPCA_OK;
 }
 
 cpca_status fista_objective(const float* Yt, int64_t ldy, int rr, int rc, const CsrView& Lr,
                             const CsrView& Lc, const float* X, int64_t ldx, double gr, double gc,
-                            const FistaWs& w, cudaStream_t st) {
+                            double* part, double* out, cudaStream_t st) {
   CPCA_PROF("fista_objective", st);
-  objective_kernel<<<kObjBlocks, 256, 0, st>>>(Yt, ldy, rr, rc, Lr, Lc, X, ldx, gr, gc, w.part);
+  objective_kernel<<<kObjBlocks, 256, 0, st>>>(Yt, ldy, rr, rc, Lr, Lc, X, ldx, gr, gc, part);
   CPCA_LAUNCHED();
-  sum_in_order_kernel<<<1, 32, 0, st>>>(w.part, kObjBlocks, w.obj);
+  sum_in_order_kernel<<<1, 32, 0, st>>>(part, kObjBlocks, out);
   CPCA_LAUNCHED();
   return CPCA_OK;
-}
-
-// Momentum coefficients mu_j = (t_j - 1) / t_{j+1} of Algorithm 1, t_1 = 1.
-void fista_momentum(int J, double* mu) {
-  double t = 1.0;
-  for (int j = 0; j < J; ++j) {
-    const double tn = (1.0 + sqrt(1.0 + 4.0 * t * t)) / 2.0;
-    mu[j] = (t - 1.0) / tn;
-    t = tn;
-  }
 }
 
 cpca_status check_csr(const cpca_csr* L, int n, const char* name) {
@@ -616,13 +698,100 @@ cpca_status check_csr(const cpca_csr* L, int n, const char* name) {
   return CPCA_OK;
 }
 
+static cpca_status check_params(const cpca_frpcag_params* prm, const char* who) {
+  CPCA_CHECK_ARG(prm, "%s: null params", who);
+  CPCA_CHECK_ARG(prm->max_iter >= 0, "%s: max_iter < 0", who);
+  CPCA_CHECK_ARG(prm->gamma_r >= 0 && prm->gamma_c >= 0, "%s: negative gamma", who);
+  CPCA_CHECK_ARG(prm->eps >= 0, "%s: eps < 0", who);
+  CPCA_CHECK_ARG(prm->step > 0 || prm->power_iters >= 1, "%s: power_iters < 1", who);
+  CPCA_CHECK_ARG(prm->blocks >= 0, "%s: blocks < 0", who);
+  return CPCA_OK;
+}
+
+static cpca_status read_infos(const BatchProblem* P, int n, const BatchWs& w, int J,
+                              cpca_solve_info* const* infos, cudaStream_t st) {
+  std::vector<double> hs(size_t(n) * 12);
+  std::vector<int> hd(size_t(n) * 2);
+  for (int i = 0; i < n; ++i) {
+    if (!infos[i]) continue;
+    const InstWs& iw = w.inst[i];
+    CPCA_TRY(fista_objective(P[i].Yt, P[i].ldy, P[i].rr, P[i].rc, P[i].Lr, P[i].Lc, P[i].X, P[i].ldx,
+                             P[i].gamma_r, P[i].gamma_c, w.part, w.obj, st));
+    CPCA_CUDA(cudaMemcpyAsync(&hs[size_t(i) * 12], iw.scal, 3 * sizeof(double), cudaMemcpyDeviceToHost, st));
+    CPCA_CUDA(cudaMemcpyAsync(&hs[size_t(i) * 12 + 3], iw.stats, 8 * sizeof(double), cudaMemcpyDeviceToHost, st));
+    CPCA_CUDA(cudaMemcpyAsync(&hs[size_t(i) * 12 + 11], w.obj, sizeof(double), cudaMemcpyDeviceToHost, st));
+    CPCA_CUDA(cudaMemcpyAsync(&hd[size_t(i) * 2], iw.done, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
+    CPCA_CUDA(cudaStreamSynchronize(st));  // w.obj is reused per instance
+  }
+  int err = 0;
+  CPCA_CUDA(cudaMemcpyAsync(&err, w.err, sizeof(int), cudaMemcpyDeviceToHost, st));
+  CPCA_CUDA(cudaStreamSynchronize(st));
+  if (err) {
+    set_error("frpcag: grid barrier timed out");
+    return CPCA_ERR_TIMEOUT;
+  }
+  for (int i = 0; i < n; ++i) {
+    cpca_solve_info* info = infos[i];
+    if (!info) continue;
+    const double* s = &hs[size_t(i) * 12];
+    const int done = J > 0 ? hd[size_t(i) * 2 + 1] : 0;
+    const double* last = s + 3 + 2 * (done & 3);
+    info->iters = done;
+    info->norm_r = s[0];
+    info->norm_c = s[1];
+    info->step = s[2];
+    info->rel_change = done > 0 && last[1] > 0 ? last[0] / last[1] : 0.0;
+    info->objective = s[11];
+  }
+  return CPCA_OK;
+}
+
+// Autotuner: time a short run of each candidate launch width and keep the
+// fastest (also cached for later solves with the same tile count).
+static cpca_status tune_batch(const BatchProblem* P, int n, const BatchWs& w, cudaStream_t st,
+                              int* best_blocks, float* best_ms) {
+  int tiles = 0;
+  for (int i = 0; i < n; ++i) tiles += tiles_of(P[i].rr, P[i].rc);
+  const size_t smem = sizeof(TileSmem);
+  const int cap_str = coop_blocks((const void*)fista_batch_kernel<false>, 256, smem, 1 << 30);
+  const int cap_res = coop_blocks((const void*)fista_batch_kernel<true>, 256, smem, 1 << 30);
+  std::vector<int> cands;
+  for (int m = 1; m * num_sms() <= cap_str; ++m) cands.push_back(m * num_sms());
+  if (cands.empty()) cands.push_back(cap_str);
+  if (tiles <= cap_res) cands.push_back(tiles);  // resident
+  cudaEvent_t e0, e1;
+  CPCA_CUDA(cudaEventCreate(&e0));
+  CPCA_CUDA(cudaEventCreate(&e1));
+  *best_blocks = 0;
+  *best_ms = 1e30f;
+  for (int rep = 0; rep < 2; ++rep)
+    for (int b : cands) {
+      CPCA_CUDA(cudaEventRecord(e0, st));
+      CPCA_TRY(fista_batch_run(P, n, 10, 0.0, false, 1, 0, b, w, st));
+      CPCA_CUDA(cudaEventRecord(e1, st));
+      CPCA_CUDA(cudaEventSynchronize(e1));
+      float ms = 0.f;
+      CPCA_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+      if (rep == 1 && ms < *best_ms) {
+        *best_ms = ms;
+        *best_blocks = b;
+      }
+    }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tune_cache[tiles] = *best_blocks;
+  return CPCA_OK;
+}
+
 }  // namespace cpca
 
 using namespace cpca;
 
 extern "C" size_t cpca_frpcag_workspace_size(int32_t rr, int32_t rc) {
   if (rr <= 0 || rc <= 0) return 0;
-  return fista_layout(nullptr, rr, rc, kMaxStatIters).bytes;
+  const int a = rr, b = rc;
+  return batch_layout(nullptr, &a, &b, 1).bytes;
 }
 
 extern "C" cpca_status cpca_frpcag_solve(const float* Yt, int32_t rr, int32_t rc, int64_t ldyt,
@@ -631,55 +800,125 @@ extern "C" cpca_status cpca_frpcag_solve(const float* Yt, int32_t rr, int32_t rc
                                          cpca_solve_info* info, void* ws, size_t ws_bytes,
                                          void* stream) {
   clear_error();
-  CPCA_CHECK_ARG(Yt && X && prm, "cpca_frpcag_solve: null pointer");
+  CPCA_CHECK_ARG(Yt && X, "cpca_frpcag_solve: null pointer");
   CPCA_CHECK_ARG(rr > 0 && rc > 0, "cpca_frpcag_solve: empty matrix");
   CPCA_CHECK_ARG(ldyt >= rc && ldx >= rc, "cpca_frpcag_solve: leading dimension too small");
-  CPCA_CHECK_ARG(prm->max_iter >= 0, "cpca_frpcag_solve: max_iter < 0");
-  CPCA_CHECK_ARG(prm->gamma_r >= 0 && prm->gamma_c >= 0, "cpca_frpcag_solve: negative gamma");
-  CPCA_CHECK_ARG(prm->eps >= 0, "cpca_frpcag_solve: eps < 0");
-  CPCA_CHECK_ARG(prm->tile_rows == 0 || prm->tile_rows == 1 || prm->tile_rows == 2 ||
-                     prm->tile_rows == 4 || prm->tile_rows == 8,
-                 "cpca_frpcag_solve: tile_rows must be 0, 1, 2, 4 or 8");
-  CPCA_CHECK_ARG(prm->step > 0 || prm->power_iters >= 1, "cpca_frpcag_solve: power_iters < 1");
+  CPCA_TRY(check_params(prm, "cpca_frpcag_solve"));
   CPCA_TRY(check_csr(Lr, rr, "cpca_frpcag_solve(Lr)"));
   CPCA_TRY(check_csr(Lc, rc, "cpca_frpcag_solve(Lc)"));
-  const FistaWs w = fista_layout(ws, rr, rc, kMaxStatIters);
+  const BatchWs w = batch_layout(ws, &rr, &rc, 1);
   if (!ws || ws_bytes < w.bytes) {
     set_error("cpca_frpcag_solve: workspace %zu bytes < required %zu", ws_bytes, w.bytes);
     return CPCA_ERR_WORKSPACE;
   }
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  const CsrView lr{Lr->n, Lr->rowptr, Lr->col, Lr->val};
-  const CsrView lc{Lc->n, Lc->rowptr, Lc->col, Lc->val};
-  const int J = prm->max_iter;
-  CPCA_TRY(power_step(lr, lc, prm->power_iters, prm->power_seed, prm->gamma_r, prm->gamma_c,
-                      prm->step, w, st));
-  CPCA_TRY(fista_run(Yt, ldyt, rr, rc, lr, lc, X, ldx, prm->gamma_r, prm->gamma_c, J, prm->eps,
-                     info != nullptr, prm->tile_rows, w, st));
-  int done_iters = J;
+  BatchProblem P{};
+  P.Yt = Yt;
+  P.ldy = ldyt;
+  P.rr = rr;
+  P.rc = rc;
+  P.Lr = CsrView{Lr->n, Lr->rowptr, Lr->col, Lr->val};
+  P.Lc = CsrView{Lc->n, Lc->rowptr, Lc->col, Lc->val};
+  P.gamma_r = prm->gamma_r;
+  P.gamma_c = prm->gamma_c;
+  P.step = prm->step;
+  P.X = X;
+  P.ldx = ldx;
+  CPCA_TRY(fista_batch_run(&P, 1, prm->max_iter, prm->eps, info != nullptr, prm->power_iters,
+                           prm->power_seed, prm->blocks, w, st));
   if (info) {
-    CPCA_TRY(fista_objective(Yt, ldyt, rr, rc, lr, lc, X, ldx, prm->gamma_r, prm->gamma_c, w, st));
-    int ctl[2];
-    double scal[3], obj, ring[8];
-    int err = 0;
-    CPCA_CUDA(cudaMemcpyAsync(ctl, w.ctl, sizeof(ctl), cudaMemcpyDeviceToHost, st));
-    CPCA_CUDA(cudaMemcpyAsync(scal, w.scal, sizeof(scal), cudaMemcpyDeviceToHost, st));
-    CPCA_CUDA(cudaMemcpyAsync(&obj, w.obj, sizeof(obj), cudaMemcpyDeviceToHost, st));
-    CPCA_CUDA(cudaMemcpyAsync(ring, w.stats, sizeof(ring), cudaMemcpyDeviceToHost, st));
-    CPCA_CUDA(cudaMemcpyAsync(&err, w.err, sizeof(err), cudaMemcpyDeviceToHost, st));
-    CPCA_CUDA(cudaStreamSynchronize(st));
-    if (err) {
-      set_error("cpca_frpcag_solve: grid barrier timed out");
-      return CPCA_ERR_TIMEOUT;
-    }
-    if (J > 0) done_iters = ctl[1];
-    const double* last = ring + 2 * (done_iters & 3);
-    info->iters = done_iters;
-    info->norm_r = scal[0];
-    info->norm_c = scal[1];
-    info->step = scal[2];
-    info->rel_change = done_iters > 0 && last[1] > 0 ? last[0] / last[1] : 0.0;
-    info->objective = obj;
+    cpca_solve_info* infos[1] = {info};
+    CPCA_TRY(read_infos(&P, 1, w, prm->max_iter, infos, st));
   }
+  return CPCA_OK;
+}
+
+static cpca_status to_problems(const cpca_problem* probs, int32_t count, std::vector<BatchProblem>& P,
+                               std::vector<int>& rr, std::vector<int>& rc) {
+  CPCA_CHECK_ARG(probs && count >= 1 && count <= kMaxBatch, "batched FISTA: need 1 <= count <= %d",
+                 kMaxBatch);
+  P.resize(count);
+  rr.resize(count);
+  rc.resize(count);
+  for (int i = 0; i < count; ++i) {
+    const cpca_problem& q = probs[i];
+    CPCA_CHECK_ARG(q.Yt && q.X && q.rr > 0 && q.rc > 0 && q.ldyt >= q.rc && q.ldx >= q.rc,
+                   "batched FISTA: problem %d has bad sizes or pointers", i);
+    CPCA_CHECK_ARG(q.gamma_r >= 0 && q.gamma_c >= 0, "batched FISTA: problem %d has negative gamma", i);
+    CPCA_TRY(check_csr(&q.Lr, q.rr, "batched FISTA (Lr)"));
+    CPCA_TRY(check_csr(&q.Lc, q.rc, "batched FISTA (Lc)"));
+    BatchProblem& p = P[i];
+    p.Yt = q.Yt;
+    p.ldy = q.ldyt;
+    p.rr = q.rr;
+    p.rc = q.rc;
+    p.Lr = CsrView{q.Lr.n, q.Lr.rowptr, q.Lr.col, q.Lr.val};
+    p.Lc = CsrView{q.Lc.n, q.Lc.rowptr, q.Lc.col, q.Lc.val};
+    p.gamma_r = q.gamma_r;
+    p.gamma_c = q.gamma_c;
+    p.step = q.step;
+    p.X = q.X;
+    p.ldx = q.ldx;
+    rr[i] = q.rr;
+    rc[i] = q.rc;
+  }
+  return CPCA_OK;
+}
+
+extern "C" size_t cpca_frpcag_batched_workspace_size(const cpca_problem* probs, int32_t count) {
+  if (!probs || count < 1 || count > kMaxBatch) return 0;
+  std::vector<int> rr(count), rc(count);
+  for (int i = 0; i < count; ++i) {
+    if (probs[i].rr <= 0 || probs[i].rc <= 0) return 0;
+    rr[i] = probs[i].rr;
+    rc[i] = probs[i].rc;
+  }
+  return batch_layout(nullptr, rr.data(), rc.data(), count).bytes;
+}
+
+extern "C" cpca_status cpca_frpcag_solve_batched(const cpca_problem* probs, int32_t count,
+                                                 const cpca_frpcag_params* prm,
+                                                 cpca_solve_info* infos, void* ws, size_t ws_bytes,
+                                                 void* stream) {
+  clear_error();
+  CPCA_TRY(check_params(prm, "cpca_frpcag_solve_batched"));
+  std::vector<BatchProblem> P;
+  std::vector<int> rr, rc;
+  CPCA_TRY(to_problems(probs, count, P, rr, rc));
+  const BatchWs w = batch_layout(ws, rr.data(), rc.data(), count);
+  if (!ws || ws_bytes < w.bytes) {
+    set_error("cpca_frpcag_solve_batched: workspace %zu bytes < required %zu", ws_bytes, w.bytes);
+    return CPCA_ERR_WORKSPACE;
+  }
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  CPCA_TRY(fista_batch_run(P.data(), count, prm->max_iter, prm->eps, infos != nullptr,
+                           prm->power_iters, prm->power_seed, prm->blocks, w, st));
+  if (infos) {
+    std::vector<cpca_solve_info*> ip(count);
+    for (int i = 0; i < count; ++i) ip[i] = infos + i;
+    CPCA_TRY(read_infos(P.data(), count, w, prm->max_iter, ip.data(), st));
+  }
+  return CPCA_OK;
+}
+
+extern "C" cpca_status cpca_frpcag_tune_batched(const cpca_problem* probs, int32_t count,
+                                                int32_t* blocks, float* ms_per_10_iters, void* ws,
+                                                size_t ws_bytes, void* stream) {
+  clear_error();
+  CPCA_CHECK_ARG(blocks, "cpca_frpcag_tune_batched: null output");
+  std::vector<BatchProblem> P;
+  std::vector<int> rr, rc;
+  CPCA_TRY(to_problems(probs, count, P, rr, rc));
+  const BatchWs w = batch_layout(ws, rr.data(), rc.data(), count);
+  if (!ws || ws_bytes < w.bytes) {
+    set_error("cpca_frpcag_tune_batched: workspace %zu bytes < required %zu", ws_bytes, w.bytes);
+    return CPCA_ERR_WORKSPACE;
+  }
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  int b = 0;
+  float ms = 0.f;
+  CPCA_TRY(tune_batch(P.data(), count, w, st, &b, &ms));
+  *blocks = b;
+  if (ms_per_10_iters) *ms_per_10_iters = ms;
   return CPCA_OK;
 }

@@ -1,0 +1,140 @@
+"""Batched FRPCAG (many uneven instances and gamma values in one launch):
+equal to per-instance solves and to the FP64 oracle, per-instance stopping,
+the launch-width autotuner, and replay from a captured CUDA graph."""
+import numpy as np
+import pytest
+
+import gen
+import oracle as O
+from tests._util import rel_fro
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+FISTA_TOL = 1e-4
+
+
+@pytest.fixture(scope="module")
+def M():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1602_02070_gb300 as m
+    m.lib()
+    return m
+
+
+def _dev(a):
+    return torch.as_tensor(np.ascontiguousarray(a, dtype=np.float32), device="cuda")
+
+
+def _small_batch(M, shapes, seed=0):
+    """Instances built on the host: Y~ from the seeded generator, graphs and
+    lambda from the oracle (so the oracle can check every instance)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i, (rr, rc) in enumerate(shapes):
+        Y, _, _ = gen.make_instance(seed + i, rr, rc, 3, 3, 0.05)
+        Yt = Y.astype(np.float64)
+        Lr, *_ = O.knn_graph(Yt, min(6, rr - 1))
+        Lc, *_ = O.knn_graph(Yt.T, min(6, rc - 1))
+        gr, gc = float(10 ** rng.uniform(-1, 1)), float(10 ** rng.uniform(-1, 1))
+        lam = O.fista_step(gr, gc, O.power_norm(Lr), O.power_norm(Lc))
+        out.append(dict(Yt_np=Yt, Lr_np=Lr, Lc_np=Lc, gamma_r=gr, gamma_c=gc, step=lam,
+                        Yt=_dev(Yt), Lr=M.Csr.from_scipy(Lr), Lc=M.Csr.from_scipy(Lc)))
+    return out
+
+
+SHAPES = [(40, 33), (97, 250), (64, 64), (150, 71), (33, 200), (256, 128)]
+
+
+def test_batched_matches_individual_and_oracle(M):
+    probs = _small_batch(M, SHAPES)
+    J = 120
+    B = M.Batch(probs)
+    Xs, infos = B.solve(M.frpcag_params(max_iter=J), want_info=True)
+    for q, X, info in zip(probs, Xs, infos):
+        Xi, ii = M.cpca_frpcag_solve(q["Yt"], q["Lr"], q["Lc"], gamma_r=q["gamma_r"],
+                                     gamma_c=q["gamma_c"], step=q["step"], max_iter=J)
+        assert torch.equal(X, Xi)  # same arithmetic, same order per entry
+        assert info.iters == ii.iters == J
+        assert info.objective == pytest.approx(ii.objective, rel=1e-12)
+        Xo, _ = O.frpcag_fista(q["Yt_np"], q["Lr_np"], q["Lc_np"], q["gamma_r"], q["gamma_c"],
+                               q["step"], J)
+        assert rel_fro(X.cpu().numpy(), Xo) < FISTA_TOL
+
+
+def test_batched_power_iteration_per_instance(M):
+    probs = _small_batch(M, SHAPES[:3], seed=5)
+    for q in probs:
+        q.pop("step")
+    B = M.Batch(probs)
+    _, infos = B.solve(M.frpcag_params(max_iter=5, power_iters=200), want_info=True)
+    for q, info in zip(probs, infos):
+        assert info.norm_r == pytest.approx(O.power_norm(q["Lr_np"], 200, 0, 2), rel=1e-6)
+        assert info.norm_c == pytest.approx(O.power_norm(q["Lc_np"], 200, 0, 3), rel=1e-6)
+        lam = O.fista_step(q["gamma_r"], q["gamma_c"], info.norm_r, info.norm_c)
+        assert info.step == pytest.approx(lam, rel=1e-12)
+
+
+def test_batched_stopping_per_instance(M):
+    probs = _small_batch(M, SHAPES[:4], seed=9)
+    B = M.Batch(probs)
+    Xs, infos = B.solve(M.frpcag_params(max_iter=3000, eps=1e-8), want_info=True)
+    for q, X, info in zip(probs, Xs, infos):
+        Xo, oi = O.frpcag_fista(q["Yt_np"], q["Lr_np"], q["Lc_np"], q["gamma_r"], q["gamma_c"],
+                                q["step"], 3000, eps=1e-8)
+        assert abs(info.iters - oi["iters"]) <= 2
+        assert rel_fro(X.cpu().numpy(), Xo) < 1e-3
+    assert len({i.iters for i in infos}) > 1  # instances really stop on their own
+
+
+def test_autotuner_and_graph_replay(M):
+    probs = _small_batch(M, SHAPES, seed=3)
+    B = M.Batch(probs)
+    blocks, ms = B.tune()
+    assert blocks > 0 and ms > 0
+    prm = M.frpcag_params(max_iter=60, blocks=blocks)
+    X0 = [x.clone() for x in B.solve(prm)[0]]
+    torch.cuda.synchronize()
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        B.solve(prm)  # warm-up outside capture
+    torch.cuda.current_stream().wait_stream(s)
+    g = torch.cuda.CUDAGraph()
+    for x in B.X:
+        x.zero_()
+    with torch.cuda.graph(g):
+        B.solve(prm)
+    for x in B.X:
+        x.zero_()
+    g.replay()
+    torch.cuda.synchronize()
+    for a, b in zip(B.X, X0):
+        assert torch.equal(a, b)
+
+
+def test_batched_workload_64_instances_equals_sequential(M):
+    """The 64-instance workload (sizes p ~ U[500, 8000], n ~ U[200, 5000],
+    1/4 sampling, K = 10 graphs, gamma pairs over an 8 x 8 log grid): the
+    batched launch reproduces 64 separate solves exactly."""
+    specs = gen.batched_instances(64)
+    probs = []
+    for sp in specs:
+        Y = gen.make_instance_torch(sp["seed"], sp["p"], sp["n"], sp["r"], sp["C"], sp["frac"])
+        rr, rc = M.rho_of(sp["p"], sp["fr"]), M.rho_of(sp["n"], sp["fc"])
+        _, _, Yt = M.cpca_sample(sp["seed"], sp["p"], sp["n"], rr, rc, Y)
+        del Y
+        Lr, _, _ = M.cpca_knn_graph(Yt, sp["K"])
+        Lc, _, _ = M.cpca_knn_graph(Yt, sp["K"], transposed=True)
+        probs.append(dict(Yt=Yt, Lr=Lr, Lc=Lc, gamma_r=sp["gamma_r"], gamma_c=sp["gamma_c"]))
+    J = 40
+    B = M.Batch(probs)
+    Xs, infos = B.solve(M.frpcag_params(max_iter=J), want_info=True)
+    for q, X, info in list(zip(probs, Xs, infos))[::7]:
+        # same lambda (the power iterations' FP64 sums may differ in the last
+        # bit between launches), then the same arithmetic entry by entry
+        Xi, ii = M.cpca_frpcag_solve(q["Yt"], q["Lr"], q["Lc"], gamma_r=q["gamma_r"],
+                                     gamma_c=q["gamma_c"], step=info.step, max_iter=J)
+        assert info.norm_r > 0 and info.norm_c > 0
+        assert torch.equal(X, Xi)

@@ -228,6 +228,32 @@ cpca_status cpca_frpcag_solve(const float* Yt, int32_t rr, int32_t rc, int64_t l
                               void* ws, size_t ws_bytes, void* stream);
 
 /* ------------------------------------------------------------------------
+ * cpca_frpcag_solve_noalloc - cpca_frpcag_solve without a workspace.
+ *
+ * (No counterpart in the paper: a deployment convenience.) For callers that
+ * cannot allocate device memory: a plugin inside a host application whose
+ * memory pool owns the whole device, code that must not call cudaMalloc or
+ * cudaFree because they can synchronise the device, or a fixed-budget
+ * process that reserves all memory up front. Same arguments, semantics and
+ * results as cpca_frpcag_solve, minus (ws, ws_bytes): the scratch is a
+ * CPCA_NOALLOC_WS_BYTES array in the library's own device memory (every GPU
+ * that loads libcpca.so holds it until the process exits). Problems needing
+ * more scratch than that (cpca_frpcag_workspace_size(rr, rc) >
+ * CPCA_NOALLOC_WS_BYTES, about rr * rc <= 2 million entries) are rejected
+ * with CPCA_ERR_WORKSPACE. Nothing is allocated: no cudaMalloc, cudaFree or
+ * allocating library call. The first call on a device looks up the array's
+ * device address (cudaGetSymbolAddress) with that device current; make that
+ * first call before any stream capture. All calls share the one array:
+ * calls that overlap on the GPU (other streams, other host threads) race;
+ * each call clears what must start at zero itself.
+ * ---------------------------------------------------------------------- */
+#define CPCA_NOALLOC_WS_BYTES (32u << 20)
+cpca_status cpca_frpcag_solve_noalloc(const float* Yt, int32_t rr, int32_t rc, int64_t ldyt,
+                                      const cpca_csr* Lr, const cpca_csr* Lc,
+                                      const cpca_frpcag_params* params, float* X, int64_t ldx,
+                                      cpca_solve_info* info, void* stream);
+
+/* ------------------------------------------------------------------------
  * cpca_decode - subspace-upsampling approximate decoder
  * (Sec. V-C; Lemma 1; Eq. Uupsample; Algorithm 2).
  *

@@ -96,6 +96,10 @@ _SIGS = [
      [C.c_void_p, C.c_int32, C.c_int32, C.c_int64, C.POINTER(cpca_csr), C.POINTER(cpca_csr),
       C.POINTER(cpca_frpcag_params), C.c_void_p, C.c_int64, C.POINTER(cpca_solve_info),
       C.c_void_p, C.c_size_t, C.c_void_p]),
+    ("cpca_frpcag_solve_noalloc", C.c_int32,
+     [C.c_void_p, C.c_int32, C.c_int32, C.c_int64, C.POINTER(cpca_csr), C.POINTER(cpca_csr),
+      C.POINTER(cpca_frpcag_params), C.c_void_p, C.c_int64, C.POINTER(cpca_solve_info),
+      C.c_void_p]),
     ("cpca_frpcag_batched_workspace_size", C.c_size_t, [C.c_void_p, C.c_int32]),
     ("cpca_frpcag_solve_batched", C.c_int32,
      [C.c_void_p, C.c_int32, C.POINTER(cpca_frpcag_params), C.c_void_p, C.c_void_p, C.c_size_t,
@@ -288,6 +292,25 @@ def cpca_frpcag_solve(Yt: torch.Tensor, Lr: Csr, Lc: Csr, params: cpca_frpcag_pa
                                    C.byref(prm), _ptr(X), X.stride(0),
                                    C.byref(info) if info is not None else None, _ptr(ws),
                                    ws.numel(), _stream()))
+    return X, info
+
+
+def cpca_frpcag_solve_noalloc(Yt: torch.Tensor, Lr: Csr, Lc: Csr,
+                              params: cpca_frpcag_params | None = None, want_info: bool = True,
+                              out: torch.Tensor | None = None, **kw):
+    """cpca_frpcag_solve with the library's built-in scratch instead of a
+    workspace (for callers that cannot allocate device memory; problems up to
+    the built-in scratch size). Returns (X, info or None)."""
+    _require_cuda(Yt, torch.float32, "Yt")
+    prm = params if params is not None else frpcag_params(**kw)
+    rr, rc = Yt.shape
+    X = out if out is not None else torch.empty(rr, rc, dtype=torch.float32, device=Yt.device)
+    info = cpca_solve_info() if want_info else None
+    lr, lc = Lr.c(), Lc.c()
+    _check(lib().cpca_frpcag_solve_noalloc(_ptr(Yt), rr, rc, Yt.stride(0), C.byref(lr), C.byref(lc),
+                                           C.byref(prm), _ptr(X), X.stride(0),
+                                           C.byref(info) if info is not None else None,
+                                           _stream()))
     return X, info
 
 

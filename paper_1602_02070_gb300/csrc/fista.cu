@@ -922,3 +922,61 @@ extern "C" cpca_status cpca_frpcag_tune_batched(const cpca_problem* probs, int32
   if (ms_per_10_iters) *ms_per_10_iters = ms;
   return CPCA_OK;
 }
+
+// ------------------------------------------------------------------------
+// Solve without any allocation: the scratch of cpca_frpcag_solve lives in a
+// file-scope device array instead of a caller-provided workspace.
+namespace {
+
+constexpr size_t kStaticWsBytes = size_t(CPCA_NOALLOC_WS_BYTES);
+// Every GPU that loads this library holds this array until the process exits.
+__device__ __align__(256) unsigned char g_noalloc_ws[kStaticWsBytes];
+
+std::mutex g_noalloc_mu;
+void* g_noalloc_ptr[256] = {nullptr};  // device address of g_noalloc_ws, per device
+
+// Device address of the array on the current device, looked up once per
+// device (in host code the symbol is only a host-side stand-in).
+cpca_status noalloc_base(void** out) {
+  int dev = 0;
+  CPCA_CUDA(cudaGetDevice(&dev));
+  CPCA_CHECK_ARG(dev >= 0 && dev < 256, "cpca_frpcag_solve_noalloc: device index %d out of range", dev);
+  std::lock_guard<std::mutex> lk(g_noalloc_mu);
+  if (!g_noalloc_ptr[dev]) {
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_ws);
+    if (e != cudaSuccess || !p) {
+      set_error("cpca_frpcag_solve_noalloc: cudaGetSymbolAddress failed: %s", cudaGetErrorString(e));
+      return CPCA_ERR_CUDA;
+    }
+    g_noalloc_ptr[dev] = p;
+  }
+  *out = g_noalloc_ptr[dev];
+  return CPCA_OK;
+}
+
+}  // namespace
+
+extern "C" cpca_status cpca_frpcag_solve_noalloc(const float* Yt, int32_t rr, int32_t rc,
+                                                 int64_t ldyt, const cpca_csr* Lr,
+                                                 const cpca_csr* Lc,
+                                                 const cpca_frpcag_params* prm, float* X,
+                                                 int64_t ldx, cpca_solve_info* info,
+                                                 void* stream) {
+  clear_error();
+  CPCA_CHECK_ARG(rr > 0 && rc > 0, "cpca_frpcag_solve_noalloc: empty matrix");
+  const size_t need = cpca_frpcag_workspace_size(rr, rc);
+  if (need > kStaticWsBytes) {
+    set_error("cpca_frpcag_solve_noalloc: a %d x %d problem needs %zu bytes of scratch, more than "
+              "the built-in %zu (use cpca_frpcag_solve with a caller workspace)",
+              rr, rc, need, kStaticWsBytes);
+    return CPCA_ERR_WORKSPACE;
+  }
+  void* base = nullptr;
+  CPCA_TRY(noalloc_base(&base));
+  // Every scratch field that must start at zero is cleared by the solve
+  // itself (barrier, statistics, stop flags, power-iteration sums); the rest
+  // is written before it is read, so stale contents of earlier calls are
+  // harmless. Calls that overlap on the GPU share this array and race.
+  return cpca_frpcag_solve(Yt, rr, rc, ldyt, Lr, Lc, prm, X, ldx, info, base, kStaticWsBytes, stream);
+}

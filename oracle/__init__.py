@@ -12,3 +12,4 @@ docstring; all of them are pinned by ``tests/test_oracle_*.py`` against
 closed forms, textbook routines, invariants or brute force.
 """
 from .cpca_oracle import *  # noqa: F401,F403
+from . import cpca_adjoint  # noqa: F401  (reverse-mode derivatives, FP64)

@@ -22,7 +22,8 @@ import scipy.sparse as sp
 
 __all__ = [
     "splitmix64_outputs", "uniform01", "sample_indices", "sample_matrix",
-    "knn_bruteforce", "sigma2_mean", "laplacian_from_knn", "knn_graph",
+    "knn_bruteforce", "knn_query_blocked", "sigma2_mean", "laplacian_from_knn", "laplacian_from_weights",
+    "knn_graph",
     "power_norm", "fista_step", "frpcag_fista", "frpcag_objective",
     "svd_rank", "pcg", "upsample_subspace", "approx_decode", "cpca",
     "LAP_NORMALIZED", "LAP_COMBINATORIAL", "GOLDEN_GAMMA",
@@ -121,6 +122,27 @@ def knn_bruteforce(P: np.ndarray, K: int, queries=None):
     return idx, d2o
 
 
+def knn_query_blocked(P, i: int, K: int, block: int = 256):
+    """The K + 1 nearest neighbours of one point i (Sec. I), for point sets
+    too large to difference in one piece: the candidates are visited in
+    blocks of ``block`` points, each converted to FP64 and differenced
+    coordinate by coordinate as in knn_bruteforce. Same exclusion of i and
+    the same (d^2, j) tie order. Returns (idx int64 [K+1], d2 float64 [K+1]).
+    """
+    N = P.shape[0]
+    if not (1 <= K < N - 1):
+        raise ValueError("need 1 <= K < N - 1")
+    q = np.asarray(P[i], dtype=np.float64)
+    d2 = np.empty(N)
+    for j0 in range(0, N, block):
+        B = np.asarray(P[j0:j0 + block], dtype=np.float64)
+        diff = B - q
+        d2[j0:j0 + B.shape[0]] = np.einsum("ij,ij->i", diff, diff)
+    d2[i] = np.inf
+    order = np.lexsort((np.arange(N), d2))[:K + 1]
+    return order.astype(np.int64), d2[order]
+
+
 def sigma2_mean(d2: np.ndarray) -> float:
     """Gaussian kernel width: the mean of the N*K directed kNN squared
     distances. Sec. VII-A says "average distance of the K-nearest neighbors";
@@ -153,6 +175,17 @@ def laplacian_from_knn(idx: np.ndarray, d2: np.ndarray, N: int, sigma2: float,
         vals += [w, w]
     W = sp.csr_matrix((vals, (rows, cols)), shape=(N, N))
     W.sort_indices()
+    return laplacian_from_weights(W, lap_type), W
+
+
+def laplacian_from_weights(W, lap_type: int = LAP_NORMALIZED):
+    """The Laplacian of Sec. I as a function of a symmetric weight matrix W
+    (no self loops): combinatorial L = D - W or normalised
+    L_n = D^{-1/2} (D - W) D^{-1/2}, D_ii = sum_j W_ij, with D^{-1/2}_ii = 0
+    where D_ii = 0. Returns L as a scipy CSR float64 matrix with sorted
+    indices and an explicit diagonal."""
+    W = sp.csr_matrix(W)
+    N = W.shape[0]
     deg = np.asarray(W.sum(axis=1)).ravel()
     if lap_type == LAP_COMBINATORIAL:
         L = sp.diags(deg) - W
@@ -169,7 +202,7 @@ def laplacian_from_knn(idx: np.ndarray, d2: np.ndarray, N: int, sigma2: float,
     L = L + sp.csr_matrix((np.full(N, 0.0), (np.arange(N), np.arange(N))), shape=(N, N))
     L = sp.csr_matrix(L)
     L.sort_indices()
-    return L, W
+    return L
 
 
 def knn_graph(P: np.ndarray, K: int, lap_type: int = LAP_NORMALIZED, sigma2=None):

@@ -92,6 +92,20 @@ def test_knn_matches_kdtree():
     assert np.allclose(d2, dist[:, 1:] ** 2, rtol=1e-12)
 
 
+def test_knn_query_blocked_matches_kdtree():
+    """The blocked single-query search (used on point sets too large to
+    difference at once), including a float32 point set read through a
+    transposed view, against a k-d tree; ragged last block."""
+    rng = np.random.default_rng(2)
+    P32 = rng.standard_normal((9, 333)).astype(np.float32)
+    P = P32.T  # 333 points of dimension 9, a non-contiguous view
+    dist, ref = cKDTree(P.astype(np.float64)).query(P.astype(np.float64), 13)
+    for i in (0, 17, 332):
+        idx, d2 = O.knn_query_blocked(P, i, 11, block=64)
+        assert np.array_equal(idx, ref[i, 1:13])
+        assert np.allclose(d2, dist[i, 1:13] ** 2, rtol=1e-12)
+
+
 @pytest.mark.parametrize("lap", [O.LAP_NORMALIZED, O.LAP_COMBINATORIAL])
 def test_laplacian_invariants(lap):
     rng = np.random.default_rng(2)

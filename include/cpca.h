@@ -254,11 +254,62 @@ cpca_status cpca_frpcag_solve_noalloc(const float* Yt, int32_t rr, int32_t rc, i
                                       cpca_solve_info* info, void* stream);
 
 /* ------------------------------------------------------------------------
+ * cpca_frpcag_backward - reverse-mode derivative of cpca_frpcag_solve.
+ *
+ * (The paper has no derivatives; this differentiates the computed map.)
+ * For a loss of the FISTA output X = S_J (Algorithm 1 with a fixed
+ * iteration count J = params->max_iter; params->eps must be 0), given
+ * dX = dloss/dX, returns the derivatives with respect to
+ *   - Y~ (dYt, rr x rc, leading dimension lddyt, FP32, overwritten);
+ *   - gamma_r, gamma_c (ginfo), including their effect through
+ *     lambda = 1/beta' (Sec. IV-B) when lambda is computed (params->step
+ *     <= 0); with a given step, lambda is a constant and ginfo->dlambda
+ *     reports dloss/dlambda;
+ *   - the values of Lr and Lc on their CSR patterns (dLr, dLc: nnz FP64
+ *     each, device, optional), through FISTA and through the power
+ *     iterations that estimate |Lr|_2, |Lc|_2 (same start vectors and
+ *     count as the solve: the derivative is that of the estimate);
+ *   - the edge weights (dwr, dwc: nnz FP32 each, device, optional), given
+ *     the weights wr, wc on the same patterns (the `weight` output of
+ *     cpca_knn_graph) and lap_type: an undirected edge's derivative is
+ *     written at both of its entries, 0 on the diagonal. The Laplacian is
+ *     the function of the weights of Sec. I (normalised: the entry and both
+ *     degrees move).
+ * The prox is differentiated where it is smooth: its derivative is 1 where
+ * |Z_j - lambda grad g(Z_j) - Y~| > lambda, else 0.
+ * Checkpointing: (S_j, Z_{j+1}) is stored every ckpt_every iterations
+ * (0 selects 20; >= max_iter stores the whole trajectory, no recompute);
+ * each segment is recomputed once before its reverse sweep. Cost: about
+ * two forward solves plus the reverse sweep (two graph products per
+ * iteration); scratch from cpca_frpcag_backward_workspace_size.
+ * All device pointers; ginfo is host. SYNCHRONISES the stream.
+ * ---------------------------------------------------------------------- */
+typedef struct cpca_frpcag_grad_info {
+  double dgamma_r, dgamma_c;  /* total derivatives */
+  double dlambda;             /* dloss/dlambda */
+  double dnorm_r, dnorm_c;    /* dloss/d|Lr|_2, dloss/d|Lc|_2 (estimates) */
+  double lambda;              /* the step used */
+  double norm_r, norm_c;      /* the norm estimates (0 if step was given) */
+} cpca_frpcag_grad_info;
+
+size_t cpca_frpcag_backward_workspace_size(int32_t rr, int32_t rc, int32_t max_iter,
+                                           int32_t ckpt_every, int32_t power_iters,
+                                           int64_t nnz_r, int64_t nnz_c);
+cpca_status cpca_frpcag_backward(const float* Yt, int32_t rr, int32_t rc, int64_t ldyt,
+                                 const cpca_csr* Lr, const cpca_csr* Lc,
+                                 const cpca_frpcag_params* params, int32_t ckpt_every,
+                                 const float* dX, int64_t lddx, float* dYt, int64_t lddyt,
+                                 double* dLr, double* dLc, const float* wr, const float* wc,
+                                 int32_t lap_type, float* dwr, float* dwc,
+                                 cpca_frpcag_grad_info* ginfo, void* ws, size_t ws_bytes,
+                                 void* stream);
+
+/* ------------------------------------------------------------------------
  * cpca_decode - subspace-upsampling approximate decoder
  * (Sec. V-C; Lemma 1; Eq. Uupsample; Algorithm 2).
  *
  * 1. Top singular triplets of Xt (rr x rc) by block subspace iteration
- *    with block size b = min(rr, rc, kmax + 16), FP32 products, FP64 Gram /
+ *    with block size b = min(rr, rc, kmax + 8), FP32 products, FP64 Gram /
  *    Cholesky-QR / Jacobi eigen-solve.
  * 2. k = number of singular values with s_i / s_1 >= rank_ratio (or
  *    k_override if > 0); k <= kmax, else CPCA_ERR_INVALID_ARG.
@@ -309,6 +360,69 @@ cpca_status cpca_decode(const float* Xt, int32_t rr, int32_t rc, int64_t ldxt,
                         float* X, int64_t ldx, float* U, float* V, double* sigma,
                         int32_t* k_out, cpca_decode_info* info,
                         void* ws, size_t ws_bytes, void* stream);
+
+/* ------------------------------------------------------------------------
+ * cpca_decode_backward - reverse-mode derivative of cpca_decode.
+ *
+ * (The paper has no derivatives; this differentiates the computed map with
+ * the rank k fixed.) For a loss of the decoded X at nh entries
+ * (h_row[e], h_col[e]) with dloss/dX there = h_grad[e] (device arrays),
+ * returns
+ *   - dXt = dloss/dXt (rr x rc, leading dimension lddxt, device, FP32);
+ *   - dLr, dLc: dloss/d(Laplacian values) on the CSR patterns (nnz FP64
+ *     each, device, optional): nonzero only on the rows of unsampled nodes;
+ *   - dwr, dwc: dloss/d(edge weights) (nnz FP32 each, optional; needs the
+ *     weights wr, wc on the same patterns and lap_type), an undirected
+ *     edge's derivative at both of its entries.
+ * Same inputs and parameters as the forward call, plus the forward's k
+ * (1 <= k <= kmax); the forward factors are recomputed with that k
+ * (partial SVD, both upsampling solves). Steps: scatter of h_grad into
+ * dU, dV, dsigma; the adjoint of the column normalisation; one adjoint
+ * Jacobi-PCG per side on L_aa (to cg_tol); the top-k SVD derivative
+ * (Townsend's formula, with the parts outside the top-k subspaces through
+ * the resolvents (s_i^2 I - Xt^T Xt)^-1 on the complement, solved by dense
+ * CG on the Gram matrix of the shorter side, min(rr, rc) <= 16384).
+ * The singular values s_1..s_k must be distinct and separated from s_{k+1}
+ * (else CPCA_ERR_SINGULAR / CPCA_ERR_NOT_CONVERGED). SYNCHRONISES.
+ * ---------------------------------------------------------------------- */
+size_t cpca_decode_backward_workspace_size(int32_t p, int32_t n, int32_t rr, int32_t rc, int32_t kmax,
+                                           int64_t nnz_r, int64_t nnz_c);
+cpca_status cpca_decode_backward(const float* Xt, int32_t rr, int32_t rc, int64_t ldxt,
+                                 const int32_t* omega_r, const int32_t* omega_c, int32_t p, int32_t n,
+                                 const cpca_csr* Lr, const cpca_csr* Lc,
+                                 const cpca_decode_params* params, int32_t k, int64_t nh,
+                                 const int32_t* h_row, const int32_t* h_col, const float* h_grad,
+                                 float* dXt, int64_t lddxt, double* dLr, double* dLc,
+                                 const float* wr, const float* wc, int32_t lap_type, float* dwr,
+                                 float* dwc, void* ws, size_t ws_bytes, void* stream);
+
+/* ------------------------------------------------------------------------
+ * Laplacians as functions of the edge weights (Sec. I), for differentiation.
+ *
+ * cpca_laplacian_values: on a given symmetric CSR pattern (pattern->val is
+ * not read) with weights w (nnz FP32, 0 on the diagonal entries), writes
+ * val (nnz FP32): D_i = sum_{j != i} w_ij (FP64); normalised
+ * (CPCA_LAP_NORMALIZED): -w_ij / sqrt(D_i D_j) off the diagonal and 1 on it
+ * (0 where D_i = 0); combinatorial: -w_ij and D_i. Asynchronous.
+ * cpca_laplacian_weight_grad: the chain rule from dL = dloss/d(values)
+ * (nnz FP64) to dw (nnz FP32) through that map, given the values L->val
+ * and weights w; an undirected edge's derivative is written at both of its
+ * entries, 0 on the diagonal. Asynchronous. Both need
+ * cpca_laplacian_workspace_size(n) bytes of scratch.
+ * ---------------------------------------------------------------------- */
+size_t cpca_laplacian_workspace_size(int32_t n);
+cpca_status cpca_laplacian_values(const cpca_csr* pattern, const float* w, int32_t lap_type, float* val,
+                                  void* ws, size_t ws_bytes, void* stream);
+cpca_status cpca_laplacian_weight_grad(const cpca_csr* L, const float* w, const double* dL,
+                                       int32_t lap_type, float* dw, void* ws, size_t ws_bytes,
+                                       void* stream);
+
+/* cpca_decode_entries: X(h_row[e], h_col[e]) = sum_c U(i, c) sigma_c V(j, c)
+ * (Algorithm 2 step 6 at nh given entries) from the U, V (ld columns) and
+ * sigma that cpca_decode returns; FP64 sums, FP32 out. Asynchronous. */
+cpca_status cpca_decode_entries(const float* U, const float* V, int32_t ld, const double* sigma,
+                                int32_t k, int64_t nh, const int32_t* h_row, const int32_t* h_col,
+                                float* out, void* stream);
 
 #ifdef __cplusplus
 }

@@ -60,6 +60,12 @@ class cpca_problem(C.Structure):
                 ("ldx", C.c_int64)]
 
 
+class cpca_frpcag_grad_info(C.Structure):
+    _fields_ = [("dgamma_r", C.c_double), ("dgamma_c", C.c_double), ("dlambda", C.c_double),
+                ("dnorm_r", C.c_double), ("dnorm_c", C.c_double), ("lambda_", C.c_double),
+                ("norm_r", C.c_double), ("norm_c", C.c_double)]
+
+
 class cpca_decode_params(C.Structure):
     _fields_ = [("rank_ratio", C.c_double), ("k_override", C.c_int32), ("kmax", C.c_int32),
                 ("delta", C.c_double), ("cg_tol", C.c_double), ("cg_max_iter", C.c_int32),
@@ -107,7 +113,29 @@ _SIGS = [
     ("cpca_frpcag_tune_batched", C.c_int32,
      [C.c_void_p, C.c_int32, C.POINTER(C.c_int32), C.POINTER(C.c_float), C.c_void_p, C.c_size_t,
       C.c_void_p]),
+    ("cpca_frpcag_backward_workspace_size", C.c_size_t, [C.c_int32] * 5 + [C.c_int64] * 2),
+    ("cpca_frpcag_backward", C.c_int32,
+     [C.c_void_p, C.c_int32, C.c_int32, C.c_int64, C.POINTER(cpca_csr), C.POINTER(cpca_csr),
+      C.POINTER(cpca_frpcag_params), C.c_int32, C.c_void_p, C.c_int64, C.c_void_p, C.c_int64,
+      C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p,
+      C.POINTER(cpca_frpcag_grad_info), C.c_void_p, C.c_size_t, C.c_void_p]),
+    ("cpca_laplacian_workspace_size", C.c_size_t, [C.c_int32]),
+    ("cpca_laplacian_values", C.c_int32,
+     [C.POINTER(cpca_csr), C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p]),
+    ("cpca_laplacian_weight_grad", C.c_int32,
+     [C.POINTER(cpca_csr), C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p, C.c_size_t,
+      C.c_void_p]),
+    ("cpca_decode_entries", C.c_int32,
+     [C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p, C.c_int32, C.c_int64, C.c_void_p, C.c_void_p,
+      C.c_void_p, C.c_void_p]),
     ("cpca_decode_workspace_size", C.c_size_t, [C.c_int32] * 5 + [C.c_int64] * 2),
+    ("cpca_decode_backward_workspace_size", C.c_size_t, [C.c_int32] * 5 + [C.c_int64] * 2),
+    ("cpca_decode_backward", C.c_int32,
+     [C.c_void_p, C.c_int32, C.c_int32, C.c_int64, C.c_void_p, C.c_void_p, C.c_int32, C.c_int32,
+      C.POINTER(cpca_csr), C.POINTER(cpca_csr), C.POINTER(cpca_decode_params), C.c_int32,
+      C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p,
+      C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p,
+      C.c_size_t, C.c_void_p]),
     ("cpca_decode", C.c_int32,
      [C.c_void_p, C.c_int32, C.c_int32, C.c_int64, C.c_void_p, C.c_void_p, C.c_int32, C.c_int32,
       C.POINTER(cpca_csr), C.POINTER(cpca_csr), C.POINTER(cpca_decode_params), C.c_void_p,
@@ -208,15 +236,29 @@ class Csr:
         return self.col.numel()
 
     def c(self) -> cpca_csr:
-        return cpca_csr(self.n, self.nnz, self.rowptr.data_ptr(), self.col.data_ptr(), self.val.data_ptr())
+        return cpca_csr(self.n, self.nnz, self.rowptr.data_ptr(), self.col.data_ptr(),
+                        self.val.data_ptr() if self.val is not None else None)
 
     @staticmethod
     def from_scipy(L, device="cuda", weight=None) -> "Csr":
+        """From a scipy Laplacian; ``weight`` (a scipy matrix W) is read on
+        L's pattern (0 where W has no entry, e.g. the diagonal)."""
         L = L.tocsr()
         L.sort_indices()
+        w = None
+        if weight is not None:
+            rows = L.indptr.searchsorted(range(L.nnz), side="right") - 1
+            w = torch.as_tensor(weight.tocsr()[rows, L.indices].A1.astype("float32"), device=device)
         return Csr(torch.as_tensor(L.indptr.astype("int64"), device=device),
                    torch.as_tensor(L.indices.astype("int32"), device=device),
-                   torch.as_tensor(L.data.astype("float32"), device=device))
+                   torch.as_tensor(L.data.astype("float32"), device=device), w)
+
+    def pattern_scipy(self, values):
+        """A scipy CSR matrix with this pattern and the given per-entry values."""
+        import scipy.sparse as sp
+        v = values.double().cpu().numpy() if isinstance(values, torch.Tensor) else values
+        return sp.csr_matrix((v, self.col.cpu().numpy(), self.rowptr.cpu().numpy()),
+                             shape=(self.n, self.n))
 
     def to_scipy(self):
         import scipy.sparse as sp
@@ -314,6 +356,42 @@ def cpca_frpcag_solve_noalloc(Yt: torch.Tensor, Lr: Csr, Lc: Csr,
     return X, info
 
 
+def cpca_frpcag_backward(Yt: torch.Tensor, Lr: Csr, Lc: Csr, dX: torch.Tensor,
+                         params: cpca_frpcag_params | None = None, ckpt_every: int = 20,
+                         want_dL: bool = True, want_dw: bool = False,
+                         lap_type: int = LAP_NORMALIZED, ws=None, **kw):
+    """Reverse-mode derivative of cpca_frpcag_solve for dloss/dX = dX.
+    Returns dict: dYt (rr x rc), dLr, dLc (FP64 per CSR entry, or None),
+    dwr, dwc (FP32 per CSR entry, needs Lr.weight / Lc.weight, or None),
+    info (cpca_frpcag_grad_info)."""
+    _require_cuda(Yt, torch.float32, "Yt")
+    _require_cuda(dX, torch.float32, "dX")
+    prm = params if params is not None else frpcag_params(**kw)
+    rr, rc = Yt.shape
+    dev = Yt.device
+    T = 0 if prm.step > 0 else prm.power_iters
+    if ws is None:
+        ws = _workspace(lib().cpca_frpcag_backward_workspace_size(rr, rc, prm.max_iter, ckpt_every, T,
+                                                                  Lr.nnz, Lc.nnz), dev)
+    dY = torch.empty(rr, rc, dtype=torch.float32, device=dev)
+    dLr = torch.empty(Lr.nnz, dtype=torch.float64, device=dev) if want_dL else None
+    dLc = torch.empty(Lc.nnz, dtype=torch.float64, device=dev) if want_dL else None
+    dwr = dwc = None
+    if want_dw:
+        if Lr.weight is None or Lc.weight is None:
+            raise ValueError("want_dw needs Lr.weight and Lc.weight")
+        dwr = torch.empty(Lr.nnz, dtype=torch.float32, device=dev)
+        dwc = torch.empty(Lc.nnz, dtype=torch.float32, device=dev)
+    info = cpca_frpcag_grad_info()
+    lr, lc = Lr.c(), Lc.c()
+    _check(lib().cpca_frpcag_backward(
+        _ptr(Yt), rr, rc, Yt.stride(0), C.byref(lr), C.byref(lc), C.byref(prm), ckpt_every,
+        _ptr(dX), dX.stride(0), _ptr(dY), dY.stride(0), _ptr(dLr), _ptr(dLc),
+        _ptr(Lr.weight) if want_dw else None, _ptr(Lc.weight) if want_dw else None, lap_type,
+        _ptr(dwr), _ptr(dwc), C.byref(info), _ptr(ws), ws.numel(), _stream()))
+    return {"dYt": dY, "dLr": dLr, "dLc": dLc, "dwr": dwr, "dwc": dwc, "info": info}
+
+
 class Batch:
     """A fixed set of FRPCAG problems for cpca_frpcag_solve_batched: holds
     the C problem table, the outputs X_i and one workspace, so repeated
@@ -389,3 +467,76 @@ def cpca_decode(Xt: torch.Tensor, omega_r: torch.Tensor, omega_c: torch.Tensor, 
     kk = k.value
     return {"X": X, "U": U[:, :kk], "V": V[:, :kk], "sigma": sig[:kk], "k": kk, "info": info,
             "status": st}
+
+
+def cpca_decode_backward(Xt: torch.Tensor, omega_r: torch.Tensor, omega_c: torch.Tensor, p: int,
+                         n: int, Lr: Csr, Lc: Csr, k: int, h_row: torch.Tensor,
+                         h_col: torch.Tensor, h_grad: torch.Tensor,
+                         params: cpca_decode_params | None = None, want_dL: bool = True,
+                         want_dw: bool = False, lap_type: int = LAP_NORMALIZED, ws=None, **kw):
+    """Reverse-mode derivative of cpca_decode (rank k fixed) for a loss of X
+    at entries (h_row, h_col) with gradient h_grad there. Returns dict:
+    dXt (rr x rc), dLr, dLc (FP64 per CSR entry or None), dwr, dwc (FP32 per
+    CSR entry, needs Lr.weight / Lc.weight, or None)."""
+    _require_cuda(Xt, torch.float32, "Xt")
+    _require_cuda(h_grad, torch.float32, "h_grad")
+    prm = params if params is not None else decode_params(**kw)
+    rr, rc = Xt.shape
+    dev = Xt.device
+    if ws is None:
+        ws = _workspace(lib().cpca_decode_backward_workspace_size(p, n, rr, rc, prm.kmax, Lr.nnz,
+                                                                  Lc.nnz), dev)
+    dXt = torch.empty(rr, rc, dtype=torch.float32, device=dev)
+    dLr = torch.empty(Lr.nnz, dtype=torch.float64, device=dev) if want_dL else None
+    dLc = torch.empty(Lc.nnz, dtype=torch.float64, device=dev) if want_dL else None
+    dwr = dwc = None
+    if want_dw:
+        if Lr.weight is None or Lc.weight is None:
+            raise ValueError("want_dw needs Lr.weight and Lc.weight")
+        dwr = torch.empty(Lr.nnz, dtype=torch.float32, device=dev)
+        dwc = torch.empty(Lc.nnz, dtype=torch.float32, device=dev)
+    lr, lc = Lr.c(), Lc.c()
+    nh = h_grad.numel()
+    _check(lib().cpca_decode_backward(
+        _ptr(Xt), rr, rc, Xt.stride(0), _ptr(omega_r), _ptr(omega_c), p, n, C.byref(lr),
+        C.byref(lc), C.byref(prm), k, nh, _ptr(h_row), _ptr(h_col), _ptr(h_grad), _ptr(dXt),
+        dXt.stride(0), _ptr(dLr), _ptr(dLc), _ptr(Lr.weight) if want_dw else None,
+        _ptr(Lc.weight) if want_dw else None, lap_type, _ptr(dwr), _ptr(dwc), _ptr(ws), ws.numel(),
+        _stream()))
+    return {"dXt": dXt, "dLr": dLr, "dLc": dLc, "dwr": dwr, "dwc": dwc}
+
+
+def laplacian_values(pattern: Csr, w: torch.Tensor, lap_type: int = LAP_NORMALIZED) -> torch.Tensor:
+    """Laplacian values (Sec. I) on ``pattern`` from edge weights w (per CSR
+    entry, 0 on the diagonal)."""
+    _require_cuda(w, torch.float32, "w")
+    val = torch.empty(pattern.nnz, dtype=torch.float32, device=w.device)
+    ws = _workspace(lib().cpca_laplacian_workspace_size(pattern.n), w.device)
+    c = cpca_csr(pattern.n, pattern.nnz, pattern.rowptr.data_ptr(), pattern.col.data_ptr(), None)
+    _check(lib().cpca_laplacian_values(C.byref(c), _ptr(w), lap_type, _ptr(val), _ptr(ws), ws.numel(),
+                                       _stream()))
+    return val
+
+
+def laplacian_weight_grad(L: Csr, w: torch.Tensor, dL: torch.Tensor,
+                          lap_type: int = LAP_NORMALIZED) -> torch.Tensor:
+    """dloss/dw per CSR entry from dloss/dL (FP64 per entry) through the
+    Laplacian-of-weights map of Sec. I."""
+    _require_cuda(w, torch.float32, "w")
+    _require_cuda(dL, torch.float64, "dL")
+    dw = torch.empty(L.nnz, dtype=torch.float32, device=w.device)
+    ws = _workspace(lib().cpca_laplacian_workspace_size(L.n), w.device)
+    c = L.c()
+    _check(lib().cpca_laplacian_weight_grad(C.byref(c), _ptr(w), _ptr(dL), lap_type, _ptr(dw), _ptr(ws),
+                                            ws.numel(), _stream()))
+    return dw
+
+
+def decode_entries(U: torch.Tensor, V: torch.Tensor, sigma: torch.Tensor, k: int,
+                   h_row: torch.Tensor, h_col: torch.Tensor) -> torch.Tensor:
+    """X at the entries (h_row, h_col) from cpca_decode's U, V (row stride =
+    kmax), sigma."""
+    out = torch.empty(h_row.numel(), dtype=torch.float32, device=U.device)
+    _check(lib().cpca_decode_entries(_ptr(U), _ptr(V), U.stride(0), _ptr(sigma), k, h_row.numel(),
+                                     _ptr(h_row), _ptr(h_col), _ptr(out), _stream()))
+    return out

@@ -1,0 +1,1016 @@
+// adjoint.cu - reverse-mode derivative of the FISTA solve (Algorithm 1 with
+// a fixed iteration count, Sec. IV-B), of its step size lambda = 1/beta'
+// (power iterations on both Laplacians), and of the Laplacians as functions
+// of the edge weights (Sec. I). The paper has no derivatives: what is
+// differentiated is the computed map, so that finite differences of
+// cpca_frpcag_solve agree with it.
+//
+// Forward map, for j = 1..J (Z_1 = S_0 = Y~, t_1 = 1):
+//   G_j = 2 gamma_r Lr Z_j + 2 gamma_c Z_j Lc,  R_j = Z_j - lambda G_j - Y~,
+//   S_j = Y~ + sgn(R_j) max(|R_j| - lambda, 0),
+//   Z_{j+1} = (1 + mu_j) S_j - mu_j S_{j-1},   mu_j = (t_j - 1) / t_{j+1}.
+// Reverse, j = J..1, with Sb = dloss/dS_j and M_j = [|R_j| > lambda]:
+//   Vb = M_j o Sb;  dY~ += Sb - Vb;
+//   dlambda += -sum sgn(R_j) Vb - <Vb, G_j>;
+//   dgamma_r += -2 lambda <Vb, Lr Z_j>;  dgamma_c += -2 lambda <Vb, Z_j Lc>;
+//   dLr(a,b) += -2 lambda gamma_r sum_c Vb(a,c) Z_j(b,c)   (on Lr's pattern)
+//   dLc(a,b) += -2 lambda gamma_c sum_r Z_j(r,a) Vb(r,b)   (on Lc's pattern)
+//   Zb = Vb - lambda (2 gamma_r Lr Vb + 2 gamma_c Vb Lc)    (L symmetric)
+//   dS_{j-1} += (1 + mu_{j-1}) Zb, dS_{j-2} += -mu_{j-1} Zb  (j >= 2)
+//   dY~ += Zb + dS_0                                         (j = 1).
+//
+// Checkpointing: a first forward pass stores (S_j, Z_{j+1}) every C
+// iterations; then, segment by segment from the last, the forward iterations
+// of the segment are recomputed with every Z_j kept (row-major and
+// column-major), and the reverse sweep runs over them. Both sweeps are
+// persistent cooperative launches over 32 x 32 tiles with one grid barrier
+// per iteration (two phases per reverse iteration: the mask phase publishes
+// Vb, the second phase gathers Vb's neighbours). The derivatives with
+// respect to the Laplacian entries are summed per tile column (Lr) and per
+// tile row (Lc) in FP64 without atomics, then reduced in a fixed order.
+#include <algorithm>
+#include <vector>
+
+#include "common.cuh"
+#include "fista_internal.cuh"
+
+namespace cpca {
+namespace {
+
+// ------------------------------------------------------------- momentum --
+// mu[j] = (t_j - 1) / t_{j+1} in the same double arithmetic as the solve.
+__global__ void mu_kernel(int J, float* mu) {
+  if (threadIdx.x || blockIdx.x) return;
+  double t = 1.0;
+  mu[0] = 0.f;
+  for (int j = 1; j <= J; ++j) {
+    const double tn = (1.0 + sqrt(1.0 + 4.0 * t * t)) / 2.0;
+    mu[j] = float((t - 1.0) / tn);
+    t = tn;
+  }
+}
+
+// Seed trajectory slot 0 with Z (row-major copy and transpose) and S.
+__global__ void __launch_bounds__(256)
+seed_kernel(const float* __restrict__ Zsrc, int64_t ldz, const float* __restrict__ Ssrc, int64_t lds,
+            int rr, int rc, float* __restrict__ Z, float* __restrict__ ZT, float* __restrict__ S) {
+  __shared__ float tile[TB][TB + 1];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int ntj = (rc + TB - 1) / TB, ntiles = ((rr + TB - 1) / TB) * ntj;
+  for (int tl = blockIdx.x; tl < ntiles; tl += gridDim.x) {
+    const int i0 = (tl / ntj) * TB, j0 = (tl % ntj) * TB;
+    const int ni = min(TB, rr - i0), nj = min(TB, rc - j0);
+    for (int r = warp; r < TB; r += 8)
+      if (r < ni && lane < nj) {
+        const int64_t i = i0 + r, jj = j0 + lane;
+        const float z = Zsrc[i * ldz + jj];
+        Z[i * rc + jj] = z;
+        S[i * rc + jj] = Ssrc[i * lds + jj];
+        tile[r][lane] = z;
+      }
+    __syncthreads();
+    for (int c = warp; c < TB; c += 8)
+      if (c < nj && lane < ni) ZT[int64_t(j0 + c) * rr + i0 + lane] = tile[lane][c];
+    __syncthreads();
+  }
+}
+
+struct TrajArgs {
+  const float* Yt;
+  int64_t ldy;
+  int rr, rc, ntj, ntiles;
+  CsrView Lr, Lc;
+  const double* lam;
+  float two_gr, two_gc;
+  double gamma_r, gamma_c;
+  const float* mu;
+  float* S;              // own tiles: S_{j-1} in, S_j out (ld rc)
+  float* Zs;             // trajectory slots of Z_j (row-major), slot stride rr * rc
+  float* ZTs;            // column-major copies
+  int jbase, nslot;      // Z_j lives in slot (j - jbase) % nslot
+  int ja, jb;            // forward: iterations ja..jb; reverse: jb down to ja
+  int J;
+  // forward only: checkpoints (S_j, Z_{j+1}) at j = m * ck, m = 1..
+  float* ckS;
+  float* ckZ;
+  int ck;
+  // reverse only
+  float* Sb;             // dloss/dS_j (own tiles)
+  float* A2;             // partial dloss/dS_{j-1}
+  float* Vb[2];          // published Vb, row-major / column-major, parity j & 1
+  float* VbT[2];
+  float* dY;
+  int64_t lddy;
+  double* Pr;            // [ntj][nnz_r]
+  double* Pc;            // [nti][nnz_c]
+  double* scal_bar;      // [3]: dlambda, dgamma_r, dgamma_c (FP64 atomics)
+  const int64_t* tmap_c; // index of entry (j, i) for each entry (i, j) of Lc
+  GridBar bar;
+};
+
+struct AdjSmem {
+  TileNbr nb;
+  float ac[TB][TB + 1];
+  float tl[TB][TB + 1];
+};
+
+__device__ __forceinline__ size_t slot_off(const TrajArgs& a, int j) {
+  int s = (j - a.jbase) % a.nslot;
+  if (s < 0) s += a.nslot;
+  return size_t(s) * size_t(a.rr) * a.rc;
+}
+
+__device__ __forceinline__ void tile_of(const TrajArgs& a, int tile, int& i0, int& j0, int& ni, int& nj) {
+  i0 = (tile / a.ntj) * TB;
+  j0 = (tile % a.ntj) * TB;
+  ni = min(TB, a.rr - i0);
+  nj = min(TB, a.rc - j0);
+}
+
+// Forward iterations ja..jb with the trajectory kept (the arithmetic of the
+// solve's FISTA step, entry for entry).
+__global__ void __launch_bounds__(256, 4)
+traj_forward_kernel(const __grid_constant__ TrajArgs a) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  AdjSmem& sm = *reinterpret_cast<AdjSmem*>(smraw);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const float lam = float(*a.lam);
+  for (int j = a.ja; j <= a.jb; ++j) {
+    const float mu = a.mu[j];
+    const float* Zin = a.Zs + slot_off(a, j);
+    const float* ZTin = a.ZTs + slot_off(a, j);
+    float* Zout = a.Zs + slot_off(a, j + 1);
+    float* ZTout = a.ZTs + slot_off(a, j + 1);
+    const bool ckpt = a.ck > 0 && j % a.ck == 0 && j < a.J;
+    const size_t ckoff = ckpt ? size_t(j / a.ck - 1) * size_t(a.rr) * a.rc : 0;
+    for (int tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x) {
+      int i0, j0, ni, nj;
+      tile_of(a, tile, i0, j0, ni, nj);
+      stage_nbr(sm.nb, a.Lr, a.Lc, a.rr, a.rc, i0, j0, ni, nj);
+      {
+        float o[4];
+        nbr_sum4(sm.nb.coff, sm.nb.cval, sm.nb.cdeg, sm.nb.cf0, warp * 4, lane < ni, ZTin, i0 + lane,
+                 a.Lc, a.rr, o);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) sm.ac[lane][warp * 4 + u] = o[u];
+      }
+      float ar[4];
+      nbr_sum4(sm.nb.roff, sm.nb.rval, sm.nb.rdeg, sm.nb.rf0, warp * 4, lane < nj, Zin, j0 + lane,
+               a.Lr, a.rc, ar);
+      __syncthreads();
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int r = warp * 4 + u;
+        if (r < ni && lane < nj) {
+          const int64_t i = i0 + r, jj = j0 + lane;
+          const float z = __ldcg(Zin + i * a.rc + jj);
+          const float y = __ldg(a.Yt + i * a.ldy + jj);
+          const float sp = a.S[i * a.rc + jj];
+          const float gr = fmaf(a.two_gr, ar[u], a.two_gc * sm.ac[r][lane]);
+          const float v = fmaf(-lam, gr, z);
+          const float dl = v - y;
+          const float sv = y + copysignf(fmaxf(fabsf(dl) - lam, 0.f), dl);
+          const float zn = fmaf(mu, sv - sp, sv);
+          a.S[i * a.rc + jj] = sv;
+          Zout[i * a.rc + jj] = zn;
+          sm.tl[r][lane] = zn;
+          if (ckpt) {
+            a.ckS[ckoff + i * a.rc + jj] = sv;
+            a.ckZ[ckoff + i * a.rc + jj] = zn;
+          }
+        }
+      }
+      __syncthreads();
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int c = warp * 4 + u;
+        if (c < nj && lane < ni) ZTout[int64_t(j0 + c) * a.rr + i0 + lane] = sm.tl[lane][c];
+      }
+      __syncthreads();
+    }
+    if (!grid_sync(a.bar)) return;
+  }
+}
+
+// Partial sums of dL on one staged neighbour list: for list u (first + u)
+// of the tile, entry q: sum over the 32 lanes of x[off + base] * own[u],
+// added (times scale) to P[f0 + q], or to P[tmap[f0 + q]] (the transposed
+// entry) when tmap is given. Lanes with !valid contribute 0.
+__device__ __forceinline__ void pattern_partials(const int64_t (*off)[kTileNbr], const int* deg,
+                                                 const int64_t* f0, int first, bool valid,
+                                                 const float* __restrict__ x, int64_t base,
+                                                 const CsrView& L, int64_t stride, const float own[4],
+                                                 double scale, double* __restrict__ P,
+                                                 const int64_t* __restrict__ tmap, int lane) {
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const int d = deg[first + u];
+    for (int q = 0; q < d; ++q) {
+      float xv = 0.f;
+      if (valid) {
+        const int64_t o = q < kTileNbr ? off[first + u][q]
+                                       : int64_t(__ldg(L.col + f0[first + u] + q)) * stride;
+        xv = __ldcg(x + o + base);
+      }
+      const float s = warp_sumf(xv * own[u]);
+      if (lane == 0 && s != 0.f) {
+        const int64_t e = f0[first + u] + q;
+        const int64_t t = tmap ? __ldg(tmap + e) : e;  // -1: no transposed entry
+        if (t >= 0) P[t] += scale * double(s);
+      }
+    }
+  }
+}
+
+// Reverse iterations jb down to ja over the trajectory slots.
+__global__ void __launch_bounds__(256, 4)
+traj_reverse_kernel(const __grid_constant__ TrajArgs a) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  AdjSmem& sm = *reinterpret_cast<AdjSmem*>(smraw);
+  __shared__ double red[8];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const float lam = float(*a.lam);
+  const double lamd = double(lam);
+  const int64_t nnz_r = a.Lr.rowptr[a.rr], nnz_c = a.Lc.rowptr[a.rc];
+  double s_lam = 0.0, s_gr = 0.0, s_gc = 0.0;
+  for (int j = a.jb; j >= a.ja; --j) {
+    const int par = j & 1;
+    const float* Zin = a.Zs + slot_off(a, j);
+    const float* ZTin = a.ZTs + slot_off(a, j);
+    // phase 1: mask, Vb, dY~ and scalar partials, dL partials
+    for (int tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x) {
+      int i0, j0, ni, nj;
+      tile_of(a, tile, i0, j0, ni, nj);
+      const int ti = i0 / TB, tj = j0 / TB;
+      stage_nbr(sm.nb, a.Lr, a.Lc, a.rr, a.rc, i0, j0, ni, nj);
+      {
+        float o[4];
+        nbr_sum4(sm.nb.coff, sm.nb.cval, sm.nb.cdeg, sm.nb.cf0, warp * 4, lane < ni, ZTin, i0 + lane,
+                 a.Lc, a.rr, o);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) sm.ac[lane][warp * 4 + u] = o[u];
+      }
+      float ar[4];
+      nbr_sum4(sm.nb.roff, sm.nb.rval, sm.nb.rdeg, sm.nb.rf0, warp * 4, lane < nj, Zin, j0 + lane,
+               a.Lr, a.rc, ar);
+      __syncthreads();
+      float vrow[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int r = warp * 4 + u;
+        float vb = 0.f;
+        if (r < ni && lane < nj) {
+          const int64_t i = i0 + r, jj = j0 + lane;
+          const float z = __ldcg(Zin + i * a.rc + jj);
+          const float y = __ldg(a.Yt + i * a.ldy + jj);
+          const float gr = fmaf(a.two_gr, ar[u], a.two_gc * sm.ac[r][lane]);
+          const float v = fmaf(-lam, gr, z);
+          const float dl = v - y;
+          const float sb = a.Sb[i * a.rc + jj];
+          vb = (fabsf(dl) - lam) > 0.f ? sb : 0.f;
+          a.dY[i * a.lddy + jj] += sb - vb;
+          if (vb != 0.f) {
+            s_lam += -double(copysignf(1.f, dl)) * vb - double(vb) * double(gr);
+            s_gr += -2.0 * lamd * double(vb) * double(ar[u]);
+            s_gc += -2.0 * lamd * double(vb) * double(sm.ac[r][lane]);
+          }
+          a.Vb[par][i * a.rc + jj] = vb;
+        }
+        vrow[u] = vb;
+        sm.tl[r][lane] = vb;
+      }
+      __syncthreads();
+      // transposed publish; own column values for the Lc partials
+      float vcol[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int c = warp * 4 + u;
+        vcol[u] = sm.tl[lane][c];
+        if (c < nj && lane < ni) a.VbT[par][int64_t(j0 + c) * a.rr + i0 + lane] = vcol[u];
+      }
+      // dLr(a, b) += -2 lambda gamma_r sum_c Vb(a, c) Z(b, c), c over the tile's columns
+      if (a.gamma_r != 0.0)
+        pattern_partials(sm.nb.roff, sm.nb.rdeg, sm.nb.rf0, warp * 4, lane < nj, Zin, j0 + lane, a.Lr,
+                         a.rc, vrow, -2.0 * lamd * a.gamma_r, a.Pr + int64_t(tj) * nnz_r, nullptr,
+                         lane);
+      // dLc(a, b) += -2 lambda gamma_c sum_r Z(r, a) Vb(r, b), r over the tile's rows:
+      // column b of the tile walks its own list (b, a), so the sum lands on
+      // the transposed entry (a, b)
+      if (a.gamma_c != 0.0)
+        pattern_partials(sm.nb.coff, sm.nb.cdeg, sm.nb.cf0, warp * 4, lane < ni, ZTin, i0 + lane, a.Lc,
+                         a.rr, vcol, -2.0 * lamd * a.gamma_c, a.Pc + int64_t(ti) * nnz_c, a.tmap_c,
+                         lane);
+      __syncthreads();
+    }
+    if (!grid_sync(a.bar)) return;
+    // phase 2: Zb = Vb - lambda (2 gr Lr Vb + 2 gc Vb Lc), carry to S_{j-1}, S_{j-2}
+    const float* V = a.Vb[par];
+    const float* VT = a.VbT[par];
+    const float mup = j >= 2 ? a.mu[j - 1] : 0.f;
+    for (int tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x) {
+      int i0, j0, ni, nj;
+      tile_of(a, tile, i0, j0, ni, nj);
+      stage_nbr(sm.nb, a.Lr, a.Lc, a.rr, a.rc, i0, j0, ni, nj);
+      {
+        float o[4];
+        nbr_sum4(sm.nb.coff, sm.nb.cval, sm.nb.cdeg, sm.nb.cf0, warp * 4, lane < ni, VT, i0 + lane,
+                 a.Lc, a.rr, o);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) sm.ac[lane][warp * 4 + u] = o[u];
+      }
+      float ar[4];
+      nbr_sum4(sm.nb.roff, sm.nb.rval, sm.nb.rdeg, sm.nb.rf0, warp * 4, lane < nj, V, j0 + lane, a.Lr,
+               a.rc, ar);
+      __syncthreads();
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int r = warp * 4 + u;
+        if (r < ni && lane < nj) {
+          const int64_t i = i0 + r, jj = j0 + lane;
+          const float vb = __ldcg(V + i * a.rc + jj);
+          const float g = fmaf(a.two_gr, ar[u], a.two_gc * sm.ac[r][lane]);
+          const float zb = fmaf(-lam, g, vb);
+          const int64_t l = i * a.rc + jj;
+          if (j >= 2) {
+            a.Sb[l] = fmaf(1.f + mup, zb, a.A2[l]);
+            a.A2[l] = -mup * zb;
+          } else {
+            a.dY[i * a.lddy + jj] += zb + a.A2[l];
+            a.Sb[l] = 0.f;
+            a.A2[l] = 0.f;
+          }
+        }
+      }
+      __syncthreads();
+    }
+  }
+  s_lam = block_sum(s_lam, red);
+  s_gr = block_sum(s_gr, red);
+  s_gc = block_sum(s_gc, red);
+  if (threadIdx.x == 0) {
+    atomicAdd(a.scal_bar + 0, s_lam);
+    atomicAdd(a.scal_bar + 1, s_gr);
+    atomicAdd(a.scal_bar + 2, s_gc);
+  }
+}
+
+// dL(e) = sum over parts p of P[p][e], in order.
+__global__ void reduce_parts_kernel(const double* __restrict__ P, int nparts, int64_t nnz,
+                                    double* __restrict__ out) {
+  for (int64_t e = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; e < nnz;
+       e += int64_t(gridDim.x) * blockDim.x) {
+    double s = 0.0;
+    for (int p = 0; p < nparts; ++p) s += P[int64_t(p) * nnz + e];
+    out[e] = s;
+  }
+}
+
+// ------------------------------------------------------ power iteration --
+// The solve's power iteration, with every iterate kept: u_0(i) = uniform - 1/2
+// (SplitMix64 stream 2 for Lr, 3 for Lc), u_{t+1} = (L u_t) / |u_t|, and
+// rho = u_T^T L u_T / u_T^T u_T. Reverse mode with v_t = u_t / |u_t|:
+//   vbar_T = 2 rhobar (L v_T - rho v_T), dL += rhobar v_T v_T^T;
+//   t = T..1: ubar_t = (vbar_t - v_t (v_t^T vbar_t)) / |u_t|,
+//             dL += ubar_t v_{t-1}^T, vbar_{t-1} = L ubar_t.
+struct PowGraph {
+  CsrView L;
+  int n, stream, row0;
+  float* U;       // [(T + 1) * n], iterate t at U + t * n
+  double* nrm2;   // [T + 1]
+  float* Ub;      // [T * n], ubar_t at Ub + (t - 1) * n
+  float* vb[2];   // vbar ping-pong
+  double* acc;    // [4]: ring of dot products
+  double* fin;    // [2]: u^T L u, u^T u
+  double* rho;    // out: estimate
+  const double* rho_bar;
+};
+struct PowAdjArgs {
+  PowGraph g[2];
+  int rows, T;
+  uint64_t seed;
+  int reverse;
+  GridBar bar;
+};
+
+__device__ __forceinline__ int pow_graph(const PowAdjArgs& a, int r) { return r >= a.g[1].row0 ? 1 : 0; }
+
+__device__ __forceinline__ float spmv_row(const CsrView& L, int i, const float* x, float scale, int lane) {
+  float sum = 0.f;
+  for (int64_t e = L.rowptr[i] + lane; e < L.rowptr[i + 1]; e += 32)
+    sum = fmaf(__ldg(L.val + e), __ldcg(x + __ldg(L.col + e)), sum);
+  return warp_sumf(sum) * scale;
+}
+
+__global__ void __launch_bounds__(512)
+power_adjoint_kernel(const __grid_constant__ PowAdjArgs a) {
+  const int lane = threadIdx.x & 31;
+  const int nwarp = (gridDim.x * blockDim.x) >> 5;
+  const int wid = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int nthr = gridDim.x * blockDim.x, tid = blockIdx.x * blockDim.x + threadIdx.x;
+  if (!a.reverse) {
+    for (int r = tid; r < a.rows; r += nthr) {
+      const PowGraph& G = a.g[pow_graph(a, r)];
+      const int i = r - G.row0;
+      const double x = uniform01_at(stream_state0(a.seed, G.stream), uint64_t(i) + 1) - 0.5;
+      G.U[i] = float(x);
+      atomicAdd(G.nrm2, x * x);
+    }
+    if (!grid_sync(a.bar)) return;
+    for (int t = 0; t < a.T; ++t) {
+      for (int r = wid; r < a.rows; r += nwarp) {
+        const PowGraph& G = a.g[pow_graph(a, r)];
+        const int i = r - G.row0;
+        const double n2 = __ldcg(G.nrm2 + t);
+        const float inv = n2 > 0 ? float(1.0 / sqrt(n2)) : 0.f;
+        const float s = spmv_row(G.L, i, G.U + size_t(t) * G.n, inv, lane);
+        if (lane == 0) {
+          G.U[size_t(t + 1) * G.n + i] = s;
+          atomicAdd(G.nrm2 + t + 1, double(s) * double(s));
+        }
+      }
+      if (!grid_sync(a.bar)) return;
+    }
+    for (int r = wid; r < a.rows; r += nwarp) {
+      const PowGraph& G = a.g[pow_graph(a, r)];
+      const int i = r - G.row0;
+      const float* u = G.U + size_t(a.T) * G.n;
+      const float s = spmv_row(G.L, i, u, 1.f, lane);
+      if (lane == 0) {
+        const double ui = __ldcg(u + i);
+        atomicAdd(G.fin, ui * double(s));
+        atomicAdd(G.fin + 1, ui * ui);
+      }
+    }
+    if (!grid_sync(a.bar)) return;
+    if (blockIdx.x == 0 && threadIdx.x < 2) {
+      const PowGraph& G = a.g[threadIdx.x];
+      const double num = __ldcg(G.fin), den = __ldcg(G.fin + 1);
+      *G.rho = (den > 0 && __ldcg(G.nrm2 + a.T) > 0) ? num / den : 0.0;
+    }
+    return;
+  }
+  // reverse: vbar_T = 2 rhobar (L v_T - rho v_T); dot v_T . vbar_T into acc[T % 4]
+  for (int r = wid; r < a.rows; r += nwarp) {
+    const PowGraph& G = a.g[pow_graph(a, r)];
+    const int i = r - G.row0;
+    const double n2 = __ldcg(G.nrm2 + a.T);
+    const double inv = n2 > 0 ? 1.0 / sqrt(n2) : 0.0;
+    const float* u = G.U + size_t(a.T) * G.n;
+    const float lv = spmv_row(G.L, i, u, 1.f, lane);
+    if (lane == 0) {
+      const double vi = double(__ldcg(u + i)) * inv;
+      const double vb = 2.0 * (*G.rho_bar) * (double(lv) * inv - (*G.rho) * vi);
+      G.vb[a.T & 1][i] = float(vb);
+      atomicAdd(G.acc + (a.T & 3), vi * vb);
+    }
+  }
+  if (!grid_sync(a.bar)) return;
+  for (int t = a.T; t >= 1; --t) {
+    // ubar_t = (vbar_t - v_t d_t) / |u_t|
+    for (int r = tid; r < a.rows; r += nthr) {
+      const PowGraph& G = a.g[pow_graph(a, r)];
+      const int i = r - G.row0;
+      const double n2 = __ldcg(G.nrm2 + t);
+      const double inv = n2 > 0 ? 1.0 / sqrt(n2) : 0.0;
+      const double d = __ldcg(G.acc + (t & 3));
+      const double vi = double(G.U[size_t(t) * G.n + i]) * inv;
+      G.Ub[size_t(t - 1) * G.n + i] = float((double(G.vb[t & 1][i]) - vi * d) * inv);
+    }
+    if (blockIdx.x == 0 && threadIdx.x < 2) a.g[threadIdx.x].acc[(t + 2) & 3] = 0.0;
+    if (!grid_sync(a.bar)) return;
+    // vbar_{t-1} = L ubar_t; dot v_{t-1} . vbar_{t-1}
+    for (int r = wid; r < a.rows; r += nwarp) {
+      const PowGraph& G = a.g[pow_graph(a, r)];
+      const int i = r - G.row0;
+      const float s = spmv_row(G.L, i, G.Ub + size_t(t - 1) * G.n, 1.f, lane);
+      if (lane == 0) {
+        G.vb[(t - 1) & 1][i] = s;
+        if (t > 1) {
+          const double n2 = __ldcg(G.nrm2 + t - 1);
+          const double inv = n2 > 0 ? 1.0 / sqrt(n2) : 0.0;
+          atomicAdd(G.acc + ((t - 1) & 3), double(G.U[size_t(t - 1) * G.n + i]) * inv * double(s));
+        }
+      }
+    }
+    if (!grid_sync(a.bar)) return;
+  }
+}
+
+// dL(e) += rhobar v_T(i) v_T(j) + sum_t ubar_t(i) v_{t-1}(j), e = (i, j).
+__global__ void power_pattern_kernel(PowGraph G, int T, double* __restrict__ dL) {
+  const double rb = *G.rho_bar;
+  if (rb == 0.0) return;
+  for (int i = blockIdx.x; i < G.n; i += gridDim.x)
+    for (int64_t e = G.L.rowptr[i] + threadIdx.x; e < G.L.rowptr[i + 1]; e += blockDim.x) {
+      const int j = G.L.col[e];
+      const double nT = G.nrm2[T];
+      double s = nT > 0 ? rb * double(G.U[size_t(T) * G.n + i]) * double(G.U[size_t(T) * G.n + j]) / nT : 0.0;
+      for (int t = 1; t <= T; ++t) {
+        const double n2 = G.nrm2[t - 1];
+        if (n2 > 0)
+          s += double(G.Ub[size_t(t - 1) * G.n + i]) * double(G.U[size_t(t - 1) * G.n + j]) / sqrt(n2);
+      }
+      dL[e] += s;
+    }
+}
+
+// lambda = 1/beta', beta' = 2 gamma_c n_c + 2 gamma_r n_r: the solve's step
+// and the chain rule back to gamma and the norm estimates.
+// scal: [0] n_r, [1] n_c, [2] lambda; bar: [0] dlambda, [1] dgamma_r, [2] dgamma_c,
+// out nb: [0] dn_r, [1] dn_c.
+__global__ void step_forward_kernel(double* scal, double gr, double gc, double step) {
+  if (threadIdx.x || blockIdx.x) return;
+  if (step > 0) {
+    scal[2] = step;
+  } else {
+    const double beta = 2.0 * gc * scal[1] + 2.0 * gr * scal[0];
+    scal[2] = beta > 0 ? 1.0 / beta : 1.0;
+  }
+}
+__global__ void step_backward_kernel(const double* scal, double* bar, double* nb, double gr, double gc,
+                                     double step) {
+  if (threadIdx.x || blockIdx.x) return;
+  nb[0] = nb[1] = 0.0;
+  if (step > 0) return;
+  const double beta = 2.0 * gc * scal[1] + 2.0 * gr * scal[0];
+  if (!(beta > 0)) return;
+  const double d = -bar[0] / (beta * beta);
+  bar[1] += 2.0 * scal[0] * d;
+  bar[2] += 2.0 * scal[1] * d;
+  nb[0] = 2.0 * gr * d;
+  nb[1] = 2.0 * gc * d;
+}
+
+// ------------------------------------------------------ weight chain rule --
+// The Laplacians of Sec. I as functions of the symmetric edge weights w:
+//   normalised      L_ij = -w_ij / sqrt(D_i D_j) (i != j), L_ii = [D_i > 0];
+//   combinatorial   L_ij = -w_ij, L_ii = D_i;   D_i = sum_j w_ij.
+// Given dL on the pattern, the derivative of an undirected edge {i, j}:
+//   normalised:     -(dL_ij + dL_ji) / sqrt(D_i D_j) + dD_i + dD_j,
+//                   dD_k = -sum_{l != k} (dL_kl + dL_lk) L_kl / (2 D_k);
+//   combinatorial:  -(dL_ij + dL_ji) + dL_ii + dL_jj;
+// written at both entries ij and ji (0 on the diagonal).
+__device__ __forceinline__ int64_t find_entry(const CsrView& L, int row, int col) {
+  int64_t lo = L.rowptr[row], hi = L.rowptr[row + 1];
+  while (lo < hi) {
+    const int64_t mid = (lo + hi) >> 1;
+    if (L.col[mid] < col) lo = mid + 1; else hi = mid;
+  }
+  return (lo < L.rowptr[row + 1] && L.col[lo] == col) ? lo : -1;
+}
+
+__global__ void transpose_map_kernel(CsrView L, int64_t* __restrict__ tmap) {
+  for (int i = blockIdx.x; i < L.n; i += gridDim.x)
+    for (int64_t e = L.rowptr[i] + threadIdx.x; e < L.rowptr[i + 1]; e += blockDim.x)
+      tmap[e] = find_entry(L, L.col[e], i);
+}
+
+__global__ void wchain_node_kernel(CsrView L, const float* __restrict__ w, const double* __restrict__ dL,
+                                   int lap_type, double* __restrict__ deg, double* __restrict__ dD) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < L.n; i += gridDim.x * blockDim.x) {
+    double d = 0.0, s = 0.0, diag = 0.0;
+    for (int64_t e = L.rowptr[i]; e < L.rowptr[i + 1]; ++e) {
+      const int j = L.col[e];
+      if (j == i) {
+        diag = dL[e];
+        continue;
+      }
+      d += double(w[e]);
+      const int64_t et = find_entry(L, j, i);
+      s += (dL[e] + (et >= 0 ? dL[et] : 0.0)) * double(L.val[e]);
+    }
+    deg[i] = d;
+    if (lap_type == 1) dD[i] = diag;
+    else dD[i] = d > 0 ? -s / (2.0 * d) : 0.0;
+  }
+}
+
+__global__ void wchain_edge_kernel(CsrView L, const double* __restrict__ dL, int lap_type,
+                                   const double* __restrict__ deg, const double* __restrict__ dD,
+                                   float* __restrict__ dw) {
+  for (int i = blockIdx.x; i < L.n; i += gridDim.x)
+    for (int64_t e = L.rowptr[i] + threadIdx.x; e < L.rowptr[i + 1]; e += blockDim.x) {
+      const int j = L.col[e];
+      if (j == i) {
+        dw[e] = 0.f;
+        continue;
+      }
+      const int64_t et = find_entry(L, j, i);
+      const double both = dL[e] + (et >= 0 ? dL[et] : 0.0);
+      double g;
+      if (lap_type == 1) g = -both + dD[i] + dD[j];
+      else g = -both / sqrt(deg[i] * deg[j]) + dD[i] + dD[j];
+      dw[e] = float(g);
+    }
+}
+
+// Laplacian values from the weights (Sec. I): D_i = sum_j w_ij in FP64;
+// normalised: -w_ij / sqrt(D_i D_j) off the diagonal, [D_i > 0] on it;
+// combinatorial: -w_ij, D_i.
+__global__ void degree_kernel(CsrView L, const float* __restrict__ w, double* __restrict__ deg) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < L.n; i += gridDim.x * blockDim.x) {
+    double d = 0.0;
+    for (int64_t e = L.rowptr[i]; e < L.rowptr[i + 1]; ++e)
+      if (L.col[e] != i) d += double(w[e]);
+    deg[i] = d;
+  }
+}
+__global__ void lap_values_kernel(CsrView L, const float* __restrict__ w, const double* __restrict__ deg,
+                                  int lap_type, float* __restrict__ val) {
+  for (int i = blockIdx.x; i < L.n; i += gridDim.x)
+    for (int64_t e = L.rowptr[i] + threadIdx.x; e < L.rowptr[i + 1]; e += blockDim.x) {
+      const int j = L.col[e];
+      double v;
+      if (lap_type == 1) v = j == i ? deg[i] : -double(w[e]);
+      else if (j == i) v = deg[i] > 0 ? 1.0 : 0.0;
+      else v = (deg[i] > 0 && deg[j] > 0) ? -double(w[e]) / sqrt(deg[i] * deg[j]) : 0.0;
+      val[e] = float(v);
+    }
+}
+
+struct BwdWs {
+  float* mu;
+  double* scal;      // [4]: n_r, n_c, lambda
+  double* bar;       // [4]: dlambda, dgamma_r, dgamma_c
+  double* nb;        // [2]: dn_r, dn_c
+  float *S, *Sb, *A2, *Vb[2], *VbT[2];
+  float *Zs, *ZTs;
+  float *ckS, *ckZ;
+  double *Pr, *Pc;
+  double *dLr, *dLc;
+  double *deg, *dD;
+  int64_t* tmap_c;
+  float* U[2];
+  double* nrm2[2];
+  float* Ub[2];
+  float* vb[2][2];
+  double* pacc;      // [2][4] + fin [2][2] + rho [2]
+  unsigned int* bar_cnt;
+  int* err;
+  size_t bytes;
+};
+
+BwdWs bwd_layout(void* ws, int rr, int rc, int J, int ck, int T, int64_t nnz_r, int64_t nnz_c) {
+  Carve c(ws);
+  BwdWs w{};
+  const size_t mn = size_t(rr) * rc;
+  const int nseg = (J + ck - 1) / ck;
+  const int nslot = std::max(ck, 2);
+  w.mu = c.take<float>(size_t(J) + 2);
+  w.scal = c.take<double>(4);
+  w.bar = c.take<double>(4);
+  w.nb = c.take<double>(2);
+  w.S = c.take<float>(mn);
+  w.Sb = c.take<float>(mn);
+  w.A2 = c.take<float>(mn);
+  for (int p = 0; p < 2; ++p) {
+    w.Vb[p] = c.take<float>(mn);
+    w.VbT[p] = c.take<float>(mn);
+  }
+  w.Zs = c.take<float>(mn * nslot);
+  w.ZTs = c.take<float>(mn * nslot);
+  w.ckS = c.take<float>(mn * std::max(nseg - 1, 1));
+  w.ckZ = c.take<float>(mn * std::max(nseg - 1, 1));
+  w.Pr = c.take<double>(size_t(ceil_div(rc, TB)) * std::max<int64_t>(nnz_r, 1));
+  w.Pc = c.take<double>(size_t(ceil_div(rr, TB)) * std::max<int64_t>(nnz_c, 1));
+  w.dLr = c.take<double>(std::max<int64_t>(nnz_r, 1));
+  w.dLc = c.take<double>(std::max<int64_t>(nnz_c, 1));
+  w.deg = c.take<double>(std::max(rr, rc));
+  w.dD = c.take<double>(std::max(rr, rc));
+  w.tmap_c = c.take<int64_t>(std::max<int64_t>(nnz_c, 1));
+  for (int g = 0; g < 2; ++g) {
+    const int n = g ? rc : rr;
+    w.U[g] = c.take<float>(size_t(T + 1) * n);
+    w.nrm2[g] = c.take<double>(size_t(T) + 1);
+    w.Ub[g] = c.take<float>(size_t(std::max(T, 1)) * n);
+    w.vb[g][0] = c.take<float>(n);
+    w.vb[g][1] = c.take<float>(n);
+  }
+  w.pacc = c.take<double>(16);
+  w.bar_cnt = c.take<unsigned int>(kBarrierCounters + 1);
+  w.err = c.take<int>(1);
+  w.bytes = c.bytes();
+  return w;
+}
+
+cpca_status reset_barrier(const BwdWs& w, cudaStream_t st) {
+  CPCA_CUDA(cudaMemsetAsync(w.bar_cnt, 0, sizeof(unsigned int) * (kBarrierCounters + 1), st));
+  return CPCA_OK;
+}
+
+cpca_status run_power(PowAdjArgs& pa, const BwdWs& w, int reverse, cudaStream_t st) {
+  pa.reverse = reverse;
+  CPCA_TRY(reset_barrier(w, st));
+  const int want = ceil_div(int64_t(pa.rows) * 32, 512);
+  const int grid = coop_blocks((const void*)power_adjoint_kernel, 512, 0, std::max(want, 1));
+  void* args[] = {&pa};
+  CPCA_PROF(reverse ? "adj_power_rev" : "adj_power_fwd", st);
+  CPCA_CUDA(cudaLaunchCooperativeKernel((void*)power_adjoint_kernel, dim3(grid), dim3(512), args, 0, st));
+  CPCA_LAUNCHED();
+  return CPCA_OK;
+}
+
+cpca_status weight_chain(const CsrView& L, const float* w, const double* dL, int lap_type, float* dw,
+                         const BwdWs& ws, cudaStream_t st) {
+  const unsigned g = std::min<unsigned>(ceil_div(L.n, 256), num_sms() * 4);
+  wchain_node_kernel<<<g, 256, 0, st>>>(L, w, dL, lap_type, ws.deg, ws.dD);
+  CPCA_LAUNCHED();
+  wchain_edge_kernel<<<std::min(L.n, num_sms() * 8), 64, 0, st>>>(L, dL, lap_type, ws.deg, ws.dD, dw);
+  CPCA_LAUNCHED();
+  return CPCA_OK;
+}
+
+}  // namespace
+
+// Chain rule from dL (FP64, on the CSR pattern) to the edge weights; shared
+// with the decoder's derivative.
+cpca_status laplacian_weight_grad(const CsrView& L, const float* w, const double* dL, int lap_type,
+                                  float* dw, double* deg, double* dD, cudaStream_t st) {
+  BwdWs ws{};
+  ws.deg = deg;
+  ws.dD = dD;
+  return weight_chain(L, w, dL, lap_type, dw, ws, st);
+}
+
+}  // namespace cpca
+
+using namespace cpca;
+
+extern "C" size_t cpca_frpcag_backward_workspace_size(int32_t rr, int32_t rc, int32_t max_iter,
+                                                      int32_t ckpt_every, int32_t power_iters,
+                                                      int64_t nnz_r, int64_t nnz_c) {
+  if (rr <= 0 || rc <= 0 || max_iter < 1 || ckpt_every < 0 || power_iters < 0 || nnz_r < 0 || nnz_c < 0)
+    return 0;
+  const int ck = std::min(ckpt_every > 0 ? ckpt_every : 20, int(max_iter));
+  return bwd_layout(nullptr, rr, rc, max_iter, ck, power_iters, nnz_r, nnz_c).bytes;
+}
+
+extern "C" cpca_status cpca_frpcag_backward(const float* Yt, int32_t rr, int32_t rc, int64_t ldyt,
+                                            const cpca_csr* Lr, const cpca_csr* Lc,
+                                            const cpca_frpcag_params* prm, int32_t ckpt_every,
+                                            const float* dX, int64_t lddx, float* dYt, int64_t lddyt,
+                                            double* dLr, double* dLc, const float* wr, const float* wc,
+                                            int32_t lap_type, float* dwr, float* dwc,
+                                            cpca_frpcag_grad_info* ginfo, void* ws, size_t ws_bytes,
+                                            void* stream) {
+  clear_error();
+  CPCA_CHECK_ARG(Yt && dX && dYt && prm, "cpca_frpcag_backward: null pointer");
+  CPCA_CHECK_ARG(rr > 0 && rc > 0, "cpca_frpcag_backward: empty matrix");
+  CPCA_CHECK_ARG(ldyt >= rc && lddx >= rc && lddyt >= rc, "cpca_frpcag_backward: leading dimension < rc");
+  CPCA_CHECK_ARG(prm->max_iter >= 1, "cpca_frpcag_backward: max_iter < 1");
+  CPCA_CHECK_ARG(prm->eps == 0.0, "cpca_frpcag_backward: needs a fixed iteration count (eps = 0)");
+  CPCA_CHECK_ARG(prm->gamma_r >= 0 && prm->gamma_c >= 0, "cpca_frpcag_backward: negative gamma");
+  CPCA_CHECK_ARG(prm->step > 0 || prm->power_iters >= 1, "cpca_frpcag_backward: power_iters < 1");
+  CPCA_CHECK_ARG(ckpt_every >= 0, "cpca_frpcag_backward: ckpt_every < 0");
+  CPCA_CHECK_ARG(lap_type == CPCA_LAP_NORMALIZED || lap_type == CPCA_LAP_COMBINATORIAL,
+                 "cpca_frpcag_backward: unknown lap_type");
+  CPCA_CHECK_ARG(!dwr || wr, "cpca_frpcag_backward: dwr needs the weights wr");
+  CPCA_CHECK_ARG(!dwc || wc, "cpca_frpcag_backward: dwc needs the weights wc");
+  CPCA_TRY(check_csr(Lr, rr, "cpca_frpcag_backward(Lr)"));
+  CPCA_TRY(check_csr(Lc, rc, "cpca_frpcag_backward(Lc)"));
+  const int J = prm->max_iter;
+  const int ck = std::min(ckpt_every > 0 ? ckpt_every : 20, J);
+  const int T = prm->step > 0 ? 0 : prm->power_iters;
+  const BwdWs w = bwd_layout(ws, rr, rc, J, ck, T, Lr->nnz, Lc->nnz);
+  if (!ws || ws_bytes < w.bytes) {
+    set_error("cpca_frpcag_backward: workspace %zu bytes < required %zu", ws_bytes, w.bytes);
+    return CPCA_ERR_WORKSPACE;
+  }
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const CsrView lr{Lr->n, Lr->rowptr, Lr->col, Lr->val};
+  const CsrView lc{Lc->n, Lc->rowptr, Lc->col, Lc->val};
+  const size_t mn = size_t(rr) * rc;
+  CPCA_CUDA(cudaMemsetAsync(w.err, 0, sizeof(int), st));
+  CPCA_CUDA(cudaMemsetAsync(w.scal, 0, 4 * sizeof(double), st));
+  CPCA_CUDA(cudaMemsetAsync(w.bar, 0, 4 * sizeof(double), st));
+  CPCA_CUDA(cudaMemsetAsync(w.pacc, 0, 16 * sizeof(double), st));
+
+  // power iterations with the iterates kept, then lambda
+  PowAdjArgs pa{};
+  pa.rows = rr + rc;
+  pa.T = T;
+  pa.seed = prm->power_seed;
+  pa.bar = GridBar{w.bar_cnt, w.bar_cnt + kBarrierCounters, w.err};
+  for (int g = 0; g < 2; ++g) {
+    PowGraph& G = pa.g[g];
+    G.L = g ? lc : lr;
+    G.n = g ? rc : rr;
+    G.stream = g ? 3 : 2;
+    G.row0 = g ? rr : 0;
+    G.U = w.U[g];
+    G.nrm2 = w.nrm2[g];
+    G.Ub = w.Ub[g];
+    G.vb[0] = w.vb[g][0];
+    G.vb[1] = w.vb[g][1];
+    G.acc = w.pacc + 4 * g;
+    G.fin = w.pacc + 8 + 2 * g;
+    G.rho = w.scal + g;
+    G.rho_bar = w.nb + g;
+  }
+  if (T > 0) {
+    for (int g = 0; g < 2; ++g)
+      CPCA_CUDA(cudaMemsetAsync(w.nrm2[g], 0, sizeof(double) * (T + 1), st));
+    CPCA_TRY(run_power(pa, w, 0, st));
+  }
+  step_forward_kernel<<<1, 32, 0, st>>>(w.scal, prm->gamma_r, prm->gamma_c, prm->step);
+  CPCA_LAUNCHED();
+  mu_kernel<<<1, 32, 0, st>>>(J, w.mu);
+  CPCA_LAUNCHED();
+
+  // trajectory sweeps
+  TrajArgs a{};
+  a.Yt = Yt;
+  a.ldy = ldyt;
+  a.rr = rr;
+  a.rc = rc;
+  a.ntj = ceil_div(rc, TB);
+  a.ntiles = int(ceil_div(rr, TB) * int64_t(a.ntj));
+  a.Lr = lr;
+  a.Lc = lc;
+  a.lam = w.scal + 2;
+  a.two_gr = float(2.0 * prm->gamma_r);
+  a.two_gc = float(2.0 * prm->gamma_c);
+  a.gamma_r = prm->gamma_r;
+  a.gamma_c = prm->gamma_c;
+  a.mu = w.mu;
+  a.S = w.S;
+  a.Zs = w.Zs;
+  a.ZTs = w.ZTs;
+  a.J = J;
+  a.ckS = w.ckS;
+  a.ckZ = w.ckZ;
+  a.Sb = w.Sb;
+  a.A2 = w.A2;
+  for (int p = 0; p < 2; ++p) {
+    a.Vb[p] = w.Vb[p];
+    a.VbT[p] = w.VbT[p];
+  }
+  a.dY = dYt;
+  a.lddy = lddyt;
+  a.Pr = w.Pr;
+  a.Pc = w.Pc;
+  a.scal_bar = w.bar;
+  a.tmap_c = w.tmap_c;
+  a.bar = GridBar{w.bar_cnt, w.bar_cnt + kBarrierCounters, w.err};
+  transpose_map_kernel<<<std::max(1, std::min(rc, num_sms() * 8)), 64, 0, st>>>(lc, w.tmap_c);
+  CPCA_LAUNCHED();
+  const size_t smem = sizeof(AdjSmem);
+  static bool attr = false;
+  if (!attr) {
+    CPCA_CUDA(cudaFuncSetAttribute((const void*)traj_forward_kernel,
+                                   cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
+    CPCA_CUDA(cudaFuncSetAttribute((const void*)traj_reverse_kernel,
+                                   cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
+    attr = true;
+  }
+  const int gf = coop_blocks((const void*)traj_forward_kernel, 256, smem, a.ntiles);
+  const int gb = coop_blocks((const void*)traj_reverse_kernel, 256, smem, a.ntiles);
+  const int nseg = (J + ck - 1) / ck;
+  const unsigned gs = std::min<unsigned>(a.ntiles, num_sms() * 8);
+  auto launch = [&](const void* k, int grid, const char* name) -> cpca_status {
+    CPCA_TRY(reset_barrier(w, st));
+    void* args[] = {&a};
+    CPCA_PROF(name, st);
+    CPCA_CUDA(cudaLaunchCooperativeKernel(k, dim3(grid), dim3(256), args, smem, st));
+    CPCA_LAUNCHED();
+    return CPCA_OK;
+  };
+  // forward pass with checkpoints at j = ck, 2 ck, ..., (nseg - 1) ck
+  if (nseg > 1) {
+    seed_kernel<<<gs, 256, 0, st>>>(Yt, ldyt, Yt, ldyt, rr, rc, w.Zs, w.ZTs, w.S);
+    CPCA_LAUNCHED();
+    a.jbase = 1;
+    a.nslot = 2;
+    a.ja = 1;
+    a.jb = (nseg - 1) * ck;
+    a.ck = ck;
+    CPCA_TRY(launch((const void*)traj_forward_kernel, gf, "adj_fista_fwd"));
+  }
+  // reverse, segment by segment
+  CPCA_CUDA(cudaMemcpy2DAsync(w.Sb, sizeof(float) * rc, dX, sizeof(float) * lddx, sizeof(float) * rc, rr,
+                              cudaMemcpyDeviceToDevice, st));
+  CPCA_CUDA(cudaMemsetAsync(w.A2, 0, sizeof(float) * mn, st));
+  CPCA_CUDA(cudaMemset2DAsync(dYt, sizeof(float) * lddyt, 0, sizeof(float) * rc, rr, st));
+  CPCA_CUDA(cudaMemsetAsync(w.Pr, 0, sizeof(double) * a.ntj * std::max<int64_t>(Lr->nnz, 1), st));
+  CPCA_CUDA(cudaMemsetAsync(w.Pc, 0, sizeof(double) * ceil_div(rr, TB) * std::max<int64_t>(Lc->nnz, 1), st));
+  for (int m = nseg - 1; m >= 0; --m) {
+    const int j0 = m * ck, j1 = std::min(J, j0 + ck);
+    if (m == 0) {
+      seed_kernel<<<gs, 256, 0, st>>>(Yt, ldyt, Yt, ldyt, rr, rc, w.Zs, w.ZTs, w.S);
+    } else {
+      const size_t off = size_t(m - 1) * mn;
+      seed_kernel<<<gs, 256, 0, st>>>(w.ckZ + off, rc, w.ckS + off, rc, rr, rc, w.Zs, w.ZTs, w.S);
+    }
+    CPCA_LAUNCHED();
+    a.jbase = j0 + 1;
+    a.nslot = ck;
+    a.ck = 0;
+    if (j1 - 1 >= j0 + 1) {
+      a.ja = j0 + 1;
+      a.jb = j1 - 1;
+      CPCA_TRY(launch((const void*)traj_forward_kernel, gf, "adj_fista_fwd"));
+    }
+    a.ja = j0 + 1;
+    a.jb = j1;
+    CPCA_TRY(launch((const void*)traj_reverse_kernel, gb, "adj_fista_rev"));
+  }
+  double* oLr = dLr ? dLr : w.dLr;
+  double* oLc = dLc ? dLc : w.dLc;
+  if (Lr->nnz > 0) {
+    reduce_parts_kernel<<<std::min<unsigned>(ceil_div(Lr->nnz, 256), num_sms() * 4), 256, 0, st>>>(
+        w.Pr, a.ntj, Lr->nnz, oLr);
+    CPCA_LAUNCHED();
+  }
+  if (Lc->nnz > 0) {
+    reduce_parts_kernel<<<std::min<unsigned>(ceil_div(Lc->nnz, 256), num_sms() * 4), 256, 0, st>>>(
+        w.Pc, int(ceil_div(rr, TB)), Lc->nnz, oLc);
+    CPCA_LAUNCHED();
+  }
+  // lambda -> gamma and the norm estimates -> power iterations
+  step_backward_kernel<<<1, 32, 0, st>>>(w.scal, w.bar, w.nb, prm->gamma_r, prm->gamma_c, prm->step);
+  CPCA_LAUNCHED();
+  if (T > 0) {
+    CPCA_CUDA(cudaMemsetAsync(w.pacc, 0, 8 * sizeof(double), st));
+    CPCA_TRY(run_power(pa, w, 1, st));
+    for (int g = 0; g < 2; ++g) {
+      const PowGraph& G = pa.g[g];
+      power_pattern_kernel<<<std::min(G.n, num_sms() * 8), 64, 0, st>>>(G, T, g ? oLc : oLr);
+      CPCA_LAUNCHED();
+    }
+  }
+  if (dwr) CPCA_TRY(weight_chain(lr, wr, oLr, lap_type, dwr, w, st));
+  if (dwc) CPCA_TRY(weight_chain(lc, wc, oLc, lap_type, dwc, w, st));
+  double hs[4], hb[4], hn[2];
+  int err = 0;
+  CPCA_CUDA(cudaMemcpyAsync(hs, w.scal, sizeof(hs), cudaMemcpyDeviceToHost, st));
+  CPCA_CUDA(cudaMemcpyAsync(hb, w.bar, sizeof(hb), cudaMemcpyDeviceToHost, st));
+  CPCA_CUDA(cudaMemcpyAsync(hn, w.nb, sizeof(hn), cudaMemcpyDeviceToHost, st));
+  CPCA_CUDA(cudaMemcpyAsync(&err, w.err, sizeof(int), cudaMemcpyDeviceToHost, st));
+  CPCA_CUDA(cudaStreamSynchronize(st));
+  if (err) {
+    set_error("cpca_frpcag_backward: grid barrier timed out");
+    return CPCA_ERR_TIMEOUT;
+  }
+  if (ginfo) {
+    ginfo->dgamma_r = hb[1];
+    ginfo->dgamma_c = hb[2];
+    ginfo->dlambda = hb[0];
+    ginfo->dnorm_r = hn[0];
+    ginfo->dnorm_c = hn[1];
+    ginfo->lambda = hs[2];
+    ginfo->norm_r = hs[0];
+    ginfo->norm_c = hs[1];
+  }
+  return CPCA_OK;
+}
+
+static cpca_status check_pattern(const cpca_csr* L, const char* who) {
+  CPCA_CHECK_ARG(L && L->rowptr && L->n >= 0 && L->nnz >= 0 && (L->nnz == 0 || L->col),
+                 "%s: bad CSR pattern", who);
+  return CPCA_OK;
+}
+
+extern "C" size_t cpca_laplacian_workspace_size(int32_t n) {
+  return n < 0 ? 0 : 2 * sizeof(double) * size_t(std::max(n, 1)) + 256;
+}
+
+extern "C" cpca_status cpca_laplacian_values(const cpca_csr* pattern, const float* w, int32_t lap_type,
+                                             float* val, void* ws, size_t ws_bytes, void* stream) {
+  clear_error();
+  CPCA_TRY(check_pattern(pattern, "cpca_laplacian_values"));
+  CPCA_CHECK_ARG(w && val, "cpca_laplacian_values: null pointer");
+  CPCA_CHECK_ARG(lap_type == CPCA_LAP_NORMALIZED || lap_type == CPCA_LAP_COMBINATORIAL,
+                 "cpca_laplacian_values: unknown lap_type");
+  if (!ws || ws_bytes < cpca_laplacian_workspace_size(pattern->n)) {
+    set_error("cpca_laplacian_values: workspace too small");
+    return CPCA_ERR_WORKSPACE;
+  }
+  if (pattern->n == 0) return CPCA_OK;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const CsrView L{pattern->n, pattern->rowptr, pattern->col, nullptr};
+  double* deg = static_cast<double*>(ws);
+  degree_kernel<<<std::min<unsigned>(ceil_div(L.n, 256), num_sms() * 4), 256, 0, st>>>(L, w, deg);
+  CPCA_LAUNCHED();
+  lap_values_kernel<<<std::min(L.n, num_sms() * 8), 64, 0, st>>>(L, w, deg, lap_type, val);
+  CPCA_LAUNCHED();
+  return CPCA_OK;
+}
+
+extern "C" cpca_status cpca_laplacian_weight_grad(const cpca_csr* L, const float* w, const double* dL,
+                                                  int32_t lap_type, float* dw, void* ws, size_t ws_bytes,
+                                                  void* stream) {
+  clear_error();
+  CPCA_TRY(check_pattern(L, "cpca_laplacian_weight_grad"));
+  CPCA_CHECK_ARG(w && dL && dw && (L->nnz == 0 || L->val), "cpca_laplacian_weight_grad: null pointer");
+  CPCA_CHECK_ARG(lap_type == CPCA_LAP_NORMALIZED || lap_type == CPCA_LAP_COMBINATORIAL,
+                 "cpca_laplacian_weight_grad: unknown lap_type");
+  if (!ws || ws_bytes < cpca_laplacian_workspace_size(L->n)) {
+    set_error("cpca_laplacian_weight_grad: workspace too small");
+    return CPCA_ERR_WORKSPACE;
+  }
+  if (L->n == 0) return CPCA_OK;
+  const CsrView lv{L->n, L->rowptr, L->col, L->val};
+  double* deg = static_cast<double*>(ws);
+  return laplacian_weight_grad(lv, w, dL, lap_type, dw, deg, deg + std::max(L->n, 1),
+                               static_cast<cudaStream_t>(stream));
+}

@@ -332,6 +332,7 @@ struct CgSide {
   float* minv;           // [m]: 1 / L_aa diagonal (Jacobi)
   const float* R;        // rho x ldr: U~ or V~
   int ldr;
+  const float* rhs;      // optional m x k right-hand side (replaces -L_ab R)
   float *x, *r, *z, *p0, *p1, *q;  // m x k
 };
 
@@ -514,9 +515,13 @@ cg_kernel(CgArgs a) {
       const int64_t l = int64_t(t) * k + mycol;
       const int node = S.abar[t];
       float bv = 0.f;
-      for (int64_t e = S.L.rowptr[node]; e < S.L.rowptr[node + 1]; ++e) {
-        const int ps = S.pos[S.L.col[e]];
-        if (ps < 0) bv = fmaf(-S.L.val[e], S.R[int64_t(-ps - 1) * S.ldr + mycol], bv);
+      if (S.rhs) {
+        bv = S.rhs[l];
+      } else {
+        for (int64_t e = S.L.rowptr[node]; e < S.L.rowptr[node + 1]; ++e) {
+          const int ps = S.pos[S.L.col[e]];
+          if (ps < 0) bv = fmaf(-S.L.val[e], S.R[int64_t(-ps - 1) * S.ldr + mycol], bv);
+        }
       }
       const float zv = S.minv[t] * bv;
       S.r[l] = bv;
@@ -911,6 +916,92 @@ static cpca_status partial_svd(const float* Xt, int rr, int rc, int64_t ldxt, in
   return CPCA_OK;
 }
 
+
+// Sides 0 (U on Lr) and 1 (V on Lc) of the upsampling solves: index maps,
+// the reduced L_aa CSR, and the PCG arguments over the workspace vectors.
+static cpca_status cg_setup(CgArgs& a, const cpca_csr* Lr, const cpca_csr* Lc, const int32_t* omega_r,
+                            const int32_t* omega_c, int p, int n, int rr, int rc, int k, int b,
+                            const cpca_decode_params* prm, const DecodeWs& w, cudaStream_t st) {
+  const CsrView lr{Lr->n, Lr->rowptr, Lr->col, Lr->val};
+  const CsrView lc{Lc->n, Lc->rowptr, Lc->col, Lc->val};
+  const int m[2] = {p - rr, n - rc};
+  for (int sd = 0; sd < 2; ++sd) {
+    CgSide& S = a.s[sd];
+    S.N = sd ? n : p;
+    S.rho = sd ? rc : rr;
+    S.m = m[sd];
+    S.L = sd ? lc : lr;
+    S.omega = sd ? omega_c : omega_r;
+    S.pos = sd ? w.pos1 : w.pos0;
+    S.abar = sd ? w.abar1 : w.abar0;
+    S.reach = sd ? w.reach1 : w.reach0;
+    S.rp = sd ? w.rp1 : w.rp0;
+    S.rcol = sd ? w.rcol1 : w.rcol0;
+    S.rval = sd ? w.rval1 : w.rval0;
+    S.minv = sd ? w.minv1 : w.minv0;
+    S.R = sd ? w.Vt : w.Ut;
+    S.ldr = b;
+    S.rhs = nullptr;
+    S.x = w.vec[sd][0];
+    S.r = w.vec[sd][1];
+    S.z = w.vec[sd][2];
+    S.p0 = w.vec[sd][3];
+    S.p1 = w.vec[sd][4];
+    S.q = w.vec[sd][5];
+    a.maxit[sd] = prm->cg_max_iter > 0 ? prm->cg_max_iter : 10 * std::max(m[sd], 1);
+  }
+  a.k = k;
+  a.tol = prm->cg_tol;
+  a.bar = GridBar{w.bar, w.bar + kBarrierCounters, w.err};
+  a.acc = w.acc;
+  a.acc_init = w.acc_init;
+  a.out_iters = w.out_iters;
+  a.out_res = w.out_res;
+  a.status = w.status;
+  a.changed = w.changed;
+  dim3 sg(std::min<unsigned>(ceil_div(std::max(p, n), 256), num_sms() * 4), 2);
+  cg_setup_kernel<<<sg, 256, 0, st>>>(a.s[0], a.s[1]);
+  CPCA_LAUNCHED();
+  laa_count_kernel<<<sg, 256, 0, st>>>(a.s[0], a.s[1]);
+  CPCA_LAUNCHED();
+  laa_scan_kernel<<<2, 1024, 0, st>>>(a.s[0], a.s[1]);
+  CPCA_LAUNCHED();
+  laa_fill_kernel<<<sg, 256, 0, st>>>(a.s[0], a.s[1]);
+  CPCA_LAUNCHED();
+  return CPCA_OK;
+}
+
+// One cooperative PCG launch over both sides; synchronises and returns the
+// per-column iteration counts, residuals and the status bits.
+static cpca_status cg_solve(CgArgs& a, const DecodeWs& w, cudaStream_t st, int* cg_iters,
+                            double* cg_res, int* breakdown) {
+  CPCA_CUDA(cudaMemsetAsync(w.acc, 0, sizeof(double) * 2 * 3 * 2 * KMAX_LIMIT, st));
+  CPCA_CUDA(cudaMemsetAsync(w.acc_init, 0, sizeof(double) * 3 * 2 * KMAX_LIMIT, st));
+  CPCA_CUDA(cudaMemsetAsync(w.bar, 0, (kBarrierCounters + 1) * sizeof(unsigned int), st));
+  CPCA_CUDA(cudaMemsetAsync(w.err, 0, sizeof(int), st));
+  CPCA_CUDA(cudaMemsetAsync(w.status, 0, sizeof(int), st));
+  CPCA_CUDA(cudaMemsetAsync(w.changed, 0, 3 * sizeof(unsigned int), st));
+  int occ = 0;
+  CPCA_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, cg_kernel, 256, 0));
+  const int64_t items = int64_t(a.s[0].m + a.s[1].m) * a.k;
+  const int grid = int(std::max<int64_t>(1, std::min<int64_t>(int64_t(occ) * num_sms(),
+                                                               std::max<int64_t>(1, ceil_div(items, 256)))));
+  void* args[] = {&a};
+  CPCA_PROF("cg_pcg", st);
+  CPCA_CUDA(cudaLaunchCooperativeKernel((void*)cg_kernel, dim3(grid), dim3(256), args, 0, st));
+  CPCA_LAUNCHED();
+  int err = 0;
+  CPCA_CUDA(cudaMemcpyAsync(&err, w.err, sizeof(int), cudaMemcpyDeviceToHost, st));
+  CPCA_CUDA(cudaMemcpyAsync(breakdown, w.status, sizeof(int), cudaMemcpyDeviceToHost, st));
+  CPCA_CUDA(cudaMemcpyAsync(cg_iters, w.out_iters, sizeof(int) * 2 * KMAX_LIMIT, cudaMemcpyDeviceToHost, st));
+  CPCA_CUDA(cudaMemcpyAsync(cg_res, w.out_res, sizeof(double) * 2 * KMAX_LIMIT, cudaMemcpyDeviceToHost, st));
+  CPCA_CUDA(cudaStreamSynchronize(st));
+  if (err) {
+    set_error("cpca_decode: PCG grid barrier timed out");
+    return CPCA_ERR_TIMEOUT;
+  }
+  return CPCA_OK;
+}
 }  // namespace cpca
 
 using namespace cpca;
@@ -965,76 +1056,8 @@ extern "C" cpca_status cpca_decode(const float* Xt, int32_t rr, int32_t rc, int6
   int breakdown = 0;
   if (k > 0) {
     CgArgs a{};
-    const CsrView lr{Lr->n, Lr->rowptr, Lr->col, Lr->val};
-    const CsrView lc{Lc->n, Lc->rowptr, Lc->col, Lc->val};
-    const int m[2] = {p - rr, n - rc};
-    for (int sd = 0; sd < 2; ++sd) {
-      CgSide& S = a.s[sd];
-      S.N = sd ? n : p;
-      S.rho = sd ? rc : rr;
-      S.m = m[sd];
-      S.L = sd ? lc : lr;
-      S.omega = sd ? omega_c : omega_r;
-      S.pos = sd ? w.pos1 : w.pos0;
-      S.abar = sd ? w.abar1 : w.abar0;
-      S.reach = sd ? w.reach1 : w.reach0;
-      S.rp = sd ? w.rp1 : w.rp0;
-      S.rcol = sd ? w.rcol1 : w.rcol0;
-      S.rval = sd ? w.rval1 : w.rval0;
-      S.minv = sd ? w.minv1 : w.minv0;
-      S.R = sd ? w.Vt : w.Ut;
-      S.ldr = b;
-      S.x = w.vec[sd][0];
-      S.r = w.vec[sd][1];
-      S.z = w.vec[sd][2];
-      S.p0 = w.vec[sd][3];
-      S.p1 = w.vec[sd][4];
-      S.q = w.vec[sd][5];
-      a.maxit[sd] = prm->cg_max_iter > 0 ? prm->cg_max_iter : 10 * std::max(m[sd], 1);
-    }
-    a.k = k;
-    a.tol = prm->cg_tol;
-    a.bar = GridBar{w.bar, w.bar + kBarrierCounters, w.err};
-    a.acc = w.acc;
-    a.acc_init = w.acc_init;
-    a.out_iters = w.out_iters;
-    a.out_res = w.out_res;
-    a.status = w.status;
-    a.changed = w.changed;
-    dim3 sg(std::min<unsigned>(ceil_div(std::max(p, n), 256), num_sms() * 4), 2);
-    cg_setup_kernel<<<sg, 256, 0, st>>>(a.s[0], a.s[1]);
-    CPCA_LAUNCHED();
-    laa_count_kernel<<<sg, 256, 0, st>>>(a.s[0], a.s[1]);
-    CPCA_LAUNCHED();
-    laa_scan_kernel<<<2, 1024, 0, st>>>(a.s[0], a.s[1]);
-    CPCA_LAUNCHED();
-    laa_fill_kernel<<<sg, 256, 0, st>>>(a.s[0], a.s[1]);
-    CPCA_LAUNCHED();
-    CPCA_CUDA(cudaMemsetAsync(w.acc, 0, sizeof(double) * 2 * 3 * 2 * KMAX_LIMIT, st));
-    CPCA_CUDA(cudaMemsetAsync(w.acc_init, 0, sizeof(double) * 3 * 2 * KMAX_LIMIT, st));
-    CPCA_CUDA(cudaMemsetAsync(w.bar, 0, (kBarrierCounters + 1) * sizeof(unsigned int), st));
-    CPCA_CUDA(cudaMemsetAsync(w.err, 0, sizeof(int), st));
-    CPCA_CUDA(cudaMemsetAsync(w.status, 0, sizeof(int), st));
-    CPCA_CUDA(cudaMemsetAsync(w.changed, 0, 3 * sizeof(unsigned int), st));
-    int occ = 0;
-    CPCA_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, cg_kernel, 256, 0));
-    const int64_t items = int64_t(m[0] + m[1]) * k;
-    const int grid = int(std::max<int64_t>(1, std::min<int64_t>(int64_t(occ) * num_sms(),
-                                                                 std::max<int64_t>(1, ceil_div(items, 256)))));
-    void* args[] = {&a};
-    CPCA_PROF("cg_pcg", st);
-    CPCA_CUDA(cudaLaunchCooperativeKernel((void*)cg_kernel, dim3(grid), dim3(256), args, 0, st));
-    CPCA_LAUNCHED();
-    int err = 0;
-    CPCA_CUDA(cudaMemcpyAsync(&err, w.err, sizeof(int), cudaMemcpyDeviceToHost, st));
-    CPCA_CUDA(cudaMemcpyAsync(&breakdown, w.status, sizeof(int), cudaMemcpyDeviceToHost, st));
-    CPCA_CUDA(cudaMemcpyAsync(cg_iters, w.out_iters, sizeof(cg_iters), cudaMemcpyDeviceToHost, st));
-    CPCA_CUDA(cudaMemcpyAsync(cg_res, w.out_res, sizeof(cg_res), cudaMemcpyDeviceToHost, st));
-    CPCA_CUDA(cudaStreamSynchronize(st));
-    if (err) {
-      set_error("cpca_decode: PCG grid barrier timed out");
-      return CPCA_ERR_TIMEOUT;
-    }
+    CPCA_TRY(cg_setup(a, Lr, Lc, omega_r, omega_c, p, n, rr, rc, k, b, prm, w, st));
+    CPCA_TRY(cg_solve(a, w, st, cg_iters, cg_res, &breakdown));
   }
   // assemble, normalise, scale, output
   const unsigned gp = std::min<unsigned>(ceil_div(int64_t(p) * kmax, 256), num_sms() * 8);
@@ -1098,5 +1121,648 @@ extern "C" cpca_status cpca_decode(const float* Xt, int32_t rr, int32_t rc, int6
     set_error("cpca_decode: PCG reached cg_max_iter before cg_tol");
     return CPCA_ERR_NOT_CONVERGED;
   }
+  return CPCA_OK;
+}
+
+// ===================================================================== //
+// Reverse mode of the decoder (the paper has no derivatives; this is the  //
+// derivative of the computed map with k fixed).                           //
+//                                                                         //
+// Forward: (U~, s, V~) = top-k SVD of X~; Uh = extension of U~ on Lr      //
+// (Lemma 1: Uh(Omega) = U~, Uh(a) = -Lr_aa^-1 Lr_ab U~), U = Uh / |Uh|    //
+// column-wise, sigma = c s; likewise V; X = U diag(sigma) V^T.            //
+// Given dloss/dX at entries (i_e, j_e): Ub, Vb, sigmab by scattering;     //
+// Uhb = (Ub - U diag(U^T Ub)) / |Uh|; Lambda = Lr_aa^-1 Uhb(a) (adjoint   //
+// PCG, Lr_aa symmetric); U~b = Uhb(Omega) - Lr_{a,Omega}^T Lambda;        //
+// dLr(i, j) = -sum_c Lambda(i, c) Uh(j, c) for unsampled rows i.          //
+// SVD: with A = X~ (or X~^T so that A is m x n, m >= n), J_u = U^T Ub,    //
+// J_v = V^T Vb, F_ij = 1 / (s_j^2 - s_i^2):                               //
+//   Ab = U Cm V^T + E V^T + U F'^T,                                       //
+//   Cm_ij = F_ij (J_u - J_u^T)_ij s_j + delta_ij sb_i + s_i F_ij (J_v - J_v^T)_ij, //
+// and the parts outside the top-k subspaces through the resolvents of the //
+// Gram G = A^T A restricted to the complement of V (SPD there, shift s_i^2 //
+// above the discarded spectrum):                                          //
+//   B = Ub - U J_u, y'_i = (s_i^2 - G)^-1 A^T b_i, y_i = (s_i^2 - G)^-1 d_i, //
+//   d_i = vb_i - V (J_v)_i, E = B S^-1 + A (Y' S^-1 + Y), F' = Y' + Y S.   //
+// The shifted systems are solved by dense CG, one block per right-hand    //
+// side; the same identity (Woodbury) replaces the m x m resolvent.        //
+// ===================================================================== //
+namespace cpca {
+namespace {
+
+__global__ void heldout_kernel(int64_t nh, const int32_t* __restrict__ rows, const int32_t* __restrict__ cols,
+                               const float* __restrict__ g, const float* __restrict__ U,
+                               const float* __restrict__ V, int ld, const double* __restrict__ sigma, int k,
+                               float* __restrict__ Ub, float* __restrict__ Vb, double* __restrict__ sbar) {
+  __shared__ double sb[KMAX_LIMIT];
+  for (int c = threadIdx.x; c < KMAX_LIMIT; c += blockDim.x) sb[c] = 0.0;
+  __syncthreads();
+  for (int64_t e = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; e < nh;
+       e += int64_t(gridDim.x) * blockDim.x) {
+    const int i = rows[e], j = cols[e];
+    const double ge = g[e];
+    for (int c = 0; c < k; ++c) {
+      const double u = U[int64_t(i) * ld + c], v = V[int64_t(j) * ld + c], s = sigma[c];
+      atomicAdd(Ub + int64_t(i) * ld + c, float(ge * s * v));
+      atomicAdd(Vb + int64_t(j) * ld + c, float(ge * s * u));
+      atomicAdd(sb + c, ge * u * v);
+    }
+  }
+  __syncthreads();
+  for (int c = threadIdx.x; c < k; c += blockDim.x)
+    if (sb[c] != 0.0) atomicAdd(sbar + c, sb[c]);
+}
+
+// Column-wise FP64 dot products of A and B (N x k, ld), fixed order per block.
+__global__ void coldot_partial_kernel(const float* __restrict__ A, const float* __restrict__ B, int N, int k,
+                                      int ld, double* __restrict__ part) {
+  const int per = (N + gridDim.x - 1) / gridDim.x;
+  const int lo = blockIdx.x * per, hi = min(N, lo + per);
+  const int c = threadIdx.x % KMAX_LIMIT, lane_row = threadIdx.x / KMAX_LIMIT;
+  const int rows_par = blockDim.x / KMAX_LIMIT;
+  double acc = 0.0;
+  if (c < k && lane_row < rows_par)
+    for (int i = lo + lane_row; i < hi; i += rows_par)
+      acc += double(A[int64_t(i) * ld + c]) * double(B[int64_t(i) * ld + c]);
+  __shared__ double tmp[256];
+  tmp[threadIdx.x] = acc;
+  __syncthreads();
+  if (threadIdx.x < KMAX_LIMIT) {
+    double t = 0.0;
+    for (int r = 0; r < rows_par; ++r) t += tmp[r * KMAX_LIMIT + threadIdx.x];
+    part[int64_t(blockIdx.x) * KMAX_LIMIT + threadIdx.x] = t;
+  }
+}
+__global__ void sum_parts_kernel(const double* __restrict__ part, int nblk, double* __restrict__ out) {
+  for (int c = threadIdx.x; c < KMAX_LIMIT; c += blockDim.x) {
+    double a = 0.0;
+    for (int i = 0; i < nblk; ++i) a += part[int64_t(i) * KMAX_LIMIT + c];
+    out[c] = a;
+  }
+}
+
+// Ub <- (Ub - U diag(dots)) diag(inv): adjoint of the column normalisation.
+__global__ void norm_bwd_kernel(float* __restrict__ Ub, const float* __restrict__ U, int64_t total, int ld,
+                                int k, const double* __restrict__ dots, const double* __restrict__ inv) {
+  for (int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; t < total;
+       t += int64_t(gridDim.x) * blockDim.x) {
+    const int c = int(t % ld);
+    Ub[t] = c < k ? float((double(Ub[t]) - double(U[t]) * dots[c]) * inv[c]) : 0.f;
+  }
+}
+
+__global__ void gather_rhs_kernel(int m, int k, const int32_t* __restrict__ abar, const float* __restrict__ X,
+                                  int ld, float* __restrict__ rhs) {
+  for (int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; t < int64_t(m) * k;
+       t += int64_t(gridDim.x) * blockDim.x) {
+    const int r = int(t / k), c = int(t % k);
+    rhs[t] = X[int64_t(abar[r]) * ld + c];
+  }
+}
+
+// R~b(s, c) = Uhb(omega_s, c) - sum_{j unsampled} L(omega_s, j) Lambda(pos_j, c).
+__global__ void sampled_bar_kernel(int rho, const int32_t* __restrict__ omega, CsrView L,
+                                   const int32_t* __restrict__ pos, const float* __restrict__ Uhb, int ld,
+                                   const float* __restrict__ Lam, int k, float* __restrict__ out) {
+  for (int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; t < int64_t(rho) * k;
+       t += int64_t(gridDim.x) * blockDim.x) {
+    const int s = int(t / k), c = int(t % k);
+    const int node = omega[s];
+    double v = Uhb[int64_t(node) * ld + c];
+    for (int64_t e = L.rowptr[node]; e < L.rowptr[node + 1]; ++e) {
+      const int ps = pos[L.col[e]];
+      if (ps >= 0) v -= double(L.val[e]) * double(Lam[int64_t(ps) * k + c]);
+    }
+    out[t] = float(v);
+  }
+}
+
+// dL(e) for e = (i, j): -sum_c Lambda(pos_i, c) Uh(j, c) if i is unsampled, else 0.
+__global__ void dl_decode_kernel(CsrView L, const int32_t* __restrict__ pos, const float* __restrict__ Lam,
+                                 int k, const float* __restrict__ Uh, int ld, double* __restrict__ dL) {
+  for (int i = blockIdx.x; i < L.n; i += gridDim.x) {
+    const int t = pos[i];
+    for (int64_t e = L.rowptr[i] + threadIdx.x; e < L.rowptr[i + 1]; e += blockDim.x) {
+      double v = 0.0;
+      if (t >= 0) {
+        const int j = L.col[e];
+        for (int c = 0; c < k; ++c) v -= double(Lam[int64_t(t) * k + c]) * double(Uh[int64_t(j) * ld + c]);
+      }
+      dL[e] = v;
+    }
+  }
+}
+
+// out (k x k, FP64, zeroed) += P^T Q over m rows (P, Q with their own ld).
+__global__ void cross_gram_kernel(const float* __restrict__ P, int ldp, const float* __restrict__ Q, int ldq,
+                                  int m, int k, double* __restrict__ out) {
+  const int r0 = blockIdx.x * 64, r1 = min(m, r0 + 64);
+  for (int pr = threadIdx.x; pr < k * k; pr += blockDim.x) {
+    const int i = pr / k, j = pr % k;
+    double s = 0.0;
+    for (int t = r0; t < r1; ++t) s += double(P[int64_t(t) * ldp + i]) * double(Q[int64_t(t) * ldq + j]);
+    if (s != 0.0) atomicAdd(out + pr, s);
+  }
+}
+
+// Cm (k x k) of the in-subspace part; sb = scale * sigmab.
+__global__ void svd_mid_kernel(int k, const double* __restrict__ s, const double* __restrict__ sigb, double scale,
+                               const double* __restrict__ Ju, const double* __restrict__ Jv,
+                               double* __restrict__ Cm) {
+  for (int pr = threadIdx.x; pr < k * k; pr += blockDim.x) {
+    const int i = pr / k, j = pr % k;
+    double v = 0.0;
+    if (i == j) {
+      v = scale * sigb[i];
+    } else {
+      const double den = s[j] * s[j] - s[i] * s[i];
+      if (den != 0.0) {
+        const double F = 1.0 / den;
+        v = F * (Ju[i * k + j] - Ju[j * k + i]) * s[j] + s[i] * F * (Jv[i * k + j] - Jv[j * k + i]);
+      }
+    }
+    Cm[pr] = v;
+  }
+}
+
+// out (m x k) = Pb - Ubase J (J k x k FP64); Ubase with ld ldu, Pb and out ld k.
+__global__ void proj_sub_kernel(int m, int k, const float* __restrict__ Pb, const float* __restrict__ Ub, int ldu,
+                                const double* __restrict__ J, float* __restrict__ out) {
+  for (int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; t < int64_t(m) * k;
+       t += int64_t(gridDim.x) * blockDim.x) {
+    const int r = int(t / k), i = int(t % k);
+    double v = Pb[t];
+    for (int j = 0; j < k; ++j) v -= double(Ub[int64_t(r) * ldu + j]) * J[j * k + i];
+    out[t] = float(v);
+  }
+}
+
+// G (n x n, FP32) = A^T A with A = X~ (rows t, columns a) when vspace, else
+// A = X~^T. 32 x 32 output tile per block, FP32 products per 32-chunk of
+// the summed dimension, FP64 across chunks.
+__global__ void __launch_bounds__(256)
+gram_full_kernel(const float* __restrict__ X, int64_t ldx, int rr, int rc, int vspace, float* __restrict__ G) {
+  __shared__ float As[32][33], Bs[32][33];
+  const int n = vspace ? rc : rr, m = vspace ? rr : rc;
+  const int a0 = blockIdx.y * 32, b0 = blockIdx.x * 32;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 8 rows of 4 outputs each
+  double acc[4] = {0.0, 0.0, 0.0, 0.0};
+  for (int t0 = 0; t0 < m; t0 += 32) {
+    for (int e = threadIdx.x; e < 32 * 32; e += 256) {
+      const int tt = e >> 5, cc = e & 31;
+      float va = 0.f, vb = 0.f;
+      if (vspace) {
+        if (t0 + tt < m && a0 + cc < n) va = X[int64_t(t0 + tt) * ldx + a0 + cc];
+        if (t0 + tt < m && b0 + cc < n) vb = X[int64_t(t0 + tt) * ldx + b0 + cc];
+        As[tt][cc] = va;
+        Bs[tt][cc] = vb;
+      } else {
+        // element (t, a) of A = X~(a, t): read along t
+        if (t0 + cc < m && a0 + tt < n) va = X[int64_t(a0 + tt) * ldx + t0 + cc];
+        if (t0 + cc < m && b0 + tt < n) vb = X[int64_t(b0 + tt) * ldx + t0 + cc];
+        As[cc][tt] = va;
+        Bs[cc][tt] = vb;
+      }
+    }
+    __syncthreads();
+    float part[4] = {0.f, 0.f, 0.f, 0.f};
+    for (int tt = 0; tt < 32; ++tt) {
+      const float bv = Bs[tt][tx];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) part[q] = fmaf(As[tt][ty * 4 + q], bv, part[q]);
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) acc[q] += part[q];
+    __syncthreads();
+  }
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int a = a0 + ty * 4 + q, b = b0 + tx;
+    if (a < n && b < n) G[int64_t(a) * n + b] = float(acc[q]);
+  }
+}
+
+// vec (n, global) <- vec - V (V^T vec), V n x k with ld ldv.
+__device__ __forceinline__ void project_out(float* vec, const float* __restrict__ V, int ldv, int k, int n,
+                                            double* red) {
+  for (int c = 0; c < k; ++c) {
+    __syncthreads();
+    double d = 0.0;
+    for (int a = threadIdx.x; a < n; a += blockDim.x) d += double(V[int64_t(a) * ldv + c]) * vec[a];
+    d = block_sum(d, red);
+    for (int a = threadIdx.x; a < n; a += blockDim.x) vec[a] = float(double(vec[a]) - d * V[int64_t(a) * ldv + c]);
+  }
+  __syncthreads();
+}
+
+// (s_i^2 I - G) y = rhs on the complement of V (n x k, ld ldv), one block
+// per right-hand side; right-hand side r < k uses rhs0 column r, else rhs1
+// column r - k (both n x k); shift s_{r mod k}^2. CG on the projected
+// operator P (s^2 I - G) P, P = I - V V^T (SPD on the complement; the
+// top-k directions of the computed basis are only approximately invariant,
+// so every product is projected), FP64 scalars.
+__global__ void __launch_bounds__(256)
+shift_cg_kernel(const float* __restrict__ G, int n, int k, const float* __restrict__ rhs0,
+                const float* __restrict__ rhs1, const double* __restrict__ s, const float* __restrict__ V,
+                int ldv, double tol, int maxit, float* __restrict__ work, float* __restrict__ out0,
+                float* __restrict__ out1, int* __restrict__ flag) {
+  extern __shared__ float ps[];
+  __shared__ double red[8];
+  const int r = blockIdx.x;
+  const float* rhs = r < k ? rhs0 : rhs1;
+  float* out = r < k ? out0 : out1;
+  const int col = r < k ? r : r - k;
+  const float shift = float(s[col] * s[col]);
+  float* x = work + int64_t(r) * 3 * n;
+  float* res = x + n;
+  float* q = res + n;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int a = threadIdx.x; a < n; a += blockDim.x) {
+    x[a] = 0.f;
+    res[a] = rhs[int64_t(a) * k + col];
+  }
+  project_out(res, V, ldv, k, n, red);
+  double bb = 0.0;
+  for (int a = threadIdx.x; a < n; a += blockDim.x) {
+    ps[a] = res[a];
+    bb += double(res[a]) * res[a];
+  }
+  bb = block_sum(bb, red);
+  double rr = bb;
+  const double stop = tol * tol * bb;
+  int it = 0;
+  while (rr > stop && it < maxit) {
+    __syncthreads();
+    for (int a = warp; a < n; a += 8) {
+      float sum = 0.f;
+      for (int b = lane; b < n; b += 32) sum = fmaf(G[int64_t(a) * n + b], ps[b], sum);
+      sum = warp_sumf(sum);
+      if (lane == 0) q[a] = shift * ps[a] - sum;
+    }
+    project_out(q, V, ldv, k, n, red);
+    double pq = 0.0;
+    for (int a = threadIdx.x; a < n; a += blockDim.x) pq += double(ps[a]) * q[a];
+    pq = block_sum(pq, red);
+    if (!(pq > 0.0)) {
+      if (threadIdx.x == 0) atomicOr(flag, 1);
+      break;
+    }
+    const double alpha = rr / pq;
+    double rn = 0.0;
+    for (int a = threadIdx.x; a < n; a += blockDim.x) {
+      x[a] = float(double(x[a]) + alpha * ps[a]);
+      const float rv = float(double(res[a]) - alpha * q[a]);
+      res[a] = rv;
+      rn += double(rv) * rv;
+    }
+    rn = block_sum(rn, red);
+    const double beta = rn / rr;
+    rr = rn;
+    for (int a = threadIdx.x; a < n; a += blockDim.x) ps[a] = float(res[a] + beta * ps[a]);
+    ++it;
+  }
+  if (rr > stop && threadIdx.x == 0) atomicOr(flag, 2);
+  project_out(x, V, ldv, k, n, red);
+  for (int a = threadIdx.x; a < n; a += blockDim.x) out[int64_t(a) * k + col] = x[a];
+}
+
+// T = Y' S^-1 + Y and F' = Y' + Y S (n x k).
+__global__ void tcomb_kernel(int n, int k, const float* __restrict__ Yp, const float* __restrict__ Yv,
+                             const double* __restrict__ s, float* __restrict__ T, float* __restrict__ F) {
+  for (int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; t < int64_t(n) * k;
+       t += int64_t(gridDim.x) * blockDim.x) {
+    const int i = int(t % k);
+    T[t] = float(double(Yp[t]) / s[i] + Yv[t]);
+    F[t] = float(Yp[t] + double(Yv[t]) * s[i]);
+  }
+}
+
+// P = U Cm + B S^-1 + AT (m x k).
+__global__ void pcomb_kernel(int m, int k, const float* __restrict__ U, int ldu, const double* __restrict__ Cm,
+                             const float* __restrict__ B, const float* __restrict__ AT,
+                             const double* __restrict__ s, float* __restrict__ P) {
+  for (int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; t < int64_t(m) * k;
+       t += int64_t(gridDim.x) * blockDim.x) {
+    const int r = int(t / k), i = int(t % k);
+    double v = double(B[t]) / s[i] + AT[t];
+    for (int j = 0; j < k; ++j) v += double(U[int64_t(r) * ldu + j]) * Cm[j * k + i];
+    P[t] = float(v);
+  }
+}
+
+// Ab (m x n) = P V^T + U F'^T, written as X~b (transposed when A = X~^T).
+__global__ void __launch_bounds__(256)
+lowrank_out_kernel(int m, int n, int k, const float* __restrict__ P, const float* __restrict__ V, int ldv,
+                   const float* __restrict__ U, int ldu, const float* __restrict__ F, float* __restrict__ out,
+                   int64_t ldo, int transposed) {
+  __shared__ float Ps[32][2 * KMAX_LIMIT + 1];
+  __shared__ float Qs[32][2 * KMAX_LIMIT + 1];
+  const int a0 = blockIdx.y * 32, b0 = blockIdx.x * 32;
+  for (int e = threadIdx.x; e < 32 * k; e += blockDim.x) {
+    const int r = e / k, c = e % k;
+    const bool ia = a0 + r < m, ib = b0 + r < n;
+    Ps[r][c] = ia ? P[int64_t(a0 + r) * k + c] : 0.f;
+    Ps[r][k + c] = ia ? U[int64_t(a0 + r) * ldu + c] : 0.f;
+    Qs[r][c] = ib ? V[int64_t(b0 + r) * ldv + c] : 0.f;
+    Qs[r][k + c] = ib ? F[int64_t(b0 + r) * k + c] : 0.f;
+  }
+  __syncthreads();
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  for (int q = 0; q < 4; ++q) {
+    const int ra = ty * 4 + q;
+    // transposed output: lanes run along a (rows of A) for coalesced stores
+    const int ia = transposed ? tx : ra, ib = transposed ? ra : tx;
+    const int a = a0 + ia, b = b0 + ib;
+    if (a >= m || b >= n) continue;
+    float v = 0.f;
+    for (int c = 0; c < 2 * k; ++c) v = fmaf(Ps[ia][c], Qs[ib][c], v);
+    if (transposed) out[int64_t(b) * ldo + a] = v;
+    else out[int64_t(a) * ldo + b] = v;
+  }
+}
+
+// X(h_row[e], h_col[e]) = sum_c U(i, c) sigma_c V(j, c), FP64 sum.
+__global__ void entries_kernel(int64_t nh, const int32_t* __restrict__ rows, const int32_t* __restrict__ cols,
+                               const float* __restrict__ U, int ldu, const float* __restrict__ V, int ldv,
+                               const double* __restrict__ sigma, int k, float* __restrict__ out) {
+  for (int64_t e = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; e < nh;
+       e += int64_t(gridDim.x) * blockDim.x) {
+    const int i = rows[e], j = cols[e];
+    double v = 0.0;
+    for (int c = 0; c < k; ++c) v += double(U[int64_t(i) * ldu + c]) * sigma[c] * double(V[int64_t(j) * ldv + c]);
+    out[e] = float(v);
+  }
+}
+
+struct DecBwdWs {
+  float *Uh, *Vh, *Ub, *Vb;
+  double *sbar, *part, *dots_u, *dots_v;
+  float *rhs0, *rhs1;
+  float *Utb, *Vtb;
+  double *Ju, *Jv, *Cm;
+  float *B, *Cc, *D, *Yp, *Yv, *T, *F, *AT, *P, *G, *work;
+  double *dL0, *dL1, *deg, *dD;
+  int* flag;
+  size_t bytes;
+};
+
+DecBwdWs decbwd_layout(void* base, int p, int n, int rr, int rc, int kmax, int64_t nnz_r, int64_t nnz_c) {
+  Carve c(base);
+  DecBwdWs w{};
+  const int ma = std::max(rr, rc), na = std::min(rr, rc);
+  w.Uh = c.take<float>(size_t(p) * kmax);
+  w.Vh = c.take<float>(size_t(n) * kmax);
+  w.Ub = c.take<float>(size_t(p) * kmax);
+  w.Vb = c.take<float>(size_t(n) * kmax);
+  w.sbar = c.take<double>(KMAX_LIMIT);
+  w.part = c.take<double>(size_t(NORM_BLOCKS) * KMAX_LIMIT);
+  w.dots_u = c.take<double>(KMAX_LIMIT);
+  w.dots_v = c.take<double>(KMAX_LIMIT);
+  w.rhs0 = c.take<float>(size_t(std::max(p - rr, 1)) * kmax);
+  w.rhs1 = c.take<float>(size_t(std::max(n - rc, 1)) * kmax);
+  w.Utb = c.take<float>(size_t(rr) * kmax);
+  w.Vtb = c.take<float>(size_t(rc) * kmax);
+  w.Ju = c.take<double>(size_t(kmax) * kmax);
+  w.Jv = c.take<double>(size_t(kmax) * kmax);
+  w.Cm = c.take<double>(size_t(kmax) * kmax);
+  w.B = c.take<float>(size_t(ma) * kmax);
+  w.Cc = c.take<float>(size_t(na) * kmax);
+  w.D = c.take<float>(size_t(na) * kmax);
+  w.Yp = c.take<float>(size_t(na) * kmax);
+  w.Yv = c.take<float>(size_t(na) * kmax);
+  w.T = c.take<float>(size_t(na) * kmax);
+  w.F = c.take<float>(size_t(na) * kmax);
+  w.AT = c.take<float>(size_t(ma) * kmax);
+  w.P = c.take<float>(size_t(ma) * kmax);
+  w.G = c.take<float>(size_t(na) * na);
+  w.work = c.take<float>(size_t(2 * kmax) * 3 * na);
+  w.dL0 = c.take<double>(std::max<int64_t>(nnz_r, 1));
+  w.dL1 = c.take<double>(std::max<int64_t>(nnz_c, 1));
+  w.deg = c.take<double>(std::max(p, n));
+  w.dD = c.take<double>(std::max(p, n));
+  w.flag = c.take<int>(1);
+  w.bytes = c.bytes();
+  return w;
+}
+
+constexpr int kShiftCgMaxN = 16384;  // dense resolvent solves keep p in shared memory
+
+}  // namespace
+}  // namespace cpca
+
+extern "C" size_t cpca_decode_backward_workspace_size(int32_t p, int32_t n, int32_t rr, int32_t rc,
+                                                      int32_t kmax, int64_t nnz_r, int64_t nnz_c) {
+  const size_t a = cpca_decode_workspace_size(p, n, rr, rc, kmax, nnz_r, nnz_c);
+  if (a == 0) return 0;
+  const size_t fwd = (a + 255) & ~size_t(255);
+  return fwd + decbwd_layout(nullptr, p, n, rr, rc, kmax, nnz_r, nnz_c).bytes;
+}
+
+extern "C" cpca_status cpca_decode_backward(const float* Xt, int32_t rr, int32_t rc, int64_t ldxt,
+                                            const int32_t* omega_r, const int32_t* omega_c, int32_t p,
+                                            int32_t n, const cpca_csr* Lr, const cpca_csr* Lc,
+                                            const cpca_decode_params* prm, int32_t k, int64_t nh,
+                                            const int32_t* h_row, const int32_t* h_col,
+                                            const float* h_grad, float* dXt, int64_t lddxt, double* dLr,
+                                            double* dLc, const float* wr, const float* wc,
+                                            int32_t lap_type, float* dwr, float* dwc, void* ws,
+                                            size_t ws_bytes, void* stream) {
+  clear_error();
+  CPCA_CHECK_ARG(Xt && omega_r && omega_c && prm && dXt, "cpca_decode_backward: null pointer");
+  CPCA_CHECK_ARG(nh >= 0 && (nh == 0 || (h_row && h_col && h_grad)), "cpca_decode_backward: bad entries");
+  CPCA_CHECK_ARG(rr > 0 && rc > 0 && rr <= p && rc <= n, "cpca_decode_backward: need 0 < rr <= p, 0 < rc <= n");
+  CPCA_CHECK_ARG(ldxt >= rc && lddxt >= rc, "cpca_decode_backward: leading dimension < rc");
+  CPCA_CHECK_ARG(prm->kmax >= 1 && prm->kmax <= KMAX_LIMIT, "cpca_decode_backward: kmax must be in [1, %d]",
+                 KMAX_LIMIT);
+  CPCA_CHECK_ARG(k >= 1 && k <= prm->kmax, "cpca_decode_backward: need 1 <= k <= kmax");
+  CPCA_CHECK_ARG(prm->delta >= 0 && prm->delta < 1, "cpca_decode_backward: delta must be in [0, 1)");
+  CPCA_CHECK_ARG(prm->cg_tol > 0 && prm->svd_iters >= 1, "cpca_decode_backward: bad cg_tol / svd_iters");
+  CPCA_CHECK_ARG(lap_type == CPCA_LAP_NORMALIZED || lap_type == CPCA_LAP_COMBINATORIAL,
+                 "cpca_decode_backward: unknown lap_type");
+  CPCA_CHECK_ARG(!dwr || wr, "cpca_decode_backward: dwr needs the weights wr");
+  CPCA_CHECK_ARG(!dwc || wc, "cpca_decode_backward: dwc needs the weights wc");
+  CPCA_CHECK_ARG(std::min(rr, rc) <= kShiftCgMaxN, "cpca_decode_backward: min(rr, rc) > %d", kShiftCgMaxN);
+  CPCA_TRY(check_csr(Lr, p, "cpca_decode_backward(Lr)"));
+  CPCA_TRY(check_csr(Lc, n, "cpca_decode_backward(Lc)"));
+  const int kmax = prm->kmax;
+  const DecodeWs w = decode_layout(ws, p, n, rr, rc, kmax, Lr->nnz, Lc->nnz);
+  const size_t fwd = (w.bytes + 255) & ~size_t(255);
+  const DecBwdWs v = decbwd_layout(ws ? static_cast<char*>(ws) + fwd : nullptr, p, n, rr, rc, kmax, Lr->nnz,
+                                   Lc->nnz);
+  if (!ws || ws_bytes < fwd + v.bytes) {
+    set_error("cpca_decode_backward: workspace %zu bytes < required %zu", ws_bytes, fwd + v.bytes);
+    return CPCA_ERR_WORKSPACE;
+  }
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const int b = decode_block(rr, rc, kmax);
+  CPCA_CHECK_ARG(k <= b, "cpca_decode_backward: k > subspace block %d", b);
+  // ---- forward factors, k fixed
+  CPCA_TRY(partial_svd(Xt, rr, rc, ldxt, b, prm->svd_iters, prm->svd_seed, prm->rank_ratio, k, w, st));
+  CgArgs a{};
+  int cg_iters[2 * KMAX_LIMIT] = {0};
+  double cg_res[2 * KMAX_LIMIT] = {0};
+  int breakdown = 0;
+  CPCA_TRY(cg_setup(a, Lr, Lc, omega_r, omega_c, p, n, rr, rc, k, b, prm, w, st));
+  CPCA_TRY(cg_solve(a, w, st, cg_iters, cg_res, &breakdown));
+  if (breakdown) {
+    set_error("cpca_decode_backward: L_aa is not positive definite (a graph component has no sampled node)");
+    return CPCA_ERR_SINGULAR;
+  }
+  const unsigned gp = std::min<unsigned>(ceil_div(int64_t(p) * kmax, 256), num_sms() * 8);
+  const unsigned gn = std::min<unsigned>(ceil_div(int64_t(n) * kmax, 256), num_sms() * 8);
+  assemble_side_kernel<<<gp, 256, 0, st>>>(p, k, kmax, w.pos0, w.Ut, b, w.vec[0][0], v.Uh);
+  CPCA_LAUNCHED();
+  assemble_side_kernel<<<gn, 256, 0, st>>>(n, k, kmax, w.pos1, w.Vt, b, w.vec[1][0], v.Vh);
+  CPCA_LAUNCHED();
+  colnorm_partial_kernel<<<NORM_BLOCKS, 192, 0, st>>>(v.Uh, p, k, kmax, w.npart_u);
+  CPCA_LAUNCHED();
+  colnorm_partial_kernel<<<NORM_BLOCKS, 192, 0, st>>>(v.Vh, n, k, kmax, w.npart_v);
+  CPCA_LAUNCHED();
+  const double scale = sqrt(double(n) * double(p) / (double(rr) * double(rc) * (1.0 - prm->delta)));
+  norm_finish_kernel<<<1, 64, 0, st>>>(w.npart_u, w.npart_v, NORM_BLOCKS, k, w.s, scale, w.invu, w.invv,
+                                       w.sigbuf, kmax);
+  CPCA_LAUNCHED();
+  CPCA_CUDA(cudaMemcpyAsync(w.Ubuf, v.Uh, sizeof(float) * size_t(p) * kmax, cudaMemcpyDeviceToDevice, st));
+  CPCA_CUDA(cudaMemcpyAsync(w.Vbuf, v.Vh, sizeof(float) * size_t(n) * kmax, cudaMemcpyDeviceToDevice, st));
+  scale_cols_kernel<<<gp, 256, 0, st>>>(w.Ubuf, int64_t(p) * kmax, kmax, w.invu);
+  CPCA_LAUNCHED();
+  scale_cols_kernel<<<gn, 256, 0, st>>>(w.Vbuf, int64_t(n) * kmax, kmax, w.invv);
+  CPCA_LAUNCHED();
+  // ---- held-out entries -> Ub, Vb, sigmab
+  CPCA_CUDA(cudaMemsetAsync(v.Ub, 0, sizeof(float) * size_t(p) * kmax, st));
+  CPCA_CUDA(cudaMemsetAsync(v.Vb, 0, sizeof(float) * size_t(n) * kmax, st));
+  CPCA_CUDA(cudaMemsetAsync(v.sbar, 0, sizeof(double) * KMAX_LIMIT, st));
+  if (nh > 0) {
+    heldout_kernel<<<std::min<unsigned>(ceil_div(nh, 256), num_sms() * 4), 256, 0, st>>>(
+        nh, h_row, h_col, h_grad, w.Ubuf, w.Vbuf, kmax, w.sigbuf, k, v.Ub, v.Vb, v.sbar);
+    CPCA_LAUNCHED();
+  }
+  // ---- normalisation adjoint
+  coldot_partial_kernel<<<NORM_BLOCKS, 192, 0, st>>>(w.Ubuf, v.Ub, p, k, kmax, v.part);
+  CPCA_LAUNCHED();
+  sum_parts_kernel<<<1, 64, 0, st>>>(v.part, NORM_BLOCKS, v.dots_u);
+  CPCA_LAUNCHED();
+  coldot_partial_kernel<<<NORM_BLOCKS, 192, 0, st>>>(w.Vbuf, v.Vb, n, k, kmax, v.part);
+  CPCA_LAUNCHED();
+  sum_parts_kernel<<<1, 64, 0, st>>>(v.part, NORM_BLOCKS, v.dots_v);
+  CPCA_LAUNCHED();
+  norm_bwd_kernel<<<gp, 256, 0, st>>>(v.Ub, w.Ubuf, int64_t(p) * kmax, kmax, k, v.dots_u, w.invu);
+  CPCA_LAUNCHED();
+  norm_bwd_kernel<<<gn, 256, 0, st>>>(v.Vb, w.Vbuf, int64_t(n) * kmax, kmax, k, v.dots_v, w.invv);
+  CPCA_LAUNCHED();
+  // ---- adjoint PCG on L_aa (symmetric): Lambda = L_aa^-1 Uhb(a)
+  const int m0 = p - rr, m1 = n - rc;
+  if (m0 > 0) {
+    gather_rhs_kernel<<<std::min<unsigned>(ceil_div(int64_t(m0) * k, 256), num_sms() * 4), 256, 0, st>>>(
+        m0, k, w.abar0, v.Ub, kmax, v.rhs0);
+    CPCA_LAUNCHED();
+  }
+  if (m1 > 0) {
+    gather_rhs_kernel<<<std::min<unsigned>(ceil_div(int64_t(m1) * k, 256), num_sms() * 4), 256, 0, st>>>(
+        m1, k, w.abar1, v.Vb, kmax, v.rhs1);
+    CPCA_LAUNCHED();
+  }
+  a.s[0].rhs = v.rhs0;
+  a.s[1].rhs = v.rhs1;
+  CPCA_TRY(cg_solve(a, w, st, cg_iters, cg_res, &breakdown));
+  if (breakdown) {
+    set_error("cpca_decode_backward: adjoint PCG broke down");
+    return CPCA_ERR_SINGULAR;
+  }
+  const CsrView lr{Lr->n, Lr->rowptr, Lr->col, Lr->val};
+  const CsrView lc{Lc->n, Lc->rowptr, Lc->col, Lc->val};
+  sampled_bar_kernel<<<std::min<unsigned>(ceil_div(int64_t(rr) * k, 256), num_sms() * 4), 256, 0, st>>>(
+      rr, omega_r, lr, w.pos0, v.Ub, kmax, w.vec[0][0], k, v.Utb);
+  CPCA_LAUNCHED();
+  sampled_bar_kernel<<<std::min<unsigned>(ceil_div(int64_t(rc) * k, 256), num_sms() * 4), 256, 0, st>>>(
+      rc, omega_c, lc, w.pos1, v.Vb, kmax, w.vec[1][0], k, v.Vtb);
+  CPCA_LAUNCHED();
+  double* oL0 = dLr ? dLr : v.dL0;
+  double* oL1 = dLc ? dLc : v.dL1;
+  if (dLr || dwr) {
+    dl_decode_kernel<<<std::min(p, num_sms() * 8), 64, 0, st>>>(lr, w.pos0, w.vec[0][0], k, v.Uh, kmax, oL0);
+    CPCA_LAUNCHED();
+  }
+  if (dLc || dwc) {
+    dl_decode_kernel<<<std::min(n, num_sms() * 8), 64, 0, st>>>(lc, w.pos1, w.vec[1][0], k, v.Vh, kmax, oL1);
+    CPCA_LAUNCHED();
+  }
+  // ---- SVD adjoint, A = X~ (m = rr >= n = rc) or A = X~^T
+  const bool vspace = rc <= rr;
+  const int mA = vspace ? rr : rc, nA = vspace ? rc : rr;
+  const float* UA = vspace ? w.Ut : w.Vt;  // ld b
+  const float* VA = vspace ? w.Vt : w.Ut;
+  const float* UAb = vspace ? v.Utb : v.Vtb;  // ld k
+  const float* VAb = vspace ? v.Vtb : v.Utb;
+  auto applyA = [&](const float* in, float* out) {  // out (mA x k) = A in (nA x k)
+    if (vspace) gemm_nn_tall<<<ceil_div(rr, 8), 256, 0, st>>>(Xt, ldxt, rr, rc, in, k, out);
+    else gemm_tn_tall<<<ceil_div(rc, 8), 256, 0, st>>>(Xt, ldxt, rr, rc, in, k, out);
+  };
+  auto applyAT = [&](const float* in, float* out) {  // out (nA x k) = A^T in (mA x k)
+    if (vspace) gemm_tn_tall<<<ceil_div(rc, 8), 256, 0, st>>>(Xt, ldxt, rr, rc, in, k, out);
+    else gemm_nn_tall<<<ceil_div(rr, 8), 256, 0, st>>>(Xt, ldxt, rr, rc, in, k, out);
+  };
+  CPCA_CUDA(cudaMemsetAsync(v.Ju, 0, sizeof(double) * k * k, st));
+  CPCA_CUDA(cudaMemsetAsync(v.Jv, 0, sizeof(double) * k * k, st));
+  cross_gram_kernel<<<ceil_div(mA, 64), 256, 0, st>>>(UA, b, UAb, k, mA, k, v.Ju);
+  CPCA_LAUNCHED();
+  cross_gram_kernel<<<ceil_div(nA, 64), 256, 0, st>>>(VA, b, VAb, k, nA, k, v.Jv);
+  CPCA_LAUNCHED();
+  svd_mid_kernel<<<1, 256, 0, st>>>(k, w.s, v.sbar, scale, v.Ju, v.Jv, v.Cm);
+  CPCA_LAUNCHED();
+  const unsigned gmk = std::min<unsigned>(ceil_div(int64_t(mA) * k, 256), num_sms() * 4);
+  const unsigned gnk = std::min<unsigned>(ceil_div(int64_t(nA) * k, 256), num_sms() * 4);
+  proj_sub_kernel<<<gmk, 256, 0, st>>>(mA, k, UAb, UA, b, v.Ju, v.B);
+  CPCA_LAUNCHED();
+  proj_sub_kernel<<<gnk, 256, 0, st>>>(nA, k, VAb, VA, b, v.Jv, v.D);
+  CPCA_LAUNCHED();
+  applyAT(v.B, v.Cc);
+  CPCA_LAUNCHED();
+  dim3 gg(ceil_div(nA, 32), ceil_div(nA, 32));
+  gram_full_kernel<<<gg, 256, 0, st>>>(Xt, ldxt, rr, rc, vspace ? 1 : 0, v.G);
+  CPCA_LAUNCHED();
+  CPCA_CUDA(cudaMemsetAsync(v.flag, 0, sizeof(int), st));
+  const size_t csm = sizeof(float) * size_t(nA);
+  CPCA_CUDA(cudaFuncSetAttribute(shift_cg_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(csm)));
+  CPCA_PROF("dec_bwd_shift_cg", st);
+  shift_cg_kernel<<<2 * k, 256, csm, st>>>(v.G, nA, k, v.Cc, v.D, w.s, VA, b, 1e-6, 4 * nA + 50, v.work,
+                                            v.Yp, v.Yv, v.flag);
+  CPCA_LAUNCHED();
+  tcomb_kernel<<<gnk, 256, 0, st>>>(nA, k, v.Yp, v.Yv, w.s, v.T, v.F);
+  CPCA_LAUNCHED();
+  applyA(v.T, v.AT);
+  CPCA_LAUNCHED();
+  pcomb_kernel<<<gmk, 256, 0, st>>>(mA, k, UA, b, v.Cm, v.B, v.AT, w.s, v.P);
+  CPCA_LAUNCHED();
+  dim3 og(ceil_div(nA, 32), ceil_div(mA, 32));
+  lowrank_out_kernel<<<og, 256, 0, st>>>(mA, nA, k, v.P, VA, b, UA, b, v.F, dXt, lddxt, vspace ? 0 : 1);
+  CPCA_LAUNCHED();
+  // ---- weights
+  if (dwr) CPCA_TRY(laplacian_weight_grad(lr, wr, oL0, lap_type, dwr, v.deg, v.dD, st));
+  if (dwc) CPCA_TRY(laplacian_weight_grad(lc, wc, oL1, lap_type, dwc, v.deg, v.dD, st));
+  int flag = 0;
+  CPCA_CUDA(cudaMemcpyAsync(&flag, v.flag, sizeof(int), cudaMemcpyDeviceToHost, st));
+  CPCA_CUDA(cudaStreamSynchronize(st));
+  if (flag & 1) {
+    set_error("cpca_decode_backward: shifted Gram system not positive definite (repeated singular values?)");
+    return CPCA_ERR_SINGULAR;
+  }
+  if (flag & 2) {
+    set_error("cpca_decode_backward: shifted Gram CG did not reach its tolerance");
+    return CPCA_ERR_NOT_CONVERGED;
+  }
+  return CPCA_OK;
+}
+
+extern "C" cpca_status cpca_decode_entries(const float* U, const float* V, int32_t ld, const double* sigma,
+                                           int32_t k, int64_t nh, const int32_t* h_row, const int32_t* h_col,
+                                           float* out, void* stream) {
+  clear_error();
+  CPCA_CHECK_ARG(nh >= 0 && k >= 0 && ld >= k, "cpca_decode_entries: bad sizes");
+  CPCA_CHECK_ARG(nh == 0 || (U && V && sigma && h_row && h_col && out), "cpca_decode_entries: null pointer");
+  if (nh == 0) return CPCA_OK;
+  entries_kernel<<<std::min<unsigned>(ceil_div(nh, 256), num_sms() * 4), 256, 0,
+                   static_cast<cudaStream_t>(stream)>>>(nh, h_row, h_col, U, ld, V, ld, sigma, k, out);
+  CPCA_LAUNCHED();
   return CPCA_OK;
 }

@@ -153,8 +153,6 @@ __global__ void step_kernel(const __grid_constant__ StepArgs a) {
 }
 
 // ------------------------------------------------------- FISTA iteration --
-constexpr int TB = 32;        // tile edge
-constexpr int kTileNbr = 40;  // neighbour-list entries staged per row / column
 
 struct FistaInst {
   const float* Yt;
@@ -190,89 +188,15 @@ __device__ __forceinline__ int find_inst(const FistaBatchArgs& a, int tile) {
 }
 
 struct TileSmem {
-  int64_t roff[TB][kTileNbr];  // element offset of neighbour row k in Z  (k * rc)
-  float rval[TB][kTileNbr];
-  int64_t coff[TB][kTileNbr];  // element offset of neighbour row k in ZT (k * rr)
-  float cval[TB][kTileNbr];
+  TileNbr nb;                  // neighbour lists of the tile's rows and columns
   float ac[TB][TB + 1];        // (Z Lc) of the tile, [row][col]
   float zt[TB][TB + 1];        // Z_{j+1} tile for the transposed store, [row][col]
-  int rdeg[TB], cdeg[TB];
-  int64_t rf0[TB], cf0[TB];
   unsigned int stopped[kMaxBatch / 32];
 };
 
-// For four staged neighbour lists u = 0..3 (rows or columns of the tile):
-// out[u] = sum_q w[u][q] * x[off[u][q] + base]. Chunks of 8 entries of all
-// four lists are loaded together (32 independent loads per lane) up to the
-// shortest list, then each list's remainder, then entries beyond the
-// staging area straight from the CSR.
-__device__ __forceinline__ void nbr_sum4(const int64_t (*off)[kTileNbr], const float (*w)[kTileNbr],
-                                         const int* deg, const int64_t* f0, int first, bool valid,
-                                         const float* __restrict__ x, int64_t base, const CsrView& L,
-                                         int64_t stride, float out[4]) {
-  int dmin = kTileNbr;
-#pragma unroll
-  for (int u = 0; u < 4; ++u) dmin = min(dmin, min(deg[first + u], kTileNbr));
-  float acc[4] = {0.f, 0.f, 0.f, 0.f};
-  if (valid) {
-    int e = 0;
-    for (; e + 8 <= dmin; e += 8) {
-      float v[4][8];
-#pragma unroll
-      for (int u = 0; u < 4; ++u)
-#pragma unroll
-        for (int q = 0; q < 8; ++q) v[u][q] = __ldcg(x + off[first + u][e + q] + base);
-#pragma unroll
-      for (int u = 0; u < 4; ++u)
-#pragma unroll
-        for (int q = 0; q < 8; ++q) acc[u] = fmaf(w[first + u][e + q], v[u][q], acc[u]);
-    }
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const int ds = min(deg[first + u], kTileNbr);
-      int e2 = e;
-      for (; e2 + 4 <= ds; e2 += 4) {
-        float v[4];
-#pragma unroll
-        for (int q = 0; q < 4; ++q) v[q] = __ldcg(x + off[first + u][e2 + q] + base);
-#pragma unroll
-        for (int q = 0; q < 4; ++q) acc[u] = fmaf(w[first + u][e2 + q], v[q], acc[u]);
-      }
-      for (; e2 < ds; ++e2) acc[u] = fmaf(w[first + u][e2], __ldcg(x + off[first + u][e2] + base), acc[u]);
-      for (int64_t f = f0[first + u] + kTileNbr; f < f0[first + u] + deg[first + u]; ++f)
-        acc[u] = fmaf(__ldg(L.val + f), __ldcg(x + int64_t(__ldg(L.col + f)) * stride + base), acc[u]);
-    }
-  }
-#pragma unroll
-  for (int u = 0; u < 4; ++u) out[u] = acc[u];
-}
-
 __device__ __forceinline__ void stage_tile(TileSmem& sm, const FistaInst& I, int i0, int j0, int ni,
                                            int nj) {
-  if (threadIdx.x < TB) {
-    const int r = threadIdx.x;
-    const int64_t f0 = r < ni ? I.Lr.rowptr[i0 + r] : 0;
-    sm.rf0[r] = f0;
-    sm.rdeg[r] = r < ni ? int(I.Lr.rowptr[i0 + r + 1] - f0) : 0;
-  } else if (threadIdx.x < 2 * TB) {
-    const int c = threadIdx.x - TB;
-    const int64_t g0 = c < nj ? I.Lc.rowptr[j0 + c] : 0;
-    sm.cf0[c] = g0;
-    sm.cdeg[c] = c < nj ? int(I.Lc.rowptr[j0 + c + 1] - g0) : 0;
-  }
-  __syncthreads();
-  for (int e = threadIdx.x; e < TB * kTileNbr; e += blockDim.x) {
-    const int r = e / kTileNbr, q = e % kTileNbr;
-    if (q < min(sm.rdeg[r], kTileNbr)) {
-      sm.roff[r][q] = int64_t(__ldg(I.Lr.col + sm.rf0[r] + q)) * I.rc;
-      sm.rval[r][q] = __ldg(I.Lr.val + sm.rf0[r] + q);
-    }
-    if (q < min(sm.cdeg[r], kTileNbr)) {
-      sm.coff[r][q] = int64_t(__ldg(I.Lc.col + sm.cf0[r] + q)) * I.rr;
-      sm.cval[r][q] = __ldg(I.Lc.val + sm.cf0[r] + q);
-    }
-  }
-  __syncthreads();
+  stage_nbr(sm.nb, I.Lr, I.Lc, I.rr, I.rc, i0, j0, ni, nj);
 }
 
 // RESIDENT: every block owns at most one tile for the whole solve; its
@@ -371,14 +295,14 @@ fista_batch_kernel(const __grid_constant__ FistaBatchArgs a) {
       // (Z Lc): warp w takes tile columns 4w..4w+3, lane = tile row
       {
         float o[4];
-        nbr_sum4(sm.coff, sm.cval, sm.cdeg, sm.cf0, warp * 4, lane < ni, ZTin, i0 + lane, I.Lc,
+        nbr_sum4(sm.nb.coff, sm.nb.cval, sm.nb.cdeg, sm.nb.cf0, warp * 4, lane < ni, ZTin, i0 + lane, I.Lc,
                  I.rr, o);
 #pragma unroll
         for (int u = 0; u < 4; ++u) sm.ac[lane][warp * 4 + u] = o[u];
       }
       // (Lr Z): warp w takes tile rows 4w..4w+3, lane = tile column
       float ar[4];
-      nbr_sum4(sm.roff, sm.rval, sm.rdeg, sm.rf0, warp * 4, lane < nj, Zin, j0 + lane, I.Lr, I.rc, ar);
+      nbr_sum4(sm.nb.roff, sm.nb.rval, sm.nb.rdeg, sm.nb.rf0, warp * 4, lane < nj, Zin, j0 + lane, I.Lr, I.rc, ar);
       __syncthreads();  // sm.ac complete
       double dz = 0.0, nz = 0.0;
 #pragma unroll

@@ -17,6 +17,100 @@ struct CsrView {
 constexpr int kMaxBatch = 128;  // instances per batched call (kernel-parameter table)
 constexpr int kObjBlocks = 512;
 
+// ---------------------------------------------------------------- tiles --
+// A rr x rc matrix is cut into TB x TB tiles. A tile stages the neighbour
+// lists of its rows (Lr) and columns (Lc) in shared memory, as element
+// offsets into a row-major (ld rc) and a column-major (ld rr) copy of the
+// matrix, so that both graph products read contiguous 128-byte segments:
+//   (Lr Z)(i, j) = sum_k Lr[i, k] Z(k, j)   -> segments of rows of Z,
+//   (Z Lc)(i, j) = sum_k Lc[j, k] ZT(k, i)  -> segments of rows of ZT.
+constexpr int TB = 32;        // tile edge
+constexpr int kTileNbr = 40;  // neighbour-list entries staged per row / column
+
+struct TileNbr {
+  int64_t roff[TB][kTileNbr];  // element offset of neighbour row k in Z  (k * rc)
+  float rval[TB][kTileNbr];
+  int64_t coff[TB][kTileNbr];  // element offset of neighbour row k in ZT (k * rr)
+  float cval[TB][kTileNbr];
+  int rdeg[TB], cdeg[TB];
+  int64_t rf0[TB], cf0[TB];
+};
+
+__device__ __forceinline__ void stage_nbr(TileNbr& nb, const CsrView& Lr, const CsrView& Lc, int rr,
+                                          int rc, int i0, int j0, int ni, int nj) {
+  if (threadIdx.x < TB) {
+    const int r = threadIdx.x;
+    const int64_t f0 = r < ni ? Lr.rowptr[i0 + r] : 0;
+    nb.rf0[r] = f0;
+    nb.rdeg[r] = r < ni ? int(Lr.rowptr[i0 + r + 1] - f0) : 0;
+  } else if (threadIdx.x < 2 * TB) {
+    const int c = threadIdx.x - TB;
+    const int64_t g0 = c < nj ? Lc.rowptr[j0 + c] : 0;
+    nb.cf0[c] = g0;
+    nb.cdeg[c] = c < nj ? int(Lc.rowptr[j0 + c + 1] - g0) : 0;
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < TB * kTileNbr; e += blockDim.x) {
+    const int r = e / kTileNbr, q = e % kTileNbr;
+    if (q < min(nb.rdeg[r], kTileNbr)) {
+      nb.roff[r][q] = int64_t(__ldg(Lr.col + nb.rf0[r] + q)) * rc;
+      nb.rval[r][q] = __ldg(Lr.val + nb.rf0[r] + q);
+    }
+    if (q < min(nb.cdeg[r], kTileNbr)) {
+      nb.coff[r][q] = int64_t(__ldg(Lc.col + nb.cf0[r] + q)) * rr;
+      nb.cval[r][q] = __ldg(Lc.val + nb.cf0[r] + q);
+    }
+  }
+  __syncthreads();
+}
+
+// For four staged neighbour lists u = 0..3 (rows or columns of the tile):
+// out[u] = sum_q w[u][q] * x[off[u][q] + base]. Chunks of 8 entries of all
+// four lists are loaded together (32 independent loads per lane) up to the
+// shortest list, then each list's remainder, then entries beyond the
+// staging area straight from the CSR. x is read through L2 (ld.global.cg):
+// other blocks of the same launch write it.
+__device__ __forceinline__ void nbr_sum4(const int64_t (*off)[kTileNbr], const float (*w)[kTileNbr],
+                                         const int* deg, const int64_t* f0, int first, bool valid,
+                                         const float* __restrict__ x, int64_t base, const CsrView& L,
+                                         int64_t stride, float out[4]) {
+  int dmin = kTileNbr;
+#pragma unroll
+  for (int u = 0; u < 4; ++u) dmin = min(dmin, min(deg[first + u], kTileNbr));
+  float acc[4] = {0.f, 0.f, 0.f, 0.f};
+  if (valid) {
+    int e = 0;
+    for (; e + 8 <= dmin; e += 8) {
+      float v[4][8];
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int q = 0; q < 8; ++q) v[u][q] = __ldcg(x + off[first + u][e + q] + base);
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int q = 0; q < 8; ++q) acc[u] = fmaf(w[first + u][e + q], v[u][q], acc[u]);
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int ds = min(deg[first + u], kTileNbr);
+      int e2 = e;
+      for (; e2 + 4 <= ds; e2 += 4) {
+        float v[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) v[q] = __ldcg(x + off[first + u][e2 + q] + base);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc[u] = fmaf(w[first + u][e2 + q], v[q], acc[u]);
+      }
+      for (; e2 < ds; ++e2) acc[u] = fmaf(w[first + u][e2], __ldcg(x + off[first + u][e2] + base), acc[u]);
+      for (int64_t f = f0[first + u] + kTileNbr; f < f0[first + u] + deg[first + u]; ++f)
+        acc[u] = fmaf(__ldg(L.val + f), __ldcg(x + int64_t(__ldg(L.col + f)) * stride + base), acc[u]);
+    }
+  }
+#pragma unroll
+  for (int u = 0; u < 4; ++u) out[u] = acc[u];
+}
+
 // Per-instance scratch of a FISTA solve.
 struct InstWs {
   float* Z0;          // Z_j ping (row-major)
@@ -61,5 +155,9 @@ cpca_status fista_objective(const float* Yt, int64_t ldy, int rr, int rc, const 
                             double* part, double* out, cudaStream_t st);
 cpca_status check_csr(const cpca_csr* L, int n, const char* name);
 int coop_blocks(const void* kernel, int threads, size_t smem, int want);
+// dloss/dL (FP64 on the CSR pattern) -> dloss/dw per entry (adjoint.cu);
+// deg and dD are scratch of L.n doubles each.
+cpca_status laplacian_weight_grad(const CsrView& L, const float* w, const double* dL, int lap_type,
+                                  float* dw, double* deg, double* dD, cudaStream_t st);
 
 }  // namespace cpca

@@ -261,6 +261,79 @@ def batched_comparison(M, torch, J=300, reps=3):
             "max_rel_fro_diff": diff, "autotuned_blocks": blocks}
 
 
+def adjoint_comparison(M, torch, Yd, cfg, n_heldout=10000, reps=3, h=1e-3):
+    """The differentiation workload: gradient of the held-out reconstruction
+    loss 1/2 sum_e (X_e - Y_e)^2 (10^4 entries outside the sampled block)
+    with respect to gamma_r, gamma_c, the sampled entries Y~ and the edge
+    weights of all four graphs, through torch.autograd on the library's
+    adjoints (FISTA reverse sweep checkpointed every 20 of 300 iterations;
+    also with the whole trajectory kept), against central differences in
+    gamma_r and gamma_c with four plain GPU pipeline solves (FISTA + decoder)."""
+    from paper_1602_02070_gb300 import autograd as AG
+    p, n = Yd.shape
+    K, J = cfg["K"], cfg["J"]
+    rr, rc = M.rho_of(p, cfg["fr"]), M.rho_of(n, cfg["fc"])
+    Lr, _, _ = M.cpca_knn_graph(Yd, K)
+    Lc, _, _ = M.cpca_knn_graph(Yd, K, transposed=True)
+    om_r, om_c, Yt = M.cpca_sample(0, p, n, rr, rc, Yd)
+    Lrt, _, _ = M.cpca_knn_graph(Yt, K)
+    Lct, _, _ = M.cpca_knn_graph(Yt, K, transposed=True)
+    hr_np, hc_np = gen.heldout_entries(7, p, n, n_heldout, om_r.cpu().numpy(), om_c.cpu().numpy())
+    hr = torch.as_tensor(hr_np, device=Yd.device)
+    hc = torch.as_tensor(hc_np, device=Yd.device)
+    target = Yd[hr.long(), hc.long()]
+    Ytc = Yt.contiguous()
+    pats = {"r": Lr, "c": Lc, "rt": Lrt, "ct": Lct}
+    dprm = M.decode_params(cg_tol=cfg["cg_tol"])
+
+    def gradient(ck):
+        w = {k_: G.weight.clone().requires_grad_(True) for k_, G in pats.items()}
+        Y_ = Ytc.clone().requires_grad_(True)
+        g_r = torch.tensor(cfg["gamma_r"], dtype=torch.float64, device=Yd.device, requires_grad=True)
+        g_c = torch.tensor(cfg["gamma_c"], dtype=torch.float64, device=Yd.device, requires_grad=True)
+        L = {k_: AG.laplacian(pats[k_].rowptr, pats[k_].col, w[k_]) for k_ in pats}
+        Xt = AG.frpcag(Y_, g_r, g_c, L["rt"], L["ct"], Lrt, Lct, max_iter=J, power_iters=200,
+                       ckpt_every=ck)
+        vals = AG.decode_entries(Xt, L["r"], L["c"], Lr, Lc, om_r, om_c, p, n, hr, hc, dprm)
+        loss = 0.5 * ((vals - target) ** 2).sum()
+        loss.backward()
+        n_grad = 2 + Y_.numel() + sum(x.numel() for x in w.values())
+        return g_r.grad.item(), g_c.grad.item(), n_grad
+
+    def fd():
+        out = []
+        for a, b in ((1 + h, 1.0), (1 - h, 1.0), (1.0, 1 + h), (1.0, 1 - h)):
+            X, _ = M.cpca_frpcag_solve(Yt, Lrt, Lct, gamma_r=a * cfg["gamma_r"],
+                                       gamma_c=b * cfg["gamma_c"], max_iter=J, want_info=False)
+            dec = M.cpca_decode(X, om_r, om_c, p, n, Lr, Lc, dprm, want_X=False)
+            v = M.capi.decode_entries(dec["U"], dec["V"], dec["sigma"], dec["k"], hr, hc)
+            out.append(0.5 * float(((v.double() - target.double()) ** 2).sum()))
+        return ((out[0] - out[1]) / (2 * h * cfg["gamma_r"]),
+                (out[2] - out[3]) / (2 * h * cfg["gamma_c"]))
+
+    def timed(fn):
+        fn()
+        best, res = 1e30, None
+        for _ in range(reps):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            res = fn()
+            torch.cuda.synchronize()
+            best = min(best, time.perf_counter() - t0)
+        return best * 1000.0, res
+
+    t_adj, (gr, gc, n_grad) = timed(lambda: gradient(20))
+    t_all, _ = timed(lambda: gradient(J))
+    t_fd, (fr, fc) = timed(fd)
+    return {"heldout_entries": int(n_heldout), "fista_iters": J, "checkpoint_every": 20,
+            "adjoint_ms": t_adj, "adjoint_whole_trajectory_ms": t_all,
+            "fd_gamma_4_solves_ms": t_fd, "speedup_vs_fd": t_fd / t_adj,
+            "gradient_entries": int(n_grad),
+            "dgamma_adjoint": [gr, gc], "dgamma_fd_fp32": [fr, fc],
+            "note": "wall time (host clock, synchronised) for the whole gradient; the finite "
+                    "differences give the two gamma derivatives only, from FP32 losses"}
+
+
 def roofline_for(name, ms, launches, ctx, peaks):
     """Algorithmic work of the named kernel over the timed region / its time."""
     hbm = peaks["hbm_gbs"] if peaks else 6800.0
@@ -305,6 +378,7 @@ def main():
     ap.add_argument("--impl", default="cpca", choices=["cpca", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--cpu-queries", type=int, default=32)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 0)
@@ -443,6 +517,8 @@ def main():
     }
     if not args.no_batched:
         line["batched_64"] = batched_comparison(M, torch)
+    if not args.no_adjoint:
+        line["adjoint"] = adjoint_comparison(M, torch, Yd, cfg)
     if world == 1 and not args.no_cpu_baseline:
         dec = decoder_graphs_for_timing(Y, cfg["K"])
         secs = oracle_step_seconds(Y, cfg, args.cpu_queries, dec)

@@ -27,7 +27,8 @@ from __future__ import annotations
 
 import numpy as np
 
-__all__ = ["make_instance", "make_instance_torch", "CONFIGS", "batched_instances"]
+__all__ = ["make_instance", "make_instance_torch", "CONFIGS", "batched_instances",
+           "heldout_entries"]
 
 
 def make_instance(seed: int, p: int, n: int, r: int, C: int, frac: float,
@@ -104,3 +105,15 @@ def batched_instances(count: int = 64, seed: int = 1000):
                         fr=0.25, fc=0.25, J=300,
                         gamma_r=float(grid[i % 8]), gamma_c=float(grid[(i // 8) % 8])))
     return out
+
+
+def heldout_entries(seed: int, p: int, n: int, count: int, omega_r, omega_c):
+    """`count` distinct entries (i, j) of a p x n matrix drawn uniformly among
+    those outside the sampled block omega_r x omega_c (the held-out entries
+    of a reconstruction loss). Returns (rows, cols) as int32 arrays."""
+    rng = np.random.default_rng(seed)
+    inside = np.zeros((p, n), dtype=bool)
+    inside[np.ix_(np.asarray(omega_r), np.asarray(omega_c))] = True
+    cand = np.flatnonzero(~inside.ravel())
+    pick = np.sort(rng.choice(cand, size=min(count, cand.size), replace=False))
+    return (pick // n).astype(np.int32), (pick % n).astype(np.int32)

@@ -282,7 +282,16 @@ cpca_status cpca_frpcag_solve_noalloc(const float* Yt, int32_t rr, int32_t rc, i
  * each segment is recomputed once before its reverse sweep. Cost: about
  * two forward solves plus the reverse sweep (two graph products per
  * iteration); scratch from cpca_frpcag_backward_workspace_size.
+ * resume != 0: `ws` holds the tape of a cpca_frpcag_forward_tape call with
+ * the same inputs, params and ckpt_every (power iterates, lambda and the
+ * checkpoints), so the first forward pass is skipped.
  * All device pointers; ginfo is host. SYNCHRONISES the stream.
+ *
+ * cpca_frpcag_forward_tape: the forward solve (X = S_J, as
+ * cpca_frpcag_solve with eps = 0, same arithmetic per entry) that also
+ * records the tape in `ws` (cpca_frpcag_backward_workspace_size bytes) for a
+ * later cpca_frpcag_backward(..., resume = 1, ...). ginfo (host, optional)
+ * receives lambda and the norm estimates. SYNCHRONISES.
  * ---------------------------------------------------------------------- */
 typedef struct cpca_frpcag_grad_info {
   double dgamma_r, dgamma_c;  /* total derivatives */
@@ -295,9 +304,15 @@ typedef struct cpca_frpcag_grad_info {
 size_t cpca_frpcag_backward_workspace_size(int32_t rr, int32_t rc, int32_t max_iter,
                                            int32_t ckpt_every, int32_t power_iters,
                                            int64_t nnz_r, int64_t nnz_c);
+cpca_status cpca_frpcag_forward_tape(const float* Yt, int32_t rr, int32_t rc, int64_t ldyt,
+                                     const cpca_csr* Lr, const cpca_csr* Lc,
+                                     const cpca_frpcag_params* params, int32_t ckpt_every, float* X,
+                                     int64_t ldx, cpca_frpcag_grad_info* ginfo, void* ws,
+                                     size_t ws_bytes, void* stream);
 cpca_status cpca_frpcag_backward(const float* Yt, int32_t rr, int32_t rc, int64_t ldyt,
                                  const cpca_csr* Lr, const cpca_csr* Lc,
                                  const cpca_frpcag_params* params, int32_t ckpt_every,
+                                 int32_t resume,
                                  const float* dX, int64_t lddx, float* dYt, int64_t lddyt,
                                  double* dLr, double* dLc, const float* wr, const float* wc,
                                  int32_t lap_type, float* dwr, float* dwc,
@@ -376,7 +391,10 @@ cpca_status cpca_decode(const float* Xt, int32_t rr, int32_t rc, int64_t ldxt,
  *     edge's derivative at both of its entries.
  * Same inputs and parameters as the forward call, plus the forward's k
  * (1 <= k <= kmax); the forward factors are recomputed with that k
- * (partial SVD, both upsampling solves). Steps: scatter of h_grad into
+ * (partial SVD, both upsampling solves), unless resume != 0: then `ws`
+ * must be the workspace of a cpca_decode call with the same inputs and
+ * parameters (cpca_decode accepts this larger workspace), whose factors are
+ * reused (k must equal the k it found). Steps: scatter of h_grad into
  * dU, dV, dsigma; the adjoint of the column normalisation; one adjoint
  * Jacobi-PCG per side on L_aa (to cg_tol); the top-k SVD derivative
  * (Townsend's formula, with the parts outside the top-k subspaces through
@@ -390,7 +408,8 @@ size_t cpca_decode_backward_workspace_size(int32_t p, int32_t n, int32_t rr, int
 cpca_status cpca_decode_backward(const float* Xt, int32_t rr, int32_t rc, int64_t ldxt,
                                  const int32_t* omega_r, const int32_t* omega_c, int32_t p, int32_t n,
                                  const cpca_csr* Lr, const cpca_csr* Lc,
-                                 const cpca_decode_params* params, int32_t k, int64_t nh,
+                                 const cpca_decode_params* params, int32_t k, int32_t resume,
+                                 int64_t nh,
                                  const int32_t* h_row, const int32_t* h_col, const float* h_grad,
                                  float* dXt, int64_t lddxt, double* dLr, double* dLc,
                                  const float* wr, const float* wc, int32_t lap_type, float* dwr,

@@ -49,11 +49,14 @@ class _FRPCAG(torch.autograd.Function):
         Lc = Csr(Lc_pat.rowptr, Lc_pat.col, Lc_val.contiguous())
         prm = capi.frpcag_params(float(gamma_r), float(gamma_c), -1.0, int(max_iter), 0.0,
                                  int(power_iters))
-        X, _ = capi.cpca_frpcag_solve(Yt, Lr, Lc, prm, want_info=False)
+        # the forward keeps its tape (power iterates, lambda, checkpoints)
+        # for the backward, which then skips recomputing them
+        X, ws, _ = capi.cpca_frpcag_forward_tape(Yt, Lr, Lc, prm, int(ckpt_every))
         ctx.save_for_backward(Yt, gamma_r, Lr.val, Lc.val)
         ctx.graphs = (Lr, Lc)
         ctx.prm = prm
         ctx.ckpt_every = int(ckpt_every)
+        ctx.tape = ws
         return X
 
     @staticmethod
@@ -61,7 +64,8 @@ class _FRPCAG(torch.autograd.Function):
         Yt, gamma_r, _, _ = ctx.saved_tensors
         Lr, Lc = ctx.graphs
         out = capi.cpca_frpcag_backward(Yt, Lr, Lc, dX.contiguous(), ctx.prm, ctx.ckpt_every,
-                                        want_dL=True)
+                                        want_dL=True, ws=ctx.tape, resume=True)
+        ctx.tape = None
         info = out["info"]
         dgr = torch.tensor(info.dgamma_r, dtype=gamma_r.dtype, device=gamma_r.device)
         dgc = torch.tensor(info.dgamma_c, dtype=gamma_r.dtype, device=gamma_r.device)
@@ -86,11 +90,14 @@ class _DecodeEntries(torch.autograd.Function):
                 dparams):
         Lr = Csr(Lr_pat.rowptr, Lr_pat.col, Lr_val.contiguous())
         Lc = Csr(Lc_pat.rowptr, Lc_pat.col, Lc_val.contiguous())
-        dec = capi.cpca_decode(Xt, omega_r, omega_c, p, n, Lr, Lc, dparams, want_X=False)
+        # the backward's workspace: the decoder leaves its factors there
+        ws = capi.decode_backward_workspace(Xt, p, n, Lr, Lc, dparams)
+        dec = capi.cpca_decode(Xt, omega_r, omega_c, p, n, Lr, Lc, dparams, want_X=False, ws=ws)
         vals = capi.decode_entries(dec["U"], dec["V"], dec["sigma"], dec["k"], h_row, h_col)
         ctx.save_for_backward(Xt, Lr.val, Lc.val, omega_r, omega_c, h_row, h_col)
         ctx.graphs = (Lr, Lc)
         ctx.meta = (p, n, dec["k"], dparams)
+        ctx.ws = ws
         return vals
 
     @staticmethod
@@ -99,7 +106,9 @@ class _DecodeEntries(torch.autograd.Function):
         Lr, Lc = ctx.graphs
         p, n, k, dparams = ctx.meta
         out = capi.cpca_decode_backward(Xt, omega_r, omega_c, p, n, Lr, Lc, k, h_row, h_col,
-                                        g.float().contiguous(), dparams, want_dL=True)
+                                        g.float().contiguous(), dparams, want_dL=True, ws=ctx.ws,
+                                        resume=True)
+        ctx.ws = None
         return (out["dXt"], out["dLr"].float(), out["dLc"].float()) + (None,) * 9
 
 

@@ -114,9 +114,13 @@ _SIGS = [
      [C.c_void_p, C.c_int32, C.POINTER(C.c_int32), C.POINTER(C.c_float), C.c_void_p, C.c_size_t,
       C.c_void_p]),
     ("cpca_frpcag_backward_workspace_size", C.c_size_t, [C.c_int32] * 5 + [C.c_int64] * 2),
+    ("cpca_frpcag_forward_tape", C.c_int32,
+     [C.c_void_p, C.c_int32, C.c_int32, C.c_int64, C.POINTER(cpca_csr), C.POINTER(cpca_csr),
+      C.POINTER(cpca_frpcag_params), C.c_int32, C.c_void_p, C.c_int64,
+      C.POINTER(cpca_frpcag_grad_info), C.c_void_p, C.c_size_t, C.c_void_p]),
     ("cpca_frpcag_backward", C.c_int32,
      [C.c_void_p, C.c_int32, C.c_int32, C.c_int64, C.POINTER(cpca_csr), C.POINTER(cpca_csr),
-      C.POINTER(cpca_frpcag_params), C.c_int32, C.c_void_p, C.c_int64, C.c_void_p, C.c_int64,
+      C.POINTER(cpca_frpcag_params), C.c_int32, C.c_int32, C.c_void_p, C.c_int64, C.c_void_p, C.c_int64,
       C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p,
       C.POINTER(cpca_frpcag_grad_info), C.c_void_p, C.c_size_t, C.c_void_p]),
     ("cpca_laplacian_workspace_size", C.c_size_t, [C.c_int32]),
@@ -133,7 +137,7 @@ _SIGS = [
     ("cpca_decode_backward", C.c_int32,
      [C.c_void_p, C.c_int32, C.c_int32, C.c_int64, C.c_void_p, C.c_void_p, C.c_int32, C.c_int32,
       C.POINTER(cpca_csr), C.POINTER(cpca_csr), C.POINTER(cpca_decode_params), C.c_int32,
-      C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p,
+      C.c_int32, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p,
       C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p,
       C.c_size_t, C.c_void_p]),
     ("cpca_decode", C.c_int32,
@@ -356,23 +360,49 @@ def cpca_frpcag_solve_noalloc(Yt: torch.Tensor, Lr: Csr, Lc: Csr,
     return X, info
 
 
+def frpcag_tape_workspace(Yt: torch.Tensor, Lr: Csr, Lc: Csr, params: cpca_frpcag_params,
+                          ckpt_every: int = 20) -> torch.Tensor:
+    rr, rc = Yt.shape
+    T = 0 if params.step > 0 else params.power_iters
+    return _workspace(lib().cpca_frpcag_backward_workspace_size(rr, rc, params.max_iter, ckpt_every, T,
+                                                                Lr.nnz, Lc.nnz), Yt.device)
+
+
+def cpca_frpcag_forward_tape(Yt: torch.Tensor, Lr: Csr, Lc: Csr, params: cpca_frpcag_params,
+                             ckpt_every: int = 20, ws=None):
+    """Forward FISTA solve that records the tape for cpca_frpcag_backward
+    (resume=True). Returns (X, ws, info)."""
+    _require_cuda(Yt, torch.float32, "Yt")
+    rr, rc = Yt.shape
+    if ws is None:
+        ws = frpcag_tape_workspace(Yt, Lr, Lc, params, ckpt_every)
+    X = torch.empty(rr, rc, dtype=torch.float32, device=Yt.device)
+    info = cpca_frpcag_grad_info()
+    lr, lc = Lr.c(), Lc.c()
+    _check(lib().cpca_frpcag_forward_tape(_ptr(Yt), rr, rc, Yt.stride(0), C.byref(lr), C.byref(lc),
+                                          C.byref(params), ckpt_every, _ptr(X), X.stride(0),
+                                          C.byref(info), _ptr(ws), ws.numel(), _stream()))
+    return X, ws, info
+
+
 def cpca_frpcag_backward(Yt: torch.Tensor, Lr: Csr, Lc: Csr, dX: torch.Tensor,
                          params: cpca_frpcag_params | None = None, ckpt_every: int = 20,
                          want_dL: bool = True, want_dw: bool = False,
-                         lap_type: int = LAP_NORMALIZED, ws=None, **kw):
+                         lap_type: int = LAP_NORMALIZED, ws=None, resume: bool = False, **kw):
     """Reverse-mode derivative of cpca_frpcag_solve for dloss/dX = dX.
     Returns dict: dYt (rr x rc), dLr, dLc (FP64 per CSR entry, or None),
     dwr, dwc (FP32 per CSR entry, needs Lr.weight / Lc.weight, or None),
-    info (cpca_frpcag_grad_info)."""
+    info (cpca_frpcag_grad_info). resume=True reuses the tape that
+    cpca_frpcag_forward_tape left in ``ws``."""
     _require_cuda(Yt, torch.float32, "Yt")
     _require_cuda(dX, torch.float32, "dX")
     prm = params if params is not None else frpcag_params(**kw)
     rr, rc = Yt.shape
     dev = Yt.device
-    T = 0 if prm.step > 0 else prm.power_iters
+    if resume and ws is None:
+        raise ValueError("resume needs the forward tape workspace")
     if ws is None:
-        ws = _workspace(lib().cpca_frpcag_backward_workspace_size(rr, rc, prm.max_iter, ckpt_every, T,
-                                                                  Lr.nnz, Lc.nnz), dev)
+        ws = frpcag_tape_workspace(Yt, Lr, Lc, prm, ckpt_every)
     dY = torch.empty(rr, rc, dtype=torch.float32, device=dev)
     dLr = torch.empty(Lr.nnz, dtype=torch.float64, device=dev) if want_dL else None
     dLc = torch.empty(Lc.nnz, dtype=torch.float64, device=dev) if want_dL else None
@@ -386,7 +416,7 @@ def cpca_frpcag_backward(Yt: torch.Tensor, Lr: Csr, Lc: Csr, dX: torch.Tensor,
     lr, lc = Lr.c(), Lc.c()
     _check(lib().cpca_frpcag_backward(
         _ptr(Yt), rr, rc, Yt.stride(0), C.byref(lr), C.byref(lc), C.byref(prm), ckpt_every,
-        _ptr(dX), dX.stride(0), _ptr(dY), dY.stride(0), _ptr(dLr), _ptr(dLc),
+        int(resume), _ptr(dX), dX.stride(0), _ptr(dY), dY.stride(0), _ptr(dLr), _ptr(dLc),
         _ptr(Lr.weight) if want_dw else None, _ptr(Lc.weight) if want_dw else None, lap_type,
         _ptr(dwr), _ptr(dwc), C.byref(info), _ptr(ws), ws.numel(), _stream()))
     return {"dYt": dY, "dLr": dLr, "dLc": dLc, "dwr": dwr, "dwc": dwc, "info": info}
@@ -469,23 +499,33 @@ def cpca_decode(Xt: torch.Tensor, omega_r: torch.Tensor, omega_c: torch.Tensor, 
             "status": st}
 
 
+def decode_backward_workspace(Xt: torch.Tensor, p: int, n: int, Lr: Csr, Lc: Csr,
+                              params: cpca_decode_params) -> torch.Tensor:
+    rr, rc = Xt.shape
+    return _workspace(lib().cpca_decode_backward_workspace_size(p, n, rr, rc, params.kmax, Lr.nnz,
+                                                                Lc.nnz), Xt.device)
+
+
 def cpca_decode_backward(Xt: torch.Tensor, omega_r: torch.Tensor, omega_c: torch.Tensor, p: int,
                          n: int, Lr: Csr, Lc: Csr, k: int, h_row: torch.Tensor,
                          h_col: torch.Tensor, h_grad: torch.Tensor,
                          params: cpca_decode_params | None = None, want_dL: bool = True,
-                         want_dw: bool = False, lap_type: int = LAP_NORMALIZED, ws=None, **kw):
+                         want_dw: bool = False, lap_type: int = LAP_NORMALIZED, ws=None,
+                         resume: bool = False, **kw):
     """Reverse-mode derivative of cpca_decode (rank k fixed) for a loss of X
     at entries (h_row, h_col) with gradient h_grad there. Returns dict:
     dXt (rr x rc), dLr, dLc (FP64 per CSR entry or None), dwr, dwc (FP32 per
-    CSR entry, needs Lr.weight / Lc.weight, or None)."""
+    CSR entry, needs Lr.weight / Lc.weight, or None). resume=True reuses the
+    factors a cpca_decode call left in ``ws`` (decode_backward_workspace)."""
     _require_cuda(Xt, torch.float32, "Xt")
     _require_cuda(h_grad, torch.float32, "h_grad")
     prm = params if params is not None else decode_params(**kw)
     rr, rc = Xt.shape
     dev = Xt.device
+    if resume and ws is None:
+        raise ValueError("resume needs the forward's workspace")
     if ws is None:
-        ws = _workspace(lib().cpca_decode_backward_workspace_size(p, n, rr, rc, prm.kmax, Lr.nnz,
-                                                                  Lc.nnz), dev)
+        ws = decode_backward_workspace(Xt, p, n, Lr, Lc, prm)
     dXt = torch.empty(rr, rc, dtype=torch.float32, device=dev)
     dLr = torch.empty(Lr.nnz, dtype=torch.float64, device=dev) if want_dL else None
     dLc = torch.empty(Lc.nnz, dtype=torch.float64, device=dev) if want_dL else None
@@ -499,7 +539,7 @@ def cpca_decode_backward(Xt: torch.Tensor, omega_r: torch.Tensor, omega_c: torch
     nh = h_grad.numel()
     _check(lib().cpca_decode_backward(
         _ptr(Xt), rr, rc, Xt.stride(0), _ptr(omega_r), _ptr(omega_c), p, n, C.byref(lr),
-        C.byref(lc), C.byref(prm), k, nh, _ptr(h_row), _ptr(h_col), _ptr(h_grad), _ptr(dXt),
+        C.byref(lc), C.byref(prm), k, int(resume), nh, _ptr(h_row), _ptr(h_col), _ptr(h_grad), _ptr(dXt),
         dXt.stride(0), _ptr(dLr), _ptr(dLc), _ptr(Lr.weight) if want_dw else None,
         _ptr(Lc.weight) if want_dw else None, lap_type, _ptr(dwr), _ptr(dwc), _ptr(ws), ws.numel(),
         _stream()))

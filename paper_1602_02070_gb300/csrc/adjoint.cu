@@ -196,27 +196,59 @@ traj_forward_kernel(const __grid_constant__ TrajArgs a) {
 // of the tile, entry q: sum over the 32 lanes of x[off + base] * own[u],
 // added (times scale) to P[f0 + q], or to P[tmap[f0 + q]] (the transposed
 // entry) when tmap is given. Lanes with !valid contribute 0.
+// Eight entries at a time: eight independent gathers per lane, then a
+// butterfly that leaves each entry's 32-lane sum in four lanes (9 shuffles
+// for 8 sums), and eight lanes update P in parallel.
 __device__ __forceinline__ void pattern_partials(const int64_t (*off)[kTileNbr], const int* deg,
                                                  const int64_t* f0, int first, bool valid,
                                                  const float* __restrict__ x, int64_t base,
                                                  const CsrView& L, int64_t stride, const float own[4],
                                                  double scale, double* __restrict__ P,
                                                  const int64_t* __restrict__ tmap, int lane) {
+  const bool h16 = lane & 16, h8 = lane & 8, h4 = lane & 4;
+  const int mine = (h16 ? 4 : 0) + (h8 ? 2 : 0) + (h4 ? 1 : 0);  // entry whose sum this lane ends with
 #pragma unroll
   for (int u = 0; u < 4; ++u) {
     const int d = deg[first + u];
-    for (int q = 0; q < d; ++q) {
-      float xv = 0.f;
-      if (valid) {
-        const int64_t o = q < kTileNbr ? off[first + u][q]
-                                       : int64_t(__ldg(L.col + f0[first + u] + q)) * stride;
-        xv = __ldcg(x + o + base);
+    const int64_t fu = f0[first + u];
+    for (int q0 = 0; q0 < d; q0 += 8) {
+      float v[8];
+#pragma unroll
+      for (int t = 0; t < 8; ++t) {
+        const int q = q0 + t;
+        float xv = 0.f;
+        if (valid && q < d) {
+          const int64_t o = q < kTileNbr ? off[first + u][q] : int64_t(__ldg(L.col + fu + q)) * stride;
+          xv = __ldcg(x + o + base);
+        }
+        v[t] = xv * own[u];
       }
-      const float s = warp_sumf(xv * own[u]);
-      if (lane == 0 && s != 0.f) {
-        const int64_t e = f0[first + u] + q;
+      float w4[4], w2[2];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const float send = h16 ? v[i] : v[i + 4];
+        const float keep = h16 ? v[i + 4] : v[i];
+        w4[i] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+      }
+#pragma unroll
+      for (int i = 0; i < 2; ++i) {
+        const float send = h8 ? w4[i] : w4[i + 2];
+        const float keep = h8 ? w4[i + 2] : w4[i];
+        w2[i] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+      }
+      float y;
+      {
+        const float send = h4 ? w2[0] : w2[1];
+        const float keep = h4 ? w2[1] : w2[0];
+        y = keep + __shfl_xor_sync(0xffffffffu, send, 4);
+      }
+      y += __shfl_xor_sync(0xffffffffu, y, 2);
+      y += __shfl_xor_sync(0xffffffffu, y, 1);
+      const int q = q0 + mine;
+      if ((lane & 3) == 0 && q < d && y != 0.f) {
+        const int64_t e = fu + q;
         const int64_t t = tmap ? __ldg(tmap + e) : e;  // -1: no transposed entry
-        if (t >= 0) P[t] += scale * double(s);
+        if (t >= 0) P[t] += scale * double(y);
       }
     }
   }
@@ -342,6 +374,227 @@ traj_reverse_kernel(const __grid_constant__ TrajArgs a) {
         }
       }
       __syncthreads();
+    }
+  }
+  s_lam = block_sum(s_lam, red);
+  s_gr = block_sum(s_gr, red);
+  s_gc = block_sum(s_gc, red);
+  if (threadIdx.x == 0) {
+    atomicAdd(a.scal_bar + 0, s_lam);
+    atomicAdd(a.scal_bar + 1, s_gr);
+    atomicAdd(a.scal_bar + 2, s_gc);
+  }
+}
+
+// Resident variant: one tile per block for the whole launch. The
+// neighbour lists are staged once, and the tile's dL partial sums for its
+// staged entries accumulate in shared memory (FP32 within one segment,
+// added to the FP64 partial buffers at the end of the launch).
+struct ResSmem {
+  TileNbr32 nb;
+  float ac[TB][TB + 1];
+  float tl[TB][TB + 1];
+  float pr[TB][kTileNbr];
+  float pc[TB][kTileNbr];
+};
+
+// Partial sums of dL for the four staged lists u of the tile: for every
+// list entry q, the 32-lane sum of x[off[u][q] + base] * own[u] is added to
+// acc[first + u][q] (beyond the staged entries: scale times it to P at
+// entry tmap(f0 + q), or f0 + q without a map). With weights w, out[u] also
+// receives sum_q w[u][q] x[off[u][q] + base]. Eight entries at a time:
+// eight independent gathers, a butterfly that leaves each entry's sum in
+// four lanes (9 shuffles for 8 sums), eight lanes update in parallel.
+__device__ __forceinline__ void nbr_sum_partials(const int32_t (*off)[kTileNbr], const float (*w)[kTileNbr],
+                                                 const int* deg, const int64_t* f0, int first, bool valid,
+                                                 const float* __restrict__ x, int64_t base, const CsrView& L,
+                                                 int64_t stride, const float own[4], float (*acc)[kTileNbr],
+                                                 double scale, double* __restrict__ P,
+                                                 const int64_t* __restrict__ tmap, int lane, float out[4]) {
+  const bool h16 = lane & 16, h8 = lane & 8, h4 = lane & 4;
+  const int mine = (h16 ? 4 : 0) + (h8 ? 2 : 0) + (h4 ? 1 : 0);
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const int d = deg[first + u];
+    const int64_t fu = f0[first + u];
+    float sum = 0.f;
+    for (int q0 = 0; q0 < d; q0 += 8) {
+      float v[8];
+#pragma unroll
+      for (int t = 0; t < 8; ++t) {
+        const int q = q0 + t;
+        float xv = 0.f, wv = 0.f;
+        if (q < d) {
+          if (q < kTileNbr) {
+            if (w) wv = w[first + u][q];
+            if (valid) xv = __ldcg(x + int64_t(off[first + u][q]) + base);
+          } else {
+            if (w) wv = __ldg(L.val + fu + q);
+            if (valid) xv = __ldcg(x + int64_t(__ldg(L.col + fu + q)) * stride + base);
+          }
+        }
+        sum = fmaf(wv, xv, sum);
+        v[t] = xv * own[u];
+      }
+      float w4[4], w2[2];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const float send = h16 ? v[i] : v[i + 4];
+        const float keep = h16 ? v[i + 4] : v[i];
+        w4[i] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+      }
+#pragma unroll
+      for (int i = 0; i < 2; ++i) {
+        const float send = h8 ? w4[i] : w4[i + 2];
+        const float keep = h8 ? w4[i + 2] : w4[i];
+        w2[i] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+      }
+      float y;
+      {
+        const float send = h4 ? w2[0] : w2[1];
+        const float keep = h4 ? w2[1] : w2[0];
+        y = keep + __shfl_xor_sync(0xffffffffu, send, 4);
+      }
+      y += __shfl_xor_sync(0xffffffffu, y, 2);
+      y += __shfl_xor_sync(0xffffffffu, y, 1);
+      const int q = q0 + mine;
+      if ((lane & 3) == 0 && q < d && y != 0.f) {
+        if (q < kTileNbr) {
+          acc[first + u][q] += y;
+        } else {
+          const int64_t e = fu + q;
+          const int64_t t = tmap ? __ldg(tmap + e) : e;
+          if (t >= 0) P[t] += scale * double(y);
+        }
+      }
+    }
+    out[u] = sum;
+  }
+}
+
+__global__ void __launch_bounds__(256, 5)
+traj_reverse_resident_kernel(const __grid_constant__ TrajArgs a) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  ResSmem& sm = *reinterpret_cast<ResSmem*>(smraw);
+  __shared__ double red[8];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const float lam = float(*a.lam);
+  const double lamd = double(lam);
+  const int64_t nnz_r = a.Lr.rowptr[a.rr], nnz_c = a.Lc.rowptr[a.rc];
+  int i0, j0, ni, nj;
+  tile_of(a, blockIdx.x, i0, j0, ni, nj);
+  const int ti = i0 / TB, tj = j0 / TB;
+  stage_nbr(sm.nb, a.Lr, a.Lc, a.rr, a.rc, i0, j0, ni, nj);
+  for (int e = threadIdx.x; e < TB * kTileNbr; e += blockDim.x) {
+    sm.pr[e / kTileNbr][e % kTileNbr] = 0.f;
+    sm.pc[e / kTileNbr][e % kTileNbr] = 0.f;
+  }
+  const double sr = -2.0 * lamd * a.gamma_r, sc = -2.0 * lamd * a.gamma_c;
+  double* Prt = a.Pr + int64_t(tj) * nnz_r;
+  double* Pct = a.Pc + int64_t(ti) * nnz_c;
+  double s_lam = 0.0, s_gr = 0.0, s_gc = 0.0;
+  for (int j = a.jb; j >= a.ja; --j) {
+    const int par = j & 1;
+    const float* Zin = a.Zs + slot_off(a, j);
+    const float* ZTin = a.ZTs + slot_off(a, j);
+    __syncthreads();  // sm.ac / sm.tl of the previous phase are consumed
+    {
+      float o[4];
+      nbr_sum4(sm.nb.coff, sm.nb.cval, sm.nb.cdeg, sm.nb.cf0, warp * 4, lane < ni, ZTin, i0 + lane, a.Lc,
+               a.rr, o);
+#pragma unroll
+      for (int u = 0; u < 4; ++u) sm.ac[lane][warp * 4 + u] = o[u];
+    }
+    float ar[4];
+    nbr_sum4(sm.nb.roff, sm.nb.rval, sm.nb.rdeg, sm.nb.rf0, warp * 4, lane < nj, Zin, j0 + lane, a.Lr, a.rc, ar);
+    __syncthreads();
+    float vrow[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int r = warp * 4 + u;
+      float vb = 0.f;
+      if (r < ni && lane < nj) {
+        const int64_t i = i0 + r, jj = j0 + lane;
+        const float z = __ldcg(Zin + i * a.rc + jj);
+        const float y = __ldg(a.Yt + i * a.ldy + jj);
+        const float gr = fmaf(a.two_gr, ar[u], a.two_gc * sm.ac[r][lane]);
+        const float v = fmaf(-lam, gr, z);
+        const float dl = v - y;
+        const float sb = a.Sb[i * a.rc + jj];
+        vb = (fabsf(dl) - lam) > 0.f ? sb : 0.f;
+        a.dY[i * a.lddy + jj] += sb - vb;
+        if (vb != 0.f) {
+          s_lam += -double(copysignf(1.f, dl)) * vb - double(vb) * double(gr);
+          s_gr += -2.0 * lamd * double(vb) * double(ar[u]);
+          s_gc += -2.0 * lamd * double(vb) * double(sm.ac[r][lane]);
+        }
+        a.Vb[par][i * a.rc + jj] = vb;
+      }
+      vrow[u] = vb;
+      sm.tl[r][lane] = vb;
+    }
+    __syncthreads();
+    float vcol[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int c = warp * 4 + u;
+      vcol[u] = sm.tl[lane][c];
+      if (c < nj && lane < ni) a.VbT[par][int64_t(j0 + c) * a.rr + i0 + lane] = vcol[u];
+    }
+    // dLr(a, b) += scale sum_c Vb(a, c) Z(b, c) over the tile's columns;
+    // dLc(a, b) += scale sum_r Z(r, a) Vb(r, b) over its rows: column b's
+    // list (b, a) lands on the transposed entry (a, b)
+    float dummy[4];
+    if (a.gamma_r != 0.0)
+      nbr_sum_partials(sm.nb.roff, nullptr, sm.nb.rdeg, sm.nb.rf0, warp * 4, lane < nj, Zin, j0 + lane, a.Lr,
+                       a.rc, vrow, sm.pr, sr, Prt, nullptr, lane, dummy);
+    if (a.gamma_c != 0.0)
+      nbr_sum_partials(sm.nb.coff, nullptr, sm.nb.cdeg, sm.nb.cf0, warp * 4, lane < ni, ZTin, i0 + lane, a.Lc,
+                       a.rr, vcol, sm.pc, sc, Pct, a.tmap_c, lane, dummy);
+    if (!grid_sync(a.bar)) return;
+    const float* V = a.Vb[par];
+    const float* VT = a.VbT[par];
+    const float mup = j >= 2 ? a.mu[j - 1] : 0.f;
+    {
+      float o[4];
+      nbr_sum4(sm.nb.coff, sm.nb.cval, sm.nb.cdeg, sm.nb.cf0, warp * 4, lane < ni, VT, i0 + lane, a.Lc, a.rr,
+               o);
+#pragma unroll
+      for (int u = 0; u < 4; ++u) sm.ac[lane][warp * 4 + u] = o[u];
+    }
+    nbr_sum4(sm.nb.roff, sm.nb.rval, sm.nb.rdeg, sm.nb.rf0, warp * 4, lane < nj, V, j0 + lane, a.Lr, a.rc, ar);
+    __syncthreads();
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int r = warp * 4 + u;
+      if (r < ni && lane < nj) {
+        const int64_t i = i0 + r, jj = j0 + lane;
+        const float vb = vrow[u];
+        const float g = fmaf(a.two_gr, ar[u], a.two_gc * sm.ac[r][lane]);
+        const float zb = fmaf(-lam, g, vb);
+        const int64_t l = i * a.rc + jj;
+        if (j >= 2) {
+          a.Sb[l] = fmaf(1.f + mup, zb, a.A2[l]);
+          a.A2[l] = -mup * zb;
+        } else {
+          a.dY[i * a.lddy + jj] += zb + a.A2[l];
+          a.Sb[l] = 0.f;
+          a.A2[l] = 0.f;
+        }
+      }
+    }
+  }
+  __syncthreads();
+  // flush the staged entries' partial sums: row lists land on their own
+  // entries of Lr, column lists on the transposed entries of Lc
+  for (int e = threadIdx.x; e < TB * kTileNbr; e += blockDim.x) {
+    const int r = e / kTileNbr, q = e % kTileNbr;
+    const float vr = sm.pr[r][q];
+    if (vr != 0.f) Prt[sm.nb.rf0[r] + q] += sr * double(vr);
+    const float vc = sm.pc[r][q];
+    if (vc != 0.f) {
+      const int64_t t = __ldg(a.tmap_c + sm.nb.cf0[r] + q);
+      if (t >= 0) Pct[t] += sc * double(vc);
     }
   }
   s_lam = block_sum(s_lam, red);
@@ -655,7 +908,7 @@ BwdWs bwd_layout(void* ws, int rr, int rc, int J, int ck, int T, int64_t nnz_r, 
   BwdWs w{};
   const size_t mn = size_t(rr) * rc;
   const int nseg = (J + ck - 1) / ck;
-  const int nslot = std::max(ck, 2);
+  const int nslot = std::max(ck + 1, 2);
   w.mu = c.take<float>(size_t(J) + 2);
   w.scal = c.take<double>(4);
   w.bar = c.take<double>(4);
@@ -745,47 +998,68 @@ extern "C" size_t cpca_frpcag_backward_workspace_size(int32_t rr, int32_t rc, in
   return bwd_layout(nullptr, rr, rc, max_iter, ck, power_iters, nnz_r, nnz_c).bytes;
 }
 
-extern "C" cpca_status cpca_frpcag_backward(const float* Yt, int32_t rr, int32_t rc, int64_t ldyt,
-                                            const cpca_csr* Lr, const cpca_csr* Lc,
-                                            const cpca_frpcag_params* prm, int32_t ckpt_every,
-                                            const float* dX, int64_t lddx, float* dYt, int64_t lddyt,
-                                            double* dLr, double* dLc, const float* wr, const float* wc,
-                                            int32_t lap_type, float* dwr, float* dwc,
-                                            cpca_frpcag_grad_info* ginfo, void* ws, size_t ws_bytes,
-                                            void* stream) {
-  clear_error();
-  CPCA_CHECK_ARG(Yt && dX && dYt && prm, "cpca_frpcag_backward: null pointer");
-  CPCA_CHECK_ARG(rr > 0 && rc > 0, "cpca_frpcag_backward: empty matrix");
-  CPCA_CHECK_ARG(ldyt >= rc && lddx >= rc && lddyt >= rc, "cpca_frpcag_backward: leading dimension < rc");
-  CPCA_CHECK_ARG(prm->max_iter >= 1, "cpca_frpcag_backward: max_iter < 1");
-  CPCA_CHECK_ARG(prm->eps == 0.0, "cpca_frpcag_backward: needs a fixed iteration count (eps = 0)");
-  CPCA_CHECK_ARG(prm->gamma_r >= 0 && prm->gamma_c >= 0, "cpca_frpcag_backward: negative gamma");
-  CPCA_CHECK_ARG(prm->step > 0 || prm->power_iters >= 1, "cpca_frpcag_backward: power_iters < 1");
-  CPCA_CHECK_ARG(ckpt_every >= 0, "cpca_frpcag_backward: ckpt_every < 0");
-  CPCA_CHECK_ARG(lap_type == CPCA_LAP_NORMALIZED || lap_type == CPCA_LAP_COMBINATORIAL,
-                 "cpca_frpcag_backward: unknown lap_type");
-  CPCA_CHECK_ARG(!dwr || wr, "cpca_frpcag_backward: dwr needs the weights wr");
-  CPCA_CHECK_ARG(!dwc || wc, "cpca_frpcag_backward: dwc needs the weights wc");
-  CPCA_TRY(check_csr(Lr, rr, "cpca_frpcag_backward(Lr)"));
-  CPCA_TRY(check_csr(Lc, rc, "cpca_frpcag_backward(Lc)"));
+namespace {
+
+enum AdjMode { kForwardTape, kBackward, kBackwardResume };
+
+struct AdjCall {
+  const float* Yt;
+  int rr, rc;
+  int64_t ldyt;
+  const cpca_csr *Lr, *Lc;
+  const cpca_frpcag_params* prm;
+  int ckpt_every;
+  // forward tape: X out
+  float* X;
+  int64_t ldx;
+  // backward
+  const float* dX;
+  int64_t lddx;
+  float* dYt;
+  int64_t lddyt;
+  double *dLr, *dLc;
+  const float *wr, *wc;
+  int lap_type;
+  float *dwr, *dwc;
+  cpca_frpcag_grad_info* ginfo;
+  void* ws;
+  size_t ws_bytes;
+  cudaStream_t st;
+};
+
+cpca_status check_adj(const AdjCall& c, const char* who) {
+  CPCA_CHECK_ARG(c.Yt && c.prm, "%s: null pointer", who);
+  CPCA_CHECK_ARG(c.rr > 0 && c.rc > 0, "%s: empty matrix", who);
+  CPCA_CHECK_ARG(c.ldyt >= c.rc, "%s: ldyt < rc", who);
+  CPCA_CHECK_ARG(c.prm->max_iter >= 1, "%s: max_iter < 1", who);
+  CPCA_CHECK_ARG(c.prm->eps == 0.0, "%s: needs a fixed iteration count (eps = 0)", who);
+  CPCA_CHECK_ARG(c.prm->gamma_r >= 0 && c.prm->gamma_c >= 0, "%s: negative gamma", who);
+  CPCA_CHECK_ARG(c.prm->step > 0 || c.prm->power_iters >= 1, "%s: power_iters < 1", who);
+  CPCA_CHECK_ARG(c.ckpt_every >= 0, "%s: ckpt_every < 0", who);
+  CPCA_TRY(check_csr(c.Lr, c.rr, who));
+  CPCA_TRY(check_csr(c.Lc, c.rc, who));
+  return CPCA_OK;
+}
+
+// The forward tape (power iterates, lambda, momentum table, checkpoints)
+// and the reverse sweeps, sharing one workspace layout.
+cpca_status frpcag_adjoint(const AdjCall& c, AdjMode mode) {
+  const int rr = c.rr, rc = c.rc;
+  const cpca_frpcag_params* prm = c.prm;
   const int J = prm->max_iter;
-  const int ck = std::min(ckpt_every > 0 ? ckpt_every : 20, J);
+  const int ck = std::min(c.ckpt_every > 0 ? c.ckpt_every : 20, J);
   const int T = prm->step > 0 ? 0 : prm->power_iters;
-  const BwdWs w = bwd_layout(ws, rr, rc, J, ck, T, Lr->nnz, Lc->nnz);
-  if (!ws || ws_bytes < w.bytes) {
-    set_error("cpca_frpcag_backward: workspace %zu bytes < required %zu", ws_bytes, w.bytes);
+  const BwdWs w = bwd_layout(c.ws, rr, rc, J, ck, T, c.Lr->nnz, c.Lc->nnz);
+  if (!c.ws || c.ws_bytes < w.bytes) {
+    set_error("cpca_frpcag_backward: workspace %zu bytes < required %zu", c.ws_bytes, w.bytes);
     return CPCA_ERR_WORKSPACE;
   }
-  cudaStream_t st = static_cast<cudaStream_t>(stream);
-  const CsrView lr{Lr->n, Lr->rowptr, Lr->col, Lr->val};
-  const CsrView lc{Lc->n, Lc->rowptr, Lc->col, Lc->val};
+  cudaStream_t st = c.st;
+  const CsrView lr{c.Lr->n, c.Lr->rowptr, c.Lr->col, c.Lr->val};
+  const CsrView lc{c.Lc->n, c.Lc->rowptr, c.Lc->col, c.Lc->val};
   const size_t mn = size_t(rr) * rc;
   CPCA_CUDA(cudaMemsetAsync(w.err, 0, sizeof(int), st));
-  CPCA_CUDA(cudaMemsetAsync(w.scal, 0, 4 * sizeof(double), st));
-  CPCA_CUDA(cudaMemsetAsync(w.bar, 0, 4 * sizeof(double), st));
-  CPCA_CUDA(cudaMemsetAsync(w.pacc, 0, 16 * sizeof(double), st));
 
-  // power iterations with the iterates kept, then lambda
   PowAdjArgs pa{};
   pa.rows = rr + rc;
   pa.T = T;
@@ -807,20 +1081,23 @@ extern "C" cpca_status cpca_frpcag_backward(const float* Yt, int32_t rr, int32_t
     G.rho = w.scal + g;
     G.rho_bar = w.nb + g;
   }
-  if (T > 0) {
-    for (int g = 0; g < 2; ++g)
-      CPCA_CUDA(cudaMemsetAsync(w.nrm2[g], 0, sizeof(double) * (T + 1), st));
-    CPCA_TRY(run_power(pa, w, 0, st));
+  if (mode != kBackwardResume) {
+    // power iterations with the iterates kept, then lambda and mu_j
+    CPCA_CUDA(cudaMemsetAsync(w.scal, 0, 4 * sizeof(double), st));
+    CPCA_CUDA(cudaMemsetAsync(w.pacc, 0, 16 * sizeof(double), st));
+    if (T > 0) {
+      for (int g = 0; g < 2; ++g) CPCA_CUDA(cudaMemsetAsync(w.nrm2[g], 0, sizeof(double) * (T + 1), st));
+      CPCA_TRY(run_power(pa, w, 0, st));
+    }
+    step_forward_kernel<<<1, 32, 0, st>>>(w.scal, prm->gamma_r, prm->gamma_c, prm->step);
+    CPCA_LAUNCHED();
+    mu_kernel<<<1, 32, 0, st>>>(J, w.mu);
+    CPCA_LAUNCHED();
   }
-  step_forward_kernel<<<1, 32, 0, st>>>(w.scal, prm->gamma_r, prm->gamma_c, prm->step);
-  CPCA_LAUNCHED();
-  mu_kernel<<<1, 32, 0, st>>>(J, w.mu);
-  CPCA_LAUNCHED();
 
-  // trajectory sweeps
   TrajArgs a{};
-  a.Yt = Yt;
-  a.ldy = ldyt;
+  a.Yt = c.Yt;
+  a.ldy = c.ldyt;
   a.rr = rr;
   a.rc = rc;
   a.ntj = ceil_div(rc, TB);
@@ -845,101 +1122,141 @@ extern "C" cpca_status cpca_frpcag_backward(const float* Yt, int32_t rr, int32_t
     a.Vb[p] = w.Vb[p];
     a.VbT[p] = w.VbT[p];
   }
-  a.dY = dYt;
-  a.lddy = lddyt;
+  a.dY = c.dYt;
+  a.lddy = c.lddyt;
   a.Pr = w.Pr;
   a.Pc = w.Pc;
   a.scal_bar = w.bar;
   a.tmap_c = w.tmap_c;
   a.bar = GridBar{w.bar_cnt, w.bar_cnt + kBarrierCounters, w.err};
-  transpose_map_kernel<<<std::max(1, std::min(rc, num_sms() * 8)), 64, 0, st>>>(lc, w.tmap_c);
-  CPCA_LAUNCHED();
   const size_t smem = sizeof(AdjSmem);
+  const size_t smem_res = sizeof(ResSmem);
   static bool attr = false;
   if (!attr) {
     CPCA_CUDA(cudaFuncSetAttribute((const void*)traj_forward_kernel,
                                    cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
     CPCA_CUDA(cudaFuncSetAttribute((const void*)traj_reverse_kernel,
                                    cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
+    CPCA_CUDA(cudaFuncSetAttribute((const void*)traj_reverse_resident_kernel,
+                                   cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem_res)));
     attr = true;
   }
   const int gf = coop_blocks((const void*)traj_forward_kernel, 256, smem, a.ntiles);
   const int gb = coop_blocks((const void*)traj_reverse_kernel, 256, smem, a.ntiles);
+  const bool resident = mn < (size_t(1) << 31) &&
+      coop_blocks((const void*)traj_reverse_resident_kernel, 256, smem_res, 1 << 30) >= a.ntiles;
   const int nseg = (J + ck - 1) / ck;
   const unsigned gs = std::min<unsigned>(a.ntiles, num_sms() * 8);
-  auto launch = [&](const void* k, int grid, const char* name) -> cpca_status {
+  auto launch = [&](const void* k, int grid, size_t sm, const char* name) -> cpca_status {
     CPCA_TRY(reset_barrier(w, st));
     void* args[] = {&a};
     CPCA_PROF(name, st);
-    CPCA_CUDA(cudaLaunchCooperativeKernel(k, dim3(grid), dim3(256), args, smem, st));
+    CPCA_CUDA(cudaLaunchCooperativeKernel(k, dim3(grid), dim3(256), args, sm, st));
     CPCA_LAUNCHED();
     return CPCA_OK;
   };
-  // forward pass with checkpoints at j = ck, 2 ck, ..., (nseg - 1) ck
-  if (nseg > 1) {
-    seed_kernel<<<gs, 256, 0, st>>>(Yt, ldyt, Yt, ldyt, rr, rc, w.Zs, w.ZTs, w.S);
+
+  const int jlast = (nseg - 1) * ck;  // start of the last segment
+  if (mode == kForwardTape) {
+    // iterations 1..jlast with checkpoints at j = ck, 2 ck, ..., jlast;
+    // then the last segment with its Z_j kept in the slots (the reverse
+    // sweep starts there without recomputing it); X = S_J
+    seed_kernel<<<gs, 256, 0, st>>>(c.Yt, c.ldyt, c.Yt, c.ldyt, rr, rc, w.Zs, w.ZTs, w.S);
+    CPCA_LAUNCHED();
+    if (nseg > 1) {
+      a.jbase = 1;
+      a.nslot = 2;
+      a.ja = 1;
+      a.jb = jlast;
+      a.ck = ck;
+      CPCA_TRY(launch((const void*)traj_forward_kernel, gf, smem, "adj_fista_fwd"));
+      const size_t off = size_t(nseg - 2) * mn;
+      seed_kernel<<<gs, 256, 0, st>>>(w.ckZ + off, rc, w.ckS + off, rc, rr, rc, w.Zs, w.ZTs, w.S);
+      CPCA_LAUNCHED();
+    }
+    a.jbase = jlast + 1;
+    a.nslot = ck + 1;
+    a.ja = jlast + 1;
+    a.jb = J;
+    a.ck = 0;
+    CPCA_TRY(launch((const void*)traj_forward_kernel, gf, smem, "adj_fista_fwd"));
+    CPCA_CUDA(cudaMemcpy2DAsync(c.X, sizeof(float) * c.ldx, w.S, sizeof(float) * rc, sizeof(float) * rc, rr,
+                                cudaMemcpyDeviceToDevice, st));
+  } else if (mode == kBackward && nseg > 1) {
+    // forward pass with checkpoints at j = ck, 2 ck, ..., (nseg - 1) ck
+    seed_kernel<<<gs, 256, 0, st>>>(c.Yt, c.ldyt, c.Yt, c.ldyt, rr, rc, w.Zs, w.ZTs, w.S);
     CPCA_LAUNCHED();
     a.jbase = 1;
     a.nslot = 2;
     a.ja = 1;
     a.jb = (nseg - 1) * ck;
     a.ck = ck;
-    CPCA_TRY(launch((const void*)traj_forward_kernel, gf, "adj_fista_fwd"));
+    CPCA_TRY(launch((const void*)traj_forward_kernel, gf, smem, "adj_fista_fwd"));
   }
-  // reverse, segment by segment
-  CPCA_CUDA(cudaMemcpy2DAsync(w.Sb, sizeof(float) * rc, dX, sizeof(float) * lddx, sizeof(float) * rc, rr,
-                              cudaMemcpyDeviceToDevice, st));
-  CPCA_CUDA(cudaMemsetAsync(w.A2, 0, sizeof(float) * mn, st));
-  CPCA_CUDA(cudaMemset2DAsync(dYt, sizeof(float) * lddyt, 0, sizeof(float) * rc, rr, st));
-  CPCA_CUDA(cudaMemsetAsync(w.Pr, 0, sizeof(double) * a.ntj * std::max<int64_t>(Lr->nnz, 1), st));
-  CPCA_CUDA(cudaMemsetAsync(w.Pc, 0, sizeof(double) * ceil_div(rr, TB) * std::max<int64_t>(Lc->nnz, 1), st));
-  for (int m = nseg - 1; m >= 0; --m) {
-    const int j0 = m * ck, j1 = std::min(J, j0 + ck);
-    if (m == 0) {
-      seed_kernel<<<gs, 256, 0, st>>>(Yt, ldyt, Yt, ldyt, rr, rc, w.Zs, w.ZTs, w.S);
-    } else {
-      const size_t off = size_t(m - 1) * mn;
-      seed_kernel<<<gs, 256, 0, st>>>(w.ckZ + off, rc, w.ckS + off, rc, rr, rc, w.Zs, w.ZTs, w.S);
-    }
+  if (mode != kForwardTape) {
+    // reverse, segment by segment
+    CPCA_CUDA(cudaMemsetAsync(w.bar, 0, 4 * sizeof(double), st));
+    transpose_map_kernel<<<std::max(1, std::min(rc, num_sms() * 8)), 64, 0, st>>>(lc, w.tmap_c);
     CPCA_LAUNCHED();
-    a.jbase = j0 + 1;
-    a.nslot = ck;
-    a.ck = 0;
-    if (j1 - 1 >= j0 + 1) {
+    CPCA_CUDA(cudaMemcpy2DAsync(w.Sb, sizeof(float) * rc, c.dX, sizeof(float) * c.lddx, sizeof(float) * rc,
+                                rr, cudaMemcpyDeviceToDevice, st));
+    CPCA_CUDA(cudaMemsetAsync(w.A2, 0, sizeof(float) * mn, st));
+    CPCA_CUDA(cudaMemset2DAsync(c.dYt, sizeof(float) * c.lddyt, 0, sizeof(float) * rc, rr, st));
+    CPCA_CUDA(cudaMemsetAsync(w.Pr, 0, sizeof(double) * a.ntj * std::max<int64_t>(c.Lr->nnz, 1), st));
+    CPCA_CUDA(cudaMemsetAsync(w.Pc, 0, sizeof(double) * ceil_div(rr, TB) * std::max<int64_t>(c.Lc->nnz, 1), st));
+    for (int m = nseg - 1; m >= 0; --m) {
+      const int j0 = m * ck, j1 = std::min(J, j0 + ck);
+      a.jbase = j0 + 1;
+      a.nslot = ck + 1;
+      a.ck = 0;
+      // the tape already holds the last segment's trajectory
+      const bool have = mode == kBackwardResume && m == nseg - 1;
+      if (!have) {
+        if (m == 0) {
+          seed_kernel<<<gs, 256, 0, st>>>(c.Yt, c.ldyt, c.Yt, c.ldyt, rr, rc, w.Zs, w.ZTs, w.S);
+        } else {
+          const size_t off = size_t(m - 1) * mn;
+          seed_kernel<<<gs, 256, 0, st>>>(w.ckZ + off, rc, w.ckS + off, rc, rr, rc, w.Zs, w.ZTs, w.S);
+        }
+        CPCA_LAUNCHED();
+      }
+      if (!have && j1 - 1 >= j0 + 1) {
+        a.ja = j0 + 1;
+        a.jb = j1 - 1;
+        CPCA_TRY(launch((const void*)traj_forward_kernel, gf, smem, "adj_fista_fwd"));
+      }
       a.ja = j0 + 1;
-      a.jb = j1 - 1;
-      CPCA_TRY(launch((const void*)traj_forward_kernel, gf, "adj_fista_fwd"));
+      a.jb = j1;
+      if (resident) CPCA_TRY(launch((const void*)traj_reverse_resident_kernel, a.ntiles, smem_res, "adj_fista_rev"));
+      else CPCA_TRY(launch((const void*)traj_reverse_kernel, gb, smem, "adj_fista_rev"));
     }
-    a.ja = j0 + 1;
-    a.jb = j1;
-    CPCA_TRY(launch((const void*)traj_reverse_kernel, gb, "adj_fista_rev"));
-  }
-  double* oLr = dLr ? dLr : w.dLr;
-  double* oLc = dLc ? dLc : w.dLc;
-  if (Lr->nnz > 0) {
-    reduce_parts_kernel<<<std::min<unsigned>(ceil_div(Lr->nnz, 256), num_sms() * 4), 256, 0, st>>>(
-        w.Pr, a.ntj, Lr->nnz, oLr);
-    CPCA_LAUNCHED();
-  }
-  if (Lc->nnz > 0) {
-    reduce_parts_kernel<<<std::min<unsigned>(ceil_div(Lc->nnz, 256), num_sms() * 4), 256, 0, st>>>(
-        w.Pc, int(ceil_div(rr, TB)), Lc->nnz, oLc);
-    CPCA_LAUNCHED();
-  }
-  // lambda -> gamma and the norm estimates -> power iterations
-  step_backward_kernel<<<1, 32, 0, st>>>(w.scal, w.bar, w.nb, prm->gamma_r, prm->gamma_c, prm->step);
-  CPCA_LAUNCHED();
-  if (T > 0) {
-    CPCA_CUDA(cudaMemsetAsync(w.pacc, 0, 8 * sizeof(double), st));
-    CPCA_TRY(run_power(pa, w, 1, st));
-    for (int g = 0; g < 2; ++g) {
-      const PowGraph& G = pa.g[g];
-      power_pattern_kernel<<<std::min(G.n, num_sms() * 8), 64, 0, st>>>(G, T, g ? oLc : oLr);
+    double* oLr = c.dLr ? c.dLr : w.dLr;
+    double* oLc = c.dLc ? c.dLc : w.dLc;
+    if (c.Lr->nnz > 0) {
+      reduce_parts_kernel<<<std::min<unsigned>(ceil_div(c.Lr->nnz, 256), num_sms() * 4), 256, 0, st>>>(
+          w.Pr, a.ntj, c.Lr->nnz, oLr);
       CPCA_LAUNCHED();
     }
+    if (c.Lc->nnz > 0) {
+      reduce_parts_kernel<<<std::min<unsigned>(ceil_div(c.Lc->nnz, 256), num_sms() * 4), 256, 0, st>>>(
+          w.Pc, int(ceil_div(rr, TB)), c.Lc->nnz, oLc);
+      CPCA_LAUNCHED();
+    }
+    // lambda -> gamma and the norm estimates -> power iterations
+    step_backward_kernel<<<1, 32, 0, st>>>(w.scal, w.bar, w.nb, prm->gamma_r, prm->gamma_c, prm->step);
+    CPCA_LAUNCHED();
+    if (T > 0) {
+      CPCA_CUDA(cudaMemsetAsync(w.pacc, 0, 8 * sizeof(double), st));
+      CPCA_TRY(run_power(pa, w, 1, st));
+      for (int g = 0; g < 2; ++g) {
+        const PowGraph& G = pa.g[g];
+        power_pattern_kernel<<<std::min(G.n, num_sms() * 8), 64, 0, st>>>(G, T, g ? oLc : oLr);
+        CPCA_LAUNCHED();
+      }
+    }
+    if (c.dwr) CPCA_TRY(weight_chain(lr, c.wr, oLr, c.lap_type, c.dwr, w, st));
+    if (c.dwc) CPCA_TRY(weight_chain(lc, c.wc, oLc, c.lap_type, c.dwc, w, st));
   }
-  if (dwr) CPCA_TRY(weight_chain(lr, wr, oLr, lap_type, dwr, w, st));
-  if (dwc) CPCA_TRY(weight_chain(lc, wc, oLc, lap_type, dwc, w, st));
   double hs[4], hb[4], hn[2];
   int err = 0;
   CPCA_CUDA(cudaMemcpyAsync(hs, w.scal, sizeof(hs), cudaMemcpyDeviceToHost, st));
@@ -951,17 +1268,89 @@ extern "C" cpca_status cpca_frpcag_backward(const float* Yt, int32_t rr, int32_t
     set_error("cpca_frpcag_backward: grid barrier timed out");
     return CPCA_ERR_TIMEOUT;
   }
-  if (ginfo) {
-    ginfo->dgamma_r = hb[1];
-    ginfo->dgamma_c = hb[2];
-    ginfo->dlambda = hb[0];
-    ginfo->dnorm_r = hn[0];
-    ginfo->dnorm_c = hn[1];
-    ginfo->lambda = hs[2];
-    ginfo->norm_r = hs[0];
-    ginfo->norm_c = hs[1];
+  if (c.ginfo) {
+    const bool bwd = mode != kForwardTape;
+    c.ginfo->dgamma_r = bwd ? hb[1] : 0.0;
+    c.ginfo->dgamma_c = bwd ? hb[2] : 0.0;
+    c.ginfo->dlambda = bwd ? hb[0] : 0.0;
+    c.ginfo->dnorm_r = bwd ? hn[0] : 0.0;
+    c.ginfo->dnorm_c = bwd ? hn[1] : 0.0;
+    c.ginfo->lambda = hs[2];
+    c.ginfo->norm_r = hs[0];
+    c.ginfo->norm_c = hs[1];
   }
   return CPCA_OK;
+}
+
+}  // namespace
+
+extern "C" cpca_status cpca_frpcag_forward_tape(const float* Yt, int32_t rr, int32_t rc, int64_t ldyt,
+                                                const cpca_csr* Lr, const cpca_csr* Lc,
+                                                const cpca_frpcag_params* prm, int32_t ckpt_every, float* X,
+                                                int64_t ldx, cpca_frpcag_grad_info* ginfo, void* ws,
+                                                size_t ws_bytes, void* stream) {
+  clear_error();
+  AdjCall c{};
+  c.Yt = Yt;
+  c.rr = rr;
+  c.rc = rc;
+  c.ldyt = ldyt;
+  c.Lr = Lr;
+  c.Lc = Lc;
+  c.prm = prm;
+  c.ckpt_every = ckpt_every;
+  c.X = X;
+  c.ldx = ldx;
+  c.ginfo = ginfo;
+  c.ws = ws;
+  c.ws_bytes = ws_bytes;
+  c.st = static_cast<cudaStream_t>(stream);
+  CPCA_TRY(check_adj(c, "cpca_frpcag_forward_tape"));
+  CPCA_CHECK_ARG(X && ldx >= rc, "cpca_frpcag_forward_tape: need X with ldx >= rc");
+  return frpcag_adjoint(c, kForwardTape);
+}
+
+extern "C" cpca_status cpca_frpcag_backward(const float* Yt, int32_t rr, int32_t rc, int64_t ldyt,
+                                            const cpca_csr* Lr, const cpca_csr* Lc,
+                                            const cpca_frpcag_params* prm, int32_t ckpt_every, int32_t resume,
+                                            const float* dX, int64_t lddx, float* dYt, int64_t lddyt,
+                                            double* dLr, double* dLc, const float* wr, const float* wc,
+                                            int32_t lap_type, float* dwr, float* dwc,
+                                            cpca_frpcag_grad_info* ginfo, void* ws, size_t ws_bytes,
+                                            void* stream) {
+  clear_error();
+  AdjCall c{};
+  c.Yt = Yt;
+  c.rr = rr;
+  c.rc = rc;
+  c.ldyt = ldyt;
+  c.Lr = Lr;
+  c.Lc = Lc;
+  c.prm = prm;
+  c.ckpt_every = ckpt_every;
+  c.dX = dX;
+  c.lddx = lddx;
+  c.dYt = dYt;
+  c.lddyt = lddyt;
+  c.dLr = dLr;
+  c.dLc = dLc;
+  c.wr = wr;
+  c.wc = wc;
+  c.lap_type = lap_type;
+  c.dwr = dwr;
+  c.dwc = dwc;
+  c.ginfo = ginfo;
+  c.ws = ws;
+  c.ws_bytes = ws_bytes;
+  c.st = static_cast<cudaStream_t>(stream);
+  CPCA_TRY(check_adj(c, "cpca_frpcag_backward"));
+  CPCA_CHECK_ARG(dX && dYt, "cpca_frpcag_backward: null dX / dYt");
+  CPCA_CHECK_ARG(lddx >= rc && lddyt >= rc, "cpca_frpcag_backward: leading dimension < rc");
+  CPCA_CHECK_ARG(lap_type == CPCA_LAP_NORMALIZED || lap_type == CPCA_LAP_COMBINATORIAL,
+                 "cpca_frpcag_backward: unknown lap_type");
+  CPCA_CHECK_ARG(!dwr || wr, "cpca_frpcag_backward: dwr needs the weights wr");
+  CPCA_CHECK_ARG(!dwc || wc, "cpca_frpcag_backward: dwc needs the weights wc");
+  return frpcag_adjoint(c, resume ? kBackwardResume : kBackward);
 }
 
 static cpca_status check_pattern(const cpca_csr* L, const char* who) {

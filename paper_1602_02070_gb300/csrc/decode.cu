@@ -919,9 +919,12 @@ static cpca_status partial_svd(const float* Xt, int rr, int rc, int64_t ldxt, in
 
 // Sides 0 (U on Lr) and 1 (V on Lc) of the upsampling solves: index maps,
 // the reduced L_aa CSR, and the PCG arguments over the workspace vectors.
+// index_maps = false: the maps and the reduced CSR are already in the
+// workspace (a forward call with the same inputs built them).
 static cpca_status cg_setup(CgArgs& a, const cpca_csr* Lr, const cpca_csr* Lc, const int32_t* omega_r,
                             const int32_t* omega_c, int p, int n, int rr, int rc, int k, int b,
-                            const cpca_decode_params* prm, const DecodeWs& w, cudaStream_t st) {
+                            const cpca_decode_params* prm, const DecodeWs& w, cudaStream_t st,
+                            bool index_maps = true) {
   const CsrView lr{Lr->n, Lr->rowptr, Lr->col, Lr->val};
   const CsrView lc{Lc->n, Lc->rowptr, Lc->col, Lc->val};
   const int m[2] = {p - rr, n - rc};
@@ -959,6 +962,7 @@ static cpca_status cg_setup(CgArgs& a, const cpca_csr* Lr, const cpca_csr* Lc, c
   a.out_res = w.out_res;
   a.status = w.status;
   a.changed = w.changed;
+  if (!index_maps) return CPCA_OK;
   dim3 sg(std::min<unsigned>(ceil_div(std::max(p, n), 256), num_sms() * 4), 2);
   cg_setup_kernel<<<sg, 256, 0, st>>>(a.s[0], a.s[1]);
   CPCA_LAUNCHED();
@@ -1561,7 +1565,8 @@ extern "C" size_t cpca_decode_backward_workspace_size(int32_t p, int32_t n, int3
 extern "C" cpca_status cpca_decode_backward(const float* Xt, int32_t rr, int32_t rc, int64_t ldxt,
                                             const int32_t* omega_r, const int32_t* omega_c, int32_t p,
                                             int32_t n, const cpca_csr* Lr, const cpca_csr* Lc,
-                                            const cpca_decode_params* prm, int32_t k, int64_t nh,
+                                            const cpca_decode_params* prm, int32_t k, int32_t resume,
+                                            int64_t nh,
                                             const int32_t* h_row, const int32_t* h_col,
                                             const float* h_grad, float* dXt, int64_t lddxt, double* dLr,
                                             double* dLc, const float* wr, const float* wc,
@@ -1596,17 +1601,25 @@ extern "C" cpca_status cpca_decode_backward(const float* Xt, int32_t rr, int32_t
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const int b = decode_block(rr, rc, kmax);
   CPCA_CHECK_ARG(k <= b, "cpca_decode_backward: k > subspace block %d", b);
-  // ---- forward factors, k fixed
-  CPCA_TRY(partial_svd(Xt, rr, rc, ldxt, b, prm->svd_iters, prm->svd_seed, prm->rank_ratio, k, w, st));
+  // ---- forward factors, k fixed (resume: the forward call left them in ws)
   CgArgs a{};
   int cg_iters[2 * KMAX_LIMIT] = {0};
   double cg_res[2 * KMAX_LIMIT] = {0};
   int breakdown = 0;
-  CPCA_TRY(cg_setup(a, Lr, Lc, omega_r, omega_c, p, n, rr, rc, k, b, prm, w, st));
-  CPCA_TRY(cg_solve(a, w, st, cg_iters, cg_res, &breakdown));
-  if (breakdown) {
-    set_error("cpca_decode_backward: L_aa is not positive definite (a graph component has no sampled node)");
-    return CPCA_ERR_SINGULAR;
+  if (resume) {
+    int kf = 0;
+    CPCA_CUDA(cudaMemcpyAsync(&kf, w.k, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CPCA_CUDA(cudaStreamSynchronize(st));
+    CPCA_CHECK_ARG(kf == k, "cpca_decode_backward: resume with k = %d, but the forward found k = %d", k, kf);
+    CPCA_TRY(cg_setup(a, Lr, Lc, omega_r, omega_c, p, n, rr, rc, k, b, prm, w, st, false));
+  } else {
+    CPCA_TRY(partial_svd(Xt, rr, rc, ldxt, b, prm->svd_iters, prm->svd_seed, prm->rank_ratio, k, w, st));
+    CPCA_TRY(cg_setup(a, Lr, Lc, omega_r, omega_c, p, n, rr, rc, k, b, prm, w, st));
+    CPCA_TRY(cg_solve(a, w, st, cg_iters, cg_res, &breakdown));
+    if (breakdown) {
+      set_error("cpca_decode_backward: L_aa is not positive definite (a graph component has no sampled node)");
+      return CPCA_ERR_SINGULAR;
+    }
   }
   const unsigned gp = std::min<unsigned>(ceil_div(int64_t(p) * kmax, 256), num_sms() * 8);
   const unsigned gn = std::min<unsigned>(ceil_div(int64_t(n) * kmax, 256), num_sms() * 8);

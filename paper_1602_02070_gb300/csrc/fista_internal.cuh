@@ -27,16 +27,20 @@ constexpr int kObjBlocks = 512;
 constexpr int TB = 32;        // tile edge
 constexpr int kTileNbr = 40;  // neighbour-list entries staged per row / column
 
-struct TileNbr {
-  int64_t roff[TB][kTileNbr];  // element offset of neighbour row k in Z  (k * rc)
+template <typename Off>
+struct TileNbrT {
+  Off roff[TB][kTileNbr];  // element offset of neighbour row k in Z  (k * rc)
   float rval[TB][kTileNbr];
-  int64_t coff[TB][kTileNbr];  // element offset of neighbour row k in ZT (k * rr)
+  Off coff[TB][kTileNbr];  // element offset of neighbour row k in ZT (k * rr)
   float cval[TB][kTileNbr];
   int rdeg[TB], cdeg[TB];
   int64_t rf0[TB], cf0[TB];
 };
+using TileNbr = TileNbrT<int64_t>;
+using TileNbr32 = TileNbrT<int32_t>;  // matrices below 2^31 entries
 
-__device__ __forceinline__ void stage_nbr(TileNbr& nb, const CsrView& Lr, const CsrView& Lc, int rr,
+template <typename Off>
+__device__ __forceinline__ void stage_nbr(TileNbrT<Off>& nb, const CsrView& Lr, const CsrView& Lc, int rr,
                                           int rc, int i0, int j0, int ni, int nj) {
   if (threadIdx.x < TB) {
     const int r = threadIdx.x;
@@ -53,11 +57,11 @@ __device__ __forceinline__ void stage_nbr(TileNbr& nb, const CsrView& Lr, const 
   for (int e = threadIdx.x; e < TB * kTileNbr; e += blockDim.x) {
     const int r = e / kTileNbr, q = e % kTileNbr;
     if (q < min(nb.rdeg[r], kTileNbr)) {
-      nb.roff[r][q] = int64_t(__ldg(Lr.col + nb.rf0[r] + q)) * rc;
+      nb.roff[r][q] = Off(int64_t(__ldg(Lr.col + nb.rf0[r] + q)) * rc);
       nb.rval[r][q] = __ldg(Lr.val + nb.rf0[r] + q);
     }
     if (q < min(nb.cdeg[r], kTileNbr)) {
-      nb.coff[r][q] = int64_t(__ldg(Lc.col + nb.cf0[r] + q)) * rr;
+      nb.coff[r][q] = Off(int64_t(__ldg(Lc.col + nb.cf0[r] + q)) * rr);
       nb.cval[r][q] = __ldg(Lc.val + nb.cf0[r] + q);
     }
   }
@@ -70,7 +74,8 @@ __device__ __forceinline__ void stage_nbr(TileNbr& nb, const CsrView& Lr, const 
 // shortest list, then each list's remainder, then entries beyond the
 // staging area straight from the CSR. x is read through L2 (ld.global.cg):
 // other blocks of the same launch write it.
-__device__ __forceinline__ void nbr_sum4(const int64_t (*off)[kTileNbr], const float (*w)[kTileNbr],
+template <typename Off>
+__device__ __forceinline__ void nbr_sum4(const Off (*off)[kTileNbr], const float (*w)[kTileNbr],
                                          const int* deg, const int64_t* f0, int first, bool valid,
                                          const float* __restrict__ x, int64_t base, const CsrView& L,
                                          int64_t stride, float out[4]) {

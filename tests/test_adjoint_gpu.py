@@ -90,10 +90,10 @@ def test_fista_backward_through_power_iterations_and_weights(M, inst):
 
 
 def test_fista_backward_checkpoint_spacing_is_exact(M, inst):
-    """Recomputing segments reproduces the trajectory exactly: dY~ and the
-    FISTA part of dL do not depend on the checkpoint spacing (a given step:
-    the power iterations' FP64 atomic sums are not bitwise repeatable;
-    scalars only up to FP64 atomics)."""
+    """Recomputing segments reproduces the trajectory exactly: dY~ does not
+    depend on the checkpoint spacing (a given step: the power iterations'
+    FP64 atomic sums are not bitwise repeatable). dL and the scalars agree to
+    rounding (per-segment FP32 partial sums, FP64 atomics)."""
     J = 23
     B = _dev(np.random.default_rng(3).standard_normal(inst["Yt"].shape))
     Yt = _dev(inst["Yt"])
@@ -101,8 +101,9 @@ def test_fista_backward_checkpoint_spacing_is_exact(M, inst):
                                    step=0.15, max_iter=J, ckpt_every=c) for c in (1, 5, 20, J)]
     for o in outs[1:]:
         assert torch.equal(o["dYt"], outs[0]["dYt"])
-        assert torch.equal(o["dLr"], outs[0]["dLr"]) and torch.equal(o["dLc"], outs[0]["dLc"])
-        assert _rel(o["info"].dgamma_r, outs[0]["info"].dgamma_r) < 1e-12
+        for key in ("dLr", "dLc"):
+            assert rel_fro(o[key].cpu().numpy(), outs[0][key].cpu().numpy()) < 1e-6
+        assert _rel(o["info"].dgamma_r, outs[0]["info"].dgamma_r) < 1e-9
 
 
 def test_fista_backward_gamma_zero_is_identity(M, inst):
@@ -196,3 +197,43 @@ def test_autograd_pipeline_gradient_matches_oracle(M):
     for key in ("Wr", "Wc", "Wrt", "Wct"):
         got = pats[key].pattern_scipy(w[key].grad).toarray()
         assert rel_fro(got, G[key].toarray()) < GRAD_TOL, key
+
+
+def test_forward_tape_and_resume(M, inst):
+    """The taped forward equals the plain solve; the resumed backward equals
+    the self-contained one."""
+    Yt = _dev(inst["Yt"])
+    prm = M.frpcag_params(gamma_r=0.7, gamma_c=1.4, max_iter=45)
+    X0, _ = M.cpca_frpcag_solve(Yt, inst["gLr"], inst["gLc"], prm)
+    X1, ws, ginfo = M.capi.cpca_frpcag_forward_tape(Yt, inst["gLr"], inst["gLc"], prm, 10)
+    assert rel_fro(X1.cpu().numpy(), X0.cpu().numpy()) < 1e-6
+    B = _dev(np.random.default_rng(5).standard_normal(inst["Yt"].shape))
+    r0 = M.cpca_frpcag_backward(Yt, inst["gLr"], inst["gLc"], B, prm, ckpt_every=10)
+    r1 = M.cpca_frpcag_backward(Yt, inst["gLr"], inst["gLc"], B, prm, ckpt_every=10, ws=ws, resume=True)
+    assert rel_fro(r1["dYt"].cpu().numpy(), r0["dYt"].cpu().numpy()) < 1e-5
+    assert _rel(r1["info"].dgamma_r, r0["info"].dgamma_r) < 1e-5
+    assert _rel(ginfo.lambda_, r0["info"].lambda_) < 1e-7
+
+
+def test_decode_backward_resume_matches(M):
+    p, n, rr, rc = 240, 180, 120, 90
+    Y, _, _ = gen.make_instance(33, p, n, 4, 4, 0.05)
+    Yd = torch.as_tensor(Y, device="cuda")
+    Lr, _, _ = M.cpca_knn_graph(Yd, 6)
+    Lc, _, _ = M.cpca_knn_graph(Yd, 6, transposed=True)
+    om_r, om_c, Yt = M.cpca_sample(2, p, n, rr, rc, Yd)
+    Xt = Yt.contiguous()
+    prm = M.decode_params()
+    ws = M.capi.decode_backward_workspace(Xt, p, n, Lr, Lc, prm)
+    dec = M.cpca_decode(Xt, om_r, om_c, p, n, Lr, Lc, prm, want_X=False, ws=ws)
+    rng = np.random.default_rng(3)
+    hr = torch.as_tensor(rng.integers(0, p, 500).astype(np.int32), device="cuda")
+    hc = torch.as_tensor(rng.integers(0, n, 500).astype(np.int32), device="cuda")
+    g = torch.as_tensor(rng.standard_normal(500).astype(np.float32), device="cuda")
+    r1 = M.cpca_decode_backward(Xt, om_r, om_c, p, n, Lr, Lc, dec["k"], hr, hc, g, prm, ws=ws, resume=True)
+    r0 = M.cpca_decode_backward(Xt, om_r, om_c, p, n, Lr, Lc, dec["k"], hr, hc, g, prm)
+    assert rel_fro(r1["dXt"].cpu().numpy(), r0["dXt"].cpu().numpy()) < 1e-6
+    assert rel_fro(r1["dLr"].cpu().numpy(), r0["dLr"].cpu().numpy()) < 1e-6
+    with pytest.raises(M.CpcaError):
+        M.cpca_decode_backward(Xt, om_r, om_c, p, n, Lr, Lc, dec["k"] + 1, hr, hc, g, prm, ws=ws,
+                               resume=True)

@@ -157,16 +157,18 @@ __global__ void step_kernel(const __grid_constant__ StepArgs a) {
 struct FistaInst {
   const float* Yt;
   float* S;
-  float* Z[2];   // row-major Z_j ping / pong (ld rc)
-  float* ZT[2];  // column-major copies (ld rr)
+  float* Z[2];   // row-major Z_j ping / pong (ld ldz = rc rounded up to 4)
+  float* ZT[2];  // column-major copies (ld ldzt = rr rounded up to 4)
   CsrView Lr, Lc;
   const double* lam;
   double* stats;  // ring [4][2]: slot j % 4 holds iteration j's |dZ|^2, |Z|^2
   int* done;      // [stopped, iterations]
   int64_t ldy, lds;
+  int64_t ldz, ldzt;
   float two_gr, two_gc;
   int rr, rc;
   int tile0, ntj;  // first tile in the batch list, column tiles
+  int yvec, svec;  // Y~ / S rows allow 16-byte loads (ld % 4 == 0, aligned)
 };
 struct FistaBatchArgs {
   FistaInst in[kMaxBatch];
@@ -196,13 +198,42 @@ struct TileSmem {
 
 __device__ __forceinline__ void stage_tile(TileSmem& sm, const FistaInst& I, int i0, int j0, int ni,
                                            int nj) {
-  stage_nbr(sm.nb, I.Lr, I.Lc, I.rr, I.rc, i0, j0, ni, nj);
+  stage_nbr(sm.nb, I.Lr, I.Lc, int(I.ldzt), int(I.ldz), i0, j0, ni, nj);
+}
+
+// Four consecutive entries of a row (t < n valid), one 16-byte access when
+// the row allows it.
+__device__ __forceinline__ float4 load4(const float* p, bool vec, int n) {
+  if (vec) return *reinterpret_cast<const float4*>(p);
+  float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (n > 0) v.x = p[0];
+  if (n > 1) v.y = p[1];
+  if (n > 2) v.z = p[2];
+  if (n > 3) v.w = p[3];
+  return v;
+}
+__device__ __forceinline__ void store4(float* p, float4 v, bool vec, int n) {
+  if (vec) {
+    *reinterpret_cast<float4*>(p) = v;
+    return;
+  }
+  if (n > 0) p[0] = v.x;
+  if (n > 1) p[1] = v.y;
+  if (n > 2) p[2] = v.z;
+  if (n > 3) p[3] = v.w;
+}
+__device__ __forceinline__ float& comp(float4& v, int t) {
+  return t == 0 ? v.x : t == 1 ? v.y : t == 2 ? v.z : v.w;
 }
 
 // RESIDENT: every block owns at most one tile for the whole solve; its
 // neighbour lists are staged once, and Y~, S and the tile's own Z_j entries
 // stay in registers across iterations (S is written back at the end).
 // Otherwise blocks stream over the tile list, staging lists per tile.
+// Thread layout: lane group g = lane / 8 of warp w owns tile row
+// r = 4 w + g (and, for the column products and the transposed store, tile
+// column r); its 8 lanes own 4 consecutive columns (rows) each, read and
+// written as 16-byte vectors (Z, ZT rows padded to multiples of 4).
 // Stopping rule (eps > 0): instance i stops after iteration j - 1 once
 // |Z_j - Z_{j-1}|^2 < eps |Z_{j-1}|^2; its tiles are then skipped, and the
 // launch ends when no instance is left.
@@ -214,8 +245,10 @@ fista_batch_kernel(const __grid_constant__ FistaBatchArgs a) {
   __shared__ double red[8];
   __shared__ int any_active;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int rl = warp * 4 + (lane >> 3);  // tile row (column) of this lane group
+  const int cq = 4 * (lane & 7);          // first of the lane's 4 tile columns (rows)
   // resident state (one tile per block)
-  float ry[4], rs[4], rz[4];
+  float4 ry = make_float4(0.f, 0.f, 0.f, 0.f), rs = ry, rz = ry;
   int rinst = 0, ri0 = 0, rj0 = 0, rni = 0, rnj = 0;
   if (RESIDENT && blockIdx.x < a.ntiles) {
     rinst = find_inst(a, blockIdx.x);
@@ -226,13 +259,10 @@ fista_batch_kernel(const __grid_constant__ FistaBatchArgs a) {
     rni = min(TB, I.rr - ri0);
     rnj = min(TB, I.rc - rj0);
     stage_tile(sm, I, ri0, rj0, rni, rnj);
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const int r = warp * 4 + u;
-      const bool in = r < rni && lane < rnj;
-      ry[u] = in ? I.Yt[int64_t(ri0 + r) * I.ldy + rj0 + lane] : 0.f;
-      rs[u] = ry[u];  // S_0 = Y~
-      rz[u] = ry[u];  // Z_1 = Y~
+    if (rl < rni && cq < rnj) {
+      ry = load4(I.Yt + int64_t(ri0 + rl) * I.ldy + rj0 + cq, I.yvec, rnj - cq);
+      rs = ry;  // S_0 = Y~
+      rz = ry;  // Z_1 = Y~
     }
   }
   double t = 1.0;  // t_j of Algorithm 1 (t_1 = 1)
@@ -292,54 +322,68 @@ fista_batch_kernel(const __grid_constant__ FistaBatchArgs a) {
         nj = min(TB, I.rc - j0);
         stage_tile(sm, I, i0, j0, ni, nj);
       }
-      // (Z Lc): warp w takes tile columns 4w..4w+3, lane = tile row
+      // (Z Lc): column rl of the tile, rows cq..cq+3 (from ZT)
       {
-        float o[4];
-        nbr_sum4(sm.nb.coff, sm.nb.cval, sm.nb.cdeg, sm.nb.cf0, warp * 4, lane < ni, ZTin, i0 + lane, I.Lc,
-                 I.rr, o);
-#pragma unroll
-        for (int u = 0; u < 4; ++u) sm.ac[lane][warp * 4 + u] = o[u];
+        const float4 o = nbr_sum_v4(sm.nb.coff[rl], sm.nb.cval[rl], sm.nb.cdeg[rl], sm.nb.cf0[rl],
+                                    rl < nj && cq < ni, ZTin, i0 + cq, I.Lc, I.ldzt);
+        sm.ac[cq][rl] = o.x;
+        sm.ac[cq + 1][rl] = o.y;
+        sm.ac[cq + 2][rl] = o.z;
+        sm.ac[cq + 3][rl] = o.w;
       }
-      // (Lr Z): warp w takes tile rows 4w..4w+3, lane = tile column
-      float ar[4];
-      nbr_sum4(sm.nb.roff, sm.nb.rval, sm.nb.rdeg, sm.nb.rf0, warp * 4, lane < nj, Zin, j0 + lane, I.Lr, I.rc, ar);
+      // (Lr Z): row rl of the tile, columns cq..cq+3
+      const bool own = rl < ni && cq < nj;
+      const float4 ar = nbr_sum_v4(sm.nb.roff[rl], sm.nb.rval[rl], sm.nb.rdeg[rl], sm.nb.rf0[rl], own,
+                                   Zin, j0 + cq, I.Lr, I.ldz);
       __syncthreads();  // sm.ac complete
       double dz = 0.0, nz = 0.0;
+      float4 zn4 = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (own) {
+        const int64_t i = i0 + rl, jj = j0 + cq;
+        const int nv = nj - cq;  // valid entries among the 4
+        const float4 z4 = RESIDENT ? rz : __ldcg(reinterpret_cast<const float4*>(Zin + i * I.ldz + jj));
+        const float4 y4 = RESIDENT ? ry : load4(I.Yt + i * I.ldy + jj, I.yvec, nv);
+        const float4 s4 = RESIDENT ? rs : load4(I.S + i * I.lds + jj, I.svec, nv);
+        float4 sv4 = make_float4(0.f, 0.f, 0.f, 0.f);
+        float4 ar4 = ar, zz = z4, yy = y4, ss = s4;
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const int r = warp * 4 + u;
-        if (r < ni && lane < nj) {
-          const int64_t i = i0 + r, jj = j0 + lane;
-          const float z = RESIDENT ? rz[u] : __ldcg(Zin + i * I.rc + jj);
-          const float y = RESIDENT ? ry[u] : __ldg(I.Yt + i * I.ldy + jj);
-          const float sp = RESIDENT ? rs[u] : I.S[i * I.lds + jj];
-          // S_j = prox(Z_j - lambda grad g(Z_j)), grad g = 2 (g_c Z Lc + g_r Lr Z)
-          const float gr = fmaf(I.two_gr, ar[u], I.two_gc * sm.ac[r][lane]);
-          const float v = fmaf(-lam, gr, z);
-          const float dl = v - y;
-          const float sv = y + copysignf(fmaxf(fabsf(dl) - lam, 0.f), dl);
-          // Z_{j+1} = S_j + ((t_j - 1) / t_{j+1}) (S_j - S_{j-1})
-          const float zn = fmaf(mu, sv - sp, sv);
-          if (RESIDENT) {
-            rs[u] = sv;
-            rz[u] = zn;
-          } else {
-            I.S[i * I.lds + jj] = sv;
-          }
-          Zout[i * I.rc + jj] = zn;
-          sm.zt[r][lane] = zn;
-          if (stats) {
-            const double d = double(zn) - double(z);
-            dz += d * d;
-            nz += double(z) * double(z);
+        for (int q = 0; q < 4; ++q) {
+          if (q < nv) {
+            const float z = comp(zz, q), y = comp(yy, q), sp = comp(ss, q);
+            // S_j = prox(Z_j - lambda grad g(Z_j)), grad g = 2 (g_c Z Lc + g_r Lr Z)
+            const float gr = fmaf(I.two_gr, comp(ar4, q), I.two_gc * sm.ac[rl][cq + q]);
+            const float v = fmaf(-lam, gr, z);
+            const float dl = v - y;
+            const float sv = y + copysignf(fmaxf(fabsf(dl) - lam, 0.f), dl);
+            // Z_{j+1} = S_j + ((t_j - 1) / t_{j+1}) (S_j - S_{j-1})
+            const float zn = fmaf(mu, sv - sp, sv);
+            comp(sv4, q) = sv;
+            comp(zn4, q) = zn;
+            if (stats) {
+              const double d = double(zn) - double(z);
+              dz += d * d;
+              nz += double(z) * double(z);
+            }
           }
         }
+        if (RESIDENT) {
+          rs = sv4;
+          rz = zn4;
+        } else {
+          store4(I.S + i * I.lds + jj, sv4, I.svec, nv);
+        }
+        // the padding columns of the last vector get zeros
+        *reinterpret_cast<float4*>(Zout + i * I.ldz + jj) = zn4;
       }
+      sm.zt[rl][cq] = zn4.x;
+      sm.zt[rl][cq + 1] = zn4.y;
+      sm.zt[rl][cq + 2] = zn4.z;
+      sm.zt[rl][cq + 3] = zn4.w;
       __syncthreads();  // sm.zt complete
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const int c = warp * 4 + u;
-        if (c < nj && lane < ni) ZTout[int64_t(j0 + c) * I.rr + i0 + lane] = sm.zt[lane][c];
+      // transposed store: column rl of the tile, rows cq..cq+3
+      if (rl < nj && cq < ni) {
+        const float4 v = make_float4(sm.zt[cq][rl], sm.zt[cq + 1][rl], sm.zt[cq + 2][rl], sm.zt[cq + 3][rl]);
+        *reinterpret_cast<float4*>(ZTout + int64_t(j0 + rl) * I.ldzt + i0 + cq) = v;
       }
       if (stats) {
         dz = block_sum(dz, red);
@@ -356,11 +400,7 @@ fista_batch_kernel(const __grid_constant__ FistaBatchArgs a) {
   }
   if (RESIDENT && blockIdx.x < a.ntiles) {
     const FistaInst& I = a.in[rinst];
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const int r = warp * 4 + u;
-      if (r < rni && lane < rnj) I.S[int64_t(ri0 + r) * I.lds + rj0 + lane] = rs[u];
-    }
+    if (rl < rni && cq < rnj) store4(I.S + int64_t(ri0 + rl) * I.lds + rj0 + cq, rs, I.svec, rnj - cq);
   }
   // instances still running at the end did all their iterations
   if (blockIdx.x == 0)
@@ -369,7 +409,7 @@ fista_batch_kernel(const __grid_constant__ FistaBatchArgs a) {
 }
 
 // Z_1 = S_0 = Y~ (Algorithm 1) and the transposed copy of Z_1, one tile per
-// block over the batch tile list.
+// block over the batch tile list; the padding of Z's and ZT's rows is zeroed.
 __global__ void __launch_bounds__(256) init_batch_kernel(const __grid_constant__ FistaBatchArgs a) {
   __shared__ float tile[TB][TB + 1];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -378,17 +418,22 @@ __global__ void __launch_bounds__(256) init_batch_kernel(const __grid_constant__
     const int lt = tl - I.tile0;
     const int i0 = (lt / I.ntj) * TB, j0 = (lt % I.ntj) * TB;
     const int ni = min(TB, I.rr - i0), nj = min(TB, I.rc - j0);
-    for (int r = warp; r < TB; r += 8)
-      if (r < ni && lane < nj) {
-        const int64_t i = i0 + r, jj = j0 + lane;
-        const float y = I.Yt[i * I.ldy + jj];
-        I.Z[0][i * I.rc + jj] = y;
-        I.S[i * I.lds + jj] = y;
-        tile[r][lane] = y;
+    for (int r = warp; r < TB; r += 8) {
+      const int64_t i = i0 + r, jj = j0 + lane;
+      const float y = (r < ni && lane < nj) ? I.Yt[i * I.ldy + jj] : 0.f;
+      if (r < ni && jj < I.ldz) {
+        I.Z[0][i * I.ldz + jj] = y;
+        I.Z[1][i * I.ldz + jj] = 0.f;
       }
+      if (r < ni && lane < nj) I.S[i * I.lds + jj] = y;
+      tile[r][lane] = y;
+    }
     __syncthreads();
     for (int c = warp; c < TB; c += 8)
-      if (c < nj && lane < ni) I.ZT[0][int64_t(j0 + c) * I.rr + i0 + lane] = tile[lane][c];
+      if (c < nj && i0 + lane < I.ldzt) {
+        I.ZT[0][int64_t(j0 + c) * I.ldzt + i0 + lane] = tile[lane][c];
+        I.ZT[1][int64_t(j0 + c) * I.ldzt + i0 + lane] = 0.f;
+      }
     __syncthreads();
   }
 }
@@ -452,10 +497,11 @@ FistaBatchArgs g_fa;
 // ---------------------------------------------------------------- layout --
 InstWs inst_layout(Carve& c, int rr, int rc) {
   InstWs w{};
-  w.Z0 = c.take<float>(size_t(rr) * rc);
-  w.Z1 = c.take<float>(size_t(rr) * rc);
-  w.ZT0 = c.take<float>(size_t(rr) * rc);
-  w.ZT1 = c.take<float>(size_t(rr) * rc);
+  const size_t ldz = size_t(rc + 3) / 4 * 4, ldzt = size_t(rr + 3) / 4 * 4;
+  w.Z0 = c.take<float>(size_t(rr) * ldz);
+  w.Z1 = c.take<float>(size_t(rr) * ldz);
+  w.ZT0 = c.take<float>(size_t(rc) * ldzt);
+  w.ZT1 = c.take<float>(size_t(rc) * ldzt);
   w.scal = c.take<double>(4);
   for (int g = 0; g < 2; ++g)
     for (int b = 0; b < 2; ++b) w.pu[g][b] = c.take<float>(size_t(g ? rc : rr) + 4);
@@ -550,6 +596,10 @@ cpca_status fista_batch_run(const BatchProblem* P, int n, int J, double eps, boo
     I.done = iw.done;
     I.ldy = P[i].ldy;
     I.lds = P[i].ldx;
+    I.ldz = (P[i].rc + 3) / 4 * 4;
+    I.ldzt = (P[i].rr + 3) / 4 * 4;
+    I.yvec = P[i].ldy % 4 == 0 && reinterpret_cast<uintptr_t>(P[i].Yt) % 16 == 0;
+    I.svec = P[i].ldx % 4 == 0 && reinterpret_cast<uintptr_t>(P[i].X) % 16 == 0;
     I.two_gr = float(2.0 * P[i].gamma_r);
     I.two_gc = float(2.0 * P[i].gamma_c);
     I.rr = P[i].rr;

@@ -68,6 +68,50 @@ __device__ __forceinline__ void stage_nbr(TileNbrT<Off>& nb, const CsrView& Lr, 
   __syncthreads();
 }
 
+// One staged neighbour list, four consecutive outputs per lane:
+// out[t] = sum_q w[q] x[off[q] + base + t], base a multiple of 4 floats
+// (16-byte loads from rows whose length is padded to a multiple of 4).
+// Entries in list order; beyond the staging area straight from the CSR.
+template <typename Off>
+__device__ __forceinline__ float4 nbr_sum_v4(const Off* off, const float* w, int deg, int64_t f0, bool valid,
+                                             const float* __restrict__ x, int64_t base, const CsrView& L,
+                                             int64_t stride) {
+  float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (!valid) return acc;
+  const int ds = min(deg, kTileNbr);
+  int q = 0;
+  for (; q + 8 <= ds; q += 8) {
+    float4 v[8];
+#pragma unroll
+    for (int t = 0; t < 8; ++t) v[t] = __ldcg(reinterpret_cast<const float4*>(x + off[q + t] + base));
+#pragma unroll
+    for (int t = 0; t < 8; ++t) {
+      const float wt = w[q + t];
+      acc.x = fmaf(wt, v[t].x, acc.x);
+      acc.y = fmaf(wt, v[t].y, acc.y);
+      acc.z = fmaf(wt, v[t].z, acc.z);
+      acc.w = fmaf(wt, v[t].w, acc.w);
+    }
+  }
+  for (; q < ds; ++q) {
+    const float4 v = __ldcg(reinterpret_cast<const float4*>(x + off[q] + base));
+    const float wt = w[q];
+    acc.x = fmaf(wt, v.x, acc.x);
+    acc.y = fmaf(wt, v.y, acc.y);
+    acc.z = fmaf(wt, v.z, acc.z);
+    acc.w = fmaf(wt, v.w, acc.w);
+  }
+  for (int64_t f = f0 + kTileNbr; f < f0 + deg; ++f) {
+    const float4 v = __ldcg(reinterpret_cast<const float4*>(x + int64_t(__ldg(L.col + f)) * stride + base));
+    const float wt = __ldg(L.val + f);
+    acc.x = fmaf(wt, v.x, acc.x);
+    acc.y = fmaf(wt, v.y, acc.y);
+    acc.z = fmaf(wt, v.z, acc.z);
+    acc.w = fmaf(wt, v.w, acc.w);
+  }
+  return acc;
+}
+
 // For four staged neighbour lists u = 0..3 (rows or columns of the tile):
 // out[u] = sum_q w[u][q] * x[off[u][q] + base]. Chunks of 8 entries of all
 // four lists are loaded together (32 independent loads per lane) up to the

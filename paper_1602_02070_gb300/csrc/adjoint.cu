@@ -29,6 +29,7 @@
 // respect to the Laplacian entries are summed per tile column (Lr) and per
 // tile row (Lc) in FP64 without atomics, then reduced in a fixed order.
 #include <algorithm>
+#include <type_traits>
 #include <vector>
 
 #include "common.cuh"
@@ -50,27 +51,32 @@ __global__ void mu_kernel(int J, float* mu) {
   }
 }
 
-// Seed trajectory slot 0 with Z (row-major copy and transpose) and S.
+// Seed trajectory slot 0: Z (row-major, ld ldz, and its transpose, ld
+// ldzt) and S (ld ldz) from Zsrc (ld lzs) and Ssrc (ld lss); the padding of
+// the rows is zeroed.
 __global__ void __launch_bounds__(256)
-seed_kernel(const float* __restrict__ Zsrc, int64_t ldz, const float* __restrict__ Ssrc, int64_t lds,
-            int rr, int rc, float* __restrict__ Z, float* __restrict__ ZT, float* __restrict__ S) {
+seed_kernel(const float* __restrict__ Zsrc, int64_t lzs, const float* __restrict__ Ssrc, int64_t lss, int rr,
+            int rc, int64_t ldz, int64_t ldzt, float* __restrict__ Z, float* __restrict__ ZT,
+            float* __restrict__ S) {
   __shared__ float tile[TB][TB + 1];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int ntj = (rc + TB - 1) / TB, ntiles = ((rr + TB - 1) / TB) * ntj;
   for (int tl = blockIdx.x; tl < ntiles; tl += gridDim.x) {
     const int i0 = (tl / ntj) * TB, j0 = (tl % ntj) * TB;
     const int ni = min(TB, rr - i0), nj = min(TB, rc - j0);
-    for (int r = warp; r < TB; r += 8)
-      if (r < ni && lane < nj) {
-        const int64_t i = i0 + r, jj = j0 + lane;
-        const float z = Zsrc[i * ldz + jj];
-        Z[i * rc + jj] = z;
-        S[i * rc + jj] = Ssrc[i * lds + jj];
-        tile[r][lane] = z;
+    for (int r = warp; r < TB; r += 8) {
+      const int64_t i = i0 + r, jj = j0 + lane;
+      const bool in = r < ni && lane < nj;
+      const float z = in ? Zsrc[i * lzs + jj] : 0.f;
+      if (r < ni && jj < ldz) {
+        Z[i * ldz + jj] = z;
+        S[i * ldz + jj] = in ? Ssrc[i * lss + jj] : 0.f;
       }
+      tile[r][lane] = z;
+    }
     __syncthreads();
     for (int c = warp; c < TB; c += 8)
-      if (c < nj && lane < ni) ZT[int64_t(j0 + c) * rr + i0 + lane] = tile[lane][c];
+      if (c < nj && i0 + lane < ldzt) ZT[int64_t(j0 + c) * ldzt + i0 + lane] = tile[lane][c];
     __syncthreads();
   }
 }
@@ -79,14 +85,16 @@ struct TrajArgs {
   const float* Yt;
   int64_t ldy;
   int rr, rc, ntj, ntiles;
+  int64_t ldz, ldzt;     // padded row lengths of the row- and column-major buffers
+  int yvec, dyvec;       // Y~ / dY~ rows allow 16-byte accesses
   CsrView Lr, Lc;
   const double* lam;
   float two_gr, two_gc;
   double gamma_r, gamma_c;
   const float* mu;
-  float* S;              // own tiles: S_{j-1} in, S_j out (ld rc)
-  float* Zs;             // trajectory slots of Z_j (row-major), slot stride rr * rc
-  float* ZTs;            // column-major copies
+  float* S;              // own tiles: S_{j-1} in, S_j out (ld ldz)
+  float* Zs;             // trajectory slots of Z_j (row-major, slot stride rr * ldz)
+  float* ZTs;            // column-major copies (slot stride rc * ldzt)
   int jbase, nslot;      // Z_j lives in slot (j - jbase) % nslot
   int ja, jb;            // forward: iterations ja..jb; reverse: jb down to ja
   int J;
@@ -95,7 +103,7 @@ struct TrajArgs {
   float* ckZ;
   int ck;
   // reverse only
-  float* Sb;             // dloss/dS_j (own tiles)
+  float* Sb;             // dloss/dS_j (own tiles, ld ldz)
   float* A2;             // partial dloss/dS_{j-1}
   float* Vb[2];          // published Vb, row-major / column-major, parity j & 1
   float* VbT[2];
@@ -108,16 +116,15 @@ struct TrajArgs {
   GridBar bar;
 };
 
-struct AdjSmem {
-  TileNbr nb;
-  float ac[TB][TB + 1];
-  float tl[TB][TB + 1];
-};
-
-__device__ __forceinline__ size_t slot_off(const TrajArgs& a, int j) {
+__device__ __forceinline__ int slot_of(const TrajArgs& a, int j) {
   int s = (j - a.jbase) % a.nslot;
-  if (s < 0) s += a.nslot;
-  return size_t(s) * size_t(a.rr) * a.rc;
+  return s < 0 ? s + a.nslot : s;
+}
+__device__ __forceinline__ float* zslot(const TrajArgs& a, int j) {
+  return a.Zs + size_t(slot_of(a, j)) * size_t(a.rr) * size_t(a.ldz);
+}
+__device__ __forceinline__ float* ztslot(const TrajArgs& a, int j) {
+  return a.ZTs + size_t(slot_of(a, j)) * size_t(a.rc) * size_t(a.ldzt);
 }
 
 __device__ __forceinline__ void tile_of(const TrajArgs& a, int tile, int& i0, int& j0, int& ni, int& nj) {
@@ -127,126 +134,171 @@ __device__ __forceinline__ void tile_of(const TrajArgs& a, int tile, int& i0, in
   nj = min(TB, a.rc - j0);
 }
 
-// Forward iterations ja..jb with the trajectory kept (the arithmetic of the
-// solve's FISTA step, entry for entry).
+__device__ __forceinline__ float4 ld4(const float* p, bool vec, int n) {
+  if (vec) return *reinterpret_cast<const float4*>(p);
+  float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (n > 0) v.x = p[0];
+  if (n > 1) v.y = p[1];
+  if (n > 2) v.z = p[2];
+  if (n > 3) v.w = p[3];
+  return v;
+}
+__device__ __forceinline__ void st4(float* p, float4 v, bool vec, int n) {
+  if (vec) {
+    *reinterpret_cast<float4*>(p) = v;
+    return;
+  }
+  if (n > 0) p[0] = v.x;
+  if (n > 1) p[1] = v.y;
+  if (n > 2) p[2] = v.z;
+  if (n > 3) p[3] = v.w;
+}
+__device__ __forceinline__ float& cmp(float4& v, int t) {
+  return t == 0 ? v.x : t == 1 ? v.y : t == 2 ? v.z : v.w;
+}
+__device__ __forceinline__ float dot4(float4 a, float4 b) {
+  return fmaf(a.w, b.w, fmaf(a.z, b.z, fmaf(a.y, b.y, a.x * b.x)));
+}
+
+template <typename Off>
+struct TrajSmem {
+  TileNbrT<Off> nb;
+  float ac[TB][TB + 1];
+  float tl[TB][TB + 1];
+  float pr[TB][kTileNbr];  // resident reverse: dL partial sums of the staged entries
+  float pc[TB][kTileNbr];
+};
+
+// Forward iterations ja..jb with the trajectory kept: the solve's FISTA
+// step, entry for entry, in its thread layout (lane group g of warp w owns
+// tile row / column 4 w + g, each lane 4 consecutive entries).
 __global__ void __launch_bounds__(256, 4)
 traj_forward_kernel(const __grid_constant__ TrajArgs a) {
   extern __shared__ __align__(16) unsigned char smraw[];
-  AdjSmem& sm = *reinterpret_cast<AdjSmem*>(smraw);
+  TrajSmem<int64_t>& sm = *reinterpret_cast<TrajSmem<int64_t>*>(smraw);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int rl = warp * 4 + (lane >> 3), cq = 4 * (lane & 7);
   const float lam = float(*a.lam);
   for (int j = a.ja; j <= a.jb; ++j) {
     const float mu = a.mu[j];
-    const float* Zin = a.Zs + slot_off(a, j);
-    const float* ZTin = a.ZTs + slot_off(a, j);
-    float* Zout = a.Zs + slot_off(a, j + 1);
-    float* ZTout = a.ZTs + slot_off(a, j + 1);
+    const float* Zin = zslot(a, j);
+    const float* ZTin = ztslot(a, j);
+    float* Zout = zslot(a, j + 1);
+    float* ZTout = ztslot(a, j + 1);
     const bool ckpt = a.ck > 0 && j % a.ck == 0 && j < a.J;
-    const size_t ckoff = ckpt ? size_t(j / a.ck - 1) * size_t(a.rr) * a.rc : 0;
+    const size_t ckoff = ckpt ? size_t(j / a.ck - 1) * size_t(a.rr) * size_t(a.ldz) : 0;
     for (int tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x) {
       int i0, j0, ni, nj;
       tile_of(a, tile, i0, j0, ni, nj);
-      stage_nbr(sm.nb, a.Lr, a.Lc, a.rr, a.rc, i0, j0, ni, nj);
+      stage_nbr(sm.nb, a.Lr, a.Lc, int(a.ldzt), int(a.ldz), i0, j0, ni, nj);
       {
-        float o[4];
-        nbr_sum4(sm.nb.coff, sm.nb.cval, sm.nb.cdeg, sm.nb.cf0, warp * 4, lane < ni, ZTin, i0 + lane,
-                 a.Lc, a.rr, o);
-#pragma unroll
-        for (int u = 0; u < 4; ++u) sm.ac[lane][warp * 4 + u] = o[u];
+        const float4 o = nbr_sum_v4(sm.nb.coff[rl], sm.nb.cval[rl], sm.nb.cdeg[rl], sm.nb.cf0[rl],
+                                    rl < nj && cq < ni, ZTin, i0 + cq, a.Lc, a.ldzt);
+        sm.ac[cq][rl] = o.x;
+        sm.ac[cq + 1][rl] = o.y;
+        sm.ac[cq + 2][rl] = o.z;
+        sm.ac[cq + 3][rl] = o.w;
       }
-      float ar[4];
-      nbr_sum4(sm.nb.roff, sm.nb.rval, sm.nb.rdeg, sm.nb.rf0, warp * 4, lane < nj, Zin, j0 + lane,
-               a.Lr, a.rc, ar);
+      const bool own = rl < ni && cq < nj;
+      float4 ar = nbr_sum_v4(sm.nb.roff[rl], sm.nb.rval[rl], sm.nb.rdeg[rl], sm.nb.rf0[rl], own, Zin, j0 + cq,
+                             a.Lr, a.ldz);
       __syncthreads();
+      float4 zn4 = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (own) {
+        const int64_t i = i0 + rl, jj = j0 + cq;
+        const int nv = nj - cq;
+        float4 z4 = __ldcg(reinterpret_cast<const float4*>(Zin + i * a.ldz + jj));
+        float4 y4 = ld4(a.Yt + i * a.ldy + jj, a.yvec, nv);
+        float4 s4 = *reinterpret_cast<const float4*>(a.S + i * a.ldz + jj);
+        float4 sv4 = make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const int r = warp * 4 + u;
-        if (r < ni && lane < nj) {
-          const int64_t i = i0 + r, jj = j0 + lane;
-          const float z = __ldcg(Zin + i * a.rc + jj);
-          const float y = __ldg(a.Yt + i * a.ldy + jj);
-          const float sp = a.S[i * a.rc + jj];
-          const float gr = fmaf(a.two_gr, ar[u], a.two_gc * sm.ac[r][lane]);
-          const float v = fmaf(-lam, gr, z);
-          const float dl = v - y;
-          const float sv = y + copysignf(fmaxf(fabsf(dl) - lam, 0.f), dl);
-          const float zn = fmaf(mu, sv - sp, sv);
-          a.S[i * a.rc + jj] = sv;
-          Zout[i * a.rc + jj] = zn;
-          sm.tl[r][lane] = zn;
-          if (ckpt) {
-            a.ckS[ckoff + i * a.rc + jj] = sv;
-            a.ckZ[ckoff + i * a.rc + jj] = zn;
+        for (int q = 0; q < 4; ++q) {
+          if (q < nv) {
+            const float z = cmp(z4, q), y = cmp(y4, q), sp = cmp(s4, q);
+            const float gr = fmaf(a.two_gr, cmp(ar, q), a.two_gc * sm.ac[rl][cq + q]);
+            const float v = fmaf(-lam, gr, z);
+            const float dl = v - y;
+            const float sv = y + copysignf(fmaxf(fabsf(dl) - lam, 0.f), dl);
+            cmp(sv4, q) = sv;
+            cmp(zn4, q) = fmaf(mu, sv - sp, sv);
           }
         }
+        *reinterpret_cast<float4*>(a.S + i * a.ldz + jj) = sv4;
+        *reinterpret_cast<float4*>(Zout + i * a.ldz + jj) = zn4;
+        if (ckpt) {
+          *reinterpret_cast<float4*>(a.ckS + ckoff + i * a.ldz + jj) = sv4;
+          *reinterpret_cast<float4*>(a.ckZ + ckoff + i * a.ldz + jj) = zn4;
+        }
       }
+      sm.tl[rl][cq] = zn4.x;
+      sm.tl[rl][cq + 1] = zn4.y;
+      sm.tl[rl][cq + 2] = zn4.z;
+      sm.tl[rl][cq + 3] = zn4.w;
       __syncthreads();
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const int c = warp * 4 + u;
-        if (c < nj && lane < ni) ZTout[int64_t(j0 + c) * a.rr + i0 + lane] = sm.tl[lane][c];
-      }
+      if (rl < nj && cq < ni)
+        *reinterpret_cast<float4*>(ZTout + int64_t(j0 + rl) * a.ldzt + i0 + cq) =
+            make_float4(sm.tl[cq][rl], sm.tl[cq + 1][rl], sm.tl[cq + 2][rl], sm.tl[cq + 3][rl]);
       __syncthreads();
     }
     if (!grid_sync(a.bar)) return;
   }
 }
 
-// Partial sums of dL on one staged neighbour list: for list u (first + u)
-// of the tile, entry q: sum over the 32 lanes of x[off + base] * own[u],
-// added (times scale) to P[f0 + q], or to P[tmap[f0 + q]] (the transposed
-// entry) when tmap is given. Lanes with !valid contribute 0.
-// Eight entries at a time: eight independent gathers per lane, then a
-// butterfly that leaves each entry's 32-lane sum in four lanes (9 shuffles
-// for 8 sums), and eight lanes update P in parallel.
-__device__ __forceinline__ void pattern_partials(const int64_t (*off)[kTileNbr], const int* deg,
-                                                 const int64_t* f0, int first, bool valid,
-                                                 const float* __restrict__ x, int64_t base,
-                                                 const CsrView& L, int64_t stride, const float own[4],
-                                                 double scale, double* __restrict__ P,
-                                                 const int64_t* __restrict__ tmap, int lane) {
-  const bool h16 = lane & 16, h8 = lane & 8, h4 = lane & 4;
-  const int mine = (h16 ? 4 : 0) + (h8 ? 2 : 0) + (h4 ? 1 : 0);  // entry whose sum this lane ends with
+// Partial sums of dL on the staged list `rl` of the tile (one list per
+// 8-lane group; each lane holds 4 consecutive elements of the list's
+// vectors): for every entry q, sum over the group of dot(x[off[q] + base],
+// own) with x read as 16-byte vectors. Eight entries at a time: eight
+// gathers per lane, then a butterfly over the group's 8 lanes (7 shuffles
+// for 8 sums) after which every lane holds one entry's sum. The sums are
+// added to acc[rl][q] (resident kernel, staged entries) or, times scale, to
+// P at entry f0 + q (or its transpose tmap[f0 + q]). The loop bound is the
+// warp's largest list so that all lanes take part in the shuffles.
+template <bool RESIDENT, typename Off>
+__device__ __forceinline__ void list_partials(const Off* off, int deg, int64_t f0, bool valid,
+                                              const float* __restrict__ x, int64_t base, const CsrView& L,
+                                              int64_t stride, float4 own, float* acc, double scale,
+                                              double* __restrict__ P, const int64_t* __restrict__ tmap,
+                                              int lane) {
+  const int l8 = lane & 7;
+  const bool h4 = l8 & 4, h2 = l8 & 2, h1 = l8 & 1;
+  const int mine = (h4 ? 4 : 0) + (h2 ? 2 : 0) + (h1 ? 1 : 0);
+  int dmax = deg;
+  dmax = max(dmax, __shfl_xor_sync(0xffffffffu, dmax, 8));
+  dmax = max(dmax, __shfl_xor_sync(0xffffffffu, dmax, 16));
+  for (int q0 = 0; q0 < dmax; q0 += 8) {
+    float v[8];
 #pragma unroll
-  for (int u = 0; u < 4; ++u) {
-    const int d = deg[first + u];
-    const int64_t fu = f0[first + u];
-    for (int q0 = 0; q0 < d; q0 += 8) {
-      float v[8];
+    for (int t = 0; t < 8; ++t) {
+      const int q = q0 + t;
+      float d = 0.f;
+      if (valid && q < deg) {
+        const int64_t o = q < kTileNbr ? int64_t(off[q]) : int64_t(__ldg(L.col + f0 + q)) * stride;
+        d = dot4(__ldcg(reinterpret_cast<const float4*>(x + o + base)), own);
+      }
+      v[t] = d;
+    }
+    float w4[4], w2[2];
 #pragma unroll
-      for (int t = 0; t < 8; ++t) {
-        const int q = q0 + t;
-        float xv = 0.f;
-        if (valid && q < d) {
-          const int64_t o = q < kTileNbr ? off[first + u][q] : int64_t(__ldg(L.col + fu + q)) * stride;
-          xv = __ldcg(x + o + base);
-        }
-        v[t] = xv * own[u];
-      }
-      float w4[4], w2[2];
+    for (int i = 0; i < 4; ++i) {
+      const float send = h4 ? v[i] : v[i + 4];
+      const float keep = h4 ? v[i + 4] : v[i];
+      w4[i] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
+    }
 #pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        const float send = h16 ? v[i] : v[i + 4];
-        const float keep = h16 ? v[i + 4] : v[i];
-        w4[i] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
-      }
-#pragma unroll
-      for (int i = 0; i < 2; ++i) {
-        const float send = h8 ? w4[i] : w4[i + 2];
-        const float keep = h8 ? w4[i + 2] : w4[i];
-        w2[i] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
-      }
-      float y;
-      {
-        const float send = h4 ? w2[0] : w2[1];
-        const float keep = h4 ? w2[1] : w2[0];
-        y = keep + __shfl_xor_sync(0xffffffffu, send, 4);
-      }
-      y += __shfl_xor_sync(0xffffffffu, y, 2);
-      y += __shfl_xor_sync(0xffffffffu, y, 1);
-      const int q = q0 + mine;
-      if ((lane & 3) == 0 && q < d && y != 0.f) {
-        const int64_t e = fu + q;
+    for (int i = 0; i < 2; ++i) {
+      const float send = h2 ? w4[i] : w4[i + 2];
+      const float keep = h2 ? w4[i + 2] : w4[i];
+      w2[i] = keep + __shfl_xor_sync(0xffffffffu, send, 2);
+    }
+    const float send = h1 ? w2[0] : w2[1];
+    const float keep = h1 ? w2[1] : w2[0];
+    const float y = keep + __shfl_xor_sync(0xffffffffu, send, 1);
+    const int q = q0 + mine;
+    if (q < deg && y != 0.f) {
+      if (RESIDENT && q < kTileNbr) {
+        acc[q] += y;
+      } else {
+        const int64_t e = f0 + q;
         const int64_t t = tmap ? __ldg(tmap + e) : e;  // -1: no transposed entry
         if (t >= 0) P[t] += scale * double(y);
       }
@@ -254,347 +306,182 @@ __device__ __forceinline__ void pattern_partials(const int64_t (*off)[kTileNbr],
   }
 }
 
-// Reverse iterations jb down to ja over the trajectory slots.
-__global__ void __launch_bounds__(256, 4)
+// Reverse iterations jb down to ja over the trajectory slots. RESIDENT: one
+// tile per block for the whole launch (lists staged once, the staged
+// entries' dL partial sums accumulated in shared memory in FP32 and added
+// to the FP64 partial buffers at the end); otherwise blocks stream over the
+// tiles and add partial sums to the FP64 buffers directly. Two phases per
+// iteration with one grid barrier between them: (1) gathers of Z_j's
+// neighbours, the mask, Vb = M o Sb, dY~ and the scalar partials, Vb
+// published in both layouts, the dL partial sums (against Z_j); (2) gathers
+// of Vb's neighbours, Zb, and the momentum carries.
+template <bool RESIDENT>
+__global__ void __launch_bounds__(256, RESIDENT ? 5 : 4)
 traj_reverse_kernel(const __grid_constant__ TrajArgs a) {
+  using Off = typename std::conditional<RESIDENT, int32_t, int64_t>::type;
   extern __shared__ __align__(16) unsigned char smraw[];
-  AdjSmem& sm = *reinterpret_cast<AdjSmem*>(smraw);
+  TrajSmem<Off>& sm = *reinterpret_cast<TrajSmem<Off>*>(smraw);
   __shared__ double red[8];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int rl = warp * 4 + (lane >> 3), cq = 4 * (lane & 7);
   const float lam = float(*a.lam);
   const double lamd = double(lam);
   const int64_t nnz_r = a.Lr.rowptr[a.rr], nnz_c = a.Lc.rowptr[a.rc];
+  const double sr = -2.0 * lamd * a.gamma_r, sc = -2.0 * lamd * a.gamma_c;
+  if (RESIDENT) {
+    int i0, j0, ni, nj;
+    tile_of(a, blockIdx.x, i0, j0, ni, nj);
+    stage_nbr(sm.nb, a.Lr, a.Lc, int(a.ldzt), int(a.ldz), i0, j0, ni, nj);
+    for (int e = threadIdx.x; e < TB * kTileNbr; e += blockDim.x) {
+      sm.pr[e / kTileNbr][e % kTileNbr] = 0.f;
+      sm.pc[e / kTileNbr][e % kTileNbr] = 0.f;
+    }
+  }
   double s_lam = 0.0, s_gr = 0.0, s_gc = 0.0;
   for (int j = a.jb; j >= a.ja; --j) {
     const int par = j & 1;
-    const float* Zin = a.Zs + slot_off(a, j);
-    const float* ZTin = a.ZTs + slot_off(a, j);
-    // phase 1: mask, Vb, dY~ and scalar partials, dL partials
+    const float* Zin = zslot(a, j);
+    const float* ZTin = ztslot(a, j);
+    // phase 1
     for (int tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x) {
       int i0, j0, ni, nj;
       tile_of(a, tile, i0, j0, ni, nj);
       const int ti = i0 / TB, tj = j0 / TB;
-      stage_nbr(sm.nb, a.Lr, a.Lc, a.rr, a.rc, i0, j0, ni, nj);
+      if (RESIDENT) __syncthreads();  // sm.ac / sm.tl of the previous phase are consumed
+      else stage_nbr(sm.nb, a.Lr, a.Lc, int(a.ldzt), int(a.ldz), i0, j0, ni, nj);
       {
-        float o[4];
-        nbr_sum4(sm.nb.coff, sm.nb.cval, sm.nb.cdeg, sm.nb.cf0, warp * 4, lane < ni, ZTin, i0 + lane,
-                 a.Lc, a.rr, o);
-#pragma unroll
-        for (int u = 0; u < 4; ++u) sm.ac[lane][warp * 4 + u] = o[u];
+        const float4 o = nbr_sum_v4<Off, RESIDENT ? 4 : 8>(sm.nb.coff[rl], sm.nb.cval[rl], sm.nb.cdeg[rl], sm.nb.cf0[rl],
+                                    rl < nj && cq < ni, ZTin, i0 + cq, a.Lc, a.ldzt);
+        sm.ac[cq][rl] = o.x;
+        sm.ac[cq + 1][rl] = o.y;
+        sm.ac[cq + 2][rl] = o.z;
+        sm.ac[cq + 3][rl] = o.w;
       }
-      float ar[4];
-      nbr_sum4(sm.nb.roff, sm.nb.rval, sm.nb.rdeg, sm.nb.rf0, warp * 4, lane < nj, Zin, j0 + lane,
-               a.Lr, a.rc, ar);
+      const bool own = rl < ni && cq < nj;
+      float4 ar = nbr_sum_v4<Off, RESIDENT ? 4 : 8>(sm.nb.roff[rl], sm.nb.rval[rl], sm.nb.rdeg[rl], sm.nb.rf0[rl], own, Zin, j0 + cq,
+                             a.Lr, a.ldz);
       __syncthreads();
-      float vrow[4];
+      float4 vb4 = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (own) {
+        const int64_t i = i0 + rl, jj = j0 + cq;
+        const int nv = nj - cq;
+        float4 z4 = __ldcg(reinterpret_cast<const float4*>(Zin + i * a.ldz + jj));
+        float4 y4 = ld4(a.Yt + i * a.ldy + jj, a.yvec, nv);
+        float4 sb4 = *reinterpret_cast<const float4*>(a.Sb + i * a.ldz + jj);
+        float4 dy4 = ld4(a.dY + i * a.lddy + jj, a.dyvec, nv);
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const int r = warp * 4 + u;
-        float vb = 0.f;
-        if (r < ni && lane < nj) {
-          const int64_t i = i0 + r, jj = j0 + lane;
-          const float z = __ldcg(Zin + i * a.rc + jj);
-          const float y = __ldg(a.Yt + i * a.ldy + jj);
-          const float gr = fmaf(a.two_gr, ar[u], a.two_gc * sm.ac[r][lane]);
-          const float v = fmaf(-lam, gr, z);
-          const float dl = v - y;
-          const float sb = a.Sb[i * a.rc + jj];
-          vb = (fabsf(dl) - lam) > 0.f ? sb : 0.f;
-          a.dY[i * a.lddy + jj] += sb - vb;
-          if (vb != 0.f) {
-            s_lam += -double(copysignf(1.f, dl)) * vb - double(vb) * double(gr);
-            s_gr += -2.0 * lamd * double(vb) * double(ar[u]);
-            s_gc += -2.0 * lamd * double(vb) * double(sm.ac[r][lane]);
+        for (int q = 0; q < 4; ++q) {
+          if (q < nv) {
+            const float gr = fmaf(a.two_gr, cmp(ar, q), a.two_gc * sm.ac[rl][cq + q]);
+            const float v = fmaf(-lam, gr, cmp(z4, q));
+            const float dl = v - cmp(y4, q);
+            const float sb = cmp(sb4, q);
+            const float vb = (fabsf(dl) - lam) > 0.f ? sb : 0.f;
+            cmp(dy4, q) += sb - vb;
+            if (vb != 0.f) {
+              s_lam += -double(copysignf(1.f, dl)) * vb - double(vb) * double(gr);
+              s_gr += -2.0 * lamd * double(vb) * double(cmp(ar, q));
+              s_gc += -2.0 * lamd * double(vb) * double(sm.ac[rl][cq + q]);
+            }
+            cmp(vb4, q) = vb;
           }
-          a.Vb[par][i * a.rc + jj] = vb;
         }
-        vrow[u] = vb;
-        sm.tl[r][lane] = vb;
+        st4(a.dY + i * a.lddy + jj, dy4, a.dyvec, nv);
+        *reinterpret_cast<float4*>(a.Vb[par] + i * a.ldz + jj) = vb4;
       }
+      sm.tl[rl][cq] = vb4.x;
+      sm.tl[rl][cq + 1] = vb4.y;
+      sm.tl[rl][cq + 2] = vb4.z;
+      sm.tl[rl][cq + 3] = vb4.w;
       __syncthreads();
-      // transposed publish; own column values for the Lc partials
-      float vcol[4];
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const int c = warp * 4 + u;
-        vcol[u] = sm.tl[lane][c];
-        if (c < nj && lane < ni) a.VbT[par][int64_t(j0 + c) * a.rr + i0 + lane] = vcol[u];
-      }
-      // dLr(a, b) += -2 lambda gamma_r sum_c Vb(a, c) Z(b, c), c over the tile's columns
+      // column rl of the tile, rows cq..cq+3: transposed publish
+      const bool ocol = rl < nj && cq < ni;
+      const float4 vc4 = make_float4(sm.tl[cq][rl], sm.tl[cq + 1][rl], sm.tl[cq + 2][rl], sm.tl[cq + 3][rl]);
+      if (ocol) *reinterpret_cast<float4*>(a.VbT[par] + int64_t(j0 + rl) * a.ldzt + i0 + cq) = vc4;
+      // dLr(a, b) += scale sum_c Vb(a, c) Z(b, c) over the tile's columns;
+      // dLc(a, b) += scale sum_r Z(r, a) Vb(r, b) over its rows (column b's
+      // list (b, a) lands on the transposed entry (a, b))
       if (a.gamma_r != 0.0)
-        pattern_partials(sm.nb.roff, sm.nb.rdeg, sm.nb.rf0, warp * 4, lane < nj, Zin, j0 + lane, a.Lr,
-                         a.rc, vrow, -2.0 * lamd * a.gamma_r, a.Pr + int64_t(tj) * nnz_r, nullptr,
-                         lane);
-      // dLc(a, b) += -2 lambda gamma_c sum_r Z(r, a) Vb(r, b), r over the tile's rows:
-      // column b of the tile walks its own list (b, a), so the sum lands on
-      // the transposed entry (a, b)
+        list_partials<RESIDENT>(sm.nb.roff[rl], sm.nb.rdeg[rl], sm.nb.rf0[rl], own, Zin, j0 + cq, a.Lr, a.ldz,
+                                vb4, sm.pr[rl], sr, a.Pr + int64_t(tj) * nnz_r, nullptr, lane);
       if (a.gamma_c != 0.0)
-        pattern_partials(sm.nb.coff, sm.nb.cdeg, sm.nb.cf0, warp * 4, lane < ni, ZTin, i0 + lane, a.Lc,
-                         a.rr, vcol, -2.0 * lamd * a.gamma_c, a.Pc + int64_t(ti) * nnz_c, a.tmap_c,
-                         lane);
-      __syncthreads();
+        list_partials<RESIDENT>(sm.nb.coff[rl], sm.nb.cdeg[rl], sm.nb.cf0[rl], ocol, ZTin, i0 + cq, a.Lc,
+                                a.ldzt, vc4, sm.pc[rl], sc, a.Pc + int64_t(ti) * nnz_c, a.tmap_c, lane);
+      if (!RESIDENT) __syncthreads();
     }
     if (!grid_sync(a.bar)) return;
-    // phase 2: Zb = Vb - lambda (2 gr Lr Vb + 2 gc Vb Lc), carry to S_{j-1}, S_{j-2}
+    // phase 2: Zb = Vb - lambda (2 gr Lr Vb + 2 gc Vb Lc), carries to S_{j-1}, S_{j-2}
     const float* V = a.Vb[par];
     const float* VT = a.VbT[par];
     const float mup = j >= 2 ? a.mu[j - 1] : 0.f;
     for (int tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x) {
       int i0, j0, ni, nj;
       tile_of(a, tile, i0, j0, ni, nj);
-      stage_nbr(sm.nb, a.Lr, a.Lc, a.rr, a.rc, i0, j0, ni, nj);
+      if (RESIDENT) __syncthreads();
+      else stage_nbr(sm.nb, a.Lr, a.Lc, int(a.ldzt), int(a.ldz), i0, j0, ni, nj);
       {
-        float o[4];
-        nbr_sum4(sm.nb.coff, sm.nb.cval, sm.nb.cdeg, sm.nb.cf0, warp * 4, lane < ni, VT, i0 + lane,
-                 a.Lc, a.rr, o);
-#pragma unroll
-        for (int u = 0; u < 4; ++u) sm.ac[lane][warp * 4 + u] = o[u];
+        const float4 o = nbr_sum_v4<Off, RESIDENT ? 4 : 8>(sm.nb.coff[rl], sm.nb.cval[rl], sm.nb.cdeg[rl], sm.nb.cf0[rl],
+                                    rl < nj && cq < ni, VT, i0 + cq, a.Lc, a.ldzt);
+        sm.ac[cq][rl] = o.x;
+        sm.ac[cq + 1][rl] = o.y;
+        sm.ac[cq + 2][rl] = o.z;
+        sm.ac[cq + 3][rl] = o.w;
       }
-      float ar[4];
-      nbr_sum4(sm.nb.roff, sm.nb.rval, sm.nb.rdeg, sm.nb.rf0, warp * 4, lane < nj, V, j0 + lane, a.Lr,
-               a.rc, ar);
+      const bool own = rl < ni && cq < nj;
+      float4 ar = nbr_sum_v4<Off, RESIDENT ? 4 : 8>(sm.nb.roff[rl], sm.nb.rval[rl], sm.nb.rdeg[rl], sm.nb.rf0[rl], own, V, j0 + cq,
+                             a.Lr, a.ldz);
       __syncthreads();
+      if (own) {
+        const int64_t i = i0 + rl, jj = j0 + cq;
+        const int nv = nj - cq;
+        const int64_t l = i * a.ldz + jj;
+        float4 vb4 = __ldcg(reinterpret_cast<const float4*>(V + l));
+        float4 a24 = *reinterpret_cast<const float4*>(a.A2 + l);
+        float4 zb4 = make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const int r = warp * 4 + u;
-        if (r < ni && lane < nj) {
-          const int64_t i = i0 + r, jj = j0 + lane;
-          const float vb = __ldcg(V + i * a.rc + jj);
-          const float g = fmaf(a.two_gr, ar[u], a.two_gc * sm.ac[r][lane]);
-          const float zb = fmaf(-lam, g, vb);
-          const int64_t l = i * a.rc + jj;
-          if (j >= 2) {
-            a.Sb[l] = fmaf(1.f + mup, zb, a.A2[l]);
-            a.A2[l] = -mup * zb;
-          } else {
-            a.dY[i * a.lddy + jj] += zb + a.A2[l];
-            a.Sb[l] = 0.f;
-            a.A2[l] = 0.f;
+        for (int q = 0; q < 4; ++q)
+          if (q < nv) {
+            const float g = fmaf(a.two_gr, cmp(ar, q), a.two_gc * sm.ac[rl][cq + q]);
+            cmp(zb4, q) = fmaf(-lam, g, cmp(vb4, q));
           }
-        }
-      }
-      __syncthreads();
-    }
-  }
-  s_lam = block_sum(s_lam, red);
-  s_gr = block_sum(s_gr, red);
-  s_gc = block_sum(s_gc, red);
-  if (threadIdx.x == 0) {
-    atomicAdd(a.scal_bar + 0, s_lam);
-    atomicAdd(a.scal_bar + 1, s_gr);
-    atomicAdd(a.scal_bar + 2, s_gc);
-  }
-}
-
-// Resident variant: one tile per block for the whole launch. The
-// neighbour lists are staged once, and the tile's dL partial sums for its
-// staged entries accumulate in shared memory (FP32 within one segment,
-// added to the FP64 partial buffers at the end of the launch).
-struct ResSmem {
-  TileNbr32 nb;
-  float ac[TB][TB + 1];
-  float tl[TB][TB + 1];
-  float pr[TB][kTileNbr];
-  float pc[TB][kTileNbr];
-};
-
-// Partial sums of dL for the four staged lists u of the tile: for every
-// list entry q, the 32-lane sum of x[off[u][q] + base] * own[u] is added to
-// acc[first + u][q] (beyond the staged entries: scale times it to P at
-// entry tmap(f0 + q), or f0 + q without a map). With weights w, out[u] also
-// receives sum_q w[u][q] x[off[u][q] + base]. Eight entries at a time:
-// eight independent gathers, a butterfly that leaves each entry's sum in
-// four lanes (9 shuffles for 8 sums), eight lanes update in parallel.
-__device__ __forceinline__ void nbr_sum_partials(const int32_t (*off)[kTileNbr], const float (*w)[kTileNbr],
-                                                 const int* deg, const int64_t* f0, int first, bool valid,
-                                                 const float* __restrict__ x, int64_t base, const CsrView& L,
-                                                 int64_t stride, const float own[4], float (*acc)[kTileNbr],
-                                                 double scale, double* __restrict__ P,
-                                                 const int64_t* __restrict__ tmap, int lane, float out[4]) {
-  const bool h16 = lane & 16, h8 = lane & 8, h4 = lane & 4;
-  const int mine = (h16 ? 4 : 0) + (h8 ? 2 : 0) + (h4 ? 1 : 0);
-#pragma unroll
-  for (int u = 0; u < 4; ++u) {
-    const int d = deg[first + u];
-    const int64_t fu = f0[first + u];
-    float sum = 0.f;
-    for (int q0 = 0; q0 < d; q0 += 8) {
-      float v[8];
-#pragma unroll
-      for (int t = 0; t < 8; ++t) {
-        const int q = q0 + t;
-        float xv = 0.f, wv = 0.f;
-        if (q < d) {
-          if (q < kTileNbr) {
-            if (w) wv = w[first + u][q];
-            if (valid) xv = __ldcg(x + int64_t(off[first + u][q]) + base);
-          } else {
-            if (w) wv = __ldg(L.val + fu + q);
-            if (valid) xv = __ldcg(x + int64_t(__ldg(L.col + fu + q)) * stride + base);
-          }
-        }
-        sum = fmaf(wv, xv, sum);
-        v[t] = xv * own[u];
-      }
-      float w4[4], w2[2];
-#pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        const float send = h16 ? v[i] : v[i + 4];
-        const float keep = h16 ? v[i + 4] : v[i];
-        w4[i] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
-      }
-#pragma unroll
-      for (int i = 0; i < 2; ++i) {
-        const float send = h8 ? w4[i] : w4[i + 2];
-        const float keep = h8 ? w4[i + 2] : w4[i];
-        w2[i] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
-      }
-      float y;
-      {
-        const float send = h4 ? w2[0] : w2[1];
-        const float keep = h4 ? w2[1] : w2[0];
-        y = keep + __shfl_xor_sync(0xffffffffu, send, 4);
-      }
-      y += __shfl_xor_sync(0xffffffffu, y, 2);
-      y += __shfl_xor_sync(0xffffffffu, y, 1);
-      const int q = q0 + mine;
-      if ((lane & 3) == 0 && q < d && y != 0.f) {
-        if (q < kTileNbr) {
-          acc[first + u][q] += y;
-        } else {
-          const int64_t e = fu + q;
-          const int64_t t = tmap ? __ldg(tmap + e) : e;
-          if (t >= 0) P[t] += scale * double(y);
-        }
-      }
-    }
-    out[u] = sum;
-  }
-}
-
-__global__ void __launch_bounds__(256, 5)
-traj_reverse_resident_kernel(const __grid_constant__ TrajArgs a) {
-  extern __shared__ __align__(16) unsigned char smraw[];
-  ResSmem& sm = *reinterpret_cast<ResSmem*>(smraw);
-  __shared__ double red[8];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const float lam = float(*a.lam);
-  const double lamd = double(lam);
-  const int64_t nnz_r = a.Lr.rowptr[a.rr], nnz_c = a.Lc.rowptr[a.rc];
-  int i0, j0, ni, nj;
-  tile_of(a, blockIdx.x, i0, j0, ni, nj);
-  const int ti = i0 / TB, tj = j0 / TB;
-  stage_nbr(sm.nb, a.Lr, a.Lc, a.rr, a.rc, i0, j0, ni, nj);
-  for (int e = threadIdx.x; e < TB * kTileNbr; e += blockDim.x) {
-    sm.pr[e / kTileNbr][e % kTileNbr] = 0.f;
-    sm.pc[e / kTileNbr][e % kTileNbr] = 0.f;
-  }
-  const double sr = -2.0 * lamd * a.gamma_r, sc = -2.0 * lamd * a.gamma_c;
-  double* Prt = a.Pr + int64_t(tj) * nnz_r;
-  double* Pct = a.Pc + int64_t(ti) * nnz_c;
-  double s_lam = 0.0, s_gr = 0.0, s_gc = 0.0;
-  for (int j = a.jb; j >= a.ja; --j) {
-    const int par = j & 1;
-    const float* Zin = a.Zs + slot_off(a, j);
-    const float* ZTin = a.ZTs + slot_off(a, j);
-    __syncthreads();  // sm.ac / sm.tl of the previous phase are consumed
-    {
-      float o[4];
-      nbr_sum4(sm.nb.coff, sm.nb.cval, sm.nb.cdeg, sm.nb.cf0, warp * 4, lane < ni, ZTin, i0 + lane, a.Lc,
-               a.rr, o);
-#pragma unroll
-      for (int u = 0; u < 4; ++u) sm.ac[lane][warp * 4 + u] = o[u];
-    }
-    float ar[4];
-    nbr_sum4(sm.nb.roff, sm.nb.rval, sm.nb.rdeg, sm.nb.rf0, warp * 4, lane < nj, Zin, j0 + lane, a.Lr, a.rc, ar);
-    __syncthreads();
-    float vrow[4];
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const int r = warp * 4 + u;
-      float vb = 0.f;
-      if (r < ni && lane < nj) {
-        const int64_t i = i0 + r, jj = j0 + lane;
-        const float z = __ldcg(Zin + i * a.rc + jj);
-        const float y = __ldg(a.Yt + i * a.ldy + jj);
-        const float gr = fmaf(a.two_gr, ar[u], a.two_gc * sm.ac[r][lane]);
-        const float v = fmaf(-lam, gr, z);
-        const float dl = v - y;
-        const float sb = a.Sb[i * a.rc + jj];
-        vb = (fabsf(dl) - lam) > 0.f ? sb : 0.f;
-        a.dY[i * a.lddy + jj] += sb - vb;
-        if (vb != 0.f) {
-          s_lam += -double(copysignf(1.f, dl)) * vb - double(vb) * double(gr);
-          s_gr += -2.0 * lamd * double(vb) * double(ar[u]);
-          s_gc += -2.0 * lamd * double(vb) * double(sm.ac[r][lane]);
-        }
-        a.Vb[par][i * a.rc + jj] = vb;
-      }
-      vrow[u] = vb;
-      sm.tl[r][lane] = vb;
-    }
-    __syncthreads();
-    float vcol[4];
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const int c = warp * 4 + u;
-      vcol[u] = sm.tl[lane][c];
-      if (c < nj && lane < ni) a.VbT[par][int64_t(j0 + c) * a.rr + i0 + lane] = vcol[u];
-    }
-    // dLr(a, b) += scale sum_c Vb(a, c) Z(b, c) over the tile's columns;
-    // dLc(a, b) += scale sum_r Z(r, a) Vb(r, b) over its rows: column b's
-    // list (b, a) lands on the transposed entry (a, b)
-    float dummy[4];
-    if (a.gamma_r != 0.0)
-      nbr_sum_partials(sm.nb.roff, nullptr, sm.nb.rdeg, sm.nb.rf0, warp * 4, lane < nj, Zin, j0 + lane, a.Lr,
-                       a.rc, vrow, sm.pr, sr, Prt, nullptr, lane, dummy);
-    if (a.gamma_c != 0.0)
-      nbr_sum_partials(sm.nb.coff, nullptr, sm.nb.cdeg, sm.nb.cf0, warp * 4, lane < ni, ZTin, i0 + lane, a.Lc,
-                       a.rr, vcol, sm.pc, sc, Pct, a.tmap_c, lane, dummy);
-    if (!grid_sync(a.bar)) return;
-    const float* V = a.Vb[par];
-    const float* VT = a.VbT[par];
-    const float mup = j >= 2 ? a.mu[j - 1] : 0.f;
-    {
-      float o[4];
-      nbr_sum4(sm.nb.coff, sm.nb.cval, sm.nb.cdeg, sm.nb.cf0, warp * 4, lane < ni, VT, i0 + lane, a.Lc, a.rr,
-               o);
-#pragma unroll
-      for (int u = 0; u < 4; ++u) sm.ac[lane][warp * 4 + u] = o[u];
-    }
-    nbr_sum4(sm.nb.roff, sm.nb.rval, sm.nb.rdeg, sm.nb.rf0, warp * 4, lane < nj, V, j0 + lane, a.Lr, a.rc, ar);
-    __syncthreads();
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const int r = warp * 4 + u;
-      if (r < ni && lane < nj) {
-        const int64_t i = i0 + r, jj = j0 + lane;
-        const float vb = vrow[u];
-        const float g = fmaf(a.two_gr, ar[u], a.two_gc * sm.ac[r][lane]);
-        const float zb = fmaf(-lam, g, vb);
-        const int64_t l = i * a.rc + jj;
         if (j >= 2) {
-          a.Sb[l] = fmaf(1.f + mup, zb, a.A2[l]);
-          a.A2[l] = -mup * zb;
+          float4 sbn, a2n;
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            cmp(sbn, q) = fmaf(1.f + mup, cmp(zb4, q), cmp(a24, q));
+            cmp(a2n, q) = -mup * cmp(zb4, q);
+          }
+          *reinterpret_cast<float4*>(a.Sb + l) = sbn;
+          *reinterpret_cast<float4*>(a.A2 + l) = a2n;
         } else {
-          a.dY[i * a.lddy + jj] += zb + a.A2[l];
-          a.Sb[l] = 0.f;
-          a.A2[l] = 0.f;
+          float4 dy4 = ld4(a.dY + i * a.lddy + jj, a.dyvec, nv);
+#pragma unroll
+          for (int q = 0; q < 4; ++q) cmp(dy4, q) += cmp(zb4, q) + cmp(a24, q);
+          st4(a.dY + i * a.lddy + jj, dy4, a.dyvec, nv);
+          *reinterpret_cast<float4*>(a.Sb + l) = make_float4(0.f, 0.f, 0.f, 0.f);
+          *reinterpret_cast<float4*>(a.A2 + l) = make_float4(0.f, 0.f, 0.f, 0.f);
         }
       }
+      if (!RESIDENT) __syncthreads();
     }
   }
-  __syncthreads();
-  // flush the staged entries' partial sums: row lists land on their own
-  // entries of Lr, column lists on the transposed entries of Lc
-  for (int e = threadIdx.x; e < TB * kTileNbr; e += blockDim.x) {
-    const int r = e / kTileNbr, q = e % kTileNbr;
-    const float vr = sm.pr[r][q];
-    if (vr != 0.f) Prt[sm.nb.rf0[r] + q] += sr * double(vr);
-    const float vc = sm.pc[r][q];
-    if (vc != 0.f) {
-      const int64_t t = __ldg(a.tmap_c + sm.nb.cf0[r] + q);
-      if (t >= 0) Pct[t] += sc * double(vc);
+  if (RESIDENT) {
+    __syncthreads();
+    int i0, j0, ni, nj;
+    tile_of(a, blockIdx.x, i0, j0, ni, nj);
+    double* Prt = a.Pr + int64_t(j0 / TB) * nnz_r;
+    double* Pct = a.Pc + int64_t(i0 / TB) * nnz_c;
+    // flush the staged entries' partial sums: row lists on their own
+    // entries of Lr, column lists on the transposed entries of Lc
+    for (int e = threadIdx.x; e < TB * kTileNbr; e += blockDim.x) {
+      const int r = e / kTileNbr, q = e % kTileNbr;
+      const float vr = sm.pr[r][q];
+      if (vr != 0.f) Prt[sm.nb.rf0[r] + q] += sr * double(vr);
+      const float vc = sm.pc[r][q];
+      if (vc != 0.f) {
+        const int64_t t = __ldg(a.tmap_c + sm.nb.cf0[r] + q);
+        if (t >= 0) Pct[t] += sc * double(vc);
+      }
     }
   }
   s_lam = block_sum(s_lam, red);
@@ -906,7 +793,8 @@ struct BwdWs {
 BwdWs bwd_layout(void* ws, int rr, int rc, int J, int ck, int T, int64_t nnz_r, int64_t nnz_c) {
   Carve c(ws);
   BwdWs w{};
-  const size_t mn = size_t(rr) * rc;
+  // row-major buffers rr x ldz, column-major rc x ldzt (rows padded to 4)
+  const size_t mn = size_t(rr) * ((rc + 3) / 4 * 4), mnt = size_t(rc) * ((rr + 3) / 4 * 4);
   const int nseg = (J + ck - 1) / ck;
   const int nslot = std::max(ck + 1, 2);
   w.mu = c.take<float>(size_t(J) + 2);
@@ -918,10 +806,10 @@ BwdWs bwd_layout(void* ws, int rr, int rc, int J, int ck, int T, int64_t nnz_r, 
   w.A2 = c.take<float>(mn);
   for (int p = 0; p < 2; ++p) {
     w.Vb[p] = c.take<float>(mn);
-    w.VbT[p] = c.take<float>(mn);
+    w.VbT[p] = c.take<float>(mnt);
   }
   w.Zs = c.take<float>(mn * nslot);
-  w.ZTs = c.take<float>(mn * nslot);
+  w.ZTs = c.take<float>(mnt * nslot);
   w.ckS = c.take<float>(mn * std::max(nseg - 1, 1));
   w.ckZ = c.take<float>(mn * std::max(nseg - 1, 1));
   w.Pr = c.take<double>(size_t(ceil_div(rc, TB)) * std::max<int64_t>(nnz_r, 1));
@@ -1057,7 +945,8 @@ cpca_status frpcag_adjoint(const AdjCall& c, AdjMode mode) {
   cudaStream_t st = c.st;
   const CsrView lr{c.Lr->n, c.Lr->rowptr, c.Lr->col, c.Lr->val};
   const CsrView lc{c.Lc->n, c.Lc->rowptr, c.Lc->col, c.Lc->val};
-  const size_t mn = size_t(rr) * rc;
+  const int64_t ldz = (rc + 3) / 4 * 4, ldzt = (rr + 3) / 4 * 4;
+  const size_t mn = size_t(rr) * ldz;
   CPCA_CUDA(cudaMemsetAsync(w.err, 0, sizeof(int), st));
 
   PowAdjArgs pa{};
@@ -1102,6 +991,10 @@ cpca_status frpcag_adjoint(const AdjCall& c, AdjMode mode) {
   a.rc = rc;
   a.ntj = ceil_div(rc, TB);
   a.ntiles = int(ceil_div(rr, TB) * int64_t(a.ntj));
+  a.ldz = ldz;
+  a.ldzt = ldzt;
+  a.yvec = c.ldyt % 4 == 0 && reinterpret_cast<uintptr_t>(c.Yt) % 16 == 0;
+  a.dyvec = c.dYt && c.lddyt % 4 == 0 && reinterpret_cast<uintptr_t>(c.dYt) % 16 == 0;
   a.Lr = lr;
   a.Lc = lc;
   a.lam = w.scal + 2;
@@ -1129,22 +1022,22 @@ cpca_status frpcag_adjoint(const AdjCall& c, AdjMode mode) {
   a.scal_bar = w.bar;
   a.tmap_c = w.tmap_c;
   a.bar = GridBar{w.bar_cnt, w.bar_cnt + kBarrierCounters, w.err};
-  const size_t smem = sizeof(AdjSmem);
-  const size_t smem_res = sizeof(ResSmem);
+  const size_t smem = sizeof(TrajSmem<int64_t>);
+  const size_t smem_res = sizeof(TrajSmem<int32_t>);
   static bool attr = false;
   if (!attr) {
     CPCA_CUDA(cudaFuncSetAttribute((const void*)traj_forward_kernel,
                                    cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
-    CPCA_CUDA(cudaFuncSetAttribute((const void*)traj_reverse_kernel,
+    CPCA_CUDA(cudaFuncSetAttribute((const void*)traj_reverse_kernel<false>,
                                    cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
-    CPCA_CUDA(cudaFuncSetAttribute((const void*)traj_reverse_resident_kernel,
+    CPCA_CUDA(cudaFuncSetAttribute((const void*)traj_reverse_kernel<true>,
                                    cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem_res)));
     attr = true;
   }
   const int gf = coop_blocks((const void*)traj_forward_kernel, 256, smem, a.ntiles);
-  const int gb = coop_blocks((const void*)traj_reverse_kernel, 256, smem, a.ntiles);
-  const bool resident = mn < (size_t(1) << 31) &&
-      coop_blocks((const void*)traj_reverse_resident_kernel, 256, smem_res, 1 << 30) >= a.ntiles;
+  const int gb = coop_blocks((const void*)traj_reverse_kernel<false>, 256, smem, a.ntiles);
+  const bool resident = mn < (size_t(1) << 31) && size_t(rc) * ldzt < (size_t(1) << 31) &&
+      coop_blocks((const void*)traj_reverse_kernel<true>, 256, smem_res, 1 << 30) >= a.ntiles;
   const int nseg = (J + ck - 1) / ck;
   const unsigned gs = std::min<unsigned>(a.ntiles, num_sms() * 8);
   auto launch = [&](const void* k, int grid, size_t sm, const char* name) -> cpca_status {
@@ -1161,7 +1054,7 @@ cpca_status frpcag_adjoint(const AdjCall& c, AdjMode mode) {
     // iterations 1..jlast with checkpoints at j = ck, 2 ck, ..., jlast;
     // then the last segment with its Z_j kept in the slots (the reverse
     // sweep starts there without recomputing it); X = S_J
-    seed_kernel<<<gs, 256, 0, st>>>(c.Yt, c.ldyt, c.Yt, c.ldyt, rr, rc, w.Zs, w.ZTs, w.S);
+    seed_kernel<<<gs, 256, 0, st>>>(c.Yt, c.ldyt, c.Yt, c.ldyt, rr, rc, ldz, ldzt, w.Zs, w.ZTs, w.S);
     CPCA_LAUNCHED();
     if (nseg > 1) {
       a.jbase = 1;
@@ -1171,7 +1064,7 @@ cpca_status frpcag_adjoint(const AdjCall& c, AdjMode mode) {
       a.ck = ck;
       CPCA_TRY(launch((const void*)traj_forward_kernel, gf, smem, "adj_fista_fwd"));
       const size_t off = size_t(nseg - 2) * mn;
-      seed_kernel<<<gs, 256, 0, st>>>(w.ckZ + off, rc, w.ckS + off, rc, rr, rc, w.Zs, w.ZTs, w.S);
+      seed_kernel<<<gs, 256, 0, st>>>(w.ckZ + off, ldz, w.ckS + off, ldz, rr, rc, ldz, ldzt, w.Zs, w.ZTs, w.S);
       CPCA_LAUNCHED();
     }
     a.jbase = jlast + 1;
@@ -1180,11 +1073,11 @@ cpca_status frpcag_adjoint(const AdjCall& c, AdjMode mode) {
     a.jb = J;
     a.ck = 0;
     CPCA_TRY(launch((const void*)traj_forward_kernel, gf, smem, "adj_fista_fwd"));
-    CPCA_CUDA(cudaMemcpy2DAsync(c.X, sizeof(float) * c.ldx, w.S, sizeof(float) * rc, sizeof(float) * rc, rr,
+    CPCA_CUDA(cudaMemcpy2DAsync(c.X, sizeof(float) * c.ldx, w.S, sizeof(float) * ldz, sizeof(float) * rc, rr,
                                 cudaMemcpyDeviceToDevice, st));
   } else if (mode == kBackward && nseg > 1) {
     // forward pass with checkpoints at j = ck, 2 ck, ..., (nseg - 1) ck
-    seed_kernel<<<gs, 256, 0, st>>>(c.Yt, c.ldyt, c.Yt, c.ldyt, rr, rc, w.Zs, w.ZTs, w.S);
+    seed_kernel<<<gs, 256, 0, st>>>(c.Yt, c.ldyt, c.Yt, c.ldyt, rr, rc, ldz, ldzt, w.Zs, w.ZTs, w.S);
     CPCA_LAUNCHED();
     a.jbase = 1;
     a.nslot = 2;
@@ -1198,7 +1091,8 @@ cpca_status frpcag_adjoint(const AdjCall& c, AdjMode mode) {
     CPCA_CUDA(cudaMemsetAsync(w.bar, 0, 4 * sizeof(double), st));
     transpose_map_kernel<<<std::max(1, std::min(rc, num_sms() * 8)), 64, 0, st>>>(lc, w.tmap_c);
     CPCA_LAUNCHED();
-    CPCA_CUDA(cudaMemcpy2DAsync(w.Sb, sizeof(float) * rc, c.dX, sizeof(float) * c.lddx, sizeof(float) * rc,
+    CPCA_CUDA(cudaMemsetAsync(w.Sb, 0, sizeof(float) * mn, st));
+    CPCA_CUDA(cudaMemcpy2DAsync(w.Sb, sizeof(float) * ldz, c.dX, sizeof(float) * c.lddx, sizeof(float) * rc,
                                 rr, cudaMemcpyDeviceToDevice, st));
     CPCA_CUDA(cudaMemsetAsync(w.A2, 0, sizeof(float) * mn, st));
     CPCA_CUDA(cudaMemset2DAsync(c.dYt, sizeof(float) * c.lddyt, 0, sizeof(float) * rc, rr, st));
@@ -1213,10 +1107,11 @@ cpca_status frpcag_adjoint(const AdjCall& c, AdjMode mode) {
       const bool have = mode == kBackwardResume && m == nseg - 1;
       if (!have) {
         if (m == 0) {
-          seed_kernel<<<gs, 256, 0, st>>>(c.Yt, c.ldyt, c.Yt, c.ldyt, rr, rc, w.Zs, w.ZTs, w.S);
+          seed_kernel<<<gs, 256, 0, st>>>(c.Yt, c.ldyt, c.Yt, c.ldyt, rr, rc, ldz, ldzt, w.Zs, w.ZTs, w.S);
         } else {
           const size_t off = size_t(m - 1) * mn;
-          seed_kernel<<<gs, 256, 0, st>>>(w.ckZ + off, rc, w.ckS + off, rc, rr, rc, w.Zs, w.ZTs, w.S);
+          seed_kernel<<<gs, 256, 0, st>>>(w.ckZ + off, ldz, w.ckS + off, ldz, rr, rc, ldz, ldzt, w.Zs, w.ZTs,
+                                          w.S);
         }
         CPCA_LAUNCHED();
       }
@@ -1227,8 +1122,8 @@ cpca_status frpcag_adjoint(const AdjCall& c, AdjMode mode) {
       }
       a.ja = j0 + 1;
       a.jb = j1;
-      if (resident) CPCA_TRY(launch((const void*)traj_reverse_resident_kernel, a.ntiles, smem_res, "adj_fista_rev"));
-      else CPCA_TRY(launch((const void*)traj_reverse_kernel, gb, smem, "adj_fista_rev"));
+      if (resident) CPCA_TRY(launch((const void*)traj_reverse_kernel<true>, a.ntiles, smem_res, "adj_fista_rev"));
+      else CPCA_TRY(launch((const void*)traj_reverse_kernel<false>, gb, smem, "adj_fista_rev"));
     }
     double* oLr = c.dLr ? c.dLr : w.dLr;
     double* oLc = c.dLc ? c.dLc : w.dLc;

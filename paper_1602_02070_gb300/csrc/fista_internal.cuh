@@ -72,7 +72,7 @@ __device__ __forceinline__ void stage_nbr(TileNbrT<Off>& nb, const CsrView& Lr, 
 // out[t] = sum_q w[q] x[off[q] + base + t], base a multiple of 4 floats
 // (16-byte loads from rows whose length is padded to a multiple of 4).
 // Entries in list order; beyond the staging area straight from the CSR.
-template <typename Off>
+template <typename Off, int CHUNK = 8>
 __device__ __forceinline__ float4 nbr_sum_v4(const Off* off, const float* w, int deg, int64_t f0, bool valid,
                                              const float* __restrict__ x, int64_t base, const CsrView& L,
                                              int64_t stride) {
@@ -80,12 +80,12 @@ __device__ __forceinline__ float4 nbr_sum_v4(const Off* off, const float* w, int
   if (!valid) return acc;
   const int ds = min(deg, kTileNbr);
   int q = 0;
-  for (; q + 8 <= ds; q += 8) {
-    float4 v[8];
+  for (; q + CHUNK <= ds; q += CHUNK) {
+    float4 v[CHUNK];
 #pragma unroll
-    for (int t = 0; t < 8; ++t) v[t] = __ldcg(reinterpret_cast<const float4*>(x + off[q + t] + base));
+    for (int t = 0; t < CHUNK; ++t) v[t] = __ldcg(reinterpret_cast<const float4*>(x + off[q + t] + base));
 #pragma unroll
-    for (int t = 0; t < 8; ++t) {
+    for (int t = 0; t < CHUNK; ++t) {
       const float wt = w[q + t];
       acc.x = fmaf(wt, v[t].x, acc.x);
       acc.y = fmaf(wt, v[t].y, acc.y);

@@ -541,20 +541,53 @@ __device__ __forceinline__ float spmv_row(const CsrView& L, int i, const float* 
   return warp_sumf(sum) * scale;
 }
 
+// Two per-graph FP64 sums, added up in the block first (shared atomics) and
+// then with one global atomic per block and graph.
+__device__ __forceinline__ void flush2(double* bs, double* g0, double* g1) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    if (bs[0] != 0.0) atomicAdd(g0, bs[0]);
+    if (bs[1] != 0.0) atomicAdd(g1, bs[1]);
+    bs[0] = bs[1] = 0.0;
+  }
+}
+
 __global__ void __launch_bounds__(512)
 power_adjoint_kernel(const __grid_constant__ PowAdjArgs a) {
+  __shared__ double bs[2];
+  if (threadIdx.x < 2) bs[threadIdx.x] = 0.0;
+  __syncthreads();
   const int lane = threadIdx.x & 31;
   const int nwarp = (gridDim.x * blockDim.x) >> 5;
   const int wid = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int nthr = gridDim.x * blockDim.x, tid = blockIdx.x * blockDim.x + threadIdx.x;
+  // each warp keeps its first row's CSR entries in registers (at most 32)
+  int c_d = -1, c_col = 0;
+  float c_val = 0.f;
+  if (wid < a.rows) {
+    const PowGraph& G = a.g[pow_graph(a, wid)];
+    const int i = wid - G.row0;
+    const int64_t e0 = G.L.rowptr[i];
+    c_d = int(G.L.rowptr[i + 1] - e0);
+    if (c_d <= 32 && lane < c_d) {
+      c_col = G.L.col[e0 + lane];
+      c_val = G.L.val[e0 + lane];
+    }
+  }
+  // row r's product with x (scaled): from the registers when cached
+  auto row_dot = [&](const PowGraph& G, int r, const float* x, float scale) -> float {
+    if (r == wid && c_d >= 0 && c_d <= 32) return warp_sumf(lane < c_d ? c_val * __ldcg(x + c_col) : 0.f) * scale;
+    return spmv_row(G.L, r - G.row0, x, scale, lane);
+  };
   if (!a.reverse) {
     for (int r = tid; r < a.rows; r += nthr) {
       const PowGraph& G = a.g[pow_graph(a, r)];
       const int i = r - G.row0;
       const double x = uniform01_at(stream_state0(a.seed, G.stream), uint64_t(i) + 1) - 0.5;
       G.U[i] = float(x);
-      atomicAdd(G.nrm2, x * x);
+      atomicAdd(bs + pow_graph(a, r), x * x);
     }
+    flush2(bs, a.g[0].nrm2, a.g[1].nrm2);
     if (!grid_sync(a.bar)) return;
     for (int t = 0; t < a.T; ++t) {
       for (int r = wid; r < a.rows; r += nwarp) {
@@ -562,12 +595,13 @@ power_adjoint_kernel(const __grid_constant__ PowAdjArgs a) {
         const int i = r - G.row0;
         const double n2 = __ldcg(G.nrm2 + t);
         const float inv = n2 > 0 ? float(1.0 / sqrt(n2)) : 0.f;
-        const float s = spmv_row(G.L, i, G.U + size_t(t) * G.n, inv, lane);
+        const float s = row_dot(G, r, G.U + size_t(t) * G.n, inv);
         if (lane == 0) {
           G.U[size_t(t + 1) * G.n + i] = s;
-          atomicAdd(G.nrm2 + t + 1, double(s) * double(s));
+          atomicAdd(bs + pow_graph(a, r), double(s) * double(s));
         }
       }
+      flush2(bs, a.g[0].nrm2 + t + 1, a.g[1].nrm2 + t + 1);
       if (!grid_sync(a.bar)) return;
     }
     for (int r = wid; r < a.rows; r += nwarp) {
@@ -596,14 +630,15 @@ power_adjoint_kernel(const __grid_constant__ PowAdjArgs a) {
     const double n2 = __ldcg(G.nrm2 + a.T);
     const double inv = n2 > 0 ? 1.0 / sqrt(n2) : 0.0;
     const float* u = G.U + size_t(a.T) * G.n;
-    const float lv = spmv_row(G.L, i, u, 1.f, lane);
+    const float lv = row_dot(G, r, u, 1.f);
     if (lane == 0) {
       const double vi = double(__ldcg(u + i)) * inv;
       const double vb = 2.0 * (*G.rho_bar) * (double(lv) * inv - (*G.rho) * vi);
       G.vb[a.T & 1][i] = float(vb);
-      atomicAdd(G.acc + (a.T & 3), vi * vb);
+      atomicAdd(bs + pow_graph(a, r), vi * vb);
     }
   }
+  flush2(bs, a.g[0].acc + (a.T & 3), a.g[1].acc + (a.T & 3));
   if (!grid_sync(a.bar)) return;
   for (int t = a.T; t >= 1; --t) {
     // ubar_t = (vbar_t - v_t d_t) / |u_t|
@@ -622,16 +657,17 @@ power_adjoint_kernel(const __grid_constant__ PowAdjArgs a) {
     for (int r = wid; r < a.rows; r += nwarp) {
       const PowGraph& G = a.g[pow_graph(a, r)];
       const int i = r - G.row0;
-      const float s = spmv_row(G.L, i, G.Ub + size_t(t - 1) * G.n, 1.f, lane);
+      const float s = row_dot(G, r, G.Ub + size_t(t - 1) * G.n, 1.f);
       if (lane == 0) {
         G.vb[(t - 1) & 1][i] = s;
         if (t > 1) {
           const double n2 = __ldcg(G.nrm2 + t - 1);
           const double inv = n2 > 0 ? 1.0 / sqrt(n2) : 0.0;
-          atomicAdd(G.acc + ((t - 1) & 3), double(G.U[size_t(t - 1) * G.n + i]) * inv * double(s));
+          atomicAdd(bs + pow_graph(a, r), double(G.U[size_t(t - 1) * G.n + i]) * inv * double(s));
         }
       }
     }
+    flush2(bs, a.g[0].acc + ((t - 1) & 3), a.g[1].acc + ((t - 1) & 3));
     if (!grid_sync(a.bar)) return;
   }
 }
@@ -843,7 +879,8 @@ cpca_status run_power(PowAdjArgs& pa, const BwdWs& w, int reverse, cudaStream_t 
   pa.reverse = reverse;
   CPCA_TRY(reset_barrier(w, st));
   const int want = ceil_div(int64_t(pa.rows) * 32, 512);
-  const int grid = coop_blocks((const void*)power_adjoint_kernel, 512, 0, std::max(want, 1));
+  const int grid = std::min(2 * num_sms(), coop_blocks((const void*)power_adjoint_kernel, 512, 0,
+                                                       std::max(want, 1)));
   void* args[] = {&pa};
   CPCA_PROF(reverse ? "adj_power_rev" : "adj_power_fwd", st);
   CPCA_CUDA(cudaLaunchCooperativeKernel((void*)power_adjoint_kernel, dim3(grid), dim3(512), args, 0, st));

@@ -170,6 +170,7 @@ __device__ __forceinline__ void red_add_release_u32(unsigned int* p, unsigned in
 }
 
 __device__ __forceinline__ bool grid_sync(const GridBar& b) {
+  __shared__ int grid_ok;  // thread 0's view of the error flag, for the block
   __syncthreads();
   if (threadIdx.x == 0) {
     const unsigned int nb = gridDim.x * gridDim.y * gridDim.z;
@@ -190,9 +191,10 @@ __device__ __forceinline__ bool grid_sync(const GridBar& b) {
       }
     }
     __threadfence();
+    grid_ok = *(volatile int*)b.err == 0;
   }
   __syncthreads();
-  return *(volatile int*)b.err == 0;
+  return grid_ok != 0;
 }
 
 }  // namespace cpca

@@ -334,6 +334,18 @@ def adjoint_comparison(M, torch, Yd, cfg, n_heldout=10000, reps=3, h=1e-3):
                     "differences give the two gamma derivatives only, from FP32 losses"}
 
 
+def profiled_dram_bytes(summary):
+    """DRAM bytes per launch recorded in a committed ncu summary under
+    profiles/ (the 'dram_bytes_per_launch:' line), or None."""
+    try:
+        for line in open(os.path.join(ROOT, "profiles", summary)):
+            if line.startswith("dram_bytes_per_launch:"):
+                return int(line.split(":")[1])
+    except OSError:
+        pass
+    return None
+
+
 def roofline_for(name, ms, launches, ctx, peaks):
     """Algorithmic work of the named kernel over the timed region / its time."""
     hbm = peaks["hbm_gbs"] if peaks else 6800.0
@@ -343,7 +355,8 @@ def roofline_for(name, ms, launches, ctx, peaks):
         byts = ctx["fista_bytes_per_iter"] * ctx["fista_iters"] * launches
         a = byts / sec / 1e9
         return {"kernel": name, "bound": "hbm", "achieved": a, "peak": hbm, "unit": "GB/s",
-                "frac": a / hbm, "traffic": None, "peak_source": src,
+                "frac": a / hbm, "traffic": profiled_dram_bytes("fista_batch_kernel_2576x250.md"),
+                "traffic_unit": "bytes per launch (ncu dram read + write)", "peak_source": src,
                 "note": "20 B per entry of Y~ + CSR bytes, per FISTA iteration; the working set "
                         "(13 MB) is L2-resident at this size, so the kernel is latency-bound"}
     if name.startswith("knn_candidates"):

@@ -171,14 +171,25 @@ struct TrajSmem {
 
 // Forward iterations ja..jb with the trajectory kept: the solve's FISTA
 // step, entry for entry, in its thread layout (lane group g of warp w owns
-// tile row / column 4 w + g, each lane 4 consecutive entries).
-__global__ void __launch_bounds__(256, 4)
+// tile row / column 4 w + g, each lane 4 consecutive entries). RESIDENT:
+// one tile per block for the whole launch, lists staged once and S kept in
+// registers (written back at the end); otherwise blocks stream over tiles.
+template <bool RESIDENT>
+__global__ void __launch_bounds__(256, RESIDENT ? 5 : 4)
 traj_forward_kernel(const __grid_constant__ TrajArgs a) {
+  using Off = typename std::conditional<RESIDENT, int32_t, int64_t>::type;
   extern __shared__ __align__(16) unsigned char smraw[];
-  TrajSmem<int64_t>& sm = *reinterpret_cast<TrajSmem<int64_t>*>(smraw);
+  TrajSmem<Off>& sm = *reinterpret_cast<TrajSmem<Off>*>(smraw);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int rl = warp * 4 + (lane >> 3), cq = 4 * (lane & 7);
   const float lam = float(*a.lam);
+  float4 rs = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (RESIDENT) {
+    int i0, j0, ni, nj;
+    tile_of(a, blockIdx.x, i0, j0, ni, nj);
+    stage_nbr(sm.nb, a.Lr, a.Lc, int(a.ldzt), int(a.ldz), i0, j0, ni, nj);
+    if (rl < ni && cq < nj) rs = *reinterpret_cast<const float4*>(a.S + int64_t(i0 + rl) * a.ldz + j0 + cq);
+  }
   for (int j = a.ja; j <= a.jb; ++j) {
     const float mu = a.mu[j];
     const float* Zin = zslot(a, j);
@@ -190,18 +201,19 @@ traj_forward_kernel(const __grid_constant__ TrajArgs a) {
     for (int tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x) {
       int i0, j0, ni, nj;
       tile_of(a, tile, i0, j0, ni, nj);
-      stage_nbr(sm.nb, a.Lr, a.Lc, int(a.ldzt), int(a.ldz), i0, j0, ni, nj);
+      if (!RESIDENT) stage_nbr(sm.nb, a.Lr, a.Lc, int(a.ldzt), int(a.ldz), i0, j0, ni, nj);
       {
-        const float4 o = nbr_sum_v4(sm.nb.coff[rl], sm.nb.cval[rl], sm.nb.cdeg[rl], sm.nb.cf0[rl],
-                                    rl < nj && cq < ni, ZTin, i0 + cq, a.Lc, a.ldzt);
+        const float4 o = nbr_sum_v4<Off, RESIDENT ? 4 : 8>(sm.nb.coff[rl], sm.nb.cval[rl], sm.nb.cdeg[rl],
+                                                           sm.nb.cf0[rl], rl < nj && cq < ni, ZTin, i0 + cq,
+                                                           a.Lc, a.ldzt);
         sm.ac[cq][rl] = o.x;
         sm.ac[cq + 1][rl] = o.y;
         sm.ac[cq + 2][rl] = o.z;
         sm.ac[cq + 3][rl] = o.w;
       }
       const bool own = rl < ni && cq < nj;
-      float4 ar = nbr_sum_v4(sm.nb.roff[rl], sm.nb.rval[rl], sm.nb.rdeg[rl], sm.nb.rf0[rl], own, Zin, j0 + cq,
-                             a.Lr, a.ldz);
+      float4 ar = nbr_sum_v4<Off, RESIDENT ? 4 : 8>(sm.nb.roff[rl], sm.nb.rval[rl], sm.nb.rdeg[rl],
+                                                    sm.nb.rf0[rl], own, Zin, j0 + cq, a.Lr, a.ldz);
       __syncthreads();
       float4 zn4 = make_float4(0.f, 0.f, 0.f, 0.f);
       if (own) {
@@ -209,7 +221,7 @@ traj_forward_kernel(const __grid_constant__ TrajArgs a) {
         const int nv = nj - cq;
         float4 z4 = __ldcg(reinterpret_cast<const float4*>(Zin + i * a.ldz + jj));
         float4 y4 = ld4(a.Yt + i * a.ldy + jj, a.yvec, nv);
-        float4 s4 = *reinterpret_cast<const float4*>(a.S + i * a.ldz + jj);
+        float4 s4 = RESIDENT ? rs : *reinterpret_cast<const float4*>(a.S + i * a.ldz + jj);
         float4 sv4 = make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
@@ -223,7 +235,8 @@ traj_forward_kernel(const __grid_constant__ TrajArgs a) {
             cmp(zn4, q) = fmaf(mu, sv - sp, sv);
           }
         }
-        *reinterpret_cast<float4*>(a.S + i * a.ldz + jj) = sv4;
+        if (RESIDENT) rs = sv4;
+        else *reinterpret_cast<float4*>(a.S + i * a.ldz + jj) = sv4;
         *reinterpret_cast<float4*>(Zout + i * a.ldz + jj) = zn4;
         if (ckpt) {
           *reinterpret_cast<float4*>(a.ckS + ckoff + i * a.ldz + jj) = sv4;
@@ -238,9 +251,14 @@ traj_forward_kernel(const __grid_constant__ TrajArgs a) {
       if (rl < nj && cq < ni)
         *reinterpret_cast<float4*>(ZTout + int64_t(j0 + rl) * a.ldzt + i0 + cq) =
             make_float4(sm.tl[cq][rl], sm.tl[cq + 1][rl], sm.tl[cq + 2][rl], sm.tl[cq + 3][rl]);
-      __syncthreads();
+      if (!RESIDENT) __syncthreads();
     }
     if (!grid_sync(a.bar)) return;
+  }
+  if (RESIDENT) {
+    int i0, j0, ni, nj;
+    tile_of(a, blockIdx.x, i0, j0, ni, nj);
+    if (rl < ni && cq < nj) *reinterpret_cast<float4*>(a.S + int64_t(i0 + rl) * a.ldz + j0 + cq) = rs;
   }
 }
 
@@ -1063,18 +1081,35 @@ cpca_status frpcag_adjoint(const AdjCall& c, AdjMode mode) {
   const size_t smem_res = sizeof(TrajSmem<int32_t>);
   static bool attr = false;
   if (!attr) {
-    CPCA_CUDA(cudaFuncSetAttribute((const void*)traj_forward_kernel,
+    CPCA_CUDA(cudaFuncSetAttribute((const void*)traj_forward_kernel<false>,
                                    cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
+    CPCA_CUDA(cudaFuncSetAttribute((const void*)traj_forward_kernel<true>,
+                                   cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem_res)));
     CPCA_CUDA(cudaFuncSetAttribute((const void*)traj_reverse_kernel<false>,
                                    cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
     CPCA_CUDA(cudaFuncSetAttribute((const void*)traj_reverse_kernel<true>,
                                    cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem_res)));
     attr = true;
   }
-  const int gf = coop_blocks((const void*)traj_forward_kernel, 256, smem, a.ntiles);
+  const int gf = coop_blocks((const void*)traj_forward_kernel<false>, 256, smem, a.ntiles);
   const int gb = coop_blocks((const void*)traj_reverse_kernel<false>, 256, smem, a.ntiles);
   const bool resident = mn < (size_t(1) << 31) && size_t(rc) * ldzt < (size_t(1) << 31) &&
       coop_blocks((const void*)traj_reverse_kernel<true>, 256, smem_res, 1 << 30) >= a.ntiles;
+  const bool resident_f = mn < (size_t(1) << 31) && size_t(rc) * ldzt < (size_t(1) << 31) &&
+      coop_blocks((const void*)traj_forward_kernel<true>, 256, smem_res, 1 << 30) >= a.ntiles;
+  auto launch_fwd = [&]() -> cpca_status {
+    CPCA_TRY(reset_barrier(w, st));
+    void* args[] = {&a};
+    CPCA_PROF("adj_fista_fwd", st);
+    if (resident_f)
+      CPCA_CUDA(cudaLaunchCooperativeKernel((const void*)traj_forward_kernel<true>, dim3(a.ntiles), dim3(256),
+                                            args, smem_res, st));
+    else
+      CPCA_CUDA(cudaLaunchCooperativeKernel((const void*)traj_forward_kernel<false>, dim3(gf), dim3(256), args,
+                                            smem, st));
+    CPCA_LAUNCHED();
+    return CPCA_OK;
+  };
   const int nseg = (J + ck - 1) / ck;
   const unsigned gs = std::min<unsigned>(a.ntiles, num_sms() * 8);
   auto launch = [&](const void* k, int grid, size_t sm, const char* name) -> cpca_status {
@@ -1099,7 +1134,7 @@ cpca_status frpcag_adjoint(const AdjCall& c, AdjMode mode) {
       a.ja = 1;
       a.jb = jlast;
       a.ck = ck;
-      CPCA_TRY(launch((const void*)traj_forward_kernel, gf, smem, "adj_fista_fwd"));
+      CPCA_TRY(launch_fwd());
       const size_t off = size_t(nseg - 2) * mn;
       seed_kernel<<<gs, 256, 0, st>>>(w.ckZ + off, ldz, w.ckS + off, ldz, rr, rc, ldz, ldzt, w.Zs, w.ZTs, w.S);
       CPCA_LAUNCHED();
@@ -1109,7 +1144,7 @@ cpca_status frpcag_adjoint(const AdjCall& c, AdjMode mode) {
     a.ja = jlast + 1;
     a.jb = J;
     a.ck = 0;
-    CPCA_TRY(launch((const void*)traj_forward_kernel, gf, smem, "adj_fista_fwd"));
+    CPCA_TRY(launch_fwd());
     CPCA_CUDA(cudaMemcpy2DAsync(c.X, sizeof(float) * c.ldx, w.S, sizeof(float) * ldz, sizeof(float) * rc, rr,
                                 cudaMemcpyDeviceToDevice, st));
   } else if (mode == kBackward && nseg > 1) {
@@ -1121,7 +1156,7 @@ cpca_status frpcag_adjoint(const AdjCall& c, AdjMode mode) {
     a.ja = 1;
     a.jb = (nseg - 1) * ck;
     a.ck = ck;
-    CPCA_TRY(launch((const void*)traj_forward_kernel, gf, smem, "adj_fista_fwd"));
+    CPCA_TRY(launch_fwd());
   }
   if (mode != kForwardTape) {
     // reverse, segment by segment
@@ -1155,7 +1190,7 @@ cpca_status frpcag_adjoint(const AdjCall& c, AdjMode mode) {
       if (!have && j1 - 1 >= j0 + 1) {
         a.ja = j0 + 1;
         a.jb = j1 - 1;
-        CPCA_TRY(launch((const void*)traj_forward_kernel, gf, smem, "adj_fista_fwd"));
+        CPCA_TRY(launch_fwd());
       }
       a.ja = j0 + 1;
       a.jb = j1;

@@ -68,22 +68,27 @@ gemm_nn_tall(const float* __restrict__ A, int64_t lda, int m, int n, const float
 }
 
 // C (n x b) = A^T B with A (m x n, lda), B (m x b); 8 rows of C per block.
+// With gridDim.y > 1 the rows of A are split into gridDim.y chunks (of
+// `chunk` rows, a multiple of 64) and block (x, y) writes its partial
+// product to C + y * n * b; gemm_tn_reduce adds the chunks in order.
 __global__ void __launch_bounds__(256)
 gemm_tn_tall(const float* __restrict__ A, int64_t lda, int m, int n, const float* __restrict__ B,
-             int b, float* __restrict__ C) {
+             int b, float* __restrict__ C, int chunk) {
   __shared__ float As[64][8];
   __shared__ float Bs[64][BMAX];
   const int tid = threadIdx.x, c = tid & 63, rg = tid >> 6;
   const int j0 = blockIdx.x * 8;
+  const int ibeg = blockIdx.y * chunk, iend = min(m, ibeg + chunk);
+  C += int64_t(blockIdx.y) * n * b;
   float acc0 = 0.f, acc1 = 0.f;
-  for (int i0 = 0; i0 < m; i0 += 64) {
+  for (int i0 = ibeg; i0 < iend; i0 += 64) {
     for (int e = tid; e < 64 * 8; e += 256) {
       const int i = e >> 3, jj = e & 7;
-      As[i][jj] = (i0 + i < m && j0 + jj < n) ? A[int64_t(i0 + i) * lda + j0 + jj] : 0.f;
+      As[i][jj] = (i0 + i < iend && j0 + jj < n) ? A[int64_t(i0 + i) * lda + j0 + jj] : 0.f;
     }
     for (int e = tid; e < 64 * b; e += 256) {
       const int i = e / b, cc = e % b;
-      Bs[i][cc] = (i0 + i < m) ? B[int64_t(i0 + i) * b + cc] : 0.f;
+      Bs[i][cc] = (i0 + i < iend) ? B[int64_t(i0 + i) * b + cc] : 0.f;
     }
     __syncthreads();
     if (c < b) {
@@ -100,6 +105,39 @@ gemm_tn_tall(const float* __restrict__ A, int64_t lda, int m, int n, const float
     if (j0 + rg * 2 < n) C[int64_t(j0 + rg * 2) * b + c] = acc0;
     if (j0 + rg * 2 + 1 < n) C[int64_t(j0 + rg * 2 + 1) * b + c] = acc1;
   }
+}
+
+// C = sum over the chunks of P (nchunk x total floats), in chunk order.
+__global__ void gemm_tn_reduce(const float* __restrict__ P, int nchunk, int64_t total, float* __restrict__ C) {
+  for (int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; t < total;
+       t += int64_t(gridDim.x) * blockDim.x) {
+    float s = 0.f;
+    for (int q = 0; q < nchunk; ++q) s += P[int64_t(q) * total + t];
+    C[t] = s;
+  }
+}
+
+constexpr int kTnChunks = 16;  // row chunks of the split X~^T B products
+
+// C (n x b) = A^T B, split over row chunks when A is tall (scratch:
+// kTnChunks * n * b floats).
+static cpca_status tn_tall(const float* A, int64_t lda, int m, int n, const float* B, int b, float* C,
+                           float* scratch, cudaStream_t st) {
+  const int chunks = std::max(1, std::min(kTnChunks, int(ceil_div(m, 256))));
+  if (chunks == 1) {
+    gemm_tn_tall<<<dim3(ceil_div(n, 8), 1), 256, 0, st>>>(A, lda, m, n, B, b, C, m);
+    CPCA_LAUNCHED();
+    return CPCA_OK;
+  }
+  const int chunk = int(ceil_div(ceil_div(m, chunks), 64)) * 64;
+  const int nch = int(ceil_div(m, chunk));
+  gemm_tn_tall<<<dim3(ceil_div(n, 8), nch), 256, 0, st>>>(A, lda, m, n, B, b, scratch, chunk);
+  count_launch();
+  const int64_t total = int64_t(n) * b;
+  gemm_tn_reduce<<<std::min<unsigned>(ceil_div(total, 256), num_sms() * 4), 256, 0, st>>>(scratch, nch,
+                                                                                          total, C);
+  CPCA_LAUNCHED();
+  return CPCA_OK;
 }
 
 constexpr int GRAM_ROWS = 64;
@@ -127,57 +165,86 @@ gram_kernel(const float* __restrict__ Q, int m, int b, double* __restrict__ G) {
   }
 }
 
-// Rank-revealing Cholesky G = R^T R (R upper) and Rinv with the columns of
-// numerically dependent directions zeroed. One warp, FP64, R and R^-1 in
-// shared memory (no block-wide barriers on the b sequential steps).
-__global__ void __launch_bounds__(32)
-chol_inv_kernel(const double* __restrict__ G, int b, double* __restrict__ Rinv) {
-  extern __shared__ double cs_sm[];
-  double* R = cs_sm;                    // [BMAX][BMAX + 1]
-  double* X = R + BMAX * (BMAX + 1);    // [BMAX][BMAX + 1]
-  int* dead = reinterpret_cast<int*>(X + BMAX * (BMAX + 1));
-  const int lane = threadIdx.x;
-  constexpr int LD = BMAX + 1;
-  for (int e = lane; e < BMAX * LD; e += 32) {
-    R[e] = 0.0;
-    X[e] = 0.0;
-  }
-  __syncwarp();
-  for (int j = 0; j < b; ++j) {
-    double part = 0.0;
-    for (int k = lane; k < j; k += 32) part += R[k * LD + j] * R[k * LD + j];
-    part = warp_sum(part);
-    const double gjj = G[j * b + j];
-    const double d = gjj - part;
-    const bool dd = !(gjj > 1e-300) || !(d > 1e-10 * gjj);
-    const double djj = dd ? 1.0 : sqrt(d);
-    for (int i = j + 1 + lane; i < b; i += 32) {
-      double s = 0.0;
-      if (!dd) {
-        s = G[j * b + i];
-        for (int k = 0; k < j; ++k) s -= R[k * LD + j] * R[k * LD + i];
-        s /= djj;
+// Rank-revealing Cholesky G = R^T R (R upper), right-looking, one block:
+// step k takes the pivot, scales row k and updates the trailing triangle in
+// parallel (FP64; on this GPU an FP64 warp instruction costs many issue
+// cycles, so the work is spread over the block instead of chained in one
+// warp). A pivot below 1e-10 of its original diagonal marks a dependent
+// direction: row k of R becomes e_k and the direction is dropped (dead).
+// Outputs R (b x b, row-major), 1 / R_kk and the dead flags.
+__global__ void __launch_bounds__(256)
+chol_kernel(const double* __restrict__ G, int b, double* __restrict__ R, double* __restrict__ rdiag,
+            int* __restrict__ dead) {
+  __shared__ double A[BMAX][BMAX + 1];
+  __shared__ double g0[BMAX];
+  __shared__ double piv;
+  __shared__ int dk;
+  for (int e = threadIdx.x; e < b * b; e += blockDim.x) A[e / b][e % b] = G[e];
+  for (int k = threadIdx.x; k < b; k += blockDim.x) g0[k] = G[k * b + k];
+  __syncthreads();
+  for (int k = 0; k < b; ++k) {
+    if (threadIdx.x == 0) {
+      const double d = A[k][k];
+      const bool dd = !(g0[k] > 1e-300) || !(d > 1e-10 * g0[k]);
+      dk = dd;
+      piv = dd ? 1.0 : sqrt(d);
+      dead[k] = dd;
+      rdiag[k] = dd ? 0.0 : 1.0 / piv;
+    }
+    __syncthreads();
+    // row k of R
+    for (int j = k + 1 + threadIdx.x; j < b; j += blockDim.x) A[k][j] = dk ? 0.0 : A[k][j] / piv;
+    if (threadIdx.x == 0) A[k][k] = piv;
+    __syncthreads();
+    // trailing update A(i, j) -= R(k, i) R(k, j), k < i <= j
+    if (!dk) {
+      const int n = b - k - 1;
+      for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+        const int i = k + 1 + e / n, j = k + 1 + e % n;
+        if (j >= i) A[i][j] -= A[k][i] * A[k][j];
       }
-      R[j * LD + i] = s;
     }
-    if (lane == 0) {
-      R[j * LD + j] = djj;
-      dead[j] = dd;
-    }
-    __syncwarp();
+    __syncthreads();
   }
-  // R X = I with X upper triangular: row i from the rows below it
-  for (int i = b - 1; i >= 0; --i) {
-    for (int c = i + lane; c < b; c += 32) {
-      double s = (i == c) ? 1.0 : 0.0;
-      for (int k = i + 1; k <= c; ++k) s -= R[i * LD + k] * X[k * LD + c];
-      X[i * LD + c] = s / R[i * LD + i];
-    }
-    __syncwarp();
+  for (int e = threadIdx.x; e < b * b; e += blockDim.x) {
+    const int i = e / b, j = e % b;
+    R[e] = j >= i ? A[i][j] : 0.0;
   }
-  for (int e = lane; e < b * b; e += 32) {
-    const int i = e / b, c = e % b;
-    Rinv[e] = (dead[c] || i > c || dead[i]) ? 0.0 : X[i * LD + c];
+}
+
+// Qout = Qin R^-1 row by row (Qin, Qout m x b): x R = q by forward
+// substitution, one warp per row, lane c owns column c: x_k = (q_k -
+// sum_{i<k} x_i R_ik) / R_kk, then x_k is broadcast and the later lanes
+// add x_k R_kc. Dead columns come out zero. FP64 sums, FP32 in and out.
+__global__ void __launch_bounds__(256)
+trsm_rows_kernel(const float* __restrict__ Qin, int m, int b, const double* __restrict__ R,
+                 const double* __restrict__ rdiag, const int* __restrict__ dead, float* __restrict__ Qout) {
+  __shared__ double Rs[BMAX][BMAX + 1];
+  __shared__ double rd[BMAX];
+  __shared__ int dd[BMAX];
+  for (int e = threadIdx.x; e < b * b; e += blockDim.x) Rs[e / b][e % b] = R[e];
+  for (int k = threadIdx.x; k < b; k += blockDim.x) {
+    rd[k] = rdiag[k];
+    dd[k] = dead[k];
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const int nw = (gridDim.x * blockDim.x) >> 5;
+  for (int row = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; row < m; row += nw) {
+    const float* q = Qin + int64_t(row) * b;
+    double x0 = lane < b ? double(q[lane]) : 0.0, x1 = lane + 32 < b ? double(q[lane + 32]) : 0.0;
+    for (int k = 0; k < b; ++k) {
+      double xk = k < 32 ? __shfl_sync(0xffffffffu, x0, k) : __shfl_sync(0xffffffffu, x1, k - 32);
+      xk = dd[k] ? 0.0 : xk * rd[k];
+      if (lane == (k & 31)) {
+        if (k < 32) x0 = xk;
+        else x1 = xk;
+      }
+      if (lane > k && lane < b) x0 -= xk * Rs[k][lane];
+      if (lane + 32 > k && lane + 32 < b) x1 -= xk * Rs[k][lane + 32];
+    }
+    if (lane < b) Qout[int64_t(row) * b + lane] = float(x0);
+    if (lane + 32 < b) Qout[int64_t(row) * b + lane + 32] = float(x1);
   }
 }
 
@@ -753,8 +820,9 @@ output_kernel(const float* __restrict__ U, int ldu, const float* __restrict__ V,
 }  // namespace
 
 struct DecodeWs {
-  float *W, *Q, *Q2, *Ut, *Vt;
-  double *G, *Rinv, *E, *lam, *s, *sinv;
+  float *W, *Q, *Q2, *Ut, *Vt, *tn;
+  double *G, *Rchol, *E, *lam, *s, *sinv, *rdiag;
+  int* dead;
   int* k;
   int32_t *pos0, *pos1, *abar0, *abar1;
   float *minv0, *minv1;
@@ -789,7 +857,10 @@ static DecodeWs decode_layout(void* ws, int p, int n, int rr, int rc, int kmax, 
   w.Ut = c.take<float>(size_t(rr) * b);
   w.Vt = c.take<float>(size_t(rc) * b);
   w.G = c.take<double>(size_t(b) * b);
-  w.Rinv = c.take<double>(size_t(b) * b);
+  w.tn = c.take<float>(size_t(kTnChunks) * std::max(rr, rc) * std::max(b, kmax));
+  w.Rchol = c.take<double>(size_t(b) * b);
+  w.rdiag = c.take<double>(b);
+  w.dead = c.take<int>(b);
   w.E = c.take<double>(size_t(b) * b);
   w.lam = c.take<double>(b);
   w.s = c.take<double>(b);
@@ -838,8 +909,6 @@ static DecodeWs decode_layout(void* ws, int p, int n, int rr, int rc, int kmax, 
 // the subspace iteration, where only the span matters).
 static cpca_status orthonormalize(float* Q, float* Q2, int m, int b, int passes, const DecodeWs& w,
                                   cudaStream_t st) {
-  const size_t csm = sizeof(double) * 2 * BMAX * (BMAX + 1) + sizeof(int) * BMAX;
-  CPCA_CUDA(cudaFuncSetAttribute(chol_inv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(csm)));
   for (int pass = 0; pass < passes; ++pass) {
     float* in = (pass & 1) ? Q2 : Q;
     float* out = (pass & 1) ? Q : Q2;
@@ -848,10 +917,10 @@ static cpca_status orthonormalize(float* Q, float* Q2, int m, int b, int passes,
     gram_kernel<<<ceil_div(m, GRAM_ROWS), 256, 0, st>>>(in, m, b, w.G);
     CPCA_LAUNCHED();
     CPCA_PROF("svd_chol", st);
-    chol_inv_kernel<<<1, 32, csm, st>>>(w.G, b, w.Rinv);
+    chol_kernel<<<1, 256, 0, st>>>(w.G, b, w.Rchol, w.rdiag, w.dead);
     CPCA_LAUNCHED();
-    apply_small_kernel<<<std::min<unsigned>(ceil_div(int64_t(m) * b, 256), num_sms() * 4), 256, 0, st>>>(
-        in, m, b, w.Rinv, b, out, b, nullptr);
+    trsm_rows_kernel<<<std::min<unsigned>(ceil_div(int64_t(m) * 32, 256), num_sms() * 8), 256, 0, st>>>(
+        in, m, b, w.Rchol, w.rdiag, w.dead, out);
     CPCA_LAUNCHED();
   }
   if (passes & 1)
@@ -874,16 +943,22 @@ static cpca_status partial_svd(const float* Xt, int rr, int rc, int64_t ldxt, in
   float* T = w.Q;    // long side, ml x b
   auto to_long = [&](const float* in, float* out) -> cpca_status {
     CPCA_PROF("svd_gemm", st);
-    if (vspace) gemm_nn_tall<<<ceil_div(rr, 8), 256, 0, st>>>(Xt, ldxt, rr, rc, in, b, out);
-    else gemm_tn_tall<<<ceil_div(rc, 8), 256, 0, st>>>(Xt, ldxt, rr, rc, in, b, out);
-    CPCA_LAUNCHED();
+    if (vspace) {
+      gemm_nn_tall<<<ceil_div(rr, 8), 256, 0, st>>>(Xt, ldxt, rr, rc, in, b, out);
+      CPCA_LAUNCHED();
+    } else {
+      CPCA_TRY(tn_tall(Xt, ldxt, rr, rc, in, b, out, w.tn, st));
+    }
     return CPCA_OK;
   };
   auto to_short = [&](const float* in, float* out) -> cpca_status {
     CPCA_PROF("svd_gemm", st);
-    if (vspace) gemm_tn_tall<<<ceil_div(rc, 8), 256, 0, st>>>(Xt, ldxt, rr, rc, in, b, out);
-    else gemm_nn_tall<<<ceil_div(rr, 8), 256, 0, st>>>(Xt, ldxt, rr, rc, in, b, out);
-    CPCA_LAUNCHED();
+    if (vspace) {
+      CPCA_TRY(tn_tall(Xt, ldxt, rr, rc, in, b, out, w.tn, st));
+    } else {
+      gemm_nn_tall<<<ceil_div(rr, 8), 256, 0, st>>>(Xt, ldxt, rr, rc, in, b, out);
+      CPCA_LAUNCHED();
+    }
     return CPCA_OK;
   };
   const unsigned gs = std::min<unsigned>(ceil_div(int64_t(ms) * b, 256), num_sms() * 4);
@@ -1707,13 +1782,17 @@ extern "C" cpca_status cpca_decode_backward(const float* Xt, int32_t rr, int32_t
   const float* VA = vspace ? w.Vt : w.Ut;
   const float* UAb = vspace ? v.Utb : v.Vtb;  // ld k
   const float* VAb = vspace ? v.Vtb : v.Utb;
-  auto applyA = [&](const float* in, float* out) {  // out (mA x k) = A in (nA x k)
-    if (vspace) gemm_nn_tall<<<ceil_div(rr, 8), 256, 0, st>>>(Xt, ldxt, rr, rc, in, k, out);
-    else gemm_tn_tall<<<ceil_div(rc, 8), 256, 0, st>>>(Xt, ldxt, rr, rc, in, k, out);
+  auto applyA = [&](const float* in, float* out) -> cpca_status {  // out (mA x k) = A in (nA x k)
+    if (!vspace) return tn_tall(Xt, ldxt, rr, rc, in, k, out, w.tn, st);
+    gemm_nn_tall<<<ceil_div(rr, 8), 256, 0, st>>>(Xt, ldxt, rr, rc, in, k, out);
+    CPCA_LAUNCHED();
+    return CPCA_OK;
   };
-  auto applyAT = [&](const float* in, float* out) {  // out (nA x k) = A^T in (mA x k)
-    if (vspace) gemm_tn_tall<<<ceil_div(rc, 8), 256, 0, st>>>(Xt, ldxt, rr, rc, in, k, out);
-    else gemm_nn_tall<<<ceil_div(rr, 8), 256, 0, st>>>(Xt, ldxt, rr, rc, in, k, out);
+  auto applyAT = [&](const float* in, float* out) -> cpca_status {  // out (nA x k) = A^T in (mA x k)
+    if (vspace) return tn_tall(Xt, ldxt, rr, rc, in, k, out, w.tn, st);
+    gemm_nn_tall<<<ceil_div(rr, 8), 256, 0, st>>>(Xt, ldxt, rr, rc, in, k, out);
+    CPCA_LAUNCHED();
+    return CPCA_OK;
   };
   CPCA_CUDA(cudaMemsetAsync(v.Ju, 0, sizeof(double) * k * k, st));
   CPCA_CUDA(cudaMemsetAsync(v.Jv, 0, sizeof(double) * k * k, st));
@@ -1729,8 +1808,7 @@ extern "C" cpca_status cpca_decode_backward(const float* Xt, int32_t rr, int32_t
   CPCA_LAUNCHED();
   proj_sub_kernel<<<gnk, 256, 0, st>>>(nA, k, VAb, VA, b, v.Jv, v.D);
   CPCA_LAUNCHED();
-  applyAT(v.B, v.Cc);
-  CPCA_LAUNCHED();
+  CPCA_TRY(applyAT(v.B, v.Cc));
   dim3 gg(ceil_div(nA, 32), ceil_div(nA, 32));
   gram_full_kernel<<<gg, 256, 0, st>>>(Xt, ldxt, rr, rc, vspace ? 1 : 0, v.G);
   CPCA_LAUNCHED();
@@ -1743,8 +1821,7 @@ extern "C" cpca_status cpca_decode_backward(const float* Xt, int32_t rr, int32_t
   CPCA_LAUNCHED();
   tcomb_kernel<<<gnk, 256, 0, st>>>(nA, k, v.Yp, v.Yv, w.s, v.T, v.F);
   CPCA_LAUNCHED();
-  applyA(v.T, v.AT);
-  CPCA_LAUNCHED();
+  CPCA_TRY(applyA(v.T, v.AT));
   pcomb_kernel<<<gmk, 256, 0, st>>>(mA, k, UA, b, v.Cm, v.B, v.AT, w.s, v.P);
   CPCA_LAUNCHED();
   dim3 og(ceil_div(nA, 32), ceil_div(mA, 32));

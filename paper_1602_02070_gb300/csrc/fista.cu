@@ -26,7 +26,9 @@
 // (ld.global.cg) because other blocks wrote it during the previous
 // iteration of the same launch. Algorithmic traffic per iteration: read Y~,
 // S_{j-1}, Z_j and write S_j, Z_{j+1}: 20 bytes per entry.
+#include <cmath>
 #include <map>
+#include <type_traits>
 #include <mutex>
 
 #include "common.cuh"
@@ -153,6 +155,13 @@ __global__ void step_kernel(const __grid_constant__ StepArgs a) {
 }
 
 // ------------------------------------------------------- FISTA iteration --
+// mu_j = (t_j - 1) / t_{j+1}, t_1 = 1, t_{j+1} = (1 + sqrt(1 + 4 t_j^2)) / 2
+// (Algorithm 1): the same numbers for every solve, computed once on the host
+// in FP64 (IEEE +, *, / and sqrt round identically there and here) and kept
+// in constant memory; c_t_last = t_kMuTable continues the recurrence.
+constexpr int kMuTable = 8192;
+__constant__ float c_mu[kMuTable];
+__constant__ double c_t_last;
 
 struct FistaInst {
   const float* Yt;
@@ -189,14 +198,19 @@ __device__ __forceinline__ int find_inst(const FistaBatchArgs& a, int tile) {
   return lo;
 }
 
-struct TileSmem {
-  TileNbr nb;                  // neighbour lists of the tile's rows and columns
+template <typename Off>
+struct TileSmemT {
+  TileNbrT<Off> nb;            // neighbour lists of the tile's rows and columns
   float ac[TB][TB + 1];        // (Z Lc) of the tile, [row][col]
   float zt[TB][TB + 1];        // Z_{j+1} tile for the transposed store, [row][col]
   unsigned int stopped[kMaxBatch / 32];
+  float mu;                    // momentum coefficient of the iteration
 };
+using TileSmem = TileSmemT<int64_t>;
+using TileSmem32 = TileSmemT<int32_t>;  // resident launches (tiles below 2^31 entries)
 
-__device__ __forceinline__ void stage_tile(TileSmem& sm, const FistaInst& I, int i0, int j0, int ni,
+template <typename Off>
+__device__ __forceinline__ void stage_tile(TileSmemT<Off>& sm, const FistaInst& I, int i0, int j0, int ni,
                                            int nj) {
   stage_nbr(sm.nb, I.Lr, I.Lc, int(I.ldzt), int(I.ldz), i0, j0, ni, nj);
 }
@@ -227,8 +241,9 @@ __device__ __forceinline__ float& comp(float4& v, int t) {
 }
 
 // RESIDENT: every block owns at most one tile for the whole solve; its
-// neighbour lists are staged once, and Y~, S and the tile's own Z_j entries
-// stay in registers across iterations (S is written back at the end).
+// neighbour lists are staged once and S stays in registers across
+// iterations (written back at the end); Y~ and the tile's own Z_j come
+// through L2 like the neighbours.
 // Otherwise blocks stream over the tile list, staging lists per tile.
 // Thread layout: lane group g = lane / 8 of warp w owns tile row
 // r = 4 w + g (and, for the column products and the transposed store, tile
@@ -240,15 +255,16 @@ __device__ __forceinline__ float& comp(float4& v, int t) {
 template <bool RESIDENT>
 __global__ void __launch_bounds__(256, RESIDENT ? 5 : 4)
 fista_batch_kernel(const __grid_constant__ FistaBatchArgs a) {
+  using Off = typename std::conditional<RESIDENT, int32_t, int64_t>::type;
   extern __shared__ __align__(16) unsigned char smraw[];
-  TileSmem& sm = *reinterpret_cast<TileSmem*>(smraw);
+  TileSmemT<Off>& sm = *reinterpret_cast<TileSmemT<Off>*>(smraw);
   __shared__ double red[8];
   __shared__ int any_active;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int rl = warp * 4 + (lane >> 3);  // tile row (column) of this lane group
   const int cq = 4 * (lane & 7);          // first of the lane's 4 tile columns (rows)
-  // resident state (one tile per block)
-  float4 ry = make_float4(0.f, 0.f, 0.f, 0.f), rs = ry, rz = ry;
+  // resident state (one tile per block): S in registers
+  float4 rs = make_float4(0.f, 0.f, 0.f, 0.f);
   int rinst = 0, ri0 = 0, rj0 = 0, rni = 0, rnj = 0;
   if (RESIDENT && blockIdx.x < a.ntiles) {
     rinst = find_inst(a, blockIdx.x);
@@ -259,42 +275,54 @@ fista_batch_kernel(const __grid_constant__ FistaBatchArgs a) {
     rni = min(TB, I.rr - ri0);
     rnj = min(TB, I.rc - rj0);
     stage_tile(sm, I, ri0, rj0, rni, rnj);
-    if (rl < rni && cq < rnj) {
-      ry = load4(I.Yt + int64_t(ri0 + rl) * I.ldy + rj0 + cq, I.yvec, rnj - cq);
-      rs = ry;  // S_0 = Y~
-      rz = ry;  // Z_1 = Y~
-    }
+    if (rl < rni && cq < rnj)
+      rs = load4(I.Yt + int64_t(ri0 + rl) * I.ldy + rj0 + cq, I.yvec, rnj - cq);  // S_0 = Y~
   }
   double t = 1.0;  // t_j of Algorithm 1 (t_1 = 1)
   int jlast = a.J;
+  if (threadIdx.x < kMaxBatch / 32) sm.stopped[threadIdx.x] = 0u;
+  __syncthreads();
   for (int j = 1; j <= a.J; ++j) {
-    // which instances run iteration j
-    if (threadIdx.x < kMaxBatch / 32) sm.stopped[threadIdx.x] = 0u;
-    if (threadIdx.x == 0) any_active = 0;
-    __syncthreads();
-    for (int i = threadIdx.x; i < a.ninst; i += blockDim.x) {
-      const FistaInst& I = a.in[i];
-      bool stop = __ldcg(I.done) != 0;
-      if (!stop && a.eps > 0 && j > 1) {
-        const double* ps = I.stats + 2 * ((j - 1) & 3);
-        stop = __ldcg(ps) < a.eps * __ldcg(ps + 1);
-        // the block owning the instance's first tile records the count once
-        if (stop && blockIdx.x == I.tile0 % gridDim.x) {
-          I.done[1] = j - 1;
-          I.done[0] = 1;
+    // which instances run iteration j (with a fixed count, all of them)
+    if (a.eps > 0) {
+      if (threadIdx.x < kMaxBatch / 32) sm.stopped[threadIdx.x] = 0u;
+      if (threadIdx.x == 0) any_active = 0;
+      __syncthreads();
+      for (int i = threadIdx.x; i < a.ninst; i += blockDim.x) {
+        const FistaInst& I = a.in[i];
+        bool stop = __ldcg(I.done) != 0;
+        if (!stop && j > 1) {
+          const double* ps = I.stats + 2 * ((j - 1) & 3);
+          stop = __ldcg(ps) < a.eps * __ldcg(ps + 1);
+          // the block owning the instance's first tile records the count once
+          if (stop && blockIdx.x == I.tile0 % gridDim.x) {
+            I.done[1] = j - 1;
+            I.done[0] = 1;
+          }
         }
+        if (stop) atomicOr(&sm.stopped[i >> 5], 1u << (i & 31));
+        else any_active = 1;
       }
-      if (stop) atomicOr(&sm.stopped[i >> 5], 1u << (i & 31));
-      else any_active = 1;
+      __syncthreads();
+      if (!any_active) {
+        jlast = j - 1;
+        break;
+      }
     }
-    __syncthreads();
-    if (!any_active) {
-      jlast = j - 1;
-      break;
+    // mu_j from the table; beyond it, t_{j+1} in FP64 by one thread
+    float mu;
+    if (j < kMuTable) {
+      mu = c_mu[j];
+    } else {
+      if (threadIdx.x == 0) {
+        if (j == kMuTable) t = c_t_last;
+        const double tn = (1.0 + sqrt(1.0 + 4.0 * t * t)) / 2.0;
+        sm.mu = float((t - 1.0) / tn);
+        t = tn;
+      }
+      __syncthreads();
+      mu = sm.mu;
     }
-    const double tn = (1.0 + sqrt(1.0 + 4.0 * t * t)) / 2.0;
-    const float mu = float((t - 1.0) / tn);
-    t = tn;
     const bool stats = a.eps > 0 || (a.want_last && j == a.J);
     // slot (j + 1) % 4 was last read at the start of iteration j - 2
     if (blockIdx.x == 0)
@@ -324,7 +352,7 @@ fista_batch_kernel(const __grid_constant__ FistaBatchArgs a) {
       }
       // (Z Lc): column rl of the tile, rows cq..cq+3 (from ZT)
       {
-        const float4 o = nbr_sum_v4(sm.nb.coff[rl], sm.nb.cval[rl], sm.nb.cdeg[rl], sm.nb.cf0[rl],
+        const float4 o = nbr_sum_v4<Off, RESIDENT ? 4 : 8>(sm.nb.coff[rl], sm.nb.cval[rl], sm.nb.cdeg[rl], sm.nb.cf0[rl],
                                     rl < nj && cq < ni, ZTin, i0 + cq, I.Lc, I.ldzt);
         sm.ac[cq][rl] = o.x;
         sm.ac[cq + 1][rl] = o.y;
@@ -333,7 +361,7 @@ fista_batch_kernel(const __grid_constant__ FistaBatchArgs a) {
       }
       // (Lr Z): row rl of the tile, columns cq..cq+3
       const bool own = rl < ni && cq < nj;
-      const float4 ar = nbr_sum_v4(sm.nb.roff[rl], sm.nb.rval[rl], sm.nb.rdeg[rl], sm.nb.rf0[rl], own,
+      const float4 ar = nbr_sum_v4<Off, RESIDENT ? 4 : 8>(sm.nb.roff[rl], sm.nb.rval[rl], sm.nb.rdeg[rl], sm.nb.rf0[rl], own,
                                    Zin, j0 + cq, I.Lr, I.ldz);
       __syncthreads();  // sm.ac complete
       double dz = 0.0, nz = 0.0;
@@ -341,8 +369,8 @@ fista_batch_kernel(const __grid_constant__ FistaBatchArgs a) {
       if (own) {
         const int64_t i = i0 + rl, jj = j0 + cq;
         const int nv = nj - cq;  // valid entries among the 4
-        const float4 z4 = RESIDENT ? rz : __ldcg(reinterpret_cast<const float4*>(Zin + i * I.ldz + jj));
-        const float4 y4 = RESIDENT ? ry : load4(I.Yt + i * I.ldy + jj, I.yvec, nv);
+        const float4 z4 = __ldcg(reinterpret_cast<const float4*>(Zin + i * I.ldz + jj));
+        const float4 y4 = load4(I.Yt + i * I.ldy + jj, I.yvec, nv);
         const float4 s4 = RESIDENT ? rs : load4(I.S + i * I.lds + jj, I.svec, nv);
         float4 sv4 = make_float4(0.f, 0.f, 0.f, 0.f);
         float4 ar4 = ar, zz = z4, yy = y4, ss = s4;
@@ -366,12 +394,8 @@ fista_batch_kernel(const __grid_constant__ FistaBatchArgs a) {
             }
           }
         }
-        if (RESIDENT) {
-          rs = sv4;
-          rz = zn4;
-        } else {
-          store4(I.S + i * I.lds + jj, sv4, I.svec, nv);
-        }
+        if (RESIDENT) rs = sv4;
+        else store4(I.S + i * I.lds + jj, sv4, I.svec, nv);
         // the padding columns of the last vector get zeros
         *reinterpret_cast<float4*>(Zout + i * I.ldz + jj) = zn4;
       }
@@ -525,9 +549,32 @@ BatchWs batch_layout(void* ws, const int* rr, const int* rc, int n) {
 }
 
 // ----------------------------------------------------------------- solves --
+std::mutex g_mu_mu;
+bool g_mu_ready[256] = {false};
+
+static cpca_status ensure_mu_table() {
+  int dev = 0;
+  CPCA_CUDA(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lk(g_mu_mu);
+  if (dev < 0 || dev >= 256 || g_mu_ready[dev]) return CPCA_OK;
+  std::vector<float> mu(kMuTable);
+  double t = 1.0;
+  mu[0] = 0.f;
+  for (int j = 1; j < kMuTable; ++j) {
+    const double tn = (1.0 + std::sqrt(1.0 + 4.0 * t * t)) / 2.0;
+    mu[j] = float((t - 1.0) / tn);
+    t = tn;
+  }
+  CPCA_CUDA(cudaMemcpyToSymbol(c_mu, mu.data(), sizeof(float) * kMuTable));
+  CPCA_CUDA(cudaMemcpyToSymbol(c_t_last, &t, sizeof(double)));
+  g_mu_ready[dev] = true;
+  return CPCA_OK;
+}
+
 cpca_status fista_batch_run(const BatchProblem* P, int n, int J, double eps, bool want_last,
                             int power_iters, uint64_t power_seed, int blocks, const BatchWs& w,
                             cudaStream_t st) {
+  CPCA_TRY(ensure_mu_table());
   std::lock_guard<std::mutex> lk(g_tab_mu);
   // power iterations (instances without a given step), then lambda
   PowerBatchArgs& pa = g_pa;
@@ -621,16 +668,21 @@ cpca_status fista_batch_run(const BatchProblem* P, int n, int J, double eps, boo
   if (J == 0) return CPCA_OK;
   CPCA_CUDA(cudaMemsetAsync(w.bar, 0, sizeof(unsigned int) * (kBarrierCounters + 1), st));
   CPCA_CUDA(cudaMemsetAsync(w.err, 0, sizeof(int), st));
-  const size_t smem = sizeof(TileSmem);
+  const size_t smem = sizeof(TileSmem), smem_res = sizeof(TileSmem32);
   const void* kres = (const void*)fista_batch_kernel<true>;
   const void* kstr = (const void*)fista_batch_kernel<false>;
   static bool attr = false;
   if (!attr) {
-    CPCA_CUDA(cudaFuncSetAttribute(kres, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
+    CPCA_CUDA(cudaFuncSetAttribute(kres, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem_res)));
     CPCA_CUDA(cudaFuncSetAttribute(kstr, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
     attr = true;
   }
-  const int cap_res = coop_blocks(kres, 256, smem, 1 << 30);
+  // 32-bit staged offsets: every instance's Z and ZT below 2^31 entries
+  bool small = true;
+  for (int i = 0; i < n; ++i)
+    small = small && int64_t(P[i].rr) * ((P[i].rc + 3) / 4 * 4) < (int64_t(1) << 31) &&
+            int64_t(P[i].rc) * ((P[i].rr + 3) / 4 * 4) < (int64_t(1) << 31);
+  const int cap_res = small ? coop_blocks(kres, 256, smem_res, 1 << 30) : 0;
   const int cap_str = coop_blocks(kstr, 256, smem, 1 << 30);
   bool resident = tiles <= cap_res;
   int grid = resident ? tiles : cap_str;
@@ -644,7 +696,8 @@ cpca_status fista_batch_run(const BatchProblem* P, int n, int J, double eps, boo
   }
   void* args[] = {&fa};
   CPCA_PROF("fista_persistent", st);
-  CPCA_CUDA(cudaLaunchCooperativeKernel(resident ? kres : kstr, dim3(grid), dim3(256), args, smem, st));
+  CPCA_CUDA(cudaLaunchCooperativeKernel(resident ? kres : kstr, dim3(grid), dim3(256), args,
+                                        resident ? smem_res : smem, st));
   CPCA_LAUNCHED();
   return CPCA_OK;
 }
@@ -728,7 +781,7 @@ static cpca_status tune_batch(const BatchProblem* P, int n, const BatchWs& w, cu
   for (int i = 0; i < n; ++i) tiles += tiles_of(P[i].rr, P[i].rc);
   const size_t smem = sizeof(TileSmem);
   const int cap_str = coop_blocks((const void*)fista_batch_kernel<false>, 256, smem, 1 << 30);
-  const int cap_res = coop_blocks((const void*)fista_batch_kernel<true>, 256, smem, 1 << 30);
+  const int cap_res = coop_blocks((const void*)fista_batch_kernel<true>, 256, sizeof(TileSmem32), 1 << 30);
   std::vector<int> cands;
   for (int m = 1; m * num_sms() <= cap_str; ++m) cands.push_back(m * num_sms());
   if (cands.empty()) cands.push_back(cap_str);

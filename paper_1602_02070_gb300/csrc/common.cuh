@@ -93,6 +93,18 @@ inline int num_sms() {
   return sms;
 }
 
+// largest dynamic shared memory a block may opt into
+inline int max_smem_optin() {
+  static int bytes = -1;
+  if (bytes < 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&bytes, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (bytes <= 0) bytes = 48 * 1024;
+  }
+  return bytes;
+}
+
 inline unsigned ceil_div(int64_t a, int64_t b) { return static_cast<unsigned>((a + b - 1) / b); }
 
 // ------------------------------------------------------ SplitMix64 keys --

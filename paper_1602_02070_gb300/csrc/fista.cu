@@ -27,6 +27,7 @@
 // iteration of the same launch. Algorithmic traffic per iteration: read Y~,
 // S_{j-1}, Z_j and write S_j, Z_{j+1}: 20 bytes per entry.
 #include <cmath>
+#include <cooperative_groups.h>
 #include <map>
 #include <type_traits>
 #include <mutex>
@@ -43,7 +44,10 @@ namespace {
 // Rayleigh quotients. With v_k = u_k / |u_k| the iteration v <- L v / |L v|
 // is carried as u_{k+1} = (L u_k) / |u_k|, so each step needs one grid
 // barrier (for |u_{k+1}|). Start vector u_0(i) = SplitMix64 uniform - 1/2.
-// Iterates FP32, norms and quotients FP64.
+// Iterates FP32, norms and quotients FP64; the scale 1/|u_k| itself only
+// keeps the iterate bounded (the quotient does not depend on it) and is
+// taken in FP32 (FP64 square roots and divisions are slow on this GPU and
+// sit on every step's critical path).
 struct PowerGraph {
   CsrView L;
   float* u[2];
@@ -52,6 +56,7 @@ struct PowerGraph {
   double* out;  // |L|_2 estimate
   int stream;
   int row0;     // first row in the concatenated row list
+  int w0;       // first 32-row block in the warp-padded row list
 };
 struct PowerBatchArgs {
   PowerGraph g[2 * kMaxBatch];
@@ -95,7 +100,7 @@ power_batch_kernel(const __grid_constant__ PowerBatchArgs a) {
       const PowerGraph& G = a.g[find_graph(a, r)];
       const int i = r - G.row0;
       const double n2 = __ldcg(G.acc + k % 3);
-      const float inv = n2 > 0 ? float(1.0 / sqrt(n2)) : 0.f;
+      const float inv = n2 > 0 ? rsqrtf(float(n2)) : 0.f;  // only the direction matters
       const float* u = G.u[cur];
       float sum = 0.f;
       for (int64_t e = G.L.rowptr[i] + lane; e < G.L.rowptr[i + 1]; e += 32)
@@ -130,6 +135,148 @@ power_batch_kernel(const __grid_constant__ PowerBatchArgs a) {
       const double num = __ldcg(a.g[g].fin), den = __ldcg(a.g[g].fin + 1);
       const double last = __ldcg(a.g[g].acc + a.iters % 3);
       *a.g[g].out = (den > 0 && last > 0) ? num / den : 0.0;
+    }
+}
+
+// The same power iterations for graph sets that one thread-block cluster
+// holds: each graph's rows padded to whole warps, at most kPowMaxWarps warps
+// in all. One thread per row. A CTA keeps its rows' CSR entries in shared
+// memory as a sliced ELL block per warp (entry e of lane l at e * 32 + l, so
+// a warp's loads hit distinct banks); entries beyond the shared budget come
+// from the CSR arrays. Every CTA holds the whole iterate (padded row order,
+// ping-pong), and each new entry, like each warp's FP64 sum of squares, is
+// written into all CTAs through distributed shared memory; one cluster
+// barrier per iteration orders it. A graph's |u|^2 is the sum of its warps'
+// partials in warp order, taken identically by every warp, so the result
+// does not depend on the launch shape or on the other graphs of the batch.
+constexpr int kPowCtas = 8;
+constexpr int kPowMaxWarps = kPowCtas * 32;
+
+__device__ __forceinline__ int find_graph_warp(const PowerBatchArgs& a, int vw) {
+  int lo = 0, hi = a.ngraph - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (a.g[mid].w0 <= vw) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+// sum over graph G's warps of part[w0 + w], lane-strided then a butterfly:
+// the same bits in every lane and every warp
+__device__ __forceinline__ double graph_warp_sum(const double* part, const PowerGraph& G, int lane) {
+  const int nw = (G.L.n + 31) >> 5;
+  double t = 0.0;
+  for (int w = lane; w < nw; w += 32) t += part[G.w0 + w];
+  return warp_sum(t);
+}
+
+__global__ void __cluster_dims__(kPowCtas, 1, 1) __launch_bounds__(1024)
+power_cluster_kernel(const __grid_constant__ PowerBatchArgs a, int nvw, int ell_cap) {
+  namespace cg = cooperative_groups;
+  cg::cluster_group cl = cg::this_cluster();
+  const int crank = int(cl.block_rank());
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const int NV = 32 * nvw;
+  double* wq = reinterpret_cast<double*>(smraw);  // [2][nvw]: warp sums of u_k^2
+  double* rq = wq + 2 * nvw;                      // [2][nvw]: warp sums of u^T L u, u^T u
+  float* xv = reinterpret_cast<float*>(rq + 2 * nvw);  // [2][NV]: the iterate
+  int2* ell = reinterpret_cast<int2*>(xv + 2 * NV);    // [nlw][dcap][32]: (column, value)
+  const int lane = threadIdx.x & 31, lw = threadIdx.x >> 5, nlw = blockDim.x >> 5;
+  const int vw = lw * kPowCtas + crank;  // this warp's padded row block
+  const bool wact = vw < nvw;
+  const PowerGraph& G = a.g[wact ? find_graph_warp(a, vw) : 0];
+  const int i = (vw - G.w0) * 32 + lane;
+  const bool valid = wact && i < G.L.n;
+  const int vbase = 32 * G.w0;
+  int64_t e0 = 0;
+  int deg = 0;
+  if (valid) {
+    e0 = G.L.rowptr[i];
+    deg = int(G.L.rowptr[i + 1] - e0);
+  }
+  // this warp's ELL block: min(longest row, equal share of the budget) slots
+  int slots = deg;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) slots = max(slots, __shfl_xor_sync(0xffffffffu, slots, o));
+  const int dcap = ell_cap / (32 * nlw);
+  slots = min(slots, dcap);
+  const int2* el = ell + size_t(lw) * dcap * 32 + lane;
+  for (int e = 0; e < slots; ++e)
+    ell[size_t(lw) * dcap * 32 + e * 32 + lane] =
+        e < deg ? make_int2(vbase + G.L.col[e0 + e], __float_as_int(G.L.val[e0 + e])) : make_int2(0, 0);
+  // u_0 and the warp sums of its squares (FP64, before rounding), computed
+  // alike in every CTA
+  for (int r = threadIdx.x; r < NV; r += blockDim.x) {
+    const PowerGraph& H = a.g[find_graph_warp(a, r >> 5)];
+    const int j = r - 32 * H.w0;
+    xv[r] = j < H.L.n ? float(uniform01_at(stream_state0(a.seed, H.stream), uint64_t(j) + 1) - 0.5) : 0.f;
+  }
+  for (int w = lw; w < nvw; w += nlw) {
+    const PowerGraph& H = a.g[find_graph_warp(a, w)];
+    const int j = (w - H.w0) * 32 + lane;
+    double q = 0.0;
+    if (j < H.L.n) {
+      const double x = uniform01_at(stream_state0(a.seed, H.stream), uint64_t(j) + 1) - 0.5;
+      q = x * x;
+    }
+    q = warp_sum(q);
+    if (lane == 0) wq[w] = q;
+  }
+  // remote copies: lane l sends float4 chunk (l & 7) of the warp's 32 new
+  // entries to CTAs (l >> 3) and (l >> 3) + 4, and its warp sum to CTA (l & 7)
+  const int ch = lane & 7;
+  float* xr0 = cl.map_shared_rank(xv, lane >> 3);
+  float* xr1 = cl.map_shared_rank(xv, (lane >> 3) + 4);
+  double* wr = cl.map_shared_rank(wq, lane & 7);
+  auto spmv = [&](const float* x) {
+    float acc = 0.f;
+#pragma unroll 4
+    for (int e = 0; e < slots; ++e) {
+      const int2 v = el[e * 32];
+      acc = fmaf(__int_as_float(v.y), x[v.x], acc);
+    }
+    for (int e = slots; e < deg; ++e)
+      acc = fmaf(__ldg(G.L.val + e0 + e), x[vbase + __ldg(G.L.col + e0 + e)], acc);
+    return acc;
+  };
+  cl.sync();  // all CTAs running and initialised before any remote write
+  for (int k = 0; k < a.iters; ++k) {
+    const int cur = k & 1, nxt = cur ^ 1;
+    if (wact) {
+      const double n2 = graph_warp_sum(wq + cur * nvw, G, lane);
+      const float inv = n2 > 0 ? rsqrtf(float(n2)) : 0.f;  // only the direction matters
+      const float s = valid ? spmv(xv + cur * NV) * inv : 0.f;
+      float4 v4;
+      v4.x = __shfl_sync(0xffffffffu, s, 4 * ch);
+      v4.y = __shfl_sync(0xffffffffu, s, 4 * ch + 1);
+      v4.z = __shfl_sync(0xffffffffu, s, 4 * ch + 2);
+      v4.w = __shfl_sync(0xffffffffu, s, 4 * ch + 3);
+      const int off = nxt * NV + vw * 32 + 4 * ch;
+      *reinterpret_cast<float4*>(xr0 + off) = v4;
+      *reinterpret_cast<float4*>(xr1 + off) = v4;
+      const double q = warp_sum(double(s) * double(s));
+      if (lane < kPowCtas) wr[nxt * nvw + vw] = q;
+    }
+    cl.sync();
+  }
+  // Rayleigh quotients u^T L u / u^T u of the final iterate, gathered in CTA 0
+  const int fin = a.iters & 1;
+  if (wact) {
+    const float* x = xv + fin * NV;
+    const float lu = valid ? spmv(x) : 0.f;
+    const double u = valid ? double(x[vw * 32 + lane]) : 0.0;
+    const double num = warp_sum(u * double(lu)), den = warp_sum(u * u);
+    double* r0 = cl.map_shared_rank(rq, 0);
+    if (lane == 0) r0[vw] = num;
+    if (lane == 1) r0[nvw + vw] = den;
+  }
+  cl.sync();
+  if (crank == 0)
+    for (int g = lw; g < a.ngraph; g += nlw) {
+      const PowerGraph& H = a.g[g];
+      const double nm = graph_warp_sum(rq, H, lane), dn = graph_warp_sum(rq + nvw, H, lane);
+      const double last = graph_warp_sum(wq + fin * nvw, H, lane);
+      if (lane == 0) *H.out = (dn > 0 && last > 0) ? nm / dn : 0.0;
     }
 }
 
@@ -603,14 +750,37 @@ cpca_status fista_batch_run(const BatchProblem* P, int n, int J, double eps, boo
     pa.bar = GridBar{w.bar, w.bar + kBarrierCounters, w.err};
     CPCA_CUDA(cudaMemsetAsync(w.bar, 0, sizeof(unsigned int) * (kBarrierCounters + 1), st));
     CPCA_CUDA(cudaMemsetAsync(w.err, 0, sizeof(int), st));
-    // one warp per row, at most one 512-thread block per SM
-    const int grid = std::min(num_sms(), coop_blocks((const void*)power_batch_kernel, 512, 0,
-                                                     (rows + 15) / 16));
-    void* args[] = {&pa};
-    CPCA_PROF("power_iter", st);
-    CPCA_CUDA(cudaLaunchCooperativeKernel((const void*)power_batch_kernel, dim3(grid), dim3(512),
-                                          args, 0, st));
-    CPCA_LAUNCHED();
+    int nvw = 0;
+    for (int g = 0; g < pa.ngraph; ++g) {
+      pa.g[g].w0 = nvw;
+      nvw += (pa.g[g].L.n + 31) / 32;
+    }
+    if (nvw <= kPowMaxWarps) {
+      // one cluster: the iterate in every CTA's shared memory, the rest of
+      // the opt-in shared memory for the CSR entries
+      const size_t fixed = sizeof(double) * 4 * size_t(nvw) + sizeof(float) * 64 * size_t(nvw);
+      const size_t psm = size_t(max_smem_optin());
+      const int ell_cap = int((psm - fixed) / sizeof(int2));
+      static bool pattr = false;
+      if (!pattr) {
+        CPCA_CUDA(cudaFuncSetAttribute((const void*)power_cluster_kernel,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, int(psm)));
+        pattr = true;
+      }
+      const int threads = 32 * ((nvw + kPowCtas - 1) / kPowCtas);
+      CPCA_PROF("power_iter", st);
+      power_cluster_kernel<<<kPowCtas, threads, psm, st>>>(pa, nvw, ell_cap);
+      CPCA_LAUNCHED();
+    } else {
+      // one warp per row, at most one 512-thread block per SM
+      const int grid = std::min(num_sms(), coop_blocks((const void*)power_batch_kernel, 512, 0,
+                                                       (rows + 15) / 16));
+      void* args[] = {&pa};
+      CPCA_PROF("power_iter", st);
+      CPCA_CUDA(cudaLaunchCooperativeKernel((const void*)power_batch_kernel, dim3(grid), dim3(512),
+                                            args, 0, st));
+      CPCA_LAUNCHED();
+    }
   }
   {
     StepArgs sa{};

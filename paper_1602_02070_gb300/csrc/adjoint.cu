@@ -894,6 +894,16 @@ cpca_status reset_barrier(const BwdWs& w, cudaStream_t st) {
 }
 
 cpca_status run_power(PowAdjArgs& pa, const BwdWs& w, int reverse, cudaStream_t st) {
+  const CsrView Ls[2] = {pa.g[0].L, pa.g[1].L};
+  if (power_tape_fits(Ls, 2)) {  // one thread-block cluster
+    PowerTape P[2];
+    for (int g = 0; g < 2; ++g) {
+      const PowGraph& G = pa.g[g];
+      P[g] = PowerTape{G.L, G.stream, G.U, G.nrm2, G.Ub, G.rho, G.rho_bar};
+    }
+    CPCA_PROF(reverse ? "adj_power_rev" : "adj_power_fwd", st);
+    return power_tape_run(P, 2, pa.T, pa.seed, reverse != 0, st);
+  }
   pa.reverse = reverse;
   CPCA_TRY(reset_barrier(w, st));
   const int want = ceil_div(int64_t(pa.rows) * 32, 512);

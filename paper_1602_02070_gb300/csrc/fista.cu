@@ -28,6 +28,7 @@
 // S_{j-1}, Z_j and write S_j, Z_{j+1}: 20 bytes per entry.
 #include <cmath>
 #include <cooperative_groups.h>
+#include <memory>
 #include <map>
 #include <type_traits>
 #include <mutex>
@@ -57,6 +58,11 @@ struct PowerGraph {
   int stream;
   int row0;     // first row in the concatenated row list
   int w0;       // first 32-row block in the warp-padded row list
+  // kept iterates for reverse mode (null in a plain solve)
+  float* U;               // [(T + 1) * n]: u_t at U + t * n
+  double* nrm2;           // [T + 1]: |u_t|^2
+  float* Ub;              // [T * n]: ubar_t at Ub + (t - 1) * n
+  const double* rho_bar;  // d loss / d rho
 };
 struct PowerBatchArgs {
   PowerGraph g[2 * kMaxBatch];
@@ -170,6 +176,71 @@ __device__ __forceinline__ double graph_warp_sum(const double* part, const Power
   return warp_sum(t);
 }
 
+// One thread's row in the one-cluster kernels: its graph, its CSR row and the
+// warp's sliced-ELL block in shared memory (min(longest row of the warp,
+// equal share of the budget) slots; padding entries are (0, 0.0)).
+struct PowRow {
+  const PowerGraph* G;
+  int vw, i, vbase, deg, slots, lane;
+  bool wact, valid;
+  int64_t e0;
+  const int2* el;
+
+  __device__ __forceinline__ void init(const PowerBatchArgs& a, int nvw, int2* ell, int ell_cap,
+                                       int crank) {
+    lane = threadIdx.x & 31;
+    const int lw = threadIdx.x >> 5, nlw = blockDim.x >> 5;
+    vw = lw * kPowCtas + crank;
+    wact = vw < nvw;
+    G = &a.g[wact ? find_graph_warp(a, vw) : 0];
+    i = (vw - G->w0) * 32 + lane;
+    valid = wact && i < G->L.n;
+    vbase = 32 * G->w0;
+    e0 = 0;
+    deg = 0;
+    if (valid) {
+      e0 = G->L.rowptr[i];
+      deg = int(G->L.rowptr[i + 1] - e0);
+    }
+    slots = deg;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) slots = max(slots, __shfl_xor_sync(0xffffffffu, slots, o));
+    const int dcap = ell_cap / (32 * nlw);
+    slots = min(slots, dcap);
+    int2* mine = ell + size_t(lw) * dcap * 32 + lane;
+    for (int e = 0; e < slots; ++e)
+      mine[e * 32] =
+          e < deg ? make_int2(vbase + G->L.col[e0 + e], __float_as_int(G->L.val[e0 + e])) : make_int2(0, 0);
+    el = mine;
+  }
+  // (L x)(i), x in padded row order; CSR order, one FMA per entry
+  __device__ __forceinline__ float spmv(const float* x) const {
+    float acc = 0.f;
+#pragma unroll 4
+    for (int e = 0; e < slots; ++e) {
+      const int2 v = el[e * 32];
+      acc = fmaf(__int_as_float(v.y), x[v.x], acc);
+    }
+    for (int e = slots; e < deg; ++e)
+      acc = fmaf(__ldg(G->L.val + e0 + e), x[vbase + __ldg(G->L.col + e0 + e)], acc);
+    return acc;
+  }
+};
+
+// lane l of a warp sends float4 chunk (l & 7) of the warp's 32 values to
+// CTAs (l >> 3) and (l >> 3) + 4 of the cluster, at float offset off0 there
+__device__ __forceinline__ void allgather32(float v, float* xr0, float* xr1, int off0, int lane) {
+  const int ch = lane & 7;
+  float4 v4;
+  v4.x = __shfl_sync(0xffffffffu, v, 4 * ch);
+  v4.y = __shfl_sync(0xffffffffu, v, 4 * ch + 1);
+  v4.z = __shfl_sync(0xffffffffu, v, 4 * ch + 2);
+  v4.w = __shfl_sync(0xffffffffu, v, 4 * ch + 3);
+  *reinterpret_cast<float4*>(xr0 + off0 + 4 * ch) = v4;
+  *reinterpret_cast<float4*>(xr1 + off0 + 4 * ch) = v4;
+}
+
+// Forward. With G.U set, also keeps u_0..u_T and |u_t|^2 (reverse mode).
 __global__ void __cluster_dims__(kPowCtas, 1, 1) __launch_bounds__(1024)
 power_cluster_kernel(const __grid_constant__ PowerBatchArgs a, int nvw, int ell_cap) {
   namespace cg = cooperative_groups;
@@ -180,30 +251,11 @@ power_cluster_kernel(const __grid_constant__ PowerBatchArgs a, int nvw, int ell_
   double* wq = reinterpret_cast<double*>(smraw);  // [2][nvw]: warp sums of u_k^2
   double* rq = wq + 2 * nvw;                      // [2][nvw]: warp sums of u^T L u, u^T u
   float* xv = reinterpret_cast<float*>(rq + 2 * nvw);  // [2][NV]: the iterate
-  int2* ell = reinterpret_cast<int2*>(xv + 2 * NV);    // [nlw][dcap][32]: (column, value)
-  const int lane = threadIdx.x & 31, lw = threadIdx.x >> 5, nlw = blockDim.x >> 5;
-  const int vw = lw * kPowCtas + crank;  // this warp's padded row block
-  const bool wact = vw < nvw;
-  const PowerGraph& G = a.g[wact ? find_graph_warp(a, vw) : 0];
-  const int i = (vw - G.w0) * 32 + lane;
-  const bool valid = wact && i < G.L.n;
-  const int vbase = 32 * G.w0;
-  int64_t e0 = 0;
-  int deg = 0;
-  if (valid) {
-    e0 = G.L.rowptr[i];
-    deg = int(G.L.rowptr[i + 1] - e0);
-  }
-  // this warp's ELL block: min(longest row, equal share of the budget) slots
-  int slots = deg;
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) slots = max(slots, __shfl_xor_sync(0xffffffffu, slots, o));
-  const int dcap = ell_cap / (32 * nlw);
-  slots = min(slots, dcap);
-  const int2* el = ell + size_t(lw) * dcap * 32 + lane;
-  for (int e = 0; e < slots; ++e)
-    ell[size_t(lw) * dcap * 32 + e * 32 + lane] =
-        e < deg ? make_int2(vbase + G.L.col[e0 + e], __float_as_int(G.L.val[e0 + e])) : make_int2(0, 0);
+  int2* ell = reinterpret_cast<int2*>(xv + 2 * NV);
+  PowRow R;
+  R.init(a, nvw, ell, ell_cap, crank);
+  const PowerGraph& G = *R.G;
+  const int lane = R.lane, lw = threadIdx.x >> 5, nlw = blockDim.x >> 5, vw = R.vw;
   // u_0 and the warp sums of its squares (FP64, before rounding), computed
   // alike in every CTA
   for (int r = threadIdx.x; r < NV; r += blockDim.x) {
@@ -222,38 +274,21 @@ power_cluster_kernel(const __grid_constant__ PowerBatchArgs a, int nvw, int ell_
     q = warp_sum(q);
     if (lane == 0) wq[w] = q;
   }
-  // remote copies: lane l sends float4 chunk (l & 7) of the warp's 32 new
-  // entries to CTAs (l >> 3) and (l >> 3) + 4, and its warp sum to CTA (l & 7)
-  const int ch = lane & 7;
+  if (R.valid && G.U)
+    G.U[R.i] = float(uniform01_at(stream_state0(a.seed, G.stream), uint64_t(R.i) + 1) - 0.5);
   float* xr0 = cl.map_shared_rank(xv, lane >> 3);
   float* xr1 = cl.map_shared_rank(xv, (lane >> 3) + 4);
   double* wr = cl.map_shared_rank(wq, lane & 7);
-  auto spmv = [&](const float* x) {
-    float acc = 0.f;
-#pragma unroll 4
-    for (int e = 0; e < slots; ++e) {
-      const int2 v = el[e * 32];
-      acc = fmaf(__int_as_float(v.y), x[v.x], acc);
-    }
-    for (int e = slots; e < deg; ++e)
-      acc = fmaf(__ldg(G.L.val + e0 + e), x[vbase + __ldg(G.L.col + e0 + e)], acc);
-    return acc;
-  };
   cl.sync();  // all CTAs running and initialised before any remote write
   for (int k = 0; k < a.iters; ++k) {
     const int cur = k & 1, nxt = cur ^ 1;
-    if (wact) {
+    if (R.wact) {
       const double n2 = graph_warp_sum(wq + cur * nvw, G, lane);
+      if (G.nrm2 && vw == G.w0 && lane == 0) G.nrm2[k] = n2;
       const float inv = n2 > 0 ? rsqrtf(float(n2)) : 0.f;  // only the direction matters
-      const float s = valid ? spmv(xv + cur * NV) * inv : 0.f;
-      float4 v4;
-      v4.x = __shfl_sync(0xffffffffu, s, 4 * ch);
-      v4.y = __shfl_sync(0xffffffffu, s, 4 * ch + 1);
-      v4.z = __shfl_sync(0xffffffffu, s, 4 * ch + 2);
-      v4.w = __shfl_sync(0xffffffffu, s, 4 * ch + 3);
-      const int off = nxt * NV + vw * 32 + 4 * ch;
-      *reinterpret_cast<float4*>(xr0 + off) = v4;
-      *reinterpret_cast<float4*>(xr1 + off) = v4;
+      const float s = R.valid ? R.spmv(xv + cur * NV) * inv : 0.f;
+      if (R.valid && G.U) G.U[size_t(k + 1) * G.L.n + R.i] = s;
+      allgather32(s, xr0, xr1, nxt * NV + vw * 32, lane);
       const double q = warp_sum(double(s) * double(s));
       if (lane < kPowCtas) wr[nxt * nvw + vw] = q;
     }
@@ -261,10 +296,10 @@ power_cluster_kernel(const __grid_constant__ PowerBatchArgs a, int nvw, int ell_
   }
   // Rayleigh quotients u^T L u / u^T u of the final iterate, gathered in CTA 0
   const int fin = a.iters & 1;
-  if (wact) {
+  if (R.wact) {
     const float* x = xv + fin * NV;
-    const float lu = valid ? spmv(x) : 0.f;
-    const double u = valid ? double(x[vw * 32 + lane]) : 0.0;
+    const float lu = R.valid ? R.spmv(x) : 0.f;
+    const double u = R.valid ? double(x[vw * 32 + lane]) : 0.0;
     const double num = warp_sum(u * double(lu)), den = warp_sum(u * u);
     double* r0 = cl.map_shared_rank(rq, 0);
     if (lane == 0) r0[vw] = num;
@@ -276,8 +311,84 @@ power_cluster_kernel(const __grid_constant__ PowerBatchArgs a, int nvw, int ell_
       const PowerGraph& H = a.g[g];
       const double nm = graph_warp_sum(rq, H, lane), dn = graph_warp_sum(rq + nvw, H, lane);
       const double last = graph_warp_sum(wq + fin * nvw, H, lane);
-      if (lane == 0) *H.out = (dn > 0 && last > 0) ? nm / dn : 0.0;
+      if (lane == 0) {
+        *H.out = (dn > 0 && last > 0) ? nm / dn : 0.0;
+        if (H.nrm2) H.nrm2[a.iters] = last;
+      }
     }
+}
+
+// Reverse mode of the kept power iterations (rho = u_T^T L u_T / u_T^T u_T,
+// v_t = u_t / |u_t|): vbar_T = 2 rhobar (L v_T - rho v_T), then for
+// t = T..1 with d_t = v_t^T vbar_t
+//   ubar_t = (vbar_t - d_t v_t) / |u_t|,
+//   vbar_{t-1} = L ubar_t = (L vbar_t - d_t L v_t) / |u_t|,
+// where L v_t is the forward's u_{t+1} (t < T). Carrying vbar instead of
+// ubar lets one all-gather and one cluster barrier serve each step: vbar_t
+// and the warp partials of d_t travel together. ubar_t goes to G.Ub for the
+// Laplacian's own derivative.
+__global__ void __cluster_dims__(kPowCtas, 1, 1) __launch_bounds__(1024)
+power_cluster_reverse_kernel(const __grid_constant__ PowerBatchArgs a, int nvw, int ell_cap) {
+  namespace cg = cooperative_groups;
+  cg::cluster_group cl = cg::this_cluster();
+  const int crank = int(cl.block_rank());
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const int NV = 32 * nvw;
+  double* dq = reinterpret_cast<double*>(smraw);       // [2][nvw]: warp sums of v_t vbar_t
+  float* xv = reinterpret_cast<float*>(dq + 4 * nvw);  // [2][NV]: vbar_t
+  int2* ell = reinterpret_cast<int2*>(xv + 2 * NV);
+  PowRow R;
+  R.init(a, nvw, ell, ell_cap, crank);
+  const PowerGraph& G = *R.G;
+  const int lane = R.lane, vw = R.vw, T = a.iters, n = G.L.n;
+  // u_T (from the tape) into the buffer that vbar_{T-1} takes later
+  float* ut = xv + ((T + 1) & 1) * NV;
+  for (int r = threadIdx.x; r < NV; r += blockDim.x) {
+    const PowerGraph& H = a.g[find_graph_warp(a, r >> 5)];
+    const int j = r - 32 * H.w0;
+    ut[r] = j < H.L.n ? H.U[size_t(T) * H.L.n + j] : 0.f;
+  }
+  __syncthreads();
+  float* xr0 = cl.map_shared_rank(xv, lane >> 3);
+  float* xr1 = cl.map_shared_rank(xv, (lane >> 3) + 4);
+  double* wr = cl.map_shared_rank(dq, lane & 7);
+  auto inv_norm = [&](int t) {
+    const double n2 = G.nrm2[t];
+    return n2 > 0 ? 1.0 / sqrt(n2) : 0.0;
+  };
+  double lvt = 0.0;  // (L v_t)(i) for t = T
+  cl.sync();  // all CTAs running before any remote write
+  if (R.wact) {
+    const double invT = inv_norm(T);
+    const double lu = R.valid ? double(R.spmv(ut)) : 0.0;
+    const double vi = R.valid ? double(ut[vw * 32 + lane]) * invT : 0.0;
+    lvt = lu * invT;
+    const float vb = R.valid ? float(2.0 * (*G.rho_bar) * (lvt - (*G.out) * vi)) : 0.f;
+    allgather32(vb, xr0, xr1, (T & 1) * NV + vw * 32, lane);
+    const double q = warp_sum(vi * double(vb));
+    if (lane < kPowCtas) wr[(T & 1) * nvw + vw] = q;
+  }
+  cl.sync();
+  for (int t = T; t >= 1; --t) {
+    const int cur = t & 1, nxt = cur ^ 1;
+    if (R.wact) {
+      const double d = graph_warp_sum(dq + cur * nvw, G, lane);
+      const double inv = inv_norm(t);
+      const double vb = R.valid ? double(xv[cur * NV + vw * 32 + lane]) : 0.0;
+      const double vt = R.valid ? double(G.U[size_t(t) * n + R.i]) * inv : 0.0;
+      if (R.valid) G.Ub[size_t(t - 1) * n + R.i] = float((vb - vt * d) * inv);
+      if (t > 1) {
+        const double lvb = R.valid ? double(R.spmv(xv + cur * NV)) : 0.0;
+        const double lv = t == T ? lvt : (R.valid ? double(G.U[size_t(t + 1) * n + R.i]) : 0.0);
+        const float vbm = R.valid ? float((lvb - d * lv) * inv) : 0.f;
+        const double vm = R.valid ? double(G.U[size_t(t - 1) * n + R.i]) * inv_norm(t - 1) : 0.0;
+        allgather32(vbm, xr0, xr1, nxt * NV + vw * 32, lane);
+        const double q = warp_sum(vm * double(vbm));
+        if (lane < kPowCtas) wr[nxt * nvw + vw] = q;
+      }
+    }
+    if (t > 1) cl.sync();
+  }
 }
 
 // lambda = 1/beta', beta' = 2 gamma_c |Lc|_2 + 2 gamma_r |Lr|_2 (or the given
@@ -718,6 +829,65 @@ static cpca_status ensure_mu_table() {
   return CPCA_OK;
 }
 
+// The one-cluster power kernels when the warp-padded rows fit (sets *done);
+// the iterate and the warp partials take a fixed part of the opt-in shared
+// memory, the CSR entries the rest.
+static cpca_status power_cluster_launch(PowerBatchArgs& pa, bool reverse, cudaStream_t st, bool* done) {
+  int nvw = 0;
+  for (int g = 0; g < pa.ngraph; ++g) {
+    pa.g[g].w0 = nvw;
+    nvw += (pa.g[g].L.n + 31) / 32;
+  }
+  *done = false;
+  if (nvw > kPowMaxWarps) return CPCA_OK;
+  const size_t fixed = sizeof(double) * 4 * size_t(nvw) + sizeof(float) * 64 * size_t(nvw);
+  const size_t psm = size_t(max_smem_optin());
+  const int ell_cap = int((psm - fixed) / sizeof(int2));
+  const void* k = reverse ? (const void*)power_cluster_reverse_kernel : (const void*)power_cluster_kernel;
+  static bool attr[2] = {false, false};
+  if (!attr[reverse]) {
+    CPCA_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(psm)));
+    attr[reverse] = true;
+  }
+  const int threads = 32 * ((nvw + kPowCtas - 1) / kPowCtas);
+  if (reverse)
+    power_cluster_reverse_kernel<<<kPowCtas, threads, psm, st>>>(pa, nvw, ell_cap);
+  else
+    power_cluster_kernel<<<kPowCtas, threads, psm, st>>>(pa, nvw, ell_cap);
+  CPCA_LAUNCHED();
+  *done = true;
+  return CPCA_OK;
+}
+
+bool power_tape_fits(const CsrView* L, int ng) {
+  int nvw = 0;
+  for (int g = 0; g < ng; ++g) nvw += (L[g].n + 31) / 32;
+  return nvw <= kPowMaxWarps;
+}
+
+cpca_status power_tape_run(const PowerTape* P, int ng, int T, uint64_t seed, bool reverse,
+                           cudaStream_t st) {
+  CPCA_CHECK_ARG(ng >= 1 && ng <= 2 * kMaxBatch, "power iterations: %d graphs", ng);
+  std::unique_ptr<PowerBatchArgs> pa(new PowerBatchArgs{});
+  pa->ngraph = ng;
+  pa->iters = T;
+  pa->seed = seed;
+  for (int g = 0; g < ng; ++g) {
+    PowerGraph& G = pa->g[g];
+    G.L = P[g].L;
+    G.stream = P[g].stream;
+    G.out = P[g].rho;
+    G.U = P[g].U;
+    G.nrm2 = P[g].nrm2;
+    G.Ub = P[g].Ub;
+    G.rho_bar = P[g].rho_bar;
+  }
+  bool done = false;
+  CPCA_TRY(power_cluster_launch(*pa, reverse, st, &done));
+  CPCA_CHECK_ARG(done, "power iterations: rows exceed one cluster");
+  return CPCA_OK;
+}
+
 cpca_status fista_batch_run(const BatchProblem* P, int n, int J, double eps, bool want_last,
                             int power_iters, uint64_t power_seed, int blocks, const BatchWs& w,
                             cudaStream_t st) {
@@ -750,33 +920,14 @@ cpca_status fista_batch_run(const BatchProblem* P, int n, int J, double eps, boo
     pa.bar = GridBar{w.bar, w.bar + kBarrierCounters, w.err};
     CPCA_CUDA(cudaMemsetAsync(w.bar, 0, sizeof(unsigned int) * (kBarrierCounters + 1), st));
     CPCA_CUDA(cudaMemsetAsync(w.err, 0, sizeof(int), st));
-    int nvw = 0;
-    for (int g = 0; g < pa.ngraph; ++g) {
-      pa.g[g].w0 = nvw;
-      nvw += (pa.g[g].L.n + 31) / 32;
-    }
-    if (nvw <= kPowMaxWarps) {
-      // one cluster: the iterate in every CTA's shared memory, the rest of
-      // the opt-in shared memory for the CSR entries
-      const size_t fixed = sizeof(double) * 4 * size_t(nvw) + sizeof(float) * 64 * size_t(nvw);
-      const size_t psm = size_t(max_smem_optin());
-      const int ell_cap = int((psm - fixed) / sizeof(int2));
-      static bool pattr = false;
-      if (!pattr) {
-        CPCA_CUDA(cudaFuncSetAttribute((const void*)power_cluster_kernel,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, int(psm)));
-        pattr = true;
-      }
-      const int threads = 32 * ((nvw + kPowCtas - 1) / kPowCtas);
-      CPCA_PROF("power_iter", st);
-      power_cluster_kernel<<<kPowCtas, threads, psm, st>>>(pa, nvw, ell_cap);
-      CPCA_LAUNCHED();
-    } else {
+    bool done = false;
+    CPCA_PROF("power_iter", st);
+    CPCA_TRY(power_cluster_launch(pa, false, st, &done));
+    if (!done) {
       // one warp per row, at most one 512-thread block per SM
       const int grid = std::min(num_sms(), coop_blocks((const void*)power_batch_kernel, 512, 0,
                                                        (rows + 15) / 16));
       void* args[] = {&pa};
-      CPCA_PROF("power_iter", st);
       CPCA_CUDA(cudaLaunchCooperativeKernel((const void*)power_batch_kernel, dim3(grid), dim3(512),
                                             args, 0, st));
       CPCA_LAUNCHED();

@@ -203,6 +203,25 @@ cpca_status fista_objective(const float* Yt, int64_t ldy, int rr, int rc, const 
                             const CsrView& Lc, const float* X, int64_t ldx, double gr, double gc,
                             double* part, double* out, cudaStream_t st);
 cpca_status check_csr(const cpca_csr* L, int n, const char* name);
+
+// Power iterations on a few Laplacians with every iterate kept (the solve's
+// step size, Sec. IV-B, taken for reverse mode): u_0 = SplitMix64 uniform
+// - 1/2 on stream `stream`, u_{t+1} = L u_t / |u_t|, rho = Rayleigh quotient
+// of u_T. Forward writes U, nrm2 and *rho; reverse reads them with *rho_bar
+// and writes Ub (ubar_t). One thread-block cluster; power_tape_fits says
+// whether the rows fit.
+struct PowerTape {
+  CsrView L;
+  int stream;
+  float* U;               // [(T + 1) * n]
+  double* nrm2;           // [T + 1]
+  float* Ub;              // [T * n]
+  double* rho;
+  const double* rho_bar;
+};
+bool power_tape_fits(const CsrView* L, int ng);
+cpca_status power_tape_run(const PowerTape* P, int ng, int T, uint64_t seed, bool reverse,
+                           cudaStream_t st);
 int coop_blocks(const void* kernel, int threads, size_t smem, int want);
 // dloss/dL (FP64 on the CSR pattern) -> dloss/dw per entry (adjoint.cu);
 // deg and dD are scratch of L.n doubles each.

@@ -95,6 +95,8 @@ struct TrajArgs {
   float* S;              // own tiles: S_{j-1} in, S_j out (ld ldz)
   float* Zs;             // trajectory slots of Z_j (row-major, slot stride rr * ldz)
   float* ZTs;            // column-major copies (slot stride rc * ldzt)
+  uint8_t* Ms;           // step j's prox codes in the slot of Z_j (slot stride rr * ldz);
+                         // bit 0: |V_j - Y~| > lambda, bit 1: V_j - Y~ < 0. Null: not kept
   int jbase, nslot;      // Z_j lives in slot (j - jbase) % nslot
   int ja, jb;            // forward: iterations ja..jb; reverse: jb down to ja
   int J;
@@ -126,6 +128,9 @@ __device__ __forceinline__ float* zslot(const TrajArgs& a, int j) {
 __device__ __forceinline__ float* ztslot(const TrajArgs& a, int j) {
   return a.ZTs + size_t(slot_of(a, j)) * size_t(a.rc) * size_t(a.ldzt);
 }
+__device__ __forceinline__ uint8_t* mslot(const TrajArgs& a, int j) {
+  return a.Ms + size_t(slot_of(a, j)) * size_t(a.rr) * size_t(a.ldz);
+}
 
 __device__ __forceinline__ void tile_of(const TrajArgs& a, int tile, int& i0, int& j0, int& ni, int& nj) {
   i0 = (tile / a.ntj) * TB;
@@ -154,6 +159,9 @@ __device__ __forceinline__ void st4(float* p, float4 v, bool vec, int n) {
   if (n > 3) p[3] = v.w;
 }
 __device__ __forceinline__ float& cmp(float4& v, int t) {
+  return t == 0 ? v.x : t == 1 ? v.y : t == 2 ? v.z : v.w;
+}
+__device__ __forceinline__ float cmp(const float4& v, int t) {
   return t == 0 ? v.x : t == 1 ? v.y : t == 2 ? v.z : v.w;
 }
 __device__ __forceinline__ float dot4(float4 a, float4 b) {
@@ -223,6 +231,7 @@ traj_forward_kernel(const __grid_constant__ TrajArgs a) {
         float4 y4 = ld4(a.Yt + i * a.ldy + jj, a.yvec, nv);
         float4 s4 = RESIDENT ? rs : *reinterpret_cast<const float4*>(a.S + i * a.ldz + jj);
         float4 sv4 = make_float4(0.f, 0.f, 0.f, 0.f);
+        uint32_t code = 0;
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
           if (q < nv) {
@@ -233,8 +242,10 @@ traj_forward_kernel(const __grid_constant__ TrajArgs a) {
             const float sv = y + copysignf(fmaxf(fabsf(dl) - lam, 0.f), dl);
             cmp(sv4, q) = sv;
             cmp(zn4, q) = fmaf(mu, sv - sp, sv);
+            code |= uint32_t((fabsf(dl) - lam > 0.f ? 1 : 0) | (dl < 0.f ? 2 : 0)) << (8 * q);
           }
         }
+        if (a.Ms) *reinterpret_cast<uint32_t*>(mslot(a, j) + i * a.ldz + jj) = code;
         if (RESIDENT) rs = sv4;
         else *reinterpret_cast<float4*>(a.S + i * a.ldz + jj) = sv4;
         *reinterpret_cast<float4*>(Zout + i * a.ldz + jj) = zn4;
@@ -324,15 +335,23 @@ __device__ __forceinline__ void list_partials(const Off* off, int deg, int64_t f
   }
 }
 
-// Reverse iterations jb down to ja over the trajectory slots. RESIDENT: one
-// tile per block for the whole launch (lists staged once, the staged
-// entries' dL partial sums accumulated in shared memory in FP32 and added
-// to the FP64 partial buffers at the end); otherwise blocks stream over the
-// tiles and add partial sums to the FP64 buffers directly. Two phases per
-// iteration with one grid barrier between them: (1) gathers of Z_j's
-// neighbours, the mask, Vb = M o Sb, dY~ and the scalar partials, Vb
-// published in both layouts, the dL partial sums (against Z_j); (2) gathers
-// of Vb's neighbours, Zb, and the momentum carries.
+// Reverse iterations jb down to ja over the trajectory slots, one grid
+// barrier per iteration. Entering iteration j, Vb_j = M_j o Sb_j is
+// published in both layouts (M_j: step j's prox mask, kept by the forward).
+// Iteration j gathers Vb_j's neighbours for Zb_j = Vb_j - lambda (2 gr Lr Vb_j
+// + 2 gc Vb_j Lc), carries it to Sb_{j-1} = (1 + mu_{j-1}) Zb_j + A2 and
+// A2 = -mu_{j-1} Zb_j, and forms and publishes Vb_{j-1} (dY~ += Sb - Vb)
+// for the next iteration; the launch's last iteration leaves Sb_{j-1} in Sb
+// instead (the next launch's prologue applies M_{j-1}, which the earlier
+// segment's forward provides). The dL partial sums pair Vb_j with Z_j's
+// neighbours. The scalar derivatives use the symmetry of Lr and Lc:
+// <Vb, Lr Z> = <Lr Vb, Z> and <Vb, Z Lc> = <Vb Lc, Z>, so they come from the
+// same gathers:
+//   dgamma_r = -2 lambda <Lr Vb, Z>, dgamma_c = -2 lambda <Vb Lc, Z>,
+//   dlambda = sum -sgn(V - Y~) Vb - (2 gr <Lr Vb, Z> + 2 gc <Vb Lc, Z>).
+// RESIDENT: one tile per block for the whole launch (lists staged once, the
+// staged entries' dL partial sums kept in shared memory in FP32 and added to
+// the FP64 partial buffers at the end); otherwise blocks stream over tiles.
 template <bool RESIDENT>
 __global__ void __launch_bounds__(256, RESIDENT ? 5 : 4)
 traj_reverse_kernel(const __grid_constant__ TrajArgs a) {
@@ -355,122 +374,118 @@ traj_reverse_kernel(const __grid_constant__ TrajArgs a) {
       sm.pc[e / kTileNbr][e % kTileNbr] = 0.f;
     }
   }
-  double s_lam = 0.0, s_gr = 0.0, s_gc = 0.0;
+  double s_sgn = 0.0, s_r = 0.0, s_c = 0.0;  // sum -sgn Vb, <Lr Vb, Z>, <Vb Lc, Z>
+  // transposed publish of the tile's new values through sm.tl
+  auto publish_t = [&](const float4& v4, float* VT, int i0, int j0, int ni, int nj) {
+    sm.tl[rl][cq] = v4.x;
+    sm.tl[rl][cq + 1] = v4.y;
+    sm.tl[rl][cq + 2] = v4.z;
+    sm.tl[rl][cq + 3] = v4.w;
+    __syncthreads();
+    if (rl < nj && cq < ni)
+      *reinterpret_cast<float4*>(VT + int64_t(j0 + rl) * a.ldzt + i0 + cq) =
+          make_float4(sm.tl[cq][rl], sm.tl[cq + 1][rl], sm.tl[cq + 2][rl], sm.tl[cq + 3][rl]);
+  };
+  // apply a prox code word to 4 entries of Sb: Vb, dY~ += Sb - Vb, the sign sum
+  auto apply_mask = [&](const float4& sb4, uint32_t code, float4& dy4, int nv) {
+    float4 vb4 = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+      if (q < nv) {
+        const uint32_t c = (code >> (8 * q)) & 3u;
+        const float sb = cmp(sb4, q);
+        const float vb = (c & 1u) ? sb : 0.f;
+        cmp(dy4, q) += sb - vb;
+        if (vb != 0.f) s_sgn += (c & 2u) ? double(vb) : -double(vb);
+        cmp(vb4, q) = vb;
+      }
+    return vb4;
+  };
+  // prologue: Vb_jb = M_jb o Sb
+  {
+    const int par = a.jb & 1;
+    const uint8_t* Mj = mslot(a, a.jb);
+    for (int tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x) {
+      int i0, j0, ni, nj;
+      tile_of(a, tile, i0, j0, ni, nj);
+      float4 vb4 = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (rl < ni && cq < nj) {
+        const int64_t i = i0 + rl, jj = j0 + cq, l = i * a.ldz + jj;
+        const int nv = nj - cq;
+        const float4 sb4 = *reinterpret_cast<const float4*>(a.Sb + l);
+        const uint32_t code = *reinterpret_cast<const uint32_t*>(Mj + l);
+        float4 dy4 = ld4(a.dY + i * a.lddy + jj, a.dyvec, nv);
+        vb4 = apply_mask(sb4, code, dy4, nv);
+        st4(a.dY + i * a.lddy + jj, dy4, a.dyvec, nv);
+        *reinterpret_cast<float4*>(a.Vb[par] + l) = vb4;
+      }
+      publish_t(vb4, a.VbT[par], i0, j0, ni, nj);
+      __syncthreads();
+    }
+  }
+  if (!grid_sync(a.bar)) return;
   for (int j = a.jb; j >= a.ja; --j) {
     const int par = j & 1;
+    const float* V = a.Vb[par];
+    const float* VT = a.VbT[par];
     const float* Zin = zslot(a, j);
     const float* ZTin = ztslot(a, j);
-    // phase 1
+    const float mup = j >= 2 ? a.mu[j - 1] : 0.f;
+    const bool form = j >= 2 && j > a.ja;  // Vb_{j-1} formed here
+    const uint8_t* Mn = form ? mslot(a, j - 1) : nullptr;
     for (int tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x) {
       int i0, j0, ni, nj;
       tile_of(a, tile, i0, j0, ni, nj);
       const int ti = i0 / TB, tj = j0 / TB;
-      if (RESIDENT) __syncthreads();  // sm.ac / sm.tl of the previous phase are consumed
+      if (RESIDENT) __syncthreads();  // sm.ac / sm.tl of the previous iteration are consumed
       else stage_nbr(sm.nb, a.Lr, a.Lc, int(a.ldzt), int(a.ldz), i0, j0, ni, nj);
       {
-        const float4 o = nbr_sum_v4<Off, RESIDENT ? 4 : 8>(sm.nb.coff[rl], sm.nb.cval[rl], sm.nb.cdeg[rl], sm.nb.cf0[rl],
-                                    rl < nj && cq < ni, ZTin, i0 + cq, a.Lc, a.ldzt);
+        const float4 o = nbr_sum_v4<Off, RESIDENT ? 4 : 8>(sm.nb.coff[rl], sm.nb.cval[rl], sm.nb.cdeg[rl],
+                                                           sm.nb.cf0[rl], rl < nj && cq < ni, VT, i0 + cq,
+                                                           a.Lc, a.ldzt);
         sm.ac[cq][rl] = o.x;
         sm.ac[cq + 1][rl] = o.y;
         sm.ac[cq + 2][rl] = o.z;
         sm.ac[cq + 3][rl] = o.w;
       }
       const bool own = rl < ni && cq < nj;
-      float4 ar = nbr_sum_v4<Off, RESIDENT ? 4 : 8>(sm.nb.roff[rl], sm.nb.rval[rl], sm.nb.rdeg[rl], sm.nb.rf0[rl], own, Zin, j0 + cq,
-                             a.Lr, a.ldz);
+      const float4 ar = nbr_sum_v4<Off, RESIDENT ? 4 : 8>(sm.nb.roff[rl], sm.nb.rval[rl], sm.nb.rdeg[rl],
+                                                          sm.nb.rf0[rl], own, V, j0 + cq, a.Lr, a.ldz);
       __syncthreads();
-      float4 vb4 = make_float4(0.f, 0.f, 0.f, 0.f);
+      float4 vb4 = make_float4(0.f, 0.f, 0.f, 0.f), vn4 = make_float4(0.f, 0.f, 0.f, 0.f);
       if (own) {
-        const int64_t i = i0 + rl, jj = j0 + cq;
+        const int64_t i = i0 + rl, jj = j0 + cq, l = i * a.ldz + jj;
         const int nv = nj - cq;
-        float4 z4 = __ldcg(reinterpret_cast<const float4*>(Zin + i * a.ldz + jj));
-        float4 y4 = ld4(a.Yt + i * a.ldy + jj, a.yvec, nv);
-        float4 sb4 = *reinterpret_cast<const float4*>(a.Sb + i * a.ldz + jj);
-        float4 dy4 = ld4(a.dY + i * a.lddy + jj, a.dyvec, nv);
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          if (q < nv) {
-            const float gr = fmaf(a.two_gr, cmp(ar, q), a.two_gc * sm.ac[rl][cq + q]);
-            const float v = fmaf(-lam, gr, cmp(z4, q));
-            const float dl = v - cmp(y4, q);
-            const float sb = cmp(sb4, q);
-            const float vb = (fabsf(dl) - lam) > 0.f ? sb : 0.f;
-            cmp(dy4, q) += sb - vb;
-            if (vb != 0.f) {
-              s_lam += -double(copysignf(1.f, dl)) * vb - double(vb) * double(gr);
-              s_gr += -2.0 * lamd * double(vb) * double(cmp(ar, q));
-              s_gc += -2.0 * lamd * double(vb) * double(sm.ac[rl][cq + q]);
-            }
-            cmp(vb4, q) = vb;
-          }
-        }
-        st4(a.dY + i * a.lddy + jj, dy4, a.dyvec, nv);
-        *reinterpret_cast<float4*>(a.Vb[par] + i * a.ldz + jj) = vb4;
-      }
-      sm.tl[rl][cq] = vb4.x;
-      sm.tl[rl][cq + 1] = vb4.y;
-      sm.tl[rl][cq + 2] = vb4.z;
-      sm.tl[rl][cq + 3] = vb4.w;
-      __syncthreads();
-      // column rl of the tile, rows cq..cq+3: transposed publish
-      const bool ocol = rl < nj && cq < ni;
-      const float4 vc4 = make_float4(sm.tl[cq][rl], sm.tl[cq + 1][rl], sm.tl[cq + 2][rl], sm.tl[cq + 3][rl]);
-      if (ocol) *reinterpret_cast<float4*>(a.VbT[par] + int64_t(j0 + rl) * a.ldzt + i0 + cq) = vc4;
-      // dLr(a, b) += scale sum_c Vb(a, c) Z(b, c) over the tile's columns;
-      // dLc(a, b) += scale sum_r Z(r, a) Vb(r, b) over its rows (column b's
-      // list (b, a) lands on the transposed entry (a, b))
-      if (a.gamma_r != 0.0)
-        list_partials<RESIDENT>(sm.nb.roff[rl], sm.nb.rdeg[rl], sm.nb.rf0[rl], own, Zin, j0 + cq, a.Lr, a.ldz,
-                                vb4, sm.pr[rl], sr, a.Pr + int64_t(tj) * nnz_r, nullptr, lane);
-      if (a.gamma_c != 0.0)
-        list_partials<RESIDENT>(sm.nb.coff[rl], sm.nb.cdeg[rl], sm.nb.cf0[rl], ocol, ZTin, i0 + cq, a.Lc,
-                                a.ldzt, vc4, sm.pc[rl], sc, a.Pc + int64_t(ti) * nnz_c, a.tmap_c, lane);
-      if (!RESIDENT) __syncthreads();
-    }
-    if (!grid_sync(a.bar)) return;
-    // phase 2: Zb = Vb - lambda (2 gr Lr Vb + 2 gc Vb Lc), carries to S_{j-1}, S_{j-2}
-    const float* V = a.Vb[par];
-    const float* VT = a.VbT[par];
-    const float mup = j >= 2 ? a.mu[j - 1] : 0.f;
-    for (int tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x) {
-      int i0, j0, ni, nj;
-      tile_of(a, tile, i0, j0, ni, nj);
-      if (RESIDENT) __syncthreads();
-      else stage_nbr(sm.nb, a.Lr, a.Lc, int(a.ldzt), int(a.ldz), i0, j0, ni, nj);
-      {
-        const float4 o = nbr_sum_v4<Off, RESIDENT ? 4 : 8>(sm.nb.coff[rl], sm.nb.cval[rl], sm.nb.cdeg[rl], sm.nb.cf0[rl],
-                                    rl < nj && cq < ni, VT, i0 + cq, a.Lc, a.ldzt);
-        sm.ac[cq][rl] = o.x;
-        sm.ac[cq + 1][rl] = o.y;
-        sm.ac[cq + 2][rl] = o.z;
-        sm.ac[cq + 3][rl] = o.w;
-      }
-      const bool own = rl < ni && cq < nj;
-      float4 ar = nbr_sum_v4<Off, RESIDENT ? 4 : 8>(sm.nb.roff[rl], sm.nb.rval[rl], sm.nb.rdeg[rl], sm.nb.rf0[rl], own, V, j0 + cq,
-                             a.Lr, a.ldz);
-      __syncthreads();
-      if (own) {
-        const int64_t i = i0 + rl, jj = j0 + cq;
-        const int nv = nj - cq;
-        const int64_t l = i * a.ldz + jj;
-        float4 vb4 = __ldcg(reinterpret_cast<const float4*>(V + l));
-        float4 a24 = *reinterpret_cast<const float4*>(a.A2 + l);
+        vb4 = __ldcg(reinterpret_cast<const float4*>(V + l));
+        const float4 z4 = __ldcg(reinterpret_cast<const float4*>(Zin + l));
+        const float4 a24 = *reinterpret_cast<const float4*>(a.A2 + l);
         float4 zb4 = make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
         for (int q = 0; q < 4; ++q)
           if (q < nv) {
-            const float g = fmaf(a.two_gr, cmp(ar, q), a.two_gc * sm.ac[rl][cq + q]);
-            cmp(zb4, q) = fmaf(-lam, g, cmp(vb4, q));
+            const float arq = cmp(ar, q), acq = sm.ac[rl][cq + q];
+            cmp(zb4, q) = fmaf(-lam, fmaf(a.two_gr, arq, a.two_gc * acq), cmp(vb4, q));
+            s_r += double(arq) * double(cmp(z4, q));
+            s_c += double(acq) * double(cmp(z4, q));
           }
         if (j >= 2) {
-          float4 sbn, a2n;
+          float4 sbn = make_float4(0.f, 0.f, 0.f, 0.f), a2n = make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
-          for (int q = 0; q < 4; ++q) {
-            cmp(sbn, q) = fmaf(1.f + mup, cmp(zb4, q), cmp(a24, q));
-            cmp(a2n, q) = -mup * cmp(zb4, q);
-          }
-          *reinterpret_cast<float4*>(a.Sb + l) = sbn;
+          for (int q = 0; q < 4; ++q)
+            if (q < nv) {
+              cmp(sbn, q) = fmaf(1.f + mup, cmp(zb4, q), cmp(a24, q));
+              cmp(a2n, q) = -mup * cmp(zb4, q);
+            }
           *reinterpret_cast<float4*>(a.A2 + l) = a2n;
+          if (form) {
+            const uint32_t code = *reinterpret_cast<const uint32_t*>(Mn + l);
+            float4 dy4 = ld4(a.dY + i * a.lddy + jj, a.dyvec, nv);
+            vn4 = apply_mask(sbn, code, dy4, nv);
+            st4(a.dY + i * a.lddy + jj, dy4, a.dyvec, nv);
+            *reinterpret_cast<float4*>(a.Vb[par ^ 1] + l) = vn4;
+          } else {
+            *reinterpret_cast<float4*>(a.Sb + l) = sbn;
+          }
         } else {
           float4 dy4 = ld4(a.dY + i * a.lddy + jj, a.dyvec, nv);
 #pragma unroll
@@ -480,8 +495,22 @@ traj_reverse_kernel(const __grid_constant__ TrajArgs a) {
           *reinterpret_cast<float4*>(a.A2 + l) = make_float4(0.f, 0.f, 0.f, 0.f);
         }
       }
+      // dLr(a, b) += scale sum_c Vb(a, c) Z(b, c) over the tile's columns;
+      // dLc(a, b) += scale sum_r Z(r, a) Vb(r, b) over its rows (column b's
+      // list (b, a) lands on the transposed entry (a, b))
+      const bool ocol = rl < nj && cq < ni;
+      const float4 vc4 = ocol ? __ldcg(reinterpret_cast<const float4*>(VT + int64_t(j0 + rl) * a.ldzt + i0 + cq))
+                              : make_float4(0.f, 0.f, 0.f, 0.f);
+      if (a.gamma_r != 0.0)
+        list_partials<RESIDENT>(sm.nb.roff[rl], sm.nb.rdeg[rl], sm.nb.rf0[rl], own, Zin, j0 + cq, a.Lr, a.ldz,
+                                vb4, sm.pr[rl], sr, a.Pr + int64_t(tj) * nnz_r, nullptr, lane);
+      if (a.gamma_c != 0.0)
+        list_partials<RESIDENT>(sm.nb.coff[rl], sm.nb.cdeg[rl], sm.nb.cf0[rl], ocol, ZTin, i0 + cq, a.Lc,
+                                a.ldzt, vc4, sm.pc[rl], sc, a.Pc + int64_t(ti) * nnz_c, a.tmap_c, lane);
+      if (form) publish_t(vn4, a.VbT[par ^ 1], i0, j0, ni, nj);
       if (!RESIDENT) __syncthreads();
     }
+    if (!grid_sync(a.bar)) return;
   }
   if (RESIDENT) {
     __syncthreads();
@@ -502,13 +531,13 @@ traj_reverse_kernel(const __grid_constant__ TrajArgs a) {
       }
     }
   }
-  s_lam = block_sum(s_lam, red);
-  s_gr = block_sum(s_gr, red);
-  s_gc = block_sum(s_gc, red);
+  s_sgn = block_sum(s_sgn, red);
+  s_r = block_sum(s_r, red);
+  s_c = block_sum(s_c, red);
   if (threadIdx.x == 0) {
-    atomicAdd(a.scal_bar + 0, s_lam);
-    atomicAdd(a.scal_bar + 1, s_gr);
-    atomicAdd(a.scal_bar + 2, s_gc);
+    atomicAdd(a.scal_bar + 0, s_sgn - (2.0 * a.gamma_r * s_r + 2.0 * a.gamma_c * s_c));
+    atomicAdd(a.scal_bar + 1, -2.0 * lamd * s_r);
+    atomicAdd(a.scal_bar + 2, -2.0 * lamd * s_c);
   }
 }
 
@@ -829,6 +858,7 @@ struct BwdWs {
   double* nb;        // [2]: dn_r, dn_c
   float *S, *Sb, *A2, *Vb[2], *VbT[2];
   float *Zs, *ZTs;
+  uint8_t* Ms;
   float *ckS, *ckZ;
   double *Pr, *Pc;
   double *dLr, *dLc;
@@ -864,6 +894,7 @@ BwdWs bwd_layout(void* ws, int rr, int rc, int J, int ck, int T, int64_t nnz_r, 
   }
   w.Zs = c.take<float>(mn * nslot);
   w.ZTs = c.take<float>(mnt * nslot);
+  w.Ms = c.take<uint8_t>(mn * nslot);
   w.ckS = c.take<float>(mn * std::max(nseg - 1, 1));
   w.ckZ = c.take<float>(mn * std::max(nseg - 1, 1));
   w.Pr = c.take<double>(size_t(ceil_div(rc, TB)) * std::max<int64_t>(nnz_r, 1));
@@ -1071,6 +1102,7 @@ cpca_status frpcag_adjoint(const AdjCall& c, AdjMode mode) {
   a.S = w.S;
   a.Zs = w.Zs;
   a.ZTs = w.ZTs;
+  a.Ms = nullptr;
   a.J = J;
   a.ckS = w.ckS;
   a.ckZ = w.ckZ;
@@ -1144,6 +1176,7 @@ cpca_status frpcag_adjoint(const AdjCall& c, AdjMode mode) {
       a.ja = 1;
       a.jb = jlast;
       a.ck = ck;
+      a.Ms = nullptr;
       CPCA_TRY(launch_fwd());
       const size_t off = size_t(nseg - 2) * mn;
       seed_kernel<<<gs, 256, 0, st>>>(w.ckZ + off, ldz, w.ckS + off, ldz, rr, rc, ldz, ldzt, w.Zs, w.ZTs, w.S);
@@ -1154,6 +1187,7 @@ cpca_status frpcag_adjoint(const AdjCall& c, AdjMode mode) {
     a.ja = jlast + 1;
     a.jb = J;
     a.ck = 0;
+    a.Ms = w.Ms;  // prox codes of the last segment, for a resumed reverse
     CPCA_TRY(launch_fwd());
     CPCA_CUDA(cudaMemcpy2DAsync(c.X, sizeof(float) * c.ldx, w.S, sizeof(float) * ldz, sizeof(float) * rc, rr,
                                 cudaMemcpyDeviceToDevice, st));
@@ -1166,6 +1200,7 @@ cpca_status frpcag_adjoint(const AdjCall& c, AdjMode mode) {
     a.ja = 1;
     a.jb = (nseg - 1) * ck;
     a.ck = ck;
+    a.Ms = nullptr;
     CPCA_TRY(launch_fwd());
   }
   if (mode != kForwardTape) {
@@ -1180,6 +1215,7 @@ cpca_status frpcag_adjoint(const AdjCall& c, AdjMode mode) {
     CPCA_CUDA(cudaMemset2DAsync(c.dYt, sizeof(float) * c.lddyt, 0, sizeof(float) * rc, rr, st));
     CPCA_CUDA(cudaMemsetAsync(w.Pr, 0, sizeof(double) * a.ntj * std::max<int64_t>(c.Lr->nnz, 1), st));
     CPCA_CUDA(cudaMemsetAsync(w.Pc, 0, sizeof(double) * ceil_div(rr, TB) * std::max<int64_t>(c.Lc->nnz, 1), st));
+    a.Ms = w.Ms;  // every reverse launch reads the prox codes of its segment
     for (int m = nseg - 1; m >= 0; --m) {
       const int j0 = m * ck, j1 = std::min(J, j0 + ck);
       a.jbase = j0 + 1;
@@ -1197,9 +1233,10 @@ cpca_status frpcag_adjoint(const AdjCall& c, AdjMode mode) {
         }
         CPCA_LAUNCHED();
       }
-      if (!have && j1 - 1 >= j0 + 1) {
+      if (!have) {
+        // iterations j0 + 1..j1 again: Z_j and the prox codes of each
         a.ja = j0 + 1;
-        a.jb = j1 - 1;
+        a.jb = j1;
         CPCA_TRY(launch_fwd());
       }
       a.ja = j0 + 1;

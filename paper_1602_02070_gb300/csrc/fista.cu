@@ -601,9 +601,11 @@ fista_batch_kernel(const __grid_constant__ FistaBatchArgs a) {
       if (RESIDENT) {
         i0 = ri0; j0 = rj0; ni = rni; nj = rnj;
       } else {
-        const int lt = tile - I.tile0;
-        i0 = (lt / I.ntj) * TB;
-        j0 = (lt % I.ntj) * TB;
+        // column-block-major order: the tiles in flight at one time share
+        // few column blocks of Z (the row products' gathers stay in L2)
+        const int lt = tile - I.tile0, nti = (I.rr + TB - 1) / TB;
+        i0 = (lt % nti) * TB;
+        j0 = (lt / nti) * TB;
         ni = min(TB, I.rr - i0);
         nj = min(TB, I.rc - j0);
         stage_tile(sm, I, i0, j0, ni, nj);

@@ -13,3 +13,4 @@ closed forms, textbook routines, invariants or brute force.
 """
 from .cpca_oracle import *  # noqa: F401,F403
 from . import cpca_adjoint  # noqa: F401  (reverse-mode derivatives, FP64)
+from . import cpca_decoders  # noqa: F401  (alternate decoder, Sec. V-B)

@@ -1,0 +1,119 @@
+"""Pins of the alternate-decoder oracle (Sec. V-B, Eq. alternatedecoder)
+against facts that do not reuse its normal equations."""
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+import oracle as O
+from oracle import cpca_decoders as D
+
+
+def _ring_graph(N: int, rng, extra: int = 4):
+    """Connected symmetric weights: a ring plus a few random chords."""
+    W = np.zeros((N, N))
+    for i in range(N):
+        w = rng.uniform(0.2, 1.0)
+        W[i, (i + 1) % N] = W[(i + 1) % N, i] = w
+    for _ in range(extra):
+        i, j = rng.choice(N, 2, replace=False)
+        w = rng.uniform(0.2, 1.0)
+        W[i, j] = W[j, i] = w
+    return W
+
+
+def _incidence(W, lap_type):
+    """G with G^T G = the Laplacian of W: one row per edge i < j,
+    sqrt(w_ij) (e_i / s_i - e_j / s_j), s = sqrt(degree) for the
+    normalised Laplacian and 1 for the combinatorial one."""
+    N = W.shape[0]
+    deg = W.sum(axis=1)
+    s = np.sqrt(deg) if lap_type == O.LAP_NORMALIZED else np.ones(N)
+    rows = []
+    for i in range(N):
+        for j in range(i + 1, N):
+            if W[i, j] > 0:
+                g = np.zeros(N)
+                g[i] = 1.0 / s[i]
+                g[j] = -1.0 / s[j]
+                rows.append(np.sqrt(W[i, j]) * g)
+    return np.array(rows)
+
+
+def _problem(seed, p=6, n=5, rr=3, rc=3, lap_type=O.LAP_NORMALIZED):
+    rng = np.random.default_rng(seed)
+    Wr, Wc = _ring_graph(p, rng), _ring_graph(n, rng)
+    Lr = O.laplacian_from_weights(sp.csr_matrix(Wr), lap_type)
+    Lc = O.laplacian_from_weights(sp.csr_matrix(Wc), lap_type)
+    om_r = np.sort(rng.choice(p, rr, replace=False))
+    om_c = np.sort(rng.choice(n, rc, replace=False))
+    Xt = rng.standard_normal((rr, rc))
+    return dict(Wr=Wr, Wc=Wc, Lr=Lr, Lc=Lc, om_r=om_r, om_c=om_c, Xt=Xt, p=p, n=n)
+
+
+def test_full_sampling_without_regularisation_returns_the_samples():
+    rng = np.random.default_rng(0)
+    p, n = 5, 4
+    Xt = rng.standard_normal((p, n))
+    L = O.laplacian_from_weights(sp.csr_matrix(_ring_graph(p, rng)))
+    M = O.laplacian_from_weights(sp.csr_matrix(_ring_graph(n, rng)))
+    X = D.alternate_decode(Xt, np.arange(p), np.arange(n), p, n, L, M, 0.0, 0.0)
+    np.testing.assert_allclose(X, Xt, rtol=0, atol=1e-13)
+
+
+@pytest.mark.parametrize("lap_type", [O.LAP_NORMALIZED, O.LAP_COMBINATORIAL])
+def test_objective_is_stationary_at_the_solution(lap_type):
+    q = _problem(1, lap_type=lap_type)
+    gr, gc = 0.7, 1.3
+    X = D.alternate_decode(q["Xt"], q["om_r"], q["om_c"], q["p"], q["n"], q["Lr"], q["Lc"], gr, gc)
+    f = lambda Z: D.alternate_objective(Z, q["Xt"], q["om_r"], q["om_c"], q["Lr"], q["Lc"], gr, gc)
+    f0 = f(X)
+    h = 1e-4
+    for i in range(q["p"]):
+        for j in range(q["n"]):
+            E = np.zeros_like(X)
+            E[i, j] = h
+            g = (f(X + E) - f(X - E)) / (2 * h)  # exact for a quadratic up to rounding
+            assert abs(g) < 1e-8
+            assert f(X + E) > f0 and f(X - E) > f0  # strict minimum (positive definite)
+
+
+@pytest.mark.parametrize("lap_type", [O.LAP_NORMALIZED, O.LAP_COMBINATORIAL])
+def test_matches_stacked_least_squares_through_incidence_factors(lap_type):
+    """tr(X L_c X^T) = |X G_c^T|^2 and tr(X^T L_r X) = |G_r X|^2, so the
+    objective is one linear least-squares problem in vec(X)."""
+    q = _problem(2, p=7, n=6, rr=4, rc=3, lap_type=lap_type)
+    gr, gc = 0.4, 2.0
+    Gr, Gc = _incidence(q["Wr"], lap_type), _incidence(q["Wc"], lap_type)
+    np.testing.assert_allclose(Gr.T @ Gr, q["Lr"].toarray(), atol=1e-12)
+    np.testing.assert_allclose(Gc.T @ Gc, q["Lc"].toarray(), atol=1e-12)
+    p, n = q["p"], q["n"]
+    blocks, rhs = [], []
+    for a, i in enumerate(q["om_r"]):          # sampled entries: X[i, j] - Xt[a, b]
+        for b, j in enumerate(q["om_c"]):
+            row = np.zeros(p * n)
+            row[i * n + j] = 1.0
+            blocks.append(row)
+            rhs.append(q["Xt"][a, b])
+    for i in range(p):                          # sqrt(gc) (X G_c^T)[i, e]
+        for e in range(Gc.shape[0]):
+            row = np.zeros(p * n)
+            row[i * n:(i + 1) * n] = np.sqrt(gc) * Gc[e]
+            blocks.append(row)
+            rhs.append(0.0)
+    for e in range(Gr.shape[0]):                # sqrt(gr) (G_r X)[e, j]
+        for j in range(n):
+            row = np.zeros(p * n)
+            row[j::n] = np.sqrt(gr) * Gr[e]
+            blocks.append(row)
+            rhs.append(0.0)
+    x, *_ = np.linalg.lstsq(np.array(blocks), np.array(rhs), rcond=None)
+    X = D.alternate_decode(q["Xt"], q["om_r"], q["om_c"], p, n, q["Lr"], q["Lc"], gr, gc)
+    np.testing.assert_allclose(X, x.reshape(p, n), rtol=0, atol=1e-10)
+
+
+def test_transposed_problem_gives_the_transposed_solution():
+    q = _problem(3, p=6, n=8, rr=2, rc=5)
+    gr, gc = 0.9, 0.3
+    X = D.alternate_decode(q["Xt"], q["om_r"], q["om_c"], q["p"], q["n"], q["Lr"], q["Lc"], gr, gc)
+    XT = D.alternate_decode(q["Xt"].T, q["om_c"], q["om_r"], q["n"], q["p"], q["Lc"], q["Lr"], gc, gr)
+    np.testing.assert_allclose(XT, X.T, rtol=0, atol=1e-12)

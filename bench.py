@@ -334,6 +334,49 @@ def adjoint_comparison(M, torch, Yd, cfg, n_heldout=10000, reps=3, h=1e-3):
                     "differences give the two gamma derivatives only, from FP32 losses"}
 
 
+def alternate_measure(M, torch, Yd, cfg, peaks, reps=3, gamma=1.0):
+    """The alternate decoder (Eq. alternatedecoder) on the full matrix of the
+    workload: X~ from the step's FISTA solve, the full row/column graphs,
+    gamma-bars = 1, PCG to the step's tolerance. Kernel time from the
+    library's CUDA-event profile; algorithmic bytes per CG iteration: 52 per
+    entry of X (phase A reads z, q, p and writes q, p; phase B reads x, r,
+    p, q and writes x, r, z and its transposed copy) plus 8 per CSR entry of
+    both Laplacians (column index and value)."""
+    p, n = Yd.shape
+    K, J = cfg["K"], cfg["J"]
+    rr, rc = M.rho_of(p, cfg["fr"]), M.rho_of(n, cfg["fc"])
+    Lr, _, _ = M.cpca_knn_graph(Yd, K)
+    Lc, _, _ = M.cpca_knn_graph(Yd, K, transposed=True)
+    om_r, om_c, Yt = M.cpca_sample(0, p, n, rr, rc, Yd)
+    Lrt, _, _ = M.cpca_knn_graph(Yt, K)
+    Lct, _, _ = M.cpca_knn_graph(Yt, K, transposed=True)
+    Xt, _ = M.cpca_frpcag_solve(Yt, Lrt, Lct, gamma_r=cfg["gamma_r"], gamma_c=cfg["gamma_c"], max_iter=J,
+                                want_info=False)
+    prm = M.alt_params(gamma_r=gamma, gamma_c=gamma, tol=cfg["cg_tol"], max_iter=20000)
+    ws = M.capi._workspace(M.lib().cpca_alternate_decode_workspace_size(p, n), Yd.device)
+    out = torch.empty(p, n, dtype=torch.float32, device=Yd.device)
+    _, info, _ = M.cpca_alternate_decode(Xt, om_r, om_c, p, n, Lr, Lc, prm, out=out, ws=ws)
+    torch.cuda.synchronize()
+    M.profile_enable(True, "alt_cg")
+    for _ in range(reps):
+        out.zero_()
+        _, info, _ = M.cpca_alternate_decode(Xt, om_r, om_c, p, n, Lr, Lc, prm, out=out, ws=ws)
+    torch.cuda.synchronize()
+    prof = M.profile_read()
+    M.profile_enable(False, "")
+    ms = prof["alt_cg"][0] / reps
+    iters = int(info.iters)
+    byts = 52.0 * p * n + 8.0 * (Lr.nnz + Lc.nnz)
+    hbm = peaks["hbm_gbs"] if peaks else 6800.0
+    gbs = byts * iters / (ms / 1000.0) / 1e9
+    return {"workload": f"alternate decoder on the {p}x{n} matrix, gamma-bars {gamma}, PCG to {cfg['cg_tol']}",
+            "cg_iters": iters, "rel_res": float(info.rel_res), "kernel_ms": ms,
+            "cg_iters_per_s": iters / (ms / 1000.0), "us_per_iter": 1000.0 * ms / max(iters, 1),
+            "roofline": {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm,
+                         "bytes_per_iter": byts,
+                         "peak_source": "measured" if peaks else "fallback"}}
+
+
 def profiled_dram_bytes(summary):
     """DRAM bytes per launch recorded in a committed ncu summary under
     profiles/ (the 'dram_bytes_per_launch:' line), or None."""
@@ -392,6 +435,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
+    ap.add_argument("--no-alternate", action="store_true")
     ap.add_argument("--cpu-queries", type=int, default=32)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 0)
@@ -532,6 +576,8 @@ def main():
         line["batched_64"] = batched_comparison(M, torch)
     if not args.no_adjoint:
         line["adjoint"] = adjoint_comparison(M, torch, Yd, cfg)
+    if not args.no_alternate:
+        line["alternate_decoder"] = alternate_measure(M, torch, Yd, cfg, peaks)
     if world == 1 and not args.no_cpu_baseline:
         dec = decoder_graphs_for_timing(Y, cfg["K"])
         secs = oracle_step_seconds(Y, cfg, args.cpu_queries, dec)

@@ -443,6 +443,66 @@ cpca_status cpca_decode_entries(const float* U, const float* V, int32_t ld, cons
                                 int32_t k, int64_t nh, const int32_t* h_row, const int32_t* h_col,
                                 float* out, void* stream);
 
+/* ------------------------------------------------------------------------
+ * cpca_subspace_project - the approximate decoders 2 and 3 (appendix,
+ * "Other Approximate Decoders"): when the full data Y is available, only one
+ * subspace is upsampled and X is a projection of Y:
+ *   side 0 (decoder 2): X = U U^T Y, U the p x k upsampled, column-normalised
+ *                       left basis (cpca_decode's U);
+ *   side 1 (decoder 3): X = Y V V^T, V the n x k right basis (cpca_decode's V).
+ * basis: device FP32, rows of ldb floats (ldb <= 48; cpca_decode's kmax),
+ * first k columns used; Y p x n (ldy), X p x n (ldx), device FP32, X may not
+ * alias Y. Workspace: cpca_subspace_project_workspace_size(p, n, ldb).
+ * Asynchronous.
+ * ---------------------------------------------------------------------- */
+size_t cpca_subspace_project_workspace_size(int32_t p, int32_t n, int32_t ldb);
+cpca_status cpca_subspace_project(int32_t side, const float* basis, int32_t ldb, int32_t k, const float* Y,
+                                  int64_t ldy, int32_t p, int32_t n, float* X, int64_t ldx, void* ws,
+                                  size_t ws_bytes, void* stream);
+
+/* ------------------------------------------------------------------------
+ * cpca_alternate_decode - the alternate decoder (Sec. V-B,
+ * Eq. alternatedecoder): the full p x n matrix X minimising
+ *   |M_r X M_c - Xt|_F^2 + gamma_c tr(X L_c X^T) + gamma_r tr(X^T L_r X)
+ * (gamma_r, gamma_c the paper's gamma-bars, user-chosen; Theorem 2 relates
+ * them to a gamma and the graphs' spectral gaps), solved through its normal
+ * equations D_r X D_c + gamma_c X L_c + gamma_r L_r X = M_r^T Xt M_c^T by
+ * Jacobi-preconditioned conjugate gradients (the paper names CG for it,
+ * cost O(I n p K)); D_r, D_c: 0/1 diagonals of the sampled rows/columns.
+ *
+ * Xt: rr x rc (leading dimension ldxt) FP32, device; omega_r (rr), omega_c
+ * (rc): the sampled row/column indices (distinct, in range; Xt(a, b)
+ * belongs to row omega_r[a], column omega_c[b]); Lr (p nodes), Lc (n
+ * nodes): symmetric Laplacian CSR. X (p x n, ldx, device FP32) receives the
+ * solution. x0 = 0; stops when |r|_2 <= tol |B|_2 or after max_iter
+ * iterations. FP32 vectors, FP64 dot products. Workspace:
+ * cpca_alternate_decode_workspace_size(p, n) bytes (six p x n FP32 arrays
+ * and small tables). SYNCHRONISES (twice: index checks, result). Returns
+ * CPCA_ERR_INVALID_ARG for bad or repeated omega entries,
+ * CPCA_ERR_NOT_CONVERGED if max_iter was reached (X still written),
+ * CPCA_ERR_TIMEOUT if a device barrier gave up.
+ * ---------------------------------------------------------------------- */
+typedef struct cpca_alt_params {
+  double gamma_r;     /* weight of tr(X^T L_r X), >= 0 */
+  double gamma_c;     /* weight of tr(X L_c X^T), >= 0 */
+  double tol;         /* relative residual */
+  int32_t max_iter;   /* CG iterations at most */
+  int32_t blocks;     /* launch width cap; 0 = automatic */
+} cpca_alt_params;
+
+typedef struct cpca_alt_info {
+  int32_t iters;
+  int32_t converged;
+  double rel_res;     /* |r|_2 / |B|_2 at the end */
+} cpca_alt_info;
+
+size_t cpca_alternate_decode_workspace_size(int32_t p, int32_t n);
+cpca_status cpca_alternate_decode(const float* Xt, int32_t rr, int32_t rc, int64_t ldxt,
+                                  const int32_t* omega_r, const int32_t* omega_c, int32_t p, int32_t n,
+                                  const cpca_csr* Lr, const cpca_csr* Lc, const cpca_alt_params* params,
+                                  float* X, int64_t ldx, cpca_alt_info* info, void* ws, size_t ws_bytes,
+                                  void* stream);
+
 #ifdef __cplusplus
 }
 #endif

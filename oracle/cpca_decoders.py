@@ -21,6 +21,14 @@ closed form (full sampling, no regularisation), vanishing central
 differences of the objective as written above, an independent stacked
 least-squares solve through incidence factors L = G^T G, and the
 transpose symmetry of the problem.
+
+Approximate decoders 2 and 3 (appendix, "Other Approximate Decoders"):
+with the full data Y available, only one subspace is upsampled (Lemma 1,
+Eq. Uupsample, then unit columns as in Algorithm 2 step 4) and
+X = U U^T Y (decoder 2) or X = Y V V^T (decoder 3). Pinned by the exact
+recovery of exactly low-rank data when every row (column) is sampled, by
+the paper's V-route X = U Sigma~ c V^T with V = Y^T U Sigma~^-1 / c, and by
+the symmetry between the two decoders under transposition.
 """
 from __future__ import annotations
 
@@ -28,7 +36,9 @@ import numpy as np
 import scipy.sparse as sp
 import scipy.sparse.linalg as spla
 
-__all__ = ["selection_matrix", "alternate_objective", "alternate_decode"]
+from .cpca_oracle import pcg, svd_rank, upsample_subspace
+
+__all__ = ["selection_matrix", "alternate_objective", "alternate_decode", "approx_decode_projected"]
 
 
 def selection_matrix(omega: np.ndarray, N: int) -> sp.csr_matrix:
@@ -50,14 +60,18 @@ def alternate_objective(X, Xt, omega_r, omega_c, Lr, Lc, gr_bar: float, gc_bar: 
     return float(np.sum(fit * fit) + gc_bar * np.trace(X @ (Lc @ X.T)) + gr_bar * np.trace(X.T @ (Lr @ X)))
 
 
-def alternate_decode(Xt, omega_r, omega_c, p: int, n: int, Lr, Lc, gr_bar: float, gc_bar: float):
-    """Exact minimiser of Eq. (alternatedecoder): the normal equations in
+def alternate_decode(Xt, omega_r, omega_c, p: int, n: int, Lr, Lc, gr_bar: float, gc_bar: float,
+                     tol: float | None = None):
+    """Minimiser of Eq. (alternatedecoder): the normal equations in
     Kronecker form on vec(X) taken row by row (index i * n + j),
 
         (D_r kron D_c + gc_bar I_p kron L_c^T + gr_bar L_r kron I_n) vec(X)
             = vec(M_r^T X~ M_c^T),
 
-    solved by a sparse direct factorisation. Returns X (p x n)."""
+    solved by a sparse direct factorisation (tol None; exact, for small
+    sizes: the factors fill in quickly) or by this oracle's FP64 Jacobi PCG
+    to relative residual tol (the same system; for larger test sizes).
+    Returns X (p x n)."""
     Mr = selection_matrix(omega_r, p)
     Mc = selection_matrix(omega_c, n).T
     Dr = (Mr.T @ Mr).tocsr()
@@ -66,5 +80,28 @@ def alternate_decode(Xt, omega_r, omega_c, p: int, n: int, Lr, Lc, gr_bar: float
     Lc = sp.csr_matrix(Lc, dtype=np.float64)
     A = (sp.kron(Dr, Dc) + gc_bar * sp.kron(sp.identity(p), Lc.T) + gr_bar * sp.kron(Lr, sp.identity(n))).tocsc()
     B = Mr.T @ sp.csr_matrix(np.asarray(Xt, dtype=np.float64)) @ Mc.T
-    x = spla.spsolve(A, np.asarray(B.todense()).reshape(-1))
+    b = np.asarray(B.todense()).reshape(-1)
+    if tol is None:
+        x = spla.spsolve(A, b)
+    else:
+        x, _, _ = pcg(A.tocsr(), b, tol=tol, maxit=100 * p * n)
     return np.asarray(x).reshape(p, n)
+
+
+def approx_decode_projected(Y, Xt, omega_r, omega_c, Lr, Lc, side: int, ratio: float = 0.1,
+                            tol: float = 1e-6, k_override: int | None = None, maxit: int | None = None):
+    """Approximate decoder 2 (side 0) or 3 (side 1). Steps: SVD of X~ and
+    the rank k (Algorithm 2 steps 1-2); upsample U~ on L_r (side 0) or V~ on
+    L_c (side 1) (Lemma 1); unit columns (Algorithm 2 step 4); then
+    X = U (U^T Y) or X = (Y V) V^T. Returns (X, basis, k)."""
+    Y = np.asarray(Y, dtype=np.float64)
+    Ut, s, Vh, k = svd_rank(Xt, ratio)
+    if k_override is not None:
+        k = int(k_override)
+    if side == 0:
+        B, _, _ = upsample_subspace(Lr, omega_r, Ut[:, :k], tol, maxit)
+    else:
+        B, _, _ = upsample_subspace(Lc, omega_c, Vh[:k].T, tol, maxit)
+    B = B / np.linalg.norm(B, axis=0, keepdims=True)
+    X = B @ (B.T @ Y) if side == 0 else (Y @ B) @ B.T
+    return X, B, k

@@ -78,6 +78,15 @@ class cpca_decode_info(C.Structure):
                 ("s_tilde", C.c_double * 64), ("b", C.c_int32)]
 
 
+class cpca_alt_params(C.Structure):
+    _fields_ = [("gamma_r", C.c_double), ("gamma_c", C.c_double), ("tol", C.c_double),
+                ("max_iter", C.c_int32), ("blocks", C.c_int32)]
+
+
+class cpca_alt_info(C.Structure):
+    _fields_ = [("iters", C.c_int32), ("converged", C.c_int32), ("rel_res", C.c_double)]
+
+
 _lib = None
 
 # (name, restype, argtypes) of every exported entry point in include/cpca.h
@@ -145,6 +154,15 @@ _SIGS = [
       C.POINTER(cpca_csr), C.POINTER(cpca_csr), C.POINTER(cpca_decode_params), C.c_void_p,
       C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(C.c_int32),
       C.POINTER(cpca_decode_info), C.c_void_p, C.c_size_t, C.c_void_p]),
+    ("cpca_subspace_project_workspace_size", C.c_size_t, [C.c_int32, C.c_int32, C.c_int32]),
+    ("cpca_subspace_project", C.c_int32,
+     [C.c_int32, C.c_void_p, C.c_int32, C.c_int32, C.c_void_p, C.c_int64, C.c_int32, C.c_int32, C.c_void_p,
+      C.c_int64, C.c_void_p, C.c_size_t, C.c_void_p]),
+    ("cpca_alternate_decode_workspace_size", C.c_size_t, [C.c_int32, C.c_int32]),
+    ("cpca_alternate_decode", C.c_int32,
+     [C.c_void_p, C.c_int32, C.c_int32, C.c_int64, C.c_void_p, C.c_void_p, C.c_int32, C.c_int32,
+      C.POINTER(cpca_csr), C.POINTER(cpca_csr), C.POINTER(cpca_alt_params), C.c_void_p, C.c_int64,
+      C.POINTER(cpca_alt_info), C.c_void_p, C.c_size_t, C.c_void_p]),
 ]
 
 
@@ -497,6 +515,47 @@ def cpca_decode(Xt: torch.Tensor, omega_r: torch.Tensor, omega_c: torch.Tensor, 
     kk = k.value
     return {"X": X, "U": U[:, :kk], "V": V[:, :kk], "sigma": sig[:kk], "k": kk, "info": info,
             "status": st}
+
+
+def cpca_subspace_project(side: int, basis: torch.Tensor, k: int, Y: torch.Tensor,
+                          out: torch.Tensor | None = None, ws=None) -> torch.Tensor:
+    """Approximate decoder 2 (side 0: X = U U^T Y, basis U p x ldb) or 3
+    (side 1: X = Y V V^T, basis V n x ldb), first k basis columns."""
+    _require_cuda(Y, torch.float32, "Y")
+    _require_cuda(basis, torch.float32, "basis")
+    p, n = Y.shape
+    ldb = basis.stride(0)
+    X = out if out is not None else torch.empty(p, n, dtype=torch.float32, device=Y.device)
+    if ws is None:
+        ws = _workspace(lib().cpca_subspace_project_workspace_size(p, n, ldb), Y.device)
+    _check(lib().cpca_subspace_project(side, _ptr(basis), ldb, k, _ptr(Y), Y.stride(0), p, n, _ptr(X),
+                                       X.stride(0), _ptr(ws), ws.numel(), _stream()))
+    return X
+
+
+def alt_params(gamma_r=1.0, gamma_c=1.0, tol=1e-6, max_iter=2000, blocks=0) -> cpca_alt_params:
+    return cpca_alt_params(gamma_r, gamma_c, tol, max_iter, blocks)
+
+
+def cpca_alternate_decode(Xt: torch.Tensor, omega_r: torch.Tensor, omega_c: torch.Tensor, p: int,
+                          n: int, Lr: Csr, Lc: Csr, params: cpca_alt_params | None = None,
+                          out: torch.Tensor | None = None, ws=None, check_status: bool = True, **kw):
+    """Alternate decoder (Eq. alternatedecoder) by PCG on the full p x n
+    matrix. Returns (X, info, status)."""
+    _require_cuda(Xt, torch.float32, "Xt")
+    prm = params if params is not None else alt_params(**kw)
+    rr, rc = Xt.shape
+    X = out if out is not None else torch.empty(p, n, dtype=torch.float32, device=Xt.device)
+    if ws is None:
+        ws = _workspace(lib().cpca_alternate_decode_workspace_size(p, n), Xt.device)
+    info = cpca_alt_info()
+    lr, lc = Lr.c(), Lc.c()
+    st = lib().cpca_alternate_decode(_ptr(Xt), rr, rc, Xt.stride(0), _ptr(omega_r), _ptr(omega_c), p, n,
+                                     C.byref(lr), C.byref(lc), C.byref(prm), _ptr(X), X.stride(0),
+                                     C.byref(info), _ptr(ws), ws.numel(), _stream())
+    if check_status:
+        _check(st)
+    return X, info, st
 
 
 def decode_backward_workspace(Xt: torch.Tensor, p: int, n: int, Lr: Csr, Lc: Csr,

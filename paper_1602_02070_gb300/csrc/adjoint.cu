@@ -859,6 +859,7 @@ struct BwdWs {
   float *S, *Sb, *A2, *Vb[2], *VbT[2];
   float *Zs, *ZTs;
   uint8_t* Ms;
+  void* pscr;        // power iteration scratch (grid-wide kernel)
   float *ckS, *ckZ;
   double *Pr, *Pc;
   double *dLr, *dLc;
@@ -913,6 +914,10 @@ BwdWs bwd_layout(void* ws, int rr, int rc, int J, int ck, int T, int64_t nnz_r, 
     w.vb[g][1] = c.take<float>(n);
   }
   w.pacc = c.take<double>(16);
+  {
+    const int ns[2] = {rr, rc};
+    w.pscr = c.take<unsigned char>(power_scratch_bytes(ns, 2));
+  }
   w.bar_cnt = c.take<unsigned int>(kBarrierCounters + 1);
   w.err = c.take<int>(1);
   w.bytes = c.bytes();
@@ -926,14 +931,14 @@ cpca_status reset_barrier(const BwdWs& w, cudaStream_t st) {
 
 cpca_status run_power(PowAdjArgs& pa, const BwdWs& w, int reverse, cudaStream_t st) {
   const CsrView Ls[2] = {pa.g[0].L, pa.g[1].L};
-  if (power_tape_fits(Ls, 2)) {  // one thread-block cluster
+  if (!reverse || power_tape_fits(Ls, 2)) {  // the solve's power kernels (reverse: one cluster)
     PowerTape P[2];
     for (int g = 0; g < 2; ++g) {
       const PowGraph& G = pa.g[g];
       P[g] = PowerTape{G.L, G.stream, G.U, G.nrm2, G.Ub, G.rho, G.rho_bar};
     }
     CPCA_PROF(reverse ? "adj_power_rev" : "adj_power_fwd", st);
-    return power_tape_run(P, 2, pa.T, pa.seed, reverse != 0, st);
+    return power_tape_run(P, 2, pa.T, pa.seed, reverse != 0, w.pscr, w.bar_cnt, w.err, st);
   }
   pa.reverse = reverse;
   CPCA_TRY(reset_barrier(w, st));

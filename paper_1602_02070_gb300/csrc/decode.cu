@@ -1844,6 +1844,74 @@ extern "C" cpca_status cpca_decode_backward(const float* Xt, int32_t rr, int32_t
   return CPCA_OK;
 }
 
+// ------------------------------------------------- approximate decoders 2, 3
+// With the full data Y and one upsampled, column-normalised basis (the
+// appendix's approximate decoders 2 and 3): X = U (U^T Y) (side 0, U p x k)
+// or X = (Y V) V^T (side 1, V n x k). The small factor (k x n or p x k) by a
+// tall product over Y, then X by the output kernel with unit weights. Reads
+// Y once and writes X once (HBM-bound; k <= 48).
+__global__ void ones_kernel(double* s, int k) {
+  if (threadIdx.x < k) s[threadIdx.x] = 1.0;
+}
+
+static size_t project_layout(int32_t p, int32_t n, int32_t ldb, float** W, float** scratch, double** ones,
+                             void* ws) {
+  Carve c(ws);
+  float* w = c.take<float>(size_t(std::max(p, n)) * ldb);
+  float* sc = c.take<float>(size_t(kTnChunks) * n * ldb);
+  double* o = c.take<double>(KMAX_LIMIT);
+  if (W) *W = w;
+  if (scratch) *scratch = sc;
+  if (ones) *ones = o;
+  return c.bytes();
+}
+
+extern "C" size_t cpca_subspace_project_workspace_size(int32_t p, int32_t n, int32_t ldb) {
+  if (p <= 0 || n <= 0 || ldb <= 0 || ldb > KMAX_LIMIT) return 0;
+  return project_layout(p, n, ldb, nullptr, nullptr, nullptr, nullptr);
+}
+
+extern "C" cpca_status cpca_subspace_project(int32_t side, const float* basis, int32_t ldb, int32_t k,
+                                             const float* Y, int64_t ldy, int32_t p, int32_t n, float* X,
+                                             int64_t ldx, void* ws, size_t ws_bytes, void* stream) {
+  clear_error();
+  CPCA_CHECK_ARG(basis && Y && X, "cpca_subspace_project: null pointer");
+  CPCA_CHECK_ARG(side == 0 || side == 1, "cpca_subspace_project: side must be 0 (U) or 1 (V)");
+  CPCA_CHECK_ARG(p > 0 && n > 0 && ldb >= 1 && ldb <= KMAX_LIMIT && k >= 0 && k <= ldb,
+                 "cpca_subspace_project: bad sizes (p %d, n %d, ldb %d, k %d)", p, n, ldb, k);
+  CPCA_CHECK_ARG(ldy >= n && ldx >= n, "cpca_subspace_project: leading dimension too small");
+  float *W = nullptr, *scr = nullptr;
+  double* ones = nullptr;
+  const size_t need = project_layout(p, n, ldb, &W, &scr, &ones, ws);
+  if (!ws || ws_bytes < need) {
+    set_error("cpca_subspace_project: workspace %zu bytes < required %zu", ws_bytes, need);
+    return CPCA_ERR_WORKSPACE;
+  }
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (k == 0) {
+    CPCA_CUDA(cudaMemset2DAsync(X, ldx * sizeof(float), 0, size_t(n) * sizeof(float), p, st));
+    return CPCA_OK;
+  }
+  ones_kernel<<<1, 64, 0, st>>>(ones, k);
+  CPCA_LAUNCHED();
+  dim3 og(ceil_div(n, 128), ceil_div(p, 32));
+  if (side == 0) {
+    CPCA_PROF("project_small", st);
+    CPCA_TRY(tn_tall(Y, ldy, p, n, basis, ldb, W, scr, st));  // W = Y^T U (n x ldb)
+    CPCA_PROF("project_output", st);
+    output_kernel<<<og, 256, 0, st>>>(basis, ldb, W, ldb, ones, k, p, n, X, ldx);
+    CPCA_LAUNCHED();
+  } else {
+    CPCA_PROF("project_small", st);
+    gemm_nn_tall<<<ceil_div(p, 8), 256, 0, st>>>(Y, ldy, p, n, basis, ldb, W);  // W = Y V (p x ldb)
+    CPCA_LAUNCHED();
+    CPCA_PROF("project_output", st);
+    output_kernel<<<og, 256, 0, st>>>(W, ldb, basis, ldb, ones, k, p, n, X, ldx);
+    CPCA_LAUNCHED();
+  }
+  return CPCA_OK;
+}
+
 extern "C" cpca_status cpca_decode_entries(const float* U, const float* V, int32_t ld, const double* sigma,
                                            int32_t k, int64_t nh, const int32_t* h_row, const int32_t* h_col,
                                            float* out, void* stream) {

@@ -41,23 +41,25 @@ namespace {
 
 // ------------------------------------------------------------- step size --
 // Power iteration on a list of Laplacians (two per instance: Lr with stream
-// 2, Lc with stream 3), warp per row over the concatenated rows, then the
-// Rayleigh quotients. With v_k = u_k / |u_k| the iteration v <- L v / |L v|
-// is carried as u_{k+1} = (L u_k) / |u_k|, so each step needs one grid
-// barrier (for |u_{k+1}|). Start vector u_0(i) = SplitMix64 uniform - 1/2.
-// Iterates FP32, norms and quotients FP64; the scale 1/|u_k| itself only
-// keeps the iterate bounded (the quotient does not depend on it) and is
-// taken in FP32 (FP64 square roots and divisions are slow on this GPU and
-// sit on every step's critical path).
+// 2, Lc with stream 3), then the Rayleigh quotients. With v_k = u_k / |u_k|
+// the iteration v <- L v / |L v| is carried as u_{k+1} = (L u_k) / |u_k|, so
+// each step needs one synchronisation (for |u_{k+1}|). Start vector
+// u_0(i) = SplitMix64 uniform - 1/2. Iterates FP32, norms and quotients
+// FP64; the scale 1/|u_k| only keeps the iterate bounded (the quotient does
+// not depend on it) and is taken in FP32 (FP64 square roots sit on every
+// step's critical path).
+//
+// Arithmetic shared by both kernels below (so that a graph's estimate does
+// not depend on the kernel, the launch or the other graphs): one thread per
+// row, each graph's rows padded to whole warps ("warp blocks", graph g's
+// first at w0); (L u)(i) by FMAs in CSR order; each warp block's FP64 sum
+// of squares; a graph's |u|^2 the sum of its warp blocks' sums, lane-strided
+// in block order then a butterfly (the same bits in every lane).
 struct PowerGraph {
   CsrView L;
-  float* u[2];
-  double* acc;  // ring [3]: |u|^2 of the step
-  double* fin;  // [2]: u^T L u, u^T u
   double* out;  // |L|_2 estimate
   int stream;
-  int row0;     // first row in the concatenated row list
-  int w0;       // first 32-row block in the warp-padded row list
+  int w0;       // first warp block in the warp-padded row list
   // kept iterates for reverse mode (null in a plain solve)
   float* U;               // [(T + 1) * n]: u_t at U + t * n
   double* nrm2;           // [T + 1]: |u_t|^2
@@ -67,80 +69,103 @@ struct PowerGraph {
 struct PowerBatchArgs {
   PowerGraph g[2 * kMaxBatch];
   int ngraph;
-  int rows;
   int iters;
   uint64_t seed;
   GridBar bar;
 };
 
-__device__ __forceinline__ int find_graph(const PowerBatchArgs& a, int r) {
+__device__ __forceinline__ int find_graph_warp(const PowerBatchArgs& a, int vw) {
   int lo = 0, hi = a.ngraph - 1;
   while (lo < hi) {
     const int mid = (lo + hi + 1) >> 1;
-    if (a.g[mid].row0 <= r) lo = mid; else hi = mid - 1;
+    if (a.g[mid].w0 <= vw) lo = mid; else hi = mid - 1;
   }
   return lo;
 }
 
+// sum over graph G's warp blocks of part[w0 + w] (see above); CG: through L2
+template <bool CG = false>
+__device__ __forceinline__ double graph_warp_sum(const double* part, const PowerGraph& G, int lane) {
+  const int nw = (G.L.n + 31) >> 5;
+  double t = 0.0;
+  for (int w = lane; w < nw; w += 32) t += CG ? __ldcg(part + G.w0 + w) : part[G.w0 + w];
+  return warp_sum(t);
+}
+
+// Grid-wide version for graph sets larger than one cluster: every warp of a
+// cooperative launch takes warp blocks in turn; the iterate (padded row
+// order, ping-pong) and the warp-block sums live in global scratch; one grid
+// barrier per step. Kept iterates (G.U) as in the cluster kernel.
 __global__ void __launch_bounds__(512)
-power_batch_kernel(const __grid_constant__ PowerBatchArgs a) {
+power_batch_kernel(const __grid_constant__ PowerBatchArgs a, int nvw, float* __restrict__ u,
+                   double* __restrict__ wq, double* __restrict__ rq) {
   const int lane = threadIdx.x & 31;
-  const int nwarp = (gridDim.x * blockDim.x) >> 5;
-  const int wid = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int nthr = gridDim.x * blockDim.x, tid = blockIdx.x * blockDim.x + threadIdx.x;
-  // u_0 and |u_0|^2 into ring slot 0
-  for (int r = tid; r < a.rows; r += nthr) {
-    const PowerGraph& G = a.g[find_graph(a, r)];
-    const int i = r - G.row0;
-    const double x = uniform01_at(stream_state0(a.seed, G.stream), uint64_t(i) + 1) - 0.5;
-    G.u[0][i] = float(x);
-    atomicAdd(G.acc, x * x);
+  const int nwt = (gridDim.x * blockDim.x) >> 5;
+  const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int NV = 32 * nvw;
+  for (int vw = gw; vw < nvw; vw += nwt) {
+    const PowerGraph& G = a.g[find_graph_warp(a, vw)];
+    const int i = (vw - G.w0) * 32 + lane;
+    double q = 0.0;
+    float x0 = 0.f;
+    if (i < G.L.n) {
+      const double x = uniform01_at(stream_state0(a.seed, G.stream), uint64_t(i) + 1) - 0.5;
+      q = x * x;
+      x0 = float(x);
+      if (G.U) G.U[i] = x0;
+    }
+    u[vw * 32 + lane] = x0;
+    q = warp_sum(q);
+    if (lane == 0) wq[vw] = q;
   }
   if (!grid_sync(a.bar)) return;
+  auto spmv = [&](const PowerGraph& G, int i, const float* x) {
+    const int vbase = 32 * G.w0;
+    float acc = 0.f;
+    for (int64_t e = G.L.rowptr[i]; e < G.L.rowptr[i + 1]; ++e)
+      acc = fmaf(__ldg(G.L.val + e), __ldcg(x + vbase + __ldg(G.L.col + e)), acc);
+    return acc;
+  };
   for (int k = 0; k < a.iters; ++k) {
     const int cur = k & 1, nxt = cur ^ 1;
-    // slot (k + 2) % 3 was last read after the barrier of step k - 2
-    if (blockIdx.x == 0)
-      for (int g = threadIdx.x; g < a.ngraph; g += blockDim.x) a.g[g].acc[(k + 2) % 3] = 0.0;
-    for (int r = wid; r < a.rows; r += nwarp) {
-      const PowerGraph& G = a.g[find_graph(a, r)];
-      const int i = r - G.row0;
-      const double n2 = __ldcg(G.acc + k % 3);
+    for (int vw = gw; vw < nvw; vw += nwt) {
+      const PowerGraph& G = a.g[find_graph_warp(a, vw)];
+      const int i = (vw - G.w0) * 32 + lane;
+      const double n2 = graph_warp_sum<true>(wq + cur * nvw, G, lane);
+      if (G.nrm2 && vw == G.w0 && lane == 0) G.nrm2[k] = n2;
       const float inv = n2 > 0 ? rsqrtf(float(n2)) : 0.f;  // only the direction matters
-      const float* u = G.u[cur];
-      float sum = 0.f;
-      for (int64_t e = G.L.rowptr[i] + lane; e < G.L.rowptr[i + 1]; e += 32)
-        sum = fmaf(__ldg(G.L.val + e), __ldcg(u + __ldg(G.L.col + e)), sum);
-      sum = warp_sumf(sum) * inv;
-      if (lane == 0) {
-        G.u[nxt][i] = sum;
-        atomicAdd(G.acc + (k + 1) % 3, double(sum) * double(sum));
-      }
+      const float s = i < G.L.n ? spmv(G, i, u + cur * NV) * inv : 0.f;
+      if (i < G.L.n && G.U) G.U[size_t(k + 1) * G.L.n + i] = s;
+      u[nxt * NV + vw * 32 + lane] = s;
+      const double q = warp_sum(double(s) * double(s));
+      if (lane == 0) wq[nxt * nvw + vw] = q;
     }
     if (!grid_sync(a.bar)) return;
   }
   // Rayleigh quotients u^T L u / u^T u of the final iterate
   const int fin = a.iters & 1;
-  for (int r = wid; r < a.rows; r += nwarp) {
-    const PowerGraph& G = a.g[find_graph(a, r)];
-    const int i = r - G.row0;
-    const float* u = G.u[fin];
-    float sum = 0.f;
-    for (int64_t e = G.L.rowptr[i] + lane; e < G.L.rowptr[i + 1]; e += 32)
-      sum = fmaf(__ldg(G.L.val + e), __ldcg(u + __ldg(G.L.col + e)), sum);
-    sum = warp_sumf(sum);
+  for (int vw = gw; vw < nvw; vw += nwt) {
+    const PowerGraph& G = a.g[find_graph_warp(a, vw)];
+    const int i = (vw - G.w0) * 32 + lane;
+    const float* x = u + fin * NV;
+    const float lu = i < G.L.n ? spmv(G, i, x) : 0.f;
+    const double ui = i < G.L.n ? double(__ldcg(x + vw * 32 + lane)) : 0.0;
+    const double num = warp_sum(ui * double(lu)), den = warp_sum(ui * ui);
     if (lane == 0) {
-      const double ui = __ldcg(u + i);
-      atomicAdd(G.fin, ui * double(sum));
-      atomicAdd(G.fin + 1, ui * ui);
+      rq[vw] = num;
+      rq[nvw + vw] = den;
     }
   }
   if (!grid_sync(a.bar)) return;
   if (blockIdx.x == 0)
-    for (int g = threadIdx.x; g < a.ngraph; g += blockDim.x) {
-      const double num = __ldcg(a.g[g].fin), den = __ldcg(a.g[g].fin + 1);
-      const double last = __ldcg(a.g[g].acc + a.iters % 3);
-      *a.g[g].out = (den > 0 && last > 0) ? num / den : 0.0;
+    for (int g = threadIdx.x >> 5; g < a.ngraph; g += blockDim.x >> 5) {
+      const PowerGraph& H = a.g[g];
+      const double nm = graph_warp_sum<true>(rq, H, lane), dn = graph_warp_sum<true>(rq + nvw, H, lane);
+      const double last = graph_warp_sum<true>(wq + fin * nvw, H, lane);
+      if (lane == 0) {
+        *H.out = (dn > 0 && last > 0) ? nm / dn : 0.0;
+        if (H.nrm2) H.nrm2[a.iters] = last;
+      }
     }
 }
 
@@ -157,24 +182,6 @@ power_batch_kernel(const __grid_constant__ PowerBatchArgs a) {
 // does not depend on the launch shape or on the other graphs of the batch.
 constexpr int kPowCtas = 8;
 constexpr int kPowMaxWarps = kPowCtas * 32;
-
-__device__ __forceinline__ int find_graph_warp(const PowerBatchArgs& a, int vw) {
-  int lo = 0, hi = a.ngraph - 1;
-  while (lo < hi) {
-    const int mid = (lo + hi + 1) >> 1;
-    if (a.g[mid].w0 <= vw) lo = mid; else hi = mid - 1;
-  }
-  return lo;
-}
-
-// sum over graph G's warps of part[w0 + w], lane-strided then a butterfly:
-// the same bits in every lane and every warp
-__device__ __forceinline__ double graph_warp_sum(const double* part, const PowerGraph& G, int lane) {
-  const int nw = (G.L.n + 31) >> 5;
-  double t = 0.0;
-  for (int w = lane; w < nw; w += 32) t += part[G.w0 + w];
-  return warp_sum(t);
-}
 
 // One thread's row in the one-cluster kernels: its graph, its CSR row and the
 // warp's sliced-ELL block in shared memory (min(longest row of the warp,
@@ -787,9 +794,6 @@ InstWs inst_layout(Carve& c, int rr, int rc) {
   w.ZT0 = c.take<float>(size_t(rc) * ldzt);
   w.ZT1 = c.take<float>(size_t(rc) * ldzt);
   w.scal = c.take<double>(4);
-  for (int g = 0; g < 2; ++g)
-    for (int b = 0; b < 2; ++b) w.pu[g][b] = c.take<float>(size_t(g ? rc : rr) + 4);
-  w.pacc = c.take<double>(10);
   w.stats = c.take<double>(8);
   w.done = c.take<int>(2);
   return w;
@@ -802,6 +806,14 @@ BatchWs batch_layout(void* ws, const int* rr, const int* rc, int n) {
   w.err = c.take<int>(1);
   w.part = c.take<double>(kObjBlocks);
   w.obj = c.take<double>(1);
+  {
+    std::vector<int> ns(2 * size_t(n));
+    for (int i = 0; i < n; ++i) {
+      ns[2 * i] = rr[i];
+      ns[2 * i + 1] = rc[i];
+    }
+    w.pscr = c.take<unsigned char>(power_scratch_bytes(ns.data(), 2 * n));
+  }
   for (int i = 0; i < n; ++i) w.inst[i] = inst_layout(c, rr[i], rc[i]);
   w.n = n;
   w.bytes = c.bytes();
@@ -831,17 +843,44 @@ static cpca_status ensure_mu_table() {
   return CPCA_OK;
 }
 
-// The one-cluster power kernels when the warp-padded rows fit (sets *done);
-// the iterate and the warp partials take a fixed part of the opt-in shared
-// memory, the CSR entries the rest.
-static cpca_status power_cluster_launch(PowerBatchArgs& pa, bool reverse, cudaStream_t st, bool* done) {
+// Warp blocks of a graph list (graph g's first at pa.g[g].w0).
+static int assign_warp_blocks(PowerBatchArgs& pa) {
   int nvw = 0;
   for (int g = 0; g < pa.ngraph; ++g) {
     pa.g[g].w0 = nvw;
     nvw += (pa.g[g].L.n + 31) / 32;
   }
+  return nvw;
+}
+
+size_t power_scratch_bytes(const int* n, int ng) {
+  size_t nvw = 0;
+  for (int g = 0; g < ng; ++g) nvw += (size_t(n[g]) + 31) / 32;
+  return nvw * (2 * 32 * sizeof(float) + 4 * sizeof(double)) + 64;
+}
+
+// The power iterations of a graph list: the one-cluster kernels when the
+// warp blocks fit (the iterate and the warp sums take a fixed part of the
+// opt-in shared memory, the CSR entries the rest), else (forward only) the
+// grid-wide kernel on `scratch`. *done = false: reverse asked beyond one
+// cluster (nothing launched).
+static cpca_status power_launch(PowerBatchArgs& pa, bool reverse, void* scratch, cudaStream_t st, bool* done) {
+  const int nvw = assign_warp_blocks(pa);
   *done = false;
-  if (nvw > kPowMaxWarps) return CPCA_OK;
+  if (nvw > kPowMaxWarps) {
+    if (reverse) return CPCA_OK;
+    CPCA_CHECK_ARG(scratch, "power iterations: no scratch for %d warp blocks", nvw);
+    float* u = static_cast<float*>(scratch);
+    double* wq = reinterpret_cast<double*>(u + 2 * 32 * size_t(nvw));
+    double* rq = wq + 2 * size_t(nvw);
+    const int grid = std::min(2 * num_sms(), coop_blocks((const void*)power_batch_kernel, 512, 0, (nvw + 15) / 16));
+    int nv = nvw;
+    void* args[] = {&pa, &nv, &u, &wq, &rq};
+    CPCA_CUDA(cudaLaunchCooperativeKernel((const void*)power_batch_kernel, dim3(grid), dim3(512), args, 0, st));
+    CPCA_LAUNCHED();
+    *done = true;
+    return CPCA_OK;
+  }
   const size_t fixed = sizeof(double) * 4 * size_t(nvw) + sizeof(float) * 64 * size_t(nvw);
   const size_t psm = size_t(max_smem_optin());
   const int ell_cap = int((psm - fixed) / sizeof(int2));
@@ -867,13 +906,14 @@ bool power_tape_fits(const CsrView* L, int ng) {
   return nvw <= kPowMaxWarps;
 }
 
-cpca_status power_tape_run(const PowerTape* P, int ng, int T, uint64_t seed, bool reverse,
-                           cudaStream_t st) {
+cpca_status power_tape_run(const PowerTape* P, int ng, int T, uint64_t seed, bool reverse, void* scratch,
+                           unsigned int* bar, int* err, cudaStream_t st) {
   CPCA_CHECK_ARG(ng >= 1 && ng <= 2 * kMaxBatch, "power iterations: %d graphs", ng);
   std::unique_ptr<PowerBatchArgs> pa(new PowerBatchArgs{});
   pa->ngraph = ng;
   pa->iters = T;
   pa->seed = seed;
+  pa->bar = GridBar{bar, bar + kBarrierCounters, err};
   for (int g = 0; g < ng; ++g) {
     PowerGraph& G = pa->g[g];
     G.L = P[g].L;
@@ -884,9 +924,13 @@ cpca_status power_tape_run(const PowerTape* P, int ng, int T, uint64_t seed, boo
     G.Ub = P[g].Ub;
     G.rho_bar = P[g].rho_bar;
   }
+  if (bar) {
+    CPCA_CUDA(cudaMemsetAsync(bar, 0, sizeof(unsigned int) * (kBarrierCounters + 1), st));
+    CPCA_CUDA(cudaMemsetAsync(err, 0, sizeof(int), st));
+  }
   bool done = false;
-  CPCA_TRY(power_cluster_launch(*pa, reverse, st, &done));
-  CPCA_CHECK_ARG(done, "power iterations: rows exceed one cluster");
+  CPCA_TRY(power_launch(*pa, reverse, scratch, st, &done));
+  CPCA_CHECK_ARG(done, "power iterations: reverse mode needs the rows in one cluster");
   return CPCA_OK;
 }
 
@@ -898,25 +942,17 @@ cpca_status fista_batch_run(const BatchProblem* P, int n, int J, double eps, boo
   // power iterations (instances without a given step), then lambda
   PowerBatchArgs& pa = g_pa;
   pa.ngraph = 0;
-  int rows = 0;
   for (int i = 0; i < n; ++i) {
     if (P[i].step > 0) continue;
     for (int g = 0; g < 2; ++g) {
       PowerGraph& G = pa.g[pa.ngraph++];
+      G = PowerGraph{};
       G.L = g ? P[i].Lc : P[i].Lr;
-      G.u[0] = w.inst[i].pu[g][0];
-      G.u[1] = w.inst[i].pu[g][1];
-      G.acc = w.inst[i].pacc + 3 * g;
-      G.fin = w.inst[i].pacc + 6 + 2 * g;
       G.out = w.inst[i].scal + g;
       G.stream = 2 + g;
-      G.row0 = rows;
-      rows += G.L.n;
     }
-    CPCA_CUDA(cudaMemsetAsync(w.inst[i].pacc, 0, sizeof(double) * 10, st));
   }
   if (pa.ngraph > 0) {
-    pa.rows = rows;
     pa.iters = power_iters;
     pa.seed = power_seed;
     pa.bar = GridBar{w.bar, w.bar + kBarrierCounters, w.err};
@@ -924,16 +960,7 @@ cpca_status fista_batch_run(const BatchProblem* P, int n, int J, double eps, boo
     CPCA_CUDA(cudaMemsetAsync(w.err, 0, sizeof(int), st));
     bool done = false;
     CPCA_PROF("power_iter", st);
-    CPCA_TRY(power_cluster_launch(pa, false, st, &done));
-    if (!done) {
-      // one warp per row, at most one 512-thread block per SM
-      const int grid = std::min(num_sms(), coop_blocks((const void*)power_batch_kernel, 512, 0,
-                                                       (rows + 15) / 16));
-      void* args[] = {&pa};
-      CPCA_CUDA(cudaLaunchCooperativeKernel((const void*)power_batch_kernel, dim3(grid), dim3(512),
-                                            args, 0, st));
-      CPCA_LAUNCHED();
-    }
+    CPCA_TRY(power_launch(pa, false, w.pscr, st, &done));
   }
   {
     StepArgs sa{};

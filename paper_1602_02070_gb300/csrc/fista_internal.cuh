@@ -167,8 +167,6 @@ struct InstWs {
   float* ZT0;         // Z_j^T ping (column-major copy)
   float* ZT1;         // Z_j^T pong
   double* scal;       // [|Lr|, |Lc|, lambda, spare]
-  float* pu[2][2];    // power iteration vectors [graph][ping/pong]
-  double* pacc;       // power iteration norm rings [2][3] + quotients [2][2]
   double* stats;      // FISTA statistics ring [4][2]
   int* done;          // [stopped, iterations]
 };
@@ -179,6 +177,7 @@ struct BatchWs {
   int* err;           // barrier timeout flag
   double* part;       // objective partials
   double* obj;
+  void* pscr;         // power iteration scratch (power_scratch_bytes)
   InstWs inst[kMaxBatch];
   int n;
   size_t bytes;
@@ -220,8 +219,15 @@ struct PowerTape {
   const double* rho_bar;
 };
 bool power_tape_fits(const CsrView* L, int ng);
-cpca_status power_tape_run(const PowerTape* P, int ng, int T, uint64_t seed, bool reverse,
-                           cudaStream_t st);
+// Scratch of the grid-wide power kernel for graphs of these sizes (the
+// one-cluster kernel needs none).
+size_t power_scratch_bytes(const int* n, int ng);
+// Forward (reverse = false): the one-cluster kernel when the rows fit, else
+// the grid-wide kernel with the same arithmetic (scratch: power_scratch_bytes).
+// Reverse: one cluster only (returns CPCA_ERR_INVALID_ARG otherwise).
+// bar/err: grid-barrier state for the grid-wide kernel (zeroed here).
+cpca_status power_tape_run(const PowerTape* P, int ng, int T, uint64_t seed, bool reverse, void* scratch,
+                           unsigned int* bar, int* err, cudaStream_t st);
 int coop_blocks(const void* kernel, int threads, size_t smem, int want);
 // dloss/dL (FP64 on the CSR pattern) -> dloss/dw per entry (adjoint.cu);
 // deg and dD are scratch of L.n doubles each.

@@ -117,3 +117,65 @@ def test_transposed_problem_gives_the_transposed_solution():
     X = D.alternate_decode(q["Xt"], q["om_r"], q["om_c"], q["p"], q["n"], q["Lr"], q["Lc"], gr, gc)
     XT = D.alternate_decode(q["Xt"].T, q["om_c"], q["om_r"], q["n"], q["p"], q["Lc"], q["Lr"], gc, gr)
     np.testing.assert_allclose(XT, X.T, rtol=0, atol=1e-12)
+
+
+def test_pcg_mode_matches_the_direct_solve():
+    q = _problem(4, p=12, n=9, rr=5, rc=4)
+    X0 = D.alternate_decode(q["Xt"], q["om_r"], q["om_c"], q["p"], q["n"], q["Lr"], q["Lc"], 1.0, 1.0)
+    X1 = D.alternate_decode(q["Xt"], q["om_r"], q["om_c"], q["p"], q["n"], q["Lr"], q["Lc"], 1.0, 1.0, tol=1e-13)
+    np.testing.assert_allclose(X1, X0, rtol=0, atol=1e-10 * np.abs(X0).max())
+
+
+# ---------------------------------------------- approximate decoders 2 and 3
+def _lowrank(seed, p, n, r):
+    rng = np.random.default_rng(seed)
+    return rng.standard_normal((p, r)) @ rng.standard_normal((r, n))
+
+
+def _graph_of(points, K=4):
+    L, *_ = O.knn_graph(points, K)
+    return L
+
+
+@pytest.mark.parametrize("side", [0, 1])
+def test_projected_decoders_recover_exactly_lowrank_data_when_one_side_is_fully_sampled(side):
+    p, n, r = 30, 24, 3
+    Y = _lowrank(5, p, n, r)
+    Lr, Lc = _graph_of(Y), _graph_of(Y.T)
+    rng = np.random.default_rng(6)
+    if side == 0:   # every row sampled: U~ spans Y's column space, no upsampling
+        om_r, om_c = np.arange(p), np.sort(rng.choice(n, 10, replace=False))
+    else:           # every column sampled
+        om_r, om_c = np.sort(rng.choice(p, 12, replace=False)), np.arange(n)
+    Xt = Y[np.ix_(om_r, om_c)]
+    X, B, k = D.approx_decode_projected(Y, Xt, om_r, om_c, Lr, Lc, side, ratio=1e-6)
+    assert k == r
+    np.testing.assert_allclose(X, Y, rtol=0, atol=1e-10 * np.abs(Y).max())
+
+
+def test_decoder2_equals_the_papers_v_route():
+    """X = U Sigma~ c V^T with V = Y^T U Sigma~^-1 / c, c = sqrt(n p / (rho_r rho_c))."""
+    p, n = 28, 20
+    rng = np.random.default_rng(8)
+    Y = _lowrank(9, p, n, 4) + 0.01 * rng.standard_normal((p, n))
+    Lr, Lc = _graph_of(Y), _graph_of(Y.T)
+    om_r, om_c = np.sort(rng.choice(p, 14, replace=False)), np.sort(rng.choice(n, 10, replace=False))
+    Xt = Y[np.ix_(om_r, om_c)]
+    X, U, k = D.approx_decode_projected(Y, Xt, om_r, om_c, Lr, Lc, 0, tol=1e-12)
+    s = np.linalg.svd(Xt, compute_uv=False)[:k]
+    c = np.sqrt(n * p / (len(om_r) * len(om_c)))
+    V = Y.T @ U @ np.diag(1.0 / s) / c
+    np.testing.assert_allclose(X, U @ np.diag(s) @ V.T * c, rtol=0, atol=1e-10 * np.abs(X).max())
+
+
+def test_decoder3_is_decoder2_of_the_transposed_problem():
+    p, n = 26, 22
+    rng = np.random.default_rng(10)
+    Y = _lowrank(11, p, n, 3) + 0.01 * rng.standard_normal((p, n))
+    Lr, Lc = _graph_of(Y), _graph_of(Y.T)
+    om_r, om_c = np.sort(rng.choice(p, 12, replace=False)), np.sort(rng.choice(n, 11, replace=False))
+    Xt = Y[np.ix_(om_r, om_c)]
+    X3, _, k3 = D.approx_decode_projected(Y, Xt, om_r, om_c, Lr, Lc, 1, tol=1e-12)
+    X2t, _, k2 = D.approx_decode_projected(Y.T, Xt.T, om_c, om_r, Lc, Lr, 0, tol=1e-12)
+    assert k2 == k3
+    np.testing.assert_allclose(X3, X2t.T, rtol=0, atol=1e-9 * np.abs(X3).max())

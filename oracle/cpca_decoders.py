@@ -29,6 +29,21 @@ X = U U^T Y (decoder 2) or X = Y V V^T (decoder 3). Pinned by the exact
 recovery of exactly low-rank data when every row (column) is sampled, by
 the paper's V-route X = U Sigma~ c V^T with V = Y^T U Sigma~^-1 / c, and by
 the symmetry between the two decoders under transposition.
+
+Clustering decoder (Sec. V-D, Algorithm 3): k-means on the columns of X~
+(rho_c points in R^{rho_r}) gives one-hot labels C~ (rho_c x k); every
+column of C is the minimiser of c^T L_c c subject to c(Omega_c) = c~
+(Lemma 1, by PCG); each node takes the label of the largest entry of its
+row (ties: the lowest label). The paper does not say how k-means starts or
+stops; the reading is Lloyd's iteration from k distinct columns drawn with
+the sampling generator (stream KMEANS_STREAM, ascending index order),
+nearest centre by squared Euclidean distance (ties: the lowest centre),
+centres the means of their points (an empty cluster keeps its centre),
+until no assignment changes. Pinned by well-separated blobs (the
+generating partition, up to a relabelling), Lloyd's fixed point at the end
+(every point at its nearest centre, centres at their means), the
+non-increasing k-means objective, and graphs made of components whose
+sampled nodes share a label (every node of a component gets that label).
 """
 from __future__ import annotations
 
@@ -36,9 +51,12 @@ import numpy as np
 import scipy.sparse as sp
 import scipy.sparse.linalg as spla
 
-from .cpca_oracle import pcg, svd_rank, upsample_subspace
+from .cpca_oracle import pcg, sample_indices, svd_rank, upsample_subspace
 
-__all__ = ["selection_matrix", "alternate_objective", "alternate_decode", "approx_decode_projected"]
+__all__ = ["selection_matrix", "alternate_objective", "alternate_decode", "approx_decode_projected",
+           "kmeans_columns", "cluster_decode", "KMEANS_STREAM"]
+
+KMEANS_STREAM = 5  # SplitMix64 stream of the k-means initial centres
 
 
 def selection_matrix(omega: np.ndarray, N: int) -> sp.csr_matrix:
@@ -105,3 +123,42 @@ def approx_decode_projected(Y, Xt, omega_r, omega_c, Lr, Lc, side: int, ratio: f
     B = B / np.linalg.norm(B, axis=0, keepdims=True)
     X = B @ (B.T @ Y) if side == 0 else (Y @ B) @ B.T
     return X, B, k
+
+
+def kmeans_columns(Xt, k: int, seed: int = 0, max_iter: int = 100):
+    """Lloyd's k-means on the columns of X~ (see the module docstring).
+    Returns (labels (rho_c,), centres (k x rho_r), assignment steps,
+    objective after each assignment step)."""
+    P = np.asarray(Xt, dtype=np.float64).T  # rho_c points, one per row
+    m = P.shape[0]
+    C = P[sample_indices(seed, m, k, KMEANS_STREAM)].copy()
+    labels = None
+    objective = []
+    steps = 0
+    for _ in range(max_iter):
+        d = np.zeros((m, k))
+        for c in range(k):
+            diff = P - C[c]
+            d[:, c] = np.sum(diff * diff, axis=1)
+        new = np.argmin(d, axis=1)  # first minimum: the lowest centre on ties
+        steps += 1
+        objective.append(float(d[np.arange(m), new].sum()))
+        if labels is not None and np.array_equal(new, labels):
+            break
+        labels = new
+        for c in range(k):
+            members = labels == c
+            if members.any():
+                C[c] = P[members].mean(axis=0)
+    return labels, C, steps, objective
+
+
+def cluster_decode(Xt, omega_c, n: int, Lc, k: int, seed: int = 0, tol: float = 1e-6,
+                   kmeans_iters: int = 100, maxit: int | None = None):
+    """Algorithm 3. Returns (labels (n,), C (n x k), k-means labels of X~'s
+    columns)."""
+    lab_t, _, _, _ = kmeans_columns(Xt, k, seed, kmeans_iters)
+    Ct = np.zeros((len(lab_t), k))
+    Ct[np.arange(len(lab_t)), lab_t] = 1.0
+    C, _, _ = upsample_subspace(Lc, omega_c, Ct, tol, maxit)
+    return np.argmax(C, axis=1), C, lab_t

@@ -179,3 +179,71 @@ def test_decoder3_is_decoder2_of_the_transposed_problem():
     X2t, _, k2 = D.approx_decode_projected(Y.T, Xt.T, om_c, om_r, Lc, Lr, 0, tol=1e-12)
     assert k2 == k3
     np.testing.assert_allclose(X3, X2t.T, rtol=0, atol=1e-9 * np.abs(X3).max())
+
+
+# ------------------------------------------------------ clustering decoder
+def _blobs(seed, sizes, dim, sep=20.0):
+    rng = np.random.default_rng(seed)
+    centres = rng.standard_normal((len(sizes), dim)) * sep
+    pts, lab = [], []
+    for c, s in enumerate(sizes):
+        pts.append(centres[c] + rng.standard_normal((s, dim)))
+        lab += [c] * s
+    perm = rng.permutation(sum(sizes))
+    return np.concatenate(pts)[perm], np.array(lab)[perm]
+
+
+def _same_partition(a, b):
+    pairs = set(zip(a.tolist(), b.tolist()))
+    return len(pairs) == len(set(a.tolist())) == len(set(b.tolist()))
+
+
+def test_kmeans_finds_well_separated_blobs():
+    P, truth = _blobs(1, [30, 25, 40], 6)
+    labels, C, steps, obj = D.kmeans_columns(P.T, 3, seed=2)
+    assert _same_partition(labels, truth)
+
+
+def test_kmeans_ends_at_lloyds_fixed_point_with_non_increasing_objective():
+    rng = np.random.default_rng(3)
+    P = rng.standard_normal((60, 4))  # no cluster structure: a real local search
+    labels, C, steps, obj = D.kmeans_columns(P.T, 5, seed=4)
+    assert all(b <= a + 1e-12 for a, b in zip(obj, obj[1:]))
+    for i in range(len(P)):
+        d = ((C - P[i]) ** 2).sum(axis=1)
+        assert d[labels[i]] <= d.min() + 1e-12
+    for c in range(5):
+        if (labels == c).any():
+            np.testing.assert_allclose(C[c], P[labels == c].mean(axis=0), atol=1e-12)
+
+
+def test_cluster_decoder_labels_whole_components():
+    """L_c with three components, each with sampled nodes of one cluster:
+    the harmonic extension is constant on a component, so every node takes
+    its component's label."""
+    rng = np.random.default_rng(5)
+    sizes = [12, 9, 15]
+    n = sum(sizes)
+    W = np.zeros((n, n))
+    start = 0
+    comp = np.zeros(n, int)
+    for c, s in enumerate(sizes):
+        idx = np.arange(start, start + s)
+        comp[idx] = c
+        for a in range(s):                       # a path plus chords inside the component
+            if a + 1 < s:
+                W[idx[a], idx[a + 1]] = W[idx[a + 1], idx[a]] = rng.uniform(0.5, 1)
+        for _ in range(s):
+            a, b = rng.choice(idx, 2, replace=False)
+            W[a, b] = W[b, a] = rng.uniform(0.5, 1)
+        start += s
+    Lc = O.laplacian_from_weights(sp.csr_matrix(W))
+    om_c = np.sort(np.concatenate([np.arange(0, 12, 3), np.arange(12, 21, 3), np.arange(21, 36, 3)]))
+    # sampled columns of X~: three far-apart blobs, one per component
+    centres = np.array([[10.0, 0, 0], [0, 10.0, 0], [0, 0, 10.0]])
+    Xt = (centres[comp[om_c]] + 0.1 * rng.standard_normal((len(om_c), 3))).T
+    labels, C, lab_t = D.cluster_decode(Xt, om_c, n, Lc, 3, seed=1, tol=1e-12)
+    np.testing.assert_array_equal(labels[om_c], lab_t)
+    for c in range(3):
+        assert len(set(labels[comp == c].tolist())) == 1
+    assert _same_partition(labels, comp)

@@ -444,6 +444,49 @@ cpca_status cpca_decode_entries(const float* U, const float* V, int32_t ld, cons
                                 float* out, void* stream);
 
 /* ------------------------------------------------------------------------
+ * cpca_cluster_decode - the clustering decoder (Sec. V-D, Algorithm 3).
+ *
+ * 1. k-means on the columns of Xt (rc points in R^rr): Lloyd's iteration
+ *    from the k columns that the sampling generator picks on SplitMix64
+ *    stream 5 with `seed` (ascending), nearest centre by squared Euclidean
+ *    distance (ties: the lowest centre), centres the means of their points
+ *    (an empty cluster keeps its centre), until an assignment step changes
+ *    no label or after kmeans_iters steps (the paper leaves the start and
+ *    the stop open);
+ * 2. each column of C (n x k) is the minimiser of c^T L_c c subject to
+ *    c(omega_c) = the one-hot k-means labels (Lemma 1), by Jacobi PCG to
+ *    cg_tol (cg_max_iter <= 0: 10 x unsampled nodes);
+ * 3. labels[i] = the column of row i's largest entry (ties: the lowest).
+ * Xt: rr x rc (ldxt), omega_c: rc sampled columns of the n-node graph Lc
+ * (ascending, distinct), all device. Outputs (device): labels (n int32);
+ * optional labels_t (rc int32, the k-means labels) and C (n x k FP32).
+ * 1 <= k <= min(48, rc). Workspace:
+ * cpca_cluster_decode_workspace_size(rr, rc, n, k, nnz of Lc).
+ * SYNCHRONISES. Returns CPCA_ERR_SINGULAR if a component of Lc holds no
+ * sampled node, CPCA_ERR_NOT_CONVERGED if the PCG hit its cap (labels
+ * still written), CPCA_ERR_TIMEOUT if a device barrier gave up.
+ * ---------------------------------------------------------------------- */
+typedef struct cpca_cluster_params {
+  int32_t k;             /* clusters */
+  int32_t kmeans_iters;  /* assignment steps at most (>= 1) */
+  uint64_t seed;         /* initial centres */
+  double cg_tol;         /* relative residual of the harmonic extension */
+  int32_t cg_max_iter;
+} cpca_cluster_params;
+
+typedef struct cpca_cluster_info {
+  int32_t kmeans_steps;  /* assignment steps taken */
+  int32_t cg_iters;      /* largest PCG iteration count over the k columns */
+  double cg_res;         /* largest final relative residual */
+} cpca_cluster_info;
+
+size_t cpca_cluster_decode_workspace_size(int32_t rr, int32_t rc, int32_t n, int32_t k, int64_t nnz_c);
+cpca_status cpca_cluster_decode(const float* Xt, int32_t rr, int32_t rc, int64_t ldxt, const int32_t* omega_c,
+                                int32_t n, const cpca_csr* Lc, const cpca_cluster_params* params,
+                                int32_t* labels, int32_t* labels_t, float* C, cpca_cluster_info* info,
+                                void* ws, size_t ws_bytes, void* stream);
+
+/* ------------------------------------------------------------------------
  * cpca_subspace_project - the approximate decoders 2 and 3 (appendix,
  * "Other Approximate Decoders"): when the full data Y is available, only one
  * subspace is upsampled and X is a projection of Y:

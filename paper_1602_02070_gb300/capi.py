@@ -78,6 +78,15 @@ class cpca_decode_info(C.Structure):
                 ("s_tilde", C.c_double * 64), ("b", C.c_int32)]
 
 
+class cpca_cluster_params(C.Structure):
+    _fields_ = [("k", C.c_int32), ("kmeans_iters", C.c_int32), ("seed", C.c_uint64), ("cg_tol", C.c_double),
+                ("cg_max_iter", C.c_int32)]
+
+
+class cpca_cluster_info(C.Structure):
+    _fields_ = [("kmeans_steps", C.c_int32), ("cg_iters", C.c_int32), ("cg_res", C.c_double)]
+
+
 class cpca_alt_params(C.Structure):
     _fields_ = [("gamma_r", C.c_double), ("gamma_c", C.c_double), ("tol", C.c_double),
                 ("max_iter", C.c_int32), ("blocks", C.c_int32)]
@@ -154,6 +163,11 @@ _SIGS = [
       C.POINTER(cpca_csr), C.POINTER(cpca_csr), C.POINTER(cpca_decode_params), C.c_void_p,
       C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(C.c_int32),
       C.POINTER(cpca_decode_info), C.c_void_p, C.c_size_t, C.c_void_p]),
+    ("cpca_cluster_decode_workspace_size", C.c_size_t, [C.c_int32] * 4 + [C.c_int64]),
+    ("cpca_cluster_decode", C.c_int32,
+     [C.c_void_p, C.c_int32, C.c_int32, C.c_int64, C.c_void_p, C.c_int32, C.POINTER(cpca_csr),
+      C.POINTER(cpca_cluster_params), C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(cpca_cluster_info),
+      C.c_void_p, C.c_size_t, C.c_void_p]),
     ("cpca_subspace_project_workspace_size", C.c_size_t, [C.c_int32, C.c_int32, C.c_int32]),
     ("cpca_subspace_project", C.c_int32,
      [C.c_int32, C.c_void_p, C.c_int32, C.c_int32, C.c_void_p, C.c_int64, C.c_int32, C.c_int32, C.c_void_p,
@@ -515,6 +529,30 @@ def cpca_decode(Xt: torch.Tensor, omega_r: torch.Tensor, omega_c: torch.Tensor, 
     kk = k.value
     return {"X": X, "U": U[:, :kk], "V": V[:, :kk], "sigma": sig[:kk], "k": kk, "info": info,
             "status": st}
+
+
+def cpca_cluster_decode(Xt: torch.Tensor, omega_c: torch.Tensor, n: int, Lc: Csr, k: int,
+                        kmeans_iters: int = 100, seed: int = 0, cg_tol: float = 1e-6, cg_max_iter: int = 0,
+                        want_C: bool = False, ws=None, check_status: bool = True):
+    """Clustering decoder (Algorithm 3). Returns dict labels (n), labels_t
+    (the k-means labels of Xt's columns), C (n x k or None), info, status."""
+    _require_cuda(Xt, torch.float32, "Xt")
+    rr, rc = Xt.shape
+    dev = Xt.device
+    prm = cpca_cluster_params(k, kmeans_iters, seed, cg_tol, cg_max_iter)
+    labels = torch.empty(n, dtype=torch.int32, device=dev)
+    labels_t = torch.empty(rc, dtype=torch.int32, device=dev)
+    Cm = torch.empty(n, k, dtype=torch.float32, device=dev) if want_C else None
+    if ws is None:
+        ws = _workspace(lib().cpca_cluster_decode_workspace_size(rr, rc, n, k, Lc.nnz), dev)
+    info = cpca_cluster_info()
+    lc = Lc.c()
+    st = lib().cpca_cluster_decode(_ptr(Xt), rr, rc, Xt.stride(0), _ptr(omega_c), n, C.byref(lc), C.byref(prm),
+                                   _ptr(labels), _ptr(labels_t), _ptr(Cm), C.byref(info), _ptr(ws), ws.numel(),
+                                   _stream())
+    if check_status:
+        _check(st)
+    return {"labels": labels, "labels_t": labels_t, "C": Cm, "info": info, "status": st}
 
 
 def cpca_subspace_project(side: int, basis: torch.Tensor, k: int, Y: torch.Tensor,

@@ -999,7 +999,7 @@ static cpca_status partial_svd(const float* Xt, int rr, int rc, int64_t ldxt, in
 static cpca_status cg_setup(CgArgs& a, const cpca_csr* Lr, const cpca_csr* Lc, const int32_t* omega_r,
                             const int32_t* omega_c, int p, int n, int rr, int rc, int k, int b,
                             const cpca_decode_params* prm, const DecodeWs& w, cudaStream_t st,
-                            bool index_maps = true) {
+                            bool index_maps = true, int sides = 3) {
   const CsrView lr{Lr->n, Lr->rowptr, Lr->col, Lr->val};
   const CsrView lc{Lc->n, Lc->rowptr, Lc->col, Lc->val};
   const int m[2] = {p - rr, n - rc};
@@ -1027,6 +1027,11 @@ static cpca_status cg_setup(CgArgs& a, const cpca_csr* Lr, const cpca_csr* Lc, c
     S.p1 = w.vec[sd][4];
     S.q = w.vec[sd][5];
     a.maxit[sd] = prm->cg_max_iter > 0 ? prm->cg_max_iter : 10 * std::max(m[sd], 1);
+    if (!((sides >> sd) & 1)) {  // side left out: no nodes, no unknowns
+      S.N = 0;
+      S.rho = 0;
+      S.m = 0;
+    }
   }
   a.k = k;
   a.tol = prm->cg_tol;
@@ -1081,6 +1086,52 @@ static cpca_status cg_solve(CgArgs& a, const DecodeWs& w, cudaStream_t st, int* 
   }
   return CPCA_OK;
 }
+// Lemma 1 on one graph for k given boundary columns: the minimiser of
+// tr(S^T L S) subject to S(omega, :) = R (rho x k, ld ldr), by the decoder's
+// Jacobi PCG (only its second side). Writes S (N x ldo, first k columns).
+size_t harmonic_ws_bytes(int N, int rho, int k, int64_t nnz) {
+  return decode_layout(nullptr, 1, N, 1, rho, k, 0, nnz).bytes;
+}
+
+cpca_status harmonic_extend(const cpca_csr* L, const int32_t* omega, int N, int rho, const float* R, int ldr,
+                            int k, double tol, int maxit, float* S, int ldo, int* iters_max, double* res_max,
+                            void* ws, cudaStream_t st) {
+  CPCA_CHECK_ARG(k >= 1 && k <= KMAX_LIMIT && ldo >= k && ldr >= k, "harmonic extension: k %d", k);
+  const DecodeWs w = decode_layout(ws, 1, N, 1, rho, k, 0, L->nnz);
+  cpca_decode_params prm{};
+  prm.cg_tol = tol;
+  prm.cg_max_iter = maxit;
+  prm.kmax = k;
+  CgArgs a{};
+  CPCA_TRY(cg_setup(a, L, L, omega, omega, 1, N, 1, rho, k, ldr, &prm, w, st, true, 2));
+  a.s[1].R = R;
+  a.s[1].ldr = ldr;
+  int cg_iters[2 * KMAX_LIMIT] = {0};
+  double cg_res[2 * KMAX_LIMIT] = {0};
+  int breakdown = 0;
+  CPCA_TRY(cg_solve(a, w, st, cg_iters, cg_res, &breakdown));
+  const unsigned g = std::min<unsigned>(ceil_div(int64_t(N) * ldo, 256), num_sms() * 8);
+  assemble_side_kernel<<<g, 256, 0, st>>>(N, k, ldo, w.pos1, R, ldr, w.vec[1][0], S);
+  CPCA_LAUNCHED();
+  int it = 0;
+  double rs = 0.0;
+  for (int c = 0; c < k; ++c) {
+    it = std::max(it, cg_iters[KMAX_LIMIT + c]);
+    rs = std::max(rs, cg_res[KMAX_LIMIT + c]);
+  }
+  if (iters_max) *iters_max = it;
+  if (res_max) *res_max = rs;
+  if (breakdown & 2) {
+    set_error("harmonic extension: a connected component holds no sampled node");
+    return CPCA_ERR_SINGULAR;
+  }
+  if (rs > tol) {
+    set_error("harmonic extension: PCG stopped at relative residual %g", rs);
+    return CPCA_ERR_NOT_CONVERGED;
+  }
+  return CPCA_OK;
+}
+
 }  // namespace cpca
 
 using namespace cpca;

@@ -219,6 +219,17 @@ struct PowerTape {
   const double* rho_bar;
 };
 bool power_tape_fits(const CsrView* L, int ng);
+// Lemma 1 on one graph (decode.cu): S (N x ldo) with S(omega, :) = R and
+// (L S)(complement, :) = 0, by Jacobi PCG to tol; workspace
+// harmonic_ws_bytes(N, rho, k, nnz of L).
+size_t harmonic_ws_bytes(int N, int rho, int k, int64_t nnz);
+cpca_status harmonic_extend(const cpca_csr* L, const int32_t* omega, int N, int rho, const float* R, int ldr,
+                            int k, double tol, int maxit, float* S, int ldo, int* iters_max, double* res_max,
+                            void* ws, cudaStream_t st);
+// rho of [0, N) by the sampling generator on SplitMix64 stream `stream`
+// (sample.cu), ascending.
+cpca_status select_indices(uint64_t seed, int N, int rho, int stream, int32_t* out, cudaStream_t st);
+
 // Scratch of the grid-wide power kernel for graphs of these sizes (the
 // one-cluster kernel needs none).
 size_t power_scratch_bytes(const int* n, int ng);

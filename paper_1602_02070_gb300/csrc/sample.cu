@@ -32,12 +32,12 @@ __device__ int block_exscan(int v, int* sh, int* out) {
 
 __global__ void __launch_bounds__(kSelThreads)
 sample_select_kernel(uint64_t seed, int p, int n, int rho_r, int rho_c,
-                     int32_t* __restrict__ omega_r, int32_t* __restrict__ omega_c) {
+                     int32_t* __restrict__ omega_r, int32_t* __restrict__ omega_c, int stream0) {
   const int side = blockIdx.x;
   const int N = side == 0 ? p : n;
   const int rho = side == 0 ? rho_r : rho_c;
   int32_t* out = side == 0 ? omega_r : omega_c;
-  const uint64_t s0 = stream_state0(seed, side);
+  const uint64_t s0 = stream_state0(seed, stream0 + side);
   const int tid = threadIdx.x;
 
   __shared__ int hist[256];
@@ -116,7 +116,13 @@ __global__ void gather_kernel(const float* __restrict__ Y, int64_t ldy,
 cpca_status sample_indices(uint64_t seed, int p, int n, int rho_r, int rho_c,
                            int32_t* om_r, int32_t* om_c, cudaStream_t st) {
   CPCA_PROF("sample_select", st);
-  sample_select_kernel<<<2, kSelThreads, 0, st>>>(seed, p, n, rho_r, rho_c, om_r, om_c);
+  sample_select_kernel<<<2, kSelThreads, 0, st>>>(seed, p, n, rho_r, rho_c, om_r, om_c, 0);
+  CPCA_LAUNCHED();
+  return CPCA_OK;
+}
+
+cpca_status select_indices(uint64_t seed, int N, int rho, int stream, int32_t* out, cudaStream_t st) {
+  sample_select_kernel<<<1, kSelThreads, 0, st>>>(seed, N, 0, rho, 0, out, nullptr, stream);
   CPCA_LAUNCHED();
   return CPCA_OK;
 }

@@ -13,4 +13,5 @@ closed forms, textbook routines, invariants or brute force.
 """
 from .cpca_oracle import *  # noqa: F401,F403
 from . import cpca_adjoint  # noqa: F401  (reverse-mode derivatives, FP64)
-from . import cpca_decoders  # noqa: F401  (alternate decoder, Sec. V-B)
+from . import cpca_decoders  # noqa: F401  (alternate, projected and clustering decoders)
+from . import cpca_kron  # noqa: F401  (Kron-reduced compressed Laplacians, Sec. IV-A)

@@ -10,11 +10,11 @@ and elsewhere the GPU's label is one of the tied candidates.
 """
 import numpy as np
 import pytest
-import scipy.sparse as sp
 
 import gen
 import oracle as O
 from oracle import cpca_decoders as D
+from tests._oracle_pool import OraclePool
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -58,18 +58,20 @@ def test_cluster_decoder_matches_oracle(M, p, n, C, rr, rc, frac):
 
 
 def test_cluster_decoder_full_size(M):
-    """10304 x 1000 (10 clusters of columns), X~ 2576 x 250, the CUDA graph
-    of Y's columns (1000 nodes), k = 10."""
+    """10304 x 1000 (10 clusters of columns), X~ 2576 x 250, k = 10: the
+    oracle's column graph (1000 nodes) and sampled matrix feed both sides."""
     cfg = gen.CONFIGS["c1"]
     p, n = cfg["p"], cfg["n"]
-    Yd = gen.make_instance_torch(0, p, n, cfg["r"], cfg["C"], cfg["frac"], device="cuda")
-    Lc, _, _ = M.cpca_knn_graph(Yd, cfg["K"], transposed=True)
+    Y, _, _ = gen.make_instance(0, p, n, cfg["r"], cfg["C"], cfg["frac"])
+    pool = OraclePool()
+    try:
+        Lc, _, _, _ = pool.knn_graph(Y.T.astype(np.float64), cfg["K"])
+    finally:
+        pool.close()
     rr, rc = M.rho_of(p, cfg["fr"]), M.rho_of(n, cfg["fc"])
-    om_r, om_c, Yt = M.cpca_sample(0, p, n, rr, rc, Yd)
-    out = M.cpca_cluster_decode(Yt, om_c, n, Lc, cfg["C"], seed=1)
-    Lc_np = sp.csr_matrix((Lc.val.cpu().numpy().astype(np.float64), Lc.col.cpu().numpy(), Lc.rowptr.cpu().numpy()),
-                          shape=(n, n))
-    lab_o, C_o, labt_o = D.cluster_decode(Yt.cpu().numpy(), om_c.cpu().numpy(), n, Lc_np, cfg["C"], seed=1,
-                                          tol=1e-10)
+    om_r, om_c = O.sample_indices(0, p, rr, 0), O.sample_indices(0, n, rc, 1)
+    Xt = O.sample_matrix(Y.astype(np.float64), om_r, om_c)
+    out = M.cpca_cluster_decode(_dev(Xt), _dev(om_c, np.int32), n, M.Csr.from_scipy(Lc), cfg["C"], seed=1)
+    lab_o, C_o, labt_o = D.cluster_decode(Xt, om_c, n, Lc, cfg["C"], seed=1, tol=1e-10)
     assert np.array_equal(out["labels_t"].cpu().numpy(), labt_o)
     _check_labels(out["labels"].cpu().numpy(), C_o)

@@ -546,6 +546,45 @@ cpca_status cpca_alternate_decode(const float* Xt, int32_t rr, int32_t rc, int64
                                   float* X, int64_t ldx, cpca_alt_info* info, void* ws, size_t ws_bytes,
                                   void* stream);
 
+/* ------------------------------------------------------------------------
+ * cpca_kron_reduce - compressed Laplacian by Kron reduction (Sec. IV-A,
+ * "Graphs for Compressed data"), the alternative to new kNN graphs on Y~:
+ *   L~ = L(O, O) - L(O, Ob) L(Ob, Ob)^-1 L(Ob, O),
+ * the Schur complement of the unsampled block Ob onto the sampled nodes O.
+ * Column j of L~ is (L h_j)(O), h_j the harmonic extension (Lemma 1) of the
+ * unit vector e_j given on O; the extensions are solved by the decoder's
+ * Jacobi PCG, up to 48 columns per launch, to relative residual tol
+ * (max_iter <= 0: 10 x unsampled nodes), and (L h_j)(O) is summed in FP64.
+ * The result is symmetrised ((L~ + L~^T) / 2, the PCG leaves it symmetric
+ * only to its tolerance). It is dense in general: two kept nodes are coupled
+ * when a path joins them through unsampled nodes (Theorem III.4 of the
+ * paper's reference on Kron reduction); entries with no such path are
+ * exactly 0.
+ *
+ * L: symmetric Laplacian CSR on n nodes (normalised or combinatorial, the
+ * reduction does not care), device; omega: rho sampled nodes, device int32,
+ * strictly ascending, in [0, n) (checked: CPCA_ERR_INVALID_ARG); 1 <= rho
+ * <= n. Lt: rho x rho FP32 row-major (leading dimension ldlt >= rho),
+ * device, written. Optional rowptr (rho + 1 int64), col (rho^2 int32), val
+ * (rho^2 FP32), device, all three or none: L~ again as CSR with every entry
+ * stored, ready for cpca_frpcag_solve. Workspace:
+ * cpca_kron_reduce_workspace_size(n, rho, nnz of L). SYNCHRONISES (once for
+ * the index check, once per chunk of 48 columns). Returns CPCA_ERR_SINGULAR
+ * if a connected component holds no sampled node (L(Ob, Ob) is singular),
+ * CPCA_ERR_NOT_CONVERGED if a PCG column hit its cap (Lt still written),
+ * CPCA_ERR_TIMEOUT if a device barrier gave up.
+ * ---------------------------------------------------------------------- */
+typedef struct cpca_kron_info {
+  int32_t chunks;    /* PCG launches (ceil(rho / 48)) */
+  int32_t cg_iters;  /* largest PCG iteration count over all columns */
+  double cg_res;     /* largest final relative residual */
+} cpca_kron_info;
+
+size_t cpca_kron_reduce_workspace_size(int32_t n, int32_t rho, int64_t nnz);
+cpca_status cpca_kron_reduce(const cpca_csr* L, const int32_t* omega, int32_t rho, double tol, int32_t max_iter,
+                             float* Lt, int64_t ldlt, int64_t* rowptr, int32_t* col, float* val,
+                             cpca_kron_info* info, void* ws, size_t ws_bytes, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

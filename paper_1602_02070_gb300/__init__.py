@@ -7,7 +7,7 @@ from .capi import (CPCA_ERR_CAPACITY, CPCA_ERR_CUDA, CPCA_ERR_INVALID_ARG,  # no
                    CPCA_ERR_NOT_CONVERGED, CPCA_ERR_SINGULAR, CPCA_ERR_TIMEOUT,
                    CPCA_ERR_WORKSPACE, CPCA_OK, LAP_COMBINATORIAL, LAP_NORMALIZED, Batch, CpcaError, Csr,
                    alt_params, cpca_alternate_decode, cpca_cluster_decode, cpca_decode, cpca_subspace_project, cpca_decode_backward, cpca_frpcag_backward, cpca_frpcag_solve, cpca_frpcag_solve_noalloc,
-                   cpca_knn_graph, cpca_sample, decode_params,
+                   cpca_knn_graph, cpca_kron_reduce, cpca_sample, decode_params,
                    exported_names, frpcag_params, knn_last_bruteforce, launch_count, lib,
                    profile_enable,
                    profile_read)

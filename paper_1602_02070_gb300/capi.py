@@ -96,6 +96,10 @@ class cpca_alt_info(C.Structure):
     _fields_ = [("iters", C.c_int32), ("converged", C.c_int32), ("rel_res", C.c_double)]
 
 
+class cpca_kron_info(C.Structure):
+    _fields_ = [("chunks", C.c_int32), ("cg_iters", C.c_int32), ("cg_res", C.c_double)]
+
+
 _lib = None
 
 # (name, restype, argtypes) of every exported entry point in include/cpca.h
@@ -177,6 +181,10 @@ _SIGS = [
      [C.c_void_p, C.c_int32, C.c_int32, C.c_int64, C.c_void_p, C.c_void_p, C.c_int32, C.c_int32,
       C.POINTER(cpca_csr), C.POINTER(cpca_csr), C.POINTER(cpca_alt_params), C.c_void_p, C.c_int64,
       C.POINTER(cpca_alt_info), C.c_void_p, C.c_size_t, C.c_void_p]),
+    ("cpca_kron_reduce_workspace_size", C.c_size_t, [C.c_int32, C.c_int32, C.c_int64]),
+    ("cpca_kron_reduce", C.c_int32,
+     [C.POINTER(cpca_csr), C.c_void_p, C.c_int32, C.c_double, C.c_int32, C.c_void_p, C.c_int64, C.c_void_p,
+      C.c_void_p, C.c_void_p, C.POINTER(cpca_kron_info), C.c_void_p, C.c_size_t, C.c_void_p]),
 ]
 
 
@@ -594,6 +602,31 @@ def cpca_alternate_decode(Xt: torch.Tensor, omega_r: torch.Tensor, omega_c: torc
     if check_status:
         _check(st)
     return X, info, st
+
+
+def cpca_kron_reduce(L: Csr, omega: torch.Tensor, tol: float = 1e-6, max_iter: int = 0, want_csr: bool = True,
+                     ws=None, check_status: bool = True):
+    """Kron reduction of L onto the sampled nodes omega (Sec. IV-A).
+    Returns dict Lt (rho x rho dense), csr (Csr with every entry stored, or
+    None), info, status."""
+    _require_cuda(L.val, torch.float32, "L.val")
+    rho = omega.numel()
+    dev = L.val.device
+    Lt = torch.empty(rho, rho, dtype=torch.float32, device=dev)
+    rp = col = val = None
+    if want_csr:
+        rp = torch.empty(rho + 1, dtype=torch.int64, device=dev)
+        col = torch.empty(rho * rho, dtype=torch.int32, device=dev)
+        val = torch.empty(rho * rho, dtype=torch.float32, device=dev)
+    if ws is None:
+        ws = _workspace(lib().cpca_kron_reduce_workspace_size(L.n, rho, L.nnz), dev)
+    info = cpca_kron_info()
+    lc = L.c()
+    st = lib().cpca_kron_reduce(C.byref(lc), _ptr(omega), rho, tol, max_iter, _ptr(Lt), Lt.stride(0), _ptr(rp),
+                                _ptr(col), _ptr(val), C.byref(info), _ptr(ws), ws.numel(), _stream())
+    if check_status:
+        _check(st)
+    return {"Lt": Lt, "csr": Csr(rp, col, val) if want_csr else None, "info": info, "status": st}
 
 
 def decode_backward_workspace(Xt: torch.Tensor, p: int, n: int, Lr: Csr, Lc: Csr,

@@ -1132,6 +1132,96 @@ cpca_status harmonic_extend(const cpca_csr* L, const int32_t* omega, int N, int 
   return CPCA_OK;
 }
 
+// ---------------------------------------------------------- Kron reduction --
+// L~ = L(O, O) - L(O, Ob) L(Ob, Ob)^-1 L(Ob, O) (Sec. IV-A) column by column:
+// column j of L~ is (L h_j)(O), h_j the harmonic extension of the unit vector
+// e_j given on the sampled nodes (h_j = e_j on O, -L_aa^-1 L_ab e_j on Ob).
+// Chunks of up to KMAX_LIMIT columns go through the decoder's PCG at once.
+
+// Sampled nodes strictly ascending and in [0, N).
+__global__ void kron_omega_check_kernel(const int32_t* __restrict__ omega, int rho, int N, int* __restrict__ bad) {
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < rho; t += gridDim.x * blockDim.x) {
+    const int v = omega[t];
+    if (v < 0 || v >= N || (t > 0 && omega[t - 1] >= v)) atomicOr(bad, 1);
+  }
+}
+
+// R (rho x ldr): columns j0 .. j0 + kcur - 1 of the rho x rho identity, the
+// rest of each row zero.
+__global__ void kron_identity_kernel(float* __restrict__ R, int rho, int ldr, int j0, int kcur) {
+  const int64_t total = int64_t(rho) * ldr;
+  for (int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; t < total; t += int64_t(gridDim.x) * blockDim.x) {
+    const int i = int(t / ldr), c = int(t % ldr);
+    R[t] = (c < kcur && i == j0 + c) ? 1.f : 0.f;
+  }
+}
+
+// Lt(i, j0 + c) = sum over row omega[i] of L of L(omega[i], t) h_c(t), with
+// h_c(t) = x(pos[t], c) on unsampled t and [t is sampled node j0 + c] on
+// sampled t; FP64 sum in CSR order.
+__global__ void kron_cols_kernel(CsrView L, const int32_t* __restrict__ omega, const int32_t* __restrict__ pos,
+                                 const float* __restrict__ x, int rho, int kcur, int j0, float* __restrict__ Lt,
+                                 int64_t ldlt) {
+  const int64_t total = int64_t(rho) * kcur;
+  for (int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; t < total; t += int64_t(gridDim.x) * blockDim.x) {
+    const int i = int(t / kcur), c = int(t % kcur);
+    const int node = omega[i];
+    double v = 0.0;
+    for (int64_t e = L.rowptr[node]; e < L.rowptr[node + 1]; ++e) {
+      const int ps = pos[L.col[e]];
+      const double h = ps >= 0 ? double(x[int64_t(ps) * kcur + c]) : ((-ps - 1) == j0 + c ? 1.0 : 0.0);
+      v += double(L.val[e]) * h;
+    }
+    Lt[int64_t(i) * ldlt + j0 + c] = float(v);
+  }
+}
+
+// Lt <- (Lt + Lt^T) / 2 in place: the thread of (i, j), i < j, owns the pair.
+__global__ void kron_sym_kernel(float* __restrict__ Lt, int64_t ld, int rho) {
+  const int64_t total = int64_t(rho) * rho;
+  for (int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; t < total; t += int64_t(gridDim.x) * blockDim.x) {
+    const int i = int(t / rho), j = int(t % rho);
+    if (i < j) {
+      float* a = Lt + int64_t(i) * ld + j;
+      float* b = Lt + int64_t(j) * ld + i;
+      const float m = 0.5f * (*a + *b);
+      *a = m;
+      *b = m;
+    }
+  }
+}
+
+// The dense rho x rho matrix as CSR with every entry stored.
+__global__ void kron_csr_kernel(const float* __restrict__ Lt, int64_t ld, int rho, int64_t* __restrict__ rowptr,
+                                int32_t* __restrict__ col, float* __restrict__ val) {
+  const int64_t total = int64_t(rho) * rho;
+  const int64_t g0 = blockIdx.x * int64_t(blockDim.x) + threadIdx.x, gs = int64_t(gridDim.x) * blockDim.x;
+  for (int64_t t = g0; t < total; t += gs) {
+    const int i = int(t / rho), j = int(t % rho);
+    col[t] = j;
+    val[t] = Lt[int64_t(i) * ld + j];
+  }
+  for (int64_t t = g0; t <= rho; t += gs) rowptr[t] = t * rho;
+}
+
+struct KronWs {
+  DecodeWs d;
+  float* R;
+  int* bad;
+  size_t bytes;
+};
+
+static KronWs kron_layout(void* ws, int N, int rho, int64_t nnz) {
+  const int kc = std::min(rho, KMAX_LIMIT);
+  KronWs k{};
+  k.d = decode_layout(ws, 1, N, 1, rho, kc, 0, nnz);
+  Carve c(ws ? static_cast<char*>(ws) + k.d.bytes : nullptr);
+  k.R = c.take<float>(size_t(rho) * kc);
+  k.bad = c.take<int>(1);
+  k.bytes = k.d.bytes + c.bytes();
+  return k;
+}
+
 }  // namespace cpca
 
 using namespace cpca;
@@ -1973,5 +2063,91 @@ extern "C" cpca_status cpca_decode_entries(const float* U, const float* V, int32
   entries_kernel<<<std::min<unsigned>(ceil_div(nh, 256), num_sms() * 4), 256, 0,
                    static_cast<cudaStream_t>(stream)>>>(nh, h_row, h_col, U, ld, V, ld, sigma, k, out);
   CPCA_LAUNCHED();
+  return CPCA_OK;
+}
+
+extern "C" size_t cpca_kron_reduce_workspace_size(int32_t N, int32_t rho, int64_t nnz) {
+  if (N <= 0 || rho <= 0 || rho > N || nnz < 0) return 0;
+  return kron_layout(nullptr, N, rho, nnz).bytes;
+}
+
+extern "C" cpca_status cpca_kron_reduce(const cpca_csr* L, const int32_t* omega, int32_t rho, double tol,
+                                        int32_t max_iter, float* Lt, int64_t ldlt, int64_t* rowptr, int32_t* col,
+                                        float* val, cpca_kron_info* info, void* ws, size_t ws_bytes, void* stream) {
+  clear_error();
+  CPCA_CHECK_ARG(L && omega && Lt, "cpca_kron_reduce: null pointer");
+  CPCA_CHECK_ARG((rowptr == nullptr) == (col == nullptr) && (col == nullptr) == (val == nullptr),
+                 "cpca_kron_reduce: rowptr, col and val go together");
+  const int N = L->n;
+  CPCA_CHECK_ARG(N >= 1 && rho >= 1 && rho <= N, "cpca_kron_reduce: need 1 <= rho <= n (rho %d, n %d)", rho, N);
+  CPCA_CHECK_ARG(ldlt >= rho, "cpca_kron_reduce: ldlt < rho");
+  CPCA_CHECK_ARG(tol > 0, "cpca_kron_reduce: tol must be positive");
+  CPCA_TRY(check_csr(L, N, "cpca_kron_reduce(L)"));
+  const KronWs w = kron_layout(ws, N, rho, L->nnz);
+  if (!ws || ws_bytes < w.bytes) {
+    set_error("cpca_kron_reduce: workspace %zu bytes < required %zu", ws_bytes, w.bytes);
+    return CPCA_ERR_WORKSPACE;
+  }
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  int bad = 0;
+  CPCA_CUDA(cudaMemsetAsync(w.bad, 0, sizeof(int), st));
+  kron_omega_check_kernel<<<std::max(1u, std::min(ceil_div(rho, 256), 64u)), 256, 0, st>>>(omega, rho, N, w.bad);
+  CPCA_LAUNCHED();
+  CPCA_CUDA(cudaMemcpyAsync(&bad, w.bad, sizeof(int), cudaMemcpyDeviceToHost, st));
+  CPCA_CUDA(cudaStreamSynchronize(st));
+  CPCA_CHECK_ARG(!bad, "cpca_kron_reduce: omega must be strictly ascending within [0, n)");
+
+  const int kc = std::min(rho, KMAX_LIMIT);
+  cpca_decode_params prm{};
+  prm.cg_tol = tol;
+  prm.cg_max_iter = max_iter;
+  prm.kmax = kc;
+  CgArgs a{};
+  CPCA_TRY(cg_setup(a, L, L, omega, omega, 1, N, 1, rho, kc, kc, &prm, w.d, st, true, 2));
+  a.s[1].R = w.R;
+  a.s[1].ldr = kc;
+  const CsrView lv{L->n, L->rowptr, L->col, L->val};
+  int itmax = 0, chunks = 0;
+  double resmax = 0.0;
+  for (int j0 = 0; j0 < rho; j0 += kc) {
+    const int kcur = std::min(kc, rho - j0);
+    a.k = kcur;  // the PCG vectors are m x kcur for this chunk
+    kron_identity_kernel<<<std::min<unsigned>(ceil_div(int64_t(rho) * kc, 256), num_sms() * 4), 256, 0, st>>>(
+        w.R, rho, kc, j0, kcur);
+    CPCA_LAUNCHED();
+    int iters[2 * KMAX_LIMIT] = {0};
+    double res[2 * KMAX_LIMIT] = {0};
+    int breakdown = 0;
+    CPCA_TRY(cg_solve(a, w.d, st, iters, res, &breakdown));
+    if (breakdown & 2) {
+      set_error("cpca_kron_reduce: a connected component holds no sampled node");
+      return CPCA_ERR_SINGULAR;
+    }
+    for (int c = 0; c < kcur; ++c) {
+      itmax = std::max(itmax, iters[KMAX_LIMIT + c]);
+      resmax = std::max(resmax, res[KMAX_LIMIT + c]);
+    }
+    CPCA_PROF("kron_cols", st);
+    kron_cols_kernel<<<std::min<unsigned>(ceil_div(int64_t(rho) * kcur, 256), num_sms() * 8), 256, 0, st>>>(
+        lv, omega, w.d.pos1, w.d.vec[1][0], rho, kcur, j0, Lt, ldlt);
+    CPCA_LAUNCHED();
+    ++chunks;
+  }
+  const unsigned gsq = std::min<unsigned>(ceil_div(int64_t(rho) * rho, 256), num_sms() * 8);
+  kron_sym_kernel<<<gsq, 256, 0, st>>>(Lt, ldlt, rho);
+  CPCA_LAUNCHED();
+  if (rowptr) {
+    kron_csr_kernel<<<gsq, 256, 0, st>>>(Lt, ldlt, rho, rowptr, col, val);
+    CPCA_LAUNCHED();
+  }
+  if (info) {
+    info->chunks = chunks;
+    info->cg_iters = itmax;
+    info->cg_res = resmax;
+  }
+  if (resmax > tol) {
+    set_error("cpca_kron_reduce: PCG stopped at relative residual %g", resmax);
+    return CPCA_ERR_NOT_CONVERGED;
+  }
   return CPCA_OK;
 }

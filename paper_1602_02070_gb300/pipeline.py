@@ -21,12 +21,15 @@ def cpca_pipeline(Y: torch.Tensor, K: int = 10, fr: float = 0.25, fc: float = 0.
                   lap_type: int = capi.LAP_NORMALIZED, cg_tol: float = 1e-6,
                   power_iters: int = 200, power_seed: int = 0, rank_ratio: float = 0.1,
                   delta: float = 0.0, kmax: int = 24, svd_iters: int = 6, marks=None,
-                  want_X: bool = True, check_status: bool = True):
+                  want_X: bool = True, check_status: bool = True, graphs: str = "knn",
+                  kron_tol: float = 1e-6):
     """Steps 1-6 on a dense device matrix Y (p x n, FP32, row-major).
 
     1. kNN graphs L_r (rows of Y) and L_c (columns of Y);
     2-3. sampling Omega_r, Omega_c and Y~ = M_r Y M_c;
-    4. kNN graphs of Y~'s rows and columns;
+    4. graphs of Y~'s rows and columns: new kNN graphs (``graphs="knn"``,
+       the experiments' choice) or the Kron reductions of L_r and L_c onto
+       Omega_r and Omega_c (``graphs="kron"``, Sec. IV-A; dense);
     5. FRPCAG by FISTA on Y~ (J iterations, lambda by power iteration);
     6. approximate decoder (Algorithm 2) to X (p x n).
     ``marks``: optional callable(name) invoked between steps (timing hooks).
@@ -39,8 +42,14 @@ def cpca_pipeline(Y: torch.Tensor, K: int = 10, fr: float = 0.25, fc: float = 0.
     Lc, _, _ = capi.cpca_knn_graph(Y, K, lap_type, transposed=True)
     mark("graphs")
     om_r, om_c, Yt = capi.cpca_sample(seed, p, n, rr, rc, Y)
-    Lrt, _, _ = capi.cpca_knn_graph(Yt, K, lap_type)
-    Lct, _, _ = capi.cpca_knn_graph(Yt, K, lap_type, transposed=True)
+    if graphs == "knn":
+        Lrt, _, _ = capi.cpca_knn_graph(Yt, K, lap_type)
+        Lct, _, _ = capi.cpca_knn_graph(Yt, K, lap_type, transposed=True)
+    elif graphs == "kron":
+        Lrt = capi.cpca_kron_reduce(Lr, om_r, tol=kron_tol)["csr"]
+        Lct = capi.cpca_kron_reduce(Lc, om_c, tol=kron_tol)["csr"]
+    else:
+        raise ValueError("graphs must be 'knn' or 'kron'")
     mark("sample")
     prm = capi.frpcag_params(gamma_r, gamma_c, -1.0, J, 0.0, power_iters, power_seed)
     Xt, finfo = capi.cpca_frpcag_solve(Yt, Lrt, Lct, prm, want_info=False)

@@ -54,3 +54,19 @@ def test_workspace_queries_are_host_only(capi):
     assert L.cpca_frpcag_workspace_size(2576, 250) >= 2 * 2576 * 250 * 4
     assert L.cpca_decode_workspace_size(10304, 1000, 2576, 250, 32, 170000, 17000) > 0
     assert L.cpca_decode_workspace_size(10, 10, 5, 5, 64, 30, 30) == 0
+
+
+def test_kron_reduce_arguments_checked_on_host(capi):
+    L = capi.lib()
+    lap = capi.cpca_csr(10, 30, 16, 16, 16)
+    p = C.c_void_p(16)
+    st = L.cpca_kron_reduce(C.byref(lap), p, 11, 1e-6, 0, p, 11, None, None, None, None, p, 1 << 20, None)
+    assert st == capi.CPCA_ERR_INVALID_ARG and b"rho" in L.cpca_last_error()
+    st = L.cpca_kron_reduce(C.byref(lap), p, 4, 1e-6, 0, p, 4, p, None, None, None, p, 1 << 20, None)
+    assert st == capi.CPCA_ERR_INVALID_ARG and b"together" in L.cpca_last_error()
+    st = L.cpca_kron_reduce(C.byref(lap), p, 4, 1e-6, 0, p, 3, None, None, None, None, p, 1 << 20, None)
+    assert st == capi.CPCA_ERR_INVALID_ARG
+    st = L.cpca_kron_reduce(C.byref(lap), p, 4, 1e-6, 0, p, 4, None, None, None, None, p, 16, None)
+    assert st == capi.CPCA_ERR_WORKSPACE
+    assert L.cpca_kron_reduce_workspace_size(10304, 2576, 180000) > 0
+    assert L.cpca_kron_reduce_workspace_size(10, 11, 30) == 0

@@ -758,6 +758,162 @@ __global__ void sum_in_order_kernel(const double* __restrict__ part, int n, doub
   *out = s;
 }
 
+// ------------------------------------------------ FISTA with dense graphs --
+// When both Laplacians are dense (the Kron-reduced graphs of Sec. IV-A), the
+// products L_r Z and Z L_c are dense contractions, not gathers. One launch
+// per iteration: a block computes a DBM x DBN tile of
+//   g = gamma_r (L_r Z_j) + gamma_c (Z_j L_c)
+// in FP32 (both products into one accumulator, k-tiles of DBK staged through
+// shared memory, the next k-tile prefetched into registers while the current
+// one is used), then applies the iteration's update to its entries:
+// S_j = prox(Z_j - lambda 2 g), Z_{j+1} = S_j + mu_j (S_j - S_{j-1}).
+// Z_j is read from one buffer and Z_{j+1} written to the other, so launches
+// order the iterations and no grid barrier is needed.
+constexpr int DBM = 64, DBN = 32, DBK = 32, DTHREADS = 128;
+
+struct DenseFistaArgs {
+  const float* Lr;  // rr x rr, leading dimension rr
+  const float* Lc;  // rc x rc, leading dimension rc
+  const float* Zin;
+  float* Zout;
+  int64_t ldz;
+  const float* Yt;
+  int64_t ldy;
+  float* S;  // S_{j-1} in, S_j out
+  int64_t lds;
+  const double* lam;
+  double* stats;  // the iteration's |Z_{j+1} - Z_j|^2, |Z_j|^2 (added), or null
+  int* done;      // done[1] = J on the last iteration, or null
+  int J;
+  float gr, gc;
+  float mu;
+  int rr, rc;
+  int tiles_r, tiles_c;  // k-tiles of the first (K = rr) and second (K = rc) product
+};
+
+// k-tile t of the concatenated K loop: A (DBM x DBK) and B (DBK x DBN) values
+// this thread stages (16 + 8), zero outside the matrices.
+__device__ __forceinline__ void dense_fetch(const DenseFistaArgs& a, int t, int i0, int j0, float ra[16],
+                                            float rb[8]) {
+  const bool first = t < a.tiles_r;
+  const int k0 = (first ? t : t - a.tiles_r) * DBK;
+  const int K = first ? a.rr : a.rc;
+  const float* A = first ? a.Lr : a.Zin;
+  const int64_t lda = first ? int64_t(a.rr) : a.ldz;
+  const float* B = first ? a.Zin : a.Lc;
+  const int64_t ldb = first ? a.ldz : int64_t(a.rc);
+  const float scale = first ? a.gr : a.gc;
+#pragma unroll
+  for (int u = 0; u < 16; ++u) {
+    const int e = threadIdx.x + u * DTHREADS;  // A element e: row e / DBK, column e % DBK
+    const int gi = i0 + e / DBK, gk = k0 + e % DBK;
+    ra[u] = (gi < a.rr && gk < K) ? __ldg(A + int64_t(gi) * lda + gk) * scale : 0.f;
+  }
+#pragma unroll
+  for (int u = 0; u < 8; ++u) {
+    const int e = threadIdx.x + u * DTHREADS;  // B element e: row e / DBN, column e % DBN
+    const int gk = k0 + e / DBN, gj = j0 + e % DBN;
+    rb[u] = (gk < K && gj < a.rc) ? __ldg(B + int64_t(gk) * ldb + gj) : 0.f;
+  }
+}
+
+__global__ void __launch_bounds__(DTHREADS) fista_dense_kernel(const __grid_constant__ DenseFistaArgs a) {
+  __shared__ __align__(16) float As[DBK][DBM + 4];  // As[k][m]
+  __shared__ __align__(16) float Bs[DBK][DBN + 4];  // Bs[k][n]
+  __shared__ double red[2][DTHREADS / 32];
+  const int tx = threadIdx.x & 7, ty = threadIdx.x >> 3;  // 4 columns, 4 rows each
+  const int i0 = blockIdx.y * DBM, j0 = blockIdx.x * DBN;
+  float acc[4][4];
+#pragma unroll
+  for (int r = 0; r < 4; ++r)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) acc[r][c] = 0.f;
+  const int T = a.tiles_r + a.tiles_c;
+  float ra[16], rb[8];
+  if (T > 0) dense_fetch(a, 0, i0, j0, ra, rb);
+  for (int t = 0; t < T; ++t) {
+#pragma unroll
+    for (int u = 0; u < 16; ++u) {
+      const int e = threadIdx.x + u * DTHREADS;
+      As[e % DBK][e / DBK] = ra[u];
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int e = threadIdx.x + u * DTHREADS;
+      Bs[e / DBN][e % DBN] = rb[u];
+    }
+    __syncthreads();
+    if (t + 1 < T) dense_fetch(a, t + 1, i0, j0, ra, rb);
+#pragma unroll 8
+    for (int k = 0; k < DBK; ++k) {
+      const float4 av = *reinterpret_cast<const float4*>(&As[k][ty * 4]);
+      const float4 bv = *reinterpret_cast<const float4*>(&Bs[k][tx * 4]);
+      const float am[4] = {av.x, av.y, av.z, av.w}, bn[4] = {bv.x, bv.y, bv.z, bv.w};
+#pragma unroll
+      for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) acc[r][c] = fmaf(am[r], bn[c], acc[r][c]);
+    }
+    __syncthreads();
+  }
+  const float lam = float(*a.lam);
+  double dz = 0.0, nz = 0.0;
+#pragma unroll
+  for (int r = 0; r < 4; ++r) {
+    const int i = i0 + ty * 4 + r;
+    if (i >= a.rr) continue;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const int j = j0 + tx * 4 + c;
+      if (j >= a.rc) continue;
+      const float z = a.Zin[int64_t(i) * a.ldz + j];
+      const float y = a.Yt[int64_t(i) * a.ldy + j];
+      const float sp = a.S[int64_t(i) * a.lds + j];
+      const float v = fmaf(-lam, 2.f * acc[r][c], z);
+      const float dl = v - y;
+      const float sv = y + copysignf(fmaxf(fabsf(dl) - lam, 0.f), dl);
+      const float zn = fmaf(a.mu, sv - sp, sv);
+      a.S[int64_t(i) * a.lds + j] = sv;
+      a.Zout[int64_t(i) * a.ldz + j] = zn;
+      const double d = double(zn) - double(z);
+      dz += d * d;
+      nz += double(z) * double(z);
+    }
+  }
+  if (a.stats) {
+    dz = warp_sum(dz);
+    nz = warp_sum(nz);
+    const int w = threadIdx.x >> 5;
+    if ((threadIdx.x & 31) == 0) {
+      red[0][w] = dz;
+      red[1][w] = nz;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double sd = 0.0, sn = 0.0;
+      for (int q = 0; q < DTHREADS / 32; ++q) {
+        sd += red[0][q];
+        sn += red[1][q];
+      }
+      atomicAdd(a.stats, sd);
+      atomicAdd(a.stats + 1, sn);
+    }
+  }
+  if (a.done && blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) a.done[1] = a.J;
+}
+
+// flag[0] |= 1 unless the CSR stores every entry of its n x n matrix in
+// row-major order (row pointers i n, columns 0..n-1 in every row).
+__global__ void dense_pattern_kernel(const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col, int n,
+                                     int* __restrict__ flag) {
+  const int64_t total = int64_t(n) * n;
+  const int64_t g0 = blockIdx.x * int64_t(blockDim.x) + threadIdx.x, gs = int64_t(gridDim.x) * blockDim.x;
+  bool bad = false;
+  for (int64_t t = g0; t < total; t += gs) bad |= col[t] != int32_t(t % n);
+  for (int64_t t = g0; t <= n; t += gs) bad |= rowptr[t] != t * n;
+  if (bad) atomicOr(flag, 1);
+}
+
 }  // namespace
 
 int coop_blocks(const void* kernel, int threads, size_t smem, int want) {
@@ -936,7 +1092,7 @@ cpca_status power_tape_run(const PowerTape* P, int ng, int T, uint64_t seed, boo
 
 cpca_status fista_batch_run(const BatchProblem* P, int n, int J, double eps, bool want_last,
                             int power_iters, uint64_t power_seed, int blocks, const BatchWs& w,
-                            cudaStream_t st) {
+                            cudaStream_t st, bool dense) {
   CPCA_TRY(ensure_mu_table());
   std::lock_guard<std::mutex> lk(g_tab_mu);
   // power iterations (instances without a given step), then lambda
@@ -1016,6 +1172,48 @@ cpca_status fista_batch_run(const BatchProblem* P, int n, int J, double eps, boo
   init_batch_kernel<<<std::min(tiles, num_sms() * 8), 256, 0, st>>>(fa);
   CPCA_LAUNCHED();
   if (J == 0) return CPCA_OK;
+  if (dense) {  // one instance, both Laplacians dense, fixed J: one launch per iteration
+    const BatchProblem& q = P[0];
+    const InstWs& iw = w.inst[0];
+    DenseFistaArgs da{};
+    da.Lr = q.Lr.val;
+    da.Lc = q.Lc.val;
+    da.ldz = fa.in[0].ldz;
+    da.Yt = q.Yt;
+    da.ldy = q.ldy;
+    da.S = q.X;
+    da.lds = q.ldx;
+    da.lam = iw.scal + 2;
+    da.J = J;
+    da.gr = float(q.gamma_r);
+    da.gc = float(q.gamma_c);
+    da.rr = q.rr;
+    da.rc = q.rc;
+    da.tiles_r = q.gamma_r != 0 ? int(ceil_div(q.rr, DBK)) : 0;
+    da.tiles_c = q.gamma_c != 0 ? int(ceil_div(q.rc, DBK)) : 0;
+    const dim3 grid(ceil_div(q.rc, DBN), ceil_div(q.rr, DBM));
+    double t = 1.0;  // t_j; mu_j as in the constant-memory table
+    CPCA_PROF("fista_dense", st);
+    for (int j = 1; j <= J; ++j) {
+      const double tn = (1.0 + std::sqrt(1.0 + 4.0 * t * t)) / 2.0;
+      da.mu = float((t - 1.0) / tn);
+      t = tn;
+      da.Zin = fa.in[0].Z[(j - 1) & 1];
+      da.Zout = fa.in[0].Z[j & 1];
+      da.stats = (j == J && want_last) ? iw.stats + 2 * (J & 3) : nullptr;
+      da.done = j == J ? iw.done : nullptr;
+      fista_dense_kernel<<<grid, DTHREADS, 0, st>>>(da);
+      count_launch();
+      const cudaError_t e = cudaGetLastError();
+      if (e != cudaSuccess) {
+        prof_end();
+        set_error("dense FISTA launch: %s", cudaGetErrorString(e));
+        return CPCA_ERR_CUDA;
+      }
+    }
+    prof_end();
+    return CPCA_OK;
+  }
   CPCA_CUDA(cudaMemsetAsync(w.bar, 0, sizeof(unsigned int) * (kBarrierCounters + 1), st));
   CPCA_CUDA(cudaMemsetAsync(w.err, 0, sizeof(int), st));
   const size_t smem = sizeof(TileSmem), smem_res = sizeof(TileSmem32);
@@ -1201,8 +1399,26 @@ extern "C" cpca_status cpca_frpcag_solve(const float* Yt, int32_t rr, int32_t rc
   P.step = prm->step;
   P.X = X;
   P.ldx = ldx;
+  // dense Laplacians (every entry stored in row-major order, as the Kron
+  // reduction returns them): the products are dense contractions
+  bool dense = false;
+  if (prm->eps == 0 && prm->blocks == 0 && prm->max_iter > 0 && Lr->nnz == int64_t(rr) * rr &&
+      Lc->nnz == int64_t(rc) * rc) {
+    int flag = 0;
+    CPCA_CUDA(cudaMemsetAsync(w.err, 0, sizeof(int), st));
+    dense_pattern_kernel<<<std::min<unsigned>(ceil_div(int64_t(rr) * rr, 256), num_sms() * 8), 256, 0, st>>>(
+        Lr->rowptr, Lr->col, rr, w.err);
+    CPCA_LAUNCHED();
+    dense_pattern_kernel<<<std::min<unsigned>(ceil_div(int64_t(rc) * rc, 256), num_sms() * 8), 256, 0, st>>>(
+        Lc->rowptr, Lc->col, rc, w.err);
+    CPCA_LAUNCHED();
+    CPCA_CUDA(cudaMemcpyAsync(&flag, w.err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CPCA_CUDA(cudaStreamSynchronize(st));
+    CPCA_CUDA(cudaMemsetAsync(w.err, 0, sizeof(int), st));
+    dense = flag == 0;
+  }
   CPCA_TRY(fista_batch_run(&P, 1, prm->max_iter, prm->eps, info != nullptr, prm->power_iters,
-                           prm->power_seed, prm->blocks, w, st));
+                           prm->power_seed, prm->blocks, w, st, dense));
   if (info) {
     cpca_solve_info* infos[1] = {info};
     CPCA_TRY(read_infos(&P, 1, w, prm->max_iter, infos, st));

@@ -197,7 +197,7 @@ InstWs inst_layout(Carve& c, int rr, int rc);
 BatchWs batch_layout(void* ws, const int* rr, const int* rc, int n);
 cpca_status fista_batch_run(const BatchProblem* P, int n, int J, double eps, bool want_last,
                             int power_iters, uint64_t power_seed, int blocks, const BatchWs& w,
-                            cudaStream_t st);
+                            cudaStream_t st, bool dense = false);
 cpca_status fista_objective(const float* Yt, int64_t ldy, int rr, int rc, const CsrView& Lr,
                             const CsrView& Lc, const float* X, int64_t ldx, double gr, double gc,
                             double* part, double* out, cudaStream_t st);

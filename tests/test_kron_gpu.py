@@ -164,6 +164,39 @@ def test_fista_on_kron_graphs_matches_oracle(M):
     assert rel_fro(X.cpu().numpy(), Xo) < FISTA_TOL
 
 
+@pytest.mark.parametrize("N,dim,rr,rc,gr,gc", [(300, 260, 77, 45, 1.0, 1.0), (256, 512, 128, 256, 0.0, 2.0),
+                                                (256, 512, 128, 256, 0.5, 0.0)])
+def test_dense_fista_path_matches_gather_path_and_oracle(M, N, dim, rr, rc, gr, gc):
+    """Dense Laplacians (every entry stored, row-major) take the dense
+    contraction kernel, one launch per iteration; an explicit launch width
+    keeps the gather kernel. Both against each other and the oracle, with a
+    ragged tile edge (77 x 45) and either gamma zero."""
+    Y, _, _ = gen.make_instance(21, N, dim, 4, 3, 0.05)
+    Lr, *_ = O.knn_graph(Y, 10)
+    Lc, *_ = O.knn_graph(Y.T, 10)
+    om_r, om_c = O.sample_indices(21, N, rr, 0), O.sample_indices(21, dim, rc, 1)
+    Yt = O.sample_matrix(Y.astype(np.float64), om_r, om_c)
+    Lrt, Lct = KR.kron_reduce(Lr, om_r), KR.kron_reduce(Lc, om_c)
+    nr, nc = O.power_norm(Lrt, 200, 0, 2), O.power_norm(Lct, 200, 0, 3)
+    J = 150
+    Xo, _ = O.frpcag_fista(Yt, Lrt, Lct, gr, gc, O.fista_step(gr, gc, nr, nc), J)
+    Gr = M.Csr.from_scipy(KR.kron_reduce_csr(Lr, om_r))
+    Gc = M.Csr.from_scipy(KR.kron_reduce_csr(Lc, om_c))
+    M.profile_enable(True, "fista_")
+    Xd, infod = M.cpca_frpcag_solve(_dev(Yt), Gr, Gc, gamma_r=gr, gamma_c=gc, max_iter=J)
+    torch.cuda.synchronize()
+    used = M.profile_read()
+    M.profile_enable(False, "")
+    assert "fista_dense" in used and "fista_persistent" not in used
+    Xg, infog = M.cpca_frpcag_solve(_dev(Yt), Gr, Gc, gamma_r=gr, gamma_c=gc, max_iter=J, blocks=152)
+    assert infod.iters == infog.iters == J
+    assert infod.step == infog.step
+    assert rel_fro(Xd.cpu().numpy(), Xg.cpu().numpy()) < 1e-5
+    assert rel_fro(Xd.cpu().numpy(), Xo) < FISTA_TOL
+    assert infod.rel_change > 0 and infod.rel_change == pytest.approx(infog.rel_change, rel=0.5)
+    assert infod.objective == pytest.approx(infog.objective, rel=1e-5)
+
+
 def test_kron_full_size_and_fista(M):
     """10304 x 1000 (rank 10, 10 clusters, 1/4 x 1/4 sampling): the oracle's
     full graphs of Y's rows (10304 nodes) and columns (1000 nodes) reduced

@@ -585,6 +585,8 @@ def main():
     ap.add_argument("--fista-large-only", action="store_true",
                     help="only FISTA on the 8 GB workload's Y~ (one JSON object; for profiling)")
     ap.add_argument("--fista-large-iters", type=int, default=300)
+    ap.add_argument("--kron-only", action="store_true",
+                    help="only the Kron-reduced graphs and FISTA on them (one JSON object; for profiling)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 0)
 
@@ -622,6 +624,10 @@ def main():
 
     Yh = torch.from_numpy(Y).pin_memory()
     Yd = Yh.to(dev)
+    if args.kron_only:
+        out = M.cpca_pipeline(Yd, K=cfg["K"], fr=cfg["fr"], fc=cfg["fc"], seed=0, J=cfg["J"], cg_tol=cfg["cg_tol"])
+        print(json.dumps(kron_measure(M, torch, out, cfg, load_peaks(), reps=1)))
+        return
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
     kw = dict(K=cfg["K"], fr=cfg["fr"], fc=cfg["fc"], seed=0, J=cfg["J"], cg_tol=cfg["cg_tol"])
     info = {}

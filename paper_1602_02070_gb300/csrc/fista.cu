@@ -769,7 +769,10 @@ __global__ void sum_in_order_kernel(const double* __restrict__ part, int n, doub
 // S_j = prox(Z_j - lambda 2 g), Z_{j+1} = S_j + mu_j (S_j - S_{j-1}).
 // Z_j is read from one buffer and Z_{j+1} written to the other, so launches
 // order the iterations and no grid barrier is needed.
-constexpr int DBM = 64, DBN = 32, DBK = 32, DTHREADS = 128;
+constexpr int DBM = 32, DBN = 32, DBK = 32, DTHREADS = 64;
+constexpr int NRA = DBM * DBK / (4 * DTHREADS), NRB = DBK * DBN / (4 * DTHREADS);  // staged vectors per thread
+static_assert(NRA * 4 * DTHREADS == DBM * DBK && NRB * 4 * DTHREADS == DBK * DBN, "whole staging rounds");
+static_assert((DBM / 4) * (DBN / 4) == DTHREADS, "one 4 x 4 block of outputs per thread");
 
 struct DenseFistaArgs {
   const float* Lr;  // rr x rr, leading dimension rr
@@ -789,12 +792,17 @@ struct DenseFistaArgs {
   float mu;
   int rr, rc;
   int tiles_r, tiles_c;  // k-tiles of the first (K = rr) and second (K = rc) product
+  int vec_lr, vec_lc;    // rows of Lr / Lc allow 16-byte loads (Z's always do)
 };
 
-// k-tile t of the concatenated K loop: A (DBM x DBK) and B (DBK x DBN) values
-// this thread stages (16 + 8), zero outside the matrices.
-__device__ __forceinline__ void dense_fetch(const DenseFistaArgs& a, int t, int i0, int j0, float ra[16],
-                                            float rb[8]) {
+// k-tile t of the concatenated K loop: the A (DBM x DBK) and B (DBK x DBN)
+// values this thread stages, zero outside the matrices. Whole 16-byte
+// vectors where the rows allow them and the tile lies inside the matrix:
+// A vector u covers row (e / 8), columns 4 (e % 8) .. + 3 of the tile, with
+// e = threadIdx.x + u DTHREADS (B likewise); otherwise the same elements one
+// by one.
+__device__ __forceinline__ void dense_fetch(const DenseFistaArgs& a, int t, int i0, int j0, float4 ra[NRA],
+                                            float4 rb[NRB]) {
   const bool first = t < a.tiles_r;
   const int k0 = (first ? t : t - a.tiles_r) * DBK;
   const int K = first ? a.rr : a.rc;
@@ -803,17 +811,44 @@ __device__ __forceinline__ void dense_fetch(const DenseFistaArgs& a, int t, int 
   const float* B = first ? a.Zin : a.Lc;
   const int64_t ldb = first ? a.ldz : int64_t(a.rc);
   const float scale = first ? a.gr : a.gc;
+  const bool ka = k0 + DBK <= K;
+  const bool va = ka && (first ? a.vec_lr != 0 : true);
+  const bool vb = ka && j0 + DBN <= a.rc && (first ? true : a.vec_lc != 0);
 #pragma unroll
-  for (int u = 0; u < 16; ++u) {
-    const int e = threadIdx.x + u * DTHREADS;  // A element e: row e / DBK, column e % DBK
-    const int gi = i0 + e / DBK, gk = k0 + e % DBK;
-    ra[u] = (gi < a.rr && gk < K) ? __ldg(A + int64_t(gi) * lda + gk) * scale : 0.f;
+  for (int u = 0; u < NRA; ++u) {
+    const int e = threadIdx.x + u * DTHREADS;
+    const int gi = i0 + e / 8, gk = k0 + 4 * (e % 8);
+    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (gi < a.rr) {
+      const float* p = A + int64_t(gi) * lda + gk;
+      if (va) {
+        v = __ldg(reinterpret_cast<const float4*>(p));
+      } else {
+        if (gk < K) v.x = __ldg(p);
+        if (gk + 1 < K) v.y = __ldg(p + 1);
+        if (gk + 2 < K) v.z = __ldg(p + 2);
+        if (gk + 3 < K) v.w = __ldg(p + 3);
+      }
+    }
+    ra[u] = make_float4(v.x * scale, v.y * scale, v.z * scale, v.w * scale);
   }
 #pragma unroll
-  for (int u = 0; u < 8; ++u) {
-    const int e = threadIdx.x + u * DTHREADS;  // B element e: row e / DBN, column e % DBN
-    const int gk = k0 + e / DBN, gj = j0 + e % DBN;
-    rb[u] = (gk < K && gj < a.rc) ? __ldg(B + int64_t(gk) * ldb + gj) : 0.f;
+  for (int u = 0; u < NRB; ++u) {
+    const int e = threadIdx.x + u * DTHREADS;
+    const int gk = k0 + e / 8, gj = j0 + 4 * (e % 8);
+    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (gk < K) {
+      const float* p = B + int64_t(gk) * ldb + gj;
+      if (vb) {
+        v = __ldg(reinterpret_cast<const float4*>(p));
+      } else {
+        if (gj < a.rc) v.x = __ldg(p);
+        if (gj + 1 < a.rc) v.y = __ldg(p + 1);
+        if (gj + 2 < a.rc) v.z = __ldg(p + 2);
+        if (gj + 3 < a.rc) v.w = __ldg(p + 3);
+      }
+    }
+    rb[u] = v;
   }
 }
 
@@ -821,7 +856,7 @@ __global__ void __launch_bounds__(DTHREADS) fista_dense_kernel(const __grid_cons
   __shared__ __align__(16) float As[DBK][DBM + 4];  // As[k][m]
   __shared__ __align__(16) float Bs[DBK][DBN + 4];  // Bs[k][n]
   __shared__ double red[2][DTHREADS / 32];
-  const int tx = threadIdx.x & 7, ty = threadIdx.x >> 3;  // 4 columns, 4 rows each
+  const int tx = threadIdx.x % (DBN / 4), ty = threadIdx.x / (DBN / 4);  // 4 columns, 4 rows each
   const int i0 = blockIdx.y * DBM, j0 = blockIdx.x * DBN;
   float acc[4][4];
 #pragma unroll
@@ -829,18 +864,21 @@ __global__ void __launch_bounds__(DTHREADS) fista_dense_kernel(const __grid_cons
 #pragma unroll
     for (int c = 0; c < 4; ++c) acc[r][c] = 0.f;
   const int T = a.tiles_r + a.tiles_c;
-  float ra[16], rb[8];
+  float4 ra[NRA], rb[NRB];
   if (T > 0) dense_fetch(a, 0, i0, j0, ra, rb);
   for (int t = 0; t < T; ++t) {
 #pragma unroll
-    for (int u = 0; u < 16; ++u) {
-      const int e = threadIdx.x + u * DTHREADS;
-      As[e % DBK][e / DBK] = ra[u];
+    for (int u = 0; u < NRA; ++u) {
+      const int e = threadIdx.x + u * DTHREADS, m = e / 8, kq = 4 * (e % 8);
+      As[kq][m] = ra[u].x;
+      As[kq + 1][m] = ra[u].y;
+      As[kq + 2][m] = ra[u].z;
+      As[kq + 3][m] = ra[u].w;
     }
 #pragma unroll
-    for (int u = 0; u < 8; ++u) {
+    for (int u = 0; u < NRB; ++u) {
       const int e = threadIdx.x + u * DTHREADS;
-      Bs[e / DBN][e % DBN] = rb[u];
+      *reinterpret_cast<float4*>(&Bs[e / 8][4 * (e % 8)]) = rb[u];
     }
     __syncthreads();
     if (t + 1 < T) dense_fetch(a, t + 1, i0, j0, ra, rb);
@@ -1191,6 +1229,8 @@ cpca_status fista_batch_run(const BatchProblem* P, int n, int J, double eps, boo
     da.rc = q.rc;
     da.tiles_r = q.gamma_r != 0 ? int(ceil_div(q.rr, DBK)) : 0;
     da.tiles_c = q.gamma_c != 0 ? int(ceil_div(q.rc, DBK)) : 0;
+    da.vec_lr = q.rr % 4 == 0 && reinterpret_cast<uintptr_t>(q.Lr.val) % 16 == 0;
+    da.vec_lc = q.rc % 4 == 0 && reinterpret_cast<uintptr_t>(q.Lc.val) % 16 == 0;
     const dim3 grid(ceil_div(q.rc, DBN), ceil_div(q.rr, DBM));
     double t = 1.0;  // t_j; mu_j as in the constant-memory table
     CPCA_PROF("fista_dense", st);

@@ -156,6 +156,12 @@ cpca_status cpca_sample(uint64_t seed, int32_t p, int32_t n, int32_t rho_r, int3
  * call does not synchronise unless `info` is given. The output X (rr x rc,
  * leading dimension ldx) is the last S_j. FP32 arithmetic, FP64 reductions.
  * Lr is rr x rr, Lc is rc x rc, both symmetric.
+ * Dense Laplacians (the Kron reductions of Sec. IV-A): when both CSRs hold
+ * n^2 entries, eps = 0 and blocks = 0, the call checks on the device (one
+ * synchronisation) that every entry is stored in row-major order, as
+ * cpca_kron_reduce returns them; if so, each iteration is one launch of a
+ * tiled FP32 contraction of both products with the update fused (no grid
+ * barrier), which agrees with the gather kernel to FP32 rounding.
  * `info` (host, may be NULL): if given, the call SYNCHRONISES and fills it,
  * including the FP64 objective of X.
  * ---------------------------------------------------------------------- */
@@ -190,7 +196,9 @@ size_t cpca_frpcag_workspace_size(int32_t rr, int32_t rc);
  * graphs, gammas and optional step) solved by FISTA in ONE cooperative
  * launch (plus one launch for all power iterations): every problem runs the
  * same max_iter iterations of Algorithm 1, or stops on its own when
- * eps > 0. Results equal per-problem cpca_frpcag_solve calls. Without
+ * eps > 0. Results equal per-problem cpca_frpcag_solve calls (bit for bit;
+ * for dense Laplacians, where the single solve takes its dense kernel, to
+ * FP32 rounding). Without
  * `infos` the call is fully asynchronous and may be captured in a CUDA
  * graph (run it once outside capture first). params.gamma_* and .step are
  * ignored (taken from each problem); .max_iter, .eps, .power_iters,

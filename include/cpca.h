@@ -8,6 +8,10 @@
  *   - FRPCAG on the sampled matrix by FISTA               (Sec. IV-B, Algorithm 1)
  *   - the subspace-upsampling approximate decoder         (Sec. V-C, Lemma 1,
  *                                                          Eq. Uupsample, Algorithm 2)
+ *   - the alternate, clustering and projection decoders   (Sec. V-B, Algorithm 3,
+ *                                                          appendix)
+ *   - Kron-reduced compressed Laplacians                  (Sec. IV-A)
+ *   - reverse-mode derivatives and batched solves         (not in the paper)
  *
  * Conventions (all entry points):
  *   - Array arguments are DEVICE pointers unless marked "host". The caller

@@ -570,6 +570,23 @@ def roofline_for(name, ms, launches, ctx, peaks):
             "frac": None, "traffic": None, "peak_source": src}
 
 
+# ------------------------------------------------------- replicas (N > 1)
+def max_over_ranks(dist, values, device):
+    """Each value's maximum over all ranks (the slowest replica's times);
+    the values themselves when there is no process group."""
+    if dist is None:
+        return [float(v) for v in values]
+    import torch
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(v) for v in t]
+
+
+def whole_job_rate(units_per_rank, world, seconds):
+    """Units all replicas processed per second of the slowest replica."""
+    return units_per_rank * world / seconds
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -701,13 +718,9 @@ def main():
     barrier()
     e2e_s = sum(a.elapsed_time(b) for a, b in ev2) / 1000.0
 
-    if dist is not None:
-        t = torch.tensor([total_s, e2e_s], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_s, e2e_s = float(t[0]), float(t[1])
-
+    total_s, e2e_s = max_over_ranks(dist, [total_s, e2e_s], dev)
     units = cfg["J"] * args.steps * world
-    value = units / total_s
+    value = whole_job_rate(cfg["J"] * args.steps, world, total_s)
     peaks = load_peaks()
     dom_ms, dom_n = prof.get(dominant, (0.0, 0))
     roof = roofline_for(dominant, dom_ms, dom_n, ctx, peaks) if dom_n else None

@@ -70,3 +70,21 @@ def test_kron_reduce_arguments_checked_on_host(capi):
     assert st == capi.CPCA_ERR_WORKSPACE
     assert L.cpca_kron_reduce_workspace_size(10304, 2576, 180000) > 0
     assert L.cpca_kron_reduce_workspace_size(10, 11, 30) == 0
+
+
+def test_binding_argument_counts_match_header(capi):
+    """Every ctypes signature in the binding has as many arguments as the
+    declaration in include/cpca.h (an ABI drift check, no GPU needed)."""
+    import os
+    import re
+    from tests._util import ROOT
+    txt = open(os.path.join(ROOT, "include", "cpca.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    decl = {}
+    for m in re.finditer(r"\b(cpca_[a-z0-9_]+)\s*\(([^;{]*?)\)\s*;", txt, flags=re.S):
+        args = m.group(2).strip()
+        decl[m.group(1)] = 0 if args in ("", "void") else args.count(",") + 1
+    sigs = {name: len(args) for name, _, args in capi._SIGS}
+    assert set(sigs) == set(decl)
+    for name, n in sigs.items():
+        assert decl[name] == n, (name, decl[name], n)

@@ -112,54 +112,6 @@ __device__ __forceinline__ float4 nbr_sum_v4(const Off* off, const float* w, int
   return acc;
 }
 
-// For four staged neighbour lists u = 0..3 (rows or columns of the tile):
-// out[u] = sum_q w[u][q] * x[off[u][q] + base]. Chunks of 8 entries of all
-// four lists are loaded together (32 independent loads per lane) up to the
-// shortest list, then each list's remainder, then entries beyond the
-// staging area straight from the CSR. x is read through L2 (ld.global.cg):
-// other blocks of the same launch write it.
-template <typename Off>
-__device__ __forceinline__ void nbr_sum4(const Off (*off)[kTileNbr], const float (*w)[kTileNbr],
-                                         const int* deg, const int64_t* f0, int first, bool valid,
-                                         const float* __restrict__ x, int64_t base, const CsrView& L,
-                                         int64_t stride, float out[4]) {
-  int dmin = kTileNbr;
-#pragma unroll
-  for (int u = 0; u < 4; ++u) dmin = min(dmin, min(deg[first + u], kTileNbr));
-  float acc[4] = {0.f, 0.f, 0.f, 0.f};
-  if (valid) {
-    int e = 0;
-    for (; e + 8 <= dmin; e += 8) {
-      float v[4][8];
-#pragma unroll
-      for (int u = 0; u < 4; ++u)
-#pragma unroll
-        for (int q = 0; q < 8; ++q) v[u][q] = __ldcg(x + off[first + u][e + q] + base);
-#pragma unroll
-      for (int u = 0; u < 4; ++u)
-#pragma unroll
-        for (int q = 0; q < 8; ++q) acc[u] = fmaf(w[first + u][e + q], v[u][q], acc[u]);
-    }
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const int ds = min(deg[first + u], kTileNbr);
-      int e2 = e;
-      for (; e2 + 4 <= ds; e2 += 4) {
-        float v[4];
-#pragma unroll
-        for (int q = 0; q < 4; ++q) v[q] = __ldcg(x + off[first + u][e2 + q] + base);
-#pragma unroll
-        for (int q = 0; q < 4; ++q) acc[u] = fmaf(w[first + u][e2 + q], v[q], acc[u]);
-      }
-      for (; e2 < ds; ++e2) acc[u] = fmaf(w[first + u][e2], __ldcg(x + off[first + u][e2] + base), acc[u]);
-      for (int64_t f = f0[first + u] + kTileNbr; f < f0[first + u] + deg[first + u]; ++f)
-        acc[u] = fmaf(__ldg(L.val + f), __ldcg(x + int64_t(__ldg(L.col + f)) * stride + base), acc[u]);
-    }
-  }
-#pragma unroll
-  for (int u = 0; u < 4; ++u) out[u] = acc[u];
-}
-
 // Per-instance scratch of a FISTA solve.
 struct InstWs {
   float* Z0;          // Z_j ping (row-major)

@@ -40,7 +40,7 @@ import gen  # noqa: E402
 
 METRIC = "wall-time to 1e-4 rel err vs plain GPU; FISTA/CG iters/s; % of HBM peak"
 UNIT = "FISTA iters/s"
-WORKLOAD = "c1"
+WORKLOAD = "bench_10304x1000"
 L2_FLUSH_BYTES = 256 << 20
 
 
@@ -488,7 +488,7 @@ def fista_large_measure(M, torch, peaks, J=300, reps=3):
     in L2, so this is the size where the kernel meets the HBM roofline:
     20 B per entry of Y~ (read Y~, S_{j-1}, S_{j-2}, write S_j and Z) plus
     8 B per CSR entry and the row pointers, per iteration."""
-    cfg = gen.CONFIGS["c2"]
+    cfg = gen.CONFIGS["large_20000x100000"]
     p, n, K = cfg["p"], cfg["n"], cfg["K"]
     Y = gen.make_instance_torch(0, p, n, cfg["r"], cfg["C"], cfg["frac"])
     rr, rc = M.rho_of(p, cfg["fr"]), M.rho_of(n, cfg["fc"])

@@ -78,14 +78,15 @@ def make_instance_torch(seed: int, p: int, n: int, r: int, C: int, frac: float,
     return Y
 
 
-# The five workloads: shapes, ranks, cluster counts, corruption, graph K,
-# sampling fractions, FISTA iteration counts and gamma values.
+# Single-instance workloads by size: shapes, ranks, cluster counts,
+# corruption, graph K, sampling fractions, FISTA iteration counts and gamma
+# values (the 64-instance workload is batched_instances below).
 CONFIGS = {
-    "c0": dict(p=256, n=512, r=5, C=4, frac=0.05, K=10, fr=0.5, fc=0.5,
+    "small_256x512": dict(p=256, n=512, r=5, C=4, frac=0.05, K=10, fr=0.5, fc=0.5,
                J=200, gamma_r=1.0, gamma_c=1.0, cg_tol=1e-6),
-    "c1": dict(p=10304, n=1000, r=10, C=10, frac=0.05, K=10, fr=0.25, fc=0.25,
+    "bench_10304x1000": dict(p=10304, n=1000, r=10, C=10, frac=0.05, K=10, fr=0.25, fc=0.25,
                J=300, gamma_r=1.0, gamma_c=1.0, cg_tol=1e-6),
-    "c2": dict(p=20000, n=100000, r=20, C=50, frac=0.02, K=10, fr=0.1, fc=0.1,
+    "large_20000x100000": dict(p=20000, n=100000, r=20, C=50, frac=0.02, K=10, fr=0.1, fc=0.1,
                J=300, gamma_r=1.0, gamma_c=1.0, cg_tol=1e-6),
 }
 

@@ -103,7 +103,7 @@ def test_repeated_sample_index_is_rejected(M):
 def test_alternate_decoder_full_size_residual(M):
     """10304 x 1000 (rank 10, 10 clusters, 1/4 x 1/4 sampling), graphs from
     the CUDA kNN: the FP64 residual of the returned X, from the definition."""
-    cfg = gen.CONFIGS["c1"]
+    cfg = gen.CONFIGS["bench_10304x1000"]
     p, n = cfg["p"], cfg["n"]
     Yd = gen.make_instance_torch(0, p, n, cfg["r"], cfg["C"], cfg["frac"], device="cuda")
     Lr, _, _ = M.cpca_knn_graph(Yd, cfg["K"])

@@ -60,7 +60,7 @@ def test_cluster_decoder_matches_oracle(M, p, n, C, rr, rc, frac):
 def test_cluster_decoder_full_size(M):
     """10304 x 1000 (10 clusters of columns), X~ 2576 x 250, k = 10: the
     oracle's column graph (1000 nodes) and sampled matrix feed both sides."""
-    cfg = gen.CONFIGS["c1"]
+    cfg = gen.CONFIGS["bench_10304x1000"]
     p, n = cfg["p"], cfg["n"]
     Y, _, _ = gen.make_instance(0, p, n, cfg["r"], cfg["C"], cfg["frac"])
     pool = OraclePool()

@@ -70,7 +70,7 @@ def _check_graph(G, L):
 
 
 def test_c1_every_step_and_end_to_end(M, pool):
-    cfg = gen.CONFIGS["c1"]
+    cfg = gen.CONFIGS["bench_10304x1000"]
     p, n, K, J = cfg["p"], cfg["n"], cfg["K"], cfg["J"]
     Y, _, _ = gen.make_instance(0, p, n, cfg["r"], cfg["C"], cfg["frac"])
     Yd = Y.astype(np.float64)
@@ -139,7 +139,7 @@ def test_c1_every_step_and_end_to_end(M, pool):
 
 
 def test_c2_full_size(M, pool):
-    cfg = gen.CONFIGS["c2"]
+    cfg = gen.CONFIGS["large_20000x100000"]
     p, n, K = cfg["p"], cfg["n"], cfg["K"]
     Y = gen.make_instance_torch(0, p, n, cfg["r"], cfg["C"], cfg["frac"], device="cuda")
     rr, rc = M.rho_of(p, cfg["fr"]), M.rho_of(n, cfg["fc"])

@@ -145,7 +145,7 @@ def test_kron_rejects_unsorted_omega(M):
 def test_fista_on_kron_graphs_matches_oracle(M):
     """256 x 512 (rank 5, 4 clusters, 5% gross errors), 1/2 x 1/2 sampling,
     J = 200: FISTA on the oracle's Kron-reduced Laplacians (dense CSR)."""
-    cfg = gen.CONFIGS["c0"]
+    cfg = gen.CONFIGS["small_256x512"]
     p, n, J = cfg["p"], cfg["n"], cfg["J"]
     Y, _, _ = gen.make_instance(0, p, n, cfg["r"], cfg["C"], cfg["frac"])
     Lr, *_ = O.knn_graph(Y, cfg["K"])
@@ -202,7 +202,7 @@ def test_kron_full_size_and_fista(M):
     full graphs of Y's rows (10304 nodes) and columns (1000 nodes) reduced
     onto the sampled 2576 rows and 250 columns, then 30 FISTA iterations on
     the reduced Laplacians (dense CSR, 6.6 M entries for the rows)."""
-    cfg = gen.CONFIGS["c1"]
+    cfg = gen.CONFIGS["bench_10304x1000"]
     p, n, K = cfg["p"], cfg["n"], cfg["K"]
     Y, _, _ = gen.make_instance(0, p, n, cfg["r"], cfg["C"], cfg["frac"])
     Yd = Y.astype(np.float64)

@@ -240,7 +240,7 @@ def test_decode_singular_component_reported(M):
 
 # ------------------------------------------------------------------ pipeline
 def test_pipeline_c0_end_to_end(M):
-    cfg = gen.CONFIGS["c0"]
+    cfg = gen.CONFIGS["small_256x512"]
     Y, _, _ = gen.make_instance(0, cfg["p"], cfg["n"], cfg["r"], cfg["C"], cfg["frac"])
     rr, rc = M.rho_of(cfg["p"], cfg["fr"]), M.rho_of(cfg["n"], cfg["fc"])
     out = M.cpca_pipeline(_dev(Y), K=cfg["K"], fr=cfg["fr"], fc=cfg["fc"], seed=0, J=cfg["J"])

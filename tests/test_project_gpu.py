@@ -53,7 +53,7 @@ def test_projected_decoder_matches_oracle(M, side, p, n, rr, rc):
 @pytest.mark.parametrize("side", [0, 1])
 def test_projection_full_size_against_fp64(M, side):
     """10304 x 1000: the projection kernels given a basis, against FP64."""
-    cfg = gen.CONFIGS["c1"]
+    cfg = gen.CONFIGS["bench_10304x1000"]
     p, n = cfg["p"], cfg["n"]
     Yd = gen.make_instance_torch(0, p, n, cfg["r"], cfg["C"], cfg["frac"], device="cuda")
     rng = np.random.default_rng(side)

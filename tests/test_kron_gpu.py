@@ -10,7 +10,10 @@ Entries with no path through unsampled nodes are exactly 0 on both sides
 (the PCG iterates never leave the support of their right-hand side), and
 the result is exactly symmetric (it is symmetrised). FISTA fed the
 oracle's reduced Laplacians: relative Frobenius 1e-4 after J iterations
-(the bar of the sparse graphs), norms within 1e-6.
+(the bar of the sparse graphs), norms within 1e-6; at 10304 x 1000 each
+side runs on its own reductions (they differ by ~1e-7), so the norms are
+held to 1e-5 there. The dense contraction kernel and the gather kernel
+agree to 1e-5 (FP32 sums in different orders).
 """
 import numpy as np
 import pytest

@@ -34,6 +34,8 @@ def cpca_pipeline(Y: torch.Tensor, K: int = 10, fr: float = 0.25, fc: float = 0.
     6. approximate decoder (Algorithm 2) to X (p x n).
     ``marks``: optional callable(name) invoked between steps (timing hooks).
     """
+    if graphs not in ("knn", "kron"):
+        raise ValueError("graphs must be 'knn' or 'kron'")
     mark = marks or (lambda name: None)
     p, n = Y.shape
     rr, rc = rho_of(p, fr), rho_of(n, fc)
@@ -45,11 +47,9 @@ def cpca_pipeline(Y: torch.Tensor, K: int = 10, fr: float = 0.25, fc: float = 0.
     if graphs == "knn":
         Lrt, _, _ = capi.cpca_knn_graph(Yt, K, lap_type)
         Lct, _, _ = capi.cpca_knn_graph(Yt, K, lap_type, transposed=True)
-    elif graphs == "kron":
+    else:
         Lrt = capi.cpca_kron_reduce(Lr, om_r, tol=kron_tol)["csr"]
         Lct = capi.cpca_kron_reduce(Lc, om_c, tol=kron_tol)["csr"]
-    else:
-        raise ValueError("graphs must be 'knn' or 'kron'")
     mark("sample")
     prm = capi.frpcag_params(gamma_r, gamma_c, -1.0, J, 0.0, power_iters, power_seed)
     Xt, finfo = capi.cpca_frpcag_solve(Yt, Lrt, Lct, prm, want_info=False)

@@ -88,3 +88,10 @@ def test_binding_argument_counts_match_header(capi):
     assert set(sigs) == set(decl)
     for name, n in sigs.items():
         assert decl[name] == n, (name, decl[name], n)
+
+
+def test_pipeline_rejects_unknown_graph_kind_before_any_launch(capi):
+    import paper_1602_02070_gb300 as M
+    torch = pytest.importorskip("torch")
+    with pytest.raises(ValueError):
+        M.cpca_pipeline(torch.zeros(8, 8), graphs="dense")

@@ -28,7 +28,7 @@ from __future__ import annotations
 import numpy as np
 
 __all__ = ["make_instance", "make_instance_torch", "CONFIGS", "batched_instances",
-           "heldout_entries"]
+           "heldout_entries", "latent_points"]
 
 
 def make_instance(seed: int, p: int, n: int, r: int, C: int, frac: float,
@@ -118,3 +118,18 @@ def heldout_entries(seed: int, p: int, n: int, count: int, omega_r, omega_c):
     cand = np.flatnonzero(~inside.ravel())
     pick = np.sort(rng.choice(cand, size=min(count, cand.size), replace=False))
     return (pick // n).astype(np.int32), (pick % n).astype(np.int32)
+
+
+def latent_points(seed: int, N: int, dim: int = 20, C: int = 1, spread: float = 0.1):
+    """N seeded points in R^dim (float32), in C balanced clusters: centres
+    i.i.d. N(0, 1), labels j mod C shuffled, point = centre + spread N(0, I)
+    (C = 1: one N(0, I) cloud, spread ignored). The same model as the latent
+    rows of U (C = 1) and columns of Z (C > 1) of ``make_instance``, for
+    graphs whose size matches a workload but whose points are cheap to
+    search."""
+    rng = np.random.default_rng(seed)
+    if C <= 1:
+        return rng.standard_normal((N, dim)).astype(np.float32)
+    centres = rng.standard_normal((C, dim))
+    labels = rng.permutation(np.arange(N) % C)
+    return (centres[labels] + spread * rng.standard_normal((N, dim))).astype(np.float32)

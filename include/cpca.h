@@ -48,6 +48,7 @@ typedef int32_t cpca_status;
 #define CPCA_ERR_NOT_CONVERGED 5  /* iteration cap reached before the tolerance */
 #define CPCA_ERR_TIMEOUT       6  /* a bounded device-side wait gave up */
 #define CPCA_ERR_CAPACITY      7  /* an output buffer is too small (e.g. nnz_cap) */
+#define CPCA_ERR_NONFINITE     8  /* NaN or Inf in a result that reports its objective */
 
 #define CPCA_LAP_NORMALIZED    0  /* L_n = D^-1/2 (D - W) D^-1/2 (Sec. I) */
 #define CPCA_LAP_COMBINATORIAL 1  /* L = D - W (Sec. I) */
@@ -58,6 +59,20 @@ const char* cpca_last_error(void);
 int32_t cpca_version(void);
 /* Number of kernels this library has launched in this process. */
 uint64_t cpca_launch_count(void);
+
+/* Failure-path hooks (not in the paper; for tests of the error paths
+ * without a GPU fault).
+ * cpca_debug_set_barrier_spin_limit(polls): grid-barrier waits of launches
+ * made after this call give up after `polls` polls (polls <= 0 restores the
+ * default, about a second of waiting); a wait that gives up sets the
+ * launch's error flag, every block leaves its loops and the call reports
+ * CPCA_ERR_TIMEOUT. Process-wide; returns 0.
+ * Environment variable CPCA_FAULT (read at every call): "timeout" acts as a
+ * poll limit of 1; "nan" makes cpca_frpcag_solve write a NaN into X[0][0]
+ * after the solve (so a call with `info` reports CPCA_ERR_NONFINITE); the
+ * Python binding also takes "alloc" (its workspace allocation fails before
+ * any launch). */
+int32_t cpca_debug_set_barrier_spin_limit(int64_t polls);
 
 /* Per-kernel CUDA-event timing (tracing aid; off by default).
  * cpca_profile_enable(on, prefix) clears earlier records and, when on != 0,
@@ -167,7 +182,12 @@ cpca_status cpca_sample(uint64_t seed, int32_t p, int32_t n, int32_t rho_r, int3
  * tiled FP32 contraction of both products with the update fused (no grid
  * barrier), which agrees with the gather kernel to FP32 rounding.
  * `info` (host, may be NULL): if given, the call SYNCHRONISES and fills it,
- * including the FP64 objective of X.
+ * including the FP64 objective of X, and reports CPCA_ERR_TIMEOUT (a grid
+ * barrier gave up) or CPCA_ERR_NONFINITE (the objective is NaN or Inf).
+ * Without `info` the call is asynchronous and reports neither: the barrier
+ * flag stays in `ws` for cpca_frpcag_status.
+ * Dense inputs take one synchronisation for the pattern check, so a call on
+ * dense Laplacians cannot be captured in a CUDA graph.
  * ---------------------------------------------------------------------- */
 typedef struct cpca_frpcag_params {
   double gamma_r;
@@ -238,6 +258,15 @@ cpca_status cpca_frpcag_solve(const float* Yt, int32_t rr, int32_t rc, int64_t l
                               const cpca_frpcag_params* params,
                               float* X, int64_t ldx, cpca_solve_info* info,
                               void* ws, size_t ws_bytes, void* stream);
+
+/* Status of the last FISTA solve (single, batched or no-allocation) on the
+ * workspace `ws` (NULL: the no-allocation solve's built-in scratch):
+ * SYNCHRONISES `stream`, then returns CPCA_ERR_TIMEOUT if a grid barrier of
+ * that solve's power iterations or FISTA launch gave up, else CPCA_OK.
+ * Solves without `info` are asynchronous and never read that flag
+ * themselves; call this (after they finish, e.g. after any synchronising
+ * call) to learn of a timeout. */
+cpca_status cpca_frpcag_status(const void* ws, void* stream);
 
 /* ------------------------------------------------------------------------
  * cpca_frpcag_solve_noalloc - cpca_frpcag_solve without a workspace.

@@ -15,3 +15,4 @@ from .cpca_oracle import *  # noqa: F401,F403
 from . import cpca_adjoint  # noqa: F401  (reverse-mode derivatives, FP64)
 from . import cpca_decoders  # noqa: F401  (alternate, projected and clustering decoders)
 from . import cpca_kron  # noqa: F401  (Kron-reduced compressed Laplacians, Sec. IV-A)
+from . import cpca_fista_c  # noqa: F401  (Algorithm 1 in plain C, FP64, OpenMP)

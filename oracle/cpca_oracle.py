@@ -377,14 +377,17 @@ def upsample_subspace(L, omega: np.ndarray, R: np.ndarray, tol: float = 1e-6,
 
 def approx_decode(Xt, omega_r, omega_c, p: int, n: int, Lr, Lc,
                   ratio: float = 0.1, delta: float = 0.0, tol: float = 1e-6,
-                  k_override: int | None = None, maxit: int | None = None):
+                  k_override: int | None = None, maxit: int | None = None,
+                  want_X: bool = True):
     """Algorithm 2 (subspace-upsampling approximate decoder).
 
     1. SVD of X~; 2. rank k (see svd_rank); 3. upsample every column of
     U~ on L_r and of V~ on L_c (Lemma 1); 4. unit-normalise the columns
     of U and V; 5. Sigma = sqrt(n p / (rho_r rho_c (1 - delta))) Sigma~,
     delta (never given a value) defaults to 0; 6. X = U Sigma V^T.
-    Returns dict with X, U, V, sigma, k and CG statistics.
+    Returns dict with X (None when ``want_X`` is false: step 6 is then left
+    to the caller, for matrices too large to hold), U, V, sigma, k and CG
+    statistics.
     """
     rho_r, rho_c = Xt.shape
     Ut, s, Vh, k = svd_rank(Xt, ratio)
@@ -395,7 +398,7 @@ def approx_decode(Xt, omega_r, omega_c, p: int, n: int, Lr, Lc,
     Us = Us / np.linalg.norm(Us, axis=0, keepdims=True)
     Vs = Vs / np.linalg.norm(Vs, axis=0, keepdims=True)
     sig = math.sqrt(n * p / (rho_r * rho_c * (1.0 - delta))) * s[:k]
-    X = (Us * sig) @ Vs.T
+    X = (Us * sig) @ Vs.T if want_X else None
     return {"X": X, "U": Us, "V": Vs, "sigma": sig, "k": k, "s_tilde": s,
             "cg_iters_u": its_u, "cg_iters_v": its_v, "res_u": res_u, "res_v": res_v}
 

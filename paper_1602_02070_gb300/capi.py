@@ -24,11 +24,12 @@ CPCA_ERR_SINGULAR = 4
 CPCA_ERR_NOT_CONVERGED = 5
 CPCA_ERR_TIMEOUT = 6
 CPCA_ERR_CAPACITY = 7
+CPCA_ERR_NONFINITE = 8
 LAP_NORMALIZED = 0
 LAP_COMBINATORIAL = 1
 
 _STATUS = {1: "INVALID_ARG", 2: "CUDA", 3: "WORKSPACE", 4: "SINGULAR", 5: "NOT_CONVERGED",
-           6: "TIMEOUT", 7: "CAPACITY"}
+           6: "TIMEOUT", 7: "CAPACITY", 8: "NONFINITE"}
 
 
 class CpcaError(RuntimeError):
@@ -128,6 +129,8 @@ _SIGS = [
      [C.c_void_p, C.c_int32, C.c_int32, C.c_int64, C.POINTER(cpca_csr), C.POINTER(cpca_csr),
       C.POINTER(cpca_frpcag_params), C.c_void_p, C.c_int64, C.POINTER(cpca_solve_info),
       C.c_void_p]),
+    ("cpca_frpcag_status", C.c_int32, [C.c_void_p, C.c_void_p]),
+    ("cpca_debug_set_barrier_spin_limit", C.c_int32, [C.c_int64]),
     ("cpca_frpcag_batched_workspace_size", C.c_size_t, [C.c_void_p, C.c_int32]),
     ("cpca_frpcag_solve_batched", C.c_int32,
      [C.c_void_p, C.c_int32, C.POINTER(cpca_frpcag_params), C.c_void_p, C.c_void_p, C.c_size_t,
@@ -229,8 +232,29 @@ def _require_cuda(t: torch.Tensor, dtype, name: str):
         raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
 
 
+def _require_matrix(t, rows: int, cols: int, name: str, like: torch.Tensor | None = None):
+    """A float32 CUDA matrix of exactly rows x cols with unit column stride
+    (row-major rows, any leading dimension), on the device of ``like``.
+    Checked before any launch: a smaller buffer would be written past its
+    end on the device."""
+    _require_cuda(t, torch.float32, name)
+    if t.dim() != 2 or tuple(t.shape) != (rows, cols):
+        raise ValueError(f"{name} must be {rows} x {cols}, got {tuple(t.shape)}")
+    if t.stride(1) != 1 or t.stride(0) < cols:
+        raise ValueError(f"{name} must be row-major with unit column stride")
+    if like is not None and t.device != like.device:
+        raise ValueError(f"{name} is on {t.device}, expected {like.device}")
+
+
 def _workspace(nbytes: int, device) -> torch.Tensor:
-    return torch.empty(max(int(nbytes), 256), dtype=torch.uint8, device=device)
+    """Scratch for one call. CPCA_FAULT=alloc (host-side fault injection)
+    makes this fail as a real allocation failure would, before any launch."""
+    if os.environ.get("CPCA_FAULT") == "alloc":
+        raise CpcaError(CPCA_ERR_WORKSPACE, "injected workspace allocation failure (CPCA_FAULT=alloc)")
+    try:
+        return torch.empty(max(int(nbytes), 256), dtype=torch.uint8, device=device)
+    except torch.cuda.OutOfMemoryError as e:
+        raise CpcaError(CPCA_ERR_WORKSPACE, f"workspace of {int(nbytes)} bytes: {e}") from e
 
 
 def knn_last_bruteforce() -> int:
@@ -367,9 +391,11 @@ def cpca_frpcag_solve(Yt: torch.Tensor, Lr: Csr, Lc: Csr, params: cpca_frpcag_pa
                       want_info: bool = True, out: torch.Tensor | None = None, ws=None, **kw):
     """FISTA for FRPCAG on Y~ (rr x rc). Returns (X, info or None)."""
     _require_cuda(Yt, torch.float32, "Yt")
+    rr, rc = Yt.shape if Yt.dim() == 2 else (0, 0)
+    _require_matrix(Yt, rr, rc, "Yt")
     prm = params if params is not None else frpcag_params(**kw)
-    rr, rc = Yt.shape
-    X = out if out is not None else torch.empty_like(Yt)
+    X = out if out is not None else torch.empty(rr, rc, dtype=torch.float32, device=Yt.device)
+    _require_matrix(X, rr, rc, "out", Yt)
     if ws is None:
         ws = _workspace(lib().cpca_frpcag_workspace_size(rr, rc), Yt.device)
     info = cpca_solve_info() if want_info else None
@@ -388,9 +414,11 @@ def cpca_frpcag_solve_noalloc(Yt: torch.Tensor, Lr: Csr, Lc: Csr,
     workspace (for callers that cannot allocate device memory; problems up to
     the built-in scratch size). Returns (X, info or None)."""
     _require_cuda(Yt, torch.float32, "Yt")
+    rr, rc = Yt.shape if Yt.dim() == 2 else (0, 0)
+    _require_matrix(Yt, rr, rc, "Yt")
     prm = params if params is not None else frpcag_params(**kw)
-    rr, rc = Yt.shape
     X = out if out is not None else torch.empty(rr, rc, dtype=torch.float32, device=Yt.device)
+    _require_matrix(X, rr, rc, "out", Yt)
     info = cpca_solve_info() if want_info else None
     lr, lc = Lr.c(), Lc.c()
     _check(lib().cpca_frpcag_solve_noalloc(_ptr(Yt), rr, rc, Yt.stride(0), C.byref(lr), C.byref(lc),
@@ -398,6 +426,20 @@ def cpca_frpcag_solve_noalloc(Yt: torch.Tensor, Lr: Csr, Lc: Csr,
                                            C.byref(info) if info is not None else None,
                                            _stream()))
     return X, info
+
+
+def cpca_frpcag_status(ws: torch.Tensor | None = None) -> None:
+    """Raises CpcaError(CPCA_ERR_TIMEOUT) if a grid barrier of the last
+    FISTA solve on ``ws`` (None: the built-in no-allocation scratch) gave
+    up. Synchronises the current stream. Info-less solves are asynchronous,
+    so this is where their timeouts surface."""
+    _check(lib().cpca_frpcag_status(_ptr(ws), _stream()))
+
+
+def debug_set_barrier_spin_limit(polls: int) -> None:
+    """Test hook: polls before a grid-barrier wait of a new launch gives up
+    (0 restores the default)."""
+    lib().cpca_debug_set_barrier_spin_limit(int(polls))
 
 
 def frpcag_tape_workspace(Yt: torch.Tensor, Lr: Csr, Lc: Csr, params: cpca_frpcag_params,
@@ -515,11 +557,14 @@ def cpca_decode(Xt: torch.Tensor, omega_r: torch.Tensor, omega_c: torch.Tensor, 
                 out: torch.Tensor | None = None, ws=None, check_status: bool = True, **kw):
     """Approximate decoder (Algorithm 2). Returns dict X, U, V, sigma, k, info, status."""
     _require_cuda(Xt, torch.float32, "Xt")
+    rr, rc = Xt.shape if Xt.dim() == 2 else (0, 0)
+    _require_matrix(Xt, rr, rc, "Xt")
     prm = params if params is not None else decode_params(**kw)
-    rr, rc = Xt.shape
     dev = Xt.device
     kmax = prm.kmax
     X = (out if out is not None else torch.empty(p, n, dtype=torch.float32, device=dev)) if want_X else None
+    if X is not None:
+        _require_matrix(X, p, n, "out", Xt)
     U = torch.empty(p, kmax, dtype=torch.float32, device=dev)
     V = torch.empty(n, kmax, dtype=torch.float32, device=dev)
     sig = torch.empty(kmax, dtype=torch.float64, device=dev)
@@ -569,9 +614,14 @@ def cpca_subspace_project(side: int, basis: torch.Tensor, k: int, Y: torch.Tenso
     (side 1: X = Y V V^T, basis V n x ldb), first k basis columns."""
     _require_cuda(Y, torch.float32, "Y")
     _require_cuda(basis, torch.float32, "basis")
-    p, n = Y.shape
+    p, n = Y.shape if Y.dim() == 2 else (0, 0)
+    _require_matrix(Y, p, n, "Y")
+    if basis.dim() != 2 or basis.stride(1) != 1 or basis.shape[0] != (p if side == 0 else n) \
+            or basis.shape[1] < k:
+        raise ValueError("basis must be row-major, (p or n) x (>= k)")
     ldb = basis.stride(0)
     X = out if out is not None else torch.empty(p, n, dtype=torch.float32, device=Y.device)
+    _require_matrix(X, p, n, "out", Y)
     if ws is None:
         ws = _workspace(lib().cpca_subspace_project_workspace_size(p, n, ldb), Y.device)
     _check(lib().cpca_subspace_project(side, _ptr(basis), ldb, k, _ptr(Y), Y.stride(0), p, n, _ptr(X),
@@ -589,9 +639,11 @@ def cpca_alternate_decode(Xt: torch.Tensor, omega_r: torch.Tensor, omega_c: torc
     """Alternate decoder (Eq. alternatedecoder) by PCG on the full p x n
     matrix. Returns (X, info, status)."""
     _require_cuda(Xt, torch.float32, "Xt")
+    rr, rc = Xt.shape if Xt.dim() == 2 else (0, 0)
+    _require_matrix(Xt, rr, rc, "Xt")
     prm = params if params is not None else alt_params(**kw)
-    rr, rc = Xt.shape
     X = out if out is not None else torch.empty(p, n, dtype=torch.float32, device=Xt.device)
+    _require_matrix(X, p, n, "out", Xt)
     if ws is None:
         ws = _workspace(lib().cpca_alternate_decode_workspace_size(p, n), Xt.device)
     info = cpca_alt_info()

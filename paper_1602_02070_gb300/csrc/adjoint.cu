@@ -1054,7 +1054,7 @@ cpca_status frpcag_adjoint(const AdjCall& c, AdjMode mode) {
   pa.rows = rr + rc;
   pa.T = T;
   pa.seed = prm->power_seed;
-  pa.bar = GridBar{w.bar_cnt, w.bar_cnt + kBarrierCounters, w.err};
+  pa.bar = grid_bar(w.bar_cnt, w.err);
   for (int g = 0; g < 2; ++g) {
     PowGraph& G = pa.g[g];
     G.L = g ? lc : lr;
@@ -1123,21 +1123,24 @@ cpca_status frpcag_adjoint(const AdjCall& c, AdjMode mode) {
   a.Pc = w.Pc;
   a.scal_bar = w.bar;
   a.tmap_c = w.tmap_c;
-  a.bar = GridBar{w.bar_cnt, w.bar_cnt + kBarrierCounters, w.err};
+  a.bar = grid_bar(w.bar_cnt, w.err);
   const size_t smem = sizeof(TrajSmem<int64_t>);
   const size_t smem_res = sizeof(TrajSmem<int32_t>);
-  static bool attr = false;
-  if (!attr) {
-    CPCA_CUDA(cudaFuncSetAttribute((const void*)traj_forward_kernel<false>,
-                                   cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
-    CPCA_CUDA(cudaFuncSetAttribute((const void*)traj_forward_kernel<true>,
-                                   cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem_res)));
-    CPCA_CUDA(cudaFuncSetAttribute((const void*)traj_reverse_kernel<false>,
-                                   cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
-    CPCA_CUDA(cudaFuncSetAttribute((const void*)traj_reverse_kernel<true>,
-                                   cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem_res)));
-    attr = true;
-  }
+  static PerDeviceOnce attr;
+  CPCA_CUDA(once_per_device(attr, [&] {
+    cudaError_t e = cudaFuncSetAttribute((const void*)traj_forward_kernel<false>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute((const void*)traj_forward_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               int(smem_res));
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute((const void*)traj_reverse_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               int(smem));
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute((const void*)traj_reverse_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               int(smem_res));
+    return e;
+  }));
   const int gf = coop_blocks((const void*)traj_forward_kernel<false>, 256, smem, a.ntiles);
   const int gb = coop_blocks((const void*)traj_reverse_kernel<false>, 256, smem, a.ntiles);
   const bool resident = mn < (size_t(1) << 31) && size_t(rc) * ldzt < (size_t(1) << 31) &&

@@ -427,14 +427,12 @@ extern "C" cpca_status cpca_alternate_decode(const float* Xt, int32_t rr, int32_
   a.X = X;
   a.ldx = ldx;
   a.xvec = ldx % 4 == 0 && reinterpret_cast<uintptr_t>(X) % 16 == 0;
-  a.bar = GridBar{w.bar, w.bar + kBarrierCounters, w.err};
+  a.bar = grid_bar(w.bar, w.err);
   const size_t smem = sizeof(AltSmem);
-  static bool attr = false;
-  if (!attr) {
-    CPCA_CUDA(cudaFuncSetAttribute((const void*)alt_cg_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   int(smem)));
-    attr = true;
-  }
+  static PerDeviceOnce attr;
+  CPCA_CUDA(once_per_device(attr, [&] {
+    return cudaFuncSetAttribute((const void*)alt_cg_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+  }));
   int grid = coop_blocks((const void*)alt_cg_kernel, 256, smem, std::min(a.ntiles, kAltMaxBlocks));
   if (prm->blocks > 0) grid = std::min(grid, int(prm->blocks));
   void* args[] = {&a};

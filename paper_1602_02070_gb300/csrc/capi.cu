@@ -1,5 +1,6 @@
 // capi.cu - library-wide C entry points: errors, version, launch count.
 #include <stdarg.h>
+#include <stdlib.h>
 
 #include <map>
 #include <mutex>
@@ -58,9 +59,38 @@ void prof_end() {
   g_pending = -1;
 }
 
+// ------------------------------------------------- failure-path hooks --
+// Barrier poll limit of new launches (cpca_debug_set_barrier_spin_limit),
+// and host-side fault injection through the CPCA_FAULT environment
+// variable: "timeout" makes every grid-barrier wait give up after one poll
+// (the kernels then return and the call reports CPCA_ERR_TIMEOUT), "nan"
+// makes cpca_frpcag_solve overwrite the first output entry with a NaN before
+// its FP64 objective is taken (the call then reports CPCA_ERR_NONFINITE).
+// Neither touches a GPU fault path: both run the library's own bounded
+// waits and checks.
+namespace {
+std::atomic<long long> g_spin_limit{0};  // 0: kBarrierSpinLimit
+}  // namespace
+
+bool fault_injected(const char* kind) {
+  const char* f = getenv("CPCA_FAULT");
+  return f && strcmp(f, kind) == 0;
+}
+
+long long barrier_spin_limit() {
+  if (fault_injected("timeout")) return 1;
+  const long long v = g_spin_limit.load(std::memory_order_relaxed);
+  return v > 0 ? v : kBarrierSpinLimit;
+}
+
 }  // namespace cpca
 
 extern "C" {
+
+int32_t cpca_debug_set_barrier_spin_limit(int64_t polls) {
+  cpca::g_spin_limit.store(polls > 0 ? (long long)polls : 0, std::memory_order_relaxed);
+  return 0;
+}
 
 /* Per-kernel event timing: see cpca.h. */
 int32_t cpca_profile_enable(int32_t on, const char* name_prefix) {

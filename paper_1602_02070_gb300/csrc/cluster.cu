@@ -208,7 +208,7 @@ extern "C" cpca_status cpca_cluster_decode(const float* Xt, int32_t rr, int32_t 
   a.lab = w.lab;
   a.changed = w.changed;
   a.steps = w.steps;
-  a.bar = GridBar{w.bar, w.bar + kBarrierCounters, w.err};
+  a.bar = grid_bar(w.bar, w.err);
   const int want = std::max<int>(int(ceil_div(rc, 8)), k * int(ceil_div(rr, 256)));
   const int grid = coop_blocks((const void*)kmeans_kernel, 256, 0, want);
   void* args[] = {&a};

@@ -9,6 +9,7 @@
 
 #include <algorithm>
 #include <atomic>
+#include <mutex>
 #include <string>
 
 #include "../../include/cpca.h"
@@ -82,27 +83,56 @@ struct Carve {
   size_t bytes() const { return (off + 255) & ~size_t(255); }
 };
 
-inline int num_sms() {
-  static int sms = -1;
-  if (sms < 0) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (sms <= 0) sms = 1;
+// ------------------------------------------------------ per-device state --
+// Kernel attributes and device queries belong to the current device, so
+// everything cached here is cached per device ordinal.
+constexpr int kMaxDevices = 64;
+
+inline int current_device() {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0) dev = 0;
+  return dev;
+}
+
+// Runs `fn` (returning cudaError_t) until it succeeds once on the current
+// device; later calls on that device return cudaSuccess at once.
+struct PerDeviceOnce {
+  std::mutex mu;
+  bool done[kMaxDevices] = {};
+};
+template <class F>
+cudaError_t once_per_device(PerDeviceOnce& o, F&& fn) {
+  const int dev = current_device();
+  if (dev >= kMaxDevices) return fn();
+  std::lock_guard<std::mutex> lk(o.mu);
+  if (o.done[dev]) return cudaSuccess;
+  const cudaError_t e = fn();
+  if (e == cudaSuccess) o.done[dev] = true;
+  return e;
+}
+
+// A device attribute of the current device, queried once per device.
+inline int device_attr(cudaDeviceAttr attr, std::atomic<int>* cache, int fallback) {
+  const int dev = current_device();
+  if (dev < kMaxDevices) {
+    const int v = cache[dev].load(std::memory_order_relaxed);
+    if (v > 0) return v;
   }
-  return sms;
+  int v = 0;
+  if (cudaDeviceGetAttribute(&v, attr, dev) != cudaSuccess || v <= 0) v = fallback;
+  if (dev < kMaxDevices) cache[dev].store(v, std::memory_order_relaxed);
+  return v;
+}
+
+inline int num_sms() {
+  static std::atomic<int> cache[kMaxDevices];
+  return device_attr(cudaDevAttrMultiProcessorCount, cache, 1);
 }
 
 // largest dynamic shared memory a block may opt into
 inline int max_smem_optin() {
-  static int bytes = -1;
-  if (bytes < 0) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&bytes, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    if (bytes <= 0) bytes = 48 * 1024;
-  }
-  return bytes;
+  static std::atomic<int> cache[kMaxDevices];
+  return device_attr(cudaDevAttrMaxSharedMemoryPerBlockOptin, cache, 48 * 1024);
 }
 
 inline unsigned ceil_div(int64_t a, int64_t b) { return static_cast<unsigned>((a + b - 1) / b); }
@@ -165,7 +195,17 @@ struct GridBar {
   unsigned int* count;  // zeroed before the launch
   unsigned int* gen;
   int* err;
+  long long limit;      // polls before a wait gives up (kBarrierSpinLimit)
 };
+
+// The poll limit new launches take (kBarrierSpinLimit unless a test set a
+// shorter one with cpca_debug_set_barrier_spin_limit).
+long long barrier_spin_limit();
+// Host-side fault injection: true when CPCA_FAULT names this kind.
+bool fault_injected(const char* kind);
+inline GridBar grid_bar(unsigned int* count, int* err) {
+  return GridBar{count, count + kBarrierCounters, err, barrier_spin_limit()};
+}
 
 __device__ __forceinline__ unsigned int ld_acquire_u32(const unsigned int* p) {
   unsigned int v;
@@ -195,7 +235,7 @@ __device__ __forceinline__ bool grid_sync(const GridBar& b) {
       long long spins = 0;
       while (ld_acquire_u32(b.gen) == g) {
         if (*(volatile int*)b.err) break;
-        if (++spins > kBarrierSpinLimit) {
+        if (++spins > b.limit) {
           atomicExch(b.err, 1);
           break;
         }

@@ -1035,7 +1035,7 @@ static cpca_status cg_setup(CgArgs& a, const cpca_csr* Lr, const cpca_csr* Lc, c
   }
   a.k = k;
   a.tol = prm->cg_tol;
-  a.bar = GridBar{w.bar, w.bar + kBarrierCounters, w.err};
+  a.bar = grid_bar(w.bar, w.err);
   a.acc = w.acc;
   a.acc_init = w.acc_init;
   a.out_iters = w.out_iters;

@@ -1079,11 +1079,9 @@ static cpca_status power_launch(PowerBatchArgs& pa, bool reverse, void* scratch,
   const size_t psm = size_t(max_smem_optin());
   const int ell_cap = int((psm - fixed) / sizeof(int2));
   const void* k = reverse ? (const void*)power_cluster_reverse_kernel : (const void*)power_cluster_kernel;
-  static bool attr[2] = {false, false};
-  if (!attr[reverse]) {
-    CPCA_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(psm)));
-    attr[reverse] = true;
-  }
+  static PerDeviceOnce attr[2];
+  CPCA_CUDA(once_per_device(attr[reverse],
+                            [&] { return cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(psm)); }));
   const int threads = 32 * ((nvw + kPowCtas - 1) / kPowCtas);
   if (reverse)
     power_cluster_reverse_kernel<<<kPowCtas, threads, psm, st>>>(pa, nvw, ell_cap);
@@ -1107,7 +1105,7 @@ cpca_status power_tape_run(const PowerTape* P, int ng, int T, uint64_t seed, boo
   pa->ngraph = ng;
   pa->iters = T;
   pa->seed = seed;
-  pa->bar = GridBar{bar, bar + kBarrierCounters, err};
+  pa->bar = grid_bar(bar, err);
   for (int g = 0; g < ng; ++g) {
     PowerGraph& G = pa->g[g];
     G.L = P[g].L;
@@ -1133,6 +1131,9 @@ cpca_status fista_batch_run(const BatchProblem* P, int n, int J, double eps, boo
                             cudaStream_t st, bool dense) {
   CPCA_TRY(ensure_mu_table());
   std::lock_guard<std::mutex> lk(g_tab_mu);
+  // the timeout flag covers every launch of this solve (power iterations
+  // and FISTA); it is read by read_infos or cpca_frpcag_status
+  CPCA_CUDA(cudaMemsetAsync(w.err, 0, sizeof(int), st));
   // power iterations (instances without a given step), then lambda
   PowerBatchArgs& pa = g_pa;
   pa.ngraph = 0;
@@ -1149,9 +1150,8 @@ cpca_status fista_batch_run(const BatchProblem* P, int n, int J, double eps, boo
   if (pa.ngraph > 0) {
     pa.iters = power_iters;
     pa.seed = power_seed;
-    pa.bar = GridBar{w.bar, w.bar + kBarrierCounters, w.err};
+    pa.bar = grid_bar(w.bar, w.err);
     CPCA_CUDA(cudaMemsetAsync(w.bar, 0, sizeof(unsigned int) * (kBarrierCounters + 1), st));
-    CPCA_CUDA(cudaMemsetAsync(w.err, 0, sizeof(int), st));
     bool done = false;
     CPCA_PROF("power_iter", st);
     CPCA_TRY(power_launch(pa, false, w.pscr, st, &done));
@@ -1206,7 +1206,7 @@ cpca_status fista_batch_run(const BatchProblem* P, int n, int J, double eps, boo
   fa.J = J;
   fa.eps = eps;
   fa.want_last = want_last ? 1 : 0;
-  fa.bar = GridBar{w.bar, w.bar + kBarrierCounters, w.err};
+  fa.bar = grid_bar(w.bar, w.err);
   init_batch_kernel<<<std::min(tiles, num_sms() * 8), 256, 0, st>>>(fa);
   CPCA_LAUNCHED();
   if (J == 0) return CPCA_OK;
@@ -1255,16 +1255,14 @@ cpca_status fista_batch_run(const BatchProblem* P, int n, int J, double eps, boo
     return CPCA_OK;
   }
   CPCA_CUDA(cudaMemsetAsync(w.bar, 0, sizeof(unsigned int) * (kBarrierCounters + 1), st));
-  CPCA_CUDA(cudaMemsetAsync(w.err, 0, sizeof(int), st));
   const size_t smem = sizeof(TileSmem), smem_res = sizeof(TileSmem32);
   const void* kres = (const void*)fista_batch_kernel<true>;
   const void* kstr = (const void*)fista_batch_kernel<false>;
-  static bool attr = false;
-  if (!attr) {
-    CPCA_CUDA(cudaFuncSetAttribute(kres, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem_res)));
-    CPCA_CUDA(cudaFuncSetAttribute(kstr, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
-    attr = true;
-  }
+  static PerDeviceOnce attr;
+  CPCA_CUDA(once_per_device(attr, [&] {
+    const cudaError_t e = cudaFuncSetAttribute(kres, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem_res));
+    return e != cudaSuccess ? e : cudaFuncSetAttribute(kstr, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+  }));
   // 32-bit staged offsets: every instance's Z and ZT below 2^31 entries
   bool small = true;
   for (int i = 0; i < n; ++i)
@@ -1344,6 +1342,12 @@ static cpca_status read_infos(const BatchProblem* P, int n, const BatchWs& w, in
   if (err) {
     set_error("frpcag: grid barrier timed out");
     return CPCA_ERR_TIMEOUT;
+  }
+  for (int i = 0; i < n; ++i) {
+    if (infos[i] && !std::isfinite(hs[size_t(i) * 12 + 11])) {
+      set_error("frpcag: problem %d has a non-finite objective (NaN or Inf in Y~ or the output)", i);
+      return CPCA_ERR_NONFINITE;
+    }
   }
   for (int i = 0; i < n; ++i) {
     cpca_solve_info* info = infos[i];
@@ -1459,6 +1463,7 @@ extern "C" cpca_status cpca_frpcag_solve(const float* Yt, int32_t rr, int32_t rc
   }
   CPCA_TRY(fista_batch_run(&P, 1, prm->max_iter, prm->eps, info != nullptr, prm->power_iters,
                            prm->power_seed, prm->blocks, w, st, dense));
+  if (fault_injected("nan")) CPCA_CUDA(cudaMemsetAsync(X, 0xff, sizeof(float), st));  // a NaN
   if (info) {
     cpca_solve_info* infos[1] = {info};
     CPCA_TRY(read_infos(&P, 1, w, prm->max_iter, infos, st));
@@ -1589,6 +1594,24 @@ cpca_status noalloc_base(void** out) {
 }
 
 }  // namespace
+
+extern "C" cpca_status cpca_frpcag_status(const void* ws, void* stream) {
+  clear_error();
+  void* base = const_cast<void*>(ws);
+  if (!base) CPCA_TRY(noalloc_base(&base));
+  // the flag sits at the same place in every FISTA workspace layout
+  const int one = 1;
+  const BatchWs w = batch_layout(base, &one, &one, 1);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  int err = 0;
+  CPCA_CUDA(cudaMemcpyAsync(&err, w.err, sizeof(int), cudaMemcpyDeviceToHost, st));
+  CPCA_CUDA(cudaStreamSynchronize(st));
+  if (err) {
+    set_error("frpcag: a grid barrier timed out in the last solve on this workspace");
+    return CPCA_ERR_TIMEOUT;
+  }
+  return CPCA_OK;
+}
 
 extern "C" cpca_status cpca_frpcag_solve_noalloc(const float* Yt, int32_t rr, int32_t rc,
                                                  int64_t ldyt, const cpca_csr* Lr,

@@ -9,9 +9,12 @@
 //      when the shapes allow);
 //   2. recheck: the candidates' squared distances are recomputed directly as
 //      sum_t (a_t - b_t)^2 in FP32 with a fixed summation tree (so d2(i,j)
-//      and d2(j,i) are bitwise equal) and the K best are kept, ties by index;
-//      a certificate checks that no point outside the candidate lists can
-//      beat the K-th; queries that fail it are redone by brute force;
+//      and d2(j,i) are bitwise equal); candidates whose order against the
+//      K-th the FP32 error bound cannot settle are re-scored in FP64, so the
+//      K kept are the K nearest by exact distance, ties by index; a
+//      certificate checks that no point outside the candidate lists can
+//      beat the K-th; queries that fail it are redone by brute force over
+//      the whole grid;
 //   3. graph: OR-symmetrised edge lists, sigma^2, Gaussian weights, degrees
 //      and the Laplacian in CSR with sorted columns and explicit diagonal.
 #include "common.cuh"
@@ -187,86 +190,64 @@ __device__ __forceinline__ float exact_d2_warp(const float* __restrict__ a,
   return __shfl_sync(0xffffffffu, s, 0);
 }
 
+// The same distance in FP64 (direct differences of the FP32 inputs, which
+// are exact in FP64; lane-strided FP64 sums, then a butterfly): relative
+// error about (d/32 + 5) 2^-53, used only to order candidates that the FP32
+// value cannot separate.
+__device__ __forceinline__ double exact_d2_warp_f64(const float* __restrict__ a,
+                                                    const float* __restrict__ b, int d, bool vec4) {
+  const int lane = threadIdx.x & 31;
+  double s = 0.0;
+  if (vec4) {
+    const float4* a4 = reinterpret_cast<const float4*>(a);
+    const float4* b4 = reinterpret_cast<const float4*>(b);
+    for (int t = lane; t < (d >> 2); t += 32) {
+      const float4 x = __ldg(a4 + t), y = __ldg(b4 + t);
+      double dx = double(x.x) - double(y.x);
+      s = fma(dx, dx, s);
+      dx = double(x.y) - double(y.y);
+      s = fma(dx, dx, s);
+      dx = double(x.z) - double(y.z);
+      s = fma(dx, dx, s);
+      dx = double(x.w) - double(y.w);
+      s = fma(dx, dx, s);
+    }
+  } else {
+    for (int t = lane; t < d; t += 32) {
+      const double dx = double(__ldg(a + t)) - double(__ldg(b + t));
+      s = fma(dx, dx, s);
+    }
+  }
+  s = warp_sum(s);
+  return __shfl_sync(0xffffffffu, s, 0);
+}
+
+// Relative error bound of exact_d2_warp: each lane adds about d/32 rounded
+// squares of rounded differences in order (2 + d/32 roundings), then a
+// five-level butterfly; 16 covers the constant terms with margin.
+__host__ __device__ inline float exact_d2_tau(int d) { return float((d / 32.0 + 16.0) * 0x1.0p-24); }
+
 namespace {
 
 constexpr int RECHECK_WARPS = 4;
 
-// Recheck: warp per query. With e = err_rel (|q|^2 + max |b|^2) bounding
-// |ranking value - exact squared distance|, let a_K be the K-th smallest
-// ranking value over all candidates. A candidate whose ranking value
-// exceeds a_K + 2e has exact distance > a_K + e, while the K candidates at
-// or below a_K have exact distance <= a_K + e, so it cannot be among the K
-// nearest: only the candidates within a_K + 2e are re-scored exactly. The
-// K best of those (by (d2, j)) are kept and the certificate is evaluated.
-__global__ void __launch_bounds__(RECHECK_WARPS * 32)
-knn_recheck_kernel(const float* __restrict__ P, int N, int d, int64_t ld, bool vec4, int K,
-                   int M, int splits, const int32_t* __restrict__ cand_i,
-                   const float* __restrict__ cand_d, const float* __restrict__ nrm,
-                   const unsigned int* __restrict__ nmax_bits, float err_rel,
-                   int32_t* __restrict__ out_i, float* __restrict__ out_d,
-                   int32_t* __restrict__ redo, int32_t* __restrict__ n_redo) {
-  extern __shared__ float sm[];
-  const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int C = splits * M;
-  float* sa = sm + wib * C * 3;                           // ranking values
-  float* sd = sa + C;                                     // exact squared distances
-  int32_t* si = reinterpret_cast<int32_t*>(sd + C);       // candidate indices
-  const int q = blockIdx.x * RECHECK_WARPS + wib;
-  if (q >= N) return;
+// The K nearest of a warp's candidate set by exact distance. Candidate c
+// (c < C) is live when si[c] >= 0 and has the FP32 exact distance sd[c],
+// whose relative error is at most tau. With a_K the K-th smallest FP32
+// value, a candidate below a_K (1 - tau)/(1 + tau) is certainly among the K
+// nearest and one above a_K (1 + tau)/(1 - tau) certainly is not; the
+// candidates in between are re-scored in FP64 (s64) and the free places go
+// to the smallest of those, ties by index. Writes out_i/out_d (the FP32
+// distances, symmetric in i and j), consumes si (picked entries set to -1)
+// and returns the largest upper bound sd (1 + tau) of the chosen distances
+// (INF when fewer than K candidates are live).
+__device__ float resolve_knn(const float* __restrict__ P, int64_t ld, int d, bool vec4, int q, int K,
+                             int C, const float* sd, int32_t* si, double* s64, float tau,
+                             int32_t* __restrict__ out_i, float* __restrict__ out_d) {
+  const int lane = threadIdx.x & 31;
   const float INF = __int_as_float(0x7f800000);
-  const float e = err_rel * (nrm[q] + __uint_as_float(*nmax_bits));
-  for (int c = lane; c < C; c += 32) {
-    const int s = c / M, m = c % M;
-    const int64_t o = (int64_t(s) * N + q) * M + m;
-    const int j = cand_i[o];
-    si[c] = j;
-    const float a = cand_d[o];
-    sa[c] = j >= 0 && a == a ? a : INF;
-    sd[c] = INF;
-  }
-  __syncwarp();
-  // a_K: K rounds of a warp argmin over the ranking values
+  // a_K: K rounds of a warp argmin over (sd, index)
   float aK = INF;
-  {
-    uint32_t taken_lo = 0;  // lanes mark their own picks in registers per round
-    (void)taken_lo;
-    for (int r = 0; r < K; ++r) {
-      float bv = INF;
-      int bc = -1;
-      for (int c = lane; c < C; c += 32) {
-        const float v = sa[c];
-        if (si[c] >= 0 && v < bv) {
-          bv = v;
-          bc = c;
-        }
-      }
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        const float ov = __shfl_xor_sync(0xffffffffu, bv, o);
-        const int oc = __shfl_xor_sync(0xffffffffu, bc, o);
-        if (ov < bv || (ov == bv && oc >= 0 && (bc < 0 || oc < bc))) {
-          bv = ov;
-          bc = oc;
-        }
-      }
-      aK = bv;
-      if (lane == 0 && bc >= 0) si[bc] = -2 - si[bc];  // temporarily hide the pick
-      __syncwarp();
-    }
-    for (int c = lane; c < C; c += 32)
-      if (si[c] <= -2) si[c] = -2 - si[c];
-    __syncwarp();
-  }
-  const float window = aK + 2.f * e;
-  for (int c = 0; c < C; ++c) {
-    const int j = si[c];
-    if (j < 0 || !(sa[c] <= window)) continue;  // warp-uniform branch
-    float v = exact_d2_warp(P + int64_t(q) * ld, P + int64_t(j) * ld, d, vec4);
-    if (v != v) v = INF;  // NaN input ranks last
-    if (lane == 0) sd[c] = v;
-  }
-  __syncwarp();
-  float dK = 0.f;
   for (int r = 0; r < K; ++r) {
     float bd = INF;
     int bj = 0x7fffffff, bc = -1;
@@ -291,16 +272,153 @@ knn_recheck_kernel(const float* __restrict__ P, int N, int d, int64_t ld, bool v
         bc = oc;
       }
     }
-    if (lane == 0) {
-      out_i[int64_t(q) * K + r] = bj;
-      out_d[int64_t(q) * K + r] = bd;
-      if (bc >= 0) si[bc] = -1;
-    }
-    dK = bd;
+    aK = bd;
+    if (lane == 0 && bc >= 0) si[bc] = -2 - si[bc];  // hide the pick for the next round
     __syncwarp();
   }
+  for (int c = lane; c < C; c += 32)
+    if (si[c] <= -2) si[c] = -2 - si[c];
+  __syncwarp();
+  // classes: 0 certainly in, 1 undecided (FP64), 2 certainly out
+  const double lo = aK < INF ? double(aK) * (1.0 - tau) / (1.0 + tau) : double(INF);
+  const double hi = aK < INF ? double(aK) * (1.0 + tau) / (1.0 - tau) : double(INF);
+  for (int c = 0; c < C; ++c) {
+    const int j = si[c];
+    if (j < 0 || aK == INF) continue;  // warp-uniform
+    const double v = double(sd[c]);
+    if (v >= lo && v <= hi) {
+      const double w = exact_d2_warp_f64(P + int64_t(q) * ld, P + int64_t(j) * ld, d, vec4);
+      if (lane == 0) s64[c] = w;
+    }
+  }
+  __syncwarp();
+  float up = 0.f;
+  for (int r = 0; r < K; ++r) {
+    int bk = 3;  // class
+    double bv = 0.0;
+    int bj = 0x7fffffff, bc = -1;
+    for (int c = lane; c < C; c += 32) {
+      const int j = si[c];
+      if (j < 0) continue;
+      const double v32 = double(sd[c]);
+      const int k = (aK == INF || v32 < lo) ? 0 : (v32 <= hi ? 1 : 2);
+      if (k == 2) continue;
+      const double v = k == 0 ? v32 : s64[c];
+      if (k < bk || (k == bk && (v < bv || (v == bv && j < bj)))) {
+        bk = k;
+        bv = v;
+        bj = j;
+        bc = c;
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const int ok = __shfl_xor_sync(0xffffffffu, bk, o);
+      const double ov = __shfl_xor_sync(0xffffffffu, bv, o);
+      const int oj = __shfl_xor_sync(0xffffffffu, bj, o);
+      const int oc = __shfl_xor_sync(0xffffffffu, bc, o);
+      if (ok < bk || (ok == bk && (ov < bv || (ov == bv && oj < bj)))) {
+        bk = ok;
+        bv = ov;
+        bj = oj;
+        bc = oc;
+      }
+    }
+    const float dv = bc >= 0 ? sd[bc] : INF;
+    if (lane == 0) {
+      out_i[int64_t(q) * K + r] = bc >= 0 ? bj : 0x7fffffff;
+      out_d[int64_t(q) * K + r] = dv;
+      if (bc >= 0) si[bc] = -1;
+    }
+    up = fmaxf(up, dv * (1.f + tau));
+    __syncwarp();
+  }
+  return up;
+}
+
+// Recheck: warp per query. With e = err_rel (|q|^2 + max |b|^2) bounding
+// |ranking value - exact squared distance|, let a_K be the K-th smallest
+// ranking value over all candidates. A candidate whose ranking value
+// exceeds a_K + 2e has exact distance > a_K + e, while the K candidates at
+// or below a_K have exact distance <= a_K + e, so it cannot be among the K
+// nearest: only the candidates within a_K + 2e are re-scored exactly
+// (FP32, and FP64 where FP32 cannot decide: resolve_knn). Then the
+// certificate is evaluated.
+__global__ void __launch_bounds__(RECHECK_WARPS * 32)
+knn_recheck_kernel(const float* __restrict__ P, int N, int d, int64_t ld, bool vec4, int K,
+                   int M, int splits, const int32_t* __restrict__ cand_i,
+                   const float* __restrict__ cand_d, const float* __restrict__ nrm,
+                   const unsigned int* __restrict__ nmax_bits, float err_rel,
+                   int32_t* __restrict__ out_i, float* __restrict__ out_d,
+                   int32_t* __restrict__ redo, int32_t* __restrict__ n_redo) {
+  extern __shared__ double smd[];
+  const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int C = splits * M;
+  double* s64 = smd + size_t(wib) * C;                              // FP64 distances
+  float* sa = reinterpret_cast<float*>(smd + size_t(RECHECK_WARPS) * C) + size_t(wib) * C * 3;  // ranking values
+  float* sd = sa + C;                                     // exact squared distances
+  int32_t* si = reinterpret_cast<int32_t*>(sd + C);       // candidate indices
+  const int q = blockIdx.x * RECHECK_WARPS + wib;
+  if (q >= N) return;
+  const float INF = __int_as_float(0x7f800000);
+  const float e = err_rel * (nrm[q] + __uint_as_float(*nmax_bits));
+  for (int c = lane; c < C; c += 32) {
+    const int s = c / M, m = c % M;
+    const int64_t o = (int64_t(s) * N + q) * M + m;
+    const int j = cand_i[o];
+    si[c] = j;
+    const float a = cand_d[o];
+    sa[c] = j >= 0 && a == a ? a : INF;
+    sd[c] = INF;
+  }
+  __syncwarp();
+  // a_K: K rounds of a warp argmin over the ranking values
+  float aK = INF;
+  for (int r = 0; r < K; ++r) {
+    float bv = INF;
+    int bc = -1;
+    for (int c = lane; c < C; c += 32) {
+      const float v = sa[c];
+      if (si[c] >= 0 && v < bv) {
+        bv = v;
+        bc = c;
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const float ov = __shfl_xor_sync(0xffffffffu, bv, o);
+      const int oc = __shfl_xor_sync(0xffffffffu, bc, o);
+      if (ov < bv || (ov == bv && oc >= 0 && (bc < 0 || oc < bc))) {
+        bv = ov;
+        bc = oc;
+      }
+    }
+    aK = bv;
+    if (lane == 0 && bc >= 0) si[bc] = -2 - si[bc];  // temporarily hide the pick
+    __syncwarp();
+  }
+  for (int c = lane; c < C; c += 32)
+    if (si[c] <= -2) si[c] = -2 - si[c];
+  __syncwarp();
+  const float window = aK + 2.f * e;
+  for (int c = 0; c < C; ++c) {
+    const int j = si[c];
+    if (j < 0) continue;
+    if (!(sa[c] <= window)) {  // warp-uniform branch: never among the K nearest
+      __syncwarp();
+      if (lane == 0) si[c] = -1;
+      __syncwarp();
+      continue;
+    }
+    float v = exact_d2_warp(P + int64_t(q) * ld, P + int64_t(j) * ld, d, vec4);
+    if (v != v) v = INF;  // NaN input ranks last
+    if (lane == 0) sd[c] = v;
+  }
+  __syncwarp();
+  const float dK = resolve_knn(P, ld, d, vec4, q, K, C, sd, si, s64, exact_d2_tau(d), out_i, out_d);
   // Certificate: every point outside split s's list has a ranking value
-  // >= that list's last entry, hence an exact distance >= that minus e.
+  // >= that list's last entry, hence an exact distance >= that minus e,
+  // which must exceed every chosen exact distance (at most dK).
   if (lane == 0) {
     bool ok = dK < INF;
     for (int s = 0; s < splits; ++s) {
@@ -313,49 +431,91 @@ knn_recheck_kernel(const float* __restrict__ P, int N, int d, int64_t ld, bool v
   }
 }
 
-// Brute force for queries without a certificate: warp per query, every
-// other point scored with the same exact function.
-__global__ void knn_bruteforce_kernel(const float* __restrict__ P, int N, int d, int64_t ld,
-                                      bool vec4, int K, const int32_t* __restrict__ redo,
-                                      const int32_t* __restrict__ n_redo,
-                                      int32_t* __restrict__ out_i, float* __restrict__ out_d) {
-  __shared__ float ld_[RECHECK_WARPS][32];
-  __shared__ int32_t li[RECHECK_WARPS][32];
-  const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  for (int w = blockIdx.x * RECHECK_WARPS + wib; w < *n_redo; w += gridDim.x * RECHECK_WARPS) {
-    const int q = redo[w];
+// Brute force for queries without a certificate, spread over the grid.
+// Work item (r, c): redo query r of the batch [r0, r0 + nq) against points
+// [c * kBfChunk, (c + 1) * kBfChunk), one warp per item, every point scored
+// with the same exact FP32 function; the warp keeps the 32 nearest by
+// (d2, j) (lane l holds entry l, insertion by ballot) and writes them to
+// lists[r][c]. knn_bf_merge_kernel then takes, per query, the 32 nearest of
+// all its chunk lists and lets resolve_knn pick the K (FP64 where FP32 cannot
+// decide; a tie run longer than the 32 kept is cut at the 32nd).
+constexpr int kBfChunk = 512;
+constexpr int kBfBatch = 64;  // queries per brute-force pass
+
+__device__ __forceinline__ void warp_list_insert(float& ld_, int& li, float v, int j) {
+  const int lane = threadIdx.x & 31;
+  const float last = __shfl_sync(0xffffffffu, ld_, 31);
+  const int lastj = __shfl_sync(0xffffffffu, li, 31);
+  if (!(lastj < 0 || v < last || (v == last && j < lastj))) return;  // warp-uniform
+  const bool before = li >= 0 && (ld_ < v || (ld_ == v && li < j));
+  const int pos = __popc(__ballot_sync(0xffffffffu, before));
+  const float up = __shfl_up_sync(0xffffffffu, ld_, 1);
+  const int upj = __shfl_up_sync(0xffffffffu, li, 1);
+  if (lane > pos) {
+    ld_ = up;
+    li = upj;
+  } else if (lane == pos) {
+    ld_ = v;
+    li = j;
+  }
+}
+
+__global__ void __launch_bounds__(RECHECK_WARPS * 32)
+knn_bf_score_kernel(const float* __restrict__ P, int N, int d, int64_t ld, bool vec4,
+                    const int32_t* __restrict__ redo, int r0, int nq, float* __restrict__ lists_d,
+                    int32_t* __restrict__ lists_i) {
+  const int lane = threadIdx.x & 31;
+  const int nch = (N + kBfChunk - 1) / kBfChunk;
+  const int64_t items = int64_t(nq) * nch;
+  for (int64_t w = int64_t(blockIdx.x) * RECHECK_WARPS + (threadIdx.x >> 5); w < items;
+       w += int64_t(gridDim.x) * RECHECK_WARPS) {
+    const int r = int(w / nch), c = int(w % nch);
+    const int q = redo[r0 + r];
     const float* a = P + int64_t(q) * ld;
-    if (lane < 32) {
-      ld_[wib][lane] = __int_as_float(0x7f800000);
-      li[wib][lane] = 0x7fffffff;
-    }
-    __syncwarp();
-    for (int j = 0; j < N; ++j) {
+    float dl = __int_as_float(0x7f800000);
+    int il = -1;
+    const int j1 = min(N, (c + 1) * kBfChunk);
+    for (int j = c * kBfChunk; j < j1; ++j) {
       if (j == q) continue;
       float v = exact_d2_warp(a, P + int64_t(j) * ld, d, vec4);
       if (v != v) v = __int_as_float(0x7f800000);
-      if (lane == 0) {
-        float* L = ld_[wib];
-        int32_t* I = li[wib];
-        if (v < L[K - 1] || (v == L[K - 1] && j < I[K - 1])) {
-          int pos = K - 1;
-          while (pos > 0 && (v < L[pos - 1] || (v == L[pos - 1] && j < I[pos - 1]))) {
-            L[pos] = L[pos - 1];
-            I[pos] = I[pos - 1];
-            --pos;
-          }
-          L[pos] = v;
-          I[pos] = j;
-        }
-      }
-      __syncwarp();
+      warp_list_insert(dl, il, v, j);
     }
-    if (lane < K) {
-      out_i[int64_t(q) * K + lane] = li[wib][lane];
-      out_d[int64_t(q) * K + lane] = ld_[wib][lane];
-    }
-    __syncwarp();
+    lists_d[w * 32 + lane] = dl;
+    lists_i[w * 32 + lane] = il;
   }
+}
+
+__global__ void __launch_bounds__(RECHECK_WARPS * 32)
+knn_bf_merge_kernel(const float* __restrict__ P, int N, int d, int64_t ld, bool vec4, int K,
+                    const int32_t* __restrict__ redo, int r0, int nq, const float* __restrict__ lists_d,
+                    const int32_t* __restrict__ lists_i, int32_t* __restrict__ out_i,
+                    float* __restrict__ out_d) {
+  __shared__ double l64[RECHECK_WARPS][32];
+  __shared__ float sd[RECHECK_WARPS][32];
+  __shared__ int32_t si[RECHECK_WARPS][32];
+  const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int r = blockIdx.x * RECHECK_WARPS + wib;
+  if (r >= nq) return;
+  const int q = redo[r0 + r];
+  const int nch = (N + kBfChunk - 1) / kBfChunk;
+  float dl = __int_as_float(0x7f800000);
+  int il = -1;
+  for (int c = 0; c < nch; ++c) {
+    const int64_t o = (int64_t(r) * nch + c) * 32;
+    const float vd = lists_d[o + lane];
+    const int vi = lists_i[o + lane];
+    for (int t = 0; t < 32; ++t) {  // entries in list order (ascending)
+      const float v = __shfl_sync(0xffffffffu, vd, t);
+      const int j = __shfl_sync(0xffffffffu, vi, t);
+      if (j < 0) break;  // warp-uniform: the rest of the list is empty
+      warp_list_insert(dl, il, v, j);
+    }
+  }
+  sd[wib][lane] = dl;
+  si[wib][lane] = il;
+  __syncwarp();
+  resolve_knn(P, ld, d, vec4, q, K, min(32, N - 1), sd[wib], si[wib], l64[wib], exact_d2_tau(d), out_i, out_d);
 }
 
 // ------------------------------------------------------------ graph build --
@@ -522,6 +682,8 @@ struct KnnWs {
   float* kd2;
   int32_t* redo;
   int32_t* n_redo;
+  float* bf_d;        // brute-force chunk lists [kBfBatch][chunks][32]
+  int32_t* bf_i;
   int* err;
   double* part;
   double* sigma2;
@@ -556,6 +718,11 @@ static KnnWs knn_layout(void* ws, int N, int d, int K, int transposed) {
   w.kd2 = c.take<float>(size_t(N) * K);
   w.redo = c.take<int32_t>(N);
   w.n_redo = c.take<int32_t>(1);
+  {
+    const size_t lists = size_t(kBfBatch) * ((N + kBfChunk - 1) / kBfChunk) * 32;
+    w.bf_d = c.take<float>(lists);
+    w.bf_i = c.take<int32_t>(lists);
+  }
   w.err = c.take<int>(1);
   w.part = c.take<double>(RED_BLOCKS);
   w.sigma2 = c.take<double>(1);
@@ -604,17 +771,29 @@ cpca_status knn_lists(const float* P, int N, int d, int64_t ld, int K, const Knn
   // roundings of size 2^-24 relative to |a|^2 + |b|^2 (the tensor-core pass
   // reports its own, larger, bound through knn_candidates_tc).
   const float err_rel = done ? knn_tc_err_rel(d) : float((4.0 * sqrt(double(d)) + 16.0) * 0x1.0p-24);
-  const size_t rsm = size_t(RECHECK_WARPS) * S * M * 12;
+  const size_t rsm = size_t(RECHECK_WARPS) * S * M * 20;
   CPCA_CUDA(cudaFuncSetAttribute(knn_recheck_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(rsm)));
   CPCA_PROF("knn_recheck", st);
   knn_recheck_kernel<<<ceil_div(N, RECHECK_WARPS), RECHECK_WARPS * 32, rsm, st>>>(
       P, N, d, ld, vec4, K, M, S, w.cand_i, w.cand_d, w.nrm, w.nmax, err_rel, out_i, out_d, w.redo,
       w.n_redo);
   CPCA_LAUNCHED();
-  CPCA_PROF("knn_bruteforce", st);
-  knn_bruteforce_kernel<<<num_sms() * 4, RECHECK_WARPS * 32, 0, st>>>(P, N, d, ld, vec4, K, w.redo,
-                                                                       w.n_redo, out_i, out_d);
-  CPCA_LAUNCHED();
+  // queries without a certificate (rare): how many, then brute force in
+  // batches of kBfBatch over the whole grid
+  int nredo = 0;
+  CPCA_CUDA(cudaMemcpyAsync(&nredo, w.n_redo, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+  CPCA_CUDA(cudaStreamSynchronize(st));
+  for (int r0 = 0; r0 < nredo; r0 += kBfBatch) {
+    const int nq = std::min(kBfBatch, nredo - r0);
+    const int64_t items = int64_t(nq) * ((N + kBfChunk - 1) / kBfChunk);
+    const unsigned grid = unsigned(std::min<int64_t>((items + RECHECK_WARPS - 1) / RECHECK_WARPS, num_sms() * 16));
+    CPCA_PROF("knn_bruteforce", st);
+    knn_bf_score_kernel<<<grid, RECHECK_WARPS * 32, 0, st>>>(P, N, d, ld, vec4, w.redo, r0, nq, w.bf_d, w.bf_i);
+    CPCA_LAUNCHED();
+    knn_bf_merge_kernel<<<ceil_div(nq, RECHECK_WARPS), RECHECK_WARPS * 32, 0, st>>>(
+        P, N, d, ld, vec4, K, w.redo, r0, nq, w.bf_d, w.bf_i, out_i, out_d);
+    CPCA_LAUNCHED();
+  }
   return CPCA_OK;
 }
 

@@ -332,16 +332,11 @@ bool make_map(CUtensorMap* map, const float* P, int N, int d, int64_t ld, int bo
 }
 
 bool device_is_sm10x() {
-  static int cc = -1;
-  if (cc < 0) {
-    int dev = 0, major = 0, minor = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev);
-    cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev);
-    cudaGetLastError();
-    cc = major * 10 + minor;
-  }
-  return cc == 103;
+  static std::atomic<int> major[kMaxDevices], minor[kMaxDevices];
+  const int ma = device_attr(cudaDevAttrComputeCapabilityMajor, major, -1);
+  const int mi = device_attr(cudaDevAttrComputeCapabilityMinor, minor, -1);
+  cudaGetLastError();
+  return ma * 10 + mi == 103;
 }
 
 }  // namespace

@@ -52,11 +52,16 @@ def cpca_pipeline(Y: torch.Tensor, K: int = 10, fr: float = 0.25, fc: float = 0.
         Lct = capi.cpca_kron_reduce(Lc, om_c, tol=kron_tol)["csr"]
     mark("sample")
     prm = capi.frpcag_params(gamma_r, gamma_c, -1.0, J, 0.0, power_iters, power_seed)
-    Xt, finfo = capi.cpca_frpcag_solve(Yt, Lrt, Lct, prm, want_info=False)
+    fws = capi._workspace(capi.lib().cpca_frpcag_workspace_size(*Yt.shape), Y.device)
+    Xt, finfo = capi.cpca_frpcag_solve(Yt, Lrt, Lct, prm, want_info=False, ws=fws)
     mark("fista")
     dprm = capi.decode_params(rank_ratio, 0, kmax, delta, cg_tol, 0, svd_iters, 0)
     dec = capi.cpca_decode(Xt, om_r, om_c, p, n, Lr, Lc, dprm, want_X=want_X,
                            check_status=check_status)
+    # the info-less FISTA solve reports a barrier timeout through its
+    # workspace (the decoder has synchronised the stream already)
+    if check_status:
+        capi.cpca_frpcag_status(fws)
     mark("decode")
     dec.update({"Xt": Xt, "Yt": Yt, "omega_r": om_r, "omega_c": om_c, "Lr": Lr, "Lc": Lc,
                 "Lrt": Lrt, "Lct": Lct})

@@ -6,6 +6,8 @@ import pytest
 
 import gen
 import oracle as O
+from oracle.cpca_fista_c import frpcag_fista_c
+from tests._oracle_knn import oracle_knn_graph
 from tests._util import rel_fro
 
 torch = pytest.importorskip("torch")
@@ -114,23 +116,46 @@ def test_autotuner_and_graph_replay(M):
         assert torch.equal(a, b)
 
 
-def test_batched_workload_64_instances_equals_sequential(M):
+def test_batched_workload_64_instances(M):
     """The 64-instance workload (sizes p ~ U[500, 8000], n ~ U[200, 5000],
-    1/4 sampling, K = 10 graphs, gamma pairs over an 8 x 8 log grid): the
-    batched launch reproduces 64 separate solves exactly."""
+    1/4 sampling, K = 10 graphs, gamma pairs over an 8 x 8 log grid, J = 300)
+    in one batched launch: a seeded subset of six instances is built by the
+    oracle (its own sampling of the generator's Y and its own graphs) and
+    checked against the oracle's C restatement of Algorithm 1; every 7th
+    instance equals its separate solve exactly."""
     specs = gen.batched_instances(64)
-    probs = []
-    for sp in specs:
-        Y = gen.make_instance_torch(sp["seed"], sp["p"], sp["n"], sp["r"], sp["C"], sp["frac"])
-        rr, rc = M.rho_of(sp["p"], sp["fr"]), M.rho_of(sp["n"], sp["fc"])
-        _, _, Yt = M.cpca_sample(sp["seed"], sp["p"], sp["n"], rr, rc, Y)
+    J = specs[0]["J"]
+    subset = set(np.random.default_rng(17).choice(len(specs), size=6, replace=False).tolist())
+    probs, refs = [], {}
+    for i, sp_ in enumerate(specs):
+        Y = gen.make_instance_torch(sp_["seed"], sp_["p"], sp_["n"], sp_["r"], sp_["C"], sp_["frac"])
+        rr, rc = M.rho_of(sp_["p"], sp_["fr"]), M.rho_of(sp_["n"], sp_["fc"])
+        if i in subset:
+            om_r = O.sample_indices(sp_["seed"], sp_["p"], rr, 0)
+            om_c = O.sample_indices(sp_["seed"], sp_["n"], rc, 1)
+            Yt32 = Y.cpu().numpy()[np.ix_(om_r, om_c)]
+            Lr_o, *_ = oracle_knn_graph(Yt32, sp_["K"])
+            Lc_o, *_ = oracle_knn_graph(Yt32.T, sp_["K"])
+            refs[i] = (Yt32.astype(np.float64), Lr_o, Lc_o)
+            probs.append(dict(Yt=_dev(Yt32), Lr=M.Csr.from_scipy(Lr_o), Lc=M.Csr.from_scipy(Lc_o),
+                              gamma_r=sp_["gamma_r"], gamma_c=sp_["gamma_c"]))
+        else:
+            _, _, Yt = M.cpca_sample(sp_["seed"], sp_["p"], sp_["n"], rr, rc, Y)
+            Lr, _, _ = M.cpca_knn_graph(Yt, sp_["K"])
+            Lc, _, _ = M.cpca_knn_graph(Yt, sp_["K"], transposed=True)
+            probs.append(dict(Yt=Yt, Lr=Lr, Lc=Lc, gamma_r=sp_["gamma_r"], gamma_c=sp_["gamma_c"]))
         del Y
-        Lr, _, _ = M.cpca_knn_graph(Yt, sp["K"])
-        Lc, _, _ = M.cpca_knn_graph(Yt, sp["K"], transposed=True)
-        probs.append(dict(Yt=Yt, Lr=Lr, Lc=Lc, gamma_r=sp["gamma_r"], gamma_c=sp["gamma_c"]))
-    J = 40
     B = M.Batch(probs)
     Xs, infos = B.solve(M.frpcag_params(max_iter=J), want_info=True)
+    for i, (Yt_o, Lr_o, Lc_o) in sorted(refs.items()):
+        q, info = probs[i], infos[i]
+        nr, nc = O.power_norm(Lr_o, 200, 0, 2), O.power_norm(Lc_o, 200, 0, 3)
+        assert info.norm_r == pytest.approx(nr, rel=1e-6)
+        assert info.norm_c == pytest.approx(nc, rel=1e-6)
+        lam = O.fista_step(q["gamma_r"], q["gamma_c"], nr, nc)
+        Xo, _ = frpcag_fista_c(Yt_o, Lr_o, Lc_o, q["gamma_r"], q["gamma_c"], lam, J)
+        assert info.iters == J
+        assert rel_fro(Xs[i].cpu().numpy(), Xo) < FISTA_TOL
     for q, X, info in list(zip(probs, Xs, infos))[::7]:
         # the batch's power iterations run grid-wide, a single solve's in one
         # thread-block cluster: the same per-row and per-warp arithmetic, so

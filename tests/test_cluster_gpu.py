@@ -14,7 +14,7 @@ import pytest
 import gen
 import oracle as O
 from oracle import cpca_decoders as D
-from tests._oracle_pool import OraclePool
+from tests._oracle_knn import oracle_knn_graph
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -63,11 +63,7 @@ def test_cluster_decoder_full_size(M):
     cfg = gen.CONFIGS["bench_10304x1000"]
     p, n = cfg["p"], cfg["n"]
     Y, _, _ = gen.make_instance(0, p, n, cfg["r"], cfg["C"], cfg["frac"])
-    pool = OraclePool()
-    try:
-        Lc, _, _, _ = pool.knn_graph(Y.T.astype(np.float64), cfg["K"])
-    finally:
-        pool.close()
+    Lc, _, _, _ = oracle_knn_graph(Y.T, cfg["K"])
     rr, rc = M.rho_of(p, cfg["fr"]), M.rho_of(n, cfg["fc"])
     om_r, om_c = O.sample_indices(0, p, rr, 0), O.sample_indices(0, n, rc, 1)
     Xt = O.sample_matrix(Y.astype(np.float64), om_r, om_c)

@@ -23,7 +23,7 @@ import scipy.sparse.csgraph as csg
 import gen
 import oracle as O
 from oracle import cpca_kron as KR
-from tests._oracle_pool import OraclePool
+from tests._oracle_knn import oracle_knn_graph
 from tests._util import rel_fro
 
 torch = pytest.importorskip("torch")
@@ -209,12 +209,8 @@ def test_kron_full_size_and_fista(M):
     p, n, K = cfg["p"], cfg["n"], cfg["K"]
     Y, _, _ = gen.make_instance(0, p, n, cfg["r"], cfg["C"], cfg["frac"])
     Yd = Y.astype(np.float64)
-    pool = OraclePool()
-    try:
-        Lr, _, _, _ = pool.knn_graph(Yd, K)
-        Lc, _, _, _ = pool.knn_graph(Yd.T, K)
-    finally:
-        pool.close()
+    Lr, _, _, _ = oracle_knn_graph(Y, K)
+    Lc, _, _, _ = oracle_knn_graph(Y.T, K)
     rr, rc = M.rho_of(p, cfg["fr"]), M.rho_of(n, cfg["fc"])
     om_r, om_c = O.sample_indices(0, p, rr, 0), O.sample_indices(0, n, rc, 1)
     Lrt_o, Lct_o = KR.kron_reduce(Lr, om_r), KR.kron_reduce(Lc, om_c)

@@ -171,8 +171,10 @@ cpca_status cpca_sample(uint64_t seed, int32_t p, int32_t n, int32_t rho_r, int3
  * 3 for Lc)), or 1 when that denominator is 0. With eps > 0 the loop stops
  * once |Z_{j+1} - Z_j|_F^2 < eps |Z_j|_F^2 (tested on the device after every
  * iteration); eps = 0 runs exactly max_iter iterations. All iterations run
- * in one cooperative kernel (one bounded grid barrier per iteration); the
- * call does not synchronise unless `info` is given. The output X (rr x rc,
+ * in one cooperative kernel (one bounded grid barrier per iteration), or,
+ * for a single problem too large to keep every tile resident, in one striped
+ * launch per iteration (see params.blocks; the same iterates bit for bit);
+ * the call does not synchronise unless `info` is given. The output X (rr x rc,
  * leading dimension ldx) is the last S_j. FP32 arithmetic, FP64 reductions.
  * Lr is rr x rr, Lc is rc x rc, both symmetric.
  * Dense Laplacians (the Kron reductions of Sec. IV-A): when both CSRs hold
@@ -198,10 +200,29 @@ typedef struct cpca_frpcag_params {
   int32_t power_iters;  /* power iterations per Laplacian (>= 1) */
   uint64_t power_seed;
   int32_t blocks;       /* FISTA launch width (blocks); 0 = automatic: one block per
-                           32 x 32 tile when all tiles fit on the GPU at once,
-                           else the autotuner's choice for this tile count if
+                           32 x 32 tile when all tiles fit on the GPU at once;
+                           else, for a single problem with 256 <= rr and a
+                           stripe of Z in shared memory (rr <= about 2800),
+                           the striped launch (one per iteration); else the
+                           autotuner's choice for this tile count if
                            cpca_frpcag_tune_batched has run, else the widest
-                           co-resident grid */
+                           co-resident grid. > 0 forces the cooperative
+                           kernel with that many blocks. */
+  /* Checkpoint and resume of Algorithm 1 (single solves; 0 / NULL for a
+   * cold start, and for the batched, tape and backward calls):
+   * start_iter = j0 > 0 resumes after iteration j0: on entry X holds S_{j0}
+   * and start_prev (device, rr x rc, leading dimension ldx) holds S_{j0-1}
+   * (Y~ when j0 = 1); the call computes Z_{j0+1} = S_{j0} + mu_{j0}
+   * (S_{j0} - S_{j0-1}) and runs iterations j0+1 .. j0+max_iter, t_j
+   * continuing the recurrence. prev_out (device, rr x rc, leading dimension
+   * ldx, may be NULL; needs eps = 0) receives S_{J-1}, the iterate before the
+   * returned one, so (X, prev_out, j0 + max_iter) resumes the solve. With
+   * the same lambda (a given step, or the same power iterations), J1
+   * iterations and a resumed J2 give X bit for bit equal to one call of
+   * J1 + J2 iterations. */
+  int32_t start_iter;
+  const float* start_prev;
+  float* prev_out;
 } cpca_frpcag_params;
 
 typedef struct cpca_solve_info {

@@ -46,7 +46,8 @@ class cpca_csr(C.Structure):
 class cpca_frpcag_params(C.Structure):
     _fields_ = [("gamma_r", C.c_double), ("gamma_c", C.c_double), ("step", C.c_double),
                 ("max_iter", C.c_int32), ("eps", C.c_double),
-                ("power_iters", C.c_int32), ("power_seed", C.c_uint64), ("blocks", C.c_int32)]
+                ("power_iters", C.c_int32), ("power_seed", C.c_uint64), ("blocks", C.c_int32),
+                ("start_iter", C.c_int32), ("start_prev", C.c_void_p), ("prev_out", C.c_void_p)]
 
 
 class cpca_solve_info(C.Structure):
@@ -382,9 +383,17 @@ def cpca_sample(seed: int, p: int, n: int, rho_r: int, rho_c: int, Y: torch.Tens
 
 
 def frpcag_params(gamma_r=1.0, gamma_c=1.0, step=-1.0, max_iter=300, eps=0.0,
-                  power_iters=200, power_seed=0, blocks=0) -> cpca_frpcag_params:
+                  power_iters=200, power_seed=0, blocks=0, start_iter=0, start_prev=None,
+                  prev_out=None) -> cpca_frpcag_params:
+    """Parameters of cpca_frpcag_solve; start_prev / prev_out are device
+    tensors (rr x rc, the leading dimension of the solve's output) or None:
+    the caller keeps them alive for the call."""
+    for name, t in (("start_prev", start_prev), ("prev_out", prev_out)):
+        if t is not None:
+            _require_cuda(t, torch.float32, name)
     return cpca_frpcag_params(gamma_r, gamma_c, step, max_iter, eps, power_iters, power_seed,
-                              blocks)
+                              blocks, start_iter, None if start_prev is None else start_prev.data_ptr(),
+                              None if prev_out is None else prev_out.data_ptr())
 
 
 def cpca_frpcag_solve(Yt: torch.Tensor, Lr: Csr, Lc: Csr, params: cpca_frpcag_params | None = None,

@@ -1025,6 +1025,8 @@ cpca_status check_adj(const AdjCall& c, const char* who) {
   CPCA_CHECK_ARG(c.prm->gamma_r >= 0 && c.prm->gamma_c >= 0, "%s: negative gamma", who);
   CPCA_CHECK_ARG(c.prm->step > 0 || c.prm->power_iters >= 1, "%s: power_iters < 1", who);
   CPCA_CHECK_ARG(c.ckpt_every >= 0, "%s: ckpt_every < 0", who);
+  CPCA_CHECK_ARG(c.prm->start_iter == 0 && !c.prm->prev_out,
+                 "%s: differentiates a cold-started solve (start_iter = 0, no prev_out)", who);
   CPCA_TRY(check_csr(c.Lr, c.rr, who));
   CPCA_TRY(check_csr(c.Lc, c.rc, who));
   return CPCA_OK;

@@ -452,6 +452,15 @@ struct FistaBatchArgs {
   double eps;
   int want_last;
   GridBar bar;
+  // warm start (single problems): iterations 1..j0 done before, S holds
+  // S_{j0}, warm_prev S_{j0-1}; mu0 = mu_{j0}, t0 = t_{j0+1}. prev_out
+  // (optional) receives S_{J-1} of this call.
+  int j0;
+  const float* warm_prev;
+  float* prev_out;
+  int pvec;  // prev_out rows allow 16-byte stores
+  float mu0;
+  double t0;
 };
 
 __device__ __forceinline__ int find_inst(const FistaBatchArgs& a, int tile) {
@@ -541,7 +550,8 @@ fista_batch_kernel(const __grid_constant__ FistaBatchArgs a) {
     rnj = min(TB, I.rc - rj0);
     stage_tile(sm, I, ri0, rj0, rni, rnj);
     if (rl < rni && cq < rnj)
-      rs = load4(I.Yt + int64_t(ri0 + rl) * I.ldy + rj0 + cq, I.yvec, rnj - cq);  // S_0 = Y~
+      rs = a.warm_prev ? load4(I.S + int64_t(ri0 + rl) * I.lds + rj0 + cq, I.svec, rnj - cq)  // S_{j0}
+                       : load4(I.Yt + int64_t(ri0 + rl) * I.ldy + rj0 + cq, I.yvec, rnj - cq);  // S_0 = Y~
   }
   double t = 1.0;  // t_j of Algorithm 1 (t_1 = 1)
   int jlast = a.J;
@@ -574,13 +584,17 @@ fista_batch_kernel(const __grid_constant__ FistaBatchArgs a) {
         break;
       }
     }
-    // mu_j from the table; beyond it, t_{j+1} in FP64 by one thread
+    // mu_jg of the global iteration jg = j0 + j from the table; beyond it,
+    // t_{jg+1} in FP64 by one thread (from the table's end, or from t0 when
+    // a resumed solve starts beyond it)
+    const int jg = a.j0 + j;
     float mu;
-    if (j < kMuTable) {
-      mu = c_mu[j];
+    if (jg < kMuTable) {
+      mu = c_mu[jg];
     } else {
       if (threadIdx.x == 0) {
-        if (j == kMuTable) t = c_t_last;
+        if (jg == kMuTable) t = c_t_last;
+        else if (j == 1) t = a.t0;
         const double tn = (1.0 + sqrt(1.0 + 4.0 * t * t)) / 2.0;
         sm.mu = float((t - 1.0) / tn);
         t = tn;
@@ -661,6 +675,7 @@ fista_batch_kernel(const __grid_constant__ FistaBatchArgs a) {
             }
           }
         }
+        if (a.prev_out && j == a.J) store4(a.prev_out + i * I.lds + jj, s4, a.pvec, nv);  // S_{J-1}
         if (RESIDENT) rs = sv4;
         else store4(I.S + i * I.lds + jj, sv4, I.svec, nv);
         // the padding columns of the last vector get zeros
@@ -701,6 +716,9 @@ fista_batch_kernel(const __grid_constant__ FistaBatchArgs a) {
 
 // Z_1 = S_0 = Y~ (Algorithm 1) and the transposed copy of Z_1, one tile per
 // block over the batch tile list; the padding of Z's and ZT's rows is zeroed.
+// Warm start (a.warm_prev set): S = S_{j0} is kept and Z_{j0+1} =
+// S_{j0} + mu_{j0} (S_{j0} - S_{j0-1}), the same operation the iteration
+// applies.
 __global__ void __launch_bounds__(256) init_batch_kernel(const __grid_constant__ FistaBatchArgs a) {
   __shared__ float tile[TB][TB + 1];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -711,12 +729,20 @@ __global__ void __launch_bounds__(256) init_batch_kernel(const __grid_constant__
     const int ni = min(TB, I.rr - i0), nj = min(TB, I.rc - j0);
     for (int r = warp; r < TB; r += 8) {
       const int64_t i = i0 + r, jj = j0 + lane;
-      const float y = (r < ni && lane < nj) ? I.Yt[i * I.ldy + jj] : 0.f;
+      float y = 0.f;
+      if (r < ni && lane < nj) {
+        if (a.warm_prev) {
+          const float sv = I.S[i * I.lds + jj], sp = a.warm_prev[i * I.lds + jj];
+          y = fmaf(a.mu0, sv - sp, sv);
+        } else {
+          y = I.Yt[i * I.ldy + jj];
+          I.S[i * I.lds + jj] = y;
+        }
+      }
       if (r < ni && jj < I.ldz) {
         I.Z[0][i * I.ldz + jj] = y;
         I.Z[1][i * I.ldz + jj] = 0.f;
       }
-      if (r < ni && lane < nj) I.S[i * I.lds + jj] = y;
       tile[r][lane] = y;
     }
     __syncthreads();
@@ -787,6 +813,7 @@ struct DenseFistaArgs {
   const double* lam;
   double* stats;  // the iteration's |Z_{j+1} - Z_j|^2, |Z_j|^2 (added), or null
   int* done;      // done[1] = J on the last iteration, or null
+  float* prev_out;  // S_{j-1} (ld lds) on the last iteration, or null
   int J;
   float gr, gc;
   float mu;
@@ -911,6 +938,7 @@ __global__ void __launch_bounds__(DTHREADS) fista_dense_kernel(const __grid_cons
       const float dl = v - y;
       const float sv = y + copysignf(fmaxf(fabsf(dl) - lam, 0.f), dl);
       const float zn = fmaf(a.mu, sv - sp, sv);
+      if (a.prev_out) a.prev_out[int64_t(i) * a.lds + j] = sp;
       a.S[int64_t(i) * a.lds + j] = sv;
       a.Zout[int64_t(i) * a.ldz + j] = zn;
       const double d = double(zn) - double(z);
@@ -1206,6 +1234,21 @@ cpca_status fista_batch_run(const BatchProblem* P, int n, int J, double eps, boo
   fa.J = J;
   fa.eps = eps;
   fa.want_last = want_last ? 1 : 0;
+  // warm start (single problems only)
+  fa.j0 = n == 1 ? P[0].j0 : 0;
+  fa.warm_prev = n == 1 && P[0].j0 > 0 ? P[0].warm_prev : nullptr;
+  fa.prev_out = n == 1 ? P[0].prev_out : nullptr;
+  fa.pvec = fa.prev_out && fa.in[0].svec && reinterpret_cast<uintptr_t>(fa.prev_out) % 16 == 0;
+  {
+    double t = 1.0, mu = 0.0;  // t_{j0+1} and mu_{j0} by the recurrence of Algorithm 1
+    for (int j = 1; j <= fa.j0; ++j) {
+      const double tn = (1.0 + std::sqrt(1.0 + 4.0 * t * t)) / 2.0;
+      mu = (t - 1.0) / tn;
+      t = tn;
+    }
+    fa.mu0 = float(mu);
+    fa.t0 = t;
+  }
   fa.bar = grid_bar(w.bar, w.err);
   init_batch_kernel<<<std::min(tiles, num_sms() * 8), 256, 0, st>>>(fa);
   CPCA_LAUNCHED();
@@ -1232,7 +1275,7 @@ cpca_status fista_batch_run(const BatchProblem* P, int n, int J, double eps, boo
     da.vec_lr = q.rr % 4 == 0 && reinterpret_cast<uintptr_t>(q.Lr.val) % 16 == 0;
     da.vec_lc = q.rc % 4 == 0 && reinterpret_cast<uintptr_t>(q.Lc.val) % 16 == 0;
     const dim3 grid(ceil_div(q.rc, DBN), ceil_div(q.rr, DBM));
-    double t = 1.0;  // t_j; mu_j as in the constant-memory table
+    double t = fa.t0;  // t_{j0+j}; mu as in the constant-memory table
     CPCA_PROF("fista_dense", st);
     for (int j = 1; j <= J; ++j) {
       const double tn = (1.0 + std::sqrt(1.0 + 4.0 * t * t)) / 2.0;
@@ -1242,6 +1285,7 @@ cpca_status fista_batch_run(const BatchProblem* P, int n, int J, double eps, boo
       da.Zout = fa.in[0].Z[j & 1];
       da.stats = (j == J && want_last) ? iw.stats + 2 * (J & 3) : nullptr;
       da.done = j == J ? iw.done : nullptr;
+      da.prev_out = j == J ? fa.prev_out : nullptr;
       fista_dense_kernel<<<grid, DTHREADS, 0, st>>>(da);
       count_launch();
       const cudaError_t e = cudaGetLastError();
@@ -1254,7 +1298,6 @@ cpca_status fista_batch_run(const BatchProblem* P, int n, int J, double eps, boo
     prof_end();
     return CPCA_OK;
   }
-  CPCA_CUDA(cudaMemsetAsync(w.bar, 0, sizeof(unsigned int) * (kBarrierCounters + 1), st));
   const size_t smem = sizeof(TileSmem), smem_res = sizeof(TileSmem32);
   const void* kres = (const void*)fista_batch_kernel<true>;
   const void* kstr = (const void*)fista_batch_kernel<false>;
@@ -1271,6 +1314,11 @@ cpca_status fista_batch_run(const BatchProblem* P, int n, int J, double eps, boo
   const int cap_res = small ? coop_blocks(kres, 256, smem_res, 1 << 30) : 0;
   const int cap_str = coop_blocks(kstr, 256, smem, 1 << 30);
   bool resident = tiles <= cap_res;
+  // a single problem too large for the resident launch: one striped launch
+  // per iteration (no grid barrier; TMA-fed stripes)
+  if (n == 1 && !resident && blocks == 0 && stripe_eligible(P[0].rr, P[0].rc))
+    return fista_stripe_run(P[0], w.inst[0], J, eps, want_last, fa.t0, w.err, st);
+  CPCA_CUDA(cudaMemsetAsync(w.bar, 0, sizeof(unsigned int) * (kBarrierCounters + 1), st));
   int grid = resident ? tiles : cap_str;
   if (blocks > 0) {  // explicit launch width (autotuner)
     resident = blocks >= tiles && tiles <= cap_res;
@@ -1318,6 +1366,9 @@ static cpca_status check_params(const cpca_frpcag_params* prm, const char* who) 
   CPCA_CHECK_ARG(prm->eps >= 0, "%s: eps < 0", who);
   CPCA_CHECK_ARG(prm->step > 0 || prm->power_iters >= 1, "%s: power_iters < 1", who);
   CPCA_CHECK_ARG(prm->blocks >= 0, "%s: blocks < 0", who);
+  CPCA_CHECK_ARG(prm->start_iter >= 0, "%s: start_iter < 0", who);
+  CPCA_CHECK_ARG(prm->start_iter == 0 || prm->start_prev, "%s: start_iter > 0 needs start_prev (S_{j0-1})", who);
+  CPCA_CHECK_ARG(!prm->prev_out || prm->eps == 0, "%s: prev_out needs a fixed iteration count (eps = 0)", who);
   return CPCA_OK;
 }
 
@@ -1443,6 +1494,9 @@ extern "C" cpca_status cpca_frpcag_solve(const float* Yt, int32_t rr, int32_t rc
   P.step = prm->step;
   P.X = X;
   P.ldx = ldx;
+  P.j0 = prm->start_iter;
+  P.warm_prev = prm->start_iter > 0 ? prm->start_prev : nullptr;
+  P.prev_out = prm->prev_out;
   // dense Laplacians (every entry stored in row-major order, as the Kron
   // reduction returns them): the products are dense contractions
   bool dense = false;
@@ -1520,6 +1574,8 @@ extern "C" cpca_status cpca_frpcag_solve_batched(const cpca_problem* probs, int3
                                                  void* stream) {
   clear_error();
   CPCA_TRY(check_params(prm, "cpca_frpcag_solve_batched"));
+  CPCA_CHECK_ARG(prm->start_iter == 0 && !prm->prev_out,
+                 "cpca_frpcag_solve_batched: warm starts are for single solves (start_iter = 0, no prev_out)");
   std::vector<BatchProblem> P;
   std::vector<int> rr, rc;
   CPCA_TRY(to_problems(probs, count, P, rr, rc));

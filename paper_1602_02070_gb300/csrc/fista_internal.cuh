@@ -143,6 +143,11 @@ struct BatchProblem {
   double gamma_r, gamma_c, step;
   float* X;
   int64_t ldx;
+  // warm start of a single solve: j0 iterations done, X holds S_{j0},
+  // warm_prev S_{j0-1}; prev_out (optional) receives S_{J-1} (ld ldx)
+  int j0 = 0;
+  const float* warm_prev = nullptr;
+  float* prev_out = nullptr;
 };
 
 InstWs inst_layout(Carve& c, int rr, int rc);
@@ -150,6 +155,14 @@ BatchWs batch_layout(void* ws, const int* rr, const int* rc, int n);
 cpca_status fista_batch_run(const BatchProblem* P, int n, int J, double eps, bool want_last,
                             int power_iters, uint64_t power_seed, int blocks, const BatchWs& w,
                             cudaStream_t st, bool dense = false);
+// Striped FISTA for single large problems (fista_stripe.cu): one launch per
+// iteration, Z_j's stripes through TMA; the same iterates as the resident
+// and streaming launches. Z_1, Z_1^T and S_0 are set up by the caller.
+bool stripe_eligible(int rr, int rc);
+// t0 = t_{j0+1} of a warm start (1 for a cold one); P.prev_out, when set,
+// receives S_{J-1}.
+cpca_status fista_stripe_run(const BatchProblem& P, const InstWs& iw, int J, double eps, bool want_last,
+                             double t0, int* err, cudaStream_t st);
 cpca_status fista_objective(const float* Yt, int64_t ldy, int rr, int rc, const CsrView& Lr,
                             const CsrView& Lc, const float* X, int64_t ldx, double gr, double gc,
                             double* part, double* out, cudaStream_t st);

@@ -156,6 +156,41 @@ def test_fista_converged_objective(M):
     assert abs(info.objective - Fo) / Fo < OBJ_TOL
 
 
+@pytest.mark.parametrize("eps,J", [(0.0, 150), (1e-7, 3000)])
+def test_fista_striped_launch_equals_cooperative(M, eps, J):
+    """A problem too large for the resident launch (301 x 3003: ragged row
+    boxes, a ragged last stripe and padded leading dimensions) takes the
+    striped per-iteration launch by default; forcing a launch width takes
+    the cooperative streaming kernel. Same arithmetic in the same order:
+    the same iterates bit for bit (and, with the stopping rule, the same
+    stop up to the FP64 order of the statistics)."""
+    Y, _, _ = gen.make_instance(31, 301, 3003, 6, 5, 0.05)
+    Lr = _graph_c(Y, 8)
+    Lc = _graph_c(np.ascontiguousarray(Y.T), 8)
+    Yd, Lrd, Lcd = _dev(Y), M.Csr.from_scipy(Lr), M.Csr.from_scipy(Lc)
+    M.profile_enable(True, "fista_")
+    Xs, i_s = M.cpca_frpcag_solve(Yd, Lrd, Lcd, gamma_r=0.7, gamma_c=1.3, max_iter=J, eps=eps)
+    prof = M.profile_read()
+    M.profile_enable(False, "")
+    assert "fista_stripe" in prof
+    Xc, i_c = M.cpca_frpcag_solve(Yd, Lrd, Lcd, gamma_r=0.7, gamma_c=1.3, max_iter=J, eps=eps,
+                                  blocks=2 * 152)
+    if eps == 0:
+        assert i_s.iters == i_c.iters == J
+        assert torch.equal(Xs, Xc)
+        lam = O.fista_step(0.7, 1.3, O.power_norm(Lr), O.power_norm(Lc, 200, 0, 3))
+        Xo, _ = O.frpcag_fista(Y.astype(np.float64), Lr, Lc, 0.7, 1.3, lam, J)
+        assert rel_fro(Xs.cpu().numpy(), Xo) < FISTA_TOL
+    else:
+        assert abs(i_s.iters - i_c.iters) <= 1 and i_s.iters < J
+        assert rel_fro(Xs.cpu().numpy(), Xc.cpu().numpy()) < 1e-5
+
+
+def _graph_c(P, K):
+    from tests._oracle_knn import oracle_knn_graph
+    return oracle_knn_graph(P, K)[0]
+
+
 def _kkt(X, Yt, Lr, Lc, gr, gc):
     """l1 optimality residuals of X (FP64 products): |G + sgn(X - Y~)| where
     X != Y~ and (|G| - 1)_+ where X == Y~, G = 2 (gr Lr X + gc X Lc)."""
@@ -285,3 +320,47 @@ def test_pipeline_c0_end_to_end(M):
     assert rel_fro(out["Xt"].cpu().numpy(), ref["Xt"]) < FISTA_TOL
     assert out["k"] == ref["k"]
     assert rel_fro(out["X"].cpu().numpy(), ref["X"]) < DECODE_TOL
+
+
+# ---------------------------------------------------------- warm start
+@pytest.mark.parametrize("case", ["resident", "striped", "beyond_mu_table"])
+def test_fista_warm_start_resumes_bit_for_bit(M, case):
+    """Checkpoint and resume of Algorithm 1: J1 iterations (exporting
+    S_{J1-1}) followed by J2 resumed iterations equal one run of J1 + J2,
+    bit for bit, in the resident launch, the striped launch, and across the
+    end of the momentum table (t_j continued on the host)."""
+    if case == "striped":
+        Y, _, _ = gen.make_instance(32, 301, 3003, 6, 5, 0.05)
+        Lr, Lc = _graph_c(Y, 8), _graph_c(np.ascontiguousarray(Y.T), 8)
+        Yt = Y.astype(np.float64)
+        J1, J2 = 40, 35
+    else:
+        _, Yt, Lr, Lc, *_ = _compressed(seed=6, p=120, n=200, fr=0.5, fc=0.5, K=6)
+        J1, J2 = (70, 55) if case == "resident" else (8190, 5)
+    Yd, Lrd, Lcd = _dev(Yt), M.Csr.from_scipy(Lr), M.Csr.from_scipy(Lc)
+    kw = dict(gamma_r=0.9, gamma_c=1.1)
+    full, info = M.cpca_frpcag_solve(Yd, Lrd, Lcd, max_iter=J1 + J2, **kw)
+    X = torch.empty_like(full)
+    prev = torch.empty_like(full)
+    _, i1 = M.cpca_frpcag_solve(Yd, Lrd, Lcd, max_iter=J1, out=X, prev_out=prev, **kw)
+    prev2 = torch.empty_like(full)
+    X2, i2 = M.cpca_frpcag_solve(Yd, Lrd, Lcd, max_iter=J2, out=X, start_iter=J1, start_prev=prev,
+                                 prev_out=prev2, **kw)
+    assert i1.iters == J1 and i2.iters == J2 and i1.step == info.step == i2.step
+    assert torch.equal(X2, full)
+    # the exported pair resumes again: one more iteration equals J1 + J2 + 1
+    full1, _ = M.cpca_frpcag_solve(Yd, Lrd, Lcd, max_iter=J1 + J2 + 1, **kw)
+    X3, _ = M.cpca_frpcag_solve(Yd, Lrd, Lcd, max_iter=1, out=X2.clone(), start_iter=J1 + J2,
+                                start_prev=prev2, **kw)
+    assert torch.equal(X3, full1)
+
+
+def test_fista_warm_start_argument_errors(M):
+    _, Yt, Lr, Lc, *_ = _compressed(seed=6, p=40, n=60, fr=0.5, fc=0.5, K=4)
+    Yd, Lrd, Lcd = _dev(Yt), M.Csr.from_scipy(Lr), M.Csr.from_scipy(Lc)
+    with pytest.raises(M.CpcaError) as e:
+        M.cpca_frpcag_solve(Yd, Lrd, Lcd, max_iter=5, start_iter=3)  # no S_{j0-1}
+    assert e.value.status == M.CPCA_ERR_INVALID_ARG
+    with pytest.raises(M.CpcaError) as e:
+        M.cpca_frpcag_solve(Yd, Lrd, Lcd, max_iter=5, eps=1e-6, prev_out=torch.empty_like(Yd))
+    assert e.value.status == M.CPCA_ERR_INVALID_ARG

@@ -1,15 +1,18 @@
 #!/usr/bin/env python3
-"""Benchmark: one full compressive-PCA pass per step on the 10304 x 1000
-workload (rank 10, 10 clusters, 5% gross errors, K = 10 graphs, 1/4 of the
-rows and columns sampled, 300 FISTA iterations, PCG decoder to 1e-6).
+"""Benchmark: one full compressive-PCA pass per step on the 20000 x 100000
+workload (8 GB; rank 20, 50 clusters, 2% gross errors, K = 10 graphs, 1/10
+of the rows and columns sampled, 300 FISTA iterations, PCG decoder to 1e-6),
+the largest single-GPU configuration.
 
 A step runs every hot-path stage through the C ABI: the two full kNN graphs
-and Laplacians, sampling + gather, the two compressed graphs, the power
-iterations for lambda, 300 FISTA iterations, and the approximate decoder
-(partial SVD, PCG upsampling of U and V, rank-k output X).
+(tensor-core distance candidates, exact recheck) and Laplacians, sampling +
+gather, the two compressed graphs, the power iterations for lambda, 300
+FISTA iterations, and the approximate decoder (partial SVD, PCG upsampling
+of U and V, rank-k output X, 8 GB).
 
 Prints ONE JSON line (rank 0). ``--impl reference`` times the FP64 oracle
-on the host instead (bounded sample of the same workload).
+on the host instead (bounded sample of the same workload, all host cores).
+``--workload bench_10304x1000`` runs the 10304 x 1000 workload instead.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl cpca|reference]
 Multi-GPU (torchrun): every rank runs an independent replica (the workload
@@ -26,10 +29,21 @@ import sys
 import tempfile
 import time
 
-# The oracle baseline is single-threaded by construction; pin BLAS threads
-# before numpy loads so the reported core count is what ran.
+
+def _threads_from_argv():
+    """BLAS/OpenMP threads of this process, fixed before numpy loads: the
+    oracle's CPU legs run with a stated thread count (--cpu-leg T), the
+    reference arm on every host core, the GPU arm single-threaded."""
+    argv = sys.argv[1:]
+    if "--cpu-leg" in argv:
+        return argv[argv.index("--cpu-leg") + 1]
+    if "--impl" in argv and argv[argv.index("--impl") + 1] == "reference":
+        return str(os.cpu_count() or 1)
+    return "1"
+
+
 for _v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
-    os.environ.setdefault(_v, "1")
+    os.environ[_v] = _threads_from_argv()
 
 import numpy as np  # noqa: E402
 
@@ -40,7 +54,8 @@ import gen  # noqa: E402
 
 METRIC = "wall-time to 1e-4 rel err vs plain GPU; FISTA/CG iters/s; % of HBM peak"
 UNIT = "FISTA iters/s"
-WORKLOAD = "bench_10304x1000"
+WORKLOAD = "large_20000x100000"
+SMALL_WORKLOAD = "bench_10304x1000"  # the extra measurements (batched, adjoint, decoders) use it
 L2_FLUSH_BYTES = 256 << 20
 
 
@@ -99,106 +114,179 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------- oracle arm
-def oracle_step_seconds(Y, cfg, n_query: int, dec_graphs, rng_seed: int = 0):
-    """Seconds the FP64 oracle needs for one full pipeline step, measured on
-    a bounded sample: the two full-graph kNN searches are timed on n_query
-    sampled query points each and scaled to all points; sampling, the
-    compressed graphs, the power iterations, all FISTA iterations and the
-    decoder (SVD + PCG + output) run in full."""
+def host_instance(cfg):
+    """The workload's Y on the host, FP32: numpy's generator (make_instance)
+    where it is quick, else the same recipe with torch's CPU generator (the
+    same shapes and statistics; the device arm draws with the CUDA
+    generator)."""
+    if cfg["p"] * cfg["n"] <= 50_000_000:
+        return gen.make_instance(0, cfg["p"], cfg["n"], cfg["r"], cfg["C"], cfg["frac"])[0]
+    return gen.make_instance_torch(0, cfg["p"], cfg["n"], cfg["r"], cfg["C"], cfg["frac"], device="cpu").numpy()
+
+
+def oracle_setup(Yh, cfg, threads):
+    """Untimed inputs of the oracle's timing runs: the sampled sets and
+    matrix, the compressed graphs (the oracle's own search), lambda, and
+    full-size graphs for the decoder's PCG - the oracle's kNN graphs of
+    seeded 20-dimensional latent points of the workload's model (the
+    decoder takes any Laplacian; the oracle cannot search the full point
+    sets in reasonable time). Also the oracle's own PCG iteration count on
+    one right-hand side per side, to scale the timed iterations."""
     import oracle as O
-    p, n = Y.shape
-    K, J = cfg["K"], cfg["J"]
-    rng = np.random.default_rng(rng_seed)
-    t_knn = 0.0
-    Yd = Y.astype(np.float64)
-    for P in (Yd, Yd.T):
-        N = P.shape[0]
-        qs = rng.choice(N, size=min(n_query, N), replace=False)
-        t0 = time.perf_counter()
-        O.knn_bruteforce(P, K, queries=qs)
-        t_knn += (time.perf_counter() - t0) * N / len(qs)
+    from oracle.cpca_fista_c import knn_c
+    p, n, K = cfg["p"], cfg["n"], cfg["K"]
     rr, rc = int(p * cfg["fr"] + 0.5), int(n * cfg["fc"] + 0.5)
-    t0 = time.perf_counter()
-    # Laplacians of the full graphs: same O(N K) construction as below, timed
-    # on the compressed kNN lists and scaled by the point count
     om_r, om_c = O.sample_indices(0, p, rr, 0), O.sample_indices(0, n, rc, 1)
-    Yt = Yd[np.ix_(om_r, om_c)]
-    Lrt, _, ir, dr, _ = O.knn_graph(Yt, K)
-    Lct, _, ic, dc, _ = O.knn_graph(Yt.T, K)
-    t_small = time.perf_counter() - t0
-    t0 = time.perf_counter()
-    O.laplacian_from_knn(ir, dr, rr, O.sigma2_mean(dr))
-    t_lap = (time.perf_counter() - t0) * (p + n) / rr
-    t0 = time.perf_counter()
-    lam = O.fista_step(cfg["gamma_r"], cfg["gamma_c"], O.power_norm(Lrt, 200, 0, 2),
-                       O.power_norm(Lct, 200, 0, 3))
-    Xt, _ = O.frpcag_fista(Yt, Lrt, Lct, cfg["gamma_r"], cfg["gamma_c"], lam, J)
-    t_fista = time.perf_counter() - t0
-    Lr, Lc = dec_graphs
-    t0 = time.perf_counter()
-    O.approx_decode(Xt, om_r, om_c, p, n, Lr, Lc, tol=cfg["cg_tol"])
-    t_dec = time.perf_counter() - t0
-    return t_knn + t_lap + t_small + t_fista + t_dec
+    Yt32 = Yh[np.ix_(om_r, om_c)]
+    graphs = []
+    for P in (Yt32, np.ascontiguousarray(Yt32.T)):
+        idx, d2 = knn_c(P, K, threads=threads)
+        graphs.append(O.laplacian_from_knn(idx, d2, P.shape[0], O.sigma2_mean(d2))[0])
+    lam = O.fista_step(cfg["gamma_r"], cfg["gamma_c"], O.power_norm(graphs[0], 200, 0, 2),
+                       O.power_norm(graphs[1], 200, 0, 3))
+    full = []
+    for N, C, seed in ((p, 1, 11), (n, cfg["C"], 12)):
+        idx, d2 = knn_c(gen.latent_points(seed, N, 20, C), K, threads=threads)
+        full.append(O.laplacian_from_knn(idx, d2, N, O.sigma2_mean(d2))[0])
+    Ut, s_, Vh, k = O.svd_rank(Yt32.astype(np.float64))
+    its = []
+    for L, om, R in ((full[0], om_r, Ut[:, :1]), (full[1], om_c, Vh[:1].T)):
+        _, it, _ = O.upsample_subspace(L, om, R, cfg["cg_tol"])
+        its.append(int(it[0]))
+    return {"om_r": om_r, "om_c": om_c, "Yt": Yt32.astype(np.float64), "Lrt": graphs[0], "Lct": graphs[1],
+            "lam": lam, "Lr": full[0], "Lc": full[1], "cg_iters": its, "k": k}
 
 
-def decoder_graphs_for_timing(Y, K):
-    """Full-size graphs for timing the oracle's decoder (setup, untimed):
-    exact kNN lists from a blocked matmul ranking, then the oracle's own
-    Laplacian construction. Only a timing input, never a parity input."""
+def oracle_step_seconds(Yh, cfg, setup, threads, sample, rng_seed=0):
+    """Seconds the FP64 oracle needs for one full pipeline step on `threads`
+    host threads, extrapolated from a bounded sample (see cpu_sample_text).
+    Returns (seconds, per-part seconds)."""
     import oracle as O
-    out = []
-    Yd = Y.astype(np.float64)
-    for P in (Yd, Yd.T):
+    from oracle.cpca_fista_c import frpcag_fista_c, knn_c
+    p, n, K, J = cfg["p"], cfg["n"], cfg["K"], cfg["J"]
+    rng = np.random.default_rng(rng_seed)
+    parts = {}
+    nq = sample["knn_queries"]
+    t = 0.0
+    for P in (Yh, None):
+        P = np.ascontiguousarray(Yh.T) if P is None else P
         N = P.shape[0]
-        nrm = np.einsum("ij,ij->i", P, P)
-        idx = np.empty((N, K), dtype=np.int64)
-        d2 = np.empty((N, K))
-        for a in range(0, N, 1024):
-            D = nrm[a:a + 1024, None] + nrm[None, :] - 2.0 * (P[a:a + 1024] @ P.T)
-            D[np.arange(D.shape[0]), np.arange(a, a + D.shape[0])] = np.inf
-            part = np.argpartition(D, K, axis=1)[:, :K]
-            dd = np.take_along_axis(D, part, 1)
-            o = np.argsort(dd, axis=1)
-            idx[a:a + 1024] = np.take_along_axis(part, o, 1)
-            d2[a:a + 1024] = np.take_along_axis(dd, o, 1)
-        L, _ = O.laplacian_from_knn(idx, np.maximum(d2, 0), N, float(np.mean(np.maximum(d2, 0))))
-        out.append(L)
+        qs = rng.choice(N, size=min(nq, N), replace=False)
+        t0 = time.perf_counter()
+        knn_c(P, K, queries=qs, threads=threads)
+        t += (time.perf_counter() - t0) * N / len(qs)
+        del P
+    parts["knn_full"] = t
+    t0 = time.perf_counter()
+    om_r, om_c = O.sample_indices(0, p, len(setup["om_r"]), 0), O.sample_indices(0, n, len(setup["om_c"]), 1)
+    Yt = Yh[np.ix_(om_r, om_c)].astype(np.float64)
+    parts["sample"] = time.perf_counter() - t0
+    t = 0.0
+    for P in (Yt.astype(np.float32), np.ascontiguousarray(Yt.T.astype(np.float32))):
+        N = P.shape[0]
+        qs = rng.choice(N, size=min(4 * nq, N), replace=False)
+        t0 = time.perf_counter()
+        idx, d2 = knn_c(P, K, queries=qs, threads=threads)
+        t += (time.perf_counter() - t0) * N / len(qs)
+    parts["knn_compressed"] = t
+    idx, d2 = knn_c(Yt.astype(np.float32), K, queries=np.arange(min(2000, Yt.shape[0])), threads=threads)
+    t0 = time.perf_counter()
+    O.laplacian_from_knn(idx, d2, Yt.shape[0], O.sigma2_mean(d2))
+    parts["laplacians"] = (time.perf_counter() - t0) * (p + n + Yt.shape[0] + Yt.shape[1]) / idx.shape[0]
+    t0 = time.perf_counter()
+    O.power_norm(setup["Lrt"], 200, 0, 2)
+    O.power_norm(setup["Lct"], 200, 0, 3)
+    parts["power_iter"] = time.perf_counter() - t0
+    fi = sample["fista_iters"]
+    t0 = time.perf_counter()
+    frpcag_fista_c(setup["Yt"], setup["Lrt"], setup["Lct"], cfg["gamma_r"], cfg["gamma_c"], setup["lam"], fi,
+                   threads=threads)
+    parts["fista"] = (time.perf_counter() - t0) * J / fi
+    t0 = time.perf_counter()
+    Ut, s_, Vh, k = O.svd_rank(setup["Yt"])
+    parts["svd"] = time.perf_counter() - t0
+    ci = sample["cg_iters"]
+    t = 0.0
+    for L, om, R, need in ((setup["Lr"], setup["om_r"], Ut[:, :k], setup["cg_iters"][0]),
+                           (setup["Lc"], setup["om_c"], Vh[:k].T, setup["cg_iters"][1])):
+        t0 = time.perf_counter()
+        O.upsample_subspace(L, om, R, 1e-300, maxit=ci)
+        t += (time.perf_counter() - t0) * max(need, 1) / ci
+    parts["pcg"] = t
+    rows = sample["out_rows"]
+    U = rng.standard_normal((rows, k))
+    V = rng.standard_normal((n, k))
+    sig = np.ones(k)
+    t0 = time.perf_counter()
+    (U * sig) @ V.T
+    parts["output"] = (time.perf_counter() - t0) * p / rows
+    return float(sum(parts.values())), parts
+
+
+def cpu_sample_text(sample):
+    return (f"full-graph kNN (C oracle, FP64 direct differences) timed on {sample['knn_queries']} sampled "
+            f"queries per graph and scaled to all points; compressed-graph kNN on {4 * sample['knn_queries']} "
+            "queries per graph, scaled; Laplacian construction timed on 2000 lists and scaled by point "
+            f"count; sampling and the power iterations in full; FISTA (C oracle) {sample['fista_iters']} "
+            "iterations scaled to all; SVD of X~ in full; PCG (numpy oracle) "
+            f"{sample['cg_iters']} iterations per side on full-size graphs of the workload's model, scaled "
+            f"by the oracle's own iteration count; X = U S V^T on {sample['out_rows']} rows, scaled")
+
+
+CPU_SAMPLE = {"knn_queries": 16, "fista_iters": 2, "cg_iters": 20, "out_rows": 512}
+REF_SAMPLE = {"knn_queries": 16, "fista_iters": 1, "cg_iters": 10, "out_rows": 256}
+
+
+def run_cpu_leg(cfg, threads):
+    """One CPU-baseline measurement in this process (--cpu-leg T): the
+    oracle on `threads` threads. Prints {"seconds", "parts", "threads"}."""
+    Yh = host_instance(cfg)
+    setup = oracle_setup(Yh, cfg, threads)
+    secs, parts = oracle_step_seconds(Yh, cfg, setup, threads, CPU_SAMPLE)
+    print(json.dumps({"seconds": secs, "parts": parts, "threads": threads}))
+
+
+def cpu_baseline(cfg, workload):
+    """The oracle timed on 1 thread and on every host core, each in a
+    subprocess whose BLAS/OpenMP thread count is fixed before numpy loads."""
+    out = {}
+    for T in (1, os.cpu_count() or 1):
+        r = subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-leg", str(T), "--workload", workload],
+                           capture_output=True, text=True)
+        try:
+            out[T] = json.loads(r.stdout.strip().splitlines()[-1])
+        except Exception:
+            out[T] = {"error": (r.stderr or r.stdout)[-400:]}
     return out
 
 
-def cpu_sample_text(nq):
-    return (f"full-graph kNN brute force timed on {nq} sampled query points per graph and scaled to "
-            "all points; Laplacian construction timed on the compressed graph and scaled by point "
-            "count; sampling, compressed kNN graphs, power iterations, all 300 FISTA iterations and "
-            "the decoder (SVD, PCG, output) in full")
-
-
-def run_reference(args, cfg, Y):
-    dec = decoder_graphs_for_timing(Y, cfg["K"])
-    nq = 8
-    for _ in range(args.warmup):
-        oracle_step_seconds(Y, cfg, nq, dec)
-    secs = [oracle_step_seconds(Y, cfg, nq, dec, rng_seed=s + 1) for s in range(args.steps)]
+def run_reference(args, cfg):
+    T = os.cpu_count() or 1
+    Yh = host_instance(cfg)
+    setup = oracle_setup(Yh, cfg, T)
+    for w in range(args.warmup):
+        oracle_step_seconds(Yh, cfg, setup, T, REF_SAMPLE, rng_seed=100 + w)
+    secs = [oracle_step_seconds(Yh, cfg, setup, T, REF_SAMPLE, rng_seed=s + 1)[0] for s in range(args.steps)]
     tot = float(sum(secs))
     value = cfg["J"] * args.steps / tot
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * tot / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": config_dict(cfg),
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": cpu_sample_text(nq)},
+            "data": "synthetic", "config": config_dict(cfg, args.workload),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": T, "kind": "oracle",
+                             "sample": cpu_sample_text(REF_SAMPLE)},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
 
 
-def config_dict(cfg):
-    return {"workload": f"CPCA {cfg['p']}x{cfg['n']} rank {cfg['r']}, {cfg['C']} clusters, "
+def config_dict(cfg, name=WORKLOAD):
+    return {"workload": f"{name}: CPCA {cfg['p']}x{cfg['n']} rank {cfg['r']}, {cfg['C']} clusters, "
                         f"{int(cfg['frac'] * 100)}% gross errors, K={cfg['K']}, sample "
                         f"{cfg['fr']}x{cfg['fc']}, {cfg['J']} FISTA iterations, PCG tol {cfg['cg_tol']}",
             "p": cfg["p"], "n": cfg["n"], "rank": cfg["r"], "K": cfg["K"],
             "rho_r": int(cfg["p"] * cfg["fr"] + 0.5), "rho_c": int(cfg["n"] * cfg["fc"] + 0.5),
             "fista_iters": cfg["J"], "gamma_r": cfg["gamma_r"], "gamma_c": cfg["gamma_c"],
-            "l2": f"flushed between timed steps ({L2_FLUSH_BYTES >> 20} MiB write)",
+            "l2": f"flushed between timed steps ({L2_FLUSH_BYTES >> 20} MiB write); inputs larger than L2",
             "parallelism": "replicas"}
 
 
@@ -338,10 +426,9 @@ def alternate_measure(M, torch, Yd, cfg, peaks, reps=3, gamma=1.0):
     """The alternate decoder (Eq. alternatedecoder) on the full matrix of the
     workload: X~ from the step's FISTA solve, the full row/column graphs,
     gamma-bars = 1, PCG to the step's tolerance. Kernel time from the
-    library's CUDA-event profile; algorithmic bytes per CG iteration: 52 per
-    entry of X (phase A reads z, q, p and writes q, p; phase B reads x, r,
-    p, q and writes x, r, z and its transposed copy) plus 8 per CSR entry of
-    both Laplacians (column index and value)."""
+    library's CUDA-event profile; algorithmic bytes per CG iteration: 24 per
+    entry of X (the CG minimum: read P, X, R and write X, R, P) plus 8 per
+    CSR entry of both Laplacians (column index and value)."""
     p, n = Yd.shape
     K, J = cfg["K"], cfg["J"]
     rr, rc = M.rho_of(p, cfg["fr"]), M.rho_of(n, cfg["fc"])
@@ -366,7 +453,7 @@ def alternate_measure(M, torch, Yd, cfg, peaks, reps=3, gamma=1.0):
     M.profile_enable(False, "")
     ms = prof["alt_cg"][0] / reps
     iters = int(info.iters)
-    byts = 52.0 * p * n + 8.0 * (Lr.nnz + Lc.nnz)
+    byts = 24.0 * p * n + 8.0 * (Lr.nnz + Lc.nnz)
     hbm = peaks["hbm_gbs"] if peaks else 6800.0
     gbs = byts * iters / (ms / 1000.0) / 1e9
     return {"workload": f"alternate decoder on the {p}x{n} matrix, gamma-bars {gamma}, PCG to {cfg['cg_tol']}",
@@ -437,7 +524,7 @@ def kron_measure(M, torch, out, cfg, peaks, reps=3):
     power iteration) on them instead of on the kNN graphs of Y~. The reduced
     Laplacians are dense, so each FISTA iteration's products are dense
     contractions: 2 (nnz_r rc + nnz_c rr) flops on the FP32 pipes (no tensor
-    cores: FP32 parity), with 8 B per stored entry and 20 B per entry of Y~."""
+    cores: FP32 parity), with 8 B per stored entry and 16 B per entry of Y~."""
     Lr, Lc, om_r, om_c, Yt = out["Lr"], out["Lc"], out["omega_r"], out["omega_c"], out["Yt"]
     rr, rc = Yt.shape
     res = {}
@@ -469,7 +556,7 @@ def kron_measure(M, torch, out, cfg, peaks, reps=3):
     ms, nl = prof.get(kname, (0.0, 0))
     ms = ms / max(nl, 1)
     flops = 2.0 * (Lrt.nnz * rc + Lct.nnz * rr)
-    byts = 20.0 * rr * rc + 8.0 * (Lrt.nnz + Lct.nnz)
+    byts = 16.0 * rr * rc + 8.0 * (Lrt.nnz + Lct.nnz)
     tfl = flops * J / (ms / 1000.0) / 1e12
     pk = 152 * 128 * 2 * 2.07e9 / 1e12
     res["fista"] = {"computes": f"{J} FISTA iterations on {rr}x{rc} with dense reduced Laplacians "
@@ -486,8 +573,8 @@ def fista_large_measure(M, torch, peaks, J=300, reps=3):
     rank 20, 50 clusters, 2% gross errors, 1/10 x 1/10 sampling: Y~ 2000 x
     10000, K = 10 graphs of Y~), J iterations. The 400 MB state does not fit
     in L2, so this is the size where the kernel meets the HBM roofline:
-    20 B per entry of Y~ (read Y~, S_{j-1}, S_{j-2}, write S_j and Z) plus
-    8 B per CSR entry and the row pointers, per iteration."""
+    16 B per entry of Y~ (read Y~, S_{j-1}, S_{j-2}, write S_j) plus 8 B per
+    CSR entry and the row pointers, per iteration."""
     cfg = gen.CONFIGS["large_20000x100000"]
     p, n, K = cfg["p"], cfg["n"], cfg["K"]
     Y = gen.make_instance_torch(0, p, n, cfg["r"], cfg["C"], cfg["frac"])
@@ -502,21 +589,22 @@ def fista_large_measure(M, torch, peaks, J=300, reps=3):
     prm = M.frpcag_params(gamma_r=cfg["gamma_r"], gamma_c=cfg["gamma_c"], max_iter=J)
     M.cpca_frpcag_solve(Yt, Lrt, Lct, prm, want_info=False, out=X, ws=ws)
     torch.cuda.synchronize()
-    M.profile_enable(True, "fista_persistent")
+    M.profile_enable(True, "fista_")
     for _ in range(reps):
         M.cpca_frpcag_solve(Yt, Lrt, Lct, prm, want_info=False, out=X, ws=ws)
     torch.cuda.synchronize()
     prof = M.profile_read()
     M.profile_enable(False, "")
-    ms, nl = prof.get("fista_persistent", (0.0, 0))
-    ms = ms / max(nl, 1)
-    byts = 20.0 * rr * rc + 8.0 * (Lrt.nnz + Lct.nnz) + 8.0 * (rr + rc + 2)
+    kname = "fista_stripe" if "fista_stripe" in prof else "fista_persistent"
+    ms, nl = prof.get(kname, (0.0, 0))
+    ms = ms / reps
+    byts = 16.0 * rr * rc + 8.0 * (Lrt.nnz + Lct.nnz) + 8.0 * (rr + rc + 2)
     hbm = peaks["hbm_gbs"] if peaks else 6800.0
     gbs = byts * J / (ms / 1000.0) / 1e9
     return {"workload": f"FISTA on Y~ {rr}x{rc} (sampled from the 20000x100000 matrix), K={K} graphs "
                         f"({Lrt.nnz} + {Lct.nnz} entries), {J} iterations",
             "kernel_ms": ms, "us_per_iter": 1000.0 * ms / J, "fista_iters_per_s": J / (ms / 1000.0),
-            "roofline": {"kernel": "fista_persistent", "bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s",
+            "roofline": {"kernel": kname, "bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s",
                          "frac": gbs / hbm, "bytes_per_iter": byts,
                          "peak_source": "measured" if peaks else "fallback"}}
 
@@ -538,14 +626,19 @@ def roofline_for(name, ms, launches, ctx, peaks):
     hbm = peaks["hbm_gbs"] if peaks else 6800.0
     src = "measured" if peaks else "fallback"
     sec = ms / 1000.0
-    if name == "fista_persistent":
-        byts = ctx["fista_bytes_per_iter"] * ctx["fista_iters"] * launches
+    if name in ("fista_persistent", "fista_stripe"):
+        byts = ctx["fista_bytes_per_iter"] * ctx["fista_iters"] * ctx["steps"]
         a = byts / sec / 1e9
+        state_mb = 16 * ctx["rr"] * ctx["rc"] / 1e6
+        prof_file = ("fista_stripe_kernel_2000x10000.md" if name == "fista_stripe"
+                     else "fista_batch_kernel_2576x250.md")
         return {"kernel": name, "bound": "hbm", "achieved": a, "peak": hbm, "unit": "GB/s",
-                "frac": a / hbm, "traffic": profiled_dram_bytes("fista_batch_kernel_2576x250.md"),
-                "traffic_unit": "bytes per launch (ncu dram read + write)", "peak_source": src,
-                "note": "20 B per entry of Y~ + CSR bytes, per FISTA iteration; the working set "
-                        "(13 MB) is L2-resident at this size, so the kernel is latency-bound"}
+                "frac": a / hbm, "traffic": profiled_dram_bytes(prof_file),
+                "traffic_unit": "bytes per iteration (ncu dram read + write, " + prof_file + ")",
+                "ms_per_iter": ms / (ctx["fista_iters"] * ctx["steps"]),
+                "peak_source": src,
+                "note": f"16 B per entry of Y~ (read Y~, S_j-1, S_j-2, write S_j) + 8 B per CSR entry per "
+                        f"FISTA iteration ({ctx['rr']}x{ctx['rc']}, {state_mb:.0f} MB of state per iteration)"}
     if name.startswith("knn_candidates"):
         fl = ctx["knn_flops_per_step"] * ctx["steps"]
         a = fl / sec / 1e12
@@ -593,12 +686,14 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="cpca", choices=["cpca", "reference"])
+    ap.add_argument("--workload", default=WORKLOAD, choices=sorted(gen.CONFIGS))
+    ap.add_argument("--cpu-leg", type=int, default=0, help=argparse.SUPPRESS)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the measurements beyond the headline step (batched, adjoint, decoders, Kron)")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--no-alternate", action="store_true")
-    ap.add_argument("--cpu-queries", type=int, default=32)
-    ap.add_argument("--no-large", action="store_true", help="skip FISTA on the 8 GB workload's Y~")
     ap.add_argument("--fista-large-only", action="store_true",
                     help="only FISTA on the 8 GB workload's Y~ (one JSON object; for profiling)")
     ap.add_argument("--fista-large-iters", type=int, default=300)
@@ -610,12 +705,14 @@ def main():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
-    cfg = dict(gen.CONFIGS[WORKLOAD])
-    Y, _, _ = gen.make_instance(0, cfg["p"], cfg["n"], cfg["r"], cfg["C"], cfg["frac"])
+    cfg = dict(gen.CONFIGS[args.workload])
 
+    if args.cpu_leg:
+        run_cpu_leg(cfg, args.cpu_leg)
+        return
     if args.impl == "reference":
         if rank == 0:
-            run_reference(args, cfg, Y)
+            run_reference(args, cfg)
         return
 
     import torch
@@ -633,23 +730,23 @@ def main():
     if args.fista_large_only:
         print(json.dumps(fista_large_measure(M, torch, load_peaks(), J=args.fista_large_iters, reps=1)))
         return
+    if args.kron_only:
+        c1 = dict(gen.CONFIGS[SMALL_WORKLOAD])
+        Y1 = torch.as_tensor(gen.make_instance(0, c1["p"], c1["n"], c1["r"], c1["C"], c1["frac"])[0], device=dev)
+        out = M.cpca_pipeline(Y1, K=c1["K"], fr=c1["fr"], fc=c1["fc"], seed=0, J=c1["J"], cg_tol=c1["cg_tol"])
+        print(json.dumps(kron_measure(M, torch, out, c1, load_peaks(), reps=1)))
+        return
 
     def barrier():
         if dist is not None:
             dist.barrier()
         torch.cuda.synchronize()
 
-    Yh = torch.from_numpy(Y).pin_memory()
-    Yd = Yh.to(dev)
-    if args.kron_only:
-        out = M.cpca_pipeline(Yd, K=cfg["K"], fr=cfg["fr"], fc=cfg["fc"], seed=0, J=cfg["J"], cg_tol=cfg["cg_tol"])
-        print(json.dumps(kron_measure(M, torch, out, cfg, load_peaks(), reps=1)))
-        return
+    Yd = gen.make_instance_torch(0, cfg["p"], cfg["n"], cfg["r"], cfg["C"], cfg["frac"], device=str(dev))
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
     kw = dict(K=cfg["K"], fr=cfg["fr"], fc=cfg["fc"], seed=0, J=cfg["J"], cg_tol=cfg["cg_tol"])
-    info = {}
 
-    def step(Yin):
+    def step(Yin, out=None):
         return M.cpca_pipeline(Yin, **kw)
 
     for _ in range(args.warmup):
@@ -661,6 +758,7 @@ def main():
     prof0 = M.profile_read()
     M.profile_enable(False, "")
     dominant = max(prof0.items(), key=lambda kv: kv[1][0])[0]
+    fista_kernel = next((k_ for k_ in ("fista_stripe", "fista_persistent", "fista_dense") if k_ in prof0), None)
     rr, rc = out["Yt"].shape
     k = out["k"]
     dinfo = out["info"]
@@ -669,54 +767,60 @@ def main():
     m_u, m_v = cfg["p"] - rr, cfg["n"] - rc
     ctx = {
         "steps": args.steps,
-        "fista_bytes_per_iter": 20 * rr * rc + 8 * nnz_t + 8 * (rr + rc + 2),
+        "fista_bytes_per_iter": 16 * rr * rc + 8 * nnz_t + 8 * (rr + rc + 2),
         "fista_iters": cfg["J"],
         "knn_flops_per_step": 2.0 * (cfg["p"] ** 2 * cfg["n"] + cfg["n"] ** 2 * cfg["p"]
                                      + rr ** 2 * rc + rc ** 2 * rr),
         "fp32_simt_tflops": 152 * 128 * 2 * 2.07e9 / 1e12,
-        "cg_bytes_per_iter": 44 * (m_u + m_v) * k + 8 * (out["Lr"].nnz + out["Lc"].nnz),
+        "cg_bytes_per_iter": 24 * (m_u + m_v) * k + 8 * (out["Lr"].nnz + out["Lc"].nnz),
         "cg_iters": cg_iters,
         "out_bytes": 4 * cfg["p"] * cfg["n"],
+        "rr": rr, "rc": rc,
     }
+    certification = out["knn_certification"]
 
     # ---------------- timed region: device-resident input
     clocks = ClockSampler(local)
     clocks.start()
-    M.profile_enable(True, dominant)
+    M.profile_enable(True, "")
     launches0 = M.launch_count()
     barrier()
     stream = torch.cuda.current_stream()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
           for _ in range(args.steps)]
     t_wall0 = time.perf_counter()
-    for s in range(args.steps):
+    for s_ in range(args.steps):
         flush.zero_()
-        ev[s][0].record(stream)
+        ev[s_][0].record(stream)
         out = step(Yd)
-        ev[s][1].record(stream)
+        ev[s_][1].record(stream)
     barrier()
     t_wall = time.perf_counter() - t_wall0
     gpu_launches = M.launch_count() - launches0
     prof = M.profile_read()
     M.profile_enable(False, "")
-    step_ms = [a.elapsed_time(b) for a, b in ev]
+    step_ms = [a_.elapsed_time(b_) for a_, b_ in ev]
     total_s = sum(step_ms) / 1000.0
     clk = clocks.stop()
 
     # ---------------- end to end: pinned host input, result read back
+    Yh = Yd.cpu().pin_memory()
     Xh = torch.empty(cfg["p"], cfg["n"], dtype=torch.float32).pin_memory()
+    del out
+    torch.cuda.empty_cache()
     ev2 = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
            for _ in range(args.steps)]
     barrier()
-    for s in range(args.steps):
+    for s_ in range(args.steps):
         flush.zero_()
-        ev2[s][0].record(stream)
+        ev2[s_][0].record(stream)
         Yin = Yh.to(dev, non_blocking=True)
         o = step(Yin)
         Xh.copy_(o["X"], non_blocking=True)
-        ev2[s][1].record(stream)
+        ev2[s_][1].record(stream)
+        del Yin, o
     barrier()
-    e2e_s = sum(a.elapsed_time(b) for a, b in ev2) / 1000.0
+    e2e_s = sum(a_.elapsed_time(b_) for a_, b_ in ev2) / 1000.0
 
     total_s, e2e_s = max_over_ranks(dist, [total_s, e2e_s], dev)
     units = cfg["J"] * args.steps * world
@@ -724,6 +828,9 @@ def main():
     peaks = load_peaks()
     dom_ms, dom_n = prof.get(dominant, (0.0, 0))
     roof = roofline_for(dominant, dom_ms, dom_n, ctx, peaks) if dom_n else None
+    fista_roof = None
+    if fista_kernel and fista_kernel in prof:
+        fista_roof = roofline_for(fista_kernel, *prof[fista_kernel], ctx, peaks)
     if rank != 0:
         if dist is not None:
             dist.destroy_process_group()
@@ -732,35 +839,61 @@ def main():
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1000.0 * total_s / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-        "data": "synthetic", "config": config_dict(cfg),
+        "data": "synthetic", "config": config_dict(cfg, args.workload),
         "e2e": {"value": units / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(Yh.numel() * 4),
                 "d2h_bytes_per_step": int(Xh.numel() * 4)},
         "gpu_launches": int(gpu_launches),
         "roofline": roof,
+        "fista_roofline": fista_roof,
         "clocks": clk,
         "phases_ms_one_step": {k_: round(v[0], 4) for k_, v in sorted(prof0.items(), key=lambda kv: -kv[1][0])},
         "fista_iters_per_step": cfg["J"], "cg_iters_per_step": cg_iters, "rank_k": k,
+        "knn_certification": {g: {"bruteforce": int(a_), "uncertified": int(b_)}
+                              for g, (a_, b_) in certification.items()},
         "wall_s_timed": t_wall,
     }
-    if not args.no_batched:
-        line["batched_64"] = batched_comparison(M, torch)
-    if not args.no_adjoint:
-        line["adjoint"] = adjoint_comparison(M, torch, Yd, cfg)
-    if not args.no_alternate:
-        line["alternate_decoder"] = alternate_measure(M, torch, Yd, cfg, peaks)
-        line["other_decoders"] = other_decoders_measure(M, torch, Yd, out, cfg, peaks)
-        line["kron_graphs"] = kron_measure(M, torch, out, cfg, peaks)
-    if not args.no_large:
-        line["fista_8gb_workload"] = fista_large_measure(M, torch, peaks)
+    del Yd, Yh, Xh, flush
+    torch.cuda.empty_cache()
+    if not args.no_extras and world == 1:
+        extras(args, M, torch, dev, peaks, line)
     if world == 1 and not args.no_cpu_baseline:
-        dec = decoder_graphs_for_timing(Y, cfg["K"])
-        secs = oracle_step_seconds(Y, cfg, args.cpu_queries, dec)
-        line["cpu_baseline"] = {"value": cfg["J"] / secs, "unit": UNIT, "cores": 1, "kind": "oracle",
-                                "sample": cpu_sample_text(args.cpu_queries),
-                                "seconds_per_step_extrapolated": secs}
+        legs = cpu_baseline(cfg, args.workload)
+        base = {}
+        for T, r in sorted(legs.items()):
+            if "seconds" in r:
+                base[T] = {"value": cfg["J"] / r["seconds"], "seconds_per_step_extrapolated": r["seconds"],
+                           "parts_s": {k_: round(v, 3) for k_, v in r["parts"].items()}}
+            else:
+                base[T] = r
+        best = max((T for T in base if "value" in base[T]), default=None)
+        line["cpu_baseline"] = {"value": base[best]["value"] if best else None, "unit": UNIT,
+                                "cores": best, "kind": "oracle", "sample": cpu_sample_text(CPU_SAMPLE),
+                                "by_threads": base}
     print(json.dumps(line))
     if dist is not None:
         dist.destroy_process_group()
+
+
+def extras(args, M, torch, dev, peaks, line):
+    """Measurements beyond the headline step, on the 10304 x 1000 workload:
+    its whole pipeline step, the batched and adjoint forms, the other
+    decoders and the Kron-reduced graphs."""
+    c1 = dict(gen.CONFIGS[SMALL_WORKLOAD])
+    Y1 = torch.as_tensor(gen.make_instance(0, c1["p"], c1["n"], c1["r"], c1["C"], c1["frac"])[0], device=dev)
+    kw1 = dict(K=c1["K"], fr=c1["fr"], fc=c1["fc"], seed=0, J=c1["J"], cg_tol=c1["cg_tol"])
+    for _ in range(3):
+        out1 = M.cpca_pipeline(Y1, **kw1)
+    ms, out1 = _event_ms(torch, lambda: M.cpca_pipeline(Y1, **kw1), 5)
+    line["step_10304x1000"] = {"ms_per_step": ms, "fista_iters_per_s": c1["J"] / (ms / 1000.0),
+                               "note": "best of 5 whole pipeline steps, L2 flushed before each"}
+    if not args.no_batched:
+        line["batched_64"] = batched_comparison(M, torch)
+    if not args.no_adjoint:
+        line["adjoint"] = adjoint_comparison(M, torch, Y1, c1)
+    if not args.no_alternate:
+        line["alternate_decoder"] = alternate_measure(M, torch, Y1, c1, peaks)
+        line["other_decoders"] = other_decoders_measure(M, torch, Y1, out1, c1, peaks)
+        line["kron_graphs"] = kron_measure(M, torch, out1, c1, peaks)
 
 
 if __name__ == "__main__":

@@ -127,10 +127,20 @@ typedef struct cpca_csr {
  * Requirements: 1 <= K <= 32, K < npts, dim >= 1.
  * ---------------------------------------------------------------------- */
 size_t cpca_knn_graph_workspace_size(int32_t npts, int32_t dim, int32_t K, int32_t transposed);
-/* Number of query points of the last cpca_knn_graph call on this host
- * thread whose candidate lists could not be certified and were therefore
- * searched by exact brute force. */
+/* Certification record of the last cpca_knn_graph call on this host
+ * thread. The tensor-core candidates of a query are certified when the
+ * worst-case TF32 error bound proves that no point outside its candidate
+ * lists can beat the K-th exact distance. Queries that fail are searched
+ * by exact brute force while their number stays within a budget of
+ * max(64, 2e11 / (npts dim)) (a query costs npts dim FMAs):
+ * cpca_knn_last_bruteforce() counts them. Beyond the budget none is
+ * redone; each keeps the exact K nearest of its tensor-core candidates (at
+ * least 4 x 32 per query in dimension >= 4096: the TF32 ranking error is
+ * far below the distance gaps in practice, but the worst-case bound can
+ * exceed the spread of a tight cluster) and cpca_knn_last_uncertified()
+ * counts them. */
 int32_t cpca_knn_last_bruteforce(void);
+int32_t cpca_knn_last_uncertified(void);
 cpca_status cpca_knn_graph(const float* pts, int32_t npts, int32_t dim, int64_t ld,
                            int32_t transposed, int32_t K, int32_t lap_type, double sigma2,
                            int64_t* rowptr, int32_t* col, float* val, float* weight,

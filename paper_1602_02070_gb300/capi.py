@@ -114,6 +114,7 @@ _SIGS = [
                                       C.POINTER(C.c_int32)]),
     ("cpca_knn_graph_workspace_size", C.c_size_t, [C.c_int32, C.c_int32, C.c_int32, C.c_int32]),
     ("cpca_knn_last_bruteforce", C.c_int32, []),
+    ("cpca_knn_last_uncertified", C.c_int32, []),
     ("cpca_knn_graph", C.c_int32,
      [C.c_void_p, C.c_int32, C.c_int32, C.c_int64, C.c_int32, C.c_int32, C.c_int32, C.c_double,
       C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p,
@@ -262,6 +263,13 @@ def knn_last_bruteforce() -> int:
     """Queries of the last cpca_knn_graph call (this thread) that fell back
     to exact brute force because their candidates were not certified."""
     return int(lib().cpca_knn_last_bruteforce())
+
+
+def knn_last_uncertified() -> int:
+    """Queries of the last cpca_knn_graph call (this thread) left with the
+    exact nearest of their tensor-core candidates, uncertified, because the
+    brute-force budget was exceeded."""
+    return int(lib().cpca_knn_last_uncertified())
 
 
 def launch_count() -> int:

@@ -697,18 +697,28 @@ struct KnnWs {
   size_t bytes;
 };
 
-static int knn_splits(int N) {
+// Base-range splits: enough blocks to fill the GPU, and, in high dimension
+// (where the tensor-core error bound rarely certifies), at least 4 x M
+// candidates per query for the exact recheck.
+static int knn_splits(int N, int d) {
   const int qt = (N + BQ - 1) / BQ;
+  const int smin = d >= 4096 ? 4 : 1;
   int s = 1;
-  while (s < 8 && qt * s < 2 * num_sms() && (N + BB - 1) / BB >= 4 * s * 2) s *= 2;
+  while (s < 8 && (qt * s < 2 * num_sms() || s < smin) && (N + BB - 1) / BB >= 4 * s * 2) s *= 2;
   return s;
+}
+
+// Brute-force budget of one graph: a query costs N d FMAs; at most
+// max(64, 2e11 / (N d)) uncertified queries are redone, else none is.
+static int knn_bruteforce_cap(int N, int d) {
+  return int(std::max<double>(64.0, std::min<double>(N, 2e11 / (double(N) * double(d)))));
 }
 static int knn_M(int K) { return K <= 16 ? 32 : 64; }
 
 static KnnWs knn_layout(void* ws, int N, int d, int K, int transposed) {
   Carve c(ws);
   KnnWs w{};
-  const int S = knn_splits(N), M = knn_M(K);
+  const int S = knn_splits(N, d), M = knn_M(K);
   w.Pt = transposed ? c.take<float>(size_t(N) * ((d + 3) & ~3)) : nullptr;
   w.nrm = c.take<float>(N);
   w.nmax = c.take<unsigned int>(1);
@@ -740,8 +750,9 @@ static KnnWs knn_layout(void* ws, int N, int d, int K, int transposed) {
 // kNN lists (idx, d2) of points P (N x d, row stride ld, K-major) into
 // out_i/out_d; P must be 16-byte aligned with ld % 4 == 0 for vector loads.
 cpca_status knn_lists(const float* P, int N, int d, int64_t ld, int K, const KnnWs& w,
-                      int32_t* out_i, float* out_d, cudaStream_t st) {
-  const int S = knn_splits(N), M = knn_M(K);
+                      int32_t* out_i, float* out_d, int* n_bruteforce, int* n_uncertified,
+                      cudaStream_t st) {
+  const int S = knn_splits(N, d), M = knn_M(K);
   const bool vec4 = (d % 4 == 0) && (ld % 4 == 0) && ((reinterpret_cast<uintptr_t>(P) & 15) == 0);
   CPCA_CUDA(cudaMemsetAsync(w.nmax, 0, sizeof(unsigned int), st));
   CPCA_CUDA(cudaMemsetAsync(w.n_redo, 0, sizeof(int32_t), st));
@@ -778,11 +789,21 @@ cpca_status knn_lists(const float* P, int N, int d, int64_t ld, int K, const Knn
       P, N, d, ld, vec4, K, M, S, w.cand_i, w.cand_d, w.nrm, w.nmax, err_rel, out_i, out_d, w.redo,
       w.n_redo);
   CPCA_LAUNCHED();
-  // queries without a certificate (rare): how many, then brute force in
-  // batches of kBfBatch over the whole grid
+  // queries without a certificate: how many, then, within the budget,
+  // brute force in batches of kBfBatch over the whole grid. Beyond the
+  // budget every such query keeps the exact K nearest of its S M
+  // tensor-core candidates (re-scored in FP32, settled in FP64) and is
+  // counted as uncertified.
   int nredo = 0;
   CPCA_CUDA(cudaMemcpyAsync(&nredo, w.n_redo, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
   CPCA_CUDA(cudaStreamSynchronize(st));
+  *n_bruteforce = 0;
+  *n_uncertified = 0;
+  if (nredo > knn_bruteforce_cap(N, d)) {
+    *n_uncertified = nredo;
+    return CPCA_OK;
+  }
+  *n_bruteforce = nredo;
   for (int r0 = 0; r0 < nredo; r0 += kBfBatch) {
     const int nq = std::min(kBfBatch, nredo - r0);
     const int64_t items = int64_t(nq) * ((N + kBfChunk - 1) / kBfChunk);
@@ -834,8 +855,10 @@ cpca_status graph_from_knn(const int32_t* kidx, const float* kd2, int N, int K, 
 using namespace cpca;
 
 static thread_local int g_knn_last_redo = 0;
+static thread_local int g_knn_last_unc = 0;
 
 extern "C" int32_t cpca_knn_last_bruteforce(void) { return g_knn_last_redo; }
+extern "C" int32_t cpca_knn_last_uncertified(void) { return g_knn_last_unc; }
 
 extern "C" size_t cpca_knn_graph_workspace_size(int32_t npts, int32_t dim, int32_t K,
                                                 int32_t transposed) {
@@ -880,17 +903,18 @@ extern "C" cpca_status cpca_knn_graph(const float* pts, int32_t npts, int32_t di
   }
   int32_t* oi = knn_idx ? knn_idx : w.kidx;
   float* od = knn_d2 ? knn_d2 : w.kd2;
-  CPCA_TRY(knn_lists(P, npts, dim, pld, K, w, oi, od, st));
+  int nbf = 0, nunc = 0;
+  CPCA_TRY(knn_lists(P, npts, dim, pld, K, w, oi, od, &nbf, &nunc, st));
+  g_knn_last_redo = nbf;
+  g_knn_last_unc = nunc;
   CPCA_TRY(graph_from_knn(oi, od, npts, K, lap_type, sigma2, w, rowptr, col, val, weight, nnz_cap, st));
   int64_t nnz = 0;
   double s2 = 0;
   CPCA_CUDA(cudaMemcpyAsync(&nnz, rowptr + npts, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
   CPCA_CUDA(cudaMemcpyAsync(&s2, w.sigma2, sizeof(double), cudaMemcpyDeviceToHost, st));
-  int terr = 0, nredo = 0;
+  int terr = 0;
   CPCA_CUDA(cudaMemcpyAsync(&terr, w.err, sizeof(int), cudaMemcpyDeviceToHost, st));
-  CPCA_CUDA(cudaMemcpyAsync(&nredo, w.n_redo, sizeof(int), cudaMemcpyDeviceToHost, st));
   CPCA_CUDA(cudaStreamSynchronize(st));
-  g_knn_last_redo = nredo;
   if (terr) {
     set_error("cpca_knn_graph: tensor-core pass timed out waiting on an mbarrier");
     return CPCA_ERR_TIMEOUT;

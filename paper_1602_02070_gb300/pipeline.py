@@ -40,13 +40,20 @@ def cpca_pipeline(Y: torch.Tensor, K: int = 10, fr: float = 0.25, fc: float = 0.
     p, n = Y.shape
     rr, rc = rho_of(p, fr), rho_of(n, fc)
     mark("start")
-    Lr, _, _ = capi.cpca_knn_graph(Y, K, lap_type)
-    Lc, _, _ = capi.cpca_knn_graph(Y, K, lap_type, transposed=True)
+    cert = {}  # per graph: (queries brute-forced, queries left uncertified)
+
+    def knn(pts, name, transposed):
+        G, _, _ = capi.cpca_knn_graph(pts, K, lap_type, transposed=transposed)
+        cert[name] = (capi.knn_last_bruteforce(), capi.knn_last_uncertified())
+        return G
+
+    Lr = knn(Y, "Lr", False)
+    Lc = knn(Y, "Lc", True)
     mark("graphs")
     om_r, om_c, Yt = capi.cpca_sample(seed, p, n, rr, rc, Y)
     if graphs == "knn":
-        Lrt, _, _ = capi.cpca_knn_graph(Yt, K, lap_type)
-        Lct, _, _ = capi.cpca_knn_graph(Yt, K, lap_type, transposed=True)
+        Lrt = knn(Yt, "Lrt", False)
+        Lct = knn(Yt, "Lct", True)
     else:
         Lrt = capi.cpca_kron_reduce(Lr, om_r, tol=kron_tol)["csr"]
         Lct = capi.cpca_kron_reduce(Lc, om_c, tol=kron_tol)["csr"]
@@ -64,5 +71,5 @@ def cpca_pipeline(Y: torch.Tensor, K: int = 10, fr: float = 0.25, fc: float = 0.
         capi.cpca_frpcag_status(fws)
     mark("decode")
     dec.update({"Xt": Xt, "Yt": Yt, "omega_r": om_r, "omega_c": om_c, "Lr": Lr, "Lc": Lc,
-                "Lrt": Lrt, "Lct": Lct})
+                "Lrt": Lrt, "Lct": Lct, "knn_certification": cert})
     return dec

@@ -1314,6 +1314,7 @@ extern "C" cpca_status cpca_frpcag_forward_tape(const float* Yt, int32_t rr, int
                                                 int64_t ldx, cpca_frpcag_grad_info* ginfo, void* ws,
                                                 size_t ws_bytes, void* stream) {
   clear_error();
+  CPCA_RANGE("cpca_frpcag_forward_tape");
   AdjCall c{};
   c.Yt = Yt;
   c.rr = rr;
@@ -1343,6 +1344,7 @@ extern "C" cpca_status cpca_frpcag_backward(const float* Yt, int32_t rr, int32_t
                                             cpca_frpcag_grad_info* ginfo, void* ws, size_t ws_bytes,
                                             void* stream) {
   clear_error();
+  CPCA_RANGE("cpca_frpcag_backward");
   AdjCall c{};
   c.Yt = Yt;
   c.rr = rr;

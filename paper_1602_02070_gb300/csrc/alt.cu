@@ -361,6 +361,7 @@ extern "C" cpca_status cpca_alternate_decode(const float* Xt, int32_t rr, int32_
                                              const cpca_alt_params* prm, float* X, int64_t ldx,
                                              cpca_alt_info* info, void* ws, size_t ws_bytes, void* stream) {
   clear_error();
+  CPCA_RANGE("cpca_alternate_decode");
   CPCA_CHECK_ARG(Xt && omega_r && omega_c && X && prm, "cpca_alternate_decode: null pointer");
   CPCA_CHECK_ARG(p > 0 && n > 0 && rr > 0 && rc > 0 && rr <= p && rc <= n,
                  "cpca_alternate_decode: bad sizes (p %d, n %d, rr %d, rc %d)", p, n, rr, rc);

@@ -174,6 +174,7 @@ extern "C" cpca_status cpca_cluster_decode(const float* Xt, int32_t rr, int32_t 
                                            float* C, cpca_cluster_info* info, void* ws, size_t ws_bytes,
                                            void* stream) {
   clear_error();
+  CPCA_RANGE("cpca_cluster_decode");
   CPCA_CHECK_ARG(Xt && omega_c && Lc && prm && labels, "cpca_cluster_decode: null pointer");
   CPCA_CHECK_ARG(rr > 0 && rc > 0 && n >= rc && ldxt >= rc, "cpca_cluster_decode: bad sizes");
   CPCA_CHECK_ARG(prm->k >= 1 && prm->k <= kClusterKmax && prm->k <= rc,

@@ -3,6 +3,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 #include <stdint.h>
 #include <stdio.h>
 #include <string.h>
@@ -47,6 +48,16 @@ void prof_end();
       return CPCA_ERR_CUDA;                                                    \
     }                                                                          \
   } while (0)
+
+// NVTX range over an entry point (tracing aid: the call's name on a
+// profiler's timeline; header-only NVTX, inert without a profiler).
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
+#define CPCA_RANGE(name) ::cpca::NvtxRange cpca_range_(name)
 
 // After a launch: count it and surface launch-configuration errors.
 #define CPCA_LAUNCHED()                                                        \

@@ -790,31 +790,85 @@ __global__ void scale_cols_kernel(float* __restrict__ U, int64_t total, int ldu,
 }
 
 // X (p x n) = U diag(sigma) V^T, 32 x 128 tile per block, streaming stores.
+// X (p x n) = U diag(sigma) V^T, X(i, j) = sum_c (U(i, c) sigma_c) V(j, c)
+// summed in c order (Algorithm 2, step 6; also the projections of
+// approximate decoders 2 and 3 with sigma = 1). A block owns 256 columns
+// and OUT_RT row tiles of 32 rows: V's 256 x k slice is staged once in shared
+// memory, k-major, then each thread computes an 8 x 4 block of X per row
+// tile (8 sigma-scaled U values and 4 V values per c from shared memory, 32
+// FMAs) and writes its 8 rows as 16-byte streaming stores. The bound is the
+// 4 B per entry written (8 GB at 20000 x 100000).
+constexpr int OUT_RT = 4;
 __global__ void __launch_bounds__(256)
 output_kernel(const float* __restrict__ U, int ldu, const float* __restrict__ V, int ldv,
               const double* __restrict__ sigma, int k, int p, int n, float* __restrict__ X, int64_t ldx) {
-  __shared__ float Us[32][KMAX_LIMIT + 1];
-  __shared__ float Vs[128][KMAX_LIMIT + 1];
-  const int i0 = blockIdx.y * 32, j0 = blockIdx.x * 128;
-  for (int e = threadIdx.x; e < 32 * k; e += blockDim.x) {
-    const int r = e / k, c = e % k;
-    Us[r][c] = (i0 + r < p) ? float(double(U[int64_t(i0 + r) * ldu + c]) * sigma[c]) : 0.f;
+  extern __shared__ __align__(16) float osm[];
+  float* VsT = osm;              // [k][256]
+  float* UsT = osm + k * 256;    // [k][32]
+  const int tid = threadIdx.x, tx = tid & 63, ty = tid >> 6;
+  const int j0 = blockIdx.x * 256;
+  for (int e = tid; e < 256 * k; e += 256) {
+    const int jj = e & 255, c = e >> 8;
+    VsT[c * 256 + jj] = (j0 + jj < n) ? __ldg(V + int64_t(j0 + jj) * ldv + c) : 0.f;
   }
-  for (int e = threadIdx.x; e < 128 * k; e += blockDim.x) {
-    const int r = e / k, c = e % k;
-    Vs[r][c] = (j0 + r < n) ? V[int64_t(j0 + r) * ldv + c] : 0.f;
+  const int j = j0 + 4 * tx;
+  const bool vec = j + 3 < n && (ldx & 3) == 0 && (reinterpret_cast<uintptr_t>(X) & 15) == 0;
+  for (int rt = 0; rt < OUT_RT; ++rt) {
+    const int i0 = (blockIdx.y * OUT_RT + rt) * 32;
+    if (i0 >= p) break;
+    __syncthreads();  // VsT complete; UsT free for the next tile
+    for (int e = tid; e < 32 * k; e += 256) {
+      const int r = e & 31, c = e >> 5;
+      UsT[c * 32 + r] = (i0 + r < p) ? float(double(__ldg(U + int64_t(i0 + r) * ldu + c)) * sigma[c]) : 0.f;
+    }
+    __syncthreads();
+    float acc[8][4];
+#pragma unroll
+    for (int r = 0; r < 8; ++r)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) acc[r][q] = 0.f;
+    for (int c = 0; c < k; ++c) {
+      const float4 u0 = *reinterpret_cast<const float4*>(UsT + c * 32 + 8 * ty);
+      const float4 u1 = *reinterpret_cast<const float4*>(UsT + c * 32 + 8 * ty + 4);
+      const float4 v = *reinterpret_cast<const float4*>(VsT + c * 256 + 4 * tx);
+      const float uu[8] = {u0.x, u0.y, u0.z, u0.w, u1.x, u1.y, u1.z, u1.w};
+      const float vv[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+      for (int r = 0; r < 8; ++r)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc[r][q] = fmaf(uu[r], vv[q], acc[r][q]);
+    }
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+      const int i = i0 + 8 * ty + r;
+      if (i >= p) break;
+      float* x = X + int64_t(i) * ldx + j;
+      if (vec) {
+        __stcs(reinterpret_cast<float4*>(x), make_float4(acc[r][0], acc[r][1], acc[r][2], acc[r][3]));
+      } else {
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+          if (j + q < n) __stcs(x + q, acc[r][q]);
+      }
+    }
   }
-  __syncthreads();
-  const int jj = threadIdx.x & 127, ig = threadIdx.x >> 7;
-  const int j = j0 + jj;
-  if (j >= n) return;
-  for (int r = ig; r < 32; r += 2) {
-    const int i = i0 + r;
-    if (i >= p) break;
-    float s = 0.f;
-    for (int c = 0; c < k; ++c) s = fmaf(Us[r][c], Vs[jj][c], s);
-    __stcs(X + int64_t(i) * ldx + j, s);
+}
+
+// launch of output_kernel for a p x n X
+static cpca_status launch_output(const float* U, int ldu, const float* V, int ldv, const double* sigma, int k,
+                                 int p, int n, float* X, int64_t ldx, cudaStream_t st) {
+  const size_t smem = size_t(k) * (256 + 32) * sizeof(float);
+  if (smem > 48 * 1024) {
+    static PerDeviceOnce attr;
+    CPCA_CUDA(once_per_device(attr, [&] {
+      return cudaFuncSetAttribute(output_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  int(size_t(KMAX_LIMIT) * (256 + 32) * sizeof(float)));
+    }));
   }
+  const dim3 og(ceil_div(n, 256), ceil_div(p, 32 * OUT_RT));
+  output_kernel<<<og, 256, smem, st>>>(U, ldu, V, ldv, sigma, k, p, n, X, ldx);
+  CPCA_LAUNCHED();
+  return CPCA_OK;
 }
 
 }  // namespace
@@ -1240,6 +1294,7 @@ extern "C" cpca_status cpca_decode(const float* Xt, int32_t rr, int32_t rc, int6
                                    float* V, double* sigma, int32_t* k_out, cpca_decode_info* info,
                                    void* ws, size_t ws_bytes, void* stream) {
   clear_error();
+  CPCA_RANGE("cpca_decode");
   CPCA_CHECK_ARG(Xt && omega_r && omega_c && prm, "cpca_decode: null pointer");
   CPCA_CHECK_ARG(rr > 0 && rc > 0 && rr <= p && rc <= n, "cpca_decode: need 0 < rr <= p, 0 < rc <= n");
   CPCA_CHECK_ARG(ldxt >= rc, "cpca_decode: ldxt < rc");
@@ -1307,10 +1362,8 @@ extern "C" cpca_status cpca_decode(const float* Xt, int32_t rr, int32_t rc, int6
     if (k == 0) {
       CPCA_CUDA(cudaMemset2DAsync(X, ldx * sizeof(float), 0, size_t(n) * sizeof(float), p, st));
     } else {
-      dim3 og(ceil_div(n, 128), ceil_div(p, 32));
       CPCA_PROF("decode_output", st);
-      output_kernel<<<og, 256, 0, st>>>(Uo, kmax, Vo, kmax, so, k, p, n, X, ldx);
-      CPCA_LAUNCHED();
+      CPCA_TRY(launch_output(Uo, kmax, Vo, kmax, so, k, p, n, X, ldx, st));
     }
   }
   if (k_out) *k_out = k;
@@ -1789,6 +1842,7 @@ extern "C" cpca_status cpca_decode_backward(const float* Xt, int32_t rr, int32_t
                                             int32_t lap_type, float* dwr, float* dwc, void* ws,
                                             size_t ws_bytes, void* stream) {
   clear_error();
+  CPCA_RANGE("cpca_decode_backward");
   CPCA_CHECK_ARG(Xt && omega_r && omega_c && prm && dXt, "cpca_decode_backward: null pointer");
   CPCA_CHECK_ARG(nh >= 0 && (nh == 0 || (h_row && h_col && h_grad)), "cpca_decode_backward: bad entries");
   CPCA_CHECK_ARG(rr > 0 && rc > 0 && rr <= p && rc <= n, "cpca_decode_backward: need 0 < rr <= p, 0 < rc <= n");
@@ -2016,6 +2070,7 @@ extern "C" cpca_status cpca_subspace_project(int32_t side, const float* basis, i
                                              const float* Y, int64_t ldy, int32_t p, int32_t n, float* X,
                                              int64_t ldx, void* ws, size_t ws_bytes, void* stream) {
   clear_error();
+  CPCA_RANGE("cpca_subspace_project");
   CPCA_CHECK_ARG(basis && Y && X, "cpca_subspace_project: null pointer");
   CPCA_CHECK_ARG(side == 0 || side == 1, "cpca_subspace_project: side must be 0 (U) or 1 (V)");
   CPCA_CHECK_ARG(p > 0 && n > 0 && ldb >= 1 && ldb <= KMAX_LIMIT && k >= 0 && k <= ldb,
@@ -2035,20 +2090,17 @@ extern "C" cpca_status cpca_subspace_project(int32_t side, const float* basis, i
   }
   ones_kernel<<<1, 64, 0, st>>>(ones, k);
   CPCA_LAUNCHED();
-  dim3 og(ceil_div(n, 128), ceil_div(p, 32));
   if (side == 0) {
     CPCA_PROF("project_small", st);
     CPCA_TRY(tn_tall(Y, ldy, p, n, basis, ldb, W, scr, st));  // W = Y^T U (n x ldb)
     CPCA_PROF("project_output", st);
-    output_kernel<<<og, 256, 0, st>>>(basis, ldb, W, ldb, ones, k, p, n, X, ldx);
-    CPCA_LAUNCHED();
+    CPCA_TRY(launch_output(basis, ldb, W, ldb, ones, k, p, n, X, ldx, st));
   } else {
     CPCA_PROF("project_small", st);
     gemm_nn_tall<<<ceil_div(p, 8), 256, 0, st>>>(Y, ldy, p, n, basis, ldb, W);  // W = Y V (p x ldb)
     CPCA_LAUNCHED();
     CPCA_PROF("project_output", st);
-    output_kernel<<<og, 256, 0, st>>>(W, ldb, basis, ldb, ones, k, p, n, X, ldx);
-    CPCA_LAUNCHED();
+    CPCA_TRY(launch_output(W, ldb, basis, ldb, ones, k, p, n, X, ldx, st));
   }
   return CPCA_OK;
 }
@@ -2075,6 +2127,7 @@ extern "C" cpca_status cpca_kron_reduce(const cpca_csr* L, const int32_t* omega,
                                         int32_t max_iter, float* Lt, int64_t ldlt, int64_t* rowptr, int32_t* col,
                                         float* val, cpca_kron_info* info, void* ws, size_t ws_bytes, void* stream) {
   clear_error();
+  CPCA_RANGE("cpca_kron_reduce");
   CPCA_CHECK_ARG(L && omega && Lt, "cpca_kron_reduce: null pointer");
   CPCA_CHECK_ARG((rowptr == nullptr) == (col == nullptr) && (col == nullptr) == (val == nullptr),
                  "cpca_kron_reduce: rowptr, col and val go together");

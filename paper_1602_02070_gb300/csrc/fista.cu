@@ -1470,6 +1470,7 @@ extern "C" cpca_status cpca_frpcag_solve(const float* Yt, int32_t rr, int32_t rc
                                          cpca_solve_info* info, void* ws, size_t ws_bytes,
                                          void* stream) {
   clear_error();
+  CPCA_RANGE("cpca_frpcag_solve");
   CPCA_CHECK_ARG(Yt && X, "cpca_frpcag_solve: null pointer");
   CPCA_CHECK_ARG(rr > 0 && rc > 0, "cpca_frpcag_solve: empty matrix");
   CPCA_CHECK_ARG(ldyt >= rc && ldx >= rc, "cpca_frpcag_solve: leading dimension too small");
@@ -1573,6 +1574,7 @@ extern "C" cpca_status cpca_frpcag_solve_batched(const cpca_problem* probs, int3
                                                  cpca_solve_info* infos, void* ws, size_t ws_bytes,
                                                  void* stream) {
   clear_error();
+  CPCA_RANGE("cpca_frpcag_solve_batched");
   CPCA_TRY(check_params(prm, "cpca_frpcag_solve_batched"));
   CPCA_CHECK_ARG(prm->start_iter == 0 && !prm->prev_out,
                  "cpca_frpcag_solve_batched: warm starts are for single solves (start_iter = 0, no prev_out)");
@@ -1676,6 +1678,7 @@ extern "C" cpca_status cpca_frpcag_solve_noalloc(const float* Yt, int32_t rr, in
                                                  int64_t ldx, cpca_solve_info* info,
                                                  void* stream) {
   clear_error();
+  CPCA_RANGE("cpca_frpcag_solve_noalloc");
   CPCA_CHECK_ARG(rr > 0 && rc > 0, "cpca_frpcag_solve_noalloc: empty matrix");
   const size_t need = cpca_frpcag_workspace_size(rr, rc);
   if (need > kStaticWsBytes) {

@@ -873,6 +873,7 @@ extern "C" cpca_status cpca_knn_graph(const float* pts, int32_t npts, int32_t di
                                       float* knn_d2, int64_t* nnz_out, double* sigma2_out,
                                       void* ws, size_t ws_bytes, void* stream) {
   clear_error();
+  CPCA_RANGE("cpca_knn_graph");
   CPCA_CHECK_ARG(pts && rowptr && col && val, "cpca_knn_graph: null pointer");
   CPCA_CHECK_ARG(npts >= 2 && dim >= 1, "cpca_knn_graph: need npts >= 2, dim >= 1");
   CPCA_CHECK_ARG(K >= 1 && K <= 32 && K < npts, "cpca_knn_graph: need 1 <= K <= 32, K < npts");

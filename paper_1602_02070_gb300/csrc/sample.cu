@@ -146,6 +146,7 @@ extern "C" cpca_status cpca_sample(uint64_t seed, int32_t p, int32_t n, int32_t 
                                    int64_t ldyt, void* stream) {
   using namespace cpca;
   clear_error();
+  CPCA_RANGE("cpca_sample");
   CPCA_CHECK_ARG(p > 0 && n > 0, "cpca_sample: p, n must be positive");
   CPCA_CHECK_ARG(rho_r > 0 && rho_r <= p && rho_c > 0 && rho_c <= n,
                  "cpca_sample: need 0 < rho_r <= p and 0 < rho_c <= n");

@@ -134,11 +134,10 @@ size_t cpca_knn_graph_workspace_size(int32_t npts, int32_t dim, int32_t K, int32
  * by exact brute force while their number stays within a budget of
  * max(64, 2e11 / (npts dim)) (a query costs npts dim FMAs):
  * cpca_knn_last_bruteforce() counts them. Beyond the budget none is
- * redone; each keeps the exact K nearest of its tensor-core candidates (at
- * least 4 x 32 per query in dimension >= 4096: the TF32 ranking error is
- * far below the distance gaps in practice, but the worst-case bound can
- * exceed the spread of a tight cluster) and cpca_knn_last_uncertified()
- * counts them. */
+ * redone; each keeps the exact K nearest of the 2K best of its tensor-core
+ * candidates (the TF32 ranking error is far below the distance gaps in
+ * practice, but the worst-case bound can exceed the spread of a tight
+ * cluster in high dimension) and cpca_knn_last_uncertified() counts them. */
 int32_t cpca_knn_last_bruteforce(void);
 int32_t cpca_knn_last_uncertified(void);
 cpca_status cpca_knn_graph(const float* pts, int32_t npts, int32_t dim, int64_t ld,

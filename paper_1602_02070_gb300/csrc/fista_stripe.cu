@@ -77,6 +77,7 @@ __global__ void __launch_bounds__(STHREADS, 1) fista_stripe_kernel(const __grid_
   extern __shared__ __align__(128) unsigned char smraw[];
   StripeSmem& sm = *reinterpret_cast<StripeSmem*>(smraw);
   float* zs0 = reinterpret_cast<float*>(smraw + ((sizeof(StripeSmem) + 127) & ~size_t(127)));
+  int32_t* rowp = reinterpret_cast<int32_t*>(zs0 + size_t(2) * a.rr_pad * SW);  // [rr + 1], from rowptr[0]
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   if (__ldcg(a.done)) return;  // stopped at an earlier iteration
   if (a.eps > 0 && a.j > 1) {
@@ -100,6 +101,9 @@ __global__ void __launch_bounds__(STHREADS, 1) fista_stripe_kernel(const __grid_
     mbar_init(&sm.mbar[1], 1);
     mbar_fence_init();
   }
+  // row pointers of Lr relative to its first entry, for every stripe
+  const int64_t rbase = a.Lr.rowptr[0];
+  for (int i = tid; i <= a.rr; i += STHREADS) rowp[i] = int32_t(a.Lr.rowptr[i] - rbase);
   __syncthreads();
   auto issue = [&](int s, int buf) {  // one thread: the whole stripe s into buffer buf
     float* dst = zs0 + size_t(buf) * a.rr_pad * SW;
@@ -164,16 +168,16 @@ __global__ void __launch_bounds__(STHREADS, 1) fista_stripe_kernel(const __grid_
           };
           int q = 0;
           if (full) {
-            for (; q + 4 <= ds; q += 4) {  // four neighbours' loads in flight
-              float4 u[4], v[4];
+            for (; q + 8 <= ds; q += 8) {  // eight neighbours' loads in flight
+              float4 u[8], v[8];
 #pragma unroll
-              for (int t = 0; t < 4; ++t) {
+              for (int t = 0; t < 8; ++t) {
                 const float* p = a.ZTin + sm.coff[c][q + t] + i;
                 u[t] = ldg4(p);
                 v[t] = ldg4(p + 4);
               }
 #pragma unroll
-              for (int t = 0; t < 4; ++t) {
+              for (int t = 0; t < 8; ++t) {
                 const float w = sm.cval[c][q + t];
                 acc[0] = fmaf(w, u[t].x, acc[0]);
                 acc[1] = fmaf(w, u[t].y, acc[1]);
@@ -194,47 +198,76 @@ __global__ void __launch_bounds__(STHREADS, 1) fista_stripe_kernel(const __grid_
         *reinterpret_cast<float4*>(&sm.ac[c][rl + 4]) = make_float4(acc[4], acc[5], acc[6], acc[7]);
       }
       __syncthreads();
-      // ---- (Lr Z) from the stripe, prox, momentum: 8 lanes per row
+      // ---- (Lr Z) from the stripe, prox, momentum: 8 lanes per row, two
+      // rows per lane group at a time (independent load chains), the row
+      // pointers from shared memory, Y~ and S_{j-1} loaded up front
       {
-        const int g = lane >> 3, c = lane & 7, j = c0 + c;
-        const unsigned gmask = 0xFFu << (lane & ~7);
-        for (int rl = warp * 4 + g; rl < SCHUNK; rl += STHREADS / 8) {
-          const int i = r0 + rl;
-          if (i >= a.rr) break;  // uniform in the lane group
-          const int64_t f0 = a.Lr.rowptr[i];
-          const int deg = int(a.Lr.rowptr[i + 1] - f0);
-          float acc = 0.f;
-          for (int e0 = 0; e0 < deg; e0 += 8) {
-            const int e = e0 + c;
-            const int kk = e < deg ? __ldg(a.Lr.col + f0 + e) : 0;
-            const float ww = e < deg ? __ldg(a.Lr.val + f0 + e) : 0.f;
-            const int n = min(8, deg - e0);
-            for (int t = 0; t < n; ++t) {
-              const int kr = __shfl_sync(gmask, kk, (lane & ~7) + t);
-              const float wr = __shfl_sync(gmask, ww, (lane & ~7) + t);
-              acc = fmaf(wr, zs[size_t(kr) * SW + c], acc);
+        const int g = lane >> 3, c = lane & 7, j = c0 + c, gl = lane & ~7;
+        const unsigned gmask = 0xFFu << gl;
+        const bool jin = j < a.rc;
+        for (int rA = warp * 4 + g; rA < SCHUNK; rA += 2 * (STHREADS / 8)) {
+          const int rB = rA + STHREADS / 8;
+          const int iA = r0 + rA, iB = r0 + rB;
+          if (iA >= a.rr) break;  // uniform in the lane group
+          const bool vB = rB < SCHUNK && iB < a.rr;
+          float yA = 0.f, spA = 0.f, yB = 0.f, spB = 0.f;
+          if (jin) {
+            yA = __ldg(a.Yt + int64_t(iA) * a.ldy + j);
+            spA = a.S[int64_t(iA) * a.lds + j];
+            if (vB) {
+              yB = __ldg(a.Yt + int64_t(iB) * a.ldy + j);
+              spB = a.S[int64_t(iB) * a.lds + j];
             }
           }
-          float zn = 0.f;
-          if (j < a.rc) {
-            const float z = zs[size_t(i) * SW + c];
-            const float y = __ldg(a.Yt + int64_t(i) * a.ldy + j);
-            const float sp = a.S[int64_t(i) * a.lds + j];
-            const float gr = fmaf(a.two_gr, acc, a.two_gc * sm.ac[c][rl]);
-            const float v = fmaf(-lam, gr, z);
-            const float dl = v - y;
-            const float sv = y + copysignf(fmaxf(fabsf(dl) - lam, 0.f), dl);
-            zn = fmaf(a.mu, sv - sp, sv);
-            if (a.prev_out && a.j == a.J) a.prev_out[int64_t(i) * a.lds + j] = sp;
-            a.S[int64_t(i) * a.lds + j] = sv;
-            a.Zout[int64_t(i) * a.ldz + j] = zn;
-            if (a.want_stats) {
-              const double d = double(zn) - double(z);
-              dz += d * d;
-              nz += double(z) * double(z);
+          const int fA = rowp[iA], dA = rowp[iA + 1] - fA;
+          const int fB = vB ? rowp[iB] : 0, dB = vB ? rowp[iB + 1] - fB : 0;
+          float accA = 0.f, accB = 0.f;
+          const int dmax = max(dA, dB);
+          int kA = 0, kB = 0;
+          float wA = 0.f, wB = 0.f;
+          if (c < dA) { kA = __ldg(a.Lr.col + rbase + fA + c); wA = __ldg(a.Lr.val + rbase + fA + c); }
+          if (c < dB) { kB = __ldg(a.Lr.col + rbase + fB + c); wB = __ldg(a.Lr.val + rbase + fB + c); }
+          for (int e0 = 0; e0 < dmax; e0 += 8) {
+            // the next eight entries of both rows, in flight during this step
+            const int e1 = e0 + 8 + c;
+            int nkA = 0, nkB = 0;
+            float nwA = 0.f, nwB = 0.f;
+            if (e1 < dA) { nkA = __ldg(a.Lr.col + rbase + fA + e1); nwA = __ldg(a.Lr.val + rbase + fA + e1); }
+            if (e1 < dB) { nkB = __ldg(a.Lr.col + rbase + fB + e1); nwB = __ldg(a.Lr.val + rbase + fB + e1); }
+            const int nA = min(8, dA - e0), nB = min(8, dB - e0);
+#pragma unroll
+            for (int t = 0; t < 8; ++t) {
+              const int k1 = __shfl_sync(gmask, kA, gl + t), k2 = __shfl_sync(gmask, kB, gl + t);
+              const float w1 = __shfl_sync(gmask, wA, gl + t), w2 = __shfl_sync(gmask, wB, gl + t);
+              if (t < nA) accA = fmaf(w1, zs[size_t(k1) * SW + c], accA);
+              if (t < nB) accB = fmaf(w2, zs[size_t(k2) * SW + c], accB);
             }
+            kA = nkA; wA = nwA; kB = nkB; wB = nwB;
           }
-          sm.zn[c][rl] = zn;
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            const int rl = h ? rB : rA, i = h ? iB : iA;
+            if (h && !vB) break;
+            float zn = 0.f;
+            if (jin) {
+              const float z = zs[size_t(i) * SW + c];
+              const float y = h ? yB : yA, sp = h ? spB : spA, acc = h ? accB : accA;
+              const float gr = fmaf(a.two_gr, acc, a.two_gc * sm.ac[c][rl]);
+              const float v = fmaf(-lam, gr, z);
+              const float dl = v - y;
+              const float sv = y + copysignf(fmaxf(fabsf(dl) - lam, 0.f), dl);
+              zn = fmaf(a.mu, sv - sp, sv);
+              if (a.prev_out && a.j == a.J) a.prev_out[int64_t(i) * a.lds + j] = sp;
+              a.S[int64_t(i) * a.lds + j] = sv;
+              a.Zout[int64_t(i) * a.ldz + j] = zn;
+              if (a.want_stats) {
+                const double d = double(zn) - double(z);
+                dz += d * d;
+                nz += double(z) * double(z);
+              }
+            }
+            sm.zn[c][rl] = zn;
+          }
         }
       }
       __syncthreads();
@@ -292,7 +325,8 @@ __global__ void __launch_bounds__(STHREADS, 1) fista_stripe_kernel(const __grid_
 }
 
 size_t stripe_smem(int rr_pad) {
-  return ((sizeof(StripeSmem) + 127) & ~size_t(127)) + size_t(2) * rr_pad * SW * sizeof(float);
+  return ((sizeof(StripeSmem) + 127) & ~size_t(127)) + size_t(2) * rr_pad * SW * sizeof(float) +
+         size_t(rr_pad + 1) * sizeof(int32_t);
 }
 
 bool make_zmap(CUtensorMap* map, const float* Z, int rr, int64_t ldz) {
@@ -313,7 +347,7 @@ bool stripe_eligible(int rr, int rc) {
   if (rr < SBOX || rc < 4 * SW) return false;
   const int rr_pad = int(ceil_div(rr, SBOX)) * SBOX;
   return stripe_smem(rr_pad) <= size_t(max_smem_optin()) && int64_t(rc) * ((rr + 3) / 4 * 4) < (int64_t(1) << 31) &&
-         encode_fn() != nullptr;
+         encode_fn() != nullptr;  // (Lr has at most rr^2 < 2^31 entries: 32-bit row offsets)
 }
 
 cpca_status fista_stripe_run(const BatchProblem& P, const InstWs& iw, int J, double eps, bool want_last,

@@ -372,9 +372,10 @@ knn_recheck_kernel(const float* __restrict__ P, int N, int d, int64_t ld, bool v
     sd[c] = INF;
   }
   __syncwarp();
-  // a_K: K rounds of a warp argmin over the ranking values
-  float aK = INF;
-  for (int r = 0; r < K; ++r) {
+  // a_K: K rounds of a warp argmin over the ranking values (continued to
+  // a_2K, the 2K-th, for the case below)
+  float aK = INF, a2K = INF;
+  for (int r = 0; r < 2 * K; ++r) {
     float bv = INF;
     int bc = -1;
     for (int c = lane; c < C; c += 32) {
@@ -393,14 +394,26 @@ knn_recheck_kernel(const float* __restrict__ P, int N, int d, int64_t ld, bool v
         bc = oc;
       }
     }
-    aK = bv;
+    if (r < K) aK = bv;
+    a2K = bv;
     if (lane == 0 && bc >= 0) si[bc] = -2 - si[bc];  // temporarily hide the pick
     __syncwarp();
   }
   for (int c = lane; c < C; c += 32)
     if (si[c] <= -2) si[c] = -2 - si[c];
   __syncwarp();
-  const float window = aK + 2.f * e;
+  float window = aK + 2.f * e;
+  // When the error bound reaches past the end of a full candidate list the
+  // certificate cannot hold: the query is searched by brute force within
+  // the budget, else left uncertified. Its exact re-scoring is then kept to
+  // the 2K best ranking values (the ranking error in practice is far below
+  // the gaps that separate them from the K-th).
+  float thr_min = INF;
+  for (int s = 0; s < splits; ++s)
+    if (cand_i[(int64_t(s) * N + q) * M + (M - 1)] >= 0)
+      thr_min = fminf(thr_min, cand_d[(int64_t(s) * N + q) * M + (M - 1)]);
+  const bool hopeless = thr_min - e <= aK;
+  if (hopeless) window = fminf(window, a2K);
   for (int c = 0; c < C; ++c) {
     const int j = si[c];
     if (j < 0) continue;
@@ -420,7 +433,7 @@ knn_recheck_kernel(const float* __restrict__ P, int N, int d, int64_t ld, bool v
   // >= that list's last entry, hence an exact distance >= that minus e,
   // which must exceed every chosen exact distance (at most dK).
   if (lane == 0) {
-    bool ok = dK < INF;
+    bool ok = dK < INF && !hopeless;
     for (int s = 0; s < splits; ++s) {
       const float thr = cand_d[(int64_t(s) * N + q) * M + (M - 1)];
       if (!(thr - e > dK)) {
@@ -697,14 +710,12 @@ struct KnnWs {
   size_t bytes;
 };
 
-// Base-range splits: enough blocks to fill the GPU, and, in high dimension
-// (where the tensor-core error bound rarely certifies), at least 4 x M
-// candidates per query for the exact recheck.
+// Base-range splits: enough blocks to fill the GPU.
 static int knn_splits(int N, int d) {
+  (void)d;
   const int qt = (N + BQ - 1) / BQ;
-  const int smin = d >= 4096 ? 4 : 1;
   int s = 1;
-  while (s < 8 && (qt * s < 2 * num_sms() || s < smin) && (N + BB - 1) / BB >= 4 * s * 2) s *= 2;
+  while (s < 8 && qt * s < 2 * num_sms() && (N + BB - 1) / BB >= 4 * s * 2) s *= 2;
   return s;
 }
 

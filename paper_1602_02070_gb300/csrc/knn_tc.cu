@@ -18,6 +18,12 @@
 // 256-column accumulators in TMEM (512 columns) so the epilogue of one base
 // tile overlaps the MMAs of the next. Every mbarrier wait is bounded: on
 // timeout the block raises *err, stops, frees its TMEM and returns.
+// Clusters of CL = 2 blocks along the queries share every base tile: each
+// block loads 256/CL rows of it with a TMA multicast into every block of the
+// cluster (the operand tile of this GPU's own memory, read once from L2 for
+// CL blocks), and each block's MMA completion releases the stage in every
+// block (tcgen05.commit multicast), so a stage is refilled only when all
+// blocks of the cluster are done with it.
 #include <cuda.h>
 
 #include "knn_internal.cuh"
@@ -60,6 +66,32 @@ __device__ __forceinline__ void umma_commit(uint64_t* bar) {
                    smem_u32(bar))
                : "memory");
 }
+// release a stage in every block of the cluster named by `mask`
+__device__ __forceinline__ void umma_commit_mc(uint64_t* bar, uint16_t mask) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
+          smem_u32(bar)),
+      "h"(mask)
+      : "memory");
+}
+// TMA 2-D load delivered to the same offset in every block of `mask`
+__device__ __forceinline__ void tma_load_2d_mc(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y,
+                                               uint16_t mask) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes.multicast::cluster"
+      " [%0], [%1, {%3, %4}], [%2], %5;" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(x), "r"(y), "h"(mask)
+      : "memory");
+}
+__device__ __forceinline__ uint32_t cluster_rank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ void cluster_barrier() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
 __device__ __forceinline__ void tc_fence_before() {
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
 }
@@ -86,11 +118,12 @@ struct TcShared {
   int abort;
 };
 
-template <int M>
+template <int M, int CL>
 __global__ void __launch_bounds__(256, 1)
 knn_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
               int N, int d, const float* __restrict__ nrm, int splits, int32_t* __restrict__ cand_i,
               float* __restrict__ cand_d, int* __restrict__ err) {
+  // mapB boxes are BN / CL rows: this block's share of a base tile
   extern __shared__ __align__(1024) unsigned char raw[];
   // operand stages must be 1024-byte aligned for the 128-byte swizzle
   unsigned char* base = reinterpret_cast<unsigned char*>(
@@ -108,10 +141,12 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ 
   const int nt = max(0, t_hi - t_lo);
   const int nk = (d + BK - 1) / BK;
 
+  const uint32_t crank = CL > 1 ? cluster_rank() : 0u;
+  constexpr uint16_t cmask = uint16_t((1u << CL) - 1u);
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
       mbar_init(&sh.full[s], 1);
-      mbar_init(&sh.empty[s], 1);
+      mbar_init(&sh.empty[s], CL);  // released by the MMAs of every block of the cluster
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(&sh.acc_full[b], 1);
@@ -130,6 +165,7 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ 
   }
   tc_fence_before();
   __syncthreads();
+  if (CL > 1) cluster_barrier();  // every block's barriers exist before any multicast
   tc_fence_after();
   const uint32_t tmem = sh.tmem_base;
   volatile int* abort = &sh.abort;
@@ -142,10 +178,14 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ 
         for (int k = 0; k < nk; ++k, ++it) {
           const int s = it % STAGES, round = it / STAGES;
           if (!mbar_wait(&sh.empty[s], (round & 1) ^ 1, abort)) break;
-          mbar_expect_tx(&sh.full[s], STAGE_BYTES);
+          mbar_expect_tx(&sh.full[s], STAGE_BYTES);  // A + all CL shares of B
           unsigned char* sa = stages + s * STAGE_BYTES;
           tma_load_2d(sa, &mapA, &sh.full[s], k * BK, q0);
-          tma_load_2d(sa + A_BYTES, &mapB, &sh.full[s], k * BK, n0);
+          if (CL > 1)
+            tma_load_2d_mc(sa + A_BYTES + crank * (B_BYTES / CL), &mapB, &sh.full[s], k * BK,
+                           n0 + int(crank) * (BN / CL), cmask);
+          else
+            tma_load_2d(sa + A_BYTES, &mapB, &sh.full[s], k * BK, n0);
         }
       }
       // drain: wait for every issued stage to be consumed before leaving
@@ -177,7 +217,10 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ 
 #pragma unroll
           for (int kk = 0; kk < BK / 8; ++kk)  // 8 TF32 (32 bytes) per MMA
             umma_tf32(dt, ad + uint64_t(kk * 2), bd + uint64_t(kk * 2), idesc, (k | kk) ? 1u : 0u);
-          umma_commit(&sh.empty[s]);
+          if (CL > 1)
+            umma_commit_mc(&sh.empty[s], cmask);
+          else
+            umma_commit(&sh.empty[s]);
         }
         if (!ok) break;
         umma_commit(&sh.acc_full[buf]);
@@ -249,6 +292,9 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ 
   }
   tc_fence_before();
   __syncthreads();
+  // no block leaves while a peer may still write into its shared memory
+  // (multicast loads) or arrive on its barriers (multicast commits)
+  if (CL > 1) cluster_barrier();
   tc_fence_after();
   if (warp == 1)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS)
@@ -292,17 +338,35 @@ cpca_status knn_candidates_tc(const float* P, int N, int d, int64_t ld, int M, i
   if (!device_is_sm10x() || N < 64 || d < 16 || (ld % 4) != 0 ||
       (reinterpret_cast<uintptr_t>(P) & 15) != 0 || (M != 32 && M != 64))
     return CPCA_OK;
+  // clusters of two query tiles share the base tiles once there are enough
+  // query tiles to pair (the last pair may hold a tile past N: its A boxes
+  // are zero-filled and its epilogue writes nothing)
+  const int qtiles = int(ceil_div(N, BM));
+  const int CL = qtiles >= 8 ? 2 : 1;
   CUtensorMap mapA, mapB;
-  if (!make_map(&mapA, P, N, d, ld, BM) || !make_map(&mapB, P, N, d, ld, BN)) return CPCA_OK;
+  if (!make_map(&mapA, P, N, d, ld, BM) || !make_map(&mapB, P, N, d, ld, BN / CL)) return CPCA_OK;
   const size_t smem = knn_tc_smem(M);
-  const void* kern = M == 32 ? (const void*)knn_tc_kernel<32> : (const void*)knn_tc_kernel<64>;
-  CPCA_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
-  dim3 grid(ceil_div(N, BM), S);
+  const void* kern = M == 32 ? (CL == 2 ? (const void*)knn_tc_kernel<32, 2> : (const void*)knn_tc_kernel<32, 1>)
+                             : (CL == 2 ? (const void*)knn_tc_kernel<64, 2> : (const void*)knn_tc_kernel<64, 1>);
+  static PerDeviceOnce attr[4];
+  CPCA_CUDA(once_per_device(attr[(M == 64) * 2 + (CL == 2)], [&] {
+    return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+  }));
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = dim3(unsigned((qtiles + CL - 1) / CL * CL), unsigned(S));
+  cfg.blockDim = dim3(256);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = unsigned(CL);
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  void* args[] = {&mapA, &mapB, &N, &d, const_cast<float**>(&nrm), &S, &cand_i, &cand_d, &err};
   CPCA_PROF("knn_candidates_tc", st);
-  if (M == 32)
-    knn_tc_kernel<32><<<grid, 256, smem, st>>>(mapA, mapB, N, d, nrm, S, cand_i, cand_d, err);
-  else
-    knn_tc_kernel<64><<<grid, 256, smem, st>>>(mapA, mapB, N, d, nrm, S, cand_i, cand_d, err);
+  CPCA_CUDA(cudaLaunchKernelExC(&cfg, kern, args));
   CPCA_LAUNCHED();
   *done = true;
   return CPCA_OK;

@@ -1037,6 +1037,7 @@ BatchWs batch_layout(void* ws, const int* rr, const int* rc, int n) {
     w.pscr = c.take<unsigned char>(power_scratch_bytes(ns.data(), 2 * n));
   }
   for (int i = 0; i < n; ++i) w.inst[i] = inst_layout(c, rr[i], rc[i]);
+  w.stripe = n == 1 ? stripe_layout(c, rr[0], rc[0]) : StripeWs{};
   w.n = n;
   w.bytes = c.bytes();
   return w;
@@ -1250,6 +1251,27 @@ cpca_status fista_batch_run(const BatchProblem* P, int n, int J, double eps, boo
     fa.t0 = t;
   }
   fa.bar = grid_bar(w.bar, w.err);
+  // a single problem too large for the resident launch: one striped launch
+  // per iteration (no grid barrier; TMA-fed stripes), which sets up its own
+  // first iterate
+  const size_t smem = sizeof(TileSmem), smem_res = sizeof(TileSmem32);
+  const void* kres = (const void*)fista_batch_kernel<true>;
+  const void* kstr = (const void*)fista_batch_kernel<false>;
+  static PerDeviceOnce attr;
+  CPCA_CUDA(once_per_device(attr, [&] {
+    const cudaError_t e = cudaFuncSetAttribute(kres, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem_res));
+    return e != cudaSuccess ? e : cudaFuncSetAttribute(kstr, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+  }));
+  // 32-bit staged offsets: every instance's Z and ZT below 2^31 entries
+  bool small = true;
+  for (int i = 0; i < n; ++i)
+    small = small && int64_t(P[i].rr) * ((P[i].rc + 3) / 4 * 4) < (int64_t(1) << 31) &&
+            int64_t(P[i].rc) * ((P[i].rr + 3) / 4 * 4) < (int64_t(1) << 31);
+  const int cap_res = small ? coop_blocks(kres, 256, smem_res, 1 << 30) : 0;
+  const int cap_str = coop_blocks(kstr, 256, smem, 1 << 30);
+  bool resident = tiles <= cap_res;
+  if (n == 1 && J > 0 && !dense && !resident && blocks == 0 && stripe_eligible(P[0].rr, P[0].rc))
+    return fista_stripe_run(P[0], w.inst[0], w.stripe, J, eps, want_last, fa.t0, fa.mu0, w.err, st);
   init_batch_kernel<<<std::min(tiles, num_sms() * 8), 256, 0, st>>>(fa);
   CPCA_LAUNCHED();
   if (J == 0) return CPCA_OK;
@@ -1298,26 +1320,6 @@ cpca_status fista_batch_run(const BatchProblem* P, int n, int J, double eps, boo
     prof_end();
     return CPCA_OK;
   }
-  const size_t smem = sizeof(TileSmem), smem_res = sizeof(TileSmem32);
-  const void* kres = (const void*)fista_batch_kernel<true>;
-  const void* kstr = (const void*)fista_batch_kernel<false>;
-  static PerDeviceOnce attr;
-  CPCA_CUDA(once_per_device(attr, [&] {
-    const cudaError_t e = cudaFuncSetAttribute(kres, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem_res));
-    return e != cudaSuccess ? e : cudaFuncSetAttribute(kstr, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
-  }));
-  // 32-bit staged offsets: every instance's Z and ZT below 2^31 entries
-  bool small = true;
-  for (int i = 0; i < n; ++i)
-    small = small && int64_t(P[i].rr) * ((P[i].rc + 3) / 4 * 4) < (int64_t(1) << 31) &&
-            int64_t(P[i].rc) * ((P[i].rr + 3) / 4 * 4) < (int64_t(1) << 31);
-  const int cap_res = small ? coop_blocks(kres, 256, smem_res, 1 << 30) : 0;
-  const int cap_str = coop_blocks(kstr, 256, smem, 1 << 30);
-  bool resident = tiles <= cap_res;
-  // a single problem too large for the resident launch: one striped launch
-  // per iteration (no grid barrier; TMA-fed stripes)
-  if (n == 1 && !resident && blocks == 0 && stripe_eligible(P[0].rr, P[0].rc))
-    return fista_stripe_run(P[0], w.inst[0], J, eps, want_last, fa.t0, w.err, st);
   CPCA_CUDA(cudaMemsetAsync(w.bar, 0, sizeof(unsigned int) * (kBarrierCounters + 1), st));
   int grid = resident ? tiles : cap_str;
   if (blocks > 0) {  // explicit launch width (autotuner)

@@ -123,6 +123,19 @@ struct InstWs {
   int* done;          // [stopped, iterations]
 };
 
+// Extra scratch of the striped launch of a large single problem: Y~, S and
+// one more iterate in the columns' locality order, the order itself and the
+// ordering kernel's scratch (all null when the problem does not take it).
+struct StripeWs {
+  float* Yp;
+  float* Sp;
+  float* Pp;            // S_{j0-1} in (warm start), S_{J-1} out
+  int32_t* perm;        // processing position -> column
+  int32_t* inv;         // column -> processing position
+  unsigned char* oscr;  // order_scratch_bytes
+  unsigned int* bar;    // the ordering kernel's grid barrier
+};
+
 // Scratch of a (batched) solve: shared barrier state plus one InstWs each.
 struct BatchWs {
   unsigned int* bar;  // grid barrier counter + generation
@@ -131,6 +144,7 @@ struct BatchWs {
   double* obj;
   void* pscr;         // power iteration scratch (power_scratch_bytes)
   InstWs inst[kMaxBatch];
+  StripeWs stripe;      // single problems only
   int n;
   size_t bytes;
 };
@@ -157,12 +171,21 @@ cpca_status fista_batch_run(const BatchProblem* P, int n, int J, double eps, boo
                             cudaStream_t st, bool dense = false);
 // Striped FISTA for single large problems (fista_stripe.cu): one launch per
 // iteration, Z_j's stripes through TMA; the same iterates as the resident
-// and streaming launches. Z_1, Z_1^T and S_0 are set up by the caller.
+// and streaming launches. It sets up Z_1 (or Z_{j0+1}) itself; t0 =
+// t_{j0+1} and mu0 = mu_{j0} of a warm start (1 and 0 for a cold one);
+// P.prev_out, when set, receives S_{J-1}. stripe_reorders: the problem also
+// takes the columns' locality order (StripeWs carved by stripe_layout).
 bool stripe_eligible(int rr, int rc);
-// t0 = t_{j0+1} of a warm start (1 for a cold one); P.prev_out, when set,
-// receives S_{J-1}.
-cpca_status fista_stripe_run(const BatchProblem& P, const InstWs& iw, int J, double eps, bool want_last,
-                             double t0, int* err, cudaStream_t st);
+bool stripe_reorders(int rr, int rc);
+StripeWs stripe_layout(Carve& c, int rr, int rc);
+cpca_status fista_stripe_run(const BatchProblem& P, const InstWs& iw, const StripeWs& sw, int J, double eps,
+                             bool want_last, double t0, float mu0, int* err, cudaStream_t st);
+// Locality order of a graph's nodes (order.cu): perm[position] = node,
+// inv[node] = position; components, then breadth-first levels, then index.
+bool order_supported(int n);
+size_t order_scratch_bytes(int n);
+cpca_status graph_order(const CsrView& L, int32_t* perm, int32_t* inv, void* scratch, unsigned int* bar,
+                        int* err, cudaStream_t st);
 cpca_status fista_objective(const float* Yt, int64_t ldy, int rr, int rc, const CsrView& Lr,
                             const CsrView& Lc, const float* X, int64_t ldx, double gr, double gc,
                             double* part, double* out, cudaStream_t st);

@@ -6,22 +6,29 @@
 // into shared memory with TMA (boxes of 8 columns x 256 rows, double-
 // buffered: the next stripe's load runs while the current one computes).
 // Then, in chunks of 512 rows:
-//   (Z Lc)(i, j) = sum_l Lc[j, l] Z^T(l, i): for each of the stripe's
-//       columns, the neighbour columns' rows of Z^T are read as 32-byte
-//       vectors through L1 (the whole Z^T of the iteration is read-only
-//       inside the launch);
+//   (Z Lc)(i, j) = sum_l Lc[j, l] Z^T(l, i): each warp takes 32 rows (a
+//       lane per row) and all 8 stripe columns, reading the neighbour
+//       columns' rows of Z^T through L1 as coalesced 128-byte segments (the
+//       whole Z^T of the iteration is read-only inside the launch);
 //   (Lr Z)(i, j) = sum_k Lr[i, k] Z(k, j): entirely from the stripe in
-//       shared memory (a row graph links arbitrary rows, and the stripe
-//       holds all of them), 8 lanes per row;
+//       shared memory (a row graph links arbitrary rows, and the stripe holds
+//       all of them), 8 lanes per row, two rows per lane group at a time;
 //   S_j = prox(Z_j - lambda 2 (g_c Z Lc + g_r Lr Z)),
 //   Z_{j+1} = S_j + mu_j (S_j - S_{j-1}),
-// written row-major (S_j, Z_{j+1}) and column-major (Z_{j+1}^T, through
-// shared memory for whole-row stores). Both graph sums run in CSR order
-// with one FMA per entry, exactly as the resident kernel's: the iterates are
-// bit for bit those of fista_batch_kernel. Launch boundaries order the
-// iterations, so there is no grid barrier; with eps > 0 every launch first
-// reads the previous iteration's statistics and all its blocks leave once
-// the stopping test holds.
+// written row-major (S_j, Z_{j+1}) and column-major (Z_{j+1}^T). Both graph
+// sums run in CSR order with one FMA per entry, exactly as the resident
+// kernel's: the iterates are bit for bit those of fista_batch_kernel.
+// Launch boundaries order the iterations, so there is no grid barrier; with
+// eps > 0 every launch first reads the previous iteration's statistics and
+// all its blocks leave once the stopping test holds.
+//
+// Column order: for large problems the columns are processed in a
+// locality order of the column graph (order.cu: components, then
+// breadth-first levels), so that the stripes in flight gather their Z^T
+// rows from a narrow band that stays in L2. Y~, S and the iterates are
+// permuted into that order once per solve and X is permuted back at the
+// end; each column keeps its CSR entry order, so the arithmetic - and the
+// result - is unchanged.
 //
 // Algorithmic bytes per iteration: read Y~, S_{j-1}, Z_j (stripe), Z_j^T
 // (gathers), write S_j, Z_{j+1}, Z_{j+1}^T: 28 B per entry when every
@@ -46,6 +53,8 @@ struct StripeArgs {
   const float* Yt;
   float* S;
   CsrView Lr, Lc;
+  const int32_t* perm;  // processing position -> column of Lc (null: identity)
+  const int32_t* inv;   // column of Lc -> processing position
   const double* lam;
   double* stats;  // ring [4][2]
   int* done;      // [stopped, iterations]
@@ -61,8 +70,7 @@ struct StripeArgs {
 
 struct StripeSmem {
   float ac[SW][SCHUNK];     // (Z Lc) of the chunk, [column][row]
-  float zn[SW][SCHUNK];     // Z_{j+1} of the chunk, [column][row]
-  int32_t coff[SW][SCN];    // neighbour column l -> element offset l * ldzt
+  int32_t coff[SW][SCN];    // neighbour column -> element offset of its Z^T row
   float cval[SW][SCN];
   int64_t cf0[SW];
   int cdeg[SW];
@@ -70,8 +78,6 @@ struct StripeSmem {
   double red[2][STHREADS / 32];
   int abort;
 };
-
-__device__ __forceinline__ float4 ldg4(const float* p) { return __ldg(reinterpret_cast<const float4*>(p)); }
 
 __global__ void __launch_bounds__(STHREADS, 1) fista_stripe_kernel(const __grid_constant__ StripeArgs a) {
   extern __shared__ __align__(128) unsigned char smraw[];
@@ -122,16 +128,18 @@ __global__ void __launch_bounds__(STHREADS, 1) fista_stripe_kernel(const __grid_
     const int c0 = s * SW;
     // neighbour lists of the stripe's columns (overlaps the stripe's load)
     if (tid < SW) {
-      const int j = c0 + tid;
-      const int64_t f0 = j < a.rc ? a.Lc.rowptr[j] : 0;
+      const int jp = c0 + tid;
+      const int jc = jp < a.rc ? (a.perm ? a.perm[jp] : jp) : 0;
+      const int64_t f0 = jp < a.rc ? a.Lc.rowptr[jc] : 0;
       sm.cf0[tid] = f0;
-      sm.cdeg[tid] = j < a.rc ? int(a.Lc.rowptr[j + 1] - f0) : 0;
+      sm.cdeg[tid] = jp < a.rc ? int(a.Lc.rowptr[jc + 1] - f0) : 0;
     }
     __syncthreads();
     for (int e = tid; e < SW * SCN; e += STHREADS) {
       const int c = e / SCN, q = e % SCN;
       if (q < min(sm.cdeg[c], SCN)) {
-        sm.coff[c][q] = int32_t(__ldg(a.Lc.col + sm.cf0[c] + q)) * int32_t(a.ldzt);
+        const int l = __ldg(a.Lc.col + sm.cf0[c] + q);
+        sm.coff[c][q] = int32_t(a.inv ? a.inv[l] : l) * int32_t(a.ldzt);
         sm.cval[c][q] = __ldg(a.Lc.val + sm.cf0[c] + q);
       }
     }
@@ -139,63 +147,45 @@ __global__ void __launch_bounds__(STHREADS, 1) fista_stripe_kernel(const __grid_
     __syncthreads();
     if (sm.abort) break;
     for (int r0 = 0; r0 < a.rr; r0 += SCHUNK) {
-      // ---- (Z Lc): warp -> stripe column c, 256-row half h; lane -> 8 rows
+      // ---- (Z Lc): warp -> 32 rows (a lane per row), all stripe columns,
+      // the columns' neighbour lists walked side by side (32 loads in
+      // flight per lane), each column's sum still in its CSR order
       {
-        const int c = warp & (SW - 1), h = warp >> 3;
-        const int rl = h * 256 + lane * 8, i = r0 + rl;
-        float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-        const int deg = sm.cdeg[c];
-        if (i < a.rr) {
-          const bool full = i + 8 <= int(a.ldzt);
-          const int ds = min(deg, SCN);
-          auto add = [&](int64_t off, float w) {
-            const float* p = a.ZTin + off + i;
-            if (full) {
-              const float4 u = ldg4(p), v = ldg4(p + 4);
-              acc[0] = fmaf(w, u.x, acc[0]);
-              acc[1] = fmaf(w, u.y, acc[1]);
-              acc[2] = fmaf(w, u.z, acc[2]);
-              acc[3] = fmaf(w, u.w, acc[3]);
-              acc[4] = fmaf(w, v.x, acc[4]);
-              acc[5] = fmaf(w, v.y, acc[5]);
-              acc[6] = fmaf(w, v.z, acc[6]);
-              acc[7] = fmaf(w, v.w, acc[7]);
-            } else {
+        const int rl = warp * 32 + lane, i = r0 + rl;
+        const bool ok = i < a.rr;
+        float acc[SW];
 #pragma unroll
-              for (int t = 0; t < 8; ++t)
-                if (i + t < a.rr) acc[t] = fmaf(w, __ldg(p + t), acc[t]);
+        for (int c = 0; c < SW; ++c) acc[c] = 0.f;
+        if (ok) {
+          int dmax = 0;
+#pragma unroll
+          for (int c = 0; c < SW; ++c) dmax = max(dmax, min(sm.cdeg[c], SCN));
+          for (int q0 = 0; q0 < dmax; q0 += 4) {
+            float v[SW][4];
+#pragma unroll
+            for (int c = 0; c < SW; ++c) {
+              const int ds = min(sm.cdeg[c], SCN);
+#pragma unroll
+              for (int t = 0; t < 4; ++t)
+                v[c][t] = q0 + t < ds ? __ldg(a.ZTin + sm.coff[c][q0 + t] + i) : 0.f;
             }
-          };
-          int q = 0;
-          if (full) {
-            for (; q + 8 <= ds; q += 8) {  // eight neighbours' loads in flight
-              float4 u[8], v[8];
 #pragma unroll
-              for (int t = 0; t < 8; ++t) {
-                const float* p = a.ZTin + sm.coff[c][q + t] + i;
-                u[t] = ldg4(p);
-                v[t] = ldg4(p + 4);
-              }
+            for (int c = 0; c < SW; ++c) {
+              const int ds = min(sm.cdeg[c], SCN);
 #pragma unroll
-              for (int t = 0; t < 8; ++t) {
-                const float w = sm.cval[c][q + t];
-                acc[0] = fmaf(w, u[t].x, acc[0]);
-                acc[1] = fmaf(w, u[t].y, acc[1]);
-                acc[2] = fmaf(w, u[t].z, acc[2]);
-                acc[3] = fmaf(w, u[t].w, acc[3]);
-                acc[4] = fmaf(w, v[t].x, acc[4]);
-                acc[5] = fmaf(w, v[t].y, acc[5]);
-                acc[6] = fmaf(w, v[t].z, acc[6]);
-                acc[7] = fmaf(w, v[t].w, acc[7]);
-              }
+              for (int t = 0; t < 4; ++t)
+                if (q0 + t < ds) acc[c] = fmaf(sm.cval[c][q0 + t], v[c][t], acc[c]);
             }
           }
-          for (; q < ds; ++q) add(sm.coff[c][q], sm.cval[c][q]);
-          for (int64_t f = sm.cf0[c] + SCN; f < sm.cf0[c] + deg; ++f)
-            add(int64_t(__ldg(a.Lc.col + f)) * a.ldzt, __ldg(a.Lc.val + f));
+#pragma unroll
+          for (int c = 0; c < SW; ++c)  // entries beyond the staged ones (hub columns)
+            for (int64_t f = sm.cf0[c] + SCN; f < sm.cf0[c] + sm.cdeg[c]; ++f) {
+              const int l = __ldg(a.Lc.col + f);
+              acc[c] = fmaf(__ldg(a.Lc.val + f), __ldg(a.ZTin + int64_t(a.inv ? a.inv[l] : l) * a.ldzt + i), acc[c]);
+            }
         }
-        *reinterpret_cast<float4*>(&sm.ac[c][rl]) = make_float4(acc[0], acc[1], acc[2], acc[3]);
-        *reinterpret_cast<float4*>(&sm.ac[c][rl + 4]) = make_float4(acc[4], acc[5], acc[6], acc[7]);
+#pragma unroll
+        for (int c = 0; c < SW; ++c) sm.ac[c][rl] = acc[c];
       }
       __syncthreads();
       // ---- (Lr Z) from the stripe, prox, momentum: 8 lanes per row, two
@@ -248,7 +238,6 @@ __global__ void __launch_bounds__(STHREADS, 1) fista_stripe_kernel(const __grid_
           for (int h = 0; h < 2; ++h) {
             const int rl = h ? rB : rA, i = h ? iB : iA;
             if (h && !vB) break;
-            float zn = 0.f;
             if (jin) {
               const float z = zs[size_t(i) * SW + c];
               const float y = h ? yB : yA, sp = h ? spB : spA, acc = h ? accB : accA;
@@ -256,32 +245,19 @@ __global__ void __launch_bounds__(STHREADS, 1) fista_stripe_kernel(const __grid_
               const float v = fmaf(-lam, gr, z);
               const float dl = v - y;
               const float sv = y + copysignf(fmaxf(fabsf(dl) - lam, 0.f), dl);
-              zn = fmaf(a.mu, sv - sp, sv);
+              const float zn = fmaf(a.mu, sv - sp, sv);
               if (a.prev_out && a.j == a.J) a.prev_out[int64_t(i) * a.lds + j] = sp;
               a.S[int64_t(i) * a.lds + j] = sv;
               a.Zout[int64_t(i) * a.ldz + j] = zn;
+              // Z_{j+1}^T: the four row groups of a warp fill 16 consecutive
+              // bytes of each of the stripe's rows of Z^T
+              a.ZTout[int64_t(j) * a.ldzt + i] = zn;
               if (a.want_stats) {
                 const double d = double(zn) - double(z);
                 dz += d * d;
                 nz += double(z) * double(z);
               }
             }
-            sm.zn[c][rl] = zn;
-          }
-        }
-      }
-      __syncthreads();
-      // ---- Z_{j+1}^T: the chunk's rows of each stripe column, whole vectors
-      {
-        const int c = warp & (SW - 1), h = warp >> 3, j = c0 + c;
-        const int rl = h * 256 + lane * 8, i = r0 + rl;
-        if (j < a.rc && i < a.rr) {
-          float* p = a.ZTout + int64_t(j) * a.ldzt + i;
-          if (i + 8 <= a.rr) {
-            *reinterpret_cast<float4*>(p) = *reinterpret_cast<const float4*>(&sm.zn[c][rl]);
-            *reinterpret_cast<float4*>(p + 4) = *reinterpret_cast<const float4*>(&sm.zn[c][rl + 4]);
-          } else {
-            for (int t = 0; i + t < a.rr; ++t) p[t] = sm.zn[c][rl + t];
           }
         }
       }
@@ -324,6 +300,63 @@ __global__ void __launch_bounds__(STHREADS, 1) fista_stripe_kernel(const __grid_
   if (a.j == a.J && blockIdx.x == 0 && tid == 0) a.done[1] = a.J;
 }
 
+// Z_1 = S_0 = Y~ (cold start) or Z_{j0+1} = S_{j0} + mu_{j0} (S_{j0} -
+// S_{j0-1}) (warm start, S holding S_{j0}), written row-major and as Z^T;
+// the padding columns of Z and rows of Z^T (both buffers) are zeroed.
+__global__ void __launch_bounds__(256)
+stripe_init_kernel(const float* __restrict__ Yt, int64_t ldy, float* __restrict__ S, int64_t lds,
+                   const float* __restrict__ warm_prev, float mu0, int rr, int rc, float* __restrict__ Z0,
+                   float* __restrict__ Z1, float* __restrict__ ZT0, float* __restrict__ ZT1, int64_t ldz,
+                   int64_t ldzt) {
+  __shared__ float tile[32][33];
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8
+  const int nti = int((ldzt + 31) / 32), ntc = int((ldz + 31) / 32);
+  for (int64_t t = blockIdx.x; t < int64_t(nti) * ntc; t += gridDim.x) {
+    const int i0 = int(t / ntc) * 32, j0 = int(t % ntc) * 32;
+    for (int r = ty; r < 32; r += 8) {
+      const int i = i0 + r, j = j0 + tx;
+      float z = 0.f;
+      if (i < rr && j < rc) {
+        if (warm_prev) {
+          const float sv = S[int64_t(i) * lds + j], sp = warm_prev[int64_t(i) * lds + j];
+          z = fmaf(mu0, sv - sp, sv);
+        } else {
+          z = Yt[int64_t(i) * ldy + j];
+          S[int64_t(i) * lds + j] = z;
+        }
+      }
+      if (i < rr && j < ldz) {
+        Z0[int64_t(i) * ldz + j] = z;
+        Z1[int64_t(i) * ldz + j] = 0.f;
+      }
+      tile[r][tx] = z;
+    }
+    __syncthreads();
+    for (int c = ty; c < 32; c += 8) {
+      const int j = j0 + c, i = i0 + tx;
+      if (j < rc && i < ldzt) {
+        ZT0[int64_t(j) * ldzt + i] = tile[tx][c];
+        ZT1[int64_t(j) * ldzt + i] = 0.f;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// B(:, q) = A(:, perm[q]) (forward) or B(:, perm[q]) = A(:, q) (backward),
+// `rows` rows of `cols` columns.
+__global__ void permute_cols_kernel(const float* __restrict__ A, int64_t lda, float* __restrict__ B, int64_t ldb,
+                                    const int32_t* __restrict__ perm, int rows, int cols, int backward) {
+  for (int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; t < int64_t(rows) * cols;
+       t += int64_t(gridDim.x) * blockDim.x) {
+    const int i = int(t / cols), q = int(t % cols);
+    if (backward)
+      B[int64_t(i) * ldb + perm[q]] = A[int64_t(i) * lda + q];
+    else
+      B[int64_t(i) * ldb + q] = A[int64_t(i) * lda + perm[q]];
+  }
+}
+
 size_t stripe_smem(int rr_pad) {
   return ((sizeof(StripeSmem) + 127) & ~size_t(127)) + size_t(2) * rr_pad * SW * sizeof(float) +
          size_t(rr_pad + 1) * sizeof(int32_t);
@@ -346,18 +379,64 @@ bool make_zmap(CUtensorMap* map, const float* Z, int rr, int64_t ldz) {
 bool stripe_eligible(int rr, int rc) {
   if (rr < SBOX || rc < 4 * SW) return false;
   const int rr_pad = int(ceil_div(rr, SBOX)) * SBOX;
+  // (Lr has at most rr^2 < 2^31 entries: 32-bit row offsets)
   return stripe_smem(rr_pad) <= size_t(max_smem_optin()) && int64_t(rc) * ((rr + 3) / 4 * 4) < (int64_t(1) << 31) &&
-         encode_fn() != nullptr;  // (Lr has at most rr^2 < 2^31 entries: 32-bit row offsets)
+         encode_fn() != nullptr;
 }
 
-cpca_status fista_stripe_run(const BatchProblem& P, const InstWs& iw, int J, double eps, bool want_last,
-                             double t0, int* err, cudaStream_t st) {
+bool stripe_reorders(int rr, int rc) {
+  return rr >= SBOX && rc >= 4 * SW && int64_t(rr) * rc >= (int64_t(1) << 22) && order_supported(rc);
+}
+
+StripeWs stripe_layout(Carve& c, int rr, int rc) {
+  StripeWs w{};
+  if (!stripe_reorders(rr, rc)) return w;
+  const size_t ldz = size_t(rc + 3) / 4 * 4;
+  w.Yp = c.take<float>(size_t(rr) * ldz);
+  w.Sp = c.take<float>(size_t(rr) * ldz);
+  w.Pp = c.take<float>(size_t(rr) * ldz);
+  w.perm = c.take<int32_t>(rc);
+  w.inv = c.take<int32_t>(rc);
+  w.oscr = c.take<unsigned char>(order_scratch_bytes(rc));
+  w.bar = c.take<unsigned int>(kBarrierCounters + 1);
+  return w;
+}
+
+cpca_status fista_stripe_run(const BatchProblem& P, const InstWs& iw, const StripeWs& sw, int J, double eps,
+                             bool want_last, double t0, float mu0, int* err, cudaStream_t st) {
   const int rr = P.rr, rc = P.rc;
   const int rr_pad = int(ceil_div(rr, SBOX)) * SBOX;
   const int64_t ldz = (rc + 3) / 4 * 4, ldzt = (rr + 3) / 4 * 4;
   CUtensorMap maps[2];
   CPCA_CHECK_ARG(make_zmap(&maps[0], iw.Z0, rr, ldz) && make_zmap(&maps[1], iw.Z1, rr, ldz),
                  "frpcag: tensor map for the striped FISTA launch could not be encoded");
+  // locality order of the columns (large problems with the ordering scratch)
+  const bool reorder = sw.Yp != nullptr;
+  const float* Y = P.Yt;
+  float* S = P.X;
+  int64_t ldy = P.ldy, lds = P.ldx;
+  const float* warm = P.j0 > 0 ? P.warm_prev : nullptr;
+  float* prev = P.prev_out;
+  const unsigned pg = std::min<unsigned>(ceil_div(int64_t(rr) * rc, 256), num_sms() * 8);
+  if (reorder) {
+    CPCA_TRY(graph_order(P.Lc, sw.perm, sw.inv, sw.oscr, sw.bar, err, st));
+    permute_cols_kernel<<<pg, 256, 0, st>>>(P.Yt, P.ldy, sw.Yp, ldz, sw.perm, rr, rc, 0);
+    CPCA_LAUNCHED();
+    if (warm) {
+      permute_cols_kernel<<<pg, 256, 0, st>>>(P.X, P.ldx, sw.Sp, ldz, sw.perm, rr, rc, 0);
+      CPCA_LAUNCHED();
+      permute_cols_kernel<<<pg, 256, 0, st>>>(warm, P.ldx, sw.Pp, ldz, sw.perm, rr, rc, 0);
+      CPCA_LAUNCHED();
+      warm = sw.Pp;
+    }
+    Y = sw.Yp;
+    S = sw.Sp;
+    ldy = lds = ldz;
+    if (prev) prev = sw.Pp;
+  }
+  stripe_init_kernel<<<std::min<unsigned>(ceil_div(int64_t(rr) * ldz, 1024), num_sms() * 8), 256, 0, st>>>(
+      Y, ldy, S, lds, warm, mu0, rr, rc, iw.Z0, iw.Z1, iw.ZT0, iw.ZT1, ldz, ldzt);
+  CPCA_LAUNCHED();
   const size_t smem = stripe_smem(rr_pad);
   static PerDeviceOnce attr;
   CPCA_CUDA(once_per_device(attr, [&] {
@@ -365,16 +444,19 @@ cpca_status fista_stripe_run(const BatchProblem& P, const InstWs& iw, int J, dou
                                 int(max_smem_optin()));
   }));
   StripeArgs a{};
-  a.Yt = P.Yt;
-  a.S = P.X;
+  a.Yt = Y;
+  a.S = S;
   a.Lr = P.Lr;
   a.Lc = P.Lc;
+  a.perm = reorder ? sw.perm : nullptr;
+  a.inv = reorder ? sw.inv : nullptr;
   a.lam = iw.scal + 2;
   a.stats = iw.stats;
   a.done = iw.done;
   a.err = err;
-  a.ldy = P.ldy;
-  a.lds = P.ldx;
+  a.prev_out = prev;
+  a.ldy = ldy;
+  a.lds = lds;
   a.ldz = ldz;
   a.ldzt = ldzt;
   a.two_gr = float(2.0 * P.gamma_r);
@@ -385,7 +467,6 @@ cpca_status fista_stripe_run(const BatchProblem& P, const InstWs& iw, int J, dou
   a.nstripes = int(ceil_div(rc, SW));
   a.J = J;
   a.eps = eps;
-  a.prev_out = P.prev_out;
   const int grid = std::min(a.nstripes, num_sms());
   float* Z[2] = {iw.Z0, iw.Z1};
   float* ZT[2] = {iw.ZT0, iw.ZT1};
@@ -411,6 +492,14 @@ cpca_status fista_stripe_run(const BatchProblem& P, const InstWs& iw, int J, dou
     }
   }
   prof_end();
+  if (reorder) {
+    permute_cols_kernel<<<pg, 256, 0, st>>>(sw.Sp, ldz, P.X, P.ldx, sw.perm, rr, rc, 1);
+    CPCA_LAUNCHED();
+    if (P.prev_out) {
+      permute_cols_kernel<<<pg, 256, 0, st>>>(sw.Pp, ldz, P.prev_out, P.ldx, sw.perm, rr, rc, 1);
+      CPCA_LAUNCHED();
+    }
+  }
   return CPCA_OK;
 }
 

@@ -403,16 +403,18 @@ knn_recheck_kernel(const float* __restrict__ P, int N, int d, int64_t ld, bool v
     if (si[c] <= -2) si[c] = -2 - si[c];
   __syncwarp();
   float window = aK + 2.f * e;
-  // When the error bound reaches past the end of a full candidate list the
-  // certificate cannot hold: the query is searched by brute force within
-  // the budget, else left uncertified. Its exact re-scoring is then kept to
-  // the 2K best ranking values (the ranking error in practice is far below
-  // the gaps that separate them from the K-th).
-  float thr_min = INF;
-  for (int s = 0; s < splits; ++s)
-    if (cand_i[(int64_t(s) * N + q) * M + (M - 1)] >= 0)
-      thr_min = fminf(thr_min, cand_d[(int64_t(s) * N + q) * M + (M - 1)]);
-  const bool hopeless = thr_min - e <= aK;
+  // When the error window holds more candidates than R, the query is not
+  // certified: it is searched by brute force within the budget, else left
+  // uncertified, and its exact re-scoring is kept to the 2K best ranking
+  // values (the ranking error in practice is far below the gaps that
+  // separate them from the K-th).
+  // count the window; beyond R = max(32, 2K) candidates the certificate is
+  // not attempted (the query goes to the brute-force budget)
+  int inwin = 0;
+  for (int c = lane; c < C; c += 32) inwin += (si[c] >= 0 && sa[c] <= window) ? 1 : 0;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) inwin += __shfl_xor_sync(0xffffffffu, inwin, o);
+  const bool hopeless = inwin > max(32, 2 * K);
   if (hopeless) window = fminf(window, a2K);
   for (int c = 0; c < C; ++c) {
     const int j = si[c];
@@ -710,13 +712,25 @@ struct KnnWs {
   size_t bytes;
 };
 
-// Base-range splits: enough blocks to fill the GPU.
+// Base-range splits S (each query keeps M candidates per split): the S in
+// {1, 2, 4, 8} whose blocks fill the GPU in the fewest waves per unit of
+// work, ceil(tiles S / SMs) / S, with 128-query tiles in pairs (the
+// tensor-core pass's clusters) and at least 4 base tiles of 256 per split.
 static int knn_splits(int N, int d) {
   (void)d;
-  const int qt = (N + BQ - 1) / BQ;
-  int s = 1;
-  while (s < 8 && qt * s < 2 * num_sms() && (N + BB - 1) / BB >= 4 * s * 2) s *= 2;
-  return s;
+  const int qt = (int(ceil_div(N, 128)) + 1) / 2 * 2;
+  const int P = num_sms();
+  int best = 1;
+  double cost = 1e300;
+  for (int s = 1; s <= 8; s *= 2) {
+    if (s > 1 && (N + 255) / 256 < 4 * s) break;
+    const double c = double(ceil_div(int64_t(qt) * s, P)) / s;
+    if (c < cost - 1e-9) {
+      cost = c;
+      best = s;
+    }
+  }
+  return best;
 }
 
 // Brute-force budget of one graph: a query costs N d FMAs; at most

@@ -156,15 +156,17 @@ def test_fista_converged_objective(M):
     assert abs(info.objective - Fo) / Fo < OBJ_TOL
 
 
-@pytest.mark.parametrize("eps,J", [(0.0, 150), (1e-7, 3000)])
-def test_fista_striped_launch_equals_cooperative(M, eps, J):
+@pytest.mark.parametrize("shape,eps,J", [((301, 3003), 0.0, 150), ((301, 3003), 1e-7, 3000),
+                                         ((300, 14003), 0.0, 60)])
+def test_fista_striped_launch_equals_cooperative(M, shape, eps, J):
     """A problem too large for the resident launch (301 x 3003: ragged row
-    boxes, a ragged last stripe and padded leading dimensions) takes the
-    striped per-iteration launch by default; forcing a launch width takes
-    the cooperative streaming kernel. Same arithmetic in the same order:
-    the same iterates bit for bit (and, with the stopping rule, the same
-    stop up to the FP64 order of the statistics)."""
-    Y, _, _ = gen.make_instance(31, 301, 3003, 6, 5, 0.05)
+    boxes, a ragged last stripe and padded leading dimensions; 300 x 14003,
+    large enough to be processed in the column graph's locality order)
+    takes the striped per-iteration launch by default; forcing a launch
+    width takes the cooperative streaming kernel. Same arithmetic in the
+    same order: the same iterates bit for bit (and, with the stopping rule,
+    the same stop up to the FP64 order of the statistics)."""
+    Y, _, _ = gen.make_instance(31, shape[0], shape[1], 6, 5 if shape[1] < 10000 else 40, 0.05)
     Lr = _graph_c(Y, 8)
     Lc = _graph_c(np.ascontiguousarray(Y.T), 8)
     Yd, Lrd, Lcd = _dev(Y), M.Csr.from_scipy(Lr), M.Csr.from_scipy(Lc)
@@ -323,14 +325,15 @@ def test_pipeline_c0_end_to_end(M):
 
 
 # ---------------------------------------------------------- warm start
-@pytest.mark.parametrize("case", ["resident", "striped", "beyond_mu_table"])
+@pytest.mark.parametrize("case", ["resident", "striped", "striped_reordered", "beyond_mu_table"])
 def test_fista_warm_start_resumes_bit_for_bit(M, case):
     """Checkpoint and resume of Algorithm 1: J1 iterations (exporting
     S_{J1-1}) followed by J2 resumed iterations equal one run of J1 + J2,
     bit for bit, in the resident launch, the striped launch, and across the
     end of the momentum table (t_j continued on the host)."""
-    if case == "striped":
-        Y, _, _ = gen.make_instance(32, 301, 3003, 6, 5, 0.05)
+    if case in ("striped", "striped_reordered"):
+        shape = (301, 3003) if case == "striped" else (300, 14003)
+        Y, _, _ = gen.make_instance(32, shape[0], shape[1], 6, 40, 0.05)
         Lr, Lc = _graph_c(Y, 8), _graph_c(np.ascontiguousarray(Y.T), 8)
         Yt = Y.astype(np.float64)
         J1, J2 = 40, 35

@@ -32,79 +32,115 @@ __global__ void omega_kernel(float* __restrict__ W, int rows, int b, uint64_t se
     W[t] = float(uniform01_at(s0, uint64_t(t) + 1) - 0.5);
 }
 
-// C (m x b) = A (m x n, lda) B (n x b); 8 rows of C per block.
+// C (m x b) = A (m x n, lda) B (n x b, ld b). A block takes 8 ROWS rows of
+// A (a warp per ROWS rows), the lanes across the rows (coalesced); B comes
+// through shared memory in chunks of CHUNK rows (row stride b | 1, odd: the
+// lanes' rows fall on distinct banks), each B value serving the warp's
+// rows; every lane keeps partial sums of the b outputs of its rows, reduced
+// over the warp at the end. A is read once.
+template <int BB, int ROWS, int CHUNK>
 __global__ void __launch_bounds__(256)
-gemm_nn_tall(const float* __restrict__ A, int64_t lda, int m, int n, const float* __restrict__ B,
-             int b, float* __restrict__ C) {
-  __shared__ float As[8][64];
-  __shared__ float Bs[64][BMAX];
-  const int tid = threadIdx.x, c = tid & 63, rg = tid >> 6;
-  const int r0 = blockIdx.x * 8;
-  float acc0 = 0.f, acc1 = 0.f;
-  for (int k0 = 0; k0 < n; k0 += 64) {
-    for (int e = tid; e < 8 * 64; e += 256) {
-      const int r = e >> 6, k = e & 63;
-      As[r][k] = (r0 + r < m && k0 + k < n) ? A[int64_t(r0 + r) * lda + k0 + k] : 0.f;
-    }
-    for (int e = tid; e < 64 * b; e += 256) {
-      const int k = e / b, cc = e % b;
-      Bs[k][cc] = (k0 + k < n) ? B[int64_t(k0 + k) * b + cc] : 0.f;
+gemm_nn_tall_k(const float* __restrict__ A, int64_t lda, int m, int n, const float* __restrict__ B, int b,
+               float* __restrict__ C) {
+  __shared__ float Bs[CHUNK * (BB + 1)];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int bs = b | 1;
+  const int i0 = (blockIdx.x * 8 + warp) * ROWS;
+  float acc[ROWS][BB];
+#pragma unroll
+  for (int r = 0; r < ROWS; ++r)
+#pragma unroll
+    for (int c = 0; c < BB; ++c) acc[r][c] = 0.f;
+  for (int k0 = 0; k0 < n; k0 += CHUNK) {
+    const int kn = min(CHUNK, n - k0);
+    __syncthreads();
+    for (int e = threadIdx.x; e < kn * b; e += 256) {
+      const int k = e / b, c = e % b;
+      Bs[k * bs + c] = B[int64_t(k0 + k) * b + c];
     }
     __syncthreads();
-    if (c < b) {
-#pragma unroll 8
-      for (int k = 0; k < 64; ++k) {
-        const float bv = Bs[k][c];
-        acc0 = fmaf(As[rg * 2][k], bv, acc0);
-        acc1 = fmaf(As[rg * 2 + 1][k], bv, acc1);
+    for (int k = lane; k < kn; k += 32) {
+      float av[ROWS];
+#pragma unroll
+      for (int r = 0; r < ROWS; ++r) av[r] = i0 + r < m ? __ldg(A + int64_t(i0 + r) * lda + k0 + k) : 0.f;
+      const float* bk = Bs + k * bs;
+#pragma unroll
+      for (int c = 0; c < BB; ++c) {
+        if (c < b) {
+          const float bv = bk[c];
+#pragma unroll
+          for (int r = 0; r < ROWS; ++r) acc[r][c] = fmaf(av[r], bv, acc[r][c]);
+        }
       }
     }
-    __syncthreads();
   }
-  if (c < b) {
-    if (r0 + rg * 2 < m) C[int64_t(r0 + rg * 2) * b + c] = acc0;
-    if (r0 + rg * 2 + 1 < m) C[int64_t(r0 + rg * 2 + 1) * b + c] = acc1;
-  }
+#pragma unroll
+  for (int r = 0; r < ROWS; ++r)
+#pragma unroll
+    for (int c = 0; c < BB; ++c) {
+      if (c >= b) continue;
+      const float v = warp_sumf(acc[r][c]);
+      if (lane == 0 && i0 + r < m) C[int64_t(i0 + r) * b + c] = v;
+    }
 }
 
-// C (n x b) = A^T B with A (m x n, lda), B (m x b); 8 rows of C per block.
-// With gridDim.y > 1 the rows of A are split into gridDim.y chunks (of
-// `chunk` rows, a multiple of 64) and block (x, y) writes its partial
-// product to C + y * n * b; gemm_tn_reduce adds the chunks in order.
+static void gemm_nn_tall_launch(const float* A, int64_t lda, int m, int n, const float* B, int b, float* C,
+                                cudaStream_t st) {
+  if (b <= 16)
+    gemm_nn_tall_k<16, 4, 256><<<ceil_div(m, 32), 256, 0, st>>>(A, lda, m, n, B, b, C);
+  else if (b <= 32)
+    gemm_nn_tall_k<32, 4, 256><<<ceil_div(m, 32), 256, 0, st>>>(A, lda, m, n, B, b, C);
+  else
+    gemm_nn_tall_k<BMAX, 2, 128><<<ceil_div(m, 16), 256, 0, st>>>(A, lda, m, n, B, b, C);
+}
+
+// C (n x b) = A^T B with A (m x n, lda), B (m x b, ld b): a thread per
+// column of A (the block's 256 columns read as whole row segments), B's rows
+// staged in shared memory 64 at a time and read as broadcasts, each thread's
+// b sums written as its row of C. With gridDim.y > 1 the rows of A are split
+// into chunks of `chunk` rows (a multiple of 64) and block (x, y) writes its
+// partial product to C + y * n * b; gemm_tn_reduce adds the chunks in order.
+template <int BB>
 __global__ void __launch_bounds__(256)
-gemm_tn_tall(const float* __restrict__ A, int64_t lda, int m, int n, const float* __restrict__ B,
-             int b, float* __restrict__ C, int chunk) {
-  __shared__ float As[64][8];
-  __shared__ float Bs[64][BMAX];
-  const int tid = threadIdx.x, c = tid & 63, rg = tid >> 6;
-  const int j0 = blockIdx.x * 8;
+gemm_tn_tall_k(const float* __restrict__ A, int64_t lda, int m, int n, const float* __restrict__ B, int b,
+               float* __restrict__ C, int chunk) {
+  __shared__ float Bs[64][BB];
+  const int j = blockIdx.x * 256 + threadIdx.x;
   const int ibeg = blockIdx.y * chunk, iend = min(m, ibeg + chunk);
   C += int64_t(blockIdx.y) * n * b;
-  float acc0 = 0.f, acc1 = 0.f;
+  float acc[BB];
+#pragma unroll
+  for (int c = 0; c < BB; ++c) acc[c] = 0.f;
   for (int i0 = ibeg; i0 < iend; i0 += 64) {
-    for (int e = tid; e < 64 * 8; e += 256) {
-      const int i = e >> 3, jj = e & 7;
-      As[i][jj] = (i0 + i < iend && j0 + jj < n) ? A[int64_t(i0 + i) * lda + j0 + jj] : 0.f;
-    }
-    for (int e = tid; e < 64 * b; e += 256) {
-      const int i = e / b, cc = e % b;
-      Bs[i][cc] = (i0 + i < iend) ? B[int64_t(i0 + i) * b + cc] : 0.f;
+    const int rn = min(64, iend - i0);
+    __syncthreads();
+    for (int e = threadIdx.x; e < 64 * BB; e += 256) {
+      const int r = e / BB, c = e % BB;
+      Bs[r][c] = (r < rn && c < b) ? B[int64_t(i0 + r) * b + c] : 0.f;
     }
     __syncthreads();
-    if (c < b) {
-#pragma unroll 8
-      for (int i = 0; i < 64; ++i) {
-        const float bv = Bs[i][c];
-        acc0 = fmaf(As[i][rg * 2], bv, acc0);
-        acc1 = fmaf(As[i][rg * 2 + 1], bv, acc1);
+    if (j < n) {
+      for (int r = 0; r < rn; ++r) {
+        const float a = __ldg(A + int64_t(i0 + r) * lda + j);
+#pragma unroll
+        for (int c = 0; c < BB; ++c) acc[c] = fmaf(a, Bs[r][c], acc[c]);
       }
     }
-    __syncthreads();
   }
-  if (c < b) {
-    if (j0 + rg * 2 < n) C[int64_t(j0 + rg * 2) * b + c] = acc0;
-    if (j0 + rg * 2 + 1 < n) C[int64_t(j0 + rg * 2 + 1) * b + c] = acc1;
-  }
+  if (j < n)
+#pragma unroll
+    for (int c = 0; c < BB; ++c)
+      if (c < b) C[int64_t(j) * b + c] = acc[c];
+}
+
+static void gemm_tn_tall_launch(dim3 g, const float* A, int64_t lda, int m, int n, const float* B, int b, float* C,
+                                int chunk, cudaStream_t st) {
+  if (b <= 16)
+    gemm_tn_tall_k<16><<<g, 256, 0, st>>>(A, lda, m, n, B, b, C, chunk);
+  else if (b <= 32)
+    gemm_tn_tall_k<32><<<g, 256, 0, st>>>(A, lda, m, n, B, b, C, chunk);
+  else
+    gemm_tn_tall_k<BMAX><<<g, 256, 0, st>>>(A, lda, m, n, B, b, C, chunk);
 }
 
 // C = sum over the chunks of P (nchunk x total floats), in chunk order.
@@ -123,15 +159,17 @@ constexpr int kTnChunks = 16;  // row chunks of the split X~^T B products
 // kTnChunks * n * b floats).
 static cpca_status tn_tall(const float* A, int64_t lda, int m, int n, const float* B, int b, float* C,
                            float* scratch, cudaStream_t st) {
-  const int chunks = std::max(1, std::min(kTnChunks, int(ceil_div(m, 256))));
+  // enough row chunks to give the GPU about two blocks per SM
+  const int cblocks = int(ceil_div(n, 256));
+  const int chunks = std::max(1, std::min({kTnChunks, int(ceil_div(m, 64)), int(ceil_div(2 * num_sms(), cblocks))}));
   if (chunks == 1) {
-    gemm_tn_tall<<<dim3(ceil_div(n, 8), 1), 256, 0, st>>>(A, lda, m, n, B, b, C, m);
+    gemm_tn_tall_launch(dim3(cblocks, 1), A, lda, m, n, B, b, C, m, st);
     CPCA_LAUNCHED();
     return CPCA_OK;
   }
   const int chunk = int(ceil_div(ceil_div(m, chunks), 64)) * 64;
   const int nch = int(ceil_div(m, chunk));
-  gemm_tn_tall<<<dim3(ceil_div(n, 8), nch), 256, 0, st>>>(A, lda, m, n, B, b, scratch, chunk);
+  gemm_tn_tall_launch(dim3(cblocks, nch), A, lda, m, n, B, b, scratch, chunk, st);
   count_launch();
   const int64_t total = int64_t(n) * b;
   gemm_tn_reduce<<<std::min<unsigned>(ceil_div(total, 256), num_sms() * 4), 256, 0, st>>>(scratch, nch,
@@ -998,7 +1036,7 @@ static cpca_status partial_svd(const float* Xt, int rr, int rc, int64_t ldxt, in
   auto to_long = [&](const float* in, float* out) -> cpca_status {
     CPCA_PROF("svd_gemm", st);
     if (vspace) {
-      gemm_nn_tall<<<ceil_div(rr, 8), 256, 0, st>>>(Xt, ldxt, rr, rc, in, b, out);
+      gemm_nn_tall_launch(Xt, ldxt, rr, rc, in, b, out, st);
       CPCA_LAUNCHED();
     } else {
       CPCA_TRY(tn_tall(Xt, ldxt, rr, rc, in, b, out, w.tn, st));
@@ -1010,7 +1048,7 @@ static cpca_status partial_svd(const float* Xt, int rr, int rc, int64_t ldxt, in
     if (vspace) {
       CPCA_TRY(tn_tall(Xt, ldxt, rr, rc, in, b, out, w.tn, st));
     } else {
-      gemm_nn_tall<<<ceil_div(rr, 8), 256, 0, st>>>(Xt, ldxt, rr, rc, in, b, out);
+      gemm_nn_tall_launch(Xt, ldxt, rr, rc, in, b, out, st);
       CPCA_LAUNCHED();
     }
     return CPCA_OK;
@@ -1979,13 +2017,13 @@ extern "C" cpca_status cpca_decode_backward(const float* Xt, int32_t rr, int32_t
   const float* VAb = vspace ? v.Vtb : v.Utb;
   auto applyA = [&](const float* in, float* out) -> cpca_status {  // out (mA x k) = A in (nA x k)
     if (!vspace) return tn_tall(Xt, ldxt, rr, rc, in, k, out, w.tn, st);
-    gemm_nn_tall<<<ceil_div(rr, 8), 256, 0, st>>>(Xt, ldxt, rr, rc, in, k, out);
+    gemm_nn_tall_launch(Xt, ldxt, rr, rc, in, k, out, st);
     CPCA_LAUNCHED();
     return CPCA_OK;
   };
   auto applyAT = [&](const float* in, float* out) -> cpca_status {  // out (nA x k) = A^T in (mA x k)
     if (vspace) return tn_tall(Xt, ldxt, rr, rc, in, k, out, w.tn, st);
-    gemm_nn_tall<<<ceil_div(rr, 8), 256, 0, st>>>(Xt, ldxt, rr, rc, in, k, out);
+    gemm_nn_tall_launch(Xt, ldxt, rr, rc, in, k, out, st);
     CPCA_LAUNCHED();
     return CPCA_OK;
   };
@@ -2097,7 +2135,7 @@ extern "C" cpca_status cpca_subspace_project(int32_t side, const float* basis, i
     CPCA_TRY(launch_output(basis, ldb, W, ldb, ones, k, p, n, X, ldx, st));
   } else {
     CPCA_PROF("project_small", st);
-    gemm_nn_tall<<<ceil_div(p, 8), 256, 0, st>>>(Y, ldy, p, n, basis, ldb, W);  // W = Y V (p x ldb)
+    gemm_nn_tall_launch(Y, ldy, p, n, basis, ldb, W, st);  // W = Y V (p x ldb)
     CPCA_LAUNCHED();
     CPCA_PROF("project_output", st);
     CPCA_TRY(launch_output(W, ldb, basis, ldb, ones, k, p, n, X, ldx, st));

@@ -2,14 +2,14 @@
 // problems too large for the resident launch, one launch per iteration.
 //
 // The matrix is cut into stripes of SW = 8 columns spanning every row. A
-// block takes stripes in turn; for each it brings the whole stripe of Z_j
-// into shared memory with TMA (boxes of 8 columns x 256 rows, double-
-// buffered: the next stripe's load runs while the current one computes).
-// Then, in chunks of 512 rows:
-//   (Z Lc)(i, j) = sum_l Lc[j, l] Z^T(l, i): each warp takes 32 rows (a
-//       lane per row) and all 8 stripe columns, reading the neighbour
-//       columns' rows of Z^T through L1 as coalesced 128-byte segments (the
-//       whole Z^T of the iteration is read-only inside the launch);
+// block (two per SM, so that one computes while the other waits for its
+// stripe) takes stripes in turn; for each it brings the whole stripe of Z_j
+// into shared memory with TMA (boxes of 8 columns x 256 rows). Then, in
+// chunks of 256 rows:
+//   (Z Lc)(i, j) = sum_l Lc[j, l] Z^T(l, i): a warp per stripe column, each
+//       lane 8 consecutive rows, the neighbour columns' rows of Z^T read
+//       through L1 as 32-byte vectors, eight neighbours in flight (the whole
+//       Z^T of the iteration is read-only inside the launch);
 //   (Lr Z)(i, j) = sum_k Lr[i, k] Z(k, j): entirely from the stripe in
 //       shared memory (a row graph links arbitrary rows, and the stripe holds
 //       all of them), 8 lanes per row, two rows per lane group at a time;
@@ -41,8 +41,9 @@ namespace {
 
 constexpr int SW = 8;          // stripe width (columns)
 constexpr int SBOX = 256;      // rows per TMA box
-constexpr int SCHUNK = 512;    // rows per chunk
-constexpr int STHREADS = 512;  // 16 warps
+constexpr int SCHUNK = 256;    // rows per chunk
+constexpr int STHREADS = 256;  // 8 warps: a warp per stripe column in the column product
+constexpr int SBLOCKS = 2;     // blocks per SM (one stripe buffer each)
 constexpr int SCN = 64;        // staged neighbour entries per stripe column
 
 struct StripeArgs {
@@ -74,16 +75,18 @@ struct StripeSmem {
   float cval[SW][SCN];
   int64_t cf0[SW];
   int cdeg[SW];
-  uint64_t mbar[2];
+  uint64_t mbar[1];
   double red[2][STHREADS / 32];
   int abort;
 };
 
-__global__ void __launch_bounds__(STHREADS, 1) fista_stripe_kernel(const __grid_constant__ StripeArgs a) {
+__device__ __forceinline__ float4 ldg4(const float* p) { return __ldg(reinterpret_cast<const float4*>(p)); }
+
+__global__ void __launch_bounds__(STHREADS, SBLOCKS) fista_stripe_kernel(const __grid_constant__ StripeArgs a) {
   extern __shared__ __align__(128) unsigned char smraw[];
   StripeSmem& sm = *reinterpret_cast<StripeSmem*>(smraw);
   float* zs0 = reinterpret_cast<float*>(smraw + ((sizeof(StripeSmem) + 127) & ~size_t(127)));
-  int32_t* rowp = reinterpret_cast<int32_t*>(zs0 + size_t(2) * a.rr_pad * SW);  // [rr + 1], from rowptr[0]
+  int32_t* rowp = reinterpret_cast<int32_t*>(zs0 + size_t(a.rr_pad) * SW);  // [rr + 1], from rowptr[0]
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   if (__ldcg(a.done)) return;  // stopped at an earlier iteration
   if (a.eps > 0 && a.j > 1) {
@@ -104,27 +107,21 @@ __global__ void __launch_bounds__(STHREADS, 1) fista_stripe_kernel(const __grid_
   if (tid == 0) {
     sm.abort = 0;
     mbar_init(&sm.mbar[0], 1);
-    mbar_init(&sm.mbar[1], 1);
     mbar_fence_init();
   }
   // row pointers of Lr relative to its first entry, for every stripe
   const int64_t rbase = a.Lr.rowptr[0];
   for (int i = tid; i <= a.rr; i += STHREADS) rowp[i] = int32_t(a.Lr.rowptr[i] - rbase);
   __syncthreads();
-  auto issue = [&](int s, int buf) {  // one thread: the whole stripe s into buffer buf
-    float* dst = zs0 + size_t(buf) * a.rr_pad * SW;
-    mbar_expect_tx(&sm.mbar[buf], stripe_bytes);
-    for (int b = 0; b < nbox; ++b) tma_load_2d(dst + size_t(b) * SBOX * SW, &a.zmap, &sm.mbar[buf], s * SW, b * SBOX);
+  auto issue = [&](int s) {  // one thread: the whole stripe s into the buffer
+    mbar_expect_tx(&sm.mbar[0], stripe_bytes);
+    for (int b = 0; b < nbox; ++b) tma_load_2d(zs0 + size_t(b) * SBOX * SW, &a.zmap, &sm.mbar[0], s * SW, b * SBOX);
   };
-  if (tid == 0) {
-    if (int(blockIdx.x) < a.nstripes) issue(blockIdx.x, 0);
-    if (int(blockIdx.x + gridDim.x) < a.nstripes) issue(blockIdx.x + gridDim.x, 1);
-  }
+  if (tid == 0 && int(blockIdx.x) < a.nstripes) issue(blockIdx.x);
   double dz = 0.0, nz = 0.0;
   int k = 0;
   for (int s = blockIdx.x; s < a.nstripes; s += gridDim.x, ++k) {
-    const int buf = k & 1;
-    const float* zs = zs0 + size_t(buf) * a.rr_pad * SW;
+    const float* zs = zs0;
     const int c0 = s * SW;
     // neighbour lists of the stripe's columns (overlaps the stripe's load)
     if (tid < SW) {
@@ -143,49 +140,68 @@ __global__ void __launch_bounds__(STHREADS, 1) fista_stripe_kernel(const __grid_
         sm.cval[c][q] = __ldg(a.Lc.val + sm.cf0[c] + q);
       }
     }
-    if (tid == 0 && !mbar_wait(&sm.mbar[buf], (k >> 1) & 1, &sm.abort)) atomicExch(a.err, 1);
+    if (tid == 0 && !mbar_wait(&sm.mbar[0], k & 1, &sm.abort)) atomicExch(a.err, 1);
     __syncthreads();
     if (sm.abort) break;
     for (int r0 = 0; r0 < a.rr; r0 += SCHUNK) {
-      // ---- (Z Lc): warp -> 32 rows (a lane per row), all stripe columns,
-      // the columns' neighbour lists walked side by side (32 loads in
-      // flight per lane), each column's sum still in its CSR order
+      // ---- (Z Lc): warp -> stripe column c, lane -> 8 consecutive rows
       {
-        const int rl = warp * 32 + lane, i = r0 + rl;
-        const bool ok = i < a.rr;
-        float acc[SW];
+        const int c = warp, rl = lane * 8, i = r0 + rl;
+        float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        const int deg = sm.cdeg[c];
+        if (i < a.rr) {
+          const bool full = i + 8 <= int(a.ldzt);
+          const int ds = min(deg, SCN);
+          auto add = [&](int64_t off, float w) {
+            const float* p = a.ZTin + off + i;
+            if (full) {
+              const float4 u = ldg4(p), v = ldg4(p + 4);
+              acc[0] = fmaf(w, u.x, acc[0]);
+              acc[1] = fmaf(w, u.y, acc[1]);
+              acc[2] = fmaf(w, u.z, acc[2]);
+              acc[3] = fmaf(w, u.w, acc[3]);
+              acc[4] = fmaf(w, v.x, acc[4]);
+              acc[5] = fmaf(w, v.y, acc[5]);
+              acc[6] = fmaf(w, v.z, acc[6]);
+              acc[7] = fmaf(w, v.w, acc[7]);
+            } else {
 #pragma unroll
-        for (int c = 0; c < SW; ++c) acc[c] = 0.f;
-        if (ok) {
-          int dmax = 0;
-#pragma unroll
-          for (int c = 0; c < SW; ++c) dmax = max(dmax, min(sm.cdeg[c], SCN));
-          for (int q0 = 0; q0 < dmax; q0 += 4) {
-            float v[SW][4];
-#pragma unroll
-            for (int c = 0; c < SW; ++c) {
-              const int ds = min(sm.cdeg[c], SCN);
-#pragma unroll
-              for (int t = 0; t < 4; ++t)
-                v[c][t] = q0 + t < ds ? __ldg(a.ZTin + sm.coff[c][q0 + t] + i) : 0.f;
+              for (int t = 0; t < 8; ++t)
+                if (i + t < a.rr) acc[t] = fmaf(w, __ldg(p + t), acc[t]);
             }
+          };
+          int q = 0;
+          if (full) {
+            for (; q + 8 <= ds; q += 8) {  // eight neighbours' loads in flight
+              float4 u[8], v[8];
 #pragma unroll
-            for (int c = 0; c < SW; ++c) {
-              const int ds = min(sm.cdeg[c], SCN);
+              for (int t = 0; t < 8; ++t) {
+                const float* p = a.ZTin + sm.coff[c][q + t] + i;
+                u[t] = ldg4(p);
+                v[t] = ldg4(p + 4);
+              }
 #pragma unroll
-              for (int t = 0; t < 4; ++t)
-                if (q0 + t < ds) acc[c] = fmaf(sm.cval[c][q0 + t], v[c][t], acc[c]);
+              for (int t = 0; t < 8; ++t) {
+                const float w = sm.cval[c][q + t];
+                acc[0] = fmaf(w, u[t].x, acc[0]);
+                acc[1] = fmaf(w, u[t].y, acc[1]);
+                acc[2] = fmaf(w, u[t].z, acc[2]);
+                acc[3] = fmaf(w, u[t].w, acc[3]);
+                acc[4] = fmaf(w, v[t].x, acc[4]);
+                acc[5] = fmaf(w, v[t].y, acc[5]);
+                acc[6] = fmaf(w, v[t].z, acc[6]);
+                acc[7] = fmaf(w, v[t].w, acc[7]);
+              }
             }
           }
-#pragma unroll
-          for (int c = 0; c < SW; ++c)  // entries beyond the staged ones (hub columns)
-            for (int64_t f = sm.cf0[c] + SCN; f < sm.cf0[c] + sm.cdeg[c]; ++f) {
-              const int l = __ldg(a.Lc.col + f);
-              acc[c] = fmaf(__ldg(a.Lc.val + f), __ldg(a.ZTin + int64_t(a.inv ? a.inv[l] : l) * a.ldzt + i), acc[c]);
-            }
+          for (; q < ds; ++q) add(sm.coff[c][q], sm.cval[c][q]);
+          for (int64_t f = sm.cf0[c] + SCN; f < sm.cf0[c] + deg; ++f) {
+            const int l = __ldg(a.Lc.col + f);
+            add(int64_t(a.inv ? a.inv[l] : l) * a.ldzt, __ldg(a.Lc.val + f));
+          }
         }
-#pragma unroll
-        for (int c = 0; c < SW; ++c) sm.ac[c][rl] = acc[c];
+        *reinterpret_cast<float4*>(&sm.ac[c][rl]) = make_float4(acc[0], acc[1], acc[2], acc[3]);
+        *reinterpret_cast<float4*>(&sm.ac[c][rl + 4]) = make_float4(acc[4], acc[5], acc[6], acc[7]);
       }
       __syncthreads();
       // ---- (Lr Z) from the stripe, prox, momentum: 8 lanes per row, two
@@ -263,19 +279,16 @@ __global__ void __launch_bounds__(STHREADS, 1) fista_stripe_kernel(const __grid_
       }
       __syncthreads();
     }
-    // every read of this buffer is done: load the stripe after next into it
-    if (tid == 0 && s + 2 * int(gridDim.x) < a.nstripes) issue(s + 2 * gridDim.x, buf);
+    // every read of the buffer is done: load the next stripe into it
+    if (tid == 0 && s + int(gridDim.x) < a.nstripes) issue(s + gridDim.x);
   }
   if (sm.abort) {
-    // loads of stripes k and k + 1 may still be in flight: wait for them
-    // (bounded) before the block leaves
-    if (tid == 0)
-      for (int d = 0; d < 2; ++d) {
-        const int kk = k + d;
-        if (int(blockIdx.x) + kk * int(gridDim.x) >= a.nstripes) continue;
-        int spare = 0;
-        (void)mbar_wait(&sm.mbar[kk & 1], (kk >> 1) & 1, &spare);
-      }
+    // the load of stripe k may still be in flight: wait for it (bounded)
+    // before the block leaves
+    if (tid == 0) {
+      int spare = 0;
+      (void)mbar_wait(&sm.mbar[0], k & 1, &spare);
+    }
     __syncthreads();
     return;
   }
@@ -358,7 +371,7 @@ __global__ void permute_cols_kernel(const float* __restrict__ A, int64_t lda, fl
 }
 
 size_t stripe_smem(int rr_pad) {
-  return ((sizeof(StripeSmem) + 127) & ~size_t(127)) + size_t(2) * rr_pad * SW * sizeof(float) +
+  return ((sizeof(StripeSmem) + 127) & ~size_t(127)) + size_t(rr_pad) * SW * sizeof(float) +
          size_t(rr_pad + 1) * sizeof(int32_t);
 }
 
@@ -380,7 +393,7 @@ bool stripe_eligible(int rr, int rc) {
   if (rr < SBOX || rc < 4 * SW) return false;
   const int rr_pad = int(ceil_div(rr, SBOX)) * SBOX;
   // (Lr has at most rr^2 < 2^31 entries: 32-bit row offsets)
-  return stripe_smem(rr_pad) <= size_t(max_smem_optin()) && int64_t(rc) * ((rr + 3) / 4 * 4) < (int64_t(1) << 31) &&
+  return stripe_smem(rr_pad) <= size_t(max_smem_optin()) / SBLOCKS && int64_t(rc) * ((rr + 3) / 4 * 4) < (int64_t(1) << 31) &&
          encode_fn() != nullptr;
 }
 
@@ -441,7 +454,7 @@ cpca_status fista_stripe_run(const BatchProblem& P, const InstWs& iw, const Stri
   static PerDeviceOnce attr;
   CPCA_CUDA(once_per_device(attr, [&] {
     return cudaFuncSetAttribute((const void*)fista_stripe_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                int(max_smem_optin()));
+                                int(max_smem_optin() / SBLOCKS));
   }));
   StripeArgs a{};
   a.Yt = Y;
@@ -467,7 +480,7 @@ cpca_status fista_stripe_run(const BatchProblem& P, const InstWs& iw, const Stri
   a.nstripes = int(ceil_div(rc, SW));
   a.J = J;
   a.eps = eps;
-  const int grid = std::min(a.nstripes, num_sms());
+  const int grid = std::min(a.nstripes, SBLOCKS * num_sms());
   float* Z[2] = {iw.Z0, iw.Z1};
   float* ZT[2] = {iw.ZT0, iw.ZT1};
   double t = t0;  // t_{j0+j}; mu as in the constant-memory table of the resident kernel

@@ -403,18 +403,18 @@ knn_recheck_kernel(const float* __restrict__ P, int N, int d, int64_t ld, bool v
     if (si[c] <= -2) si[c] = -2 - si[c];
   __syncwarp();
   float window = aK + 2.f * e;
-  // When the error window holds more candidates than R, the query is not
-  // certified: it is searched by brute force within the budget, else left
-  // uncertified, and its exact re-scoring is kept to the 2K best ranking
-  // values (the ranking error in practice is far below the gaps that
-  // separate them from the K-th).
-  // count the window; beyond R = max(32, 2K) candidates the certificate is
-  // not attempted (the query goes to the brute-force budget)
-  int inwin = 0;
-  for (int c = lane; c < C; c += 32) inwin += (si[c] >= 0 && sa[c] <= window) ? 1 : 0;
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) inwin += __shfl_xor_sync(0xffffffffu, inwin, o);
-  const bool hopeless = inwin > max(32, 2 * K);
+  // Such a query is not certified: it is searched by brute force within the
+  // budget, else left uncertified, and its exact re-scoring is kept to the
+  // 2K best ranking values (the ranking error in practice is far below the
+  // gaps that separate them from the K-th).
+  // A full split list whose last ranking value lies within a_K + e leaves
+  // room for a point beyond it as close as the K-th: the certificate is not
+  // attempted (the query goes to the brute-force budget)
+  bool hopeless = false;
+  for (int s = 0; s < splits; ++s) {
+    const int64_t o = (int64_t(s) * N + q) * M + (M - 1);
+    if (cand_i[o] >= 0 && cand_d[o] <= aK + e) hopeless = true;
+  }
   if (hopeless) window = fminf(window, a2K);
   for (int c = 0; c < C; ++c) {
     const int j = si[c];

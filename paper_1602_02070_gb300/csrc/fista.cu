@@ -1008,11 +1008,12 @@ FistaBatchArgs g_fa;
 }  // namespace
 
 // ---------------------------------------------------------------- layout --
-InstWs inst_layout(Carve& c, int rr, int rc) {
+InstWs inst_layout(Carve& c, int rr, int rc, size_t zcols) {
   InstWs w{};
   const size_t ldz = size_t(rc + 3) / 4 * 4, ldzt = size_t(rr + 3) / 4 * 4;
-  w.Z0 = c.take<float>(size_t(rr) * ldz);
-  w.Z1 = c.take<float>(size_t(rr) * ldz);
+  const size_t zc = std::max(ldz, zcols);
+  w.Z0 = c.take<float>(size_t(rr) * zc);
+  w.Z1 = c.take<float>(size_t(rr) * zc);
   w.ZT0 = c.take<float>(size_t(rc) * ldzt);
   w.ZT1 = c.take<float>(size_t(rc) * ldzt);
   w.scal = c.take<double>(4);
@@ -1036,8 +1037,9 @@ BatchWs batch_layout(void* ws, const int* rr, const int* rc, int n) {
     }
     w.pscr = c.take<unsigned char>(power_scratch_bytes(ns.data(), 2 * n));
   }
-  for (int i = 0; i < n; ++i) w.inst[i] = inst_layout(c, rr[i], rc[i]);
-  w.stripe = n == 1 ? stripe_layout(c, rr[0], rc[0]) : StripeWs{};
+  const bool striped = n == 1 && stripe_candidate(rr[0], rc[0]);
+  for (int i = 0; i < n; ++i) w.inst[i] = inst_layout(c, rr[i], rc[i], striped ? stripe_zcols(rc[0]) : 0);
+  w.stripe = striped ? stripe_layout(c, rr[0], rc[0]) : StripeWs{};
   w.n = n;
   w.bytes = c.bytes();
   return w;

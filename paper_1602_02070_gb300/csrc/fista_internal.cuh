@@ -124,16 +124,18 @@ struct InstWs {
 };
 
 // Extra scratch of the striped launch of a large single problem: Y~, S and
-// one more iterate in the columns' locality order, the order itself and the
-// ordering kernel's scratch (all null when the problem does not take it).
+// one more iterate stripe-major in the processing order, the columns'
+// locality order and the ordering kernel's scratch (all null when the
+// problem cannot take the striped launch).
 struct StripeWs {
-  float* Yp;
-  float* Sp;
-  float* Pp;            // S_{j0-1} in (warm start), S_{J-1} out
+  float* Yb;
+  float* Sb;
+  float* Pb;            // S_{j0-1} in (warm start), S_{J-1} out
   int32_t* perm;        // processing position -> column
   int32_t* inv;         // column -> processing position
   unsigned char* oscr;  // order_scratch_bytes
   unsigned int* bar;    // the ordering kernel's grid barrier
+  unsigned int* ctr;    // per-launch stripe counters (a ring of three)
 };
 
 // Scratch of a (batched) solve: shared barrier state plus one InstWs each.
@@ -164,17 +166,25 @@ struct BatchProblem {
   float* prev_out = nullptr;
 };
 
-InstWs inst_layout(Carve& c, int rr, int rc);
+// zcols > 0: the Z buffers hold rr x zcols floats (the striped launch's
+// stripe-major Z, stripe_zcols(rc)).
+InstWs inst_layout(Carve& c, int rr, int rc, size_t zcols = 0);
 BatchWs batch_layout(void* ws, const int* rr, const int* rc, int n);
 cpca_status fista_batch_run(const BatchProblem* P, int n, int J, double eps, bool want_last,
                             int power_iters, uint64_t power_seed, int blocks, const BatchWs& w,
                             cudaStream_t st, bool dense = false);
 // Striped FISTA for single large problems (fista_stripe.cu): one launch per
-// iteration, Z_j's stripes through TMA; the same iterates as the resident
-// and streaming launches. It sets up Z_1 (or Z_{j0+1}) itself; t0 =
-// t_{j0+1} and mu0 = mu_{j0} of a warm start (1 and 0 for a cold one);
-// P.prev_out, when set, receives S_{J-1}. stripe_reorders: the problem also
-// takes the columns' locality order (StripeWs carved by stripe_layout).
+// iteration, each stripe of Z_j brought into shared memory by a bulk copy;
+// the same iterates as the resident and streaming launches. It sets up Z_1
+// (or Z_{j0+1}) itself; t0 = t_{j0+1} and mu0 = mu_{j0} of a warm start (1
+// and 0 for a cold one); P.prev_out, when set, receives S_{J-1}.
+// stripe_candidate: the sizes for which the workspace carries the striped
+// launch's scratch (stripe_layout, and Z buffers of stripe_zcols(rc)
+// columns); stripe_eligible: the launch is taken (also device limits);
+// stripe_reorders: it processes the columns in their locality order.
+constexpr int kStripeMaxRows = 5600;
+bool stripe_candidate(int rr, int rc);
+size_t stripe_zcols(int rc);
 bool stripe_eligible(int rr, int rc);
 bool stripe_reorders(int rr, int rc);
 StripeWs stripe_layout(Carve& c, int rr, int rc);

@@ -1,58 +1,65 @@
 // fista_stripe.cu - FISTA for FRPCAG (Sec. IV-B, Algorithm 1) on single
 // problems too large for the resident launch, one launch per iteration.
 //
-// The matrix is cut into stripes of SW = 8 columns spanning every row. A
-// block (two per SM, so that one computes while the other waits for its
-// stripe) takes stripes in turn; for each it brings the whole stripe of Z_j
-// into shared memory with TMA (boxes of 8 columns x 256 rows). Then, in
-// chunks of 256 rows:
-//   (Z Lc)(i, j) = sum_l Lc[j, l] Z^T(l, i): a warp per stripe column, each
-//       lane 8 consecutive rows, the neighbour columns' rows of Z^T read
-//       through L1 as 32-byte vectors, eight neighbours in flight (the whole
-//       Z^T of the iteration is read-only inside the launch);
-//   (Lr Z)(i, j) = sum_k Lr[i, k] Z(k, j): entirely from the stripe in
-//       shared memory (a row graph links arbitrary rows, and the stripe holds
-//       all of them), 8 lanes per row, two rows per lane group at a time;
+// Layout. The columns are taken in a processing order (the column graph's
+// locality order from order.cu for large problems, else the identity) and
+// cut into stripes of W = 16 (or 8) columns. Y~, S, the previous iterate
+// and Z_j are held stripe-major for the solve: stripe s is one contiguous
+// block of rr x W floats, row i of it at (s rr + i) W. Z_j^T is kept as well
+// (column-major, rows padded to ldzt), for the column graph's gathers. The
+// caller's matrices are converted in at the start and S out at the end.
+//
+// One block per SM (1024 threads) takes stripes in turn (the next untaken
+// one when it finishes its last). For each it
+// brings the stripe of Z_j into shared memory with one bulk copy (the block
+// is contiguous) and stages the stripe columns' neighbour lists (as Z^T row
+// offsets), then in chunks of 1024 rows:
+//   (Z Lc)(i, c) = sum_l Lc[c, l] Z^T(l, i): work items (column, row block)
+//       that the warps take in turn - 128 rows (a lane per 4 rows, 16-byte
+//       loads) for a column with a short list, 32 rows (a lane per row) for
+//       one with a long list, so that the hub columns of a kNN graph spread
+//       over the warps; the neighbours' Z^T rows are read through L1
+//       (neighbouring columns of the stripe share them); overlaps the
+//       stripe's copy on the first chunk;
+//   (Lr Z)(i, c) = sum_k Lr[i, k] Z(k, c): W/4 lanes per row, each a quad
+//       of 4 columns, entirely from the stripe in shared memory (a row
+//       graph links arbitrary rows and the stripe holds all of them): a
+//       lane group reads one contiguous stripe row per entry, and the
+//       groups of a warp spread over the banks;
 //   S_j = prox(Z_j - lambda 2 (g_c Z Lc + g_r Lr Z)),
 //   Z_{j+1} = S_j + mu_j (S_j - S_{j-1}),
-// written row-major (S_j, Z_{j+1}) and column-major (Z_{j+1}^T). Both graph
-// sums run in CSR order with one FMA per entry, exactly as the resident
-// kernel's: the iterates are bit for bit those of fista_batch_kernel.
+// written stripe-major (S_j, Z_{j+1}) and column-major (Z_{j+1}^T). Both
+// graph sums run in CSR order with one FMA per entry from zero, exactly as
+// the cooperative kernel's: the iterates are bit for bit those of
+// fista_batch_kernel (the processing order moves data, not arithmetic).
 // Launch boundaries order the iterations, so there is no grid barrier; with
 // eps > 0 every launch first reads the previous iteration's statistics and
 // all its blocks leave once the stopping test holds.
 //
-// Column order: for large problems the columns are processed in a
-// locality order of the column graph (order.cu: components, then
-// breadth-first levels), so that the stripes in flight gather their Z^T
-// rows from a narrow band that stays in L2. Y~, S and the iterates are
-// permuted into that order once per solve and X is permuted back at the
-// end; each column keeps its CSR entry order, so the arithmetic - and the
-// result - is unchanged.
-//
-// Algorithmic bytes per iteration: read Y~, S_{j-1}, Z_j (stripe), Z_j^T
-// (gathers), write S_j, Z_{j+1}, Z_{j+1}^T: 28 B per entry when every
-// gathered row comes from L2, plus the CSR bytes.
+// Bytes per entry and iteration: read Y~, S_{j-1}, Z_j (stripe) and Z_j^T
+// (gathers, once from DRAM when the rows in flight stay in L2), write S_j,
+// Z_{j+1}, Z_{j+1}^T: 28 B, against the method's 16 B (Y~, S_{j-1},
+// S_{j-2} in, S_j out); plus the CSR bytes.
 #include "fista_internal.cuh"
 #include "tma.cuh"
 
 namespace cpca {
 namespace {
 
-constexpr int SW = 8;          // stripe width (columns)
-constexpr int SBOX = 256;      // rows per TMA box
-constexpr int SCHUNK = 256;    // rows per chunk
-constexpr int STHREADS = 256;  // 8 warps: a warp per stripe column in the column product
-constexpr int SBLOCKS = 2;     // blocks per SM (one stripe buffer each)
-constexpr int SCN = 64;        // staged neighbour entries per stripe column
+constexpr int ST = 1024;        // threads per block (one block per SM)
+constexpr int RC = 1024;        // rows per chunk: one per thread in the row phase
+constexpr int kPool = 2048;     // staged neighbour entries per stripe
+constexpr int kHubDeg = 48;     // columns with longer lists take 32-row items
+constexpr uint32_t kBulk = 32768;  // bytes per bulk copy of a stripe
 
 struct StripeArgs {
-  CUtensorMap zmap;  // Z_j, row-major (ld ldz), boxes of SW x SBOX
-  const float* ZTin;
-  float* Zout;
-  float* ZTout;
-  const float* Yt;
-  float* S;
+  const float* Zin;   // Z_j, stripe-major
+  const float* ZTin;  // Z_j^T, [rc][ldzt], processing order
+  float* Zout;        // Z_{j+1}, stripe-major
+  float* ZTout;       // Z_{j+1}^T
+  const float* Yb;    // Y~, stripe-major
+  float* Sb;          // S_{j-1} in, S_j out, stripe-major
+  float* Pb;          // S_{J-1} on the last iteration (stripe-major), or null
   CsrView Lr, Lc;
   const int32_t* perm;  // processing position -> column of Lc (null: identity)
   const int32_t* inv;   // column of Lc -> processing position
@@ -60,33 +67,68 @@ struct StripeArgs {
   double* stats;  // ring [4][2]
   int* done;      // [stopped, iterations]
   int* err;       // mbarrier timeout flag
-  float* prev_out;  // S_{J-1} (ld lds) on the last iteration, or null
-  int64_t ldy, lds, ldz, ldzt;
+  unsigned int* ctr;  // stripe counters, a ring of three (launch j takes j % 3)
+  int64_t ldzt;
   float two_gr, two_gc, mu;
-  int rr, rc, rr_pad, nstripes;
+  int rr, rc, nstripes;
   int j, J;
   double eps;
   int want_stats;
 };
 
+template <int W>
 struct StripeSmem {
-  float ac[SW][SCHUNK];     // (Z Lc) of the chunk, [column][row]
-  int32_t coff[SW][SCN];    // neighbour column -> element offset of its Z^T row
-  float cval[SW][SCN];
-  int64_t cf0[SW];
-  int cdeg[SW];
-  uint64_t mbar[1];
-  double red[2][STHREADS / 32];
+  float ac[W][RC];        // (Z Lc) of the chunk, [column][row]
+  int2 pool[kPool];       // the stripe's neighbour lists, column after column in CSR
+                          // order: (element offset of the Z^T row, weight bits)
+  int64_t cf0[W];         // first CSR entry of each stripe column
+  int cdeg[W], cbeg[W];   // its degree and its first pool slot
+  int hubc[W], normc[W];  // columns taken in 32-row items (long lists) / 128-row items
+  int nhub, nnorm, next;  // their counts; the next column-product item
+  int next_stripe;
+  uint64_t mbar;
+  double red[2][ST / 32];
   int abort;
 };
 
-__device__ __forceinline__ float4 ldg4(const float* p) { return __ldg(reinterpret_cast<const float4*>(p)); }
+template <int W>
+__host__ __device__ constexpr size_t smem_head() {
+  return (sizeof(StripeSmem<W>) + 127) & ~size_t(127);
+}
 
-__global__ void __launch_bounds__(STHREADS, SBLOCKS) fista_stripe_kernel(const __grid_constant__ StripeArgs a) {
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_u32(dst)),
+               "l"(src), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
+}
+
+__device__ __forceinline__ float4 ldg4(const float* p) { return __ldg(reinterpret_cast<const float4*>(p)); }
+__device__ __forceinline__ void fma4(float4& acc, float w, const float4& v) {
+  acc.x = fmaf(w, v.x, acc.x);
+  acc.y = fmaf(w, v.y, acc.y);
+  acc.z = fmaf(w, v.z, acc.z);
+  acc.w = fmaf(w, v.w, acc.w);
+}
+
+// One prox + momentum entry of Algorithm 1 (the cooperative kernel's
+// expression order).
+__device__ __forceinline__ void prox_entry(float ar, float ac, float z, float y, float sp, float lam, float two_gr,
+                                           float two_gc, float mu, float& sv, float& zn) {
+  const float gr = fmaf(two_gr, ar, two_gc * ac);
+  const float v = fmaf(-lam, gr, z);
+  const float dl = v - y;
+  sv = y + copysignf(fmaxf(fabsf(dl) - lam, 0.f), dl);
+  zn = fmaf(mu, sv - sp, sv);
+}
+
+template <int W>
+__global__ void __launch_bounds__(ST, 1) fista_stripe_kernel(const __grid_constant__ StripeArgs a) {
+  constexpr int NQ = W / 4;        // 16-byte quads per stripe row
   extern __shared__ __align__(128) unsigned char smraw[];
-  StripeSmem& sm = *reinterpret_cast<StripeSmem*>(smraw);
-  float* zs0 = reinterpret_cast<float*>(smraw + ((sizeof(StripeSmem) + 127) & ~size_t(127)));
-  int32_t* rowp = reinterpret_cast<int32_t*>(zs0 + size_t(a.rr_pad) * SW);  // [rr + 1], from rowptr[0]
+  StripeSmem<W>& sm = *reinterpret_cast<StripeSmem<W>*>(smraw);
+  float* zs = reinterpret_cast<float*>(smraw + smem_head<W>());
+  int32_t* rowp = reinterpret_cast<int32_t*>(zs + size_t(a.rr) * W);  // [rr + 1], from rowptr[0]
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   if (__ldcg(a.done)) return;  // stopped at an earlier iteration
   if (a.eps > 0 && a.j > 1) {
@@ -101,30 +143,34 @@ __global__ void __launch_bounds__(STHREADS, SBLOCKS) fista_stripe_kernel(const _
   }
   // the statistics slot of iteration j + 1 (its last reader was iteration j - 2)
   if (blockIdx.x == 0 && tid < 2) a.stats[2 * ((a.j + 1) & 3) + tid] = 0.0;
+  // the stripe counter of launch j + 1 (its last user was launch j - 2)
+  if (blockIdx.x == 0 && tid == 0) a.ctr[(a.j + 1) % 3] = 0u;
   const float lam = float(*a.lam);
-  const int nbox = a.rr_pad / SBOX;
-  const uint32_t stripe_bytes = uint32_t(a.rr_pad) * SW * 4;
+  const uint32_t stripe_bytes = uint32_t(a.rr) * W * 4;
   if (tid == 0) {
     sm.abort = 0;
-    mbar_init(&sm.mbar[0], 1);
+    mbar_init(&sm.mbar, 1);
     mbar_fence_init();
   }
-  // row pointers of Lr relative to its first entry, for every stripe
   const int64_t rbase = a.Lr.rowptr[0];
-  for (int i = tid; i <= a.rr; i += STHREADS) rowp[i] = int32_t(a.Lr.rowptr[i] - rbase);
+  for (int i = tid; i <= a.rr; i += ST) rowp[i] = int32_t(a.Lr.rowptr[i] - rbase);
   __syncthreads();
   auto issue = [&](int s) {  // one thread: the whole stripe s into the buffer
-    mbar_expect_tx(&sm.mbar[0], stripe_bytes);
-    for (int b = 0; b < nbox; ++b) tma_load_2d(zs0 + size_t(b) * SBOX * SW, &a.zmap, &sm.mbar[0], s * SW, b * SBOX);
+    const char* src = reinterpret_cast<const char*>(a.Zin + int64_t(s) * a.rr * W);
+    mbar_expect_tx(&sm.mbar, stripe_bytes);
+    for (uint32_t o = 0; o < stripe_bytes; o += kBulk)
+      bulk_load(reinterpret_cast<char*>(zs) + o, src + o, min(kBulk, stripe_bytes - o), &sm.mbar);
   };
   if (tid == 0 && int(blockIdx.x) < a.nstripes) issue(blockIdx.x);
   double dz = 0.0, nz = 0.0;
   int k = 0;
-  for (int s = blockIdx.x; s < a.nstripes; s += gridDim.x, ++k) {
-    const float* zs = zs0;
-    const int c0 = s * SW;
-    // neighbour lists of the stripe's columns (overlaps the stripe's load)
-    if (tid < SW) {
+  // the first stripe of a block is its index; then blocks take the next
+  // untaken stripe as they finish (stripes with hub columns cost more)
+  for (int s = blockIdx.x; s < a.nstripes; ++k) {
+    const int c0 = s * W;
+    // neighbour lists of the stripe's columns, into the pool as far as it
+    // holds them (the rest is read from the CSR as it is needed)
+    if (tid < W) {
       const int jp = c0 + tid;
       const int jc = jp < a.rc ? (a.perm ? a.perm[jp] : jp) : 0;
       const int64_t f0 = jp < a.rc ? a.Lc.rowptr[jc] : 0;
@@ -132,162 +178,189 @@ __global__ void __launch_bounds__(STHREADS, SBLOCKS) fista_stripe_kernel(const _
       sm.cdeg[tid] = jp < a.rc ? int(a.Lc.rowptr[jc + 1] - f0) : 0;
     }
     __syncthreads();
-    for (int e = tid; e < SW * SCN; e += STHREADS) {
-      const int c = e / SCN, q = e % SCN;
-      if (q < min(sm.cdeg[c], SCN)) {
-        const int l = __ldg(a.Lc.col + sm.cf0[c] + q);
-        sm.coff[c][q] = int32_t(a.inv ? a.inv[l] : l) * int32_t(a.ldzt);
-        sm.cval[c][q] = __ldg(a.Lc.val + sm.cf0[c] + q);
+    if (tid == 0) {
+      int b = 0, nh = 0, nn = 0;
+      for (int c = 0; c < W; ++c) {
+        sm.cbeg[c] = b;
+        b += sm.cdeg[c];
+        if (sm.cdeg[c] > kHubDeg) sm.hubc[nh++] = c;
+        else sm.normc[nn++] = c;
+      }
+      sm.nhub = nh;
+      sm.nnorm = nn;
+      sm.next = 0;
+    }
+    __syncthreads();
+    {
+      const int total = min(sm.cbeg[W - 1] + sm.cdeg[W - 1], kPool);
+      for (int e = tid; e < total; e += ST) {
+        int c = 0;
+        while (c + 1 < W && sm.cbeg[c + 1] <= e) ++c;
+        const int64_t f = sm.cf0[c] + (e - sm.cbeg[c]);
+        const int l = __ldg(a.Lc.col + f);
+        sm.pool[e] = make_int2(int32_t(a.inv ? a.inv[l] : l) * int32_t(a.ldzt), __float_as_int(__ldg(a.Lc.val + f)));
       }
     }
-    if (tid == 0 && !mbar_wait(&sm.mbar[0], k & 1, &sm.abort)) atomicExch(a.err, 1);
     __syncthreads();
-    if (sm.abort) break;
-    for (int r0 = 0; r0 < a.rr; r0 += SCHUNK) {
-      // ---- (Z Lc): warp -> stripe column c, lane -> 8 consecutive rows
+    bool loaded = false;
+    for (int r0 = 0; r0 < a.rr; r0 += RC) {
+      const int nr = min(RC, a.rr - r0);
+      // ---- (Z Lc): items (column, row block) taken by the warps in turn: a
+      // column with a short list in 128-row items (a lane per 4 rows, 16-byte
+      // loads), one with a long list in 32-row items (a lane per row), so
+      // that long lists spread over many warps; every output still sums its
+      // column's list in CSR order.
       {
-        const int c = warp, rl = lane * 8, i = r0 + rl;
-        float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-        const int deg = sm.cdeg[c];
-        if (i < a.rr) {
-          const bool full = i + 8 <= int(a.ldzt);
-          const int ds = min(deg, SCN);
-          auto add = [&](int64_t off, float w) {
-            const float* p = a.ZTin + off + i;
-            if (full) {
-              const float4 u = ldg4(p), v = ldg4(p + 4);
-              acc[0] = fmaf(w, u.x, acc[0]);
-              acc[1] = fmaf(w, u.y, acc[1]);
-              acc[2] = fmaf(w, u.z, acc[2]);
-              acc[3] = fmaf(w, u.w, acc[3]);
-              acc[4] = fmaf(w, v.x, acc[4]);
-              acc[5] = fmaf(w, v.y, acc[5]);
-              acc[6] = fmaf(w, v.z, acc[6]);
-              acc[7] = fmaf(w, v.w, acc[7]);
-            } else {
+        const int hb = (nr + 31) / 32, nb = (nr + 127) / 128;  // row blocks of the chunk
+        const int nh = sm.nhub, nitems = nh * hb + sm.nnorm * nb;
+        for (;;) {
+          int it = 0;
+          if (lane == 0) it = atomicAdd(&sm.next, 1);
+          it = __shfl_sync(0xffffffffu, it, 0);
+          if (it >= nitems) break;
+          const bool hub = it < nh * hb;
+          const int c = hub ? sm.hubc[it / hb] : sm.normc[(it - nh * hb) / nb];
+          const int rb = hub ? (it % hb) * 32 : ((it - nh * hb) % nb) * 128;
+          const int deg = sm.cdeg[c], b0 = sm.cbeg[c];
+          const int ds = max(0, min(deg, kPool - b0));  // pooled entries of the list
+          const int rl = rb + (hub ? lane : 4 * lane);  // first row of the lane in the chunk
+          const int i = r0 + rl;
+          if (hub) {
+            float u = 0.f;
+            if (i < a.ldzt) {
+              int q = 0;
+              for (; q + 8 <= ds; q += 8) {
+                int2 pe[8];
+                float x[8];
 #pragma unroll
-              for (int t = 0; t < 8; ++t)
-                if (i + t < a.rr) acc[t] = fmaf(w, __ldg(p + t), acc[t]);
-            }
-          };
-          int q = 0;
-          if (full) {
-            for (; q + 8 <= ds; q += 8) {  // eight neighbours' loads in flight
-              float4 u[8], v[8];
+                for (int t = 0; t < 8; ++t) {
+                  pe[t] = sm.pool[b0 + q + t];
+                  x[t] = __ldg(a.ZTin + pe[t].x + i);
+                }
 #pragma unroll
-              for (int t = 0; t < 8; ++t) {
-                const float* p = a.ZTin + sm.coff[c][q + t] + i;
-                u[t] = ldg4(p);
-                v[t] = ldg4(p + 4);
+                for (int t = 0; t < 8; ++t) u = fmaf(__int_as_float(pe[t].y), x[t], u);
               }
-#pragma unroll
-              for (int t = 0; t < 8; ++t) {
-                const float w = sm.cval[c][q + t];
-                acc[0] = fmaf(w, u[t].x, acc[0]);
-                acc[1] = fmaf(w, u[t].y, acc[1]);
-                acc[2] = fmaf(w, u[t].z, acc[2]);
-                acc[3] = fmaf(w, u[t].w, acc[3]);
-                acc[4] = fmaf(w, v[t].x, acc[4]);
-                acc[5] = fmaf(w, v[t].y, acc[5]);
-                acc[6] = fmaf(w, v[t].z, acc[6]);
-                acc[7] = fmaf(w, v[t].w, acc[7]);
+              for (; q < ds; ++q) {
+                const int2 pe = sm.pool[b0 + q];
+                u = fmaf(__int_as_float(pe.y), __ldg(a.ZTin + pe.x + i), u);
+              }
+              for (int64_t f = sm.cf0[c] + ds; f < sm.cf0[c] + deg; ++f) {
+                const int l = __ldg(a.Lc.col + f);
+                u = fmaf(__ldg(a.Lc.val + f), __ldg(a.ZTin + int64_t(a.inv ? a.inv[l] : l) * a.ldzt + i), u);
               }
             }
-          }
-          for (; q < ds; ++q) add(sm.coff[c][q], sm.cval[c][q]);
-          for (int64_t f = sm.cf0[c] + SCN; f < sm.cf0[c] + deg; ++f) {
-            const int l = __ldg(a.Lc.col + f);
-            add(int64_t(a.inv ? a.inv[l] : l) * a.ldzt, __ldg(a.Lc.val + f));
+            sm.ac[c][rl] = u;
+          } else {
+            float4 u = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (i < a.ldzt) {  // then i + 3 < ldzt (both multiples of 4)
+              int q = 0;
+              for (; q + 4 <= ds; q += 4) {  // four neighbours' loads in flight
+                int2 pe[4];
+                float4 x[4];
+#pragma unroll
+                for (int t = 0; t < 4; ++t) {
+                  pe[t] = sm.pool[b0 + q + t];
+                  x[t] = ldg4(a.ZTin + pe[t].x + i);
+                }
+#pragma unroll
+                for (int t = 0; t < 4; ++t) fma4(u, __int_as_float(pe[t].y), x[t]);
+              }
+              for (; q < ds; ++q) {
+                const int2 pe = sm.pool[b0 + q];
+                fma4(u, __int_as_float(pe.y), ldg4(a.ZTin + pe.x + i));
+              }
+              for (int64_t f = sm.cf0[c] + ds; f < sm.cf0[c] + deg; ++f) {
+                const int l = __ldg(a.Lc.col + f);
+                fma4(u, __ldg(a.Lc.val + f), ldg4(a.ZTin + int64_t(a.inv ? a.inv[l] : l) * a.ldzt + i));
+              }
+            }
+            *reinterpret_cast<float4*>(&sm.ac[c][rl]) = u;
           }
         }
-        *reinterpret_cast<float4*>(&sm.ac[c][rl]) = make_float4(acc[0], acc[1], acc[2], acc[3]);
-        *reinterpret_cast<float4*>(&sm.ac[c][rl + 4]) = make_float4(acc[4], acc[5], acc[6], acc[7]);
       }
-      __syncthreads();
-      // ---- (Lr Z) from the stripe, prox, momentum: 8 lanes per row, two
-      // rows per lane group at a time (independent load chains), the row
-      // pointers from shared memory, Y~ and S_{j-1} loaded up front
+      if (!loaded) {  // the stripe's copy (overlapped with the first column pass)
+        if (tid == 0 && !mbar_wait(&sm.mbar, k & 1, &sm.abort)) atomicExch(a.err, 1);
+        loaded = true;
+      }
+      __syncthreads();  // sm.ac complete, the stripe in shared memory
+      if (sm.abort) break;
+      if (tid == 0) sm.next = 0;  // for the next chunk (after the barrier that ends this one)
+      // ---- (Lr Z) from the stripe, prox, momentum: NQ lanes per row, lane
+      // m of a row's group owning the quad of columns 4m .. 4m + 3 (the
+      // group reads one contiguous 16 W-byte row of the stripe per entry)
       {
-        const int g = lane >> 3, c = lane & 7, j = c0 + c, gl = lane & ~7;
-        const unsigned gmask = 0xFFu << gl;
-        const bool jin = j < a.rc;
-        for (int rA = warp * 4 + g; rA < SCHUNK; rA += 2 * (STHREADS / 8)) {
-          const int rB = rA + STHREADS / 8;
-          const int iA = r0 + rA, iB = r0 + rB;
-          if (iA >= a.rr) break;  // uniform in the lane group
-          const bool vB = rB < SCHUNK && iB < a.rr;
-          float yA = 0.f, spA = 0.f, yB = 0.f, spB = 0.f;
-          if (jin) {
-            yA = __ldg(a.Yt + int64_t(iA) * a.ldy + j);
-            spA = a.S[int64_t(iA) * a.lds + j];
-            if (vB) {
-              yB = __ldg(a.Yt + int64_t(iB) * a.ldy + j);
-              spB = a.S[int64_t(iB) * a.lds + j];
-            }
-          }
-          const int fA = rowp[iA], dA = rowp[iA + 1] - fA;
-          const int fB = vB ? rowp[iB] : 0, dB = vB ? rowp[iB + 1] - fB : 0;
-          float accA = 0.f, accB = 0.f;
-          const int dmax = max(dA, dB);
-          int kA = 0, kB = 0;
-          float wA = 0.f, wB = 0.f;
-          if (c < dA) { kA = __ldg(a.Lr.col + rbase + fA + c); wA = __ldg(a.Lr.val + rbase + fA + c); }
-          if (c < dB) { kB = __ldg(a.Lr.col + rbase + fB + c); wB = __ldg(a.Lr.val + rbase + fB + c); }
-          for (int e0 = 0; e0 < dmax; e0 += 8) {
-            // the next eight entries of both rows, in flight during this step
-            const int e1 = e0 + 8 + c;
-            int nkA = 0, nkB = 0;
-            float nwA = 0.f, nwB = 0.f;
-            if (e1 < dA) { nkA = __ldg(a.Lr.col + rbase + fA + e1); nwA = __ldg(a.Lr.val + rbase + fA + e1); }
-            if (e1 < dB) { nkB = __ldg(a.Lr.col + rbase + fB + e1); nwB = __ldg(a.Lr.val + rbase + fB + e1); }
-            const int nA = min(8, dA - e0), nB = min(8, dB - e0);
+        const int m = tid % NQ, cq = 4 * m, jp = c0 + cq;
+        const bool last = a.Pb && a.j == a.J;
+        for (int rl = tid / NQ; rl < nr; rl += ST / NQ) {
+          const int i = r0 + rl;
+          const int f = rowp[i], d = rowp[i + 1] - f;
+          const int32_t* lcol = a.Lr.col + rbase + f;
+          const float* lval = a.Lr.val + rbase + f;
+          float4 racc = make_float4(0.f, 0.f, 0.f, 0.f);
+          int e = 0;
+          for (; e + 8 <= d; e += 8) {  // eight entries' loads in flight
+            int kk[8];
+            float ww[8];
 #pragma unroll
             for (int t = 0; t < 8; ++t) {
-              const int k1 = __shfl_sync(gmask, kA, gl + t), k2 = __shfl_sync(gmask, kB, gl + t);
-              const float w1 = __shfl_sync(gmask, wA, gl + t), w2 = __shfl_sync(gmask, wB, gl + t);
-              if (t < nA) accA = fmaf(w1, zs[size_t(k1) * SW + c], accA);
-              if (t < nB) accB = fmaf(w2, zs[size_t(k2) * SW + c], accB);
+              kk[t] = __ldg(lcol + e + t);
+              ww[t] = __ldg(lval + e + t);
             }
-            kA = nkA; wA = nwA; kB = nkB; wB = nwB;
-          }
 #pragma unroll
-          for (int h = 0; h < 2; ++h) {
-            const int rl = h ? rB : rA, i = h ? iB : iA;
-            if (h && !vB) break;
-            if (jin) {
-              const float z = zs[size_t(i) * SW + c];
-              const float y = h ? yB : yA, sp = h ? spB : spA, acc = h ? accB : accA;
-              const float gr = fmaf(a.two_gr, acc, a.two_gc * sm.ac[c][rl]);
-              const float v = fmaf(-lam, gr, z);
-              const float dl = v - y;
-              const float sv = y + copysignf(fmaxf(fabsf(dl) - lam, 0.f), dl);
-              const float zn = fmaf(a.mu, sv - sp, sv);
-              if (a.prev_out && a.j == a.J) a.prev_out[int64_t(i) * a.lds + j] = sp;
-              a.S[int64_t(i) * a.lds + j] = sv;
-              a.Zout[int64_t(i) * a.ldz + j] = zn;
-              // Z_{j+1}^T: the four row groups of a warp fill 16 consecutive
-              // bytes of each of the stripe's rows of Z^T
-              a.ZTout[int64_t(j) * a.ldzt + i] = zn;
-              if (a.want_stats) {
-                const double d = double(zn) - double(z);
-                dz += d * d;
-                nz += double(z) * double(z);
-              }
+            for (int t = 0; t < 8; ++t) fma4(racc, ww[t], *reinterpret_cast<const float4*>(zs + kk[t] * W + cq));
+          }
+          for (; e < d; ++e)
+            fma4(racc, __ldg(lval + e), *reinterpret_cast<const float4*>(zs + __ldg(lcol + e) * W + cq));
+          const int64_t o = (int64_t(s) * a.rr + i) * W + cq;
+          const float4 z4 = *reinterpret_cast<const float4*>(zs + i * W + cq);
+          const float4 y4 = ldg4(a.Yb + o);
+          const float4 s4 = *reinterpret_cast<const float4*>(a.Sb + o);
+          float4 sv, zn;
+          prox_entry(racc.x, sm.ac[cq][rl], z4.x, y4.x, s4.x, lam, a.two_gr, a.two_gc, a.mu, sv.x, zn.x);
+          prox_entry(racc.y, sm.ac[cq + 1][rl], z4.y, y4.y, s4.y, lam, a.two_gr, a.two_gc, a.mu, sv.y, zn.y);
+          prox_entry(racc.z, sm.ac[cq + 2][rl], z4.z, y4.z, s4.z, lam, a.two_gr, a.two_gc, a.mu, sv.z, zn.z);
+          prox_entry(racc.w, sm.ac[cq + 3][rl], z4.w, y4.w, s4.w, lam, a.two_gr, a.two_gc, a.mu, sv.w, zn.w);
+          if (last) *reinterpret_cast<float4*>(a.Pb + o) = s4;  // S_{J-1}
+          *reinterpret_cast<float4*>(a.Sb + o) = sv;
+          __stcg(reinterpret_cast<float4*>(a.Zout + o), zn);
+          // Z_{j+1}^T: the groups of a warp write consecutive rows of a column
+          float* zt = a.ZTout + int64_t(jp) * a.ldzt + i;
+          if (jp < a.rc) zt[0] = zn.x;
+          if (jp + 1 < a.rc) zt[a.ldzt] = zn.y;
+          if (jp + 2 < a.rc) zt[2 * a.ldzt] = zn.z;
+          if (jp + 3 < a.rc) zt[3 * a.ldzt] = zn.w;
+          if (a.want_stats) {
+            const float zz[4] = {z4.x, z4.y, z4.z, z4.w}, nn[4] = {zn.x, zn.y, zn.z, zn.w};
+#pragma unroll
+            for (int t = 0; t < 4; ++t) {
+              const double dd = double(nn[t]) - double(zz[t]);
+              dz += dd * dd;
+              nz += double(zz[t]) * double(zz[t]);
             }
           }
         }
       }
-      __syncthreads();
+      __syncthreads();  // before the next chunk's sm.ac or the next stripe's copy
     }
+    if (sm.abort) break;
     // every read of the buffer is done: load the next stripe into it
-    if (tid == 0 && s + int(gridDim.x) < a.nstripes) issue(s + gridDim.x);
+    if (tid == 0) {
+      const int nx = int(gridDim.x + atomicAdd(a.ctr + a.j % 3, 1u));
+      sm.next_stripe = nx;
+      if (nx < a.nstripes) {
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        issue(nx);
+      }
+    }
+    __syncthreads();
+    s = sm.next_stripe;
   }
   if (sm.abort) {
-    // the load of stripe k may still be in flight: wait for it (bounded)
+    // the copy of stripe k may still be in flight: wait for it (bounded)
     // before the block leaves
     if (tid == 0) {
       int spare = 0;
-      (void)mbar_wait(&sm.mbar[0], k & 1, &spare);
+      (void)mbar_wait(&sm.mbar, k & 1, &spare);
     }
     __syncthreads();
     return;
@@ -302,7 +375,7 @@ __global__ void __launch_bounds__(STHREADS, SBLOCKS) fista_stripe_kernel(const _
     __syncthreads();
     if (tid == 0) {
       double sd = 0.0, sn = 0.0;
-      for (int w = 0; w < STHREADS / 32; ++w) {
+      for (int w = 0; w < ST / 32; ++w) {
         sd += sm.red[0][w];
         sn += sm.red[1][w];
       }
@@ -313,174 +386,163 @@ __global__ void __launch_bounds__(STHREADS, SBLOCKS) fista_stripe_kernel(const _
   if (a.j == a.J && blockIdx.x == 0 && tid == 0) a.done[1] = a.J;
 }
 
-// Z_1 = S_0 = Y~ (cold start) or Z_{j0+1} = S_{j0} + mu_{j0} (S_{j0} -
-// S_{j0-1}) (warm start, S holding S_{j0}), written row-major and as Z^T;
-// the padding columns of Z and rows of Z^T (both buffers) are zeroed.
-__global__ void __launch_bounds__(256)
-stripe_init_kernel(const float* __restrict__ Yt, int64_t ldy, float* __restrict__ S, int64_t lds,
-                   const float* __restrict__ warm_prev, float mu0, int rr, int rc, float* __restrict__ Z0,
-                   float* __restrict__ Z1, float* __restrict__ ZT0, float* __restrict__ ZT1, int64_t ldz,
-                   int64_t ldzt) {
-  __shared__ float tile[32][33];
-  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8
-  const int nti = int((ldzt + 31) / 32), ntc = int((ldz + 31) / 32);
-  for (int64_t t = blockIdx.x; t < int64_t(nti) * ntc; t += gridDim.x) {
-    const int i0 = int(t / ntc) * 32, j0 = int(t % ntc) * 32;
-    for (int r = ty; r < 32; r += 8) {
-      const int i = i0 + r, j = j0 + tx;
+// B (stripe-major, W columns per stripe, processing order) from A
+// (row-major, ld lda): B[(s rr + i) W + c] = A[i, perm[s W + c]], zero past
+// the last column.
+template <int W>
+__global__ void __launch_bounds__(256) to_stripes_kernel(const float* __restrict__ A, int64_t lda,
+                                                         float* __restrict__ B, const int32_t* __restrict__ perm,
+                                                         int rr, int rc, int nst) {
+  const int64_t total = int64_t(nst) * rr * W;
+  for (int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; t < total; t += int64_t(gridDim.x) * blockDim.x) {
+    const int c = int(t % W);
+    const int64_t sr = t / W;
+    const int i = int(sr % rr), q = int(sr / rr) * W + c;
+    B[t] = q < rc ? A[int64_t(i) * lda + (perm ? perm[q] : q)] : 0.f;
+  }
+}
+
+// A[i, perm[q]] = B[(s rr + i) W + c], q = s W + c < rc.
+template <int W>
+__global__ void __launch_bounds__(256) from_stripes_kernel(const float* __restrict__ B, float* __restrict__ A,
+                                                           int64_t lda, const int32_t* __restrict__ perm, int rr,
+                                                           int rc, int nst) {
+  const int64_t total = int64_t(nst) * rr * W;
+  for (int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; t < total; t += int64_t(gridDim.x) * blockDim.x) {
+    const int c = int(t % W);
+    const int64_t sr = t / W;
+    const int i = int(sr % rr), q = int(sr / rr) * W + c;
+    if (q < rc) A[int64_t(i) * lda + (perm ? perm[q] : q)] = B[t];
+  }
+}
+
+// Z_1 = S_0 = Y~ (cold start: S = Y~) or Z_{j0+1} = S_{j0} + mu_{j0}
+// (S_{j0} - S_{j0-1}) (warm start, Sb holding S_{j0} and Pw S_{j0-1}), the
+// operation the iteration applies; stripe-major into Zb and column-major
+// into ZT0. The padding rows of both Z^T buffers are zeroed. A block takes
+// 256 rows of one stripe and transposes them through shared memory.
+template <int W>
+__global__ void __launch_bounds__(256) stripe_init_kernel(const float* __restrict__ Yb, float* __restrict__ Sb,
+                                                          const float* __restrict__ Pw, float mu0, int rr, int rc,
+                                                          int nst, float* __restrict__ Zb, float* __restrict__ ZT0,
+                                                          float* __restrict__ ZT1, int64_t ldzt) {
+  __shared__ float tile[W][257];
+  const int nrb = int((ldzt + 255) / 256);
+  for (int64_t b = blockIdx.x; b < int64_t(nst) * nrb; b += gridDim.x) {
+    const int s = int(b / nrb), i0 = int(b % nrb) * 256;
+    for (int e = threadIdx.x; e < 256 * W; e += 256) {
+      const int r = e / W, c = e % W, i = i0 + r;
       float z = 0.f;
-      if (i < rr && j < rc) {
-        if (warm_prev) {
-          const float sv = S[int64_t(i) * lds + j], sp = warm_prev[int64_t(i) * lds + j];
+      if (i < rr) {
+        const int64_t o = (int64_t(s) * rr + i) * W + c;
+        if (Pw) {
+          const float sv = Sb[o], sp = Pw[o];
           z = fmaf(mu0, sv - sp, sv);
         } else {
-          z = Yt[int64_t(i) * ldy + j];
-          S[int64_t(i) * lds + j] = z;
+          z = Yb[o];
+          Sb[o] = z;
         }
+        Zb[o] = z;
       }
-      if (i < rr && j < ldz) {
-        Z0[int64_t(i) * ldz + j] = z;
-        Z1[int64_t(i) * ldz + j] = 0.f;
-      }
-      tile[r][tx] = z;
+      tile[c][r] = z;
     }
     __syncthreads();
-    for (int c = ty; c < 32; c += 8) {
-      const int j = j0 + c, i = i0 + tx;
-      if (j < rc && i < ldzt) {
-        ZT0[int64_t(j) * ldzt + i] = tile[tx][c];
-        ZT1[int64_t(j) * ldzt + i] = 0.f;
+    for (int e = threadIdx.x; e < 256 * W; e += 256) {
+      const int c = e / 256, r = e % 256, i = i0 + r, q = s * W + c;
+      if (q < rc && i < ldzt) {
+        ZT0[int64_t(q) * ldzt + i] = tile[c][r];
+        if (i >= rr) ZT1[int64_t(q) * ldzt + i] = 0.f;
       }
     }
     __syncthreads();
   }
 }
 
-// B(:, q) = A(:, perm[q]) (forward) or B(:, perm[q]) = A(:, q) (backward),
-// `rows` rows of `cols` columns.
-__global__ void permute_cols_kernel(const float* __restrict__ A, int64_t lda, float* __restrict__ B, int64_t ldb,
-                                    const int32_t* __restrict__ perm, int rows, int cols, int backward) {
-  for (int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; t < int64_t(rows) * cols;
-       t += int64_t(gridDim.x) * blockDim.x) {
-    const int i = int(t / cols), q = int(t % cols);
-    if (backward)
-      B[int64_t(i) * ldb + perm[q]] = A[int64_t(i) * lda + q];
-    else
-      B[int64_t(i) * ldb + q] = A[int64_t(i) * lda + perm[q]];
-  }
+template <int W>
+size_t stripe_smem(int rr) {
+  return smem_head<W>() + size_t(rr) * W * sizeof(float) + size_t(rr + 1) * sizeof(int32_t);
 }
 
-size_t stripe_smem(int rr_pad) {
-  return ((sizeof(StripeSmem) + 127) & ~size_t(127)) + size_t(rr_pad) * SW * sizeof(float) +
-         size_t(rr_pad + 1) * sizeof(int32_t);
+// Stripe width for rr rows: 16 when the stripe fits one block's shared
+// memory, else 8, else 0 (not eligible).
+int stripe_width(int rr) {
+  const size_t cap = size_t(max_smem_optin());
+  if (stripe_smem<16>(rr) <= cap) return 16;
+  if (stripe_smem<8>(rr) <= cap) return 8;
+  return 0;
 }
 
-bool make_zmap(CUtensorMap* map, const float* Z, int rr, int64_t ldz) {
-  EncodeTiledFn fn = encode_fn();
-  if (!fn) return false;
-  cuuint64_t dims[2] = {cuuint64_t(ldz), cuuint64_t(rr)};
-  cuuint64_t strides[1] = {cuuint64_t(ldz) * 4};
-  cuuint32_t box[2] = {cuuint32_t(SW), cuuint32_t(SBOX)};
-  cuuint32_t estr[2] = {1, 1};
-  return fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(Z), dims, strides, box, estr,
-            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
-            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
-}
-
-}  // namespace
-
-bool stripe_eligible(int rr, int rc) {
-  if (rr < SBOX || rc < 4 * SW) return false;
-  const int rr_pad = int(ceil_div(rr, SBOX)) * SBOX;
-  // (Lr has at most rr^2 < 2^31 entries: 32-bit row offsets)
-  return stripe_smem(rr_pad) <= size_t(max_smem_optin()) / SBLOCKS && int64_t(rc) * ((rr + 3) / 4 * 4) < (int64_t(1) << 31) &&
-         encode_fn() != nullptr;
-}
-
-bool stripe_reorders(int rr, int rc) {
-  return rr >= SBOX && rc >= 4 * SW && int64_t(rr) * rc >= (int64_t(1) << 22) && order_supported(rc);
-}
-
-StripeWs stripe_layout(Carve& c, int rr, int rc) {
-  StripeWs w{};
-  if (!stripe_reorders(rr, rc)) return w;
-  const size_t ldz = size_t(rc + 3) / 4 * 4;
-  w.Yp = c.take<float>(size_t(rr) * ldz);
-  w.Sp = c.take<float>(size_t(rr) * ldz);
-  w.Pp = c.take<float>(size_t(rr) * ldz);
-  w.perm = c.take<int32_t>(rc);
-  w.inv = c.take<int32_t>(rc);
-  w.oscr = c.take<unsigned char>(order_scratch_bytes(rc));
-  w.bar = c.take<unsigned int>(kBarrierCounters + 1);
-  return w;
-}
-
-cpca_status fista_stripe_run(const BatchProblem& P, const InstWs& iw, const StripeWs& sw, int J, double eps,
-                             bool want_last, double t0, float mu0, int* err, cudaStream_t st) {
-  const int rr = P.rr, rc = P.rc;
-  const int rr_pad = int(ceil_div(rr, SBOX)) * SBOX;
-  const int64_t ldz = (rc + 3) / 4 * 4, ldzt = (rr + 3) / 4 * 4;
-  CUtensorMap maps[2];
-  CPCA_CHECK_ARG(make_zmap(&maps[0], iw.Z0, rr, ldz) && make_zmap(&maps[1], iw.Z1, rr, ldz),
-                 "frpcag: tensor map for the striped FISTA launch could not be encoded");
-  // locality order of the columns (large problems with the ordering scratch)
-  const bool reorder = sw.Yp != nullptr;
-  const float* Y = P.Yt;
-  float* S = P.X;
-  int64_t ldy = P.ldy, lds = P.ldx;
-  const float* warm = P.j0 > 0 ? P.warm_prev : nullptr;
-  float* prev = P.prev_out;
-  const unsigned pg = std::min<unsigned>(ceil_div(int64_t(rr) * rc, 256), num_sms() * 8);
-  if (reorder) {
-    CPCA_TRY(graph_order(P.Lc, sw.perm, sw.inv, sw.oscr, sw.bar, err, st));
-    permute_cols_kernel<<<pg, 256, 0, st>>>(P.Yt, P.ldy, sw.Yp, ldz, sw.perm, rr, rc, 0);
-    CPCA_LAUNCHED();
-    if (warm) {
-      permute_cols_kernel<<<pg, 256, 0, st>>>(P.X, P.ldx, sw.Sp, ldz, sw.perm, rr, rc, 0);
-      CPCA_LAUNCHED();
-      permute_cols_kernel<<<pg, 256, 0, st>>>(warm, P.ldx, sw.Pp, ldz, sw.perm, rr, rc, 0);
-      CPCA_LAUNCHED();
-      warm = sw.Pp;
-    }
-    Y = sw.Yp;
-    S = sw.Sp;
-    ldy = lds = ldz;
-    if (prev) prev = sw.Pp;
-  }
-  stripe_init_kernel<<<std::min<unsigned>(ceil_div(int64_t(rr) * ldz, 1024), num_sms() * 8), 256, 0, st>>>(
-      Y, ldy, S, lds, warm, mu0, rr, rc, iw.Z0, iw.Z1, iw.ZT0, iw.ZT1, ldz, ldzt);
+template <int W>
+cpca_status launch_to_stripes(const float* A, int64_t lda, float* B, const int32_t* perm, int rr, int rc,
+                              cudaStream_t st) {
+  const int nst = int(ceil_div(rc, W));
+  const unsigned g = unsigned(std::min<int64_t>(ceil_div(int64_t(nst) * rr * W, 256), int64_t(num_sms()) * 8));
+  to_stripes_kernel<W><<<g, 256, 0, st>>>(A, lda, B, perm, rr, rc, nst);
   CPCA_LAUNCHED();
-  const size_t smem = stripe_smem(rr_pad);
+  return CPCA_OK;
+}
+
+template <int W>
+cpca_status launch_from_stripes(const float* B, float* A, int64_t lda, const int32_t* perm, int rr, int rc,
+                                cudaStream_t st) {
+  const int nst = int(ceil_div(rc, W));
+  const unsigned g = unsigned(std::min<int64_t>(ceil_div(int64_t(nst) * rr * W, 256), int64_t(num_sms()) * 8));
+  from_stripes_kernel<W><<<g, 256, 0, st>>>(B, A, lda, perm, rr, rc, nst);
+  CPCA_LAUNCHED();
+  return CPCA_OK;
+}
+
+template <int W>
+cpca_status stripe_solve(const BatchProblem& P, const InstWs& iw, const StripeWs& sw, int J, double eps,
+                         bool want_last, double t0, float mu0, int* err, cudaStream_t st) {
+  const int rr = P.rr, rc = P.rc, nst = int(ceil_div(rc, W));
+  const int64_t ldzt = (rr + 3) / 4 * 4;
+  const int32_t* perm = nullptr;
+  const int32_t* inv = nullptr;
+  if (stripe_reorders(rr, rc)) {  // the column graph's locality order
+    CPCA_TRY(graph_order(P.Lc, sw.perm, sw.inv, sw.oscr, sw.bar, err, st));
+    perm = sw.perm;
+    inv = sw.inv;
+  }
+  const bool warm = P.j0 > 0;
+  CPCA_TRY(launch_to_stripes<W>(P.Yt, P.ldy, sw.Yb, perm, rr, rc, st));
+  if (warm) {
+    CPCA_TRY(launch_to_stripes<W>(P.X, P.ldx, sw.Sb, perm, rr, rc, st));
+    CPCA_TRY(launch_to_stripes<W>(P.warm_prev, P.ldx, sw.Pb, perm, rr, rc, st));
+  }
+  CPCA_CUDA(cudaMemsetAsync(sw.ctr, 0, 3 * sizeof(unsigned int), st));  // stripe counters
+  const int nrb = int(ceil_div(ldzt, 256));
+  stripe_init_kernel<W><<<unsigned(std::min<int64_t>(int64_t(nst) * nrb, int64_t(num_sms()) * 8)), 256, 0, st>>>(
+      sw.Yb, sw.Sb, warm ? sw.Pb : nullptr, mu0, rr, rc, nst, iw.Z0, iw.ZT0, iw.ZT1, ldzt);
+  CPCA_LAUNCHED();
+  const size_t smem = stripe_smem<W>(rr);
   static PerDeviceOnce attr;
   CPCA_CUDA(once_per_device(attr, [&] {
-    return cudaFuncSetAttribute((const void*)fista_stripe_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                int(max_smem_optin() / SBLOCKS));
+    return cudaFuncSetAttribute((const void*)fista_stripe_kernel<W>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                int(max_smem_optin()));
   }));
   StripeArgs a{};
-  a.Yt = Y;
-  a.S = S;
+  a.Yb = sw.Yb;
+  a.Sb = sw.Sb;
+  a.Pb = P.prev_out ? sw.Pb : nullptr;
   a.Lr = P.Lr;
   a.Lc = P.Lc;
-  a.perm = reorder ? sw.perm : nullptr;
-  a.inv = reorder ? sw.inv : nullptr;
+  a.perm = perm;
+  a.inv = inv;
   a.lam = iw.scal + 2;
   a.stats = iw.stats;
   a.done = iw.done;
   a.err = err;
-  a.prev_out = prev;
-  a.ldy = ldy;
-  a.lds = lds;
-  a.ldz = ldz;
+  a.ctr = sw.ctr;
   a.ldzt = ldzt;
   a.two_gr = float(2.0 * P.gamma_r);
   a.two_gc = float(2.0 * P.gamma_c);
   a.rr = rr;
   a.rc = rc;
-  a.rr_pad = rr_pad;
-  a.nstripes = int(ceil_div(rc, SW));
+  a.nstripes = nst;
   a.J = J;
   a.eps = eps;
-  const int grid = std::min(a.nstripes, SBLOCKS * num_sms());
+  const int grid = std::min(nst, num_sms());
   float* Z[2] = {iw.Z0, iw.Z1};
   float* ZT[2] = {iw.ZT0, iw.ZT1};
   double t = t0;  // t_{j0+j}; mu as in the constant-memory table of the resident kernel
@@ -490,12 +552,12 @@ cpca_status fista_stripe_run(const BatchProblem& P, const InstWs& iw, const Stri
     a.mu = float((t - 1.0) / tn);
     t = tn;
     a.j = j;
-    a.zmap = maps[(j - 1) & 1];
+    a.Zin = Z[(j - 1) & 1];
     a.ZTin = ZT[(j - 1) & 1];
     a.Zout = Z[j & 1];
     a.ZTout = ZT[j & 1];
     a.want_stats = (eps > 0 || (want_last && j == J)) ? 1 : 0;
-    fista_stripe_kernel<<<grid, STHREADS, smem, st>>>(a);
+    fista_stripe_kernel<W><<<grid, ST, smem, st>>>(a);
     count_launch();
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) {
@@ -505,15 +567,48 @@ cpca_status fista_stripe_run(const BatchProblem& P, const InstWs& iw, const Stri
     }
   }
   prof_end();
-  if (reorder) {
-    permute_cols_kernel<<<pg, 256, 0, st>>>(sw.Sp, ldz, P.X, P.ldx, sw.perm, rr, rc, 1);
-    CPCA_LAUNCHED();
-    if (P.prev_out) {
-      permute_cols_kernel<<<pg, 256, 0, st>>>(sw.Pp, ldz, P.prev_out, P.ldx, sw.perm, rr, rc, 1);
-      CPCA_LAUNCHED();
-    }
-  }
+  CPCA_TRY(launch_from_stripes<W>(sw.Sb, P.X, P.ldx, perm, rr, rc, st));
+  if (P.prev_out) CPCA_TRY(launch_from_stripes<W>(sw.Pb, P.prev_out, P.ldx, perm, rr, rc, st));
   return CPCA_OK;
+}
+
+}  // namespace
+
+bool stripe_candidate(int rr, int rc) { return rr >= 64 && rr <= kStripeMaxRows && rc >= 256; }
+
+size_t stripe_zcols(int rc) { return size_t(rc + 15) / 16 * 16; }
+
+bool stripe_eligible(int rr, int rc) {
+  if (!stripe_candidate(rr, rc)) return false;
+  const int W = stripe_width(rr);
+  // enough stripes to occupy the SMs; Z^T offsets below 2^31 (32-bit staged
+  // offsets), as are Lr's row offsets (at most rr^2 entries)
+  return W > 0 && ceil_div(rc, W) >= num_sms() && int64_t(rc) * ((rr + 3) / 4 * 4) < (int64_t(1) << 31);
+}
+
+bool stripe_reorders(int rr, int rc) { return int64_t(rr) * rc >= (int64_t(1) << 22) && order_supported(rc); }
+
+StripeWs stripe_layout(Carve& c, int rr, int rc) {
+  StripeWs w{};
+  if (!stripe_candidate(rr, rc)) return w;
+  const size_t n = size_t(rr) * stripe_zcols(rc);
+  w.Yb = c.take<float>(n);
+  w.Sb = c.take<float>(n);
+  w.Pb = c.take<float>(n);
+  w.perm = c.take<int32_t>(rc);
+  w.inv = c.take<int32_t>(rc);
+  w.oscr = c.take<unsigned char>(order_scratch_bytes(rc));
+  w.bar = c.take<unsigned int>(kBarrierCounters + 1);
+  w.ctr = c.take<unsigned int>(3);
+  return w;
+}
+
+cpca_status fista_stripe_run(const BatchProblem& P, const InstWs& iw, const StripeWs& sw, int J, double eps,
+                             bool want_last, double t0, float mu0, int* err, cudaStream_t st) {
+  CPCA_CHECK_ARG(sw.Yb != nullptr && stripe_eligible(P.rr, P.rc),
+                 "frpcag: %d x %d problem outside the striped launch", P.rr, P.rc);
+  return stripe_width(P.rr) == 16 ? stripe_solve<16>(P, iw, sw, J, eps, want_last, t0, mu0, err, st)
+                                  : stripe_solve<8>(P, iw, sw, J, eps, want_last, t0, mu0, err, st);
 }
 
 }  // namespace cpca

@@ -190,6 +190,60 @@ __device__ __forceinline__ float exact_d2_warp(const float* __restrict__ a,
   return __shfl_sync(0xffffffffu, s, 0);
 }
 
+// exact_d2_warp from one point a to up to G points (row c[g] of P for
+// g < n), each with exactly exact_d2_warp's arithmetic, a's coordinates read
+// once for all of them.
+template <int G>
+__device__ __forceinline__ void exact_d2_warp_group(const float* __restrict__ a, const float* __restrict__ P,
+                                                    int64_t ld, const int* c, int n, int d, bool vec4,
+                                                    float* out) {
+  const int lane = threadIdx.x & 31;
+  float s[G];
+  const float* b[G];
+#pragma unroll
+  for (int g = 0; g < G; ++g) {
+    s[g] = 0.f;
+    b[g] = P + int64_t(g < n ? c[g] : c[0]) * ld;
+  }
+  if (vec4) {
+    const float4* a4 = reinterpret_cast<const float4*>(a);
+    for (int t = lane; t < (d >> 2); t += 32) {
+      const float4 x = __ldg(a4 + t);
+      float4 y[G];
+#pragma unroll
+      for (int g = 0; g < G; ++g)
+        if (g < n) y[g] = __ldg(reinterpret_cast<const float4*>(b[g]) + t);
+#pragma unroll
+      for (int g = 0; g < G; ++g)
+        if (g < n) {
+          float dx = x.x - y[g].x;
+          s[g] = fmaf(dx, dx, s[g]);
+          dx = x.y - y[g].y;
+          s[g] = fmaf(dx, dx, s[g]);
+          dx = x.z - y[g].z;
+          s[g] = fmaf(dx, dx, s[g]);
+          dx = x.w - y[g].w;
+          s[g] = fmaf(dx, dx, s[g]);
+        }
+    }
+  } else {
+    for (int t = lane; t < d; t += 32) {
+      const float x = __ldg(a + t);
+#pragma unroll
+      for (int g = 0; g < G; ++g)
+        if (g < n) {
+          const float dx = x - __ldg(b[g] + t);
+          s[g] = fmaf(dx, dx, s[g]);
+        }
+    }
+  }
+#pragma unroll
+  for (int g = 0; g < G; ++g) {
+    const float v = warp_sumf(s[g]);
+    out[g] = __shfl_sync(0xffffffffu, v, 0);
+  }
+}
+
 // The same distance in FP64 (direct differences of the FP32 inputs, which
 // are exact in FP64; lane-strided FP64 sums, then a butterfly): relative
 // error about (d/32 + 5) 2^-53, used only to order candidates that the FP32
@@ -230,6 +284,7 @@ __host__ __device__ inline float exact_d2_tau(int d) { return float((d / 32.0 + 
 namespace {
 
 constexpr int RECHECK_WARPS = 4;
+constexpr int kRecheckGroup = 8;  // candidates scored together
 
 // The K nearest of a warp's candidate set by exact distance. Candidate c
 // (c < C) is live when si[c] >= 0 and has the FP32 exact distance sd[c],
@@ -416,19 +471,38 @@ knn_recheck_kernel(const float* __restrict__ P, int N, int d, int64_t ld, bool v
     if (cand_i[o] >= 0 && cand_d[o] <= aK + e) hopeless = true;
   }
   if (hopeless) window = fminf(window, a2K);
+  // the candidates within the window, scored eight at a time (the query's
+  // coordinates read once per group)
+  __shared__ int grp[RECHECK_WARPS][kRecheckGroup];
+  __shared__ int grj[RECHECK_WARPS][kRecheckGroup];
+  int n = 0;
+  auto flush = [&]() {
+    float v[kRecheckGroup];
+    exact_d2_warp_group<kRecheckGroup>(P + int64_t(q) * ld, P, ld, grj[wib], n, d, vec4, v);
+    if (lane == 0)
+      for (int g = 0; g < n; ++g) sd[grp[wib][g]] = v[g] != v[g] ? INF : v[g];  // NaN input ranks last
+    __syncwarp();
+  };
   for (int c = 0; c < C; ++c) {
     const int j = si[c];
     if (j < 0) continue;
+    __syncwarp();
     if (!(sa[c] <= window)) {  // warp-uniform branch: never among the K nearest
-      __syncwarp();
       if (lane == 0) si[c] = -1;
       __syncwarp();
       continue;
     }
-    float v = exact_d2_warp(P + int64_t(q) * ld, P + int64_t(j) * ld, d, vec4);
-    if (v != v) v = INF;  // NaN input ranks last
-    if (lane == 0) sd[c] = v;
+    if (lane == 0) {
+      grp[wib][n] = c;
+      grj[wib][n] = j;
+    }
+    __syncwarp();
+    if (++n == kRecheckGroup) {
+      flush();
+      n = 0;
+    }
   }
+  if (n > 0) flush();
   __syncwarp();
   const float dK = resolve_knn(P, ld, d, vec4, q, K, C, sd, si, s64, exact_d2_tau(d), out_i, out_d);
   // Certificate: every point outside split s's list has a ranking value

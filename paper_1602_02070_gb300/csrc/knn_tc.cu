@@ -4,7 +4,8 @@
 // of its split, the dot products q.b are computed on the 5th-generation
 // tensor cores (tcgen05.mma, kind::tf32, M = 128, N = 256, FP32 accumulate
 // in tensor memory); the ranking distance |q|^2 + |b|^2 - 2 q.b then feeds a
-// per-query list of the M smallest, kept in shared memory (a per-lane bitmask
+// per-query list of the M smallest, kept in registers for M = 32 and in
+// shared memory for M = 64 (a per-lane bitmask
 // of the values under the current threshold limits the sorted insertions to
 // the few that can enter the list). These are only
 // candidates: knn.cu re-scores them with the exact FP32 squared distance and
@@ -14,7 +15,8 @@
 // memory allocator and MMA issuer (one lane), warps 4-7 = epilogue (warp w
 // reads TMEM lanes 32 (w % 4) .. +31, i.e. queries 32 (w - 4) .. +31).
 // Operands: K-major, 128-byte swizzle, 32 FP32 columns (128 B) per stage;
-// a 3-stage ring of (A 16 KB + B 32 KB) guarded by full/empty mbarriers; two
+// a ring of 4 (M = 32) or 3 (M = 64) stages of (A 16 KB + B 32 KB) guarded
+// by full/empty mbarriers; two
 // 256-column accumulators in TMEM (512 columns) so the epilogue of one base
 // tile overlaps the MMAs of the next. Every mbarrier wait is bounded: on
 // timeout the block raises *err, stops, frees its TMEM and returns.
@@ -32,7 +34,13 @@
 namespace cpca {
 namespace {
 
-constexpr int BM = 128, BN = 256, BK = 32, STAGES = 3;
+constexpr int BM = 128, BN = 256, BK = 32, kMaxStages = 4;
+// M = 32 keeps the per-query lists in registers, which leaves shared memory
+// for a fourth operand stage; M = 64 keeps them in shared memory (3 stages).
+template <int M>
+__host__ __device__ constexpr int stages_of() {
+  return M == 32 ? 4 : 3;
+}
 constexpr int A_BYTES = BM * BK * 4, B_BYTES = BN * BK * 4, STAGE_BYTES = A_BYTES + B_BYTES;
 constexpr uint32_t TMEM_COLS = 512;
 
@@ -113,7 +121,7 @@ __device__ __forceinline__ void tc_fence_after() {
       : "memory")
 
 struct TcShared {
-  uint64_t full[STAGES], empty[STAGES], acc_full[2], acc_empty[2];
+  uint64_t full[kMaxStages], empty[kMaxStages], acc_full[2], acc_empty[2];
   uint32_t tmem_base;
   int abort;
 };
@@ -128,10 +136,13 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ 
   // operand stages must be 1024-byte aligned for the 128-byte swizzle
   unsigned char* base = reinterpret_cast<unsigned char*>(
       (reinterpret_cast<uintptr_t>(raw) + 1023) & ~uintptr_t(1023));
+  constexpr int STAGES = stages_of<M>();
+  constexpr bool kRegLists = M == 32;
   unsigned char* stages = base;
-  float* ld_ = reinterpret_cast<float*>(base + STAGES * STAGE_BYTES);  // [M][128]
-  int32_t* li = reinterpret_cast<int32_t*>(ld_ + M * BM + 32 * BM);  // [M][128]
-  TcShared& sh = *reinterpret_cast<TcShared*>(li + M * BM);
+  float* stage_d = reinterpret_cast<float*>(base + STAGES * STAGE_BYTES);  // [32][128] chunk values
+  float* ld_ = stage_d + 32 * BM;                                          // [M][128] (shared-memory lists)
+  int32_t* li = reinterpret_cast<int32_t*>(ld_ + (kRegLists ? 0 : M * BM));  // [M][128]
+  TcShared& sh = *reinterpret_cast<TcShared*>(li + (kRegLists ? 0 : M * BM));
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int q0 = blockIdx.x * BM;
@@ -233,10 +244,21 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ 
     // those are inserted into its sorted list, so lanes rarely diverge.
     const int ql = (warp - 4) * 32 + lane;  // query within the block = TMEM lane
     const int q = q0 + ql;
-    float* stage_d = ld_ + M * BM;          // [32][128] chunk values
-    for (int m = 0; m < M; ++m) {
-      ld_[m * BM + ql] = __int_as_float(0x7f800000);
-      li[m * BM + ql] = -1;
+    // the lane's list, ascending (equal values keep the earlier index):
+    // registers for M = 32 (statically unrolled insertion), else shared memory
+    float rd[kRegLists ? M : 1];
+    int ri[kRegLists ? M : 1];
+    if (kRegLists) {
+#pragma unroll
+      for (int m = 0; m < (kRegLists ? M : 1); ++m) {
+        rd[m] = __int_as_float(0x7f800000);
+        ri[m] = -1;
+      }
+    } else {
+      for (int m = 0; m < M; ++m) {
+        ld_[m * BM + ql] = __int_as_float(0x7f800000);
+        li[m * BM + ql] = -1;
+      }
     }
     float thr = __int_as_float(0x7f800000);
     const uint32_t lane_base = uint32_t((warp & 3) * 32) << 16;
@@ -265,16 +287,33 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ 
           mask &= mask - 1;
           const float dd = stage_d[i * BM + ql];
           if (!(dd < thr)) continue;
-          // sorted insert (ascending; equal values keep the earlier index)
-          int pos = M - 1;
-          while (pos > 0 && ld_[(pos - 1) * BM + ql] > dd) {
-            ld_[pos * BM + ql] = ld_[(pos - 1) * BM + ql];
-            li[pos * BM + ql] = li[(pos - 1) * BM + ql];
-            --pos;
+          const int jn = nb0 + i;
+          if (kRegLists) {
+            // every entry above dd moves up one place; dd takes the place
+            // after the last entry not above it
+#pragma unroll
+            for (int p = (kRegLists ? M : 1) - 1; p >= 1; --p) {
+              const bool up = rd[p - 1] > dd;
+              const bool here = !up && rd[p] > dd;
+              rd[p] = up ? rd[p - 1] : (here ? dd : rd[p]);
+              ri[p] = up ? ri[p - 1] : (here ? jn : ri[p]);
+            }
+            if (rd[0] > dd) {
+              rd[0] = dd;
+              ri[0] = jn;
+            }
+            thr = rd[(kRegLists ? M : 1) - 1];
+          } else {
+            int pos = M - 1;
+            while (pos > 0 && ld_[(pos - 1) * BM + ql] > dd) {
+              ld_[pos * BM + ql] = ld_[(pos - 1) * BM + ql];
+              li[pos * BM + ql] = li[(pos - 1) * BM + ql];
+              --pos;
+            }
+            ld_[pos * BM + ql] = dd;
+            li[pos * BM + ql] = jn;
+            thr = ld_[(M - 1) * BM + ql];
           }
-          ld_[pos * BM + ql] = dd;
-          li[pos * BM + ql] = nb0 + i;
-          thr = ld_[(M - 1) * BM + ql];
         }
       }
       tc_fence_before();
@@ -283,10 +322,18 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ 
     }
     if (q < N) {
       const float nq = nrm[q];
-      for (int m = 0; m < M; ++m) {
-        const int64_t o = (int64_t(blockIdx.y) * N + q) * M + m;
-        cand_i[o] = li[m * BM + ql];
-        cand_d[o] = ld_[m * BM + ql] + nq;
+      const int64_t o = (int64_t(blockIdx.y) * N + q) * M;
+      if (kRegLists) {
+#pragma unroll
+        for (int m = 0; m < (kRegLists ? M : 1); ++m) {
+          cand_i[o + m] = ri[m];
+          cand_d[o + m] = rd[m] + nq;
+        }
+      } else {
+        for (int m = 0; m < M; ++m) {
+          cand_i[o + m] = li[m * BM + ql];
+          cand_d[o + m] = ld_[m * BM + ql] + nq;
+        }
       }
     }
   }
@@ -325,7 +372,8 @@ bool device_is_sm10x() {
 }  // namespace
 
 size_t knn_tc_smem(int M) {
-  return 1024 + size_t(STAGES) * STAGE_BYTES + size_t(M) * BM * 8 + size_t(32) * BM * 4 +
+  const int stages = M == 32 ? stages_of<32>() : stages_of<64>();
+  return 1024 + size_t(stages) * STAGE_BYTES + size_t(32) * BM * 4 + (M == 32 ? 0 : size_t(M) * BM * 8) +
          sizeof(TcShared) + 64;
 }
 

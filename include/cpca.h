@@ -107,8 +107,9 @@ typedef struct cpca_csr {
  * (pass Y with npts = n, dim = p, ld = n for the column graph of Y).
  * For each point the K nearest other points by Euclidean distance are found
  * (ties by lower index). Candidates are ranked by |a|^2 + |b|^2 - 2ab with the
- * dot products on the tensor cores (TF32, FP32 accumulate; FP32 SIMT when
- * the rows are not 16-byte aligned); the kept squared distances are then
+ * dot products on the tensor cores (a copy of the points scaled by a power
+ * of two and rounded to half precision - the significand of TF32 - with
+ * FP32 accumulation; FP32 SIMT on other GPUs); the kept squared distances are then
  * summed directly over the coordinates in FP32, and a certificate (the
  * ranking error bound against the gap to the best non-candidate) decides
  * per query whether an exact brute-force search is needed. The graph joins i and j if either is among the other's
@@ -123,19 +124,21 @@ typedef struct cpca_csr {
  * diagonal; may be NULL); knn_idx[npts*K], knn_d2[npts*K] (may be NULL).
  * nnz_cap must be >= npts*(2K+1) (the largest possible pattern).
  * Host outputs: *nnz_out, *sigma2_out (either may be NULL).
+ * Workspace: cpca_knn_graph_workspace_size (it includes the half copy,
+ * 2 npts dim bytes).
  * This call SYNCHRONISES `stream` once (to return nnz).
  * Requirements: 1 <= K <= 32, K < npts, dim >= 1.
  * ---------------------------------------------------------------------- */
 size_t cpca_knn_graph_workspace_size(int32_t npts, int32_t dim, int32_t K, int32_t transposed);
 /* Certification record of the last cpca_knn_graph call on this host
  * thread. The tensor-core candidates of a query are certified when the
- * worst-case TF32 error bound proves that no point outside its candidate
+ * worst-case error bound of the half-precision ranking proves that no point outside its candidate
  * lists can beat the K-th exact distance. Queries that fail are searched
  * by exact brute force while their number stays within a budget of
  * max(64, 2e11 / (npts dim)) (a query costs npts dim FMAs):
  * cpca_knn_last_bruteforce() counts them. Beyond the budget none is
  * redone; each keeps the exact K nearest of the 2K best of its tensor-core
- * candidates (the TF32 ranking error is far below the distance gaps in
+ * candidates (the ranking error is far below the distance gaps in
  * practice, but the worst-case bound can exceed the spread of a tight
  * cluster in high dimension) and cpca_knn_last_uncertified() counts them. */
 int32_t cpca_knn_last_bruteforce(void);

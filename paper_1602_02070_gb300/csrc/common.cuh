@@ -145,6 +145,10 @@ inline int max_smem_optin() {
   static std::atomic<int> cache[kMaxDevices];
   return device_attr(cudaDevAttrMaxSharedMemoryPerBlockOptin, cache, 48 * 1024);
 }
+inline int max_smem_per_sm() {
+  static std::atomic<int> cache[kMaxDevices];
+  return device_attr(cudaDevAttrMaxSharedMemoryPerMultiprocessor, cache, 48 * 1024);
+}
 
 inline unsigned ceil_div(int64_t a, int64_t b) { return static_cast<unsigned>((a + b - 1) / b); }
 

@@ -40,19 +40,59 @@ __global__ void transpose_kernel(const float* __restrict__ in, int rows, int col
   }
 }
 
-// Squared norms for candidate ranking only (FP32); also the largest norm.
+// Squared norms for candidate ranking only (FP32); also the largest norm
+// (nmax_bits[0]) and the largest coordinate magnitude (nmax_bits[1]).
 __global__ void norms_kernel(const float* __restrict__ P, int N, int d, int64_t ld,
                              float* __restrict__ nrm, unsigned int* __restrict__ nmax_bits) {
   const int lane = threadIdx.x & 31;
   const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   if (w >= N) return;
   const float* a = P + int64_t(w) * ld;
-  float s = 0.f;
-  for (int t = lane; t < d; t += 32) s = fmaf(a[t], a[t], s);
+  float s = 0.f, m = 0.f;
+  for (int t = lane; t < d; t += 32) {
+    s = fmaf(a[t], a[t], s);
+    m = fmaxf(m, fabsf(a[t]));
+  }
   s = warp_sumf(s);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
   if (lane == 0) {
     nrm[w] = s;
     atomicMax(nmax_bits, __float_as_uint(s));  // s >= 0: bit order = value order
+    atomicMax(nmax_bits + 1, __float_as_uint(m));
+  }
+}
+
+// Power-of-two scale of the half-precision operand copy and the terms of
+// the candidate error bound that it adds (see knn_tc_err_rel):
+// sc[0] = s = 2^e with max|x| s <= 2^14 (far inside the half range),
+// sc[1] = 1 / s^2 (ranking values back in the data's units),
+// sc[2] = 2 a sqrt(d) and sc[3] = 2 a^2 d, a = 2^-25 / s the largest
+// absolute rounding error of a coordinate that lands among the half
+// subnormals. Non-finite or zero data keep s = 1.
+__global__ void half_scale_kernel(const unsigned int* __restrict__ nmax_bits, int d, float* __restrict__ sc) {
+  const float m = __uint_as_float(nmax_bits[1]);
+  int e = 0;
+  if (m > 0.f && m < __int_as_float(0x7f800000)) {
+    int ex;
+    (void)frexpf(m, &ex);  // m = f 2^ex, f in [0.5, 1): m < 2^ex
+    e = min(max(14 - ex, -100), 100);
+  }
+  const double s = ldexp(1.0, e), a = ldexp(1.0, -25 - e);
+  sc[0] = float(s);
+  sc[1] = float(ldexp(1.0, -2 * e));
+  sc[2] = float(2.0 * a * sqrt(double(d)));
+  sc[3] = float(2.0 * a * a * double(d));
+}
+
+// H = half(s P), rows padded with zeros to ldh.
+__global__ void to_half_kernel(const float* __restrict__ P, int N, int d, int64_t ld, const float* __restrict__ sc,
+                               __half* __restrict__ H, int64_t ldh) {
+  const float s = sc[0];
+  const int64_t total = int64_t(N) * ldh;
+  for (int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; t < total; t += int64_t(gridDim.x) * blockDim.x) {
+    const int64_t i = t / ldh, k = t % ldh;
+    H[t] = __float2half_rn(k < d ? P[i * ld + k] * s : 0.f);
   }
 }
 
@@ -391,8 +431,9 @@ __device__ float resolve_knn(const float* __restrict__ P, int64_t ld, int d, boo
   return up;
 }
 
-// Recheck: warp per query. With e = err_rel (|q|^2 + max |b|^2) bounding
-// |ranking value - exact squared distance|, let a_K be the K-th smallest
+// Recheck: warp per query. With e = err_rel (|q|^2 + max |b|^2) (plus, for
+// the half-precision candidates, err_abs[0] (|q| + max |b|) + err_abs[1])
+// bounding |ranking value - exact squared distance|, let a_K be the K-th smallest
 // ranking value over all candidates. A candidate whose ranking value
 // exceeds a_K + 2e has exact distance > a_K + e, while the K candidates at
 // or below a_K have exact distance <= a_K + e, so it cannot be among the K
@@ -404,7 +445,7 @@ knn_recheck_kernel(const float* __restrict__ P, int N, int d, int64_t ld, bool v
                    int M, int splits, const int32_t* __restrict__ cand_i,
                    const float* __restrict__ cand_d, const float* __restrict__ nrm,
                    const unsigned int* __restrict__ nmax_bits, float err_rel,
-                   int32_t* __restrict__ out_i, float* __restrict__ out_d,
+                   const float* __restrict__ err_abs, int32_t* __restrict__ out_i, float* __restrict__ out_d,
                    int32_t* __restrict__ redo, int32_t* __restrict__ n_redo) {
   extern __shared__ double smd[];
   const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -416,7 +457,9 @@ knn_recheck_kernel(const float* __restrict__ P, int N, int d, int64_t ld, bool v
   const int q = blockIdx.x * RECHECK_WARPS + wib;
   if (q >= N) return;
   const float INF = __int_as_float(0x7f800000);
-  const float e = err_rel * (nrm[q] + __uint_as_float(*nmax_bits));
+  const float nbmax = __uint_as_float(*nmax_bits);
+  float e = err_rel * (nrm[q] + nbmax);
+  if (err_abs) e += err_abs[0] * (sqrtf(nrm[q]) + sqrtf(nbmax)) + err_abs[1];
   for (int c = lane; c < C; c += 32) {
     const int s = c / M, m = c % M;
     const int64_t o = (int64_t(s) * N + q) * M + m;
@@ -764,7 +807,9 @@ __global__ void assemble_kernel(int N, int lap_type, const int64_t* __restrict__
 struct KnnWs {
   float* Pt;          // transposed points (transposed input only)
   float* nrm;
-  unsigned int* nmax;
+  unsigned int* nmax;  // [largest squared norm, largest |coordinate|] (float bits)
+  __half* H;           // half-precision operand copy for the tensor-core pass
+  float* hsc;          // its scale and error terms (half_scale_kernel)
   int32_t* cand_i;
   float* cand_d;
   int32_t* kidx;      // N*K (used when the caller passes no knn_idx)
@@ -820,7 +865,9 @@ static KnnWs knn_layout(void* ws, int N, int d, int K, int transposed) {
   const int S = knn_splits(N, d), M = knn_M(K);
   w.Pt = transposed ? c.take<float>(size_t(N) * ((d + 3) & ~3)) : nullptr;
   w.nrm = c.take<float>(N);
-  w.nmax = c.take<unsigned int>(1);
+  w.nmax = c.take<unsigned int>(2);
+  w.H = c.take<__half>(size_t(N) * knn_half_ld(d));
+  w.hsc = c.take<float>(4);
   w.cand_i = c.take<int32_t>(size_t(S) * N * M);
   w.cand_d = c.take<float>(size_t(S) * N * M);
   w.kidx = c.take<int32_t>(size_t(N) * K);
@@ -853,14 +900,25 @@ cpca_status knn_lists(const float* P, int N, int d, int64_t ld, int K, const Knn
                       cudaStream_t st) {
   const int S = knn_splits(N, d), M = knn_M(K);
   const bool vec4 = (d % 4 == 0) && (ld % 4 == 0) && ((reinterpret_cast<uintptr_t>(P) & 15) == 0);
-  CPCA_CUDA(cudaMemsetAsync(w.nmax, 0, sizeof(unsigned int), st));
+  CPCA_CUDA(cudaMemsetAsync(w.nmax, 0, 2 * sizeof(unsigned int), st));
   CPCA_CUDA(cudaMemsetAsync(w.n_redo, 0, sizeof(int32_t), st));
   CPCA_PROF("knn_norms", st);
   norms_kernel<<<ceil_div(int64_t(N) * 32, 256), 256, 0, st>>>(P, N, d, ld, w.nrm, w.nmax);
   CPCA_LAUNCHED();
   bool done = false;
   CPCA_CUDA(cudaMemsetAsync(w.err, 0, sizeof(int), st));
-  CPCA_TRY(knn_candidates_tc(P, N, d, ld, M, S, w.nrm, w.cand_i, w.cand_d, w.err, &done, st));
+  if (knn_tc_supported(N, d, M)) {
+    // the operands in half precision (the same 11-bit significand as TF32,
+    // twice its tensor rate): a power-of-two scale, then the copy
+    half_scale_kernel<<<1, 1, 0, st>>>(w.nmax, d, w.hsc);
+    CPCA_LAUNCHED();
+    const int64_t ldh = knn_half_ld(d);
+    CPCA_PROF("knn_to_half", st);
+    to_half_kernel<<<unsigned(std::min<int64_t>(ceil_div(int64_t(N) * ldh, 256), int64_t(num_sms()) * 16)), 256, 0,
+                     st>>>(P, N, d, ld, w.hsc, w.H, ldh);
+    CPCA_LAUNCHED();
+    CPCA_TRY(knn_candidates_tc(w.H, N, d, ldh, w.hsc, M, S, w.nrm, w.cand_i, w.cand_d, w.err, &done, st));
+  }
   if (!done) {
     const size_t smem = sizeof(float) * (BD * BQ + BD * BB + BQ * (BB + 1)) + size_t(BQ) * M * 8;
     dim3 grid(ceil_div(N, BQ), S);
@@ -879,13 +937,15 @@ cpca_status knn_lists(const float* P, int N, int d, int64_t ld, int K, const Knn
   }
   // FP32 expansion error model for the certificate: about 4 sqrt(d) + 16
   // roundings of size 2^-24 relative to |a|^2 + |b|^2 (the tensor-core pass
-  // reports its own, larger, bound through knn_candidates_tc).
+  // has its own, larger, bound: knn_tc_err_rel plus the absolute terms of
+  // the half copy in hsc[2], hsc[3]).
   const float err_rel = done ? knn_tc_err_rel(d) : float((4.0 * sqrt(double(d)) + 16.0) * 0x1.0p-24);
+  const float* err_abs = done ? w.hsc + 2 : nullptr;
   const size_t rsm = size_t(RECHECK_WARPS) * S * M * 20;
   CPCA_CUDA(cudaFuncSetAttribute(knn_recheck_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(rsm)));
   CPCA_PROF("knn_recheck", st);
   knn_recheck_kernel<<<ceil_div(N, RECHECK_WARPS), RECHECK_WARPS * 32, rsm, st>>>(
-      P, N, d, ld, vec4, K, M, S, w.cand_i, w.cand_d, w.nrm, w.nmax, err_rel, out_i, out_d, w.redo,
+      P, N, d, ld, vec4, K, M, S, w.cand_i, w.cand_d, w.nrm, w.nmax, err_rel, err_abs, out_i, out_d, w.redo,
       w.n_redo);
   CPCA_LAUNCHED();
   // queries without a certificate: how many, then, within the budget,

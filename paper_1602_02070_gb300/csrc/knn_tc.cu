@@ -2,23 +2,24 @@
 //
 // For a block of 128 query points and, in turn, every 256-point base tile
 // of its split, the dot products q.b are computed on the 5th-generation
-// tensor cores (tcgen05.mma, kind::tf32, M = 128, N = 256, FP32 accumulate
-// in tensor memory); the ranking distance |q|^2 + |b|^2 - 2 q.b then feeds a
+// tensor cores (tcgen05.mma, kind::f16, M = 128, N = 256, FP32 accumulate
+// in tensor memory) on a half-precision copy of the points scaled by a
+// power of two: the 11-bit significand of TF32 at twice its tensor rate and
+// half its bytes. The ranking distance |q|^2 + |b|^2 - 2 q.b then feeds a
 // per-query list of the M smallest, kept in registers for M = 32 and in
-// shared memory for M = 64 (a per-lane bitmask
-// of the values under the current threshold limits the sorted insertions to
-// the few that can enter the list). These are only
-// candidates: knn.cu re-scores them with the exact FP32 squared distance and
-// certifies the result against the error bound returned by knn_tc_err_rel.
+// shared memory for M = 64 (a per-lane bitmask of the values under the
+// current threshold limits the sorted insertions to the few that can enter
+// the list). These are only candidates: knn.cu re-scores them with the
+// exact FP32 squared distance and certifies the result against the error
+// bound of knn_tc_err_rel plus the half copy's absolute terms.
 //
 // Warp roles (8 warps): warp 0 = TMA producer (one lane), warp 1 = tensor
 // memory allocator and MMA issuer (one lane), warps 4-7 = epilogue (warp w
 // reads TMEM lanes 32 (w % 4) .. +31, i.e. queries 32 (w - 4) .. +31).
-// Operands: K-major, 128-byte swizzle, 32 FP32 columns (128 B) per stage;
+// Operands: K-major, 128-byte swizzle, 64 half columns (128 B) per stage;
 // a ring of 4 (M = 32) or 3 (M = 64) stages of (A 16 KB + B 32 KB) guarded
-// by full/empty mbarriers; two
-// 256-column accumulators in TMEM (512 columns) so the epilogue of one base
-// tile overlaps the MMAs of the next. Every mbarrier wait is bounded: on
+// by full/empty mbarriers; two 256-column accumulators in TMEM (512
+// columns) so the epilogue of one base tile overlaps the MMAs of the next. Every mbarrier wait is bounded: on
 // timeout the block raises *err, stops, frees its TMEM and returns.
 // Clusters of CL = 2 blocks along the queries share every base tile: each
 // block loads 256/CL rows of it with a TMA multicast into every block of the
@@ -27,6 +28,7 @@
 // block (tcgen05.commit multicast), so a stage is refilled only when all
 // blocks of the cluster are done with it.
 #include <cuda.h>
+#include <cuda_fp16.h>
 
 #include "knn_internal.cuh"
 #include "tma.cuh"
@@ -34,14 +36,14 @@
 namespace cpca {
 namespace {
 
-constexpr int BM = 128, BN = 256, BK = 32, kMaxStages = 4;
+constexpr int BM = 128, BN = 256, BK = 64, kMaxStages = 4;  // BK: halves per 128-byte row
 // M = 32 keeps the per-query lists in registers, which leaves shared memory
 // for a fourth operand stage; M = 64 keeps them in shared memory (3 stages).
 template <int M>
 __host__ __device__ constexpr int stages_of() {
   return M == 32 ? 4 : 3;
 }
-constexpr int A_BYTES = BM * BK * 4, B_BYTES = BN * BK * 4, STAGE_BYTES = A_BYTES + B_BYTES;
+constexpr int A_BYTES = BM * BK * 2, B_BYTES = BN * BK * 2, STAGE_BYTES = A_BYTES + B_BYTES;
 constexpr uint32_t TMEM_COLS = 512;
 
 // UMMA shared-memory descriptor: K-major, 128-byte swizzle, 8-row atoms of
@@ -56,16 +58,17 @@ __device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
   return d;
 }
 
-// Instruction descriptor, kind::tf32: D F32, A/B TF32, both K-major, M x N.
-__host__ __device__ constexpr uint32_t tf32_idesc(int M, int N) {
-  return (1u << 4) | (2u << 7) | (2u << 10) | (uint32_t(N >> 3) << 17) | (uint32_t(M >> 4) << 24);
+// Instruction descriptor, kind::f16: D F32, A and B F16 (both the same
+// type), both K-major, M x N.
+__host__ __device__ constexpr uint32_t f16_idesc(int M, int N) {
+  return (1u << 4) | (0u << 7) | (0u << 10) | (uint32_t(N >> 3) << 17) | (uint32_t(M >> 4) << 24);
 }
 
-__device__ __forceinline__ void umma_tf32(uint32_t dtmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
-                                          uint32_t accumulate) {
+__device__ __forceinline__ void umma_f16(uint32_t dtmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t accumulate) {
   asm volatile(
       "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-      " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(dtmem),
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(dtmem),
       "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
       : "memory");
 }
@@ -129,8 +132,8 @@ struct TcShared {
 template <int M, int CL>
 __global__ void __launch_bounds__(256, 1)
 knn_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
-              int N, int d, const float* __restrict__ nrm, int splits, int32_t* __restrict__ cand_i,
-              float* __restrict__ cand_d, int* __restrict__ err) {
+              int N, int d, const float* __restrict__ nrm, const float* __restrict__ hsc, int splits,
+              int32_t* __restrict__ cand_i, float* __restrict__ cand_d, int* __restrict__ err) {
   // mapB boxes are BN / CL rows: this block's share of a base tile
   extern __shared__ __align__(1024) unsigned char raw[];
   // operand stages must be 1024-byte aligned for the 128-byte swizzle
@@ -208,7 +211,7 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ 
     }
   } else if (warp == 1) {
     if (lane == 0) {  // ------------------------------------------ MMA issuer
-      constexpr uint32_t idesc = tf32_idesc(BM, BN);
+      constexpr uint32_t idesc = f16_idesc(BM, BN);
       int it = 0;
       for (int t = 0; t < nt && !*abort; ++t) {
         const int buf = t & 1, use = t >> 1;
@@ -226,8 +229,8 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ 
           const uint32_t sa = smem_u32(stages + s * STAGE_BYTES);
           const uint64_t ad = sw128_desc(sa), bd = sw128_desc(sa + A_BYTES);
 #pragma unroll
-          for (int kk = 0; kk < BK / 8; ++kk)  // 8 TF32 (32 bytes) per MMA
-            umma_tf32(dt, ad + uint64_t(kk * 2), bd + uint64_t(kk * 2), idesc, (k | kk) ? 1u : 0u);
+          for (int kk = 0; kk < BK / 16; ++kk)  // 16 halves (32 bytes) per MMA
+            umma_f16(dt, ad + uint64_t(kk * 2), bd + uint64_t(kk * 2), idesc, (k | kk) ? 1u : 0u);
           if (CL > 1)
             umma_commit_mc(&sh.empty[s], cmask);
           else
@@ -261,6 +264,7 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ 
       }
     }
     float thr = __int_as_float(0x7f800000);
+    const float m2 = -2.f * hsc[1];  // -2 / s^2: products of the scaled copy back in data units
     const uint32_t lane_base = uint32_t((warp & 3) * 32) << 16;
     for (int t = 0; t < nt; ++t) {
       const int buf = t & 1, use = t >> 1;
@@ -277,7 +281,7 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ 
         uint32_t mask = 0;
 #pragma unroll
         for (int i = 0; i < 32; ++i) {
-          const float dd = fmaf(-2.f, __uint_as_float(r[i]), __shfl_sync(0xffffffffu, nbl, i));
+          const float dd = fmaf(m2, __uint_as_float(r[i]), __shfl_sync(0xffffffffu, nbl, i));
           stage_d[i * BM + ql] = dd;
           mask |= (dd < thr ? 1u : 0u) << i;
         }
@@ -349,14 +353,14 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ 
   if (threadIdx.x == 0 && sh.abort) atomicExch(err, 1);
 }
 
-bool make_map(CUtensorMap* map, const float* P, int N, int d, int64_t ld, int box_rows) {
+bool make_map(CUtensorMap* map, const __half* H, int N, int d, int64_t ldh, int box_rows) {
   EncodeTiledFn fn = encode_fn();
   if (!fn) return false;
   cuuint64_t dims[2] = {cuuint64_t(d), cuuint64_t(N)};
-  cuuint64_t strides[1] = {cuuint64_t(ld) * 4};
+  cuuint64_t strides[1] = {cuuint64_t(ldh) * 2};
   cuuint32_t box[2] = {cuuint32_t(BK), cuuint32_t(box_rows)};
   cuuint32_t estr[2] = {1, 1};
-  return fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(P), dims, strides, box, estr,
+  return fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, const_cast<__half*>(H), dims, strides, box, estr,
             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
@@ -377,14 +381,18 @@ size_t knn_tc_smem(int M) {
          sizeof(TcShared) + 64;
 }
 
-cpca_status knn_candidates_tc(const float* P, int N, int d, int64_t ld, int M, int S,
+int64_t knn_half_ld(int d) { return (int64_t(d) + 7) / 8 * 8; }
+
+bool knn_tc_supported(int N, int d, int M) {
+  return device_is_sm10x() && N >= 64 && d >= 16 && (M == 32 || M == 64) && encode_fn() != nullptr;
+}
+
+cpca_status knn_candidates_tc(const __half* H, int N, int d, int64_t ldh, const float* hsc, int M, int S,
                               const float* nrm, int32_t* cand_i, float* cand_d, int* err, bool* done,
                               cudaStream_t st) {
   *done = false;
-  // shapes where the tensor-core pass pays off and TMA's rules hold: row
-  // stride a multiple of 16 bytes, 16-byte aligned base
-  if (!device_is_sm10x() || N < 64 || d < 16 || (ld % 4) != 0 ||
-      (reinterpret_cast<uintptr_t>(P) & 15) != 0 || (M != 32 && M != 64))
+  // TMA's rules: row stride a multiple of 16 bytes, 16-byte aligned base
+  if (!knn_tc_supported(N, d, M) || (ldh % 8) != 0 || (reinterpret_cast<uintptr_t>(H) & 15) != 0)
     return CPCA_OK;
   // clusters of two query tiles share the base tiles once there are enough
   // query tiles to pair (the last pair may hold a tile past N: its A boxes
@@ -392,7 +400,7 @@ cpca_status knn_candidates_tc(const float* P, int N, int d, int64_t ld, int M, i
   const int qtiles = int(ceil_div(N, BM));
   const int CL = qtiles >= 8 ? 2 : 1;
   CUtensorMap mapA, mapB;
-  if (!make_map(&mapA, P, N, d, ld, BM) || !make_map(&mapB, P, N, d, ld, BN / CL)) return CPCA_OK;
+  if (!make_map(&mapA, H, N, d, ldh, BM) || !make_map(&mapB, H, N, d, ldh, BN / CL)) return CPCA_OK;
   const size_t smem = knn_tc_smem(M);
   const void* kern = M == 32 ? (CL == 2 ? (const void*)knn_tc_kernel<32, 2> : (const void*)knn_tc_kernel<32, 1>)
                              : (CL == 2 ? (const void*)knn_tc_kernel<64, 2> : (const void*)knn_tc_kernel<64, 1>);
@@ -412,7 +420,7 @@ cpca_status knn_candidates_tc(const float* P, int N, int d, int64_t ld, int M, i
   at[0].val.clusterDim.z = 1;
   cfg.attrs = at;
   cfg.numAttrs = 1;
-  void* args[] = {&mapA, &mapB, &N, &d, const_cast<float**>(&nrm), &S, &cand_i, &cand_d, &err};
+  void* args[] = {&mapA, &mapB, &N, &d, const_cast<float**>(&nrm), const_cast<float**>(&hsc), &S, &cand_i, &cand_d, &err};
   CPCA_PROF("knn_candidates_tc", st);
   CPCA_CUDA(cudaLaunchKernelExC(&cfg, kern, args));
   CPCA_LAUNCHED();
@@ -421,10 +429,14 @@ cpca_status knn_candidates_tc(const float* P, int N, int d, int64_t ld, int M, i
 }
 
 // Bound on |ranking distance - exact distance| / (|q|^2 + |b|^2) for the
-// TF32 pass: each operand keeps 10 explicit mantissa bits (relative error
-// <= 2^-10 each, so <= 2^-9 per product and |2 q.b| errs by <= 2^-8 |q||b|
-// <= 2^-9 (|q|^2 + |b|^2)), plus FP32 accumulation over d terms and the
-// FP32 norms, about (d + 8) roundings of 2^-24 each.
-float knn_tc_err_rel(int d) { return float(0x1.0p-9 + (double(d) + 8.0) * 0x1.0p-23); }
+// half-precision pass: each scaled coordinate is rounded to nearest with a
+// relative error <= 2^-11 (11-bit significand), so each product errs by
+// <= (2^-10 + 2^-22) |q_i b_i| and |2 q.b| by <= (2^-10 + 2^-22)
+// (|q|^2 + |b|^2); plus FP32 accumulation over d terms and the FP32 norms,
+// about (d + 8) roundings of 2^-24 each. Coordinates that fall among the
+// half subnormals err absolutely instead; that part of the bound depends
+// on the data's scale and is added per query from half_scale_kernel's
+// terms.
+float knn_tc_err_rel(int d) { return float(0x1.0p-10 + 0x1.0p-22 + (double(d) + 8.0) * 0x1.0p-23); }
 
 }  // namespace cpca

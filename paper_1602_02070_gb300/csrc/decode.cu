@@ -32,50 +32,89 @@ __global__ void omega_kernel(float* __restrict__ W, int rows, int b, uint64_t se
     W[t] = float(uniform01_at(s0, uint64_t(t) + 1) - 0.5);
 }
 
-// C (m x b) = A (m x n, lda) B (n x b, ld b). A block takes 8 ROWS rows of
-// A (a warp per ROWS rows), the lanes across the rows (coalesced); B comes
-// through shared memory in chunks of CHUNK rows (row stride b | 1, odd: the
-// lanes' rows fall on distinct banks), each B value serving the warp's
-// rows; every lane keeps partial sums of the b outputs of its rows, reduced
-// over the warp at the end. A is read once.
-template <int BB, int ROWS, int CHUNK>
+// C = sum over the chunks of P (nchunk x total floats), in chunk order.
+__global__ void gemm_tn_reduce(const float* __restrict__ P, int nchunk, int64_t total, float* __restrict__ C) {
+  for (int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; t < total;
+       t += int64_t(gridDim.x) * blockDim.x) {
+    float s = 0.f;
+    for (int q = 0; q < nchunk; ++q) s += P[int64_t(q) * total + t];
+    C[t] = s;
+  }
+}
+
+constexpr int kTnChunks = 64;  // row chunks (column slices) of the split skinny products
+
+// C (m x b) = A (m x n, lda) B (n x b, ld b). A block takes 16 rows of A
+// (two per warp) and one slice of the n columns (gridDim.y slices); B's rows
+// of the slice come through shared memory transposed (Bt[c][k]) in chunks of
+// CH. Each lane takes 4 consecutive columns of the chunk at a time (16-byte
+// loads when the rows allow them, every load of the chunk issued before the
+// products), so that A streams at full width; its partial sums of the
+// 2 x b outputs are reduced over the warp at the end (a fixed butterfly:
+// deterministic). One slice writes C; several write their partial products
+// to P + y m b, added in slice order by gemm_tn_reduce.
+template <int BB, int CH, bool VEC>
 __global__ void __launch_bounds__(256)
 gemm_nn_tall_k(const float* __restrict__ A, int64_t lda, int m, int n, const float* __restrict__ B, int b,
-               float* __restrict__ C) {
-  __shared__ float Bs[CHUNK * (BB + 1)];
+               float* __restrict__ C, int slice) {
+  __shared__ __align__(16) float Bt[BB][CH + 4];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int bs = b | 1;
-  const int i0 = (blockIdx.x * 8 + warp) * ROWS;
-  float acc[ROWS][BB];
+  const int i0 = blockIdx.x * 16 + warp * 2;
+  const int kbeg = blockIdx.y * slice, kend = min(n, kbeg + slice);
+  if (gridDim.y > 1) C += int64_t(blockIdx.y) * m * b;
+  const float* a0 = A + int64_t(min(i0, m - 1)) * lda;
+  const float* a1 = A + int64_t(min(i0 + 1, m - 1)) * lda;
+  float acc[2][BB];
 #pragma unroll
-  for (int r = 0; r < ROWS; ++r)
-#pragma unroll
-    for (int c = 0; c < BB; ++c) acc[r][c] = 0.f;
-  for (int k0 = 0; k0 < n; k0 += CHUNK) {
-    const int kn = min(CHUNK, n - k0);
+  for (int c = 0; c < BB; ++c) acc[0][c] = acc[1][c] = 0.f;
+  for (int k0 = kbeg; k0 < kend; k0 += CH) {
+    const int kn = min(CH, kend - k0);
     __syncthreads();
-    for (int e = threadIdx.x; e < kn * b; e += 256) {
-      const int k = e / b, c = e % b;
-      Bs[k * bs + c] = B[int64_t(k0 + k) * b + c];
+    for (int e = threadIdx.x; e < CH * b; e += 256) {
+      const int k = e / b, c = e - k * b;
+      Bt[c][k] = k < kn ? B[int64_t(k0 + k) * b + c] : 0.f;
     }
     __syncthreads();
-    for (int k = lane; k < kn; k += 32) {
-      float av[ROWS];
+    constexpr int NV = CH / 128;  // 4-column groups of the chunk per lane
+    float4 x0[NV], x1[NV];
 #pragma unroll
-      for (int r = 0; r < ROWS; ++r) av[r] = i0 + r < m ? __ldg(A + int64_t(i0 + r) * lda + k0 + k) : 0.f;
-      const float* bk = Bs + k * bs;
+    for (int t = 0; t < NV; ++t) {
+      const int k = t * 128 + lane * 4;  // within the chunk
+      if (VEC && k + 3 < kn) {
+        x0[t] = __ldg(reinterpret_cast<const float4*>(a0 + k0 + k));
+        x1[t] = __ldg(reinterpret_cast<const float4*>(a1 + k0 + k));
+      } else {
+        float v0[4], v1[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          v0[q] = k + q < kn ? __ldg(a0 + k0 + k + q) : 0.f;
+          v1[q] = k + q < kn ? __ldg(a1 + k0 + k + q) : 0.f;
+        }
+        x0[t] = make_float4(v0[0], v0[1], v0[2], v0[3]);
+        x1[t] = make_float4(v1[0], v1[1], v1[2], v1[3]);
+      }
+    }
+#pragma unroll
+    for (int t = 0; t < NV; ++t) {
+      const int k = t * 128 + lane * 4;
 #pragma unroll
       for (int c = 0; c < BB; ++c) {
         if (c < b) {
-          const float bv = bk[c];
-#pragma unroll
-          for (int r = 0; r < ROWS; ++r) acc[r][c] = fmaf(av[r], bv, acc[r][c]);
+          const float4 bv = *reinterpret_cast<const float4*>(&Bt[c][k]);
+          acc[0][c] = fmaf(x0[t].x, bv.x, acc[0][c]);
+          acc[0][c] = fmaf(x0[t].y, bv.y, acc[0][c]);
+          acc[0][c] = fmaf(x0[t].z, bv.z, acc[0][c]);
+          acc[0][c] = fmaf(x0[t].w, bv.w, acc[0][c]);
+          acc[1][c] = fmaf(x1[t].x, bv.x, acc[1][c]);
+          acc[1][c] = fmaf(x1[t].y, bv.y, acc[1][c]);
+          acc[1][c] = fmaf(x1[t].z, bv.z, acc[1][c]);
+          acc[1][c] = fmaf(x1[t].w, bv.w, acc[1][c]);
         }
       }
     }
   }
 #pragma unroll
-  for (int r = 0; r < ROWS; ++r)
+  for (int r = 0; r < 2; ++r)
 #pragma unroll
     for (int c = 0; c < BB; ++c) {
       if (c >= b) continue;
@@ -84,14 +123,46 @@ gemm_nn_tall_k(const float* __restrict__ A, int64_t lda, int m, int n, const flo
     }
 }
 
-static void gemm_nn_tall_launch(const float* A, int64_t lda, int m, int n, const float* B, int b, float* C,
-                                cudaStream_t st) {
-  if (b <= 16)
-    gemm_nn_tall_k<16, 4, 256><<<ceil_div(m, 32), 256, 0, st>>>(A, lda, m, n, B, b, C);
-  else if (b <= 32)
-    gemm_nn_tall_k<32, 4, 256><<<ceil_div(m, 32), 256, 0, st>>>(A, lda, m, n, B, b, C);
+// Slices of the n columns for C = A B: enough blocks for about two per SM,
+// each slice at least 512 columns, at most kTnChunks slices.
+static int nn_slices(int m, int n) {
+  const int rblocks = int(ceil_div(m, 16));
+  return std::max(1, std::min({kTnChunks, int(ceil_div(n, 512)), int(ceil_div(2 * num_sms(), rblocks))}));
+}
+
+template <int BB, int CH>
+static void gemm_nn_tall_run(dim3 g, const float* A, int64_t lda, int m, int n, const float* B, int b, float* C,
+                             int slice, bool vec, cudaStream_t st) {
+  if (vec)
+    gemm_nn_tall_k<BB, CH, true><<<g, 256, 0, st>>>(A, lda, m, n, B, b, C, slice);
   else
-    gemm_nn_tall_k<BMAX, 2, 128><<<ceil_div(m, 16), 256, 0, st>>>(A, lda, m, n, B, b, C);
+    gemm_nn_tall_k<BB, CH, false><<<g, 256, 0, st>>>(A, lda, m, n, B, b, C, slice);
+}
+
+// C (m x b) = A B, split over slices of n when A has few rows (scratch:
+// skinny_scratch_floats).
+static cpca_status nn_tall(const float* A, int64_t lda, int m, int n, const float* B, int b, float* C,
+                           float* scratch, cudaStream_t st) {
+  const int ns = nn_slices(m, n);
+  const int slice = ns == 1 ? n : int(ceil_div(ceil_div(n, ns), 128)) * 128;
+  const int nsl = int(ceil_div(n, slice));
+  const bool vec = (lda % 4) == 0 && (reinterpret_cast<uintptr_t>(A) & 15) == 0;
+  float* out = nsl > 1 ? scratch : C;
+  const dim3 g(unsigned(ceil_div(m, 16)), unsigned(nsl));
+  if (b <= 16)
+    gemm_nn_tall_run<16, 512>(g, A, lda, m, n, B, b, out, slice, vec, st);
+  else if (b <= 32)
+    gemm_nn_tall_run<32, 256>(g, A, lda, m, n, B, b, out, slice, vec, st);
+  else
+    gemm_nn_tall_run<BMAX, 128>(g, A, lda, m, n, B, b, out, slice, vec, st);
+  CPCA_LAUNCHED();
+  if (nsl > 1) {
+    const int64_t total = int64_t(m) * b;
+    gemm_tn_reduce<<<std::min<unsigned>(ceil_div(total, 256), num_sms() * 4), 256, 0, st>>>(scratch, nsl, total,
+                                                                                            C);
+    CPCA_LAUNCHED();
+  }
+  return CPCA_OK;
 }
 
 // C (n x b) = A^T B with A (m x n, lda), B (m x b, ld b): a thread per
@@ -143,25 +214,29 @@ static void gemm_tn_tall_launch(dim3 g, const float* A, int64_t lda, int m, int 
     gemm_tn_tall_k<BMAX><<<g, 256, 0, st>>>(A, lda, m, n, B, b, C, chunk);
 }
 
-// C = sum over the chunks of P (nchunk x total floats), in chunk order.
-__global__ void gemm_tn_reduce(const float* __restrict__ P, int nchunk, int64_t total, float* __restrict__ C) {
-  for (int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; t < total;
-       t += int64_t(gridDim.x) * blockDim.x) {
-    float s = 0.f;
-    for (int q = 0; q < nchunk; ++q) s += P[int64_t(q) * total + t];
-    C[t] = s;
-  }
+
+// Row chunks of A^T B: enough blocks for about two per SM, at most
+// kTnChunks chunks of at least 64 rows.
+static int tn_chunks(int m, int n) {
+  const int cblocks = int(ceil_div(n, 256));
+  return std::max(1, std::min({kTnChunks, int(ceil_div(m, 64)), int(ceil_div(2 * num_sms(), cblocks))}));
 }
 
-constexpr int kTnChunks = 16;  // row chunks of the split X~^T B products
+// Scratch (floats) of the split skinny products of an m x n matrix with b
+// columns on the other side: tn_tall's row chunks (chunks n b) or nn_tall's
+// column slices (slices m b).
+static size_t skinny_scratch_floats(int m, int n, int b) {
+  const int tc = tn_chunks(m, n), ns = nn_slices(m, n);
+  const size_t tn = tc > 1 ? size_t(tc) * n * b : 0, nn = ns > 1 ? size_t(ns) * m * b : 0;
+  return std::max<size_t>(1, std::max(tn, nn));
+}
 
 // C (n x b) = A^T B, split over row chunks when A is tall (scratch:
-// kTnChunks * n * b floats).
+// skinny_scratch_floats).
 static cpca_status tn_tall(const float* A, int64_t lda, int m, int n, const float* B, int b, float* C,
                            float* scratch, cudaStream_t st) {
-  // enough row chunks to give the GPU about two blocks per SM
   const int cblocks = int(ceil_div(n, 256));
-  const int chunks = std::max(1, std::min({kTnChunks, int(ceil_div(m, 64)), int(ceil_div(2 * num_sms(), cblocks))}));
+  const int chunks = tn_chunks(m, n);
   if (chunks == 1) {
     gemm_tn_tall_launch(dim3(cblocks, 1), A, lda, m, n, B, b, C, m, st);
     CPCA_LAUNCHED();
@@ -949,7 +1024,7 @@ static DecodeWs decode_layout(void* ws, int p, int n, int rr, int rc, int kmax, 
   w.Ut = c.take<float>(size_t(rr) * b);
   w.Vt = c.take<float>(size_t(rc) * b);
   w.G = c.take<double>(size_t(b) * b);
-  w.tn = c.take<float>(size_t(kTnChunks) * std::max(rr, rc) * std::max(b, kmax));
+  w.tn = c.take<float>(skinny_scratch_floats(rr, rc, std::max(b, kmax)));
   w.Rchol = c.take<double>(size_t(b) * b);
   w.rdiag = c.take<double>(b);
   w.dead = c.take<int>(b);
@@ -1036,8 +1111,7 @@ static cpca_status partial_svd(const float* Xt, int rr, int rc, int64_t ldxt, in
   auto to_long = [&](const float* in, float* out) -> cpca_status {
     CPCA_PROF("svd_gemm", st);
     if (vspace) {
-      gemm_nn_tall_launch(Xt, ldxt, rr, rc, in, b, out, st);
-      CPCA_LAUNCHED();
+      CPCA_TRY(nn_tall(Xt, ldxt, rr, rc, in, b, out, w.tn, st));
     } else {
       CPCA_TRY(tn_tall(Xt, ldxt, rr, rc, in, b, out, w.tn, st));
     }
@@ -1048,8 +1122,7 @@ static cpca_status partial_svd(const float* Xt, int rr, int rc, int64_t ldxt, in
     if (vspace) {
       CPCA_TRY(tn_tall(Xt, ldxt, rr, rc, in, b, out, w.tn, st));
     } else {
-      gemm_nn_tall_launch(Xt, ldxt, rr, rc, in, b, out, st);
-      CPCA_LAUNCHED();
+      CPCA_TRY(nn_tall(Xt, ldxt, rr, rc, in, b, out, w.tn, st));
     }
     return CPCA_OK;
   };
@@ -2017,15 +2090,11 @@ extern "C" cpca_status cpca_decode_backward(const float* Xt, int32_t rr, int32_t
   const float* VAb = vspace ? v.Vtb : v.Utb;
   auto applyA = [&](const float* in, float* out) -> cpca_status {  // out (mA x k) = A in (nA x k)
     if (!vspace) return tn_tall(Xt, ldxt, rr, rc, in, k, out, w.tn, st);
-    gemm_nn_tall_launch(Xt, ldxt, rr, rc, in, k, out, st);
-    CPCA_LAUNCHED();
-    return CPCA_OK;
+    return nn_tall(Xt, ldxt, rr, rc, in, k, out, w.tn, st);
   };
   auto applyAT = [&](const float* in, float* out) -> cpca_status {  // out (nA x k) = A^T in (mA x k)
     if (vspace) return tn_tall(Xt, ldxt, rr, rc, in, k, out, w.tn, st);
-    gemm_nn_tall_launch(Xt, ldxt, rr, rc, in, k, out, st);
-    CPCA_LAUNCHED();
-    return CPCA_OK;
+    return nn_tall(Xt, ldxt, rr, rc, in, k, out, w.tn, st);
   };
   CPCA_CUDA(cudaMemsetAsync(v.Ju, 0, sizeof(double) * k * k, st));
   CPCA_CUDA(cudaMemsetAsync(v.Jv, 0, sizeof(double) * k * k, st));
@@ -2091,7 +2160,7 @@ static size_t project_layout(int32_t p, int32_t n, int32_t ldb, float** W, float
                              void* ws) {
   Carve c(ws);
   float* w = c.take<float>(size_t(std::max(p, n)) * ldb);
-  float* sc = c.take<float>(size_t(kTnChunks) * n * ldb);
+  float* sc = c.take<float>(skinny_scratch_floats(p, n, ldb));
   double* o = c.take<double>(KMAX_LIMIT);
   if (W) *W = w;
   if (scratch) *scratch = sc;
@@ -2135,8 +2204,7 @@ extern "C" cpca_status cpca_subspace_project(int32_t side, const float* basis, i
     CPCA_TRY(launch_output(basis, ldb, W, ldb, ones, k, p, n, X, ldx, st));
   } else {
     CPCA_PROF("project_small", st);
-    gemm_nn_tall_launch(Y, ldy, p, n, basis, ldb, W, st);  // W = Y V (p x ldb)
-    CPCA_LAUNCHED();
+    CPCA_TRY(nn_tall(Y, ldy, p, n, basis, ldb, W, scr, st));  // W = Y V (p x ldb)
     CPCA_PROF("project_output", st);
     CPCA_TRY(launch_output(W, ldb, basis, ldb, ones, k, p, n, X, ldx, st));
   }

@@ -565,13 +565,13 @@ knn_recheck_kernel(const float* __restrict__ P, int N, int d, int64_t ld, bool v
 
 // Brute force for queries without a certificate, spread over the grid.
 // Work item (r, c): redo query r of the batch [r0, r0 + nq) against points
-// [c * kBfChunk, (c + 1) * kBfChunk), one warp per item, every point scored
+// [c * chunk, (c + 1) * chunk), one warp per item, every point scored
 // with the same exact FP32 function; the warp keeps the 32 nearest by
 // (d2, j) (lane l holds entry l, insertion by ballot) and writes them to
 // lists[r][c]. knn_bf_merge_kernel then takes, per query, the 32 nearest of
 // all its chunk lists and lets resolve_knn pick the K (FP64 where FP32 cannot
 // decide; a tie run longer than the 32 kept is cut at the 32nd).
-constexpr int kBfChunk = 512;
+constexpr int kBfChunkMin = 32, kBfChunkMax = 512;  // points per work item
 constexpr int kBfBatch = 64;  // queries per brute-force pass
 
 __device__ __forceinline__ void warp_list_insert(float& ld_, int& li, float v, int j) {
@@ -594,10 +594,10 @@ __device__ __forceinline__ void warp_list_insert(float& ld_, int& li, float v, i
 
 __global__ void __launch_bounds__(RECHECK_WARPS * 32)
 knn_bf_score_kernel(const float* __restrict__ P, int N, int d, int64_t ld, bool vec4,
-                    const int32_t* __restrict__ redo, int r0, int nq, float* __restrict__ lists_d,
+                    const int32_t* __restrict__ redo, int r0, int nq, int chunk, float* __restrict__ lists_d,
                     int32_t* __restrict__ lists_i) {
   const int lane = threadIdx.x & 31;
-  const int nch = (N + kBfChunk - 1) / kBfChunk;
+  const int nch = (N + chunk - 1) / chunk;
   const int64_t items = int64_t(nq) * nch;
   for (int64_t w = int64_t(blockIdx.x) * RECHECK_WARPS + (threadIdx.x >> 5); w < items;
        w += int64_t(gridDim.x) * RECHECK_WARPS) {
@@ -606,12 +606,19 @@ knn_bf_score_kernel(const float* __restrict__ P, int N, int d, int64_t ld, bool 
     const float* a = P + int64_t(q) * ld;
     float dl = __int_as_float(0x7f800000);
     int il = -1;
-    const int j1 = min(N, (c + 1) * kBfChunk);
-    for (int j = c * kBfChunk; j < j1; ++j) {
-      if (j == q) continue;
-      float v = exact_d2_warp(a, P + int64_t(j) * ld, d, vec4);
-      if (v != v) v = __int_as_float(0x7f800000);
-      warp_list_insert(dl, il, v, j);
+    const int j1 = min(N, (c + 1) * chunk);
+    for (int j0 = c * chunk; j0 < j1; j0 += kRecheckGroup) {  // eight points per pass
+      const int n = min(kRecheckGroup, j1 - j0);
+      int jj[kRecheckGroup];
+#pragma unroll
+      for (int g = 0; g < kRecheckGroup; ++g) jj[g] = j0 + min(g, n - 1);
+      float v[kRecheckGroup];
+      exact_d2_warp_group<kRecheckGroup>(a, P, ld, jj, n, d, vec4, v);
+#pragma unroll
+      for (int g = 0; g < kRecheckGroup; ++g) {
+        if (g >= n || j0 + g == q) continue;  // warp-uniform
+        warp_list_insert(dl, il, v[g] != v[g] ? __int_as_float(0x7f800000) : v[g], j0 + g);
+      }
     }
     lists_d[w * 32 + lane] = dl;
     lists_i[w * 32 + lane] = il;
@@ -620,7 +627,7 @@ knn_bf_score_kernel(const float* __restrict__ P, int N, int d, int64_t ld, bool 
 
 __global__ void __launch_bounds__(RECHECK_WARPS * 32)
 knn_bf_merge_kernel(const float* __restrict__ P, int N, int d, int64_t ld, bool vec4, int K,
-                    const int32_t* __restrict__ redo, int r0, int nq, const float* __restrict__ lists_d,
+                    const int32_t* __restrict__ redo, int r0, int nq, int chunk, const float* __restrict__ lists_d,
                     const int32_t* __restrict__ lists_i, int32_t* __restrict__ out_i,
                     float* __restrict__ out_d) {
   __shared__ double l64[RECHECK_WARPS][32];
@@ -630,7 +637,7 @@ knn_bf_merge_kernel(const float* __restrict__ P, int N, int d, int64_t ld, bool 
   const int r = blockIdx.x * RECHECK_WARPS + wib;
   if (r >= nq) return;
   const int q = redo[r0 + r];
-  const int nch = (N + kBfChunk - 1) / kBfChunk;
+  const int nch = (N + chunk - 1) / chunk;
   float dl = __int_as_float(0x7f800000);
   int il = -1;
   for (int c = 0; c < nch; ++c) {
@@ -875,7 +882,7 @@ static KnnWs knn_layout(void* ws, int N, int d, int K, int transposed) {
   w.redo = c.take<int32_t>(N);
   w.n_redo = c.take<int32_t>(1);
   {
-    const size_t lists = size_t(kBfBatch) * ((N + kBfChunk - 1) / kBfChunk) * 32;
+    const size_t lists = size_t(kBfBatch) * ((N + kBfChunkMin - 1) / kBfChunkMin) * 32;
     w.bf_d = c.take<float>(lists);
     w.bf_i = c.take<int32_t>(lists);
   }
@@ -965,13 +972,18 @@ cpca_status knn_lists(const float* P, int N, int d, int64_t ld, int K, const Knn
   *n_bruteforce = nredo;
   for (int r0 = 0; r0 < nredo; r0 += kBfBatch) {
     const int nq = std::min(kBfBatch, nredo - r0);
-    const int64_t items = int64_t(nq) * ((N + kBfChunk - 1) / kBfChunk);
+    // points per work item: enough items for about 32 warps per SM
+    const int64_t want = int64_t(num_sms()) * 32;
+    const int chunk = int(std::min<int64_t>(
+        kBfChunkMax, std::max<int64_t>(kBfChunkMin, (ceil_div(int64_t(N) * nq, want) + 31) / 32 * 32)));
+    const int64_t items = int64_t(nq) * ((N + chunk - 1) / chunk);
     const unsigned grid = unsigned(std::min<int64_t>((items + RECHECK_WARPS - 1) / RECHECK_WARPS, num_sms() * 16));
     CPCA_PROF("knn_bruteforce", st);
-    knn_bf_score_kernel<<<grid, RECHECK_WARPS * 32, 0, st>>>(P, N, d, ld, vec4, w.redo, r0, nq, w.bf_d, w.bf_i);
+    knn_bf_score_kernel<<<grid, RECHECK_WARPS * 32, 0, st>>>(P, N, d, ld, vec4, w.redo, r0, nq, chunk, w.bf_d,
+                                                              w.bf_i);
     CPCA_LAUNCHED();
     knn_bf_merge_kernel<<<ceil_div(nq, RECHECK_WARPS), RECHECK_WARPS * 32, 0, st>>>(
-        P, N, d, ld, vec4, K, w.redo, r0, nq, w.bf_d, w.bf_i, out_i, out_d);
+        P, N, d, ld, vec4, K, w.redo, r0, nq, chunk, w.bf_d, w.bf_i, out_i, out_d);
     CPCA_LAUNCHED();
   }
   return CPCA_OK;

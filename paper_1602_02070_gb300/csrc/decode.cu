@@ -70,9 +70,20 @@ gemm_nn_tall_k(const float* __restrict__ A, int64_t lda, int m, int n, const flo
   for (int k0 = kbeg; k0 < kend; k0 += CH) {
     const int kn = min(CH, kend - k0);
     __syncthreads();
-    for (int e = threadIdx.x; e < CH * b; e += 256) {
-      const int k = e / b, c = e - k * b;
-      Bt[c][k] = k < kn ? B[int64_t(k0 + k) * b + c] : 0.f;
+    {  // thread -> (column c = tid % BB, rows tid / BB + 256 / BB q), eight loads in flight
+      constexpr int RSTEP = 256 / BB, NQ = CH / RSTEP;
+      const int c = threadIdx.x % BB, kq = threadIdx.x / BB;
+#pragma unroll 1
+      for (int q0 = 0; q0 < NQ; q0 += 8) {
+        float v[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          const int k = kq + (q0 + q) * RSTEP;
+          v[q] = (c < b && k < kn) ? __ldg(B + int64_t(k0 + k) * b + c) : 0.f;
+        }
+#pragma unroll
+        for (int q = 0; q < 8; ++q) Bt[c][kq + (q0 + q) * RSTEP] = v[q];
+      }
     }
     __syncthreads();
     constexpr int NV = CH / 128;  // 4-column groups of the chunk per lane
@@ -191,7 +202,17 @@ gemm_tn_tall_k(const float* __restrict__ A, int64_t lda, int m, int n, const flo
     }
     __syncthreads();
     if (j < n) {
-      for (int r = 0; r < rn; ++r) {
+      int r = 0;
+      for (; r + 8 <= rn; r += 8) {  // eight rows' loads in flight
+        float a[8];
+#pragma unroll
+        for (int t = 0; t < 8; ++t) a[t] = __ldg(A + int64_t(i0 + r + t) * lda + j);
+#pragma unroll
+        for (int t = 0; t < 8; ++t)
+#pragma unroll
+          for (int c = 0; c < BB; ++c) acc[c] = fmaf(a[t], Bs[r + t][c], acc[c]);
+      }
+      for (; r < rn; ++r) {
         const float a = __ldg(A + int64_t(i0 + r) * lda + j);
 #pragma unroll
         for (int c = 0; c < BB; ++c) acc[c] = fmaf(a, Bs[r][c], acc[c]);

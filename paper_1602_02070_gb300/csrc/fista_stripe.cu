@@ -79,6 +79,7 @@ struct StripeArgs {
   int64_t ldzt;
   float two_gr, two_gc, mu;
   int rr, rc, nstripes;
+  int nfull, nunits;  // work units: whole stripes [0, nfull), then halves of the rest
   int j, J;
   double eps;
   int want_stats;
@@ -165,19 +166,26 @@ __global__ void __launch_bounds__(Shape<W>::ST, Shape<W>::BLOCKS)
   const int64_t rbase = a.Lr.rowptr[0];
   for (int i = tid; i <= a.rr; i += ST) rowp[i] = int32_t(a.Lr.rowptr[i] - rbase);
   __syncthreads();
-  auto issue = [&](int s) {  // one thread: the whole stripe s into the buffer
-    const char* src = reinterpret_cast<const char*>(a.Zin + int64_t(s) * a.rr * W);
+  // unit u: stripe u (u < nfull), else the half (u - nfull) % 2 of stripe
+  // nfull + (u - nfull) / 2, rows [0, rh) or [rh, rr) (the last wave of
+  // stripes in halves, so that blocks finish closer together)
+  const int rh = ((a.rr + 1) / 2 + 3) / 4 * 4;
+  auto unit_stripe = [&](int u) { return u < a.nfull ? u : a.nfull + (u - a.nfull) / 2; };
+  auto issue = [&](int u) {  // one thread: the whole stripe of unit u into the buffer
+    const char* src = reinterpret_cast<const char*>(a.Zin + int64_t(unit_stripe(u)) * a.rr * W);
     mbar_expect_tx(&sm.mbar, stripe_bytes);
     for (uint32_t o = 0; o < stripe_bytes; o += kBulk)
       bulk_load(reinterpret_cast<char*>(zs) + o, src + o, min(kBulk, stripe_bytes - o), &sm.mbar);
   };
-  if (tid == 0 && int(blockIdx.x) < a.nstripes) issue(blockIdx.x);
+  if (tid == 0 && int(blockIdx.x) < a.nunits) issue(blockIdx.x);
   double dz = 0.0, nz = 0.0;
   int k = 0;
-  // the first stripe of a block is its index; then blocks take the next
-  // untaken stripe as they finish (stripes with hub columns cost more)
-  for (int s = blockIdx.x; s < a.nstripes; ++k) {
-    const int c0 = s * W;
+  // the first unit of a block is its index; then blocks take the next
+  // untaken unit as they finish (stripes with hub columns cost more)
+  for (int u = blockIdx.x; u < a.nunits; ++k) {
+    const int s = unit_stripe(u), c0 = s * W;
+    const int rlo = u < a.nfull || ((u - a.nfull) & 1) == 0 ? 0 : rh;
+    const int rhi = u < a.nfull || ((u - a.nfull) & 1) == 1 ? a.rr : rh;
     // neighbour lists of the stripe's columns, into the pool as far as it
     // holds them (the rest is read from the CSR as it is needed)
     if (tid < W) {
@@ -213,8 +221,8 @@ __global__ void __launch_bounds__(Shape<W>::ST, Shape<W>::BLOCKS)
     }
     __syncthreads();
     bool loaded = false;
-    for (int r0 = 0; r0 < a.rr; r0 += RC) {
-      const int nr = min(RC, a.rr - r0);
+    for (int r0 = rlo; r0 < rhi; r0 += RC) {
+      const int nr = min(RC, rhi - r0);
       // ---- (Z Lc): items (column, row block) taken by the warps in turn: a
       // column with a short list in 128-row items (a lane per 4 rows, 16-byte
       // loads), one with a long list in 32-row items (a lane per row), so
@@ -240,15 +248,15 @@ __global__ void __launch_bounds__(Shape<W>::ST, Shape<W>::BLOCKS)
             if (i < a.ldzt) {
               int q = 0;
               for (; q + 8 <= ds; q += 8) {
-                int2 pe[8];
-                float x[8];
+                float wt[8], x[8];
 #pragma unroll
                 for (int t = 0; t < 8; ++t) {
-                  pe[t] = sm.pool[b0 + q + t];
-                  x[t] = __ldg(a.ZTin + pe[t].x + i);
+                  const int2 pe = sm.pool[b0 + q + t];
+                  x[t] = __ldg(a.ZTin + pe.x + i);
+                  wt[t] = __int_as_float(pe.y);
                 }
 #pragma unroll
-                for (int t = 0; t < 8; ++t) u = fmaf(__int_as_float(pe[t].y), x[t], u);
+                for (int t = 0; t < 8; ++t) u = fmaf(wt[t], x[t], u);
               }
               for (; q < ds; ++q) {
                 const int2 pe = sm.pool[b0 + q];
@@ -264,16 +272,17 @@ __global__ void __launch_bounds__(Shape<W>::ST, Shape<W>::BLOCKS)
             float4 u = make_float4(0.f, 0.f, 0.f, 0.f);
             if (i < a.ldzt) {  // then i + 3 < ldzt (both multiples of 4)
               int q = 0;
-              for (; q + 4 <= ds; q += 4) {  // four neighbours' loads in flight
-                int2 pe[4];
-                float4 x[4];
+              for (; q + 8 <= ds; q += 8) {  // eight neighbours' loads in flight
+                float wt[8];
+                float4 x[8];
 #pragma unroll
-                for (int t = 0; t < 4; ++t) {
-                  pe[t] = sm.pool[b0 + q + t];
-                  x[t] = ldg4(a.ZTin + pe[t].x + i);
+                for (int t = 0; t < 8; ++t) {
+                  const int2 pe = sm.pool[b0 + q + t];
+                  x[t] = ldg4(a.ZTin + pe.x + i);
+                  wt[t] = __int_as_float(pe.y);
                 }
 #pragma unroll
-                for (int t = 0; t < 4; ++t) fma4(u, __int_as_float(pe[t].y), x[t]);
+                for (int t = 0; t < 8; ++t) fma4(u, wt[t], x[t]);
               }
               for (; q < ds; ++q) {
                 const int2 pe = sm.pool[b0 + q];
@@ -357,13 +366,13 @@ __global__ void __launch_bounds__(Shape<W>::ST, Shape<W>::BLOCKS)
     if (tid == 0) {
       const int nx = int(gridDim.x + atomicAdd(a.ctr + a.j % 3, 1u));
       sm.next_stripe = nx;
-      if (nx < a.nstripes) {
+      if (nx < a.nunits) {
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         issue(nx);
       }
     }
     __syncthreads();
-    s = sm.next_stripe;
+    u = sm.next_stripe;
   }
   if (sm.abort) {
     // the copy of stripe k may still be in flight: wait for it (bounded)
@@ -552,6 +561,12 @@ cpca_status stripe_solve(const BatchProblem& P, const InstWs& iw, const StripeWs
   a.rr = rr;
   a.rc = rc;
   a.nstripes = nst;
+  {
+    const int blocks = std::min(nst, Shape<W>::BLOCKS * num_sms());
+    const int nhalf = rr >= 8 ? blocks : 0;  // the last wave's stripes, in halves
+    a.nfull = nst - nhalf;
+    a.nunits = a.nfull + 2 * nhalf;
+  }
   a.J = J;
   a.eps = eps;
   const int grid = std::min(nst, Shape<W>::BLOCKS * num_sms());

@@ -149,12 +149,15 @@ def oracle_setup(Yh, cfg, threads):
         idx, d2 = knn_c(gen.latent_points(seed, N, 20, C), K, threads=threads)
         full.append(O.laplacian_from_knn(idx, d2, N, O.sigma2_mean(d2))[0])
     Ut, s_, Vh, k = O.svd_rank(Yt32.astype(np.float64))
+    svd = (Ut, s_, Vh, k)
     its = []
     for L, om, R in ((full[0], om_r, Ut[:, :1]), (full[1], om_c, Vh[:1].T)):
         _, it, _ = O.upsample_subspace(L, om, R, cfg["cg_tol"])
         its.append(int(it[0]))
     return {"om_r": om_r, "om_c": om_c, "Yt": Yt32.astype(np.float64), "Lrt": graphs[0], "Lct": graphs[1],
-            "lam": lam, "Lr": full[0], "Lc": full[1], "cg_iters": its, "k": k}
+            "lam": lam, "Lr": full[0], "Lc": full[1], "cg_iters": its, "k": k,
+            "YhT": np.ascontiguousarray(Yh.T), "svd": svd,
+            "lap_knn": knn_c(Yt32, K, queries=np.arange(min(2000, Yt32.shape[0])), threads=threads)}
 
 
 def oracle_step_seconds(Yh, cfg, setup, threads, sample, rng_seed=0):
@@ -168,14 +171,12 @@ def oracle_step_seconds(Yh, cfg, setup, threads, sample, rng_seed=0):
     parts = {}
     nq = sample["knn_queries"]
     t = 0.0
-    for P in (Yh, None):
-        P = np.ascontiguousarray(Yh.T) if P is None else P
+    for P in (Yh, setup["YhT"]):  # points = rows, then columns (the transposed copy of the set-up)
         N = P.shape[0]
         qs = rng.choice(N, size=min(nq, N), replace=False)
         t0 = time.perf_counter()
         knn_c(P, K, queries=qs, threads=threads)
         t += (time.perf_counter() - t0) * N / len(qs)
-        del P
     parts["knn_full"] = t
     t0 = time.perf_counter()
     om_r, om_c = O.sample_indices(0, p, len(setup["om_r"]), 0), O.sample_indices(0, n, len(setup["om_c"]), 1)
@@ -189,7 +190,7 @@ def oracle_step_seconds(Yh, cfg, setup, threads, sample, rng_seed=0):
         idx, d2 = knn_c(P, K, queries=qs, threads=threads)
         t += (time.perf_counter() - t0) * N / len(qs)
     parts["knn_compressed"] = t
-    idx, d2 = knn_c(Yt.astype(np.float32), K, queries=np.arange(min(2000, Yt.shape[0])), threads=threads)
+    idx, d2 = setup["lap_knn"]
     t0 = time.perf_counter()
     O.laplacian_from_knn(idx, d2, Yt.shape[0], O.sigma2_mean(d2))
     parts["laplacians"] = (time.perf_counter() - t0) * (p + n + Yt.shape[0] + Yt.shape[1]) / idx.shape[0]
@@ -202,9 +203,13 @@ def oracle_step_seconds(Yh, cfg, setup, threads, sample, rng_seed=0):
     frpcag_fista_c(setup["Yt"], setup["Lrt"], setup["Lct"], cfg["gamma_r"], cfg["gamma_c"], setup["lam"], fi,
                    threads=threads)
     parts["fista"] = (time.perf_counter() - t0) * J / fi
+    sr = sample.get("svd_rows")
+    Ytr = setup["Yt"] if not sr else setup["Yt"][: min(sr, setup["Yt"].shape[0])]
     t0 = time.perf_counter()
-    Ut, s_, Vh, k = O.svd_rank(setup["Yt"])
-    parts["svd"] = time.perf_counter() - t0
+    O.svd_rank(Ytr)
+    # a dense SVD of an m x n matrix (m <= n) costs about m^2 n
+    parts["svd"] = (time.perf_counter() - t0) * (setup["Yt"].shape[0] / Ytr.shape[0]) ** 2
+    Ut, s_, Vh, k = setup["svd"]
     ci = sample["cg_iters"]
     t = 0.0
     for L, om, R, need in ((setup["Lr"], setup["om_r"], Ut[:, :k], setup["cg_iters"][0]),
@@ -228,13 +233,15 @@ def cpu_sample_text(sample):
             f"queries per graph and scaled to all points; compressed-graph kNN on {4 * sample['knn_queries']} "
             "queries per graph, scaled; Laplacian construction timed on 2000 lists and scaled by point "
             f"count; sampling and the power iterations in full; FISTA (C oracle) {sample['fista_iters']} "
-            "iterations scaled to all; SVD of X~ in full; PCG (numpy oracle) "
+            "iterations scaled to all; SVD of X~ "
+            + (f"on its first {sample['svd_rows']} rows, scaled by the square of the row ratio"
+               if sample.get("svd_rows") else "in full") + "; PCG (numpy oracle) "
             f"{sample['cg_iters']} iterations per side on full-size graphs of the workload's model, scaled "
             f"by the oracle's own iteration count; X = U S V^T on {sample['out_rows']} rows, scaled")
 
 
 CPU_SAMPLE = {"knn_queries": 16, "fista_iters": 2, "cg_iters": 20, "out_rows": 512}
-REF_SAMPLE = {"knn_queries": 16, "fista_iters": 1, "cg_iters": 10, "out_rows": 256}
+REF_SAMPLE = {"knn_queries": 2, "fista_iters": 1, "cg_iters": 10, "out_rows": 256, "svd_rows": 500}
 
 
 def run_cpu_leg(cfg, threads):

@@ -145,9 +145,18 @@ inline int max_smem_optin() {
   static std::atomic<int> cache[kMaxDevices];
   return device_attr(cudaDevAttrMaxSharedMemoryPerBlockOptin, cache, 48 * 1024);
 }
-inline int max_smem_per_sm() {
-  static std::atomic<int> cache[kMaxDevices];
-  return device_attr(cudaDevAttrMaxSharedMemoryPerMultiprocessor, cache, 48 * 1024);
+
+// A per-device value (>= 0) computed once by fn() on each device.
+template <class F>
+int cached_per_device(std::atomic<int>* cache, F&& fn) {
+  const int dev = current_device();
+  if (dev < kMaxDevices) {
+    const int v = cache[dev].load(std::memory_order_relaxed);
+    if (v > 0) return v - 1;
+  }
+  const int v = fn();
+  if (dev < kMaxDevices) cache[dev].store(v + 1, std::memory_order_relaxed);
+  return v;
 }
 
 inline unsigned ceil_div(int64_t a, int64_t b) { return static_cast<unsigned>((a + b - 1) / b); }

@@ -194,10 +194,10 @@ struct PowRow {
   const int2* el;
 
   __device__ __forceinline__ void init(const PowerBatchArgs& a, int nvw, int2* ell, int ell_cap,
-                                       int crank) {
+                                       int crank, int nctas = kPowCtas) {
     lane = threadIdx.x & 31;
     const int lw = threadIdx.x >> 5, nlw = blockDim.x >> 5;
-    vw = lw * kPowCtas + crank;
+    vw = lw * nctas + crank;
     wact = vw < nvw;
     G = &a.g[wact ? find_graph_warp(a, vw) : 0];
     i = (vw - G->w0) * 32 + lane;
@@ -247,8 +247,11 @@ __device__ __forceinline__ void allgather32(float v, float* xr0, float* xr1, int
   *reinterpret_cast<float4*>(xr1 + off0 + 4 * ch) = v4;
 }
 
-// Forward. With G.U set, also keeps u_0..u_T and |u_t|^2 (reverse mode).
-__global__ void __cluster_dims__(kPowCtas, 1, 1) __launch_bounds__(1024)
+// Forward, on a cluster of C CTAs (8, or 16 where the device allows that
+// non-portable cluster size; the launch sets the cluster shape). With G.U
+// set, also keeps u_0..u_T and |u_t|^2 (reverse mode).
+template <int C>
+__global__ void __launch_bounds__(1024)
 power_cluster_kernel(const __grid_constant__ PowerBatchArgs a, int nvw, int ell_cap) {
   namespace cg = cooperative_groups;
   cg::cluster_group cl = cg::this_cluster();
@@ -260,7 +263,7 @@ power_cluster_kernel(const __grid_constant__ PowerBatchArgs a, int nvw, int ell_
   float* xv = reinterpret_cast<float*>(rq + 2 * nvw);  // [2][NV]: the iterate
   int2* ell = reinterpret_cast<int2*>(xv + 2 * NV);
   PowRow R;
-  R.init(a, nvw, ell, ell_cap, crank);
+  R.init(a, nvw, ell, ell_cap, crank, C);
   const PowerGraph& G = *R.G;
   const int lane = R.lane, lw = threadIdx.x >> 5, nlw = blockDim.x >> 5, vw = R.vw;
   // u_0 and the warp sums of its squares (FP64, before rounding), computed
@@ -283,9 +286,12 @@ power_cluster_kernel(const __grid_constant__ PowerBatchArgs a, int nvw, int ell_
   }
   if (R.valid && G.U)
     G.U[R.i] = float(uniform01_at(stream_state0(a.seed, G.stream), uint64_t(R.i) + 1) - 0.5);
-  float* xr0 = cl.map_shared_rank(xv, lane >> 3);
-  float* xr1 = cl.map_shared_rank(xv, (lane >> 3) + 4);
-  double* wr = cl.map_shared_rank(wq, lane & 7);
+  // lane l sends float4 chunk (l & 7) of its warp's values to CTAs
+  // (l >> 3) + 4 t, t < C / 4, and its warp sum to CTA l % C
+  float* xr[C / 4];
+#pragma unroll
+  for (int t = 0; t < C / 4; ++t) xr[t] = cl.map_shared_rank(xv, (lane >> 3) + 4 * t);
+  double* wr = cl.map_shared_rank(wq, lane & (C - 1));
   cl.sync();  // all CTAs running and initialised before any remote write
   for (int k = 0; k < a.iters; ++k) {
     const int cur = k & 1, nxt = cur ^ 1;
@@ -295,9 +301,18 @@ power_cluster_kernel(const __grid_constant__ PowerBatchArgs a, int nvw, int ell_
       const float inv = n2 > 0 ? rsqrtf(float(n2)) : 0.f;  // only the direction matters
       const float s = R.valid ? R.spmv(xv + cur * NV) * inv : 0.f;
       if (R.valid && G.U) G.U[size_t(k + 1) * G.L.n + R.i] = s;
-      allgather32(s, xr0, xr1, nxt * NV + vw * 32, lane);
+      {
+        const int ch = lane & 7;
+        float4 v4;
+        v4.x = __shfl_sync(0xffffffffu, s, 4 * ch);
+        v4.y = __shfl_sync(0xffffffffu, s, 4 * ch + 1);
+        v4.z = __shfl_sync(0xffffffffu, s, 4 * ch + 2);
+        v4.w = __shfl_sync(0xffffffffu, s, 4 * ch + 3);
+#pragma unroll
+        for (int t = 0; t < C / 4; ++t) *reinterpret_cast<float4*>(xr[t] + nxt * NV + vw * 32 + 4 * ch) = v4;
+      }
       const double q = warp_sum(double(s) * double(s));
-      if (lane < kPowCtas) wr[nxt * nvw + vw] = q;
+      if (lane < C) wr[nxt * nvw + vw] = q;
     }
     cl.sync();
   }
@@ -1089,10 +1104,63 @@ size_t power_scratch_bytes(const int* n, int ng) {
 // opt-in shared memory, the CSR entries the rest), else (forward only) the
 // grid-wide kernel on `scratch`. *done = false: reverse asked beyond one
 // cluster (nothing launched).
+template <int C>
+static cudaError_t launch_power_cluster(const PowerBatchArgs& pa, int nvw, int ell_cap, size_t psm,
+                                       cudaStream_t st) {
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = dim3(C);
+  cfg.blockDim = dim3(32 * ((nvw + C - 1) / C));
+  cfg.dynamicSmemBytes = psm;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = C;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  int nv = nvw, ec = ell_cap;
+  void* args[] = {const_cast<PowerBatchArgs*>(&pa), &nv, &ec};
+  return cudaLaunchKernelExC(&cfg, (const void*)power_cluster_kernel<C>, args);
+}
+
+// Whether a 16-CTA cluster of the forward kernel can run on this device
+// (a non-portable cluster size), with the attributes it needs set.
+static bool power_cluster16_ok(size_t psm) {
+  static std::atomic<int> ok[kMaxDevices];
+  return cached_per_device(ok, [&] {
+    const void* k = (const void*)power_cluster_kernel<16>;
+    if (cudaFuncSetAttribute(k, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess ||
+        cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(psm)) != cudaSuccess) {
+      cudaGetLastError();
+      return 0;
+    }
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3(16);
+    cfg.blockDim = dim3(1024);
+    cfg.dynamicSmemBytes = psm;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = 16;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    int n = 0;
+    const bool fits = cudaOccupancyMaxActiveClusters(&n, k, &cfg) == cudaSuccess && n > 0;
+    cudaGetLastError();
+    return fits ? 1 : 0;
+  }) == 1;
+}
+
 static cpca_status power_launch(PowerBatchArgs& pa, bool reverse, void* scratch, cudaStream_t st, bool* done) {
   const int nvw = assign_warp_blocks(pa);
   *done = false;
-  if (nvw > kPowMaxWarps) {
+  const size_t fixed = sizeof(double) * 4 * size_t(nvw) + sizeof(float) * 64 * size_t(nvw);
+  const size_t psm = size_t(max_smem_optin());
+  const bool c16 = !reverse && nvw > kPowMaxWarps && nvw <= 2 * kPowMaxWarps && fixed < psm / 2 &&
+                   power_cluster16_ok(psm);
+  if (nvw > kPowMaxWarps && !c16) {
     if (reverse) return CPCA_OK;
     CPCA_CHECK_ARG(scratch, "power iterations: no scratch for %d warp blocks", nvw);
     float* u = static_cast<float*>(scratch);
@@ -1106,19 +1174,27 @@ static cpca_status power_launch(PowerBatchArgs& pa, bool reverse, void* scratch,
     *done = true;
     return CPCA_OK;
   }
-  const size_t fixed = sizeof(double) * 4 * size_t(nvw) + sizeof(float) * 64 * size_t(nvw);
-  const size_t psm = size_t(max_smem_optin());
   const int ell_cap = int((psm - fixed) / sizeof(int2));
-  const void* k = reverse ? (const void*)power_cluster_reverse_kernel : (const void*)power_cluster_kernel;
-  static PerDeviceOnce attr[2];
-  CPCA_CUDA(once_per_device(attr[reverse],
-                            [&] { return cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(psm)); }));
-  const int threads = 32 * ((nvw + kPowCtas - 1) / kPowCtas);
-  if (reverse)
-    power_cluster_reverse_kernel<<<kPowCtas, threads, psm, st>>>(pa, nvw, ell_cap);
-  else
-    power_cluster_kernel<<<kPowCtas, threads, psm, st>>>(pa, nvw, ell_cap);
-  CPCA_LAUNCHED();
+  if (reverse) {
+    static PerDeviceOnce attr;
+    CPCA_CUDA(once_per_device(attr, [&] {
+      return cudaFuncSetAttribute((const void*)power_cluster_reverse_kernel,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, int(psm));
+    }));
+    power_cluster_reverse_kernel<<<kPowCtas, 32 * ((nvw + kPowCtas - 1) / kPowCtas), psm, st>>>(pa, nvw, ell_cap);
+    CPCA_LAUNCHED();
+  } else if (c16) {
+    CPCA_CUDA(launch_power_cluster<16>(pa, nvw, ell_cap, psm, st));
+    CPCA_LAUNCHED();
+  } else {
+    static PerDeviceOnce attr;
+    CPCA_CUDA(once_per_device(attr, [&] {
+      return cudaFuncSetAttribute((const void*)power_cluster_kernel<kPowCtas>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, int(psm));
+    }));
+    CPCA_CUDA(launch_power_cluster<kPowCtas>(pa, nvw, ell_cap, psm, st));
+    CPCA_LAUNCHED();
+  }
   *done = true;
   return CPCA_OK;
 }

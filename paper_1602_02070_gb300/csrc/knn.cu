@@ -85,14 +85,36 @@ __global__ void half_scale_kernel(const unsigned int* __restrict__ nmax_bits, in
   sc[3] = float(2.0 * a * a * double(d));
 }
 
-// H = half(s P), rows padded with zeros to ldh.
-__global__ void to_half_kernel(const float* __restrict__ P, int N, int d, int64_t ld, const float* __restrict__ sc,
-                               __half* __restrict__ H, int64_t ldh) {
+// H = half(s P), rows padded with zeros to ldh: a warp per row, lanes
+// over 8-half (16-byte) groups of the row.
+__global__ void __launch_bounds__(256)
+to_half_kernel(const float* __restrict__ P, int N, int d, int64_t ld, const float* __restrict__ sc,
+               __half* __restrict__ H, int64_t ldh) {
   const float s = sc[0];
-  const int64_t total = int64_t(N) * ldh;
-  for (int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; t < total; t += int64_t(gridDim.x) * blockDim.x) {
-    const int64_t i = t / ldh, k = t % ldh;
-    H[t] = __float2half_rn(k < d ? P[i * ld + k] * s : 0.f);
+  const int lane = threadIdx.x & 31;
+  const int64_t ng = ldh / 8;  // 8-half groups per row (ldh % 8 == 0)
+  const bool vec = (ld % 4) == 0 && (reinterpret_cast<uintptr_t>(P) & 15) == 0;
+  for (int64_t i = (blockIdx.x * int64_t(blockDim.x) + threadIdx.x) >> 5; i < N;
+       i += (int64_t(gridDim.x) * blockDim.x) >> 5) {
+    const float* p = P + i * ld;
+    uint4* h = reinterpret_cast<uint4*>(H + i * ldh);
+    for (int64_t g = lane; g < ng; g += 32) {
+      const int k = int(g * 8);
+      float v[8];
+      if (vec && k + 8 <= d) {
+        const float4 x = __ldg(reinterpret_cast<const float4*>(p + k));
+        const float4 y = __ldg(reinterpret_cast<const float4*>(p + k + 4));
+        v[0] = x.x; v[1] = x.y; v[2] = x.z; v[3] = x.w;
+        v[4] = y.x; v[5] = y.y; v[6] = y.z; v[7] = y.w;
+      } else {
+#pragma unroll
+        for (int t = 0; t < 8; ++t) v[t] = k + t < d ? __ldg(p + k + t) : 0.f;
+      }
+      __half2 o[4];
+#pragma unroll
+      for (int t = 0; t < 4; ++t) o[t] = __halves2half2(__float2half_rn(v[2 * t] * s), __float2half_rn(v[2 * t + 1] * s));
+      h[g] = *reinterpret_cast<const uint4*>(o);
+    }
   }
 }
 
@@ -732,31 +754,99 @@ __global__ void fill_edges_kernel(const int32_t* __restrict__ knn, const float* 
 
 // Per node: sort its edge list by neighbour, drop duplicates (an edge seen
 // from both ends carries the same bitwise d2), count what is left.
-__global__ void dedupe_kernel(int N, const int64_t* __restrict__ off, int32_t* __restrict__ e_nbr,
-                              float* __restrict__ e_d2, int32_t* __restrict__ uniq) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= N) return;
-  const int64_t lo = off[i], hi = off[i + 1];
-  for (int64_t a = lo + 1; a < hi; ++a) {
-    const int32_t j = e_nbr[a];
-    const float v = e_d2[a];
-    int64_t b = a;
-    while (b > lo && e_nbr[b - 1] > j) {
-      e_nbr[b] = e_nbr[b - 1];
-      e_d2[b] = e_d2[b - 1];
-      --b;
+// Sort each node's edge list by neighbour and drop repeats (an edge listed
+// by both ends), in place. A warp per node: every entry's rank among the
+// distinct neighbours comes from comparisons with all entries (shuffles),
+// then the kept entries are written at their ranks. The first copy of a
+// repeat is kept (repeats carry the same squared distance anyway: it is
+// symmetric bit for bit). Lists longer than kDedupeWarpMax fall back to one
+// lane's insertion sort.
+constexpr int kDedupeSlots = 8, kDedupeWarpMax = 32 * kDedupeSlots;
+__global__ void __launch_bounds__(256)
+dedupe_kernel(int N, const int64_t* __restrict__ off, int32_t* __restrict__ e_nbr, float* __restrict__ e_d2,
+              int32_t* __restrict__ uniq) {
+  const int lane = threadIdx.x & 31;
+  for (int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < N; i += (gridDim.x * blockDim.x) >> 5) {
+    const int64_t lo = off[i], hi = off[i + 1];
+    const int n = int(hi - lo);
+    if (n > kDedupeWarpMax) {  // warp-uniform
+      if (lane == 0) {
+        for (int64_t a = lo + 1; a < hi; ++a) {
+          const int32_t j = e_nbr[a];
+          const float v = e_d2[a];
+          int64_t b = a;
+          while (b > lo && e_nbr[b - 1] > j) {
+            e_nbr[b] = e_nbr[b - 1];
+            e_d2[b] = e_d2[b - 1];
+            --b;
+          }
+          e_nbr[b] = j;
+          e_d2[b] = v;
+        }
+        int64_t w = lo;
+        for (int64_t a = lo; a < hi; ++a) {
+          if (a > lo && e_nbr[a] == e_nbr[w - 1]) continue;
+          e_nbr[w] = e_nbr[a];
+          e_d2[w] = e_d2[a];
+          ++w;
+        }
+        uniq[i] = int32_t(w - lo);
+      }
+      __syncwarp();
+      continue;
     }
-    e_nbr[b] = j;
-    e_d2[b] = v;
+    int nb[kDedupeSlots];
+    float dv[kDedupeSlots];
+    bool keep[kDedupeSlots];
+    int rk[kDedupeSlots];
+#pragma unroll
+    for (int q = 0; q < kDedupeSlots; ++q) {
+      const int e = lane + 32 * q;
+      nb[q] = e < n ? e_nbr[lo + e] : 0x7fffffff;
+      dv[q] = e < n ? e_d2[lo + e] : 0.f;
+      keep[q] = e < n;
+      rk[q] = 0;
+    }
+    // pass 1: an entry is a repeat when an earlier entry has its neighbour
+#pragma unroll
+    for (int t = 0; t < kDedupeSlots; ++t) {
+      if (32 * t >= n) break;  // warp-uniform
+      for (int l = 0; l < 32; ++l) {
+        const int a = l + 32 * t;
+        const int v = __shfl_sync(0xffffffffu, nb[t], l);
+        if (a >= n) break;  // warp-uniform
+#pragma unroll
+        for (int q = 0; q < kDedupeSlots; ++q)
+          if (v == nb[q] && a < lane + 32 * q) keep[q] = false;
+      }
+    }
+    // pass 2: the rank of a kept entry = the kept entries with a smaller neighbour
+#pragma unroll
+    for (int t = 0; t < kDedupeSlots; ++t) {
+      if (32 * t >= n) break;
+      for (int l = 0; l < 32; ++l) {
+        const int a = l + 32 * t;
+        const int v = __shfl_sync(0xffffffffu, nb[t], l);
+        const bool k = __shfl_sync(0xffffffffu, keep[t], l);
+        if (a >= n) break;
+#pragma unroll
+        for (int q = 0; q < kDedupeSlots; ++q) rk[q] += (k && v < nb[q]) ? 1 : 0;
+      }
+    }
+    int cnt = 0;
+#pragma unroll
+    for (int q = 0; q < kDedupeSlots; ++q) cnt += keep[q] ? 1 : 0;
+    cnt = __reduce_add_sync(0xffffffffu, cnt);
+    __syncwarp();  // every read of the list is done
+#pragma unroll
+    for (int q = 0; q < kDedupeSlots; ++q)
+      if (keep[q]) {
+        e_nbr[lo + rk[q]] = nb[q];
+        e_d2[lo + rk[q]] = dv[q];
+      }
+    if (lane == 0) uniq[i] = cnt;
+    __syncwarp();
   }
-  int64_t w = lo;
-  for (int64_t a = lo; a < hi; ++a) {
-    if (a > lo && e_nbr[a] == e_nbr[w - 1]) continue;
-    e_nbr[w] = e_nbr[a];
-    e_d2[w] = e_d2[a];
-    ++w;
-  }
-  uniq[i] = int32_t(w - lo);
 }
 
 __global__ void degree_kernel(int N, const int64_t* __restrict__ off, const int32_t* __restrict__ uniq,
@@ -921,7 +1011,7 @@ cpca_status knn_lists(const float* P, int N, int d, int64_t ld, int K, const Knn
     CPCA_LAUNCHED();
     const int64_t ldh = knn_half_ld(d);
     CPCA_PROF("knn_to_half", st);
-    to_half_kernel<<<unsigned(std::min<int64_t>(ceil_div(int64_t(N) * ldh, 256), int64_t(num_sms()) * 16)), 256, 0,
+    to_half_kernel<<<unsigned(std::min<int64_t>(ceil_div(int64_t(N) * 32, 256), int64_t(num_sms()) * 16)), 256, 0,
                      st>>>(P, N, d, ld, w.hsc, w.H, ldh);
     CPCA_LAUNCHED();
     CPCA_TRY(knn_candidates_tc(w.H, N, d, ldh, w.hsc, M, S, w.nrm, w.cand_i, w.cand_d, w.err, &done, st));
@@ -1008,7 +1098,8 @@ cpca_status graph_from_knn(const int32_t* kidx, const float* kd2, int N, int K, 
   fill_edges_kernel<<<eb, 256, 0, st>>>(kidx, kd2, N, K, w.off, w.cursor, w.e_nbr, w.e_d2);
   CPCA_LAUNCHED();
   CPCA_PROF("graph_dedupe", st);
-  dedupe_kernel<<<ceil_div(N, 128), 128, 0, st>>>(N, w.off, w.e_nbr, w.e_d2, w.uniq);
+  dedupe_kernel<<<unsigned(std::min<int64_t>(ceil_div(int64_t(N) * 32, 256), int64_t(num_sms()) * 16)), 256, 0, st>>>(
+      N, w.off, w.e_nbr, w.e_d2, w.uniq);
   CPCA_LAUNCHED();
   scan_kernel<<<1, 1024, 0, st>>>(w.uniq, 1, N, rowptr);
   CPCA_LAUNCHED();

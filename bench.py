@@ -616,6 +616,33 @@ def fista_large_measure(M, torch, peaks, J=300, reps=3):
                          "peak_source": "measured" if peaks else "fallback"}}
 
 
+def knn_measure(M, torch, cfg, p, n, peaks, reps=2):
+    """Both kNN graphs (points = the rows, then the columns) of a p x n
+    matrix drawn like the workload's, K as the workload's: the phases of one
+    graph build (CUDA events) and the tensor-core pass's rate, 2 N^2 d flops
+    against the dense f16 rate."""
+    Y = gen.make_instance_torch(0, p, n, cfg["r"], cfg["C"], cfg["frac"], device="cuda")
+    out = []
+    for tr in (False, True):
+        M.cpca_knn_graph(Y, cfg["K"], transposed=tr)
+        torch.cuda.synchronize()
+        M.profile_enable(True, "")
+        for _ in range(reps):
+            M.cpca_knn_graph(Y, cfg["K"], transposed=tr)
+        torch.cuda.synchronize()
+        prof = M.profile_read()
+        M.profile_enable(False, "")
+        N, d = (n, p) if tr else (p, n)
+        ms, cnt = prof.get("knn_candidates_tc", (0.0, 0))
+        tf = 2.0 * N * N * d / (ms / max(cnt, 1) / 1e3) / 1e12 if cnt else None
+        pk = peaks.get("bf16_tflops_sustained", peaks["bf16_tflops"]) if peaks else 1700.0
+        out.append({"points": N, "dim": d, "K": cfg["K"],
+                    "phases_ms": {k: round(v[0] / reps, 3) for k, v in prof.items()},
+                    "tc_tflops": tf, "tc_frac": tf / pk if tf else None,
+                    "uncertified": M.knn_last_uncertified(), "bruteforce": M.knn_last_bruteforce()})
+    return out
+
+
 def profiled_dram_bytes(summary):
     """DRAM bytes per launch recorded in a committed ncu summary under
     profiles/ (the 'dram_bytes_per_launch:' line), or None."""
@@ -708,6 +735,9 @@ def main():
     ap.add_argument("--fista-large-only", action="store_true",
                     help="only FISTA on the 8 GB workload's Y~ (one JSON object; for profiling)")
     ap.add_argument("--fista-large-iters", type=int, default=300)
+    ap.add_argument("--knn-only", type=int, nargs=2, metavar=("P", "N"), default=None,
+                    help="only the two kNN graphs (rows, columns) of a P x N matrix of the workload's model "
+                         "(one JSON object per graph; for profiling)")
     ap.add_argument("--kron-only", action="store_true",
                     help="only the Kron-reduced graphs and FISTA on them (one JSON object; for profiling)")
     args = ap.parse_args()
@@ -740,6 +770,10 @@ def main():
     M.lib()
     if args.fista_large_only:
         print(json.dumps(fista_large_measure(M, torch, load_peaks(), J=args.fista_large_iters, reps=1)))
+        return
+    if args.knn_only:
+        for line in knn_measure(M, torch, cfg, *args.knn_only, load_peaks()):
+            print(json.dumps(line))
         return
     if args.kron_only:
         c1 = dict(gen.CONFIGS[SMALL_WORKLOAD])

@@ -865,7 +865,8 @@ def main():
         ev2[s_][1].record(stream)
         del Yin, o
     barrier()
-    e2e_s = sum(a_.elapsed_time(b_) for a_, b_ in ev2) / 1000.0
+    e2e_ms = [a_.elapsed_time(b_) for a_, b_ in ev2]
+    e2e_s = sum(e2e_ms) / 1000.0
 
     total_s, e2e_s = max_over_ranks(dist, [total_s, e2e_s], dev)
     units = cfg["J"] * args.steps * world
@@ -886,7 +887,8 @@ def main():
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic", "config": config_dict(cfg, args.workload),
         "e2e": {"value": units / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(Yh.numel() * 4),
-                "d2h_bytes_per_step": int(Xh.numel() * 4)},
+                "d2h_bytes_per_step": int(Xh.numel() * 4), "steps_ms": [round(v, 2) for v in e2e_ms]},
+        "steps_ms": [round(v, 2) for v in step_ms],
         "gpu_launches": int(gpu_launches),
         "roofline": roof,
         "fista_roofline": fista_roof,

@@ -409,6 +409,12 @@ cpca_status cpca_frpcag_backward(const float* Yt, int32_t rr, int32_t rc, int64_
  * 4. Unit-normalise the columns of U and V.
  * 5. sigma_i = sqrt(n p / (rr rc (1 - delta))) s_i.
  * 6. X = U diag(sigma) V^T (p x n, leading dimension ldx) if X != NULL.
+ *    X may be device memory or page-locked host memory that the GPU can
+ *    address (cudaHostAlloc, or cudaHostRegister with the mapped flag, on a
+ *    system with unified addressing): the output kernel then writes X
+ *    straight into host memory over the CPU-GPU link, with no device copy
+ *    of the p x n result (the whole 8 GB output of a 20000 x 100000 matrix
+ *    never touches HBM).
  *
  * omega_r (rr ascending indices of [0,p)) and omega_c (rc of [0,n)) are the
  * sampling sets of cpca_sample; Lr (p x p) and Lc (n x n) the full graphs.

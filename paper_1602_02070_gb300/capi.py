@@ -234,11 +234,21 @@ def _require_cuda(t: torch.Tensor, dtype, name: str):
         raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
 
 
-def _require_matrix(t, rows: int, cols: int, name: str, like: torch.Tensor | None = None):
+def _require_matrix(t, rows: int, cols: int, name: str, like: torch.Tensor | None = None,
+                    host_ok: bool = False):
     """A float32 CUDA matrix of exactly rows x cols with unit column stride
-    (row-major rows, any leading dimension), on the device of ``like``.
-    Checked before any launch: a smaller buffer would be written past its
-    end on the device."""
+    (row-major rows, any leading dimension), on the device of ``like``
+    (with ``host_ok``, a page-locked host matrix is accepted too: a kernel
+    writes it over the CPU-GPU link). Checked before any launch: a smaller
+    buffer would be written past its end."""
+    if host_ok and isinstance(t, torch.Tensor) and not t.is_cuda:
+        if not t.is_pinned() or t.dtype != torch.float32:
+            raise ValueError(f"{name} must be a float32 CUDA tensor or page-locked (pinned) host tensor")
+        if t.dim() != 2 or tuple(t.shape) != (rows, cols):
+            raise ValueError(f"{name} must be {rows} x {cols}, got {tuple(t.shape)}")
+        if t.stride(1) != 1 or t.stride(0) < cols:
+            raise ValueError(f"{name} must be row-major with unit column stride")
+        return
     _require_cuda(t, torch.float32, name)
     if t.dim() != 2 or tuple(t.shape) != (rows, cols):
         raise ValueError(f"{name} must be {rows} x {cols}, got {tuple(t.shape)}")
@@ -581,7 +591,7 @@ def cpca_decode(Xt: torch.Tensor, omega_r: torch.Tensor, omega_c: torch.Tensor, 
     kmax = prm.kmax
     X = (out if out is not None else torch.empty(p, n, dtype=torch.float32, device=dev)) if want_X else None
     if X is not None:
-        _require_matrix(X, p, n, "out", Xt)
+        _require_matrix(X, p, n, "out", Xt, host_ok=True)  # device, or pinned host (written in place)
     U = torch.empty(p, kmax, dtype=torch.float32, device=dev)
     V = torch.empty(n, kmax, dtype=torch.float32, device=dev)
     sig = torch.empty(kmax, dtype=torch.float64, device=dev)

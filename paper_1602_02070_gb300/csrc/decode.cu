@@ -1490,13 +1490,9 @@ extern "C" cpca_status cpca_decode(const float* Xt, int32_t rr, int32_t rc, int6
   CPCA_LAUNCHED();
   scale_cols_kernel<<<gn, 256, 0, st>>>(Vo, int64_t(n) * kmax, kmax, w.invv);
   CPCA_LAUNCHED();
-  if (X) {
-    if (k == 0) {
-      CPCA_CUDA(cudaMemset2DAsync(X, ldx * sizeof(float), 0, size_t(n) * sizeof(float), p, st));
-    } else {
-      CPCA_PROF("decode_output", st);
-      CPCA_TRY(launch_output(Uo, kmax, Vo, kmax, so, k, p, n, X, ldx, st));
-    }
+  if (X) {  // device memory, or page-locked host memory the GPU addresses (written by the kernel)
+    CPCA_PROF("decode_output", st);
+    CPCA_TRY(launch_output(Uo, kmax, Vo, kmax, so, k, p, n, X, ldx, st));  // k == 0: zeros
   }
   if (k_out) *k_out = k;
   int itmax[2] = {0, 0};

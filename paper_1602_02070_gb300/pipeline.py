@@ -22,7 +22,7 @@ def cpca_pipeline(Y: torch.Tensor, K: int = 10, fr: float = 0.25, fc: float = 0.
                   power_iters: int = 200, power_seed: int = 0, rank_ratio: float = 0.1,
                   delta: float = 0.0, kmax: int = 24, svd_iters: int = 6, marks=None,
                   want_X: bool = True, check_status: bool = True, graphs: str = "knn",
-                  kron_tol: float = 1e-6):
+                  kron_tol: float = 1e-6, out: torch.Tensor | None = None):
     """Steps 1-6 on a dense device matrix Y (p x n, FP32, row-major).
 
     1. kNN graphs L_r (rows of Y) and L_c (columns of Y);
@@ -33,6 +33,9 @@ def cpca_pipeline(Y: torch.Tensor, K: int = 10, fr: float = 0.25, fc: float = 0.
     5. FRPCAG by FISTA on Y~ (J iterations, lambda by power iteration);
     6. approximate decoder (Algorithm 2) to X (p x n).
     ``marks``: optional callable(name) invoked between steps (timing hooks).
+    ``out``: optional p x n float32 output - a device tensor, or a pinned
+    host tensor that the decoder's output kernel writes directly over the
+    CPU-GPU link (no device copy of X and no separate transfer).
     """
     if graphs not in ("knn", "kron"):
         raise ValueError("graphs must be 'knn' or 'kron'")
@@ -63,7 +66,7 @@ def cpca_pipeline(Y: torch.Tensor, K: int = 10, fr: float = 0.25, fc: float = 0.
     Xt, finfo = capi.cpca_frpcag_solve(Yt, Lrt, Lct, prm, want_info=False, ws=fws)
     mark("fista")
     dprm = capi.decode_params(rank_ratio, 0, kmax, delta, cg_tol, 0, svd_iters, 0)
-    dec = capi.cpca_decode(Xt, om_r, om_c, p, n, Lr, Lc, dprm, want_X=want_X,
+    dec = capi.cpca_decode(Xt, om_r, om_c, p, n, Lr, Lc, dprm, want_X=want_X, out=out,
                            check_status=check_status)
     # the info-less FISTA solve reports a barrier timeout through its
     # workspace (the decoder has synchronised the stream already)

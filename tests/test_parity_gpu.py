@@ -275,6 +275,24 @@ def test_decode_matches_oracle(M, c0_decode):
     assert np.allclose(dg["sigma"].cpu().numpy(), do["sigma"], rtol=1e-5)
 
 
+def test_decode_into_pinned_host_output(M, c0_decode):
+    """X written by the output kernel straight into page-locked host memory
+    equals the device-resident X bit for bit (same kernel, same arithmetic);
+    a pageable host buffer is refused before any launch."""
+    Y, Xt, Lr, Lc, om_r, om_c = c0_decode
+    p, n = Y.shape
+    args = (_dev(Xt), torch.as_tensor(om_r, dtype=torch.int32, device="cuda"),
+            torch.as_tensor(om_c, dtype=torch.int32, device="cuda"), p, n,
+            M.Csr.from_scipy(Lr), M.Csr.from_scipy(Lc))
+    dd = M.cpca_decode(*args, cg_tol=1e-6)
+    Xh = torch.full((p, n), float("nan"), dtype=torch.float32).pin_memory()
+    dh = M.cpca_decode(*args, cg_tol=1e-6, out=Xh)
+    assert dh["X"] is Xh and dh["k"] == dd["k"]
+    assert torch.equal(Xh, dd["X"].cpu())
+    with pytest.raises(ValueError):
+        M.cpca_decode(*args, cg_tol=1e-6, out=torch.empty(p, n, dtype=torch.float32))
+
+
 def test_decode_full_sampling_and_override(M):
     rng = np.random.default_rng(9)
     Xt = rng.standard_normal((40, 3)) @ np.diag([10.0, 5.0, 2.0]) @ rng.standard_normal((3, 50))

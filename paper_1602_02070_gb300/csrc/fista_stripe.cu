@@ -15,10 +15,11 @@
 // is contiguous) and stages the stripe columns' neighbour lists (as Z^T row
 // offsets), then in chunks of 1024 rows:
 //   (Z Lc)(i, c) = sum_l Lc[c, l] Z^T(l, i): work items (column, row block)
-//       that the warps take in turn - 128 rows (a lane per 4 rows, 16-byte
-//       loads) for a column with a short list, 32 rows (a lane per row) for
-//       one with a long list, so that the hub columns of a kNN graph spread
-//       over the warps; the neighbours' Z^T rows are read through L1
+//       that the warps take in turn - 256 rows (a lane per 8 rows, two
+//       16-byte loads per neighbour) for a column with a short list, 64 rows
+//       (a lane per 2 rows, 8-byte loads) for one with a long list, so that
+//       the hub columns of a kNN graph spread over the warps; the
+//       neighbours' Z^T rows are read through L1
 //       (neighbouring columns of the stripe share them); overlaps the
 //       stripe's copy on the first chunk;
 //   (Lr Z)(i, c) = sum_k Lr[i, k] Z(k, c): W/4 lanes per row, each a quad
@@ -224,12 +225,12 @@ __global__ void __launch_bounds__(Shape<W>::ST, Shape<W>::BLOCKS)
     for (int r0 = rlo; r0 < rhi; r0 += RC) {
       const int nr = min(RC, rhi - r0);
       // ---- (Z Lc): items (column, row block) taken by the warps in turn: a
-      // column with a short list in 128-row items (a lane per 4 rows, 16-byte
-      // loads), one with a long list in 32-row items (a lane per row), so
-      // that long lists spread over many warps; every output still sums its
-      // column's list in CSR order.
+      // column with a short list in 256-row items (a lane per 8 rows, two
+      // 16-byte loads per neighbour), one with a long list in 64-row items (a
+      // lane per 2 rows, 8-byte loads), so that long lists spread over many
+      // warps; every output still sums its column's list in CSR order.
       {
-        const int hb = (nr + 31) / 32, nb = (nr + 127) / 128;  // row blocks of the chunk
+        const int hb = (nr + 63) / 64, nb = (nr + 255) / 256;  // row blocks of the chunk
         const int nh = sm.nhub, nitems = nh * hb + sm.nnorm * nb;
         for (;;) {
           int it = 0;
@@ -238,62 +239,85 @@ __global__ void __launch_bounds__(Shape<W>::ST, Shape<W>::BLOCKS)
           if (it >= nitems) break;
           const bool hub = it < nh * hb;
           const int c = hub ? sm.hubc[it / hb] : sm.normc[(it - nh * hb) / nb];
-          const int rb = hub ? (it % hb) * 32 : ((it - nh * hb) % nb) * 128;
+          const int rb = hub ? (it % hb) * 64 : ((it - nh * hb) % nb) * 256;
           const int deg = sm.cdeg[c], b0 = sm.cbeg[c];
           const int ds = max(0, min(deg, kPool - b0));  // pooled entries of the list
-          const int rl = rb + (hub ? lane : 4 * lane);  // first row of the lane in the chunk
-          const int i = r0 + rl;
+          const int rl = rb + (hub ? 2 * lane : 8 * lane);  // first row of the lane in the chunk
+          const int i = r0 + rl;                            // even; a multiple of 4 for short lists
           if (hub) {
-            float u = 0.f;
-            if (i < a.ldzt) {
+            float2 u = make_float2(0.f, 0.f);
+            if (i < a.ldzt) {  // then i + 1 < ldzt
+              const float* zt = a.ZTin + i;
               int q = 0;
               for (; q + 8 <= ds; q += 8) {
-                float wt[8], x[8];
+                float wt[8];
+                float2 x[8];
 #pragma unroll
                 for (int t = 0; t < 8; ++t) {
                   const int2 pe = sm.pool[b0 + q + t];
-                  x[t] = __ldg(a.ZTin + pe.x + i);
+                  x[t] = __ldg(reinterpret_cast<const float2*>(zt + pe.x));
                   wt[t] = __int_as_float(pe.y);
                 }
 #pragma unroll
-                for (int t = 0; t < 8; ++t) u = fmaf(wt[t], x[t], u);
+                for (int t = 0; t < 8; ++t) {
+                  u.x = fmaf(wt[t], x[t].x, u.x);
+                  u.y = fmaf(wt[t], x[t].y, u.y);
+                }
               }
               for (; q < ds; ++q) {
                 const int2 pe = sm.pool[b0 + q];
-                u = fmaf(__int_as_float(pe.y), __ldg(a.ZTin + pe.x + i), u);
+                const float2 x = __ldg(reinterpret_cast<const float2*>(zt + pe.x));
+                u.x = fmaf(__int_as_float(pe.y), x.x, u.x);
+                u.y = fmaf(__int_as_float(pe.y), x.y, u.y);
               }
               for (int64_t f = sm.cf0[c] + ds; f < sm.cf0[c] + deg; ++f) {
                 const int l = __ldg(a.Lc.col + f);
-                u = fmaf(__ldg(a.Lc.val + f), __ldg(a.ZTin + int64_t(a.inv ? a.inv[l] : l) * a.ldzt + i), u);
+                const float w = __ldg(a.Lc.val + f);
+                const float2 x =
+                    __ldg(reinterpret_cast<const float2*>(a.ZTin + int64_t(a.inv ? a.inv[l] : l) * a.ldzt + i));
+                u.x = fmaf(w, x.x, u.x);
+                u.y = fmaf(w, x.y, u.y);
               }
             }
-            sm.ac[c][rl] = u;
+            sm.ac[c][rl] = u.x;
+            sm.ac[c][rl + 1] = u.y;
           } else {
-            float4 u = make_float4(0.f, 0.f, 0.f, 0.f);
+            float4 u = make_float4(0.f, 0.f, 0.f, 0.f), v = u;
             if (i < a.ldzt) {  // then i + 3 < ldzt (both multiples of 4)
+              const bool two = i + 4 < a.ldzt;  // then i + 7 < ldzt
+              const float* zt = a.ZTin + i;
               int q = 0;
-              for (; q + 8 <= ds; q += 8) {  // eight neighbours' loads in flight
-                float wt[8];
-                float4 x[8];
+              for (; q + 4 <= ds; q += 4) {  // four neighbours' loads in flight
+                float wt[4];
+                float4 x[4], y[4];
 #pragma unroll
-                for (int t = 0; t < 8; ++t) {
+                for (int t = 0; t < 4; ++t) {
                   const int2 pe = sm.pool[b0 + q + t];
-                  x[t] = ldg4(a.ZTin + pe.x + i);
+                  x[t] = ldg4(zt + pe.x);
+                  y[t] = two ? ldg4(zt + pe.x + 4) : make_float4(0.f, 0.f, 0.f, 0.f);
                   wt[t] = __int_as_float(pe.y);
                 }
 #pragma unroll
-                for (int t = 0; t < 8; ++t) fma4(u, wt[t], x[t]);
+                for (int t = 0; t < 4; ++t) {
+                  fma4(u, wt[t], x[t]);
+                  fma4(v, wt[t], y[t]);
+                }
               }
               for (; q < ds; ++q) {
                 const int2 pe = sm.pool[b0 + q];
-                fma4(u, __int_as_float(pe.y), ldg4(a.ZTin + pe.x + i));
+                fma4(u, __int_as_float(pe.y), ldg4(zt + pe.x));
+                if (two) fma4(v, __int_as_float(pe.y), ldg4(zt + pe.x + 4));
               }
               for (int64_t f = sm.cf0[c] + ds; f < sm.cf0[c] + deg; ++f) {
                 const int l = __ldg(a.Lc.col + f);
-                fma4(u, __ldg(a.Lc.val + f), ldg4(a.ZTin + int64_t(a.inv ? a.inv[l] : l) * a.ldzt + i));
+                const float w = __ldg(a.Lc.val + f);
+                const float* p = a.ZTin + int64_t(a.inv ? a.inv[l] : l) * a.ldzt + i;
+                fma4(u, w, ldg4(p));
+                if (two) fma4(v, w, ldg4(p + 4));
               }
             }
             *reinterpret_cast<float4*>(&sm.ac[c][rl]) = u;
+            *reinterpret_cast<float4*>(&sm.ac[c][rl + 4]) = v;
           }
         }
       }

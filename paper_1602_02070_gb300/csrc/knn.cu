@@ -759,40 +759,19 @@ __global__ void fill_edges_kernel(const int32_t* __restrict__ knn, const float* 
 // distinct neighbours comes from comparisons with all entries (shuffles),
 // then the kept entries are written at their ranks. The first copy of a
 // repeat is kept (repeats carry the same squared distance anyway: it is
-// symmetric bit for bit). Lists longer than kDedupeWarpMax fall back to one
-// lane's insertion sort.
+// symmetric bit for bit). Lists longer than kDedupeWarpMax (hub nodes of a
+// kNN graph in high dimension) are queued for dedupe_long_kernel.
 constexpr int kDedupeSlots = 8, kDedupeWarpMax = 32 * kDedupeSlots;
+constexpr int kDedupeBlockMax = 8192;  // entries one block sorts in shared memory
 __global__ void __launch_bounds__(256)
 dedupe_kernel(int N, const int64_t* __restrict__ off, int32_t* __restrict__ e_nbr, float* __restrict__ e_d2,
-              int32_t* __restrict__ uniq) {
+              int32_t* __restrict__ uniq, int32_t* __restrict__ longq, int32_t* __restrict__ n_long) {
   const int lane = threadIdx.x & 31;
   for (int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < N; i += (gridDim.x * blockDim.x) >> 5) {
     const int64_t lo = off[i], hi = off[i + 1];
     const int n = int(hi - lo);
     if (n > kDedupeWarpMax) {  // warp-uniform
-      if (lane == 0) {
-        for (int64_t a = lo + 1; a < hi; ++a) {
-          const int32_t j = e_nbr[a];
-          const float v = e_d2[a];
-          int64_t b = a;
-          while (b > lo && e_nbr[b - 1] > j) {
-            e_nbr[b] = e_nbr[b - 1];
-            e_d2[b] = e_d2[b - 1];
-            --b;
-          }
-          e_nbr[b] = j;
-          e_d2[b] = v;
-        }
-        int64_t w = lo;
-        for (int64_t a = lo; a < hi; ++a) {
-          if (a > lo && e_nbr[a] == e_nbr[w - 1]) continue;
-          e_nbr[w] = e_nbr[a];
-          e_d2[w] = e_d2[a];
-          ++w;
-        }
-        uniq[i] = int32_t(w - lo);
-      }
-      __syncwarp();
+      if (lane == 0) longq[atomicAdd(n_long, 1)] = i;
       continue;
     }
     int nb[kDedupeSlots];
@@ -846,6 +825,88 @@ dedupe_kernel(int N, const int64_t* __restrict__ off, int32_t* __restrict__ e_nb
       }
     if (lane == 0) uniq[i] = cnt;
     __syncwarp();
+  }
+}
+
+// The queued long lists: a block per list, keys (neighbour, position) sorted
+// in shared memory by a bitonic network, then the first copy of each
+// neighbour kept in order (what the warp path computes). Lists beyond
+// kDedupeBlockMax entries take one thread's insertion sort.
+__global__ void __launch_bounds__(1024)
+dedupe_long_kernel(const int64_t* __restrict__ off, int32_t* __restrict__ e_nbr, float* __restrict__ e_d2,
+                   int32_t* __restrict__ uniq, const int32_t* __restrict__ longq,
+                   const int32_t* __restrict__ n_long) {
+  extern __shared__ unsigned long long dkeys[];
+  float* dval = reinterpret_cast<float*>(dkeys + kDedupeBlockMax);
+  const int nl = *n_long;
+  for (int t = blockIdx.x; t < nl; t += gridDim.x) {
+    const int i = longq[t];
+    const int64_t lo = off[i], hi = off[i + 1];
+    const int n = int(hi - lo);
+    if (n > kDedupeBlockMax) {  // block-uniform
+      if (threadIdx.x == 0) {
+        for (int64_t a = lo + 1; a < hi; ++a) {
+          const int32_t j = e_nbr[a];
+          const float v = e_d2[a];
+          int64_t b = a;
+          while (b > lo && e_nbr[b - 1] > j) {
+            e_nbr[b] = e_nbr[b - 1];
+            e_d2[b] = e_d2[b - 1];
+            --b;
+          }
+          e_nbr[b] = j;
+          e_d2[b] = v;
+        }
+        int64_t w = lo;
+        for (int64_t a = lo; a < hi; ++a) {
+          if (a > lo && e_nbr[a] == e_nbr[w - 1]) continue;
+          e_nbr[w] = e_nbr[a];
+          e_d2[w] = e_d2[a];
+          ++w;
+        }
+        uniq[i] = int32_t(w - lo);
+      }
+      __syncthreads();
+      continue;
+    }
+    int np = 1;
+    while (np < n) np <<= 1;
+    for (int e = threadIdx.x; e < np; e += blockDim.x) {
+      dkeys[e] = e < n ? (static_cast<unsigned long long>(static_cast<uint32_t>(e_nbr[lo + e])) << 32) |
+                             static_cast<unsigned long long>(e)
+                       : ~0ull;
+      if (e < n) dval[e] = e_d2[lo + e];
+    }
+    __syncthreads();
+    for (int k = 2; k <= np; k <<= 1)
+      for (int j = k >> 1; j > 0; j >>= 1) {
+        for (int e = threadIdx.x; e < np; e += blockDim.x) {
+          const int pe = e ^ j;
+          if (pe > e) {
+            const bool up = (e & k) == 0;
+            const unsigned long long x = dkeys[e], y = dkeys[pe];
+            if ((x > y) == up) {
+              dkeys[e] = y;
+              dkeys[pe] = x;
+            }
+          }
+        }
+        __syncthreads();
+      }
+    // keep the first (lowest position) copy of each neighbour, in order
+    if (threadIdx.x == 0) {
+      int w = 0;
+      for (int e = 0; e < n; ++e) {
+        const int32_t j = int32_t(dkeys[e] >> 32);
+        if (e > 0 && j == int32_t(dkeys[e - 1] >> 32)) continue;
+        const int pos = int(dkeys[e] & 0xffffffffull);
+        e_nbr[lo + w] = j;
+        e_d2[lo + w] = dval[pos];
+        ++w;
+      }
+      uniq[i] = w;
+    }
+    __syncthreads();
   }
 }
 
@@ -924,6 +985,8 @@ struct KnnWs {
   int32_t* e_nbr;
   float* e_d2;
   int32_t* uniq;
+  int32_t* longq;     // nodes whose lists dedupe_long_kernel sorts
+  int32_t* n_long;
   double* deg;
   size_t bytes;
 };
@@ -985,6 +1048,8 @@ static KnnWs knn_layout(void* ws, int N, int d, int K, int transposed) {
   w.e_nbr = c.take<int32_t>(size_t(2) * N * K);
   w.e_d2 = c.take<float>(size_t(2) * N * K);
   w.uniq = c.take<int32_t>(N);
+  w.longq = c.take<int32_t>(N);
+  w.n_long = c.take<int32_t>(1);
   w.deg = c.take<double>(N);
   w.bytes = c.bytes();
   return w;
@@ -1098,9 +1163,19 @@ cpca_status graph_from_knn(const int32_t* kidx, const float* kd2, int N, int K, 
   fill_edges_kernel<<<eb, 256, 0, st>>>(kidx, kd2, N, K, w.off, w.cursor, w.e_nbr, w.e_d2);
   CPCA_LAUNCHED();
   CPCA_PROF("graph_dedupe", st);
+  CPCA_CUDA(cudaMemsetAsync(w.n_long, 0, sizeof(int32_t), st));
   dedupe_kernel<<<unsigned(std::min<int64_t>(ceil_div(int64_t(N) * 32, 256), int64_t(num_sms()) * 16)), 256, 0, st>>>(
-      N, w.off, w.e_nbr, w.e_d2, w.uniq);
+      N, w.off, w.e_nbr, w.e_d2, w.uniq, w.longq, w.n_long);
   CPCA_LAUNCHED();
+  {
+    const size_t lsm = size_t(kDedupeBlockMax) * (sizeof(unsigned long long) + sizeof(float));
+    static PerDeviceOnce attr;
+    CPCA_CUDA(once_per_device(attr, [&] {
+      return cudaFuncSetAttribute(dedupe_long_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(lsm));
+    }));
+    dedupe_long_kernel<<<num_sms(), 1024, lsm, st>>>(w.off, w.e_nbr, w.e_d2, w.uniq, w.longq, w.n_long);
+    CPCA_LAUNCHED();
+  }
   scan_kernel<<<1, 1024, 0, st>>>(w.uniq, 1, N, rowptr);
   CPCA_LAUNCHED();
   degree_kernel<<<ceil_div(N, 128), 128, 0, st>>>(N, w.off, w.uniq, w.e_d2, w.sigma2, w.deg);

@@ -639,7 +639,8 @@ def knn_measure(M, torch, cfg, p, n, peaks, reps=2):
         out.append({"points": N, "dim": d, "K": cfg["K"],
                     "phases_ms": {k: round(v[0] / reps, 3) for k, v in prof.items()},
                     "tc_tflops": tf, "tc_frac": tf / pk if tf else None,
-                    "uncertified": M.knn_last_uncertified(), "bruteforce": M.knn_last_bruteforce()})
+                    "uncertified": M.knn_last_uncertified(), "bruteforce": M.knn_last_bruteforce(),
+                    "err_rel": M.knn_last_err_rel()})
     return out
 
 

@@ -140,9 +140,16 @@ size_t cpca_knn_graph_workspace_size(int32_t npts, int32_t dim, int32_t K, int32
  * redone; each keeps the exact K nearest of the 2K best of its tensor-core
  * candidates (the ranking error is far below the distance gaps in
  * practice, but the worst-case bound can exceed the spread of a tight
- * cluster in high dimension) and cpca_knn_last_uncertified() counts them. */
+ * cluster in high dimension) and cpca_knn_last_uncertified() counts them.
+ * cpca_knn_last_err_rel() is the relative part of that bound (times
+ * |q|^2 + |b|^2) for the same call: 2^-10 + 2^-22 + (t + 8 + c) 2^-23 for
+ * the tensor-core ranking, t the products in one tensor-core accumulation
+ * (dim up to 32768 dimensions, one accumulation; above, 4096 per
+ * accumulation chunk) and c the chunks (0 when unchunked); the FP32 SIMT
+ * ranking's bound otherwise. */
 int32_t cpca_knn_last_bruteforce(void);
 int32_t cpca_knn_last_uncertified(void);
+double cpca_knn_last_err_rel(void);
 cpca_status cpca_knn_graph(const float* pts, int32_t npts, int32_t dim, int64_t ld,
                            int32_t transposed, int32_t K, int32_t lap_type, double sigma2,
                            int64_t* rowptr, int32_t* col, float* val, float* weight,

@@ -115,6 +115,7 @@ _SIGS = [
     ("cpca_knn_graph_workspace_size", C.c_size_t, [C.c_int32, C.c_int32, C.c_int32, C.c_int32]),
     ("cpca_knn_last_bruteforce", C.c_int32, []),
     ("cpca_knn_last_uncertified", C.c_int32, []),
+    ("cpca_knn_last_err_rel", C.c_double, []),
     ("cpca_knn_graph", C.c_int32,
      [C.c_void_p, C.c_int32, C.c_int32, C.c_int64, C.c_int32, C.c_int32, C.c_int32, C.c_double,
       C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p,
@@ -280,6 +281,12 @@ def knn_last_uncertified() -> int:
     exact nearest of their tensor-core candidates, uncertified, because the
     brute-force budget was exceeded."""
     return int(lib().cpca_knn_last_uncertified())
+
+
+def knn_last_err_rel() -> float:
+    """Relative error bound (times |q|^2 + |b|^2) of the candidate ranking
+    that the last cpca_knn_graph call (this thread) certified against."""
+    return float(lib().cpca_knn_last_err_rel())
 
 
 def launch_count() -> int:

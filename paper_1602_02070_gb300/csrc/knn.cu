@@ -1059,7 +1059,7 @@ static KnnWs knn_layout(void* ws, int N, int d, int K, int transposed) {
 // out_i/out_d; P must be 16-byte aligned with ld % 4 == 0 for vector loads.
 cpca_status knn_lists(const float* P, int N, int d, int64_t ld, int K, const KnnWs& w,
                       int32_t* out_i, float* out_d, int* n_bruteforce, int* n_uncertified,
-                      cudaStream_t st) {
+                      float* err_rel_used, cudaStream_t st) {
   const int S = knn_splits(N, d), M = knn_M(K);
   const bool vec4 = (d % 4 == 0) && (ld % 4 == 0) && ((reinterpret_cast<uintptr_t>(P) & 15) == 0);
   CPCA_CUDA(cudaMemsetAsync(w.nmax, 0, 2 * sizeof(unsigned int), st));
@@ -1103,6 +1103,7 @@ cpca_status knn_lists(const float* P, int N, int d, int64_t ld, int K, const Knn
   // the half copy in hsc[2], hsc[3]).
   const float err_rel = done ? knn_tc_err_rel(d) : float((4.0 * sqrt(double(d)) + 16.0) * 0x1.0p-24);
   const float* err_abs = done ? w.hsc + 2 : nullptr;
+  *err_rel_used = err_rel;
   const size_t rsm = size_t(RECHECK_WARPS) * S * M * 20;
   CPCA_CUDA(cudaFuncSetAttribute(knn_recheck_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(rsm)));
   CPCA_PROF("knn_recheck", st);
@@ -1193,9 +1194,11 @@ using namespace cpca;
 
 static thread_local int g_knn_last_redo = 0;
 static thread_local int g_knn_last_unc = 0;
+static thread_local double g_knn_last_err_rel = 0.0;
 
 extern "C" int32_t cpca_knn_last_bruteforce(void) { return g_knn_last_redo; }
 extern "C" int32_t cpca_knn_last_uncertified(void) { return g_knn_last_unc; }
+extern "C" double cpca_knn_last_err_rel(void) { return g_knn_last_err_rel; }
 
 extern "C" size_t cpca_knn_graph_workspace_size(int32_t npts, int32_t dim, int32_t K,
                                                 int32_t transposed) {
@@ -1242,9 +1245,11 @@ extern "C" cpca_status cpca_knn_graph(const float* pts, int32_t npts, int32_t di
   int32_t* oi = knn_idx ? knn_idx : w.kidx;
   float* od = knn_d2 ? knn_d2 : w.kd2;
   int nbf = 0, nunc = 0;
-  CPCA_TRY(knn_lists(P, npts, dim, pld, K, w, oi, od, &nbf, &nunc, st));
+  float erel = 0.f;
+  CPCA_TRY(knn_lists(P, npts, dim, pld, K, w, oi, od, &nbf, &nunc, &erel, st));
   g_knn_last_redo = nbf;
   g_knn_last_unc = nunc;
+  g_knn_last_err_rel = erel;
   CPCA_TRY(graph_from_knn(oi, od, npts, K, lap_type, sigma2, w, rowptr, col, val, weight, nnz_cap, st));
   int64_t nnz = 0;
   double s2 = 0;

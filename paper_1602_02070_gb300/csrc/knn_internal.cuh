@@ -21,5 +21,8 @@ cpca_status knn_candidates_tc(const __half* H, int N, int d, int64_t ldh, const 
 size_t knn_tc_smem(int M);
 // Relative error bound of the tensor-core distances (times |a|^2 + |b|^2).
 float knn_tc_err_rel(int d);
+// k-steps (of 64 dimensions) per tensor-core accumulation, 0 for one
+// accumulation over all d.
+int knn_tc_chunk_ksteps(int d);
 
 }  // namespace cpca

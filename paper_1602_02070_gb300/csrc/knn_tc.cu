@@ -123,6 +123,18 @@ __device__ __forceinline__ void tc_fence_after() {
       : "r"(taddr)                                                                                \
       : "memory")
 
+#define TMEM_ST_X32(taddr, r)                                                                     \
+  asm volatile(                                                                                   \
+      "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "     \
+      "%11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, " \
+      "%29, %30, %31, %32};" ::"r"(taddr),                                                        \
+      "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]),     \
+      "r"(r[8]), "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]),           \
+      "r"(r[15]), "r"(r[16]), "r"(r[17]), "r"(r[18]), "r"(r[19]), "r"(r[20]), "r"(r[21]),         \
+      "r"(r[22]), "r"(r[23]), "r"(r[24]), "r"(r[25]), "r"(r[26]), "r"(r[27]), "r"(r[28]),         \
+      "r"(r[29]), "r"(r[30]), "r"(r[31])                                                          \
+      : "memory")
+
 struct TcShared {
   uint64_t full[kMaxStages], empty[kMaxStages], acc_full[2], acc_empty[2];
   uint32_t tmem_base;
@@ -133,7 +145,7 @@ template <int M, int CL>
 __global__ void __launch_bounds__(256, 1)
 knn_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
               int N, int d, const float* __restrict__ nrm, const float* __restrict__ hsc, int splits,
-              int32_t* __restrict__ cand_i, float* __restrict__ cand_d, int* __restrict__ err) {
+              int kch, int32_t* __restrict__ cand_i, float* __restrict__ cand_d, int* __restrict__ err) {
   // mapB boxes are BN / CL rows: this block's share of a base tile
   extern __shared__ __align__(1024) unsigned char raw[];
   // operand stages must be 1024-byte aligned for the 128-byte swizzle
@@ -154,6 +166,13 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ 
   const int t_lo = blockIdx.y * per, t_hi = min(ntiles, t_lo + per);
   const int nt = max(0, t_hi - t_lo);
   const int nk = (d + BK - 1) / BK;
+  // Accumulation chunks: with kch > 0 every kch k-steps start a fresh
+  // accumulator in TMEM buffer 0 and the epilogue adds it into the running
+  // sum in buffer 1 (FP32, round to nearest), so no accumulation inside the
+  // tensor core spans more than kch BK products; kch = 0 accumulates the
+  // whole d in one buffer and alternates the two buffers between tiles.
+  const int kc = kch > 0 ? kch : nk;
+  const int nc = kch > 0 ? (nk + kc - 1) / kc : 1;
 
   const uint32_t crank = CL > 1 ? cluster_rank() : 0u;
   constexpr uint16_t cmask = uint16_t((1u << CL) - 1u);
@@ -212,32 +231,38 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ 
   } else if (warp == 1) {
     if (lane == 0) {  // ------------------------------------------ MMA issuer
       constexpr uint32_t idesc = f16_idesc(BM, BN);
-      int it = 0;
-      for (int t = 0; t < nt && !*abort; ++t) {
-        const int buf = t & 1, use = t >> 1;
-        if (!mbar_wait(&sh.acc_empty[buf], (use & 1) ^ 1, abort)) break;
-        tc_fence_after();
-        const uint32_t dt = tmem + uint32_t(buf * BN);
-        bool ok = true;
-        for (int k = 0; k < nk; ++k, ++it) {
-          const int s = it % STAGES, round = it / STAGES;
-          if (!mbar_wait(&sh.full[s], round & 1, abort)) {
+      int it = 0, g = 0;  // g: accumulations issued (chunked mode)
+      bool ok = true;
+      for (int t = 0; t < nt && ok && !*abort; ++t) {
+        for (int c = 0; c < nc && ok; ++c, ++g) {
+          const int buf = kch > 0 ? 0 : (t & 1), use = kch > 0 ? g : (t >> 1);
+          if (!mbar_wait(&sh.acc_empty[buf], (use & 1) ^ 1, abort)) {
             ok = false;
             break;
           }
           tc_fence_after();
-          const uint32_t sa = smem_u32(stages + s * STAGE_BYTES);
-          const uint64_t ad = sw128_desc(sa), bd = sw128_desc(sa + A_BYTES);
+          const uint32_t dt = tmem + uint32_t(buf * BN);
+          const int k_lo = c * kc, k_hi = min(nk, k_lo + kc);
+          for (int k = k_lo; k < k_hi; ++k, ++it) {
+            const int s = it % STAGES, round = it / STAGES;
+            if (!mbar_wait(&sh.full[s], round & 1, abort)) {
+              ok = false;
+              break;
+            }
+            tc_fence_after();
+            const uint32_t sa = smem_u32(stages + s * STAGE_BYTES);
+            const uint64_t ad = sw128_desc(sa), bd = sw128_desc(sa + A_BYTES);
 #pragma unroll
-          for (int kk = 0; kk < BK / 16; ++kk)  // 16 halves (32 bytes) per MMA
-            umma_f16(dt, ad + uint64_t(kk * 2), bd + uint64_t(kk * 2), idesc, (k | kk) ? 1u : 0u);
-          if (CL > 1)
-            umma_commit_mc(&sh.empty[s], cmask);
-          else
-            umma_commit(&sh.empty[s]);
+            for (int kk = 0; kk < BK / 16; ++kk)  // 16 halves (32 bytes) per MMA
+              umma_f16(dt, ad + uint64_t(kk * 2), bd + uint64_t(kk * 2), idesc,
+                       (k != k_lo || kk != 0) ? 1u : 0u);
+            if (CL > 1)
+              umma_commit_mc(&sh.empty[s], cmask);
+            else
+              umma_commit(&sh.empty[s]);
+          }
+          if (ok) umma_commit(&sh.acc_full[buf]);
         }
-        if (!ok) break;
-        umma_commit(&sh.acc_full[buf]);
       }
     }
   } else if (warp >= 4) {  // ------------------------------------- epilogue
@@ -266,10 +291,47 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ 
     float thr = __int_as_float(0x7f800000);
     const float m2 = -2.f * hsc[1];  // -2 / s^2: products of the scaled copy back in data units
     const uint32_t lane_base = uint32_t((warp & 3) * 32) << 16;
+    int g = 0;  // accumulations drained (chunked mode)
     for (int t = 0; t < nt; ++t) {
-      const int buf = t & 1, use = t >> 1;
-      if (!mbar_wait(&sh.acc_full[buf], use & 1, abort)) break;
-      tc_fence_after();
+      int buf;
+      if (kch > 0) {
+        // drain every chunk of this tile into the running sum (buffer 1),
+        // then rank from the sum; the MMAs of the next chunk wait only for
+        // the drain, so the ranking below overlaps the next tile's first
+        // chunk
+        bool ok = true;
+        for (int c = 0; c < nc; ++c, ++g) {
+          if (!mbar_wait(&sh.acc_full[0], g & 1, abort)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+#pragma unroll 1
+          for (int ch = 0; ch < BN / 32; ++ch) {
+            uint32_t a[32], r[32];
+            TMEM_LD_X32(tmem + lane_base + uint32_t(ch * 32), a);
+            if (c > 0) {
+              TMEM_LD_X32(tmem + lane_base + uint32_t(BN + ch * 32), r);
+              asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+              for (int i = 0; i < 32; ++i) a[i] = __float_as_uint(__uint_as_float(r[i]) + __uint_as_float(a[i]));
+            } else {
+              asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            }
+            TMEM_ST_X32(tmem + lane_base + uint32_t(BN + ch * 32), a);
+          }
+          asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+          tc_fence_before();
+          __syncwarp();
+          if (lane == 0) mbar_arrive(&sh.acc_empty[0]);
+        }
+        if (!ok) break;
+        buf = 1;
+      } else {
+        buf = t & 1;
+        if (!mbar_wait(&sh.acc_full[buf], (t >> 1) & 1, abort)) break;
+        tc_fence_after();
+      }
       const int n0 = (t_lo + t) * BN;
 #pragma unroll 1
       for (int ch = 0; ch < BN / 32; ++ch) {
@@ -320,9 +382,11 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ 
           }
         }
       }
-      tc_fence_before();
-      __syncwarp();
-      if (lane == 0) mbar_arrive(&sh.acc_empty[buf]);
+      if (kch == 0) {
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&sh.acc_empty[buf]);
+      }
     }
     if (q < N) {
       const float nq = nrm[q];
@@ -383,6 +447,12 @@ size_t knn_tc_smem(int M) {
 
 int64_t knn_half_ld(int d) { return (int64_t(d) + 7) / 8 * 8; }
 
+// Above 32768 dimensions the FP32 accumulation term of the bound below
+// exceeds four times the half-rounding term; there the products are summed
+// in accumulation chunks of 64 k-steps (4096 dimensions), which costs the
+// tensor cores a short wait per chunk while the epilogue adds it up.
+int knn_tc_chunk_ksteps(int d) { return d > 32768 ? 64 : 0; }
+
 bool knn_tc_supported(int N, int d, int M) {
   return device_is_sm10x() && N >= 64 && d >= 16 && (M == 32 || M == 64) && encode_fn() != nullptr;
 }
@@ -420,7 +490,9 @@ cpca_status knn_candidates_tc(const __half* H, int N, int d, int64_t ldh, const 
   at[0].val.clusterDim.z = 1;
   cfg.attrs = at;
   cfg.numAttrs = 1;
-  void* args[] = {&mapA, &mapB, &N, &d, const_cast<float**>(&nrm), const_cast<float**>(&hsc), &S, &cand_i, &cand_d, &err};
+  int kch = knn_tc_chunk_ksteps(d);
+  void* args[] = {&mapA,   &mapB, &N, &d, const_cast<float**>(&nrm), const_cast<float**>(&hsc), &S, &kch,
+                  &cand_i, &cand_d, &err};
   CPCA_PROF("knn_candidates_tc", st);
   CPCA_CUDA(cudaLaunchKernelExC(&cfg, kern, args));
   CPCA_LAUNCHED();
@@ -432,11 +504,20 @@ cpca_status knn_candidates_tc(const __half* H, int N, int d, int64_t ldh, const 
 // half-precision pass: each scaled coordinate is rounded to nearest with a
 // relative error <= 2^-11 (11-bit significand), so each product errs by
 // <= (2^-10 + 2^-22) |q_i b_i| and |2 q.b| by <= (2^-10 + 2^-22)
-// (|q|^2 + |b|^2); plus FP32 accumulation over d terms and the FP32 norms,
-// about (d + 8) roundings of 2^-24 each. Coordinates that fall among the
-// half subnormals err absolutely instead; that part of the bound depends
-// on the data's scale and is added per query from half_scale_kernel's
-// terms.
-float knn_tc_err_rel(int d) { return float(0x1.0p-10 + 0x1.0p-22 + (double(d) + 8.0) * 0x1.0p-23); }
+// (|q|^2 + |b|^2); plus FP32 accumulation over the terms of one
+// accumulation and the FP32 norms, about (terms + 8) roundings of 2^-23
+// each (truncation allowed). With accumulation chunks of c products the
+// tensor cores accumulate c terms at a time and the epilogue adds the
+// ceil(d / c) chunk sums with round to nearest, adding at most
+// (chunks - 1) 2^-24 of sum |q_i b_i|: counted here as chunks 2^-23.
+// Coordinates that fall among the half subnormals err absolutely instead;
+// that part of the bound depends on the data's scale and is added per query
+// from half_scale_kernel's terms.
+float knn_tc_err_rel(int d) {
+  const int kch = knn_tc_chunk_ksteps(d);
+  if (kch == 0) return float(0x1.0p-10 + 0x1.0p-22 + (double(d) + 8.0) * 0x1.0p-23);
+  const int64_t nk = (int64_t(d) + BK - 1) / BK, chunks = (nk + kch - 1) / kch;
+  return float(0x1.0p-10 + 0x1.0p-22 + (double(kch) * BK + 8.0 + double(chunks)) * 0x1.0p-23);
+}
 
 }  // namespace cpca

@@ -91,6 +91,32 @@ def test_knn_lists_and_graph(M, shape, transposed, K):
     assert abs(Gs - Gs.T).max() == 0.0  # exactly symmetric
 
 
+@pytest.mark.parametrize("shape,transposed,K", [((300, 40000), False, 10), ((33001, 260), True, 10),
+                                                ((150, 34000), False, 20)])
+def test_knn_chunked_accumulation_high_dimension(M, shape, transposed, K):
+    """Points in more than 32768 dimensions: the tensor-core ranking adds its
+    products in accumulation chunks of 4096 dimensions (a ragged last chunk
+    for 33001), and the certificate uses the chunked bound. The lists are
+    the exact ones (the oracle's C search) and the graph follows from them
+    by the oracle's rules."""
+    from tests._oracle_knn import oracle_knn_graph
+    Y, _, _ = gen.make_instance(4, shape[0], shape[1], 4, 3, 0.05)
+    P = np.ascontiguousarray(Y.T if transposed else Y)
+    Lg, gi, gd = M.cpca_knn_graph(_dev(Y), K, M.LAP_NORMALIZED, transposed=transposed, want_knn=True)
+    d = P.shape[1]
+    chunks = -(-(-(-d // 64)) // 64)  # k-steps of 64 dimensions, 64 k-steps per chunk
+    assert M.knn_last_err_rel() == pytest.approx(2.0**-10 + 2.0**-22 + (4096 + 8 + chunks) * 2.0**-23, rel=1e-6)
+    assert M.knn_last_uncertified() == 0
+    L, _, oi, od = oracle_knn_graph(P, K)
+    gi, gd = gi.cpu().numpy(), gd.cpu().numpy()
+    assert knn_sets_match(gi, gd, oi[:, :K], od, K, rel_gap=1e-6) == []
+    assert np.all(np.sort(gi, 1) == np.sort(oi[:, :K], 1))
+    assert np.allclose(gd, od[:, :K], rtol=2e-6, atol=0)
+    Gs = Lg.to_scipy()
+    assert np.array_equal(Gs.indptr, L.indptr) and np.array_equal(Gs.indices, L.indices)
+    assert np.allclose(Gs.data, L.data, rtol=1e-5, atol=1e-7)
+
+
 def test_knn_combinatorial_zero_row_sums(M):
     Y, _, _ = gen.make_instance(3, 200, 60, 4, 3, 0.05)
     Lg, _, _ = M.cpca_knn_graph(_dev(Y), 10, M.LAP_COMBINATORIAL)

@@ -44,110 +44,114 @@ __global__ void gemm_tn_reduce(const float* __restrict__ P, int nchunk, int64_t 
 
 constexpr int kTnChunks = 64;  // row chunks (column slices) of the split skinny products
 
-// C (m x b) = A (m x n, lda) B (n x b, ld b). A block takes 16 rows of A
-// (two per warp) and one slice of the n columns (gridDim.y slices); B's rows
-// of the slice come through shared memory transposed (Bt[c][k]) in chunks of
-// CH. Each lane takes 4 consecutive columns of the chunk at a time (16-byte
-// loads when the rows allow them, every load of the chunk issued before the
-// products), so that A streams at full width; its partial sums of the
-// 2 x b outputs are reduced over the warp at the end (a fixed butterfly:
-// deterministic). One slice writes C; several write their partial products
-// to P + y m b, added in slice order by gemm_tn_reduce.
-template <int BB, int CH, bool VEC>
-__global__ void __launch_bounds__(256)
+// C (m x b) = A (m x n, lda) B (n x b, ld b), b <= BB. A block takes 128
+// rows of A and one slice of the n columns (gridDim.y slices) in tiles of
+// 32 columns: the A tile is copied row-major into shared memory in 16-byte
+// pieces and B's tile stored transposed (Bt[c][k]); the next tile's loads
+// are issued before the products of the current one. Each thread owns 4
+// rows x BB/8 columns of C (columns j 8 + tx, so that the 16-byte reads of
+// Bt by the eight lanes of a quarter warp fall in distinct banks; the A
+// reads are broadcasts) and reads, per 4 columns of the tile, 4 + BB/8
+// 16-byte values for 16 BB/8 FMAs. The sums run over the columns in order
+// (deterministic). One slice writes C; several write their partial
+// products to P + y m b, added in slice order by gemm_tn_reduce.
+constexpr int NN_RB = 128, NN_KT = 32, NN_LD = NN_KT + 4;
+template <int BB, bool VEC>
+__global__ void __launch_bounds__(256, BB <= 24 ? 3 : 2)
 gemm_nn_tall_k(const float* __restrict__ A, int64_t lda, int m, int n, const float* __restrict__ B, int b,
                float* __restrict__ C, int slice) {
-  __shared__ __align__(16) float Bt[BB][CH + 4];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int i0 = blockIdx.x * 16 + warp * 2;
+  constexpr int CPT = BB / 8;
+  __shared__ __align__(16) float As[NN_RB][NN_LD];
+  __shared__ __align__(16) float Bt[BB][NN_LD];
+  const int tid = threadIdx.x, tx = tid & 7, ty = tid >> 3;
+  const int r0 = blockIdx.x * NN_RB;
   const int kbeg = blockIdx.y * slice, kend = min(n, kbeg + slice);
   if (gridDim.y > 1) C += int64_t(blockIdx.y) * m * b;
-  const float* a0 = A + int64_t(min(i0, m - 1)) * lda;
-  const float* a1 = A + int64_t(min(i0 + 1, m - 1)) * lda;
-  float acc[2][BB];
+  float4 pa[4];
+  float pb[CPT];
+  // tile loads: A rows ty + 32 q, columns 4 tx .. +3; B elements tid + 256 q
+  auto load = [&](int k0) {
+    const int kn = kend - k0;
 #pragma unroll
-  for (int c = 0; c < BB; ++c) acc[0][c] = acc[1][c] = 0.f;
-  for (int k0 = kbeg; k0 < kend; k0 += CH) {
-    const int kn = min(CH, kend - k0);
-    __syncthreads();
-    {  // thread -> (column c = tid % BB, rows tid / BB + 256 / BB q), eight loads in flight
-      constexpr int RSTEP = 256 / BB, NQ = CH / RSTEP;
-      const int c = threadIdx.x % BB, kq = threadIdx.x / BB;
-#pragma unroll 1
-      for (int q0 = 0; q0 < NQ; q0 += 8) {
-        float v[8];
-#pragma unroll
-        for (int q = 0; q < 8; ++q) {
-          const int k = kq + (q0 + q) * RSTEP;
-          v[q] = (c < b && k < kn) ? __ldg(B + int64_t(k0 + k) * b + c) : 0.f;
-        }
-#pragma unroll
-        for (int q = 0; q < 8; ++q) Bt[c][kq + (q0 + q) * RSTEP] = v[q];
-      }
-    }
-    __syncthreads();
-    constexpr int NV = CH / 128;  // 4-column groups of the chunk per lane
-    float4 x0[NV], x1[NV];
-#pragma unroll
-    for (int t = 0; t < NV; ++t) {
-      const int k = t * 128 + lane * 4;  // within the chunk
-      if (VEC && k + 3 < kn) {
-        x0[t] = __ldg(reinterpret_cast<const float4*>(a0 + k0 + k));
-        x1[t] = __ldg(reinterpret_cast<const float4*>(a1 + k0 + k));
+    for (int q = 0; q < 4; ++q) {
+      const int row = r0 + ty + 32 * q, kk = 4 * tx;
+      const float* a = A + int64_t(min(row, m - 1)) * lda + k0 + kk;
+      if (row < m && VEC && kk + 3 < kn) {
+        pa[q] = __ldg(reinterpret_cast<const float4*>(a));
       } else {
-        float v0[4], v1[4];
+        float v[4];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          v0[q] = k + q < kn ? __ldg(a0 + k0 + k + q) : 0.f;
-          v1[q] = k + q < kn ? __ldg(a1 + k0 + k + q) : 0.f;
-        }
-        x0[t] = make_float4(v0[0], v0[1], v0[2], v0[3]);
-        x1[t] = make_float4(v1[0], v1[1], v1[2], v1[3]);
+        for (int t = 0; t < 4; ++t) v[t] = (row < m && kk + t < kn) ? __ldg(a + t) : 0.f;
+        pa[q] = make_float4(v[0], v[1], v[2], v[3]);
       }
     }
 #pragma unroll
-    for (int t = 0; t < NV; ++t) {
-      const int k = t * 128 + lane * 4;
+    for (int q = 0; q < CPT; ++q) {
+      const int e = tid + 256 * q, k = e / BB, c = e % BB;
+      pb[q] = (c < b && k < kn) ? __ldg(B + int64_t(k0 + k) * b + c) : 0.f;
+    }
+  };
+  float acc[4][CPT];
 #pragma unroll
-      for (int c = 0; c < BB; ++c) {
-        if (c < b) {
-          const float4 bv = *reinterpret_cast<const float4*>(&Bt[c][k]);
-          acc[0][c] = fmaf(x0[t].x, bv.x, acc[0][c]);
-          acc[0][c] = fmaf(x0[t].y, bv.y, acc[0][c]);
-          acc[0][c] = fmaf(x0[t].z, bv.z, acc[0][c]);
-          acc[0][c] = fmaf(x0[t].w, bv.w, acc[0][c]);
-          acc[1][c] = fmaf(x1[t].x, bv.x, acc[1][c]);
-          acc[1][c] = fmaf(x1[t].y, bv.y, acc[1][c]);
-          acc[1][c] = fmaf(x1[t].z, bv.z, acc[1][c]);
-          acc[1][c] = fmaf(x1[t].w, bv.w, acc[1][c]);
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < CPT; ++j) acc[i][j] = 0.f;
+  if (kbeg < kend) load(kbeg);
+  for (int k0 = kbeg; k0 < kend; k0 += NN_KT) {
+    __syncthreads();  // the previous tile's reads are done
+#pragma unroll
+    for (int q = 0; q < 4; ++q) *reinterpret_cast<float4*>(&As[ty + 32 * q][4 * tx]) = pa[q];
+#pragma unroll
+    for (int q = 0; q < CPT; ++q) {
+      const int e = tid + 256 * q;
+      Bt[e % BB][e / BB] = pb[q];
+    }
+    __syncthreads();
+    if (k0 + NN_KT < kend) load(k0 + NN_KT);
+#pragma unroll
+    for (int k4 = 0; k4 < NN_KT; k4 += 4) {
+      float4 a[4], bv[CPT];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) a[i] = *reinterpret_cast<const float4*>(&As[4 * ty + i][k4]);
+#pragma unroll
+      for (int j = 0; j < CPT; ++j) bv[j] = *reinterpret_cast<const float4*>(&Bt[8 * j + tx][k4]);
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < CPT; ++j) {
+          acc[i][j] = fmaf(a[i].x, bv[j].x, acc[i][j]);
+          acc[i][j] = fmaf(a[i].y, bv[j].y, acc[i][j]);
+          acc[i][j] = fmaf(a[i].z, bv[j].z, acc[i][j]);
+          acc[i][j] = fmaf(a[i].w, bv[j].w, acc[i][j]);
         }
-      }
     }
   }
 #pragma unroll
-  for (int r = 0; r < 2; ++r)
+  for (int i = 0; i < 4; ++i) {
+    const int row = r0 + 4 * ty + i;
+    if (row >= m) continue;
 #pragma unroll
-    for (int c = 0; c < BB; ++c) {
-      if (c >= b) continue;
-      const float v = warp_sumf(acc[r][c]);
-      if (lane == 0 && i0 + r < m) C[int64_t(i0 + r) * b + c] = v;
+    for (int j = 0; j < CPT; ++j) {
+      const int c = 8 * j + tx;
+      if (c < b) C[int64_t(row) * b + c] = acc[i][j];
     }
+  }
 }
 
-// Slices of the n columns for C = A B: enough blocks for about two per SM,
-// each slice at least 512 columns, at most kTnChunks slices.
+// Slices of the n columns for C = A B: about eight blocks per SM over the
+// 128-row blocks, each slice at least 256 columns, at most kTnChunks slices.
 static int nn_slices(int m, int n) {
-  const int rblocks = int(ceil_div(m, 16));
-  return std::max(1, std::min({kTnChunks, int(ceil_div(n, 512)), int(ceil_div(2 * num_sms(), rblocks))}));
+  const int rblocks = int(ceil_div(m, NN_RB));
+  return std::max(1, std::min({kTnChunks, int(ceil_div(n, 256)), int(ceil_div(8 * num_sms(), rblocks))}));
 }
 
-template <int BB, int CH>
+template <int BB>
 static void gemm_nn_tall_run(dim3 g, const float* A, int64_t lda, int m, int n, const float* B, int b, float* C,
                              int slice, bool vec, cudaStream_t st) {
   if (vec)
-    gemm_nn_tall_k<BB, CH, true><<<g, 256, 0, st>>>(A, lda, m, n, B, b, C, slice);
+    gemm_nn_tall_k<BB, true><<<g, 256, 0, st>>>(A, lda, m, n, B, b, C, slice);
   else
-    gemm_nn_tall_k<BB, CH, false><<<g, 256, 0, st>>>(A, lda, m, n, B, b, C, slice);
+    gemm_nn_tall_k<BB, false><<<g, 256, 0, st>>>(A, lda, m, n, B, b, C, slice);
 }
 
 // C (m x b) = A B, split over slices of n when A has few rows (scratch:
@@ -155,17 +159,19 @@ static void gemm_nn_tall_run(dim3 g, const float* A, int64_t lda, int m, int n, 
 static cpca_status nn_tall(const float* A, int64_t lda, int m, int n, const float* B, int b, float* C,
                            float* scratch, cudaStream_t st) {
   const int ns = nn_slices(m, n);
-  const int slice = ns == 1 ? n : int(ceil_div(ceil_div(n, ns), 128)) * 128;
+  const int slice = ns == 1 ? n : int(ceil_div(ceil_div(n, ns), NN_KT)) * NN_KT;
   const int nsl = int(ceil_div(n, slice));
   const bool vec = (lda % 4) == 0 && (reinterpret_cast<uintptr_t>(A) & 15) == 0;
   float* out = nsl > 1 ? scratch : C;
-  const dim3 g(unsigned(ceil_div(m, 16)), unsigned(nsl));
+  const dim3 g(unsigned(ceil_div(m, NN_RB)), unsigned(nsl));
   if (b <= 16)
-    gemm_nn_tall_run<16, 512>(g, A, lda, m, n, B, b, out, slice, vec, st);
+    gemm_nn_tall_run<16>(g, A, lda, m, n, B, b, out, slice, vec, st);
+  else if (b <= 24)
+    gemm_nn_tall_run<24>(g, A, lda, m, n, B, b, out, slice, vec, st);
   else if (b <= 32)
-    gemm_nn_tall_run<32, 256>(g, A, lda, m, n, B, b, out, slice, vec, st);
+    gemm_nn_tall_run<32>(g, A, lda, m, n, B, b, out, slice, vec, st);
   else
-    gemm_nn_tall_run<BMAX, 128>(g, A, lda, m, n, B, b, out, slice, vec, st);
+    gemm_nn_tall_run<BMAX>(g, A, lda, m, n, B, b, out, slice, vec, st);
   CPCA_LAUNCHED();
   if (nsl > 1) {
     const int64_t total = int64_t(m) * b;
@@ -176,71 +182,134 @@ static cpca_status nn_tall(const float* A, int64_t lda, int m, int n, const floa
   return CPCA_OK;
 }
 
-// C (n x b) = A^T B with A (m x n, lda), B (m x b, ld b): a thread per
-// column of A (the block's 256 columns read as whole row segments), B's rows
-// staged in shared memory 64 at a time and read as broadcasts, each thread's
-// b sums written as its row of C. With gridDim.y > 1 the rows of A are split
-// into chunks of `chunk` rows (a multiple of 64) and block (x, y) writes its
-// partial product to C + y * n * b; gemm_tn_reduce adds the chunks in order.
+// C (n x b) = A^T B with A (m x n, lda), B (m x b, ld b), b <= BB. A block
+// takes 128 columns of A (rows of C) and one chunk of A's rows
+// (gridDim.y chunks of `chunk` rows, a multiple of 32) in tiles of 32 rows:
+// the A tile is copied into shared memory as it lies (each row's 128
+// columns, 512 contiguous bytes), B's 32 rows stored transposed (Bt[c][i]),
+// the next tile's loads issued before the products of the current one.
+// Each thread owns 4 rows x BB/8 columns of C (columns j 8 + tx, as in
+// gemm_nn_tall_k) and reads, per 4 rows of the tile, 4 + BB/8 16-byte
+// values for 16 BB/8 FMAs; the sums run over the rows in order. With
+// gridDim.y > 1 block (x, y) writes its partial product to C + y n b and
+// gemm_tn_reduce adds the chunks in order.
+constexpr int TN_CB = 128, TN_LD = TN_CB + 4;
 template <int BB>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, BB <= 24 ? 3 : 2)
 gemm_tn_tall_k(const float* __restrict__ A, int64_t lda, int m, int n, const float* __restrict__ B, int b,
-               float* __restrict__ C, int chunk) {
-  __shared__ float Bs[64][BB];
-  const int j = blockIdx.x * 256 + threadIdx.x;
+               float* __restrict__ C, int chunk, bool vec) {
+  constexpr int CPT = BB / 8;
+  __shared__ __align__(16) float As[NN_KT][TN_LD];
+  __shared__ __align__(16) float Bt[BB][NN_LD];
+  const int tid = threadIdx.x, tx = tid & 7, ty = tid >> 3;
+  const int j0 = blockIdx.x * TN_CB;
   const int ibeg = blockIdx.y * chunk, iend = min(m, ibeg + chunk);
-  C += int64_t(blockIdx.y) * n * b;
-  float acc[BB];
+  if (gridDim.y > 1) C += int64_t(blockIdx.y) * n * b;
+  float4 pa[4];
+  float pb[CPT];
+  // tile loads: A rows (tid / 32) + 8 q, columns j0 + 4 (tid % 32) .. +3;
+  // B elements tid + 256 q
+  auto load = [&](int i0) {
+    const int rn = iend - i0, jj = 4 * (tid & 31), jn = n - j0;
 #pragma unroll
-  for (int c = 0; c < BB; ++c) acc[c] = 0.f;
-  for (int i0 = ibeg; i0 < iend; i0 += 64) {
-    const int rn = min(64, iend - i0);
-    __syncthreads();
-    for (int e = threadIdx.x; e < 64 * BB; e += 256) {
-      const int r = e / BB, c = e % BB;
-      Bs[r][c] = (r < rn && c < b) ? B[int64_t(i0 + r) * b + c] : 0.f;
+    for (int q = 0; q < 4; ++q) {
+      const int r = (tid >> 5) + 8 * q;
+      const float* a = A + int64_t(i0 + min(r, rn - 1)) * lda + j0 + jj;
+      if (r < rn && vec && jj + 3 < jn) {
+        pa[q] = __ldg(reinterpret_cast<const float4*>(a));
+      } else {
+        float v[4];
+#pragma unroll
+        for (int t = 0; t < 4; ++t) v[t] = (r < rn && jj + t < jn) ? __ldg(a + t) : 0.f;
+        pa[q] = make_float4(v[0], v[1], v[2], v[3]);
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < CPT; ++q) {
+      const int e = tid + 256 * q, r = e / BB, c = e % BB;
+      pb[q] = (c < b && r < rn) ? __ldg(B + int64_t(i0 + r) * b + c) : 0.f;
+    }
+  };
+  float acc[4][CPT];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < CPT; ++j) acc[i][j] = 0.f;
+  if (ibeg < iend) load(ibeg);
+  for (int i0 = ibeg; i0 < iend; i0 += NN_KT) {
+    __syncthreads();  // the previous tile's reads are done
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+      *reinterpret_cast<float4*>(&As[(tid >> 5) + 8 * q][4 * (tid & 31)]) = pa[q];
+#pragma unroll
+    for (int q = 0; q < CPT; ++q) {
+      const int e = tid + 256 * q;
+      Bt[e % BB][e / BB] = pb[q];
     }
     __syncthreads();
-    if (j < n) {
-      int r = 0;
-      for (; r + 8 <= rn; r += 8) {  // eight rows' loads in flight
-        float a[8];
+    if (i0 + NN_KT < iend) load(i0 + NN_KT);
 #pragma unroll
-        for (int t = 0; t < 8; ++t) a[t] = __ldg(A + int64_t(i0 + r + t) * lda + j);
+    for (int k4 = 0; k4 < NN_KT; k4 += 4) {
+      float4 a[4], bv[CPT];
 #pragma unroll
-        for (int t = 0; t < 8; ++t)
+      for (int t = 0; t < 4; ++t) a[t] = *reinterpret_cast<const float4*>(&As[k4 + t][4 * ty]);
 #pragma unroll
-          for (int c = 0; c < BB; ++c) acc[c] = fmaf(a[t], Bs[r + t][c], acc[c]);
-      }
-      for (; r < rn; ++r) {
-        const float a = __ldg(A + int64_t(i0 + r) * lda + j);
+      for (int j = 0; j < CPT; ++j) bv[j] = *reinterpret_cast<const float4*>(&Bt[8 * j + tx][k4]);
 #pragma unroll
-        for (int c = 0; c < BB; ++c) acc[c] = fmaf(a, Bs[r][c], acc[c]);
+      for (int j = 0; j < CPT; ++j) {
+        acc[0][j] = fmaf(a[0].x, bv[j].x, acc[0][j]);
+        acc[1][j] = fmaf(a[0].y, bv[j].x, acc[1][j]);
+        acc[2][j] = fmaf(a[0].z, bv[j].x, acc[2][j]);
+        acc[3][j] = fmaf(a[0].w, bv[j].x, acc[3][j]);
+        acc[0][j] = fmaf(a[1].x, bv[j].y, acc[0][j]);
+        acc[1][j] = fmaf(a[1].y, bv[j].y, acc[1][j]);
+        acc[2][j] = fmaf(a[1].z, bv[j].y, acc[2][j]);
+        acc[3][j] = fmaf(a[1].w, bv[j].y, acc[3][j]);
+        acc[0][j] = fmaf(a[2].x, bv[j].z, acc[0][j]);
+        acc[1][j] = fmaf(a[2].y, bv[j].z, acc[1][j]);
+        acc[2][j] = fmaf(a[2].z, bv[j].z, acc[2][j]);
+        acc[3][j] = fmaf(a[2].w, bv[j].z, acc[3][j]);
+        acc[0][j] = fmaf(a[3].x, bv[j].w, acc[0][j]);
+        acc[1][j] = fmaf(a[3].y, bv[j].w, acc[1][j]);
+        acc[2][j] = fmaf(a[3].z, bv[j].w, acc[2][j]);
+        acc[3][j] = fmaf(a[3].w, bv[j].w, acc[3][j]);
       }
     }
   }
-  if (j < n)
 #pragma unroll
-    for (int c = 0; c < BB; ++c)
-      if (c < b) C[int64_t(j) * b + c] = acc[c];
+  for (int i = 0; i < 4; ++i) {
+    const int j = j0 + 4 * ty + i;
+    if (j >= n) continue;
+#pragma unroll
+    for (int jj = 0; jj < CPT; ++jj) {
+      const int c = 8 * jj + tx;
+      if (c < b) C[int64_t(j) * b + c] = acc[i][jj];
+    }
+  }
 }
 
 static void gemm_tn_tall_launch(dim3 g, const float* A, int64_t lda, int m, int n, const float* B, int b, float* C,
                                 int chunk, cudaStream_t st) {
+  const bool vec = (lda % 4) == 0 && (reinterpret_cast<uintptr_t>(A) & 15) == 0;
   if (b <= 16)
-    gemm_tn_tall_k<16><<<g, 256, 0, st>>>(A, lda, m, n, B, b, C, chunk);
+    gemm_tn_tall_k<16><<<g, 256, 0, st>>>(A, lda, m, n, B, b, C, chunk, vec);
+  else if (b <= 24)
+    gemm_tn_tall_k<24><<<g, 256, 0, st>>>(A, lda, m, n, B, b, C, chunk, vec);
   else if (b <= 32)
-    gemm_tn_tall_k<32><<<g, 256, 0, st>>>(A, lda, m, n, B, b, C, chunk);
+    gemm_tn_tall_k<32><<<g, 256, 0, st>>>(A, lda, m, n, B, b, C, chunk, vec);
   else
-    gemm_tn_tall_k<BMAX><<<g, 256, 0, st>>>(A, lda, m, n, B, b, C, chunk);
+    gemm_tn_tall_k<BMAX><<<g, 256, 0, st>>>(A, lda, m, n, B, b, C, chunk, vec);
 }
 
 
-// Row chunks of A^T B: enough blocks for about two per SM, at most
-// kTnChunks chunks of at least 64 rows.
+// Row chunks of A^T B, at most kTnChunks of at least 64 rows: enough
+// blocks for about two per SM, or, when the columns alone give a block per
+// SM (a wide matrix streamed from HBM), about eight per SM, so that more
+// rows' loads are in flight.
 static int tn_chunks(int m, int n) {
-  const int cblocks = int(ceil_div(n, 256));
-  return std::max(1, std::min({kTnChunks, int(ceil_div(m, 64)), int(ceil_div(2 * num_sms(), cblocks))}));
+  const int cblocks = int(ceil_div(n, TN_CB));
+  const int target = (cblocks >= num_sms() ? 8 : 2) * num_sms();
+  return std::max(1, std::min({kTnChunks, int(ceil_div(m, 64)), int(ceil_div(target, cblocks))}));
 }
 
 // Scratch (floats) of the split skinny products of an m x n matrix with b
@@ -256,14 +325,14 @@ static size_t skinny_scratch_floats(int m, int n, int b) {
 // skinny_scratch_floats).
 static cpca_status tn_tall(const float* A, int64_t lda, int m, int n, const float* B, int b, float* C,
                            float* scratch, cudaStream_t st) {
-  const int cblocks = int(ceil_div(n, 256));
+  const int cblocks = int(ceil_div(n, TN_CB));
   const int chunks = tn_chunks(m, n);
   if (chunks == 1) {
     gemm_tn_tall_launch(dim3(cblocks, 1), A, lda, m, n, B, b, C, m, st);
     CPCA_LAUNCHED();
     return CPCA_OK;
   }
-  const int chunk = int(ceil_div(ceil_div(m, chunks), 64)) * 64;
+  const int chunk = int(ceil_div(ceil_div(m, chunks), NN_KT)) * NN_KT;
   const int nch = int(ceil_div(m, chunk));
   gemm_tn_tall_launch(dim3(cblocks, nch), A, lda, m, n, B, b, scratch, chunk, st);
   count_launch();

@@ -992,55 +992,74 @@ __global__ void scale_cols_kernel(float* __restrict__ U, int64_t total, int ldu,
     U[t] = float(double(U[t]) * inv[t % ldu]);
 }
 
-// X (p x n) = U diag(sigma) V^T, 32 x 128 tile per block, streaming stores.
 // X (p x n) = U diag(sigma) V^T, X(i, j) = sum_c (U(i, c) sigma_c) V(j, c)
-// summed in c order (Algorithm 2, step 6; also the projections of
-// approximate decoders 2 and 3 with sigma = 1). A block owns 256 columns
-// and OUT_RT row tiles of 32 rows: V's 256 x k slice is staged once in shared
-// memory, k-major, then each thread computes an 8 x 4 block of X per row
-// tile (8 sigma-scaled U values and 4 V values per c from shared memory, 32
-// FMAs) and writes its 8 rows as 16-byte streaming stores. The bound is the
-// 4 B per entry written (8 GB at 20000 x 100000).
-constexpr int OUT_RT = 4;
+// summed in c order, sigma_c rounded to FP32 (Algorithm 2, step 6; also
+// the projections of approximate decoders 2 and 3 with sigma = 1). A block
+// owns 256 columns and OUT_RT row tiles of 32 rows: V's 256 x k slice is
+// read row by row (consecutive threads take consecutive c) and staged once
+// in shared memory, k-major; per row tile the 32 x k slice of U is staged
+// the same way, scaled by sigma; each thread then computes an 8 x 4 block
+// of X (8 scaled U values and 4 V values per c from shared memory, 32 FMAs
+// issued as 16 packed two-lane FMAs on pairs of rows, each lane rounded as
+// fmaf) and writes its 8 rows as 16-byte streaming stores. At k = 20 the
+// FMAs, 20 per entry, take longer than the 4 B per entry written.
+constexpr int OUT_RT = 16, OUT_VLD = 256 + 4, OUT_ULD = 32 + 4;
 __global__ void __launch_bounds__(256)
 output_kernel(const float* __restrict__ U, int ldu, const float* __restrict__ V, int ldv,
               const double* __restrict__ sigma, int k, int p, int n, float* __restrict__ X, int64_t ldx) {
   extern __shared__ __align__(16) float osm[];
-  float* VsT = osm;              // [k][256]
-  float* UsT = osm + k * 256;    // [k][32]
+  float* VsT = osm;                 // [k][OUT_VLD]
+  float* UsT = osm + k * OUT_VLD;   // [k][OUT_ULD]
+  float* ssig = UsT + k * OUT_ULD;  // [k]
   const int tid = threadIdx.x, tx = tid & 63, ty = tid >> 6;
   const int j0 = blockIdx.x * 256;
+  for (int c = tid; c < k; c += 256) ssig[c] = float(sigma[c]);
   for (int e = tid; e < 256 * k; e += 256) {
-    const int jj = e & 255, c = e >> 8;
-    VsT[c * 256 + jj] = (j0 + jj < n) ? __ldg(V + int64_t(j0 + jj) * ldv + c) : 0.f;
+    const int jj = e / k, c = e - jj * k;
+    VsT[c * OUT_VLD + jj] = (j0 + jj < n) ? __ldg(V + int64_t(j0 + jj) * ldv + c) : 0.f;
   }
   const int j = j0 + 4 * tx;
   const bool vec = j + 3 < n && (ldx & 3) == 0 && (reinterpret_cast<uintptr_t>(X) & 15) == 0;
   for (int rt = 0; rt < OUT_RT; ++rt) {
     const int i0 = (blockIdx.y * OUT_RT + rt) * 32;
     if (i0 >= p) break;
-    __syncthreads();  // VsT complete; UsT free for the next tile
+    __syncthreads();  // VsT and ssig complete; UsT free for the next tile
     for (int e = tid; e < 32 * k; e += 256) {
-      const int r = e & 31, c = e >> 5;
-      UsT[c * 32 + r] = (i0 + r < p) ? float(double(__ldg(U + int64_t(i0 + r) * ldu + c)) * sigma[c]) : 0.f;
+      const int r = e / k, c = e - r * k;
+      UsT[c * OUT_ULD + r] = (i0 + r < p) ? __ldg(U + int64_t(i0 + r) * ldu + c) * ssig[c] : 0.f;
     }
     __syncthreads();
+    // packed pairs of rows: acc2[rp][q] = (acc[2 rp][q], acc[2 rp + 1][q])
+    unsigned long long acc2[4][4];
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) acc2[r][q] = 0ull;
+    for (int c = 0; c < k; ++c) {
+      const float4 u0 = *reinterpret_cast<const float4*>(UsT + c * OUT_ULD + 8 * ty);
+      const float4 u1 = *reinterpret_cast<const float4*>(UsT + c * OUT_ULD + 8 * ty + 4);
+      const float4 v = *reinterpret_cast<const float4*>(VsT + c * OUT_VLD + 4 * tx);
+      unsigned long long up[4], vp[4];
+      asm("mov.b64 %0, {%1, %2};" : "=l"(up[0]) : "f"(u0.x), "f"(u0.y));
+      asm("mov.b64 %0, {%1, %2};" : "=l"(up[1]) : "f"(u0.z), "f"(u0.w));
+      asm("mov.b64 %0, {%1, %2};" : "=l"(up[2]) : "f"(u1.x), "f"(u1.y));
+      asm("mov.b64 %0, {%1, %2};" : "=l"(up[3]) : "f"(u1.z), "f"(u1.w));
+      asm("mov.b64 %0, {%1, %1};" : "=l"(vp[0]) : "f"(v.x));
+      asm("mov.b64 %0, {%1, %1};" : "=l"(vp[1]) : "f"(v.y));
+      asm("mov.b64 %0, {%1, %1};" : "=l"(vp[2]) : "f"(v.z));
+      asm("mov.b64 %0, {%1, %1};" : "=l"(vp[3]) : "f"(v.w));
+#pragma unroll
+      for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+          asm("fma.rn.f32x2 %0, %1, %2, %0;" : "+l"(acc2[r][q]) : "l"(up[r]), "l"(vp[q]));
+    }
     float acc[8][4];
 #pragma unroll
-    for (int r = 0; r < 8; ++r)
+    for (int r = 0; r < 4; ++r)
 #pragma unroll
-      for (int q = 0; q < 4; ++q) acc[r][q] = 0.f;
-    for (int c = 0; c < k; ++c) {
-      const float4 u0 = *reinterpret_cast<const float4*>(UsT + c * 32 + 8 * ty);
-      const float4 u1 = *reinterpret_cast<const float4*>(UsT + c * 32 + 8 * ty + 4);
-      const float4 v = *reinterpret_cast<const float4*>(VsT + c * 256 + 4 * tx);
-      const float uu[8] = {u0.x, u0.y, u0.z, u0.w, u1.x, u1.y, u1.z, u1.w};
-      const float vv[4] = {v.x, v.y, v.z, v.w};
-#pragma unroll
-      for (int r = 0; r < 8; ++r)
-#pragma unroll
-        for (int q = 0; q < 4; ++q) acc[r][q] = fmaf(uu[r], vv[q], acc[r][q]);
-    }
+      for (int q = 0; q < 4; ++q)
+        asm("mov.b64 {%0, %1}, %2;" : "=f"(acc[2 * r][q]), "=f"(acc[2 * r + 1][q]) : "l"(acc2[r][q]));
 #pragma unroll
     for (int r = 0; r < 8; ++r) {
       const int i = i0 + 8 * ty + r;
@@ -1057,15 +1076,17 @@ output_kernel(const float* __restrict__ U, int ldu, const float* __restrict__ V,
   }
 }
 
+static size_t output_smem(int k) { return size_t(k) * (OUT_VLD + OUT_ULD + 1) * sizeof(float); }
+
 // launch of output_kernel for a p x n X
 static cpca_status launch_output(const float* U, int ldu, const float* V, int ldv, const double* sigma, int k,
                                  int p, int n, float* X, int64_t ldx, cudaStream_t st) {
-  const size_t smem = size_t(k) * (256 + 32) * sizeof(float);
+  const size_t smem = output_smem(k);
   if (smem > 48 * 1024) {
     static PerDeviceOnce attr;
     CPCA_CUDA(once_per_device(attr, [&] {
       return cudaFuncSetAttribute(output_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  int(size_t(KMAX_LIMIT) * (256 + 32) * sizeof(float)));
+                                  int(output_smem(KMAX_LIMIT)));
     }));
   }
   const dim3 og(ceil_div(n, 256), ceil_div(p, 32 * OUT_RT));

@@ -865,24 +865,48 @@ def main():
     if not args.no_extras and world == 1:
         projections_big = projections_measure(M, torch, Yd, out, load_peaks())
 
-    # ---------------- end to end: pinned host input, result read back
+    # ---------------- end to end: pinned host input, result read back.
+    # Double-buffered as a serving loop would run it: step s + 1's 8 GB
+    # input is copied in from pinned host memory on a second stream while
+    # step s computes (into the other of two device buffers, once step
+    # s - 1 is done with it), and each step's X is written by the decoder's
+    # output kernel straight into a pinned host buffer. Every step's copy in
+    # and write out lies inside the timed region, which runs from before the
+    # first copy to the end of the last step.
     Yh = Yd.cpu().pin_memory()
     Xh = torch.empty(cfg["p"], cfg["n"], dtype=torch.float32).pin_memory()
     del out
     torch.cuda.empty_cache()
-    ev2 = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-           for _ in range(args.steps)]
+    ybuf = [Yd, torch.empty_like(Yd)]
+    copy_stream = torch.cuda.Stream(device=dev)
+    ready = [torch.cuda.Event() for _ in range(args.steps)]
+    done = [torch.cuda.Event() for _ in range(args.steps)]
+    e_start = torch.cuda.Event(enable_timing=True)
+    e_end = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     barrier()
+    e_start.record(stream)
+    copy_stream.wait_event(e_start)
+    with torch.cuda.stream(copy_stream):
+        ybuf[0].copy_(Yh, non_blocking=True)
+        ready[0].record(copy_stream)
     for s_ in range(args.steps):
+        if s_ + 1 < args.steps:
+            if s_ >= 1:
+                copy_stream.wait_event(done[s_ - 1])  # the buffer step s_ - 1 read
+            with torch.cuda.stream(copy_stream):
+                ybuf[(s_ + 1) % 2].copy_(Yh, non_blocking=True)
+                ready[s_ + 1].record(copy_stream)
         flush.zero_()
-        ev2[s_][0].record(stream)
-        Yin = Yh.to(dev, non_blocking=True)
-        o = step(Yin, Xh)  # X written straight into the pinned host buffer
-        ev2[s_][1].record(stream)
-        del Yin, o
+        stream.wait_event(ready[s_])
+        o = step(ybuf[s_ % 2], Xh)  # X written straight into the pinned host buffer
+        done[s_].record(stream)
+        e_end[s_].record(stream)
+        del o
     barrier()
-    e2e_ms = [a_.elapsed_time(b_) for a_, b_ in ev2]
-    e2e_s = sum(e2e_ms) / 1000.0
+    e2e_ms = [e_start.elapsed_time(e_end[0])] + [e_end[i - 1].elapsed_time(e_end[i])
+                                                 for i in range(1, args.steps)]
+    e2e_s = e_start.elapsed_time(e_end[-1]) / 1000.0
+    del ybuf
 
     total_s, e2e_s = max_over_ranks(dist, [total_s, e2e_s], dev)
     units = cfg["J"] * args.steps * world
@@ -903,7 +927,9 @@ def main():
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic", "config": config_dict(cfg, args.workload),
         "e2e": {"value": units / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(Yh.numel() * 4),
-                "d2h_bytes_per_step": int(Xh.numel() * 4), "steps_ms": [round(v, 2) for v in e2e_ms]},
+                "d2h_bytes_per_step": int(Xh.numel() * 4), "steps_ms": [round(v, 2) for v in e2e_ms],
+                "pipelining": "step s+1's input copied in on a second stream while step s computes; "
+                              "X written into pinned host memory by the output kernel"},
         "steps_ms": [round(v, 2) for v in step_ms],
         "gpu_launches": int(gpu_launches),
         "roofline": roof,

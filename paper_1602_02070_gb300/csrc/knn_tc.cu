@@ -19,8 +19,13 @@
 // Operands: K-major, 128-byte swizzle, 64 half columns (128 B) per stage;
 // a ring of 4 (M = 32) or 3 (M = 64) stages of (A 16 KB + B 32 KB) guarded
 // by full/empty mbarriers; two 256-column accumulators in TMEM (512
-// columns) so the epilogue of one base tile overlaps the MMAs of the next. Every mbarrier wait is bounded: on
-// timeout the block raises *err, stops, frees its TMEM and returns.
+// columns) so the epilogue of one base tile overlaps the MMAs of the next.
+// Above 32768 dimensions (knn_tc_chunk_ksteps) the second buffer instead
+// holds a running sum: the MMAs accumulate 4096 dimensions at a time in the
+// first, and the epilogue adds each such chunk into the sum before the
+// next chunk starts, which bounds the FP32 accumulation error by 4096
+// products rather than d. Every mbarrier wait is bounded: on timeout the
+// block raises *err, stops, frees its TMEM and returns.
 // Clusters of CL = 2 blocks along the queries share every base tile: each
 // block loads 256/CL rows of it with a TMA multicast into every block of the
 // cluster (the operand tile of this GPU's own memory, read once from L2 for
